@@ -1,0 +1,260 @@
+"""FP64 CPU oracle for the STARRED loss and gradient (arXiv 2402.08725).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(the CUDA library in ``paper_2402_08725_gb300`` and its binding) never imports
+it, and the two share no code: the arithmetic lives in ``starred_oracle.c``
+(plain C, double precision, literal operator order) and this module only
+marshals numpy arrays into it.
+
+Every function converts its inputs to float64 first, so the oracle evaluates
+the exact loss of the float32 values the GPU receives.
+
+Functions and the passages they follow:
+  conv_same / conv_same_adjoint   S_i, the narrow-PSF convolution (Eq. 8, Eq. 10)
+  downsample / downsample_adjoint D, the block-sum subsampling (Eq. 1)
+  starlet_analysis / _adjoint     Phi^T, the starlet transform of the prior (Eq. 6)
+  starlet_prior                   lambda ||W o Phi^T h||_1 and its subgradient (Eq. 6, Eq. 11)
+  deconv_model / deconv_loss_grad the two-channel multi-epoch model and loss (Eq. 9-11)
+  moffat                          the analytic part of the narrow PSF (Eq. 2)
+  psf_model / psf_loss_grad       PSF reconstruction (Eq. 2-4, Eq. 7)
+  optim_step                      AdaBelief / Adam update used by the optimiser (sec. 2.4)
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "starred_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def _lib_path() -> str:
+    with open(_SRC, "rb") as fh:
+        digest = hashlib.sha1(fh.read()).hexdigest()[:12]
+    return os.path.join(_BUILD, f"liborc_{os.uname().machine}_{digest}.so")
+
+
+def build() -> str:
+    """Compile the C oracle (gcc, -O2, OpenMP) if it is not built yet; return the .so path."""
+    path = _lib_path()
+    if os.path.exists(path):
+        return path
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, path)
+    return path
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i, d, sz = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        sig = {
+            "orc_version": ([], i),
+            "orc_max_threads": ([], i),
+            "orc_conv_same": ([i, i, _dp, _dp, _dp], i),
+            "orc_conv_same_adjoint": ([i, i, _dp, _dp, _dp], i),
+            "orc_downsample": ([i, i, _dp, _dp], i),
+            "orc_downsample_adjoint": ([i, i, _dp, _dp], i),
+            "orc_starlet_valid": ([i, i], i),
+            "orc_starlet_analysis": ([i, i, _dp, _dp], i),
+            "orc_starlet_adjoint": ([i, i, _dp, _dp], i),
+            "orc_starlet_prior": ([i, i, d, _dp, _dp, _dp, _dp], i),
+            "orc_add_gaussian": ([i, d, d, d, _dp], i),
+            "orc_deconv_param_count": ([i, i, i, i], sz),
+            "orc_deconv_model": ([i, i, i, i, i, _dp, _dp, _dp], i),
+            "orc_deconv_loss_grad": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
+            "orc_moffat": ([i, d, d, _dp, _dp, _dp], i),
+            "orc_psf_param_count": ([i, i, i], sz),
+            "orc_psf_model": ([i, i, i, _dp, _dp], i),
+            "orc_psf_loss_grad": ([i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
+            "orc_optim_step": ([i, ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.c_long, _dp, d, d, d, _dp, _dp], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+# --- building blocks -------------------------------------------------------
+
+def conv_same(x, s):
+    """S: out[u] = sum_q s[q] x[u - q + o], o = K//2, zero padding, F x F output."""
+    x, s = _f64(x), _f64(s)
+    F, K = x.shape[0], s.shape[0]
+    out = np.empty((F, F))
+    _check(_load().orc_conv_same(F, K, _ptr(x), _ptr(s), _ptr(out)), "conv_same")
+    return out
+
+
+def conv_same_adjoint(y, s):
+    y, s = _f64(y), _f64(s)
+    F, K = y.shape[0], s.shape[0]
+    out = np.empty((F, F))
+    _check(_load().orc_conv_same_adjoint(F, K, _ptr(y), _ptr(s), _ptr(out)), "conv_same_adjoint")
+    return out
+
+
+def downsample(x, f: int):
+    x = _f64(x)
+    N = x.shape[0] // f
+    out = np.empty((N, N))
+    _check(_load().orc_downsample(N, f, _ptr(x), _ptr(out)), "downsample")
+    return out
+
+
+def downsample_adjoint(e, f: int):
+    e = _f64(e)
+    N = e.shape[0]
+    out = np.empty((N * f, N * f))
+    _check(_load().orc_downsample_adjoint(N, f, _ptr(e), _ptr(out)), "downsample_adjoint")
+    return out
+
+
+def starlet_valid(F: int, J: int) -> bool:
+    return bool(_load().orc_starlet_valid(F, J))
+
+
+def starlet_analysis(h, J: int):
+    """Planes [w_1, ..., w_{J-1}, c_{J-1}] of the B3 a trous transform of h."""
+    h = _f64(h)
+    F = h.shape[0]
+    out = np.empty((J, F, F))
+    _check(_load().orc_starlet_analysis(F, J, _ptr(h), _ptr(out)), "starlet_analysis")
+    return out
+
+
+def starlet_adjoint(y):
+    y = _f64(y)
+    J, F = y.shape[0], y.shape[1]
+    out = np.empty((F, F))
+    _check(_load().orc_starlet_adjoint(F, J, _ptr(y), _ptr(out)), "starlet_adjoint")
+    return out
+
+
+def starlet_prior(h, J: int, lam: float, W, grad: bool = True):
+    h, W = _f64(h), _f64(W)
+    F = h.shape[0]
+    p = np.zeros(1)
+    g = np.empty((F, F)) if grad else None
+    _check(_load().orc_starlet_prior(F, J, float(lam), _ptr(W), _ptr(h), _ptr(p), _ptr(g)), "starlet_prior")
+    return (float(p[0]), g) if grad else float(p[0])
+
+
+def add_gaussian(img, amp: float, ux: float, uy: float):
+    img = _f64(img).copy()
+    _check(_load().orc_add_gaussian(img.shape[0], float(amp), float(ux), float(uy), _ptr(img)), "add_gaussian")
+    return img
+
+
+# --- deconvolution (Eq. 9-11) ----------------------------------------------
+
+def deconv_param_count(E: int, N: int, f: int, M: int) -> int:
+    return int(_load().orc_deconv_param_count(E, N, f, M))
+
+
+def deconv_model(E, N, f, K, M, s, params):
+    s, params = _f64(s), _f64(params)
+    out = np.empty((E, N, N))
+    _check(_load().orc_deconv_model(E, N, f, K, M, _ptr(s), _ptr(params), _ptr(out)), "deconv_model")
+    return out
+
+
+def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, nthreads=0):
+    """Return (loss, parts[chi2, prior], grad or None, chi2 per epoch)."""
+    d, sigma, s, W, params = _f64(d), _f64(sigma), _f64(s), _f64(W), _f64(params)
+    n = deconv_param_count(E, N, f, M)
+    if params.size != n:
+        raise ValueError(f"params has {params.size} values, expected {n}")
+    parts = np.zeros(2)
+    g = np.empty(n) if grad else None
+    chi = np.empty(E)
+    rc = _load().orc_deconv_loss_grad(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W),
+                                      _ptr(params), _ptr(parts), _ptr(g), _ptr(chi), int(nthreads))
+    _check(rc, "deconv_loss_grad")
+    return float(parts.sum()), parts, g, chi
+
+
+# --- PSF reconstruction (Eq. 2-4, 7) ----------------------------------------
+
+def moffat(F: int, alpha: float, beta: float):
+    m, da, db = np.empty((F, F)), np.empty((F, F)), np.empty((F, F))
+    _check(_load().orc_moffat(F, float(alpha), float(beta), _ptr(m), _ptr(da), _ptr(db)), "moffat")
+    return m, da, db
+
+
+def psf_param_count(S: int, N: int, f: int) -> int:
+    return int(_load().orc_psf_param_count(S, N, f))
+
+
+def psf_model(S, N, f, params):
+    params = _f64(params)
+    out = np.empty((S, N, N))
+    _check(_load().orc_psf_model(S, N, f, _ptr(params), _ptr(out)), "psf_model")
+    return out
+
+
+def psf_loss_grad(S, N, f, J, lam, t, sigma, W, params, grad=True, nthreads=0):
+    t, sigma, W, params = _f64(t), _f64(sigma), _f64(W), _f64(params)
+    n = psf_param_count(S, N, f)
+    if params.size != n:
+        raise ValueError(f"params has {params.size} values, expected {n}")
+    parts = np.zeros(2)
+    g = np.empty(n) if grad else None
+    rc = _load().orc_psf_loss_grad(S, N, f, J, float(lam), _ptr(t), _ptr(sigma), _ptr(W), _ptr(params),
+                                   _ptr(parts), _ptr(g), int(nthreads))
+    _check(rc, "psf_loss_grad")
+    return float(parts.sum()), parts, g
+
+
+# --- optimiser ----------------------------------------------------------------
+
+ADABELIEF, ADAM = 0, 1
+
+
+def optim_step(kind, theta, g, m, v, t, lr, beta1, beta2, eps, lo, hi):
+    """One in-place update of theta, m, v (all float64 arrays). t is 1-based."""
+    for a in (theta, g, m, v, lr, lo, hi):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("optim_step wants contiguous float64 arrays")
+    rc = _load().orc_optim_step(int(kind), theta.size, _ptr(theta), _ptr(g), _ptr(m), _ptr(v), int(t), _ptr(lr),
+                                float(beta1), float(beta2), float(eps), _ptr(lo), _ptr(hi))
+    _check(rc, "optim_step")

@@ -1,0 +1,725 @@
+/*
+ * FP64 CPU oracle for the STARRED loss and gradient (Millon et al., arXiv 2402.08725).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  The product path (the CUDA
+ * library and its Python binding) never calls it and shares no code with it.
+ *
+ * Everything here is written literally, in the paper's operator order, in
+ * double precision:
+ *   - the model is rasterised at full fine resolution (no truncation of the
+ *     Gaussians),
+ *   - the narrow-PSF convolution S is the plain double sum over the fine grid,
+ *   - D is the plain f x f block sum,
+ *   - every adjoint is the explicit transpose of its forward step (scatter
+ *     form), not a re-derived gather.
+ * It is slow on purpose; a reader can check each function against the cited
+ * equation by eye.
+ *
+ * Conventions (the paper leaves these open; the readings are fixed here):
+ *   fine grid F = f*N; arrays are [row][col] row-major; a 2-vector (x, y) has
+ *   x along columns.  Fine pixel u has data coordinate (u + 0.5)/f - 0.5; the
+ *   stamp centre (N-1)/2 maps to u0 = (F-1)/2, so a source at offset c (data px
+ *   from the stamp centre) sits at fine coordinate u0 + f*c.
+ *   PSF kernels have odd or even size K with origin o = K/2 (integer division);
+ *   S is a true convolution (kernel flipped) with zero padding, output F x F.
+ *   D is a flux-conserving block SUM over f x f fine pixels.
+ *   The narrow Gaussian r has FWHM 2 fine px (Eq. 1, sec. 2.1), point-sampled:
+ *   g(v) = exp(-|v|^2 / (2 sigma^2)) / (2 pi sigma^2), sigma = 1/sqrt(2 ln 2).
+ *   The starlet is the isotropic undecimated (a trous) B3-spline transform,
+ *   filter [1,4,6,4,1]/16 with holes 2^j at level j, whole-sample mirror borders.
+ *   J counts all planes (J-1 detail planes, penalised, plus one coarse plane,
+ *   not penalised).
+ *   Gamma_i is the spatially constant background of Eq. 9 (sec. 2.2), added
+ *   after D as f^2 * Gamma_i per data pixel.
+ *   Noise: w = 1/sigma^2 (Eq. 10: C diagonal); sigma = +inf masks a pixel (w = 0).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_SHAPE 2
+#define ORC_ERR_OOM 5
+
+static const double B3[5] = {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};
+
+/* sigma of the narrow Gaussian: FWHM 2 fine px (Eq. 1, sec. 2.1). */
+static double gauss_sigma(void) { return 2.0 / (2.0 * sqrt(2.0 * log(2.0))); }
+
+/* 2-D point-sampled unit-flux Gaussian value at offset (vx, vy). */
+static double gauss2(double vx, double vy) {
+    double s = gauss_sigma();
+    return exp(-(vx * vx + vy * vy) / (2.0 * s * s)) / (2.0 * M_PI * s * s);
+}
+
+/* 1-D factor of the same Gaussian: gauss2(vx, vy) = gauss1(vx) * gauss1(vy). */
+static double gauss1(double v) {
+    double s = gauss_sigma();
+    return exp(-v * v / (2.0 * s * s)) / (sqrt(2.0 * M_PI) * s);
+}
+
+static int orc_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+    return nthreads;
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+int orc_version(void) { return 1; }
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* S: narrow-PSF convolution on the fine grid (Eq. 8 and Eq. 10, sec. 2.2).  */
+/* ------------------------------------------------------------------------- */
+
+/* out[u] = sum_q s[q] * x[u - q + o], zero outside [0,F)^2, o = K/2. */
+int orc_conv_same(int F, int K, const double *x, const double *s, double *out) {
+    if (F <= 0 || K <= 0) return ORC_ERR_SHAPE;
+    int o = K / 2;
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double acc = 0.0;
+            for (int qy = 0; qy < K; ++qy) {
+                int y = uy - qy + o;
+                if (y < 0 || y >= F) continue;
+                for (int qx = 0; qx < K; ++qx) {
+                    int xx = ux - qx + o;
+                    if (xx < 0 || xx >= F) continue;
+                    acc += s[qy * K + qx] * x[y * F + xx];
+                }
+            }
+            out[uy * F + ux] = acc;
+        }
+    return ORC_OK;
+}
+
+/* Transpose of orc_conv_same, written as the scatter of each forward term:
+ * every term s[q]*x[u-q+o] of out[u] sends s[q]*y[u] to position u-q+o. */
+int orc_conv_same_adjoint(int F, int K, const double *y, const double *s, double *out) {
+    if (F <= 0 || K <= 0) return ORC_ERR_SHAPE;
+    int o = K / 2;
+    memset(out, 0, sizeof(double) * (size_t)F * F);
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double yu = y[uy * F + ux];
+            if (yu == 0.0) continue;
+            for (int qy = 0; qy < K; ++qy) {
+                int vy = uy - qy + o;
+                if (vy < 0 || vy >= F) continue;
+                for (int qx = 0; qx < K; ++qx) {
+                    int vx = ux - qx + o;
+                    if (vx < 0 || vx >= F) continue;
+                    out[vy * F + vx] += s[qy * K + qx] * yu;
+                }
+            }
+        }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* D: block-sum downsampling (the subsampling arrow of Eq. 1) and its adjoint */
+/* ------------------------------------------------------------------------- */
+
+int orc_downsample(int N, int f, const double *x, double *out) {
+    if (N <= 0 || f <= 0) return ORC_ERR_SHAPE;
+    int F = f * N;
+    for (int py = 0; py < N; ++py)
+        for (int px = 0; px < N; ++px) {
+            double acc = 0.0;
+            for (int a = 0; a < f; ++a)
+                for (int b = 0; b < f; ++b) acc += x[(f * py + a) * F + (f * px + b)];
+            out[py * N + px] = acc;
+        }
+    return ORC_OK;
+}
+
+/* D^T: each data pixel's value is sent to every fine pixel of its block. */
+int orc_downsample_adjoint(int N, int f, const double *e, double *out) {
+    if (N <= 0 || f <= 0) return ORC_ERR_SHAPE;
+    int F = f * N;
+    memset(out, 0, sizeof(double) * (size_t)F * F);
+    for (int py = 0; py < N; ++py)
+        for (int px = 0; px < N; ++px)
+            for (int a = 0; a < f; ++a)
+                for (int b = 0; b < f; ++b) out[(f * py + a) * F + (f * px + b)] += e[py * N + px];
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Starlet transform Phi^T (Eq. 6, sec. 2.1): B3-spline a trous, mirror borders */
+/* ------------------------------------------------------------------------- */
+
+static int mirror(int t, int F) {
+    if (t < 0) return -t;
+    if (t > F - 1) return 2 * (F - 1) - t;
+    return t;
+}
+
+int orc_starlet_valid(int F, int J) {
+    if (J < 2 || F < 2) return 0;
+    /* widest hole used is 2 * 2^(J-2); single-bounce mirroring needs it <= F-1 */
+    return 2 * (1 << (J - 2)) <= F - 1;
+}
+
+/* out = H_j x: separable smoothing with holes 2^j, rows first then columns. */
+static void starlet_smooth(int F, int j, const double *x, double *tmp, double *out) {
+    int step = 1 << j;
+    for (int y = 0; y < F; ++y)
+        for (int xx = 0; xx < F; ++xx) {
+            double acc = 0.0;
+            for (int n = -2; n <= 2; ++n) acc += B3[n + 2] * x[y * F + mirror(xx + n * step, F)];
+            tmp[y * F + xx] = acc;
+        }
+    for (int y = 0; y < F; ++y)
+        for (int xx = 0; xx < F; ++xx) {
+            double acc = 0.0;
+            for (int m = -2; m <= 2; ++m) acc += B3[m + 2] * tmp[mirror(y + m * step, F) * F + xx];
+            out[y * F + xx] = acc;
+        }
+}
+
+/* out = H_j^T y, as the scatter transpose of the column pass then of the row pass. */
+static void starlet_smooth_adjoint(int F, int j, const double *y, double *tmp, double *out) {
+    int step = 1 << j;
+    memset(tmp, 0, sizeof(double) * (size_t)F * F);
+    for (int r = 0; r < F; ++r)
+        for (int xx = 0; xx < F; ++xx)
+            for (int m = -2; m <= 2; ++m) tmp[mirror(r + m * step, F) * F + xx] += B3[m + 2] * y[r * F + xx];
+    memset(out, 0, sizeof(double) * (size_t)F * F);
+    for (int r = 0; r < F; ++r)
+        for (int xx = 0; xx < F; ++xx)
+            for (int n = -2; n <= 2; ++n) out[r * F + mirror(xx + n * step, F)] += B3[n + 2] * tmp[r * F + xx];
+}
+
+/* Analysis A: out[0..J-2] = detail planes w_1..w_{J-1}, out[J-1] = coarse c_{J-1}.
+ * c_0 = h, c_{j+1} = H_j c_j, w_{j+1} = c_j - c_{j+1}. */
+int orc_starlet_analysis(int F, int J, const double *h, double *out) {
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t n = (size_t)F * F;
+    double *c = malloc(sizeof(double) * n), *cn = malloc(sizeof(double) * n), *tmp = malloc(sizeof(double) * n);
+    if (!c || !cn || !tmp) { free(c); free(cn); free(tmp); return ORC_ERR_OOM; }
+    memcpy(c, h, sizeof(double) * n);
+    for (int j = 0; j < J - 1; ++j) {
+        starlet_smooth(F, j, c, tmp, cn);
+        for (size_t k = 0; k < n; ++k) out[(size_t)j * n + k] = c[k] - cn[k];
+        memcpy(c, cn, sizeof(double) * n);
+    }
+    memcpy(out + (size_t)(J - 1) * n, c, sizeof(double) * n);
+    free(c); free(cn); free(tmp);
+    return ORC_OK;
+}
+
+/* Adjoint A^T of orc_starlet_analysis: y[0..J-2] pair with w_1..w_{J-1},
+ * y[J-1] with the coarse plane.  With T_j the gradient reaching c_j through
+ * w_{j+1} and c_{j+1}:  T_{J-1} = y_coarse,
+ * T_j = y_{j+1} + H_j^T (T_{j+1} - y_{j+1}),  A^T y = T_0. */
+int orc_starlet_adjoint(int F, int J, const double *y, double *out) {
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t n = (size_t)F * F;
+    double *T = malloc(sizeof(double) * n), *v = malloc(sizeof(double) * n), *tmp = malloc(sizeof(double) * n);
+    if (!T || !v || !tmp) { free(T); free(v); free(tmp); return ORC_ERR_OOM; }
+    memcpy(T, y + (size_t)(J - 1) * n, sizeof(double) * n);
+    for (int j = J - 2; j >= 0; --j) {
+        const double *yj = y + (size_t)j * n; /* pairs with w_{j+1} */
+        for (size_t k = 0; k < n; ++k) v[k] = T[k] - yj[k];
+        starlet_smooth_adjoint(F, j, v, tmp, T);
+        for (size_t k = 0; k < n; ++k) T[k] += yj[k];
+    }
+    memcpy(out, T, sizeof(double) * n);
+    free(T); free(v); free(tmp);
+    return ORC_OK;
+}
+
+/* Prior P = lambda * sum_{j=1}^{J-1} W_j * sum_u |w_j[u]| (Eq. 6 / Eq. 11),
+ * one weight per detail scale.  Returns P; writes dP/dh into grad (if not NULL),
+ * with the subgradient sign(0) = 0. */
+int orc_starlet_prior(int F, int J, double lam, const double *W, const double *h, double *prior, double *grad) {
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t n = (size_t)F * F;
+    double *planes = malloc(sizeof(double) * n * J);
+    if (!planes) return ORC_ERR_OOM;
+    int rc = orc_starlet_analysis(F, J, h, planes);
+    if (rc) { free(planes); return rc; }
+    double p = 0.0;
+    for (int j = 0; j < J - 1; ++j) {
+        double sj = 0.0;
+        for (size_t k = 0; k < n; ++k) sj += fabs(planes[(size_t)j * n + k]);
+        p += lam * W[j] * sj;
+    }
+    *prior = p;
+    if (grad) {
+        /* y_j = lambda W_j sign(w_j) for detail planes, 0 for the coarse plane */
+        for (int j = 0; j < J - 1; ++j)
+            for (size_t k = 0; k < n; ++k) {
+                double w = planes[(size_t)j * n + k];
+                planes[(size_t)j * n + k] = lam * W[j] * (w > 0 ? 1.0 : (w < 0 ? -1.0 : 0.0));
+            }
+        memset(planes + (size_t)(J - 1) * n, 0, sizeof(double) * n);
+        rc = orc_starlet_adjoint(F, J, planes, grad);
+    }
+    free(planes);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Point-source channel (Eq. 9, sec. 2.2; r_k of Eq. 3)                       */
+/* ------------------------------------------------------------------------- */
+
+/* out[u] += amp * g(u - (ux_c, uy_c)) over the whole fine grid. */
+int orc_add_gaussian(int F, double amp, double ux_c, double uy_c, double *out) {
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) out[uy * F + ux] += amp * gauss2(ux - ux_c, uy - uy_c);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Joint multi-epoch deconvolution: loss Eq. 11 (lambda_pts = 0), Eq. 9, 10   */
+/* ------------------------------------------------------------------------- */
+
+/* Packed parameters: [h F*F | a E*M | c M*2 | delta E*2 | Gamma E]. */
+static void deconv_offsets(int E, int N, int f, int M, size_t *oh, size_t *oa, size_t *oc, size_t *od, size_t *og,
+                           size_t *total) {
+    size_t F = (size_t)f * N;
+    *oh = 0;
+    *oa = F * F;
+    *oc = *oa + (size_t)E * M;
+    *od = *oc + (size_t)M * 2;
+    *og = *od + (size_t)E * 2;
+    *total = *og + (size_t)E;
+}
+
+size_t orc_deconv_param_count(int E, int N, int f, int M) {
+    size_t oh, oa, oc, od, og, t;
+    deconv_offsets(E, N, f, M, &oh, &oa, &oc, &od, &og, &t);
+    return t;
+}
+
+/* Fine coordinate of point source k in epoch i: u0 + f * (c_k + delta_i). */
+static void source_centre(int F, int f, const double *c, const double *dl, int k, int i, double *ux, double *uy) {
+    double u0 = 0.5 * (F - 1);
+    *ux = u0 + f * (c[2 * k + 0] + dl[2 * i + 0]);
+    *uy = u0 + f * (c[2 * k + 1] + dl[2 * i + 1]);
+}
+
+/* Model of epoch i on the data grid: M_i = D S_i (h + sum_k a_ki r_k) + f^2 Gamma_i. */
+static void deconv_model_epoch(int i, int N, int f, int K, int M, const double *s_i, const double *params,
+                               size_t oa, size_t oc, size_t od, size_t og, double *fimg, double *conv, double *model) {
+    int F = f * N;
+    size_t n = (size_t)F * F;
+    memcpy(fimg, params, sizeof(double) * n); /* h */
+    for (int k = 0; k < M; ++k) {
+        double ux, uy;
+        source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
+        orc_add_gaussian(F, params[oa + (size_t)i * M + k], ux, uy, fimg);
+    }
+    orc_conv_same(F, K, fimg, s_i, conv);
+    orc_downsample(N, f, conv, model);
+    double bg = (double)f * f * params[og + i];
+    for (int p = 0; p < N * N; ++p) model[p] += bg;
+}
+
+static double inv_var(double sigma) { return isinf(sigma) ? 0.0 : 1.0 / (sigma * sigma); }
+
+int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const double *params, double *model_out) {
+    if (E <= 0 || N <= 0 || f <= 0 || K <= 0 || M < 0) return ORC_ERR_SHAPE;
+    int F = f * N;
+    size_t oh, oa, oc, od, og, tot;
+    deconv_offsets(E, N, f, M, &oh, &oa, &oc, &od, &og, &tot);
+    size_t n = (size_t)F * F;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *fimg = malloc(sizeof(double) * n), *conv = malloc(sizeof(double) * n);
+        if (!fimg || !conv) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(static)
+            for (int i = 0; i < E; ++i)
+                deconv_model_epoch(i, N, f, K, M, s + (size_t)i * K * K, params, oa, oc, od, og, fimg, conv,
+                                   model_out + (size_t)i * N * N);
+        }
+        free(fimg); free(conv);
+    }
+    return err ? ORC_ERR_OOM : ORC_OK;
+}
+
+/* Loss and gradient of the deconvolution problem.
+ *   parts[0] = chi^2 term (Eq. 10), parts[1] = starlet prior on h (Eq. 11, first
+ *   prior term), loss = parts[0] + parts[1].
+ *   grad (nullable) is d loss / d params in the packed layout.
+ *   chi2_epoch (nullable) receives the chi^2 of each epoch. */
+int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d, const double *sigma,
+                         const double *s, const double *W, const double *params, double *parts, double *grad,
+                         double *chi2_epoch, int nthreads) {
+    if (E <= 0 || N <= 0 || f <= 0 || K <= 0 || M < 0) return ORC_ERR_SHAPE;
+    int F = f * N;
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t oh, oa, oc, od, og, tot;
+    deconv_offsets(E, N, f, M, &oh, &oa, &oc, &od, &og, &tot);
+    size_t n = (size_t)F * F;
+    int nt = orc_threads(nthreads);
+    double *chi = calloc((size_t)E, sizeof(double));
+    /* per-epoch gradient wrt the fine image f_i, summed into dh afterwards in epoch order */
+    double *gfine = grad ? malloc(sizeof(double) * n * (size_t)E) : NULL;
+    /* d loss / d (fine centre of source k in epoch i), reduced in fixed order below */
+    double *dcen = grad ? calloc((size_t)E * M * 2 + 1, sizeof(double)) : NULL;
+    if (!chi || (grad && (!gfine || !dcen))) { free(chi); free(gfine); free(dcen); return ORC_ERR_OOM; }
+    if (grad) memset(grad, 0, sizeof(double) * tot);
+    const double sg = gauss_sigma();
+    int err = 0;
+#pragma omp parallel num_threads(nt)
+    {
+        double *fimg = malloc(sizeof(double) * n), *conv = malloc(sizeof(double) * n);
+        double *model = malloc(sizeof(double) * (size_t)N * N), *e = malloc(sizeof(double) * (size_t)N * N);
+        double *ey = malloc(sizeof(double) * n);
+        if (!fimg || !conv || !model || !e || !ey) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int i = 0; i < E; ++i) {
+                const double *s_i = s + (size_t)i * K * K;
+                deconv_model_epoch(i, N, f, K, M, s_i, params, oa, oc, od, og, fimg, conv, model);
+                double c2 = 0.0;
+                for (int p = 0; p < N * N; ++p) {
+                    size_t ip = (size_t)i * N * N + p;
+                    double w = inv_var(sigma[ip]);
+                    double r = d[ip] - model[p];
+                    c2 += 0.5 * w * r * r;
+                    e[p] = -w * r; /* d chi^2 / d model */
+                }
+                chi[i] = c2;
+                if (!grad) continue;
+                /* dGamma_i = f^2 sum_p e_p */
+                double se = 0.0;
+                for (int p = 0; p < N * N; ++p) se += e[p];
+                grad[og + i] = (double)f * f * se;
+                /* d chi^2 / d f_i = S_i^T D^T e */
+                orc_downsample_adjoint(N, f, e, ey);
+                double *G = gfine + (size_t)i * n;
+                orc_conv_same_adjoint(F, K, ey, s_i, G);
+                /* point sources: d/da_ki and d/d(centre) through the Gaussian */
+                for (int k = 0; k < M; ++k) {
+                    double ux, uy;
+                    source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
+                    double aki = params[oa + (size_t)i * M + k];
+                    double ga = 0.0, gx = 0.0, gy = 0.0;
+                    for (int vy = 0; vy < F; ++vy)
+                        for (int vx = 0; vx < F; ++vx) {
+                            double gv = gauss2(vx - ux, vy - uy);
+                            double Gv = G[vy * F + vx];
+                            ga += Gv * gv;
+                            /* d g(v - u_c) / d u_c = g * (v - u_c) / sigma^2 */
+                            gx += Gv * gv * (vx - ux) / (sg * sg);
+                            gy += Gv * gv * (vy - uy) / (sg * sg);
+                        }
+                    grad[oa + (size_t)i * M + k] = ga;
+                    dcen[((size_t)i * M + k) * 2 + 0] = aki * gx;
+                    dcen[((size_t)i * M + k) * 2 + 1] = aki * gy;
+                }
+            }
+        }
+        free(fimg); free(conv); free(model); free(e); free(ey);
+    }
+    if (err) { free(chi); free(gfine); free(dcen); return ORC_ERR_OOM; }
+    if (grad) {
+        /* fine centre = u0 + f (c_k + delta_i): both chain factors are f */
+        for (int i = 0; i < E; ++i)
+            for (int k = 0; k < M; ++k)
+                for (int ax = 0; ax < 2; ++ax) {
+                    double v = f * dcen[((size_t)i * M + k) * 2 + ax];
+                    grad[oc + 2 * k + ax] += v;
+                    grad[od + 2 * i + ax] += v;
+                }
+    }
+    free(dcen);
+    double chi2 = 0.0;
+    for (int i = 0; i < E; ++i) chi2 += chi[i];
+    if (chi2_epoch) memcpy(chi2_epoch, chi, sizeof(double) * E);
+    double prior = 0.0;
+    double *gprior = grad ? malloc(sizeof(double) * n) : NULL;
+    int rc = orc_starlet_prior(F, J, lam, W, params + oh, &prior, gprior);
+    if (grad && rc == ORC_OK) {
+        for (size_t u = 0; u < n; ++u) {
+            double acc = gprior[u];
+            for (int i = 0; i < E; ++i) acc += gfine[(size_t)i * n + u];
+            grad[oh + u] = acc;
+        }
+    }
+    parts[0] = chi2;
+    parts[1] = prior;
+    free(gprior); free(chi); free(gfine);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* PSF reconstruction: Eq. 2 (Moffat + pixel grid), Eq. 3, Eq. 4, Eq. 7      */
+/* ------------------------------------------------------------------------- */
+
+/* Isotropic unit-flux Moffat on the F x F fine grid centred on pixel (F/2, F/2):
+ * m = (beta-1)/(pi alpha^2) (1 + rho^2/alpha^2)^(-beta); with its derivatives. */
+int orc_moffat(int F, double alpha, double beta, double *m, double *dm_dalpha, double *dm_dbeta) {
+    if (F <= 0 || !(alpha > 0) || !(beta > 1)) return ORC_ERR_ARG;
+    int cen = F / 2;
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double rho2 = (double)(ux - cen) * (ux - cen) + (double)(uy - cen) * (uy - cen);
+            double B = 1.0 + rho2 / (alpha * alpha);
+            double v = (beta - 1.0) / (M_PI * alpha * alpha) * pow(B, -beta);
+            size_t k = (size_t)uy * F + ux;
+            m[k] = v;
+            if (dm_dalpha) dm_dalpha[k] = v * (-2.0 / alpha + 2.0 * beta * rho2 / (alpha * alpha * alpha * B));
+            if (dm_dbeta) dm_dbeta[k] = v * (1.0 / (beta - 1.0) - log(B));
+        }
+    return ORC_OK;
+}
+
+/* Packed parameters: [b F*F | alpha, beta | a S | c S*2]  (S stars). */
+size_t orc_psf_param_count(int S, int N, int f) {
+    size_t F = (size_t)f * N;
+    return F * F + 2 + (size_t)S + (size_t)S * 2;
+}
+
+/* out[u] = sum_v s[v] g(u - v - shift): the narrow PSF convolved with the
+ * Gaussian r_k of Eq. 3 displaced by (sx, sy).  The 2-D Gaussian factorises
+ * exactly into 1-D factors, so the sum is taken over v_x, then over v_y. */
+static void star_blur(int F, const double *s, double sx, double sy, double *tmp, double *out) {
+    for (int vy = 0; vy < F; ++vy)
+        for (int ux = 0; ux < F; ++ux) {
+            double acc = 0.0;
+            for (int vx = 0; vx < F; ++vx) acc += s[vy * F + vx] * gauss1(ux - vx - sx);
+            tmp[vy * F + ux] = acc;
+        }
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double acc = 0.0;
+            for (int vy = 0; vy < F; ++vy) acc += tmp[vy * F + ux] * gauss1(uy - vy - sy);
+            out[uy * F + ux] = acc;
+        }
+}
+
+/* Literal transpose of star_blur (scatter of each term). */
+static void star_blur_adjoint(int F, const double *y, double sx, double sy, double *tmp, double *out) {
+    memset(tmp, 0, sizeof(double) * (size_t)F * F);
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux)
+            for (int vy = 0; vy < F; ++vy) tmp[vy * F + ux] += y[uy * F + ux] * gauss1(uy - vy - sy);
+    memset(out, 0, sizeof(double) * (size_t)F * F);
+    for (int vy = 0; vy < F; ++vy)
+        for (int ux = 0; ux < F; ++ux)
+            for (int vx = 0; vx < F; ++vx) out[vy * F + vx] += tmp[vy * F + ux] * gauss1(ux - vx - sx);
+}
+
+/* Derivative of star_blur with respect to the shift: d out / d sx and d sy.
+ * d/dsx g1(ux - vx - sx) = g1(.) (ux - vx - sx) / sigma^2. */
+static void star_blur_dshift(int F, const double *s, double sx, double sy, double *tmp, double *tmpd, double *dx,
+                             double *dy) {
+    double s2 = gauss_sigma() * gauss_sigma();
+    for (int vy = 0; vy < F; ++vy)
+        for (int ux = 0; ux < F; ++ux) {
+            double acc = 0.0, accd = 0.0;
+            for (int vx = 0; vx < F; ++vx) {
+                double t = ux - vx - sx;
+                double g = gauss1(t);
+                acc += s[vy * F + vx] * g;
+                accd += s[vy * F + vx] * g * t / s2;
+            }
+            tmp[vy * F + ux] = acc;
+            tmpd[vy * F + ux] = accd;
+        }
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double ax = 0.0, ay = 0.0;
+            for (int vy = 0; vy < F; ++vy) {
+                double t = uy - vy - sy;
+                double g = gauss1(t);
+                ax += tmpd[vy * F + ux] * g;
+                ay += tmp[vy * F + ux] * g * t / s2;
+            }
+            dx[uy * F + ux] = ax;
+            dy[uy * F + ux] = ay;
+        }
+}
+
+/* Narrow PSF s = m(alpha, beta) + b (Eq. 2). */
+static int psf_narrow(int F, const double *params, double *s, double *dma, double *dmb) {
+    size_t n = (size_t)F * F;
+    int rc = orc_moffat(F, params[n], params[n + 1], s, dma, dmb);
+    if (rc) return rc;
+    for (size_t k = 0; k < n; ++k) s[k] += params[k];
+    return ORC_OK;
+}
+
+/* Shift of star k's Gaussian relative to the PSF centre pixel F/2. */
+static void star_shift(int F, int f, const double *c, int k, double *sx, double *sy) {
+    double u0 = 0.5 * (F - 1);
+    *sx = u0 + f * c[2 * k + 0] - F / 2;
+    *sy = u0 + f * c[2 * k + 1] - F / 2;
+}
+
+/* Model stamps t_k = D(a_k * (s * r_k)) on the data grid (Eq. 3, no noise). */
+int orc_psf_model(int S, int N, int f, const double *params, double *model_out) {
+    int F = f * N;
+    size_t n = (size_t)F * F;
+    double *s = malloc(sizeof(double) * n);
+    if (!s) return ORC_ERR_OOM;
+    int rc = psf_narrow(F, params, s, NULL, NULL);
+    if (rc) { free(s); return rc; }
+    const double *a = params + n + 2, *c = params + n + 2 + S;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *tmp = malloc(sizeof(double) * n), *blur = malloc(sizeof(double) * n);
+        if (!tmp || !blur) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(static)
+            for (int k = 0; k < S; ++k) {
+                double sx, sy;
+                star_shift(F, f, c, k, &sx, &sy);
+                star_blur(F, s, sx, sy, tmp, blur);
+                for (size_t u = 0; u < n; ++u) blur[u] *= a[k];
+                orc_downsample(N, f, blur, model_out + (size_t)k * N * N);
+            }
+        }
+        free(tmp); free(blur);
+    }
+    free(s);
+    return err ? ORC_ERR_OOM : ORC_OK;
+}
+
+/* Loss (Eq. 7) and gradient of the PSF reconstruction. parts = {chi^2, prior on b}. */
+int orc_psf_loss_grad(int S, int N, int f, int J, double lam, const double *t, const double *sigma, const double *W,
+                      const double *params, double *parts, double *grad, int nthreads) {
+    if (S <= 0 || N <= 0 || f <= 0) return ORC_ERR_SHAPE;
+    int F = f * N;
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t n = (size_t)F * F;
+    size_t tot = orc_psf_param_count(S, N, f);
+    int nt = orc_threads(nthreads);
+    double *s = malloc(sizeof(double) * n), *dma = malloc(sizeof(double) * n), *dmb = malloc(sizeof(double) * n);
+    double *chi = calloc((size_t)S, sizeof(double));
+    double *gs_star = grad ? calloc(n * (size_t)S, sizeof(double)) : NULL;
+    if (!s || !dma || !dmb || !chi || (grad && !gs_star)) {
+        free(s); free(dma); free(dmb); free(chi); free(gs_star);
+        return ORC_ERR_OOM;
+    }
+    int rc = psf_narrow(F, params, s, dma, dmb);
+    if (rc) { free(s); free(dma); free(dmb); free(chi); free(gs_star); return rc; }
+    if (grad) memset(grad, 0, sizeof(double) * tot);
+    const double *a = params + n + 2, *c = params + n + 2 + S;
+    int err = 0;
+#pragma omp parallel num_threads(nt)
+    {
+        double *tmp = malloc(sizeof(double) * n), *tmpd = malloc(sizeof(double) * n);
+        double *blur = malloc(sizeof(double) * n), *ey = malloc(sizeof(double) * n);
+        double *dx = malloc(sizeof(double) * n), *dy = malloc(sizeof(double) * n);
+        double *model = malloc(sizeof(double) * (size_t)N * N), *e = malloc(sizeof(double) * (size_t)N * N);
+        if (!tmp || !tmpd || !blur || !ey || !dx || !dy || !model || !e) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int k = 0; k < S; ++k) {
+                double sx, sy;
+                star_shift(F, f, c, k, &sx, &sy);
+                star_blur(F, s, sx, sy, tmp, blur);
+                for (size_t u = 0; u < n; ++u) ey[u] = a[k] * blur[u];
+                orc_downsample(N, f, ey, model);
+                double c2 = 0.0;
+                for (int p = 0; p < N * N; ++p) {
+                    size_t ip = (size_t)k * N * N + p;
+                    double w = inv_var(sigma[ip]);
+                    double r = t[ip] - model[p];
+                    c2 += 0.5 * w * r * r;
+                    e[p] = -w * r;
+                }
+                chi[k] = c2;
+                if (!grad) continue;
+                orc_downsample_adjoint(N, f, e, ey);
+                /* d/da_k = <D^T e, s * r_k> */
+                double ga = 0.0;
+                for (size_t u = 0; u < n; ++u) ga += ey[u] * blur[u];
+                grad[n + 2 + k] = ga;
+                /* d/dc_k = f a_k <D^T e, d(s * r_k)/d shift> */
+                star_blur_dshift(F, s, sx, sy, tmp, tmpd, dx, dy);
+                double gx = 0.0, gy = 0.0;
+                for (size_t u = 0; u < n; ++u) { gx += ey[u] * dx[u]; gy += ey[u] * dy[u]; }
+                grad[n + 2 + S + 2 * k + 0] = f * a[k] * gx;
+                grad[n + 2 + S + 2 * k + 1] = f * a[k] * gy;
+                /* d/ds from this star: a_k B_k^T D^T e */
+                double *gsk = gs_star + (size_t)k * n;
+                star_blur_adjoint(F, ey, sx, sy, tmp, gsk);
+                for (size_t u = 0; u < n; ++u) gsk[u] *= a[k];
+            }
+        }
+        free(tmp); free(tmpd); free(blur); free(ey); free(dx); free(dy); free(model); free(e);
+    }
+    if (err) { free(s); free(dma); free(dmb); free(chi); free(gs_star); return ORC_ERR_OOM; }
+    double chi2 = 0.0;
+    for (int k = 0; k < S; ++k) chi2 += chi[k];
+    double prior = 0.0;
+    double *gprior = grad ? malloc(sizeof(double) * n) : NULL;
+    rc = orc_starlet_prior(F, J, lam, W, params, &prior, gprior);
+    if (grad && rc == ORC_OK) {
+        double galpha = 0.0, gbeta = 0.0;
+        for (size_t u = 0; u < n; ++u) {
+            double gs = 0.0;
+            for (int k = 0; k < S; ++k) gs += gs_star[(size_t)k * n + u];
+            grad[u] = gs + gprior[u]; /* s = m + b: ds/db = 1 */
+            galpha += gs * dma[u];
+            gbeta += gs * dmb[u];
+        }
+        grad[n] = galpha;
+        grad[n + 1] = gbeta;
+    }
+    parts[0] = chi2;
+    parts[1] = prior;
+    free(gprior); free(s); free(dma); free(dmb); free(chi); free(gs_star);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Optimiser: AdaBelief (Zhuang et al. 2020, the published update) and Adam, */
+/* followed by projection onto per-element lower bounds.  Used as in sec. 2.4 */
+/* ------------------------------------------------------------------------- */
+
+/* kind 0 = AdaBelief, 1 = Adam.  t is the 1-based step index of this update.
+ * lo[k] = -inf for unconstrained elements.  hi[k] = +inf likewise. */
+int orc_optim_step(int kind, long n, double *theta, const double *g, double *m, double *v, long t, const double *lr,
+                   double beta1, double beta2, double eps, const double *lo, const double *hi) {
+    if (n < 0 || t < 1) return ORC_ERR_ARG;
+    double bc1 = 1.0 - pow(beta1, (double)t), bc2 = 1.0 - pow(beta2, (double)t);
+    for (long k = 0; k < n; ++k) {
+        m[k] = beta1 * m[k] + (1.0 - beta1) * g[k];
+        if (kind == 0) {
+            double dev = g[k] - m[k];
+            v[k] = beta2 * v[k] + (1.0 - beta2) * dev * dev + eps;
+        } else {
+            v[k] = beta2 * v[k] + (1.0 - beta2) * g[k] * g[k];
+        }
+        double mh = m[k] / bc1, vh = v[k] / bc2;
+        double th = theta[k] - lr[k] * mh / (sqrt(vh) + eps);
+        if (th < lo[k]) th = lo[k];
+        if (th > hi[k]) th = hi[k];
+        theta[k] = th;
+    }
+    return ORC_OK;
+}
