@@ -1,0 +1,488 @@
+#!/usr/bin/env python
+"""Throughput of the STARRED loss-and-gradient hot path on GB300.
+
+Default workload: the uneven batch of 256 SN + host fields (stamp sizes
+32..128, 10..500 epochs each, f = 2, 64x64 narrow PSFs, 1 point source,
+4-6 starlet scales) together with the 16-star PSF reconstruction (64x64
+stamps, f = 2, 5 scales).  One step = one loss-and-gradient evaluation of
+every field of the batch and of the PSF fit, plus the fused AdaBelief update
+of all their parameters.  The metric is epoch-pixels per second: data pixels
+of all epochs (and star stamps) evaluated per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank evaluates its own
+batch (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2402_08725_gb300 import synthetic as syn  # noqa: E402
+
+WORKLOADS = {
+    "config4": "uneven batch of 256 SN+host fields (N 32-128, E 10-500, f=2, K=64, M=1, J 4-6) "
+               "+ 16-star PSF fit (64x64, f=2, J=5)",
+    "config3": "lensed quasar: 300 epochs of 64x64, f=2, K=64, M=4, J=4",
+    "config1": "joint deconvolution: 4 epochs of 32x32, f=2, K=64, M=2, J=4",
+    "config5": "JWST-like: 6 frames of 512x512, f=3, K=255, M=40, J=6",
+    "config2": "PSF fit: 16 stars of 64x64, f=2, J=5",
+}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config4")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--fields", type=int, default=0,
+                    help="config4 only: evaluate the first FIELDS fields (a smaller case for profiling)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# --- workloads ---------------------------------------------------------------------------
+
+def make_workload(name, rank, n_fields=0):
+    """(deconv fields, psf problem or None); rank shifts the seeds (weak scaling)."""
+    seed_shift = 7919 * rank
+    if name == "config4":
+        sel = range(n_fields) if n_fields else None
+        fields = syn.config4(seed=syn.BASE_SEED + 4 + seed_shift, fields=sel)
+        return fields, syn.config2(seed=syn.BASE_SEED + 2 + seed_shift)
+    if name == "config3":
+        return [syn.config3(seed=syn.BASE_SEED + 3 + seed_shift)], None
+    if name == "config1":
+        return [syn.config1(seed=syn.BASE_SEED + 1 + seed_shift)], None
+    if name == "config5":
+        return [syn.config5(seed=syn.BASE_SEED + 5 + seed_shift)], None
+    if name == "config2":
+        return [], syn.config2(seed=syn.BASE_SEED + 2 + seed_shift)
+    raise ValueError(name)
+
+
+def units_of(fields, pb):
+    u = sum(fd.epoch_pixels for fd in fields)
+    if pb is not None:
+        u += pb.epoch_pixels
+    return u
+
+
+def folded_taps_1d(N, f, K):
+    """sum over data pixels p of #{fine u in [0, F): f p - u in the folded-kernel support}."""
+    o = K // 2
+    t_lo, t_hi = -o - f + 1, K - 1 - o
+    F = f * N
+    p = np.arange(N)
+    lo = np.maximum(f * p - t_hi, 0)
+    hi = np.minimum(f * p - t_lo, F - 1)
+    return int(np.maximum(hi - lo + 1, 0).sum())
+
+
+def fwd_flops(fields):
+    """Algorithmic FLOPs of one forward (= one adjoint) tile-kernel launch: 2 per
+    in-bounds tap of the D-folded convolution, over all epochs of all fields."""
+    return sum(2.0 * fd.E * folded_taps_1d(fd.N, fd.f, fd.K) ** 2 for fd in fields)
+
+
+def fwd_bytes(fields):
+    """Algorithmic DRAM bytes of one forward launch: data, weights, folded kernels, e out, h in."""
+    b = 0
+    for fd in fields:
+        Tk = -(-(fd.K + fd.f - 1) // fd.f) + 1
+        b += fd.E * fd.N * fd.N * 4 * 3 + fd.E * fd.f * fd.f * Tk * Tk * 4 + fd.F * fd.F * 4
+    return b
+
+
+def lr_groups(fd):
+    amp = float(np.mean(np.abs(fd.params[fd.F ** 2:fd.F ** 2 + fd.E * fd.M]))) if fd.M else 1.0
+    return (1e-2 * max(float(np.max(np.abs(fd.params[:fd.F ** 2]))), 1.0) / 100.0, 1e-2 * amp, 1e-3, 1e-3, 1e-2)
+
+
+# --- clocks --------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --- CPU baseline (the FP64 oracle as it stands) --------------------------------------------
+
+def oracle_sample(fields, pb, budget_macs=2.0e11, seed=0):
+    """Pick fields (seeded order) until the literal oracle's estimated work reaches the budget."""
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(fields)) if fields else []
+    picked, macs = [], 0.0
+    for i in order:
+        fd = fields[i]
+        c = 2.0 * fd.E * (fd.F ** 2) * (fd.K ** 2)
+        if picked and macs + c > budget_macs:
+            continue
+        picked.append(int(i))
+        macs += c
+        if macs >= 0.5 * budget_macs:
+            break
+    return picked
+
+
+def time_oracle(fields, picked, pb):
+    import oracle
+    t0 = time.perf_counter()
+    units = 0
+    for i in picked:
+        fd = fields[i]
+        oracle.deconv_loss_grad(fd.E, fd.N, fd.f, fd.K, fd.M, fd.J, fd.lam, fd.d, fd.sigma, fd.s, fd.W, fd.params)
+        units += fd.epoch_pixels
+    if pb is not None:
+        oracle.psf_loss_grad(pb.S, pb.N, pb.f, pb.J, pb.lam, pb.t, pb.sigma, pb.W, pb.params)
+        units += pb.epoch_pixels
+    dt = time.perf_counter() - t0
+    return units, dt, oracle.max_threads()
+
+
+def cpu_baseline(fields, pb, budget_macs=2.0e11):
+    picked = oracle_sample(fields, pb, budget_macs)
+    units, dt, cores = time_oracle(fields, picked, pb)
+    desc = f"{len(picked)} of {len(fields)} fields (" + ", ".join(
+        f"N={fields[i].N} E={fields[i].E}" for i in picked) + ")" + (" + the PSF fit" if pb is not None else "") + \
+        ", one loss+gradient evaluation each, literal FP64 oracle (OpenMP)"
+    return {"value": units / dt, "unit": "epoch-px/s", "cores": cores, "kind": "oracle", "sample": desc,
+            "seconds": dt}
+
+
+# --- our implementation --------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2402_08725_gb300.binding import Batch, Problem, optim_cfg
+
+    t_gen = time.perf_counter()
+    fields, pb = make_workload(args.workload, rank, args.fields)
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.Stream()
+    units = units_of(fields, pb)
+    with torch.cuda.stream(stream):
+        probs = [Problem.from_field(fd, stream=stream) for fd in fields]
+        batch = Batch(probs, stream=stream) if probs else None
+        psf = Problem.from_psf(pb, stream=stream) if pb is not None else None
+        P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda() if batch else None
+        P0 = P.clone() if P is not None else None
+        Q = torch.from_numpy(pb.params).cuda() if psf else None
+        Q0 = Q.clone() if Q is not None else None
+        cfg = optim_cfg("adabelief", lr=lr_groups(fields[0])) if fields else None
+        cfg_psf = optim_cfg("adabelief", lr=(1e-5, 1e-3, 10.0, 1e-3))
+        stream.synchronize()
+
+        def one_step():
+            if batch is not None:
+                batch.step(P, 1, cfg)
+            if psf is not None:
+                psf.step(Q, 1, cfg_psf)
+
+        for _ in range(args.warmup):
+            one_step()
+        if batch is not None:
+            batch.profile(True)
+        stream.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop()
+        n_ev, fwd_ms, adj_ms = batch.profile_read() if batch is not None else (0, 0.0, 0.0)
+        if batch is not None:
+            batch.profile(False)
+        launches = 0
+        if batch is not None:
+            launches += (batch.launches_per_eval() + 2) * args.steps
+        if psf is not None:
+            launches += (psf.launches_per_eval() + 2) * args.steps
+        # the same steps replayed from the captured CUDA graph (no kernel events)
+        graph_ms = None
+        if batch is not None:
+            stream.synchronize()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(args.steps):
+                one_step()
+            g1.record(stream)
+            stream.synchronize()
+            graph_ms = g0.elapsed_time(g1) / args.steps
+
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = units * args.steps * world / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e and batch is not None:
+        e2e = measure_e2e(fields, probs, batch, psf, pb, max(1, min(args.steps, 3)), stream)
+
+    peaks, peak_src = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roof = None
+    kernels = None
+    if batch is not None and n_ev > 0:
+        fl = fwd_flops(fields)
+        avg_f, avg_a = fwd_ms / n_ev, adj_ms / n_ev
+        dom_ms, dom = (avg_f, "fwd") if avg_f >= avg_a else (avg_a, "adj")
+        achieved = fl / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "traffic": None, "kernel": f"{dom}_kernel<16>",
+                "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max clock)"}
+        kernels = {"fwd_ms": round(avg_f, 4), "adj_ms": round(avg_a, 4), "fwd_tflops": round(fl / avg_f / 1e9, 3),
+                   "adj_tflops": round(fl / avg_a / 1e9, 3), "flops_per_launch": fl,
+                   "evals_profiled": n_ev}
+
+    plain = None
+    if not args.no_plain and fields and rank == 0:
+        plain = measure_plain(fields, value / world, stream)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(fields, pb)
+
+    if rank == 0:
+        line = {
+            "metric": "loss+grad evals/sec (epoch-pixels/s), batched adjoint vs plain, % HBM roofline",
+            "value": value, "unit": "epoch-px/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload + (f" (first {args.fields} fields)" if args.fields else ""),
+                       "description": WORKLOADS[args.workload],
+                       "epoch_pixels_per_step": units, "fields": len(fields), "psf_stars": pb.S if pb else 0,
+                       "l2": "inputs larger than L2" if units * 12 > 129e6 else "inputs smaller than L2 (no flush)",
+                       "generation_s": round(t_gen, 1)},
+            "graph_ms_per_step": graph_ms,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "roofline": roof,
+            "kernels": kernels,
+            "e2e": e2e,
+            "plain": plain,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measure_e2e(fields, probs, batch, psf, pb, steps, stream):
+    """Host arrays in page-locked memory; each step copies data, noise, PSFs and
+    parameters to the device through the C ABI, evaluates, and reads back the
+    gradient and the loss."""
+    import torch
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+        return t
+
+    hd = [(pinned(fd.d), pinned(fd.sigma), pinned(fd.s)) for fd in fields]
+    params = pinned(np.concatenate([fd.params for fd in fields])).numpy()
+    grad = torch.empty(batch.n_params, dtype=torch.float32).pin_memory().numpy()
+    h2d = sum(d.numel() + s.numel() + p.numel() for d, s, p in hd) * 4 + params.nbytes
+    d2h = grad.nbytes + 8
+    if psf is not None:
+        qd, qs = pinned(pb.t), pinned(pb.sigma)
+        qp = pinned(pb.params).numpy()
+        qg = torch.empty(psf.n_params, dtype=torch.float32).pin_memory().numpy()
+        h2d += (qd.numel() + qs.numel()) * 4 + qp.nbytes
+        d2h += qg.nbytes + 8
+    units = units_of(fields, pb)
+
+    def one():
+        for pr, (d, s, p) in zip(probs, hd):
+            pr.set_data(d)
+            pr.set_noise(s)
+            pr.set_psfs(p)
+        batch.loss_and_grad_host(params, grad)
+        if psf is not None:
+            psf.set_data(qd)
+            psf.set_noise(qs)
+            psf.loss_and_grad_host(qp, qg)
+
+    one()
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": units * steps / dt, "unit": "epoch-px/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+def measure_plain(fields, batched_value, stream, max_fields=6, evals=2):
+    """The plain per-epoch form (fine-grid convolution, D, residual, D^T,
+    correlation as separate launches per epoch) on a sample of the fields,
+    against the batched fused form's per-GPU throughput."""
+    import torch
+    from paper_2402_08725_gb300.binding import Problem
+    rng = np.random.default_rng(1)
+    idx = sorted(rng.permutation(len(fields))[:max_fields].tolist())
+    with torch.cuda.stream(stream):
+        probs = [Problem.from_field(fields[i], conv_mode="plain", stream=stream) for i in idx]
+        ps = [torch.from_numpy(fields[i].params).cuda() for i in idx]
+        gs = [torch.empty_like(p) for p in ps]
+        for pr, p, g in zip(probs, ps, gs):
+            pr.loss_and_grad(p, g, sync=False)
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(evals):
+            for pr, p, g in zip(probs, ps, gs):
+                pr.loss_and_grad(p, g, sync=False)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        for pr in probs:
+            pr.close()
+    units = sum(fields[i].epoch_pixels for i in idx) * evals
+    val = units / (ms / 1e3)
+    return {"value": val, "unit": "epoch-px/s", "fields": idx, "speedup_batched_over_plain": batched_value / val}
+
+
+# --- reference arm: the oracle as it stands ----------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    fields, pb = make_workload(args.workload, 0)
+    # each step a bounded sample of the workload (about 5-10 s of CPU work)
+    picked = oracle_sample(fields, pb, budget_macs=4.0e10, seed=2)
+    for _ in range(args.warmup):
+        time_oracle(fields, picked[:1], None)
+    tot_units, tot_dt, cores = 0, 0.0, 1
+    for _ in range(args.steps):
+        u, dt, cores = time_oracle(fields, picked, pb)
+        tot_units += u
+        tot_dt += dt
+    value = tot_units / tot_dt
+    desc = f"{len(picked)} of {len(fields)} fields per step (" + ", ".join(
+        f"N={fields[i].N} E={fields[i].E}" for i in picked) + ")" + (" + the PSF fit" if pb is not None else "")
+    line = {
+        "metric": "loss+grad evals/sec (epoch-pixels/s), batched adjoint vs plain, % HBM roofline",
+        "value": value, "unit": "epoch-px/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+        "cpu_baseline": {"value": value, "unit": "epoch-px/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "epoch-px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * starred.h — C ABI of the GB300 (sm_103a) STARRED loss-and-gradient library.
+ *
+ * The library evaluates, on one GPU, the regularised loss and its gradient of
+ * STARRED (Millon et al., arXiv 2402.08725):
+ *
+ *  - joint multi-epoch two-channel deconvolution (sec. 2.2, Eq. 9-11 with
+ *    lambda_pts = 0): per epoch i the fine image f_i = h + sum_k a_ki r_k is
+ *    convolved with the epoch's narrow PSF s_i (operator S_i), block-summed to
+ *    the data grid (operator D, the subsampling arrow of Eq. 1), compared with
+ *    the data under diagonal inverse-variance weights (Eq. 10), and the
+ *    starlet prior lambda ||W o Phi^T h||_1 (Eq. 6) is added;
+ *  - PSF reconstruction (sec. 2.1, Eq. 2-4 and Eq. 7): narrow PSF
+ *    s = Moffat(alpha, beta) + b, star k modelled as D(a_k (s * r_k)) with r_k
+ *    the 2-pixel-FWHM Gaussian shifted to the star centre (Eq. 3), plus the
+ *    starlet prior on b;
+ *  - the gradient-based optimiser step the paper uses (sec. 2.4: AdaBelief;
+ *    Adam is also offered), with projection a >= 0.
+ *
+ * Conventions (fixed readings of points the paper leaves open):
+ *   Fine grid F = f*N (f = supersampling).  Arrays are row-major [row][col];
+ *   2-vectors are (x, y) with x along columns.  Fine pixel u has data
+ *   coordinate (u + 0.5)/f - 0.5; a point source at offset c (data pixels from
+ *   the stamp centre (N-1)/2) sits at fine coordinate (F-1)/2 + f*c.
+ *   Narrow PSFs are K x K with origin (K/2, K/2) (integer division); S is a
+ *   true (flipped-kernel) linear convolution with zero padding and F x F output.
+ *   D is a flux-conserving block sum of f x f fine pixels.
+ *   The Gaussian r has FWHM 2 fine pixels, unit flux, point-sampled (Eq. 1).
+ *   The per-epoch background Gamma_i (Eq. 9) adds f^2 * Gamma_i to every data
+ *   pixel after D.  The per-epoch shift delta_i moves the point sources only.
+ *   Starlet: isotropic undecimated B3-spline (1-4-6-4-1)/16 with holes 2^j,
+ *   whole-sample mirror borders; J counts all planes (J-1 detail planes are
+ *   penalised with weight W[j], the coarse plane is not); needs
+ *   2 * 2^(J-2) <= F - 1.
+ *   Noise: weights w = 1/sigma^2 (C diagonal, Eq. 4 and Eq. 10); sigma = +inf
+ *   masks a pixel.
+ *
+ * Packed parameter vector (float32, device memory, owned by the caller):
+ *   DECONV: [ h F*F | a E*M | c M*2 | delta E*2 | Gamma E ]
+ *   PSF:    [ b F*F | alpha, beta | a S | c S*2 ]          (S = number of stars)
+ *
+ * Precision: FP32 arithmetic; the chi^2 and prior sums are accumulated in
+ * FP64.  The loss is returned as a double.
+ *
+ * Ownership and streams: set_* calls copy the caller's arrays into device
+ * buffers the library allocates at create time and frees at destroy; the
+ * caller keeps its arrays.  Parameter and gradient pointers are caller-owned
+ * device pointers that must stay valid until the call's work has finished on
+ * the problem's stream.  All work is ordered on the stream given at create
+ * (a cudaStream_t, NULL for the legacy default stream).  Calls that return a
+ * value to a host pointer synchronise that stream; calls that write only to
+ * device pointers do not.
+ *
+ * Errors: every call returns an sr_status; nothing is thrown across the ABI.
+ * sr_last_error() gives a message for the calling thread's last failure.
+ * Calls that need data not yet set return SR_ERR_STATE.  Non-finite inputs
+ * (NaN data, NaN or non-positive sigma, non-finite PSF values) are rejected
+ * with SR_ERR_NONFINITE by the first call after them that returns a host value.  A problem is not thread-safe: use one per thread or
+ * serialise calls.
+ */
+#ifndef STARRED_H
+#define STARRED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SR_OK = 0,
+    SR_ERR_ARG = 1,         /* null pointer, out-of-range argument */
+    SR_ERR_SHAPE = 2,       /* inconsistent or unsupported sizes */
+    SR_ERR_STATE = 3,       /* required data not set, or wrong problem kind */
+    SR_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error) */
+    SR_ERR_OOM = 5,         /* device or host allocation failed */
+    SR_ERR_NONFINITE = 6,   /* NaN/Inf input or non-finite loss */
+    SR_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
+    SR_ERR_UNSUPPORTED = 8  /* valid request that this build does not support */
+} sr_status;
+
+typedef enum { SR_DECONV = 0, SR_PSF = 1 } sr_kind;
+
+/* How S (and D) are evaluated.  AUTO lets the library choose.  DIRECT is the
+ * fused D-folded direct form.  PLAIN is the literal per-epoch form (fine-grid
+ * convolution, then D, residual, D^T, correlation, each a separate launch per
+ * epoch), kept as the measured baseline. */
+typedef enum { SR_CONV_AUTO = 0, SR_CONV_DIRECT = 1, SR_CONV_PLAIN = 2 } sr_conv_mode;
+
+typedef struct {
+    int kind;            /* sr_kind */
+    int n_epochs;        /* DECONV: E epochs; PSF: S star cutouts */
+    int data_n;          /* N: data stamps are N x N (1 <= N <= 4096) */
+    int supersampling;   /* f >= 1: fine grid F = f*N */
+    int psf_k;           /* DECONV: narrow PSF size K (1 <= K <= 511); PSF: ignored */
+    int n_sources;       /* DECONV: point sources M (0 <= M <= 64); PSF: ignored */
+    int n_scales;        /* J >= 2 starlet planes including the coarse one (<= 8) */
+    double lambda;       /* prior strength lambda >= 0 (noise-sigma units, Eq. 6) */
+    int conv_mode;       /* sr_conv_mode */
+} sr_problem_desc;
+
+/* Parameter groups of the packed vector, in order.
+ * DECONV: 0 h, 1 a, 2 c, 3 delta, 4 Gamma.  PSF: 0 b, 1 (alpha, beta), 2 a, 3 c. */
+#define SR_MAX_GROUPS 8
+typedef struct {
+    int n_groups;
+    size_t offset[SR_MAX_GROUPS];
+    size_t count[SR_MAX_GROUPS];
+    size_t total;
+} sr_layout;
+
+typedef enum { SR_ADABELIEF = 0, SR_ADAM = 1 } sr_optim_kind;
+
+/* Optimiser settings (sec. 2.4).  AdaBelief is the published update of
+ * Zhuang et al. (2020): m = b1 m + (1-b1) g; s = b2 s + (1-b2)(g-m)^2 + eps;
+ * theta -= lr * mhat / (sqrt(shat) + eps) with bias corrections.  Adam uses
+ * g^2 in place of (g-m)^2 and no eps inside s.  lr is per parameter group
+ * (sr_layout order).  After the update, a (both kinds) is projected onto
+ * a >= 0, and for PSF problems alpha >= 1e-3 and beta >= 1.001. */
+typedef struct {
+    int kind;                   /* sr_optim_kind */
+    float beta1, beta2, eps;
+    float lr[SR_MAX_GROUPS];
+} sr_optim_cfg;
+
+typedef struct sr_problem sr_problem;
+typedef struct sr_batch sr_batch;
+
+/* Thread-local message describing the calling thread's last error ("" if none). */
+const char *sr_last_error(void);
+
+/* Library version and the device compute capability it was built for (103). */
+int sr_version(void);
+int sr_build_arch(void);
+
+/* Create a problem on the current CUDA device.  Validates desc (SR_ERR_SHAPE
+ * for sizes the method does not define, e.g. a starlet wider than the grid),
+ * allocates all device buffers the problem needs, and binds `cuda_stream`.
+ * On failure *out is NULL and nothing is leaked. */
+sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_problem **out);
+
+/* Free everything the problem owns.  NULL is accepted.  Synchronises the stream. */
+sr_status sr_destroy(sr_problem *p);
+
+/* Data d_i (Eq. 8 / Eq. 10; for PSF problems the star cutouts t_k of Eq. 3):
+ * float32 [E][N][N], host (on_device = 0) or device (1) pointer.  Must be
+ * finite.  The set_* calls do not synchronise: the copy is ordered on the
+ * problem's stream (from page-locked host memory it is asynchronous, so keep
+ * the array unchanged until the next synchronising call), and the finiteness
+ * check runs on the device; a bad input makes the next call that returns a
+ * host value fail with SR_ERR_NONFINITE. */
+sr_status sr_set_data(sr_problem *p, const float *d, int on_device);
+
+/* Noise standard deviation sigma (diagonal C of Eq. 4 / Eq. 10):
+ * float32 [E][N][N]; each value > 0, or +inf to mask the pixel. */
+sr_status sr_set_noise(sr_problem *p, const float *sigma, int on_device);
+
+/* Narrow PSFs s_i of the epochs (sec. 2.2): float32 [E][K][K], origin
+ * (K/2, K/2).  DECONV only (SR_ERR_STATE for PSF problems).  The library folds
+ * D into each kernel here (kappa_i(t) = sum of s_i over an f x f block), so the
+ * per-evaluation work uses the folded form. */
+sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device);
+
+/* Prior weights W, one per detail scale (Eq. 6; sec. 2.3 gives their meaning):
+ * float32 [J-1], host pointer, each finite and >= 0 (checked at once,
+ * SR_ERR_NONFINITE otherwise); the array may be reused when the call returns. */
+sr_status sr_set_weights(sr_problem *p, const float *W);
+
+/* Number of float32 values in the packed parameter vector, and its layout. */
+size_t sr_param_count(const sr_problem *p);
+sr_status sr_param_layout(const sr_problem *p, sr_layout *out);
+
+/* Loss L (Eq. 11 for DECONV, Eq. 7 for PSF) at params (device pointer).
+ * Writes *loss_host; synchronises the stream. */
+sr_status sr_loss(sr_problem *p, const float *params_dev, double *loss_host);
+
+/* Loss and gradient dL/dparams (same packed layout) at params.  grad_dev is a
+ * device pointer with sr_param_count floats; it is fully overwritten.  The loss
+ * goes to loss_dev (device double, no synchronisation) and/or loss_host
+ * (synchronises); either may be NULL.  Returns SR_ERR_NONFINITE if a host loss
+ * was requested and it is not finite. */
+sr_status sr_loss_and_grad(sr_problem *p, const float *params_dev, double *loss_host, double *loss_dev,
+                           float *grad_dev);
+
+/* End-to-end variant with HOST buffers: copies params_host (sr_param_count
+ * floats) to the device, evaluates, and copies the gradient back to grad_host
+ * and the loss to *loss_host.  Synchronises.  For best throughput the host
+ * buffers should be page-locked. */
+sr_status sr_loss_and_grad_host(sr_problem *p, const float *params_host, double *loss_host, float *grad_host);
+
+/* Optimiser: run n_steps of {loss_and_grad; update} on params_dev in place.
+ * The moment buffers and step counter live in the problem (sr_reset_optimizer
+ * clears them; sr_get_state/sr_set_state save and restore them).  The steps
+ * are captured once as a CUDA graph and replayed.  losses_dev (nullable,
+ * device, n_steps doubles) receives the loss before each update;
+ * last_loss_host (nullable) receives the last one and synchronises. */
+sr_status sr_step(sr_problem *p, float *params_dev, int n_steps, const sr_optim_cfg *cfg, double *losses_dev,
+                  double *last_loss_host);
+sr_status sr_reset_optimizer(sr_problem *p);
+/* Optimiser state as plain buffers: m and v (device, sr_param_count floats
+ * each) and the 1-based count of updates done.  Restoring a saved state makes
+ * the following steps bitwise identical to an uninterrupted run. */
+sr_status sr_get_state(sr_problem *p, float *m_dev, float *v_dev, int64_t *t);
+sr_status sr_set_state(sr_problem *p, const float *m_dev, const float *v_dev, int64_t t);
+
+/* Batch of independent DECONV problems (fields of uneven sizes, epoch counts
+ * and starlet depths) evaluated together: every kernel of the evaluation runs
+ * once for all fields (persistent launches over one work list sorted by cost).
+ * The problems must be fully set (data, noise, PSFs, weights) and must outlive
+ * the batch; later set_* calls on them are seen by the batch.  The batch's
+ * parameter vector is the concatenation of the fields' packed vectors;
+ * sr_batch_param_offset gives field i's offset. */
+sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream, sr_batch **out);
+sr_status sr_batch_destroy(sr_batch *b);
+size_t sr_batch_param_count(const sr_batch *b);
+sr_status sr_batch_param_offset(const sr_batch *b, int i, size_t *offset);
+/* losses_dev (nullable, device, n doubles): loss of each field.  total_dev
+ * (nullable, device double) and total_host (nullable, synchronises): sum over
+ * fields.  grad_dev: device, sr_batch_param_count floats, fully overwritten. */
+sr_status sr_batch_loss_and_grad(sr_batch *b, const float *params_dev, double *losses_dev, double *total_dev,
+                                 double *total_host, float *grad_dev);
+/* End-to-end variant with HOST buffers (see sr_loss_and_grad_host). */
+sr_status sr_batch_loss_and_grad_host(sr_batch *b, const float *params_host, double *total_host, float *grad_host);
+/* n_steps optimiser updates of all fields at once (same cfg for every field),
+ * captured as one CUDA graph and replayed. */
+sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_optim_cfg *cfg,
+                        double *last_total_host);
+sr_status sr_batch_reset_optimizer(sr_batch *b);
+
+/* Launch statistics of the last evaluation on this problem/batch: number of
+ * kernel launches one loss_and_grad issues. */
+int sr_launches_per_eval(const sr_problem *p);
+int sr_batch_launches_per_eval(const sr_batch *b);
+
+/* Kernel timing: while enabled, every evaluation of the batch records CUDA
+ * events on the batch's stream before the forward tile kernel, between it and
+ * the adjoint tile kernel, and after the adjoint (a ring of the last 512
+ * evaluations); sr_batch_step runs without graph capture meanwhile.
+ * enable = 1 also clears the record. */
+sr_status sr_batch_profile(sr_batch *b, int enable);
+/* Evaluations recorded and the summed durations in milliseconds of the
+ * forward and adjoint tile kernels.  Synchronises the batch's stream. */
+sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STARRED_H */

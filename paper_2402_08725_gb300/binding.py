@@ -1,0 +1,282 @@
+"""Python front end of the C ABI: Problem and Batch objects over torch device memory.
+
+Every computation happens in the CUDA library; this module converts torch
+tensors and numpy arrays into pointers and sizes and passes the caller's
+current CUDA stream.  Parameter vectors follow the packed layouts of
+include/starred.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as nat
+
+
+def _stream_ptr(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _as_input(x, n_expected: int):
+    """(pointer, on_device, keepalive) for a float32 array given as a CUDA tensor,
+    CPU tensor or numpy array."""
+    if isinstance(x, torch.Tensor):
+        t = x.detach()
+        if t.dtype != torch.float32:
+            t = t.float()
+        t = t.contiguous()
+        if t.numel() != n_expected:
+            raise ValueError(f"expected {n_expected} values, got {t.numel()}")
+        return ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0, t
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    if a.size != n_expected:
+        raise ValueError(f"expected {n_expected} values, got {a.size}")
+    return ctypes.c_void_p(a.ctypes.data), 0, a
+
+
+def _cuda_f32(t: torch.Tensor, n: int, name: str):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} values, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def optim_cfg(kind="adabelief", lr=(1e-2,), beta1=0.9, beta2=0.999, eps=None) -> nat.OptimCfg:
+    k = nat.SR_ADABELIEF if kind == "adabelief" else nat.SR_ADAM
+    if eps is None:
+        eps = 1e-16 if k == nat.SR_ADABELIEF else 1e-8
+    cfg = nat.OptimCfg()
+    cfg.kind = k
+    cfg.beta1, cfg.beta2, cfg.eps = beta1, beta2, eps
+    lrs = list(lr) + [0.0] * (nat.SR_MAX_GROUPS - len(lr))
+    for i in range(nat.SR_MAX_GROUPS):
+        cfg.lr[i] = float(lrs[i])
+    return cfg
+
+
+class Problem:
+    """One STARRED problem (a deconvolution field, or a PSF fit) on the current GPU."""
+
+    def __init__(self, kind: str, E: int, N: int, f: int, K: int = 1, M: int = 0, J: int = 4, lam: float = 0.0,
+                 conv_mode: str = "auto", stream=None):
+        self.lib = nat.load()
+        self.kind = nat.SR_DECONV if kind == "deconv" else nat.SR_PSF
+        self.E, self.N, self.f, self.K, self.M, self.J, self.lam = E, N, f, K, M, J, lam
+        d = nat.ProblemDesc()
+        d.kind, d.n_epochs, d.data_n, d.supersampling = self.kind, E, N, f
+        d.psf_k, d.n_sources, d.n_scales, d.lam = K, M, J, lam
+        d.conv_mode = {"auto": nat.SR_CONV_AUTO, "direct": nat.SR_CONV_DIRECT, "plain": nat.SR_CONV_PLAIN}[conv_mode]
+        self._stream = stream
+        h = ctypes.c_void_p()
+        nat.check(self.lib.sr_create_problem(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "sr_create_problem")
+        self.handle = h
+        self.n_params = int(self.lib.sr_param_count(h))
+        self._grad = None
+        self._loss_dev = None
+
+    @classmethod
+    def from_field(cls, fd, conv_mode="auto", stream=None, data=True):
+        """Problem for a synthetic.DeconvField (data, noise, PSFs and weights set)."""
+        p = cls("deconv", fd.E, fd.N, fd.f, fd.K, fd.M, fd.J, fd.lam, conv_mode=conv_mode, stream=stream)
+        if data:
+            p.set_data(fd.d)
+            p.set_noise(fd.sigma)
+            p.set_psfs(fd.s)
+            p.set_weights(fd.W)
+        return p
+
+    @classmethod
+    def from_psf(cls, pb, stream=None):
+        p = cls("psf", pb.S, pb.N, pb.f, J=pb.J, lam=pb.lam, stream=stream)
+        p.set_data(pb.t)
+        p.set_noise(pb.sigma)
+        p.set_weights(pb.W)
+        return p
+
+    # --- inputs -------------------------------------------------------------------------
+    def set_data(self, x):
+        ptr, dev, keep = _as_input(x, self.E * self.N * self.N)
+        nat.check(self.lib.sr_set_data(self.handle, ptr, dev), "sr_set_data")
+        self._keep_d = keep
+
+    def set_noise(self, x):
+        ptr, dev, keep = _as_input(x, self.E * self.N * self.N)
+        nat.check(self.lib.sr_set_noise(self.handle, ptr, dev), "sr_set_noise")
+        self._keep_s = keep
+
+    def set_psfs(self, x):
+        ptr, dev, keep = _as_input(x, self.E * self.K * self.K)
+        nat.check(self.lib.sr_set_psfs(self.handle, ptr, dev), "sr_set_psfs")
+        self._keep_p = keep
+
+    def set_weights(self, W):
+        a = np.ascontiguousarray(np.asarray(W, dtype=np.float32))
+        if a.size != self.J - 1:
+            raise ValueError(f"expected {self.J - 1} weights")
+        nat.check(self.lib.sr_set_weights(self.handle, ctypes.c_void_p(a.ctypes.data)), "sr_set_weights")
+
+    def layout(self):
+        L = nat.Layout()
+        nat.check(self.lib.sr_param_layout(self.handle, ctypes.byref(L)), "sr_param_layout")
+        return [(int(L.offset[g]), int(L.count[g])) for g in range(L.n_groups)]
+
+    # --- evaluation ------------------------------------------------------------------------
+    def loss_and_grad(self, params: torch.Tensor, grad: torch.Tensor | None = None, sync: bool = True):
+        """Returns (loss, grad).  loss is a float when sync, else a 0-d float64 CUDA tensor."""
+        if grad is None:
+            grad = torch.empty(self.n_params, dtype=torch.float32, device=params.device)
+        pp = _cuda_f32(params, self.n_params, "params")
+        gp = _cuda_f32(grad, self.n_params, "grad")
+        if sync:
+            loss = ctypes.c_double()
+            nat.check(self.lib.sr_loss_and_grad(self.handle, pp, ctypes.byref(loss), None, gp), "sr_loss_and_grad")
+            return loss.value, grad
+        loss_t = torch.empty((), dtype=torch.float64, device=params.device)
+        nat.check(self.lib.sr_loss_and_grad(self.handle, pp, None, ctypes.c_void_p(loss_t.data_ptr()), gp),
+                  "sr_loss_and_grad")
+        return loss_t, grad
+
+    def loss(self, params: torch.Tensor) -> float:
+        loss = ctypes.c_double()
+        nat.check(self.lib.sr_loss(self.handle, _cuda_f32(params, self.n_params, "params"), ctypes.byref(loss)), "sr_loss")
+        return loss.value
+
+    def loss_and_grad_host(self, params_host: np.ndarray, grad_host: np.ndarray | None = None):
+        p = np.ascontiguousarray(params_host, dtype=np.float32)
+        if grad_host is None:
+            grad_host = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        nat.check(self.lib.sr_loss_and_grad_host(self.handle, ctypes.c_void_p(p.ctypes.data), ctypes.byref(loss),
+                                                 ctypes.c_void_p(grad_host.ctypes.data)), "sr_loss_and_grad_host")
+        return loss.value, grad_host
+
+    def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg, losses: torch.Tensor | None = None) -> float:
+        last = ctypes.c_double()
+        lp = None
+        if losses is not None:
+            if losses.dtype != torch.float64 or not losses.is_cuda or losses.numel() < n_steps:
+                raise TypeError("losses must be a float64 CUDA tensor with n_steps values")
+            lp = ctypes.c_void_p(losses.data_ptr())
+        nat.check(self.lib.sr_step(self.handle, _cuda_f32(params, self.n_params, "params"), int(n_steps),
+                                   ctypes.byref(cfg), lp, ctypes.byref(last)), "sr_step")
+        return last.value
+
+    def reset_optimizer(self):
+        nat.check(self.lib.sr_reset_optimizer(self.handle), "sr_reset_optimizer")
+
+    def get_state(self):
+        m = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        v = torch.empty_like(m)
+        t = ctypes.c_int64()
+        nat.check(self.lib.sr_get_state(self.handle, ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                        ctypes.byref(t)), "sr_get_state")
+        return m, v, t.value
+
+    def set_state(self, m: torch.Tensor, v: torch.Tensor, t: int):
+        nat.check(self.lib.sr_set_state(self.handle, _cuda_f32(m, self.n_params, "m"), _cuda_f32(v, self.n_params, "v"),
+                                        int(t)), "sr_set_state")
+
+    def launches_per_eval(self) -> int:
+        return int(self.lib.sr_launches_per_eval(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many deconvolution fields evaluated together (one launch per kernel for all fields)."""
+
+    def __init__(self, problems, stream=None):
+        self.lib = nat.load()
+        self.problems = list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.handle for p in self.problems])
+        h = ctypes.c_void_p()
+        nat.check(self.lib.sr_batch_create(arr, len(self.problems), _stream_ptr(stream), ctypes.byref(h)),
+                  "sr_batch_create")
+        self.handle = h
+        self.n_params = int(self.lib.sr_batch_param_count(h))
+        self.offsets = []
+        for i in range(len(self.problems)):
+            o = ctypes.c_size_t()
+            nat.check(self.lib.sr_batch_param_offset(h, i, ctypes.byref(o)), "sr_batch_param_offset")
+            self.offsets.append(int(o.value))
+
+    def pack(self, vectors):
+        """Concatenate per-field parameter vectors (numpy or torch) in batch order."""
+        if isinstance(vectors[0], torch.Tensor):
+            return torch.cat([v.reshape(-1).float() for v in vectors])
+        return np.concatenate([np.asarray(v, dtype=np.float32).ravel() for v in vectors])
+
+    def loss_and_grad(self, params: torch.Tensor, grad: torch.Tensor | None = None, losses: torch.Tensor | None = None,
+                      sync: bool = True):
+        if grad is None:
+            grad = torch.empty(self.n_params, dtype=torch.float32, device=params.device)
+        lp = None
+        if losses is not None:
+            lp = ctypes.c_void_p(losses.data_ptr())
+        pp = _cuda_f32(params, self.n_params, "params")
+        gp = _cuda_f32(grad, self.n_params, "grad")
+        if sync:
+            tot = ctypes.c_double()
+            nat.check(self.lib.sr_batch_loss_and_grad(self.handle, pp, lp, None, ctypes.byref(tot), gp),
+                      "sr_batch_loss_and_grad")
+            return tot.value, grad
+        tot_t = torch.empty((), dtype=torch.float64, device=params.device)
+        nat.check(self.lib.sr_batch_loss_and_grad(self.handle, pp, lp, ctypes.c_void_p(tot_t.data_ptr()), None, gp),
+                  "sr_batch_loss_and_grad")
+        return tot_t, grad
+
+    def loss_and_grad_host(self, params_host: np.ndarray, grad_host: np.ndarray | None = None):
+        p = np.ascontiguousarray(params_host, dtype=np.float32)
+        if grad_host is None:
+            grad_host = np.empty(self.n_params, dtype=np.float32)
+        tot = ctypes.c_double()
+        nat.check(self.lib.sr_batch_loss_and_grad_host(self.handle, ctypes.c_void_p(p.ctypes.data), ctypes.byref(tot),
+                                                       ctypes.c_void_p(grad_host.ctypes.data)),
+                  "sr_batch_loss_and_grad_host")
+        return tot.value, grad_host
+
+    def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg) -> float:
+        last = ctypes.c_double()
+        nat.check(self.lib.sr_batch_step(self.handle, _cuda_f32(params, self.n_params, "params"), int(n_steps),
+                                         ctypes.byref(cfg), ctypes.byref(last)), "sr_batch_step")
+        return last.value
+
+    def reset_optimizer(self):
+        nat.check(self.lib.sr_batch_reset_optimizer(self.handle), "sr_batch_reset_optimizer")
+
+    def launches_per_eval(self) -> int:
+        return int(self.lib.sr_batch_launches_per_eval(self.handle))
+
+    def profile(self, enable: bool = True):
+        nat.check(self.lib.sr_batch_profile(self.handle, 1 if enable else 0), "sr_batch_profile")
+
+    def profile_read(self):
+        """(evaluations recorded, summed forward-kernel ms, summed adjoint-kernel ms)."""
+        n, fm, am = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        nat.check(self.lib.sr_batch_profile_read(self.handle, ctypes.byref(n), ctypes.byref(fm), ctypes.byref(am)),
+                  "sr_batch_profile_read")
+        return n.value, fm.value, am.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

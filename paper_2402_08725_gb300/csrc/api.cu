@@ -1,0 +1,976 @@
+// Host side of the C ABI (include/starred.h): problem and batch objects, input validation,
+// work-list construction, the evaluation launch sequence, and optimiser graphs.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sr {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+sr_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s failed: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();  // clear the sticky-free error state
+    return e == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA;
+}
+
+static sr_status fail(sr_status s, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+// Device allocations owned by one object, freed together.
+struct DevArena {
+    std::vector<void *> ptrs;
+    template <typename T>
+    sr_status alloc(T **p, size_t n) {
+        *p = nullptr;
+        if (n == 0) n = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        ptrs.push_back(q);
+        *p = static_cast<T *>(q);
+        return SR_OK;
+    }
+    void release() {
+        for (void *q : ptrs) cudaFree(q);
+        ptrs.clear();
+    }
+    ~DevArena() { release(); }
+};
+
+static int g_smem_optin = -1;
+static int g_num_sms = 0;
+
+static sr_status device_limits() {
+    if (g_smem_optin >= 0) return SR_OK;
+    int dev = 0;
+    SR_CUDA(cudaGetDevice(&dev));
+    SR_CUDA(cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    SR_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    // reserve the static shared memory of the kernels (a few hundred bytes)
+    const int dyn = g_smem_optin - 1024;
+    sr_status s = configure_tile_kernels(dyn, dyn);
+    if (s != SR_OK) return s;
+    return SR_OK;
+}
+
+// Polyphase extent of the folded kernels: tau in [tau_lo, tau_lo + Tk).
+static void folded_extent(int K, int f, int *Tk, int *tau_lo) {
+    const int o = K / 2;
+    const int t_lo = -o - f + 1, t_hi = K - 1 - o;
+    auto cdiv = [](int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); };
+    auto fdiv = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+    const int lo = cdiv(t_lo, f);
+    const int hi = fdiv(t_hi + f - 1, f);
+    *tau_lo = lo;
+    *Tk = hi - lo + 1;
+}
+
+}  // namespace sr
+
+using namespace sr;
+
+// ------------------------------------------------------------------------------------------
+// Execution plan: fields, work lists and scratch for one evaluation of one or many fields.
+// ------------------------------------------------------------------------------------------
+struct Plan {
+    int kind = SR_DECONV;
+    bool plain = false;
+    int n_fields = 0;
+    std::vector<FieldDev> h_fields;
+    FieldDev *d_fields = nullptr;
+    std::vector<size_t> param_off;
+    size_t n_params = 0;
+    // deconvolution work lists
+    int n_items = 0;
+    TileItem *d_items = nullptr;
+    int *d_counters = nullptr;
+    int smem_fwd = 0, smem_adj = 0, grid_fwd = 0, grid_adj = 0;
+    int n_ps = 0;
+    int4 *d_ps = nullptr;
+    int n_chunks = 0;
+    ChunkItem *d_chunks = nullptr;
+    int Jmax = 0;
+    float *ebuf = nullptr, *gbuf = nullptr, *ps_da = nullptr, *ps_du = nullptr;
+    double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
+    // PSF
+    PsfBuffers psf{};
+    // plain form
+    PlainBuffers plainb{};
+    std::vector<const float *> s_raw;
+    // optimiser
+    uint8_t *d_group = nullptr;
+    float *opt_m = nullptr, *opt_v = nullptr, *grad_int = nullptr, *params_int = nullptr;
+    long long *d_t = nullptr;
+    float *d_bc = nullptr;
+    double **d_hist_ptr = nullptr;
+    long long *d_hist_base = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    const float *graph_params = nullptr;
+    sr_optim_cfg graph_cfg{};
+    int launches = 0;
+    // kernel timing ring: events before the forward, between forward and adjoint, after the adjoint
+    bool profiling = false;
+    int prof_count = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    DevArena arena;
+    ~Plan() {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    }
+};
+
+struct sr_problem {
+    sr_problem_desc desc{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int F = 0, Tk = 0, tau_lo = 0;
+    float *d = nullptr, *w = nullptr, *s = nullptr, *kappa = nullptr, *Wd = nullptr, *starlet = nullptr;
+    float *psf_s = nullptr, *psf_tmp = nullptr, *psf_gs = nullptr;
+    int *d_flag = nullptr;
+    float W_host[kMaxScales] = {0};
+    bool has_data = false, has_noise = false, has_psfs = false, has_weights = false;
+    bool pending_check = false;
+    Plan *plan = nullptr;
+    DevArena arena;
+};
+
+struct sr_batch {
+    cudaStream_t stream = nullptr;
+    std::vector<sr_problem *> probs;
+    Plan *plan = nullptr;
+};
+
+// ------------------------------------------------------------------------------------------
+static sr_status validate_desc(const sr_problem_desc *d) {
+    if (!d) return fail(SR_ERR_ARG, "desc is NULL");
+    if (d->kind != SR_DECONV && d->kind != SR_PSF) return fail(SR_ERR_ARG, "unknown kind %d", d->kind);
+    if (d->n_epochs < 1 || d->n_epochs > 1000000) return fail(SR_ERR_SHAPE, "n_epochs %d out of range", d->n_epochs);
+    if (d->data_n < 1 || d->data_n > 4096) return fail(SR_ERR_SHAPE, "data_n %d out of range", d->data_n);
+    if (d->supersampling < 1 || d->supersampling > 8) return fail(SR_ERR_SHAPE, "supersampling %d out of range", d->supersampling);
+    if (d->n_scales < 2 || d->n_scales > kMaxScales) return fail(SR_ERR_SHAPE, "n_scales %d out of range", d->n_scales);
+    const int F = d->supersampling * d->data_n;
+    if (2 * (1 << (d->n_scales - 2)) > F - 1)
+        return fail(SR_ERR_SHAPE, "starlet with %d scales needs a grid wider than %d", d->n_scales, F);
+    if (!(d->lambda >= 0.0) || !std::isfinite(d->lambda)) return fail(SR_ERR_ARG, "lambda must be finite and >= 0");
+    if (d->kind == SR_DECONV) {
+        if (d->psf_k < 1 || d->psf_k > 511) return fail(SR_ERR_SHAPE, "psf_k %d out of range", d->psf_k);
+        if (d->n_sources < 0 || d->n_sources > 64) return fail(SR_ERR_SHAPE, "n_sources %d out of range", d->n_sources);
+    }
+    if (d->conv_mode < SR_CONV_AUTO || d->conv_mode > SR_CONV_PLAIN) return fail(SR_ERR_ARG, "unknown conv_mode");
+    if (d->kind == SR_PSF && d->conv_mode == SR_CONV_PLAIN)
+        return fail(SR_ERR_UNSUPPORTED, "the plain form exists for deconvolution problems only");
+    return SR_OK;
+}
+
+static size_t deconv_param_count(const sr_problem_desc &d) {
+    const size_t F = (size_t)d.supersampling * d.data_n;
+    const size_t E = d.n_epochs, M = d.n_sources;
+    return F * F + E * M + 2 * M + 2 * E + E;
+}
+static size_t psf_param_count(const sr_problem_desc &d) {
+    const size_t F = (size_t)d.supersampling * d.data_n;
+    const size_t S = d.n_epochs;
+    return F * F + 2 + S + 2 * S;
+}
+static size_t param_count(const sr_problem_desc &d) {
+    return d.kind == SR_DECONV ? deconv_param_count(d) : psf_param_count(d);
+}
+
+static void layout_of(const sr_problem_desc &d, sr_layout *L) {
+    memset(L, 0, sizeof *L);
+    const size_t F = (size_t)d.supersampling * d.data_n;
+    const size_t E = d.n_epochs;
+    if (d.kind == SR_DECONV) {
+        const size_t M = d.n_sources;
+        const size_t cnt[5] = {F * F, E * M, 2 * M, 2 * E, E};
+        size_t o = 0;
+        for (int g = 0; g < 5; ++g) {
+            L->offset[g] = o;
+            L->count[g] = cnt[g];
+            o += cnt[g];
+        }
+        L->n_groups = 5;
+        L->total = o;
+    } else {
+        const size_t cnt[4] = {F * F, 2, E, 2 * E};
+        size_t o = 0;
+        for (int g = 0; g < 4; ++g) {
+            L->offset[g] = o;
+            L->count[g] = cnt[g];
+            o += cnt[g];
+        }
+        L->n_groups = 4;
+        L->total = o;
+    }
+}
+
+static void fill_field_common(FieldDev &fd, sr_problem *p) {
+    const sr_problem_desc &d = p->desc;
+    memset(&fd, 0, sizeof fd);
+    fd.kind = d.kind;
+    fd.E = d.n_epochs;
+    fd.N = d.data_n;
+    fd.f = d.supersampling;
+    fd.K = d.psf_k;
+    fd.M = d.kind == SR_DECONV ? d.n_sources : 0;
+    fd.J = d.n_scales;
+    fd.F = p->F;
+    fd.Tk = p->Tk;
+    fd.tau_lo = p->tau_lo;
+    fd.lambda = (float)d.lambda;
+    fd.Wd = p->Wd;
+    fd.d = p->d;
+    fd.w = p->w;
+    fd.kappa = p->kappa;
+    fd.starlet = p->starlet;
+    fd.psf_s = p->psf_s;
+    fd.psf_tmp = p->psf_tmp;
+    fd.psf_gs = p->psf_gs;
+    fd.n_chunks = (fd.F * fd.F + 255) / 256;
+}
+
+static int choose_pg(int nph, int threads_per_group) {
+    int best = 1;
+    for (int pg = 1; pg <= nph; ++pg)
+        if (nph % pg == 0 && pg * threads_per_group <= kThreads) best = pg;
+    return best;
+}
+
+// Build the evaluation plan of `n` problems of the same kind.
+static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plain) {
+    sr_status st = device_limits();
+    if (st != SR_OK) return st;
+    pl->kind = probs[0]->desc.kind;
+    pl->plain = plain;
+    pl->n_fields = n;
+    pl->h_fields.resize(n);
+    pl->param_off.resize(n);
+    std::vector<TileItem> items;
+    std::vector<int4> ps;
+    std::vector<ChunkItem> chunks;
+    std::vector<uint8_t> groups;
+    long long ebuf = 0, gbuf = 0, tslot = 0, psslot = 0, l1slot = 0;
+    size_t poff = 0;
+    int Jmax = 0;
+    int smem_fwd = 0, smem_adj = 0;
+    for (int i = 0; i < n; ++i) {
+        sr_problem *p = probs[i];
+        if (p->desc.kind != pl->kind) return fail(SR_ERR_ARG, "a batch mixes problem kinds");
+        FieldDev &fd = pl->h_fields[i];
+        fill_field_common(fd, p);
+        fd.param_off = (long long)poff;
+        pl->param_off[i] = poff;
+        const size_t np = param_count(p->desc);
+        // optimiser groups
+        sr_layout L;
+        layout_of(p->desc, &L);
+        const size_t g0 = groups.size();
+        groups.resize(g0 + np);
+        for (int g = 0; g < L.n_groups; ++g) {
+            uint8_t gid = (uint8_t)g;
+            if (pl->kind == SR_PSF) gid = (uint8_t)(g == 0 ? 0 : g + 1);  // 0 b, 1 alpha, 2 beta, 3 a, 4 c
+            for (size_t k = 0; k < L.count[g]; ++k) groups[g0 + L.offset[g] + k] = gid;
+        }
+        if (pl->kind == SR_PSF) groups[g0 + L.offset[1] + 1] = 2;  // beta
+        poff += np;
+        fd.ebuf_off = ebuf;
+        ebuf += (long long)fd.E * fd.N * fd.N;
+        fd.gbuf_off = gbuf;
+        fd.l1_slot = l1slot;
+        l1slot += (long long)(fd.J - 1) * fd.n_chunks;
+        for (int c = 0; c < fd.n_chunks; ++c) chunks.push_back(ChunkItem{i, c * 256, c});
+        Jmax = std::max(Jmax, fd.J);
+        if (pl->kind == SR_DECONV && !plain) {
+            gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
+            const int nph = fd.f * fd.f;
+            std::vector<TileItem> tiles;
+            for (int y0 = 0; y0 < fd.N; y0 += 64)
+                for (int x0 = 0; x0 < fd.N; x0 += 64) {
+                    TileItem t{};
+                    t.field = i;
+                    t.y0 = (short)y0;
+                    t.x0 = (short)x0;
+                    t.h = (short)std::min(64, fd.N - y0);
+                    t.w = (short)(((std::min(64, fd.N - x0)) + kR - 1) / kR * kR);
+                    t.pg = choose_pg(nph, t.h * (t.w / kR));
+                    tiles.push_back(t);
+                }
+            fd.n_tiles = (int)tiles.size();
+            fd.tile_slot = tslot;
+            for (int e = 0; e < fd.E; ++e)
+                for (int k = 0; k < fd.n_tiles; ++k) {
+                    TileItem t = tiles[k];
+                    t.epoch = e;
+                    t.slot = (int)(tslot + (long long)e * fd.n_tiles + k);
+                    items.push_back(t);
+                    smem_fwd = std::max(smem_fwd, tile_smem_bytes(t, fd.Tk, true));
+                    smem_adj = std::max(smem_adj, tile_smem_bytes(t, fd.Tk, false));
+                }
+            tslot += (long long)fd.E * fd.n_tiles;
+            fd.ps_slot = psslot;
+            for (int e = 0; e < fd.E; ++e)
+                for (int k = 0; k < fd.M; ++k) ps.push_back(make_int4(i, e, k, 0));
+            psslot += (long long)fd.E * fd.M;
+        } else if (pl->kind == SR_DECONV) {
+            // plain form: per-epoch partials of the residual kernel, one slot per 256 data px
+            const int nb = (fd.N * fd.N + 255) / 256;
+            fd.n_tiles = nb;
+            fd.tile_slot = tslot;
+            tslot += (long long)fd.E * nb;
+            fd.ps_slot = psslot;
+            psslot += (long long)fd.E * fd.M;
+        }
+    }
+    if (tslot > 0x7fffffff) return fail(SR_ERR_SHAPE, "too many tiles");
+    pl->Jmax = Jmax;
+    pl->n_params = poff;
+    DevArena &A = pl->arena;
+    // sort the tile work list by decreasing cost so the persistent loops balance (LPT order)
+    std::stable_sort(items.begin(), items.end(), [&](const TileItem &a, const TileItem &b) {
+        const FieldDev &fa = pl->h_fields[a.field], &fb = pl->h_fields[b.field];
+        const double ca = (double)a.h * a.w * fa.Tk * fa.Tk * fa.f * fa.f;
+        const double cb = (double)b.h * b.w * fb.Tk * fb.Tk * fb.f * fb.f;
+        return ca > cb;
+    });
+    pl->n_items = (int)items.size();
+    pl->n_ps = (int)ps.size();
+    pl->n_chunks = (int)chunks.size();
+    if ((st = A.alloc(&pl->d_fields, n)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_items, items.size())) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_ps, ps.size())) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_chunks, chunks.size())) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_counters, 4)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->ebuf, (size_t)ebuf)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->gbuf, (size_t)gbuf)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->chi_part, (size_t)tslot)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->se_part, (size_t)tslot)) != SR_OK) return st;
+    const size_t n_ps_slots = (size_t)std::max<long long>(psslot, 1);
+    if ((st = A.alloc(&pl->ps_da, n_ps_slots)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->ps_du, 2 * n_ps_slots)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->l1_part, (size_t)l1slot)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->losses, (size_t)n)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->total, 1)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_group, poff)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_t, 1)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_bc, 2)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_hist_ptr, 1)) != SR_OK) return st;
+    if ((st = A.alloc(&pl->d_hist_base, 1)) != SR_OK) return st;
+    SR_CUDA(cudaMemset(pl->ps_da, 0, sizeof(float) * n_ps_slots));
+    SR_CUDA(cudaMemset(pl->ps_du, 0, 2 * sizeof(float) * n_ps_slots));
+    SR_CUDA(cudaMemset(pl->d_t, 0, sizeof(long long)));
+    if (pl->kind == SR_PSF) {
+        const FieldDev &fd = pl->h_fields[0];
+        pl->psf.n_dchunks = (fd.N * fd.N + 255) / 256;
+        pl->psf.ebuf = pl->ebuf;
+        if ((st = A.alloc(&pl->psf.star_part, (size_t)fd.E * pl->psf.n_dchunks * 4)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->psf.ab_part, (size_t)fd.n_chunks * 2)) != SR_OK) return st;
+    }
+    if (plain) {
+        const FieldDev &fd = pl->h_fields[0];
+        const size_t F2 = (size_t)fd.F * fd.F;
+        if ((st = A.alloc(&pl->plainb.fimg, F2)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->plainb.conv, F2)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->plainb.ey, F2)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->plainb.gsum, F2)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->plainb.gi, F2)) != SR_OK) return st;
+        const int K = fd.K;
+        const int T = 64;
+        const long long need = (((long long)(T + K - 1) * ((T + K) | 1) + 3) / 4 * 4 + (long long)K * ((K + 3) & ~3)) * 4;
+        if (need > g_smem_optin - 1024)
+            return fail(SR_ERR_UNSUPPORTED, "plain form: PSF size %d needs %lld bytes of shared memory", K, need);
+        if ((st = configure_plain_kernels(K)) != SR_OK) return st;
+    }
+    SR_CUDA(cudaMemcpy(pl->d_fields, pl->h_fields.data(), sizeof(FieldDev) * n, cudaMemcpyHostToDevice));
+    if (!items.empty()) SR_CUDA(cudaMemcpy(pl->d_items, items.data(), sizeof(TileItem) * items.size(), cudaMemcpyHostToDevice));
+    if (!ps.empty()) SR_CUDA(cudaMemcpy(pl->d_ps, ps.data(), sizeof(int4) * ps.size(), cudaMemcpyHostToDevice));
+    if (!chunks.empty()) SR_CUDA(cudaMemcpy(pl->d_chunks, chunks.data(), sizeof(ChunkItem) * chunks.size(), cudaMemcpyHostToDevice));
+    SR_CUDA(cudaMemcpy(pl->d_group, groups.data(), groups.size(), cudaMemcpyHostToDevice));
+    if (pl->kind == SR_DECONV && !plain) {
+        const int limit = g_smem_optin - 1024;
+        if (smem_fwd > limit || smem_adj > limit)
+            return fail(SR_ERR_UNSUPPORTED, "PSF size needs %d bytes of shared memory per block (limit %d)",
+                        std::max(smem_fwd, smem_adj), limit);
+        pl->smem_fwd = smem_fwd;
+        pl->smem_adj = smem_adj;
+        int bf = 0, ba = 0;
+        if ((st = occupancy_tile_kernels(smem_fwd, smem_adj, &bf, &ba)) != SR_OK) return st;
+        bf = std::max(bf, 1);
+        ba = std::max(ba, 1);
+        pl->grid_fwd = std::max(1, std::min(pl->n_items, bf * g_num_sms));
+        pl->grid_adj = std::max(1, std::min(pl->n_items, ba * g_num_sms));
+    }
+    return SR_OK;
+}
+
+// Enqueue one loss-and-gradient evaluation of the plan on `st`.
+static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
+                    const std::vector<const float *> *s_raw) {
+    int n = 0;
+    if (pl->kind == SR_PSF) {
+        n += launch_psf_eval(pl->d_fields, pl->h_fields[0], pl->d_chunks, pl->n_chunks, params, grad, pl->psf,
+                             pl->l1_part, pl->losses, pl->total, st);
+        return n;
+    }
+    if (pl->plain) {
+        n += launch_plain_eval(pl->d_fields, pl->h_fields[0], (*s_raw)[0], pl->d_chunks, pl->n_chunks, params, grad,
+                               pl->plainb, pl->ebuf, pl->chi_part, pl->se_part, pl->ps_da, pl->ps_du, pl->d_ps,
+                               pl->l1_part, pl->losses, pl->total, st);
+        return n;
+    }
+    cudaMemsetAsync(pl->d_counters, 0, 4 * sizeof(int), st);
+    cudaEvent_t *ev = nullptr;
+    if (pl->profiling && !pl->prof_ev.empty()) {
+        const int ring = (int)pl->prof_ev.size() / 3;
+        ev = &pl->prof_ev[3 * (pl->prof_count % ring)];
+        ++pl->prof_count;
+        cudaEventRecord(ev[0], st);
+    }
+    launch_fwd(pl->d_fields, pl->d_items, pl->n_items, pl->d_counters, params, pl->ebuf, pl->chi_part, pl->se_part,
+               pl->grid_fwd, pl->smem_fwd, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    launch_adj(pl->d_fields, pl->d_items, pl->n_items, pl->d_counters + 1, pl->ebuf, pl->gbuf, pl->grid_adj,
+               pl->smem_adj, st);
+    if (ev) cudaEventRecord(ev[2], st);
+    n += 2;
+    if (pl->n_ps > 0) {
+        launch_psgrad(pl->d_fields, pl->d_ps, pl->n_ps, params, pl->gbuf, pl->ps_da, pl->ps_du, st);
+        ++n;
+    }
+    n += launch_starlet(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->Jmax, params, pl->l1_part, st);
+    launch_hgrad(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->gbuf, grad, st);
+    ++n;
+    launch_finalize(pl->d_fields, pl->n_fields, pl->chi_part, pl->se_part, pl->l1_part, pl->ps_da, pl->ps_du, grad,
+                    pl->losses, pl->total, st);
+    n += 2;
+    return n;
+}
+
+static sr_status check_ready(sr_problem *p) {
+    if (!p) return fail(SR_ERR_ARG, "problem is NULL");
+    if (!p->has_data) return fail(SR_ERR_STATE, "data not set");
+    if (!p->has_noise) return fail(SR_ERR_STATE, "noise not set");
+    if (p->desc.kind == SR_DECONV && !p->has_psfs) return fail(SR_ERR_STATE, "PSFs not set");
+    if (!p->has_weights) return fail(SR_ERR_STATE, "weights not set");
+    return SR_OK;
+}
+
+static sr_status check_flag(sr_problem *p) {
+    int flag = 0;
+    SR_CUDA(cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    SR_CUDA(cudaStreamSynchronize(p->stream));
+    p->pending_check = false;
+    if (flag) {
+        SR_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream));
+        return fail(SR_ERR_NONFINITE, "a non-finite value (or sigma <= 0) was found in the inputs");
+    }
+    return SR_OK;
+}
+
+static sr_status ensure_plan(sr_problem *p) {
+    if (p->plan) return SR_OK;
+    Plan *pl = new (std::nothrow) Plan();
+    if (!pl) return fail(SR_ERR_OOM, "host allocation failed");
+    sr_problem *arr[1] = {p};
+    sr_status st = build_plan(pl, arr, 1, p->desc.kind == SR_DECONV && p->desc.conv_mode == SR_CONV_PLAIN);
+    if (st != SR_OK) {
+        delete pl;
+        return st;
+    }
+    pl->s_raw.push_back(p->s);
+    p->plan = pl;
+    return SR_OK;
+}
+
+static sr_status ensure_opt_buffers(Plan *pl) {
+    if (pl->opt_m) return SR_OK;
+    sr_status st;
+    if ((st = pl->arena.alloc(&pl->opt_m, pl->n_params)) != SR_OK) return st;
+    if ((st = pl->arena.alloc(&pl->opt_v, pl->n_params)) != SR_OK) return st;
+    if ((st = pl->arena.alloc(&pl->grad_int, pl->n_params)) != SR_OK) return st;
+    SR_CUDA(cudaMemset(pl->opt_m, 0, sizeof(float) * pl->n_params));
+    SR_CUDA(cudaMemset(pl->opt_v, 0, sizeof(float) * pl->n_params));
+    SR_CUDA(cudaMemset(pl->d_t, 0, sizeof(long long)));
+    return SR_OK;
+}
+
+static OptimArgs optim_args(const Plan *pl, const sr_optim_cfg &c) {
+    OptimArgs a{};
+    a.kind = c.kind;
+    a.beta1 = c.beta1;
+    a.beta2 = c.beta2;
+    a.eps = c.eps;
+    for (int g = 0; g < SR_MAX_GROUPS; ++g) {
+        a.lr[g] = 0.f;
+        a.lo[g] = -INFINITY;
+    }
+    if (pl->kind == SR_DECONV) {
+        for (int g = 0; g < 5; ++g) a.lr[g] = c.lr[g];
+        a.lo[1] = 0.f;  // a >= 0
+    } else {
+        a.lr[0] = c.lr[0];
+        a.lr[1] = c.lr[1];
+        a.lr[2] = c.lr[1];
+        a.lr[3] = c.lr[2];
+        a.lr[4] = c.lr[3];
+        a.lo[1] = 1e-3f;   // alpha
+        a.lo[2] = 1.001f;  // beta
+        a.lo[3] = 0.f;     // a >= 0
+    }
+    return a;
+}
+
+__global__ void record_loss_kernel(const double *total, double *const *hist_ptr, const long long *t,
+                                   const long long *base) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double *h = *hist_ptr;
+        if (h) h[*t - *base] = *total;
+    }
+}
+
+// n optimiser steps on plan `pl` (eager when the stream cannot be captured).
+static sr_status run_steps(Plan *pl, cudaStream_t st, float *params, int n_steps, const sr_optim_cfg *cfg,
+                           double *losses_dev, const std::vector<const float *> *s_raw) {
+    sr_status s;
+    if ((s = ensure_opt_buffers(pl)) != SR_OK) return s;
+    const OptimArgs oa = optim_args(pl, *cfg);
+    SR_CUDA(cudaMemcpyAsync(pl->d_hist_ptr, &losses_dev, sizeof(double *), cudaMemcpyHostToDevice, st));
+    SR_CUDA(cudaMemcpyAsync(pl->d_hist_base, pl->d_t, sizeof(long long), cudaMemcpyDeviceToDevice, st));
+    auto enqueue_one = [&](cudaStream_t s2) {
+        run_eval(pl, params, pl->grad_int, s2, s_raw);
+        record_loss_kernel<<<1, 32, 0, s2>>>(pl->total, pl->d_hist_ptr, pl->d_t, pl->d_hist_base);
+        launch_opt_step((long long)pl->n_params, params, pl->grad_int, pl->opt_m, pl->opt_v, pl->d_group, oa, pl->d_t,
+                        pl->d_bc, s2);
+    };
+    // the host copy of losses_dev must outlive the async copy above
+    SR_CUDA(cudaStreamSynchronize(st));
+    const bool capturable = st != nullptr && !pl->plain && !pl->profiling;
+    if (!capturable) {
+        for (int i = 0; i < n_steps; ++i) enqueue_one(st);
+        SR_CUDA(cudaGetLastError());
+        return SR_OK;
+    }
+    const bool same = pl->graph && pl->graph_params == params && memcmp(&pl->graph_cfg, cfg, sizeof *cfg) == 0;
+    if (!same) {
+        if (pl->graph) {
+            cudaGraphExecDestroy(pl->graph);
+            pl->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        SR_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        enqueue_one(st);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&pl->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        pl->graph_params = params;
+        pl->graph_cfg = *cfg;
+    }
+    for (int i = 0; i < n_steps; ++i) SR_CUDA(cudaGraphLaunch(pl->graph, st));
+    return SR_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char *sr_last_error(void) { return g_err.c_str(); }
+int sr_version(void) { return 1; }
+int sr_build_arch(void) { return 103; }
+
+sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_problem **out) {
+    if (!out) return fail(SR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    sr_status st = validate_desc(desc);
+    if (st != SR_OK) return st;
+    sr_problem *p = new (std::nothrow) sr_problem();
+    if (!p) return fail(SR_ERR_OOM, "host allocation failed");
+    p->desc = *desc;
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaGetDevice(&p->device);
+    const sr_problem_desc &d = *desc;
+    p->F = d.supersampling * d.data_n;
+    const size_t E = d.n_epochs, N = d.data_n, F = p->F;
+    DevArena &A = p->arena;
+    auto bail = [&](sr_status s) {
+        delete p;
+        return s;
+    };
+    if ((st = A.alloc(&p->d, E * N * N)) != SR_OK) return bail(st);
+    if ((st = A.alloc(&p->w, E * N * N)) != SR_OK) return bail(st);
+    if ((st = A.alloc(&p->Wd, kMaxScales)) != SR_OK) return bail(st);
+    if ((st = A.alloc(&p->starlet, (size_t)(d.n_scales + 2) * F * F)) != SR_OK) return bail(st);
+    if ((st = A.alloc(&p->d_flag, 1)) != SR_OK) return bail(st);
+    if (cudaMemset(p->d_flag, 0, sizeof(int)) != cudaSuccess) return bail(fail(SR_ERR_CUDA, "cudaMemset failed"));
+    if (d.kind == SR_DECONV) {
+        folded_extent(d.psf_k, d.supersampling, &p->Tk, &p->tau_lo);
+        const size_t K = d.psf_k;
+        if ((st = A.alloc(&p->s, E * K * K)) != SR_OK) return bail(st);
+        if ((st = A.alloc(&p->kappa, E * d.supersampling * d.supersampling * (size_t)p->Tk * p->Tk)) != SR_OK)
+            return bail(st);
+    } else {
+        if ((st = A.alloc(&p->psf_s, F * F)) != SR_OK) return bail(st);
+        if ((st = A.alloc(&p->psf_tmp, 3 * E * F * F)) != SR_OK) return bail(st);
+        if ((st = A.alloc(&p->psf_gs, E * F * F)) != SR_OK) return bail(st);
+    }
+    *out = p;
+    return SR_OK;
+}
+
+sr_status sr_destroy(sr_problem *p) {
+    if (!p) return SR_OK;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    delete p->plan;
+    delete p;
+    return SR_OK;
+}
+
+static sr_status copy_in(sr_problem *p, float *dst, const float *src, size_t n, int on_device) {
+    SR_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            p->stream));
+    return SR_OK;
+}
+
+sr_status sr_set_data(sr_problem *p, const float *d, int on_device) {
+    if (!p || !d) return fail(SR_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)p->desc.n_epochs * p->desc.data_n * p->desc.data_n;
+    sr_status st = copy_in(p, p->d, d, n, on_device);
+    if (st != SR_OK) return st;
+    launch_check_finite(p->d, (long long)n, p->d_flag, p->stream);
+    p->pending_check = true;
+    p->has_data = true;
+    return SR_OK;
+}
+
+sr_status sr_set_noise(sr_problem *p, const float *sigma, int on_device) {
+    if (!p || !sigma) return fail(SR_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)p->desc.n_epochs * p->desc.data_n * p->desc.data_n;
+    // sigma is staged in the weight buffer, then converted in place to w = 1/sigma^2
+    sr_status st = copy_in(p, p->w, sigma, n, on_device);
+    if (st != SR_OK) return st;
+    launch_inv_var(p->w, p->w, (long long)n, p->d_flag, p->stream);
+    p->pending_check = true;
+    p->has_noise = true;
+    return SR_OK;
+}
+
+sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device) {
+    if (!p || !s) return fail(SR_ERR_ARG, "NULL argument");
+    if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "set_psfs is for deconvolution problems");
+    const sr_problem_desc &d = p->desc;
+    const size_t n = (size_t)d.n_epochs * d.psf_k * d.psf_k;
+    sr_status st = copy_in(p, p->s, s, n, on_device);
+    if (st != SR_OK) return st;
+    launch_check_finite(p->s, (long long)n, p->d_flag, p->stream);
+    launch_kappa_prep(p->s, p->kappa, d.n_epochs, d.psf_k, d.supersampling, p->Tk, p->tau_lo, p->stream);
+    SR_CUDA(cudaGetLastError());
+    p->pending_check = true;
+    p->has_psfs = true;
+    return SR_OK;
+}
+
+sr_status sr_set_weights(sr_problem *p, const float *W) {
+    if (!p || !W) return fail(SR_ERR_ARG, "NULL argument");
+    const int nw = p->desc.n_scales - 1;
+    for (int j = 0; j < nw; ++j)
+        if (!(W[j] >= 0.f) || !std::isfinite(W[j])) return fail(SR_ERR_NONFINITE, "weight %d is not finite and >= 0", j);
+    float tmp[kMaxScales] = {0};
+    memcpy(tmp, W, sizeof(float) * nw);
+    // staged through the problem's host copy so the caller's array may be reused at once
+    memcpy(p->W_host, tmp, sizeof tmp);
+    SR_CUDA(cudaMemcpyAsync(p->Wd, p->W_host, sizeof tmp, cudaMemcpyHostToDevice, p->stream));
+    p->has_weights = true;
+    return SR_OK;
+}
+
+size_t sr_param_count(const sr_problem *p) { return p ? param_count(p->desc) : 0; }
+
+sr_status sr_param_layout(const sr_problem *p, sr_layout *out) {
+    if (!p || !out) return fail(SR_ERR_ARG, "NULL argument");
+    layout_of(p->desc, out);
+    return SR_OK;
+}
+
+sr_status sr_loss_and_grad(sr_problem *p, const float *params_dev, double *loss_host, double *loss_dev,
+                           float *grad_dev) {
+    sr_status st = check_ready(p);
+    if (st != SR_OK) return st;
+    if (!params_dev || !grad_dev) return fail(SR_ERR_ARG, "NULL params or grad");
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    Plan *pl = p->plan;
+    pl->launches = run_eval(pl, params_dev, grad_dev, p->stream, &pl->s_raw);
+    SR_CUDA(cudaGetLastError());
+    if (loss_dev) SR_CUDA(cudaMemcpyAsync(loss_dev, pl->total, sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    if (loss_host) {
+        SR_CUDA(cudaMemcpyAsync(loss_host, pl->total, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        SR_CUDA(cudaStreamSynchronize(p->stream));
+        if (p->pending_check && (st = check_flag(p)) != SR_OK) return st;
+        if (!std::isfinite(*loss_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
+    }
+    return SR_OK;
+}
+
+sr_status sr_loss(sr_problem *p, const float *params_dev, double *loss_host) {
+    sr_status st = check_ready(p);
+    if (st != SR_OK) return st;
+    if (!loss_host) return fail(SR_ERR_ARG, "loss_host is NULL");
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    if ((st = ensure_opt_buffers(p->plan)) != SR_OK) return st;
+    return sr_loss_and_grad(p, params_dev, loss_host, nullptr, p->plan->grad_int);
+}
+
+sr_status sr_loss_and_grad_host(sr_problem *p, const float *params_host, double *loss_host, float *grad_host) {
+    sr_status st = check_ready(p);
+    if (st != SR_OK) return st;
+    if (!params_host || !loss_host || !grad_host) return fail(SR_ERR_ARG, "NULL argument");
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    Plan *pl = p->plan;
+    if ((st = ensure_opt_buffers(pl)) != SR_OK) return st;
+    if (!pl->params_int && (st = pl->arena.alloc(&pl->params_int, pl->n_params)) != SR_OK) return st;
+    SR_CUDA(cudaMemcpyAsync(pl->params_int, params_host, sizeof(float) * pl->n_params, cudaMemcpyHostToDevice, p->stream));
+    if ((st = sr_loss_and_grad(p, pl->params_int, nullptr, nullptr, pl->grad_int)) != SR_OK) return st;
+    SR_CUDA(cudaMemcpyAsync(grad_host, pl->grad_int, sizeof(float) * pl->n_params, cudaMemcpyDeviceToHost, p->stream));
+    SR_CUDA(cudaMemcpyAsync(loss_host, pl->total, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    SR_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->pending_check && (st = check_flag(p)) != SR_OK) return st;
+    if (!std::isfinite(*loss_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
+    return SR_OK;
+}
+
+sr_status sr_step(sr_problem *p, float *params_dev, int n_steps, const sr_optim_cfg *cfg, double *losses_dev,
+                  double *last_loss_host) {
+    sr_status st = check_ready(p);
+    if (st != SR_OK) return st;
+    if (!params_dev || !cfg || n_steps < 0) return fail(SR_ERR_ARG, "bad argument");
+    if (cfg->kind != SR_ADABELIEF && cfg->kind != SR_ADAM) return fail(SR_ERR_ARG, "unknown optimiser");
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    if ((st = run_steps(p->plan, p->stream, params_dev, n_steps, cfg, losses_dev, &p->plan->s_raw)) != SR_OK) return st;
+    if (last_loss_host) {
+        SR_CUDA(cudaMemcpyAsync(last_loss_host, p->plan->total, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        SR_CUDA(cudaStreamSynchronize(p->stream));
+        if (p->pending_check && (st = check_flag(p)) != SR_OK) return st;
+    }
+    return SR_OK;
+}
+
+sr_status sr_reset_optimizer(sr_problem *p) {
+    if (!p) return fail(SR_ERR_ARG, "NULL problem");
+    sr_status st;
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    if ((st = ensure_opt_buffers(p->plan)) != SR_OK) return st;
+    Plan *pl = p->plan;
+    SR_CUDA(cudaMemsetAsync(pl->opt_m, 0, sizeof(float) * pl->n_params, p->stream));
+    SR_CUDA(cudaMemsetAsync(pl->opt_v, 0, sizeof(float) * pl->n_params, p->stream));
+    SR_CUDA(cudaMemsetAsync(pl->d_t, 0, sizeof(long long), p->stream));
+    return SR_OK;
+}
+
+sr_status sr_get_state(sr_problem *p, float *m_dev, float *v_dev, int64_t *t) {
+    if (!p || !m_dev || !v_dev || !t) return fail(SR_ERR_ARG, "NULL argument");
+    sr_status st;
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    if ((st = ensure_opt_buffers(p->plan)) != SR_OK) return st;
+    Plan *pl = p->plan;
+    long long tv = 0;
+    SR_CUDA(cudaMemcpyAsync(m_dev, pl->opt_m, sizeof(float) * pl->n_params, cudaMemcpyDeviceToDevice, p->stream));
+    SR_CUDA(cudaMemcpyAsync(v_dev, pl->opt_v, sizeof(float) * pl->n_params, cudaMemcpyDeviceToDevice, p->stream));
+    SR_CUDA(cudaMemcpyAsync(&tv, pl->d_t, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
+    SR_CUDA(cudaStreamSynchronize(p->stream));
+    *t = (int64_t)tv;
+    return SR_OK;
+}
+
+sr_status sr_set_state(sr_problem *p, const float *m_dev, const float *v_dev, int64_t t) {
+    if (!p || !m_dev || !v_dev || t < 0) return fail(SR_ERR_ARG, "bad argument");
+    sr_status st;
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    if ((st = ensure_opt_buffers(p->plan)) != SR_OK) return st;
+    Plan *pl = p->plan;
+    long long tv = (long long)t;
+    SR_CUDA(cudaMemcpyAsync(pl->opt_m, m_dev, sizeof(float) * pl->n_params, cudaMemcpyDeviceToDevice, p->stream));
+    SR_CUDA(cudaMemcpyAsync(pl->opt_v, v_dev, sizeof(float) * pl->n_params, cudaMemcpyDeviceToDevice, p->stream));
+    SR_CUDA(cudaMemcpyAsync(pl->d_t, &tv, sizeof(long long), cudaMemcpyHostToDevice, p->stream));
+    SR_CUDA(cudaStreamSynchronize(p->stream));
+    return SR_OK;
+}
+
+int sr_launches_per_eval(const sr_problem *p) { return (p && p->plan) ? p->plan->launches : 0; }
+
+// --- batches ------------------------------------------------------------------------------
+
+sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream, sr_batch **out) {
+    if (!out) return fail(SR_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!problems || n < 1) return fail(SR_ERR_ARG, "empty batch");
+    for (int i = 0; i < n; ++i) {
+        sr_status st = check_ready(problems[i]);
+        if (st != SR_OK) return st;
+        if (problems[i]->desc.kind != SR_DECONV)
+            return fail(SR_ERR_UNSUPPORTED, "batches hold deconvolution problems (field %d is a PSF fit)", i);
+    }
+    sr_batch *b = new (std::nothrow) sr_batch();
+    if (!b) return fail(SR_ERR_OOM, "host allocation failed");
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->probs.assign(problems, problems + n);
+    b->plan = new (std::nothrow) Plan();
+    if (!b->plan) {
+        delete b;
+        return fail(SR_ERR_OOM, "host allocation failed");
+    }
+    sr_status st = build_plan(b->plan, problems, n, false);
+    if (st != SR_OK) {
+        delete b->plan;
+        delete b;
+        return st;
+    }
+    *out = b;
+    return SR_OK;
+}
+
+sr_status sr_batch_destroy(sr_batch *b) {
+    if (!b) return SR_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    delete b->plan;
+    delete b;
+    return SR_OK;
+}
+
+size_t sr_batch_param_count(const sr_batch *b) { return b ? b->plan->n_params : 0; }
+
+sr_status sr_batch_param_offset(const sr_batch *b, int i, size_t *offset) {
+    if (!b || !offset || i < 0 || i >= (int)b->probs.size()) return fail(SR_ERR_ARG, "bad argument");
+    *offset = b->plan->param_off[i];
+    return SR_OK;
+}
+
+static sr_status batch_check(sr_batch *b) {
+    for (sr_problem *p : b->probs) {
+        if (p->pending_check) {
+            sr_status st = check_flag(p);
+            if (st != SR_OK) return st;
+        }
+    }
+    return SR_OK;
+}
+
+sr_status sr_batch_loss_and_grad(sr_batch *b, const float *params_dev, double *losses_dev, double *total_dev,
+                                 double *total_host, float *grad_dev) {
+    if (!b || !params_dev || !grad_dev) return fail(SR_ERR_ARG, "NULL argument");
+    Plan *pl = b->plan;
+    pl->launches = run_eval(pl, params_dev, grad_dev, b->stream, nullptr);
+    SR_CUDA(cudaGetLastError());
+    if (losses_dev)
+        SR_CUDA(cudaMemcpyAsync(losses_dev, pl->losses, sizeof(double) * pl->n_fields, cudaMemcpyDeviceToDevice, b->stream));
+    if (total_dev) SR_CUDA(cudaMemcpyAsync(total_dev, pl->total, sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    if (total_host) {
+        SR_CUDA(cudaMemcpyAsync(total_host, pl->total, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        SR_CUDA(cudaStreamSynchronize(b->stream));
+        sr_status st = batch_check(b);
+        if (st != SR_OK) return st;
+        if (!std::isfinite(*total_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
+    }
+    return SR_OK;
+}
+
+sr_status sr_batch_loss_and_grad_host(sr_batch *b, const float *params_host, double *total_host, float *grad_host) {
+    if (!b || !params_host || !total_host || !grad_host) return fail(SR_ERR_ARG, "NULL argument");
+    Plan *pl = b->plan;
+    sr_status st;
+    if ((st = ensure_opt_buffers(pl)) != SR_OK) return st;
+    if (!pl->params_int && (st = pl->arena.alloc(&pl->params_int, pl->n_params)) != SR_OK) return st;
+    SR_CUDA(cudaMemcpyAsync(pl->params_int, params_host, sizeof(float) * pl->n_params, cudaMemcpyHostToDevice, b->stream));
+    if ((st = sr_batch_loss_and_grad(b, pl->params_int, nullptr, nullptr, nullptr, pl->grad_int)) != SR_OK) return st;
+    SR_CUDA(cudaMemcpyAsync(grad_host, pl->grad_int, sizeof(float) * pl->n_params, cudaMemcpyDeviceToHost, b->stream));
+    SR_CUDA(cudaMemcpyAsync(total_host, pl->total, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    SR_CUDA(cudaStreamSynchronize(b->stream));
+    if ((st = batch_check(b)) != SR_OK) return st;
+    if (!std::isfinite(*total_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
+    return SR_OK;
+}
+
+sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_optim_cfg *cfg, double *last_total_host) {
+    if (!b || !params_dev || !cfg || n_steps < 0) return fail(SR_ERR_ARG, "bad argument");
+    sr_status st = run_steps(b->plan, b->stream, params_dev, n_steps, cfg, nullptr, nullptr);
+    if (st != SR_OK) return st;
+    if (last_total_host) {
+        SR_CUDA(cudaMemcpyAsync(last_total_host, b->plan->total, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        SR_CUDA(cudaStreamSynchronize(b->stream));
+        if ((st = batch_check(b)) != SR_OK) return st;
+    }
+    return SR_OK;
+}
+
+sr_status sr_batch_reset_optimizer(sr_batch *b) {
+    if (!b) return fail(SR_ERR_ARG, "NULL batch");
+    Plan *pl = b->plan;
+    sr_status st;
+    if ((st = ensure_opt_buffers(pl)) != SR_OK) return st;
+    SR_CUDA(cudaMemsetAsync(pl->opt_m, 0, sizeof(float) * pl->n_params, b->stream));
+    SR_CUDA(cudaMemsetAsync(pl->opt_v, 0, sizeof(float) * pl->n_params, b->stream));
+    SR_CUDA(cudaMemsetAsync(pl->d_t, 0, sizeof(long long), b->stream));
+    return SR_OK;
+}
+
+int sr_batch_launches_per_eval(const sr_batch *b) { return b ? b->plan->launches : 0; }
+
+sr_status sr_batch_profile(sr_batch *b, int enable) {
+    if (!b) return fail(SR_ERR_ARG, "NULL batch");
+    Plan *pl = b->plan;
+    if (enable && pl->prof_ev.empty()) {
+        pl->prof_ev.resize(3 * 512);
+        for (cudaEvent_t &e : pl->prof_ev) SR_CUDA(cudaEventCreate(&e));
+    }
+    pl->profiling = enable != 0;
+    pl->prof_count = 0;
+    return SR_OK;
+}
+
+sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms) {
+    if (!b || !n_evals || !fwd_ms || !adj_ms) return fail(SR_ERR_ARG, "NULL argument");
+    Plan *pl = b->plan;
+    *n_evals = 0;
+    *fwd_ms = *adj_ms = 0.0;
+    if (pl->prof_ev.empty()) return SR_OK;
+    SR_CUDA(cudaStreamSynchronize(b->stream));
+    const int ring = (int)pl->prof_ev.size() / 3;
+    const int n = std::min(pl->prof_count, ring);
+    for (int i = 0; i < n; ++i) {
+        float a = 0.f, c = 0.f;
+        SR_CUDA(cudaEventElapsedTime(&a, pl->prof_ev[3 * i], pl->prof_ev[3 * i + 1]));
+        SR_CUDA(cudaEventElapsedTime(&c, pl->prof_ev[3 * i + 1], pl->prof_ev[3 * i + 2]));
+        *fwd_ms += a;
+        *adj_ms += c;
+    }
+    *n_evals = n;
+    return SR_OK;
+}
+
+}  // extern "C"

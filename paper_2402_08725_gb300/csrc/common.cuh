@@ -1,0 +1,78 @@
+// Internal definitions shared by the kernels and the host side of the library.
+// Not part of the public ABI (see include/starred.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "starred.h"
+
+namespace sr {
+
+// Narrow Gaussian r of Eq. 1 (FWHM 2 fine px): sigma^2 = 1/(2 ln 2), so
+// g(v) = exp(-|v|^2/(2 sigma^2)) / (2 pi sigma^2) = (ln 2 / pi) * 2^(-|v|^2).
+constexpr float kGaussNorm = 0.220635600152f;      // ln 2 / pi
+constexpr float kGaussInvSig2 = 1.386294361120f;   // 1/sigma^2 = 2 ln 2
+constexpr float kGauss1Norm = 0.469718639349f;     // 1-D factor: sqrt(ln 2 / pi)
+// Point sources are rasterised on a 16 x 16 fine-pixel window starting at
+// floor(centre) - 7: every omitted pixel is >= 8 px away, where g < 1e-19 g(0).
+constexpr int kWin = 16;
+constexpr int kWinLo = 7;
+// 1-D Gaussian taps of the PSF-fit blur: |t| <= 8 (g1(8)/g1(0) = 2^-64).
+constexpr int kBlurHalf = 8;
+
+constexpr int kMaxScales = 8;
+constexpr int kThreads = 256;
+
+struct FieldDev {
+    int kind;          // SR_DECONV / SR_PSF
+    int E, N, f, K, M, J, F;
+    int Tk, tau_lo;    // extent and first index of the polyphase folded kernels
+    int n_tiles;       // output tiles per epoch (fwd/adj work items)
+    float lambda;
+    const float *Wd;       // [J-1] prior weights (device, owned by the problem)
+    long long param_off;   // offset of the field in the parameter vector
+    long long ebuf_off;    // floats, E*N*N residual-weight buffer
+    long long gbuf_off;    // floats, E*f*f*N*N per-epoch adjoint images (polyphase layout)
+    long long tile_slot;   // first (epoch, tile) slot of the field's partial sums
+    long long ps_slot;     // first (epoch, source) slot
+    long long l1_slot;     // first (level, chunk) slot of the prior partial sums
+    int n_chunks;          // 256-pixel chunks of the F x F grid
+    const float *d;        // [E][N][N]
+    const float *w;        // [E][N][N] inverse variance (0 = masked)
+    const float *kappa;    // [E][f*f][Tk][Tk] folded kernels (DECONV)
+    float *starlet;        // [(J + 2)][F][F] scratch planes
+    float *psf_s;          // PSF kind: [F][F] narrow PSF s = m + b
+    float *psf_tmp;        // PSF kind: [S][3][F][F] row-pass planes (value, d/dx) and adjoint plane
+    float *psf_gs;         // PSF kind: [S][F][F] per-star gradient wrt s
+};
+
+// One output tile of one epoch: rows [y0, y0+h), cols [x0, x0+w) of the data
+// grid.  pg = number of thread groups working on different phases at once.
+struct TileItem {
+    int field;
+    int epoch;
+    int slot;      // (epoch, tile) partial-sum slot
+    short y0, x0, h, w;
+    int pg;
+};
+
+struct ChunkItem {
+    int field;
+    int start;     // first pixel (row-major F*F index) of the chunk
+    int chunk;     // chunk index within the field
+};
+
+}  // namespace sr
+
+// --- host-side helpers shared by the .cu files ---------------------------------
+namespace sr {
+void set_error(const char *fmt, ...);
+sr_status cuda_fail(cudaError_t e, const char *what);
+}  // namespace sr
+
+#define SR_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::sr::cuda_fail(_e, #call);       \
+    } while (0)

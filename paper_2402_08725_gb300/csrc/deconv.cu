@@ -1,0 +1,514 @@
+// Joint multi-epoch deconvolution: loss and gradient kernels (sm_103a).
+//
+// The model of sec. 2.2 (Eq. 9-10) per epoch i is M_i = D S_i (h + P_i) + f^2 Gamma_i,
+// with S_i the convolution by the narrow PSF s_i and D the f x f block sum.
+// D is folded into S once per PSF (set_psfs):
+//     M_i[p] = sum_u kappa_i(f p - u) f_i[u],   kappa_i(t) = sum_{a,b<f} s_i[t + (a,b) + o].
+// Splitting the fine pixel u = f m + phi by its phase phi in [0,f)^2 turns this into f^2
+// ordinary convolutions on the data grid:
+//     M_i[p] = sum_phi sum_tau kappa_{i,phi}(tau) F_phi[p - tau],  F_phi[m] = f_i[f m + phi],
+//     kappa_{i,phi}(tau) = kappa_i(f tau - phi),
+// and the adjoint (D^T then S_i^T) becomes, per phase,
+//     G_{i,phi}[m] = sum_tau kappa_{i,phi}(tau) e_i[m + tau],   e_i = -w (d_i - M_i).
+// This needs f^2 times fewer multiply-adds than the fine-resolution form.
+//
+// Kernels here:
+//   kappa_prep_kernel   folded polyphase kernels, once per set_psfs
+//   fwd_kernel<R>       persistent over (field, epoch, tile): stage F_phi tiles of h plus the
+//                       rasterised point sources in shared memory, accumulate M over all phases,
+//                       residual, FP64 chi^2 and sum(e) partials (warp shuffles), write e
+//   adj_kernel<R>       persistent over (field, epoch, tile): stage the e tile once, correlate
+//                       with each phase's kernel, write G_{i,phi} (per-epoch images)
+//   psgrad_kernel       per (epoch, source): <G_i, g>, <G_i, grad g> on the source window
+//   hgrad_kernel        dL/dh = sum_i G_i + starlet prior gradient (fixed epoch order, FP64)
+//   finalize_kernel     loss, dGamma, da, dc, ddelta per field in fixed order
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "corr.cuh"
+
+namespace sr {
+
+// ---------------------------------------------------------------------------------------
+// Folded kernels: kappa_{i,phi}(tau) for tau in [tau_lo, tau_lo + Tk)^2, stored
+// [E][f*f][Tk][Tk] (phi = phy*f + phx).
+// ---------------------------------------------------------------------------------------
+__global__ void kappa_prep_kernel(const float *__restrict__ s, float *__restrict__ kappa, int E, int K, int f,
+                                  int Tk, int tau_lo) {
+    const long long total = (long long)E * f * f * Tk * Tk;
+    const int o = K / 2;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long r = idx;
+        const int tx = (int)(r % Tk); r /= Tk;
+        const int ty = (int)(r % Tk); r /= Tk;
+        const int ph = (int)(r % (f * f)); r /= (f * f);
+        const int i = (int)r;
+        const int phy = ph / f, phx = ph - phy * f;
+        // kappa(t) with t = f*tau - phi; kappa(t) = sum_{a,b<f} s[t + (a,b) + o]
+        const int t_y = f * (tau_lo + ty) - phy;
+        const int t_x = f * (tau_lo + tx) - phx;
+        double acc = 0.0;
+        const float *si = s + (long long)i * K * K;
+        for (int a = 0; a < f; ++a) {
+            const int qy = t_y + a + o;
+            if (qy < 0 || qy >= K) continue;
+            for (int b = 0; b < f; ++b) {
+                const int qx = t_x + b + o;
+                if (qx < 0 || qx >= K) continue;
+                acc += (double)si[qy * K + qx];
+            }
+        }
+        kappa[idx] = (float)acc;
+    }
+}
+
+void launch_kappa_prep(const float *s, float *kappa, int E, int K, int f, int Tk, int tau_lo, cudaStream_t st) {
+    const long long total = (long long)E * f * f * Tk * Tk;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 32) grid = 152 * 32;
+    kappa_prep_kernel<<<grid, 256, 0, st>>>(s, kappa, E, K, f, Tk, tau_lo);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum of two doubles (fixed shuffle tree, warps summed in order).
+__device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[kThreads / 32]) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = a;
+        red[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            sa += red[0][i];
+            sb += red[1][i];
+        }
+        a = sa;
+        b = sb;
+    }
+}
+
+struct TileGeom {
+    int h, w, PG, per_group, g, row, chunk, xrows, xcols, xpitch, kpitch;
+};
+
+template <int R>
+__device__ __forceinline__ TileGeom tile_geom(const TileItem &t, int Tk) {
+    TileGeom G;
+    G.h = t.h;
+    G.w = t.w;
+    G.PG = t.pg;
+    const int chunks = G.w / R;
+    G.per_group = G.h * chunks;
+    G.g = threadIdx.x / G.per_group;
+    const int l = threadIdx.x - G.g * G.per_group;
+    G.row = l % G.h;       // consecutive lanes take consecutive rows: odd pitch -> no bank conflicts
+    G.chunk = l / G.h;
+    G.xrows = G.h + Tk - 1;
+    G.xcols = G.w + Tk - 1;
+    G.xpitch = (G.w + Tk) | 1;
+    G.kpitch = (Tk + 3) & ~3;
+    return G;
+}
+
+__device__ __forceinline__ int align4(int n) { return (n + 3) & ~3; }
+
+// ceil(a / b) for b > 0 and any sign of a
+__device__ __forceinline__ int ceil_div(int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); }
+
+// Fine-grid centre of point source k in epoch i: (F-1)/2 + f (c_k + delta_i).
+__device__ __forceinline__ float2 source_centre(const float *__restrict__ c, const float *__restrict__ dl, int k,
+                                                int F, int f) {
+    const float u0 = 0.5f * (float)(F - 1);
+    return make_float2(u0 + (float)f * (c[2 * k] + dl[0]), u0 + (float)f * (c[2 * k + 1] + dl[1]));
+}
+
+__device__ __forceinline__ float gauss_at(float dx, float dy) {
+    return kGaussNorm * exp2f(-(dx * dx + dy * dy));
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ items, int n_items,
+           int *__restrict__ counter, const float *__restrict__ params, float *__restrict__ ebuf,
+           double *__restrict__ chi_part, double *__restrict__ se_part) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_item;
+    __shared__ double s_red[2][kThreads / 32];
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const TileItem t = items[it];
+        const FieldDev &fd = fields[t.field];
+        const int f = fd.f, N = fd.N, F = fd.F, Tk = fd.Tk, M = fd.M, E = fd.E;
+        const int thi = fd.tau_lo + Tk - 1;
+        const int nph = f * f;
+        const TileGeom G = tile_geom<R>(t, Tk);
+        const int xsize = G.xrows * G.xpitch;
+        float *Kall = smem + align4(G.PG * xsize);
+        const float *hpar = params + fd.param_off;
+        const float *apar = hpar + (long long)F * F + (long long)t.epoch * M;
+        const float *cpar = hpar + (long long)F * F + (long long)E * M;
+        const float *dpar = cpar + 2 * M + 2 * t.epoch;
+        const float gam = cpar[2 * M + 2 * E + t.epoch];
+        const int my0 = t.y0 - thi, mx0 = t.x0 - thi;  // data-grid origin of the staged tiles
+
+        float acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0.f;
+
+        for (int iter = 0; iter < nph / G.PG; ++iter) {
+            // stage F_phi = h[f m + phi] (zero outside the grid) for every group's phase
+            const int per = G.xrows * G.xcols;
+            for (int idx = tid; idx < G.PG * per; idx += kThreads) {
+                const int grp = idx / per;
+                const int rr = idx - grp * per;
+                const int i = rr / G.xcols, j = rr - i * G.xcols;
+                const int ph = iter * G.PG + grp;
+                const int phy = ph / f, phx = ph - phy * f;
+                const int my = my0 + i, mx = mx0 + j;
+                float v = 0.f;
+                if (my >= 0 && my < N && mx >= 0 && mx < N) v = __ldg(hpar + (long long)(f * my + phy) * F + f * mx + phx);
+                smem[grp * xsize + i * G.xpitch + j] = v;
+            }
+            // flipped folded kernels: Kp[jy][jx] = kappa_phi(thi - jy, thi - jx)
+            const int ksz = Tk * G.kpitch;
+            const float *kap = fd.kappa + (long long)t.epoch * nph * Tk * Tk;
+            for (int idx = tid; idx < G.PG * ksz; idx += kThreads) {
+                const int grp = idx / ksz;
+                const int rr = idx - grp * ksz;
+                const int jy = rr / G.kpitch, jx = rr - jy * G.kpitch;
+                const int ph = iter * G.PG + grp;
+                float v = 0.f;
+                if (jx < Tk) v = __ldg(kap + ((long long)ph * Tk + (Tk - 1 - jy)) * Tk + (Tk - 1 - jx));
+                Kall[idx] = v;
+            }
+            __syncthreads();
+            // point-source channel (Eq. 9): add a_ki g(u - centre) on the window pixels of this phase
+            if (M > 0) {
+                const int nw = kWin / f + 1;
+                const int work = G.PG * M * nw * nw;
+                for (int idx = tid; idx < work; idx += kThreads) {
+                    int rr = idx;
+                    const int b = rr % nw; rr /= nw;
+                    const int a = rr % nw; rr /= nw;
+                    const int k = rr % M; rr /= M;
+                    const int grp = rr;
+                    const int ph = iter * G.PG + grp;
+                    const int phy = ph / f, phx = ph - phy * f;
+                    const float2 cen = source_centre(cpar, dpar, k, F, f);
+                    const int uy_lo = (int)floorf(cen.y) - kWinLo, ux_lo = (int)floorf(cen.x) - kWinLo;
+                    // data rows/cols m whose phase pixel f m + phi lies in the window
+                    const int my = ceil_div(uy_lo - phy, f) + a;
+                    const int mx = ceil_div(ux_lo - phx, f) + b;
+                    const int uy = f * my + phy, ux = f * mx + phx;
+                    if (uy < uy_lo || uy >= uy_lo + kWin || ux < ux_lo || ux >= ux_lo + kWin) continue;
+                    if (uy < 0 || uy >= F || ux < 0 || ux >= F) continue;
+                    const int i = my - my0, j = mx - mx0;
+                    if (i < 0 || i >= G.xrows || j < 0 || j >= G.xcols) continue;
+                    const float val = apar[k] * gauss_at((float)ux - cen.x, (float)uy - cen.y);
+                    atomicAdd(&smem[grp * xsize + i * G.xpitch + j], val);
+                }
+                __syncthreads();
+            }
+            if (G.g < G.PG)
+                corr_accumulate<R>(acc, smem + G.g * xsize + G.row * G.xpitch + G.chunk * R, G.xpitch,
+                                   Kall + G.g * ksz, G.kpitch, Tk);
+            __syncthreads();
+        }
+        // sum the phase groups (fixed order)
+        if (G.PG > 1) {
+            float *red = smem;
+            if (G.g >= 1 && G.g < G.PG) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) red[((G.g - 1) * G.h + G.row) * G.w + G.chunk * R + r] = acc[r];
+            }
+            __syncthreads();
+            if (G.g == 0) {
+                for (int gg = 1; gg < G.PG; ++gg) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += red[((gg - 1) * G.h + G.row) * G.w + G.chunk * R + r];
+                }
+            }
+        }
+        // residual, chi^2 (FP64 accumulation), e = -w r
+        double chi = 0.0, se = 0.0;
+        const int py = t.y0 + G.row;
+        if (G.g == 0 && py < N) {
+            const float bg = (float)(f * f) * gam;
+            const long long base = ((long long)t.epoch * N + py) * N;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int px = t.x0 + G.chunk * R + r;
+                if (px < N) {
+                    const float Mv = acc[r] + bg;
+                    const float res = __ldg(fd.d + base + px) - Mv;
+                    const float wv = __ldg(fd.w + base + px);
+                    chi += (double)(0.5f * wv * res * res);
+                    const float e = -wv * res;
+                    ebuf[fd.ebuf_off + base + px] = e;
+                    se += (double)e;
+                }
+            }
+        }
+        block_sum2(chi, se, s_red);
+        if (tid == 0) {
+            chi_part[t.slot] = chi;
+            se_part[t.slot] = se;
+        }
+        __syncthreads();
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+adj_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ items, int n_items,
+           int *__restrict__ counter, const float *__restrict__ ebuf, float *__restrict__ gbuf) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const TileItem t = items[it];
+        const FieldDev &fd = fields[t.field];
+        const int f = fd.f, N = fd.N, Tk = fd.Tk, tlo = fd.tau_lo;
+        const int nph = f * f;
+        const TileGeom G = tile_geom<R>(t, Tk);
+        const int ysize = G.xrows * G.xpitch;
+        float *Kall = smem + align4(ysize);
+        const int my0 = t.y0 + tlo, mx0 = t.x0 + tlo;
+        const float *ep = ebuf + fd.ebuf_off + (long long)t.epoch * N * N;
+        // stage e on the tile plus halo (zero outside the data grid)
+        for (int idx = tid; idx < G.xrows * G.xcols; idx += kThreads) {
+            const int i = idx / G.xcols, j = idx - i * G.xcols;
+            const int my = my0 + i, mx = mx0 + j;
+            float v = 0.f;
+            if (my >= 0 && my < N && mx >= 0 && mx < N) v = ep[(long long)my * N + mx];
+            smem[i * G.xpitch + j] = v;
+        }
+        const int ksz = Tk * G.kpitch;
+        const float *kap = fd.kappa + (long long)t.epoch * nph * Tk * Tk;
+        float *gout = gbuf + fd.gbuf_off + (long long)t.epoch * nph * N * N;
+        for (int iter = 0; iter < nph / G.PG; ++iter) {
+            for (int idx = tid; idx < G.PG * ksz; idx += kThreads) {
+                const int grp = idx / ksz;
+                const int rr = idx - grp * ksz;
+                const int jy = rr / G.kpitch, jx = rr - jy * G.kpitch;
+                const int ph = iter * G.PG + grp;
+                Kall[idx] = (jx < Tk) ? __ldg(kap + ((long long)ph * Tk + jy) * Tk + jx) : 0.f;
+            }
+            __syncthreads();
+            if (G.g < G.PG) {
+                float acc[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = 0.f;
+                corr_accumulate<R>(acc, smem + G.row * G.xpitch + G.chunk * R, G.xpitch, Kall + G.g * ksz,
+                                   G.kpitch, Tk);
+                const int ph = iter * G.PG + G.g;
+                const int py = t.y0 + G.row;
+                if (py < N) {
+                    float *go = gout + ((long long)ph * N + py) * N;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int px = t.x0 + G.chunk * R + r;
+                        if (px < N) go[px] = acc[r];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// dL/da_ki = <G_i, g_ki>,  dL/d(centre) = a_ki <G_i, g_ki (u - centre)/sigma^2>  (window).
+// One warp per (epoch, source) slot; ps_items[s] = (field, epoch, k).
+__global__ void psgrad_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ ps_items, int n,
+                              const float *__restrict__ params, const float *__restrict__ gbuf,
+                              float *__restrict__ ps_da, float *__restrict__ ps_du) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int4 w4 = ps_items[warp];
+    const FieldDev &fd = fields[w4.x];
+    const int i = w4.y, k = w4.z;
+    const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E;
+    const int nph = f * f;
+    const float *hpar = params + fd.param_off;
+    const float *cpar = hpar + (long long)F * F + (long long)E * M;
+    const float *dpar = cpar + 2 * M + 2 * i;
+    const float a = hpar[(long long)F * F + (long long)i * M + k];
+    const float2 cen = source_centre(cpar, dpar, k, F, f);
+    const int uy_lo = (int)floorf(cen.y) - kWinLo, ux_lo = (int)floorf(cen.x) - kWinLo;
+    const float *G = gbuf + fd.gbuf_off + (long long)i * nph * N * N;
+    float sa = 0.f, sx = 0.f, sy = 0.f;
+    for (int idx = lane; idx < kWin * kWin; idx += 32) {
+        const int uy = uy_lo + idx / kWin, ux = ux_lo + idx % kWin;
+        if (uy < 0 || uy >= F || ux < 0 || ux >= F) continue;
+        const int my = uy / f, mx = ux / f;
+        const int ph = (uy - my * f) * f + (ux - mx * f);
+        const float gv = G[((long long)ph * N + my) * N + mx];
+        const float dx = (float)ux - cen.x, dy = (float)uy - cen.y;
+        const float gg = gv * gauss_at(dx, dy);
+        sa += gg;
+        sx += gg * dx;
+        sy += gg * dy;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sx += __shfl_down_sync(0xffffffffu, sx, o);
+        sy += __shfl_down_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+        const long long s = fd.ps_slot + (long long)i * M + k;
+        ps_da[s] = sa;
+        ps_du[2 * s] = a * kGaussInvSig2 * sx;
+        ps_du[2 * s + 1] = a * kGaussInvSig2 * sy;
+    }
+}
+
+// dL/dh[u] = T0[u] + sum_i G_i[u]: one thread per polyphase index q = phi*N*N + m.
+__global__ void hgrad_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__restrict__ chunks, int n_chunks,
+                             const float *__restrict__ gbuf, float *__restrict__ grad) {
+    const int c = blockIdx.x;
+    if (c >= n_chunks) return;
+    const ChunkItem ch = chunks[c];
+    const FieldDev &fd = fields[ch.field];
+    const int q = ch.start + threadIdx.x;
+    const int f = fd.f, N = fd.N, F = fd.F;
+    if (q >= F * F) return;
+    const long long plane = (long long)f * f * N * N;
+    const float *G = gbuf + fd.gbuf_off + q;
+    double s = 0.0;
+    for (int i = 0; i < fd.E; ++i) s += (double)G[(long long)i * plane];
+    const int ph = q / (N * N), m = q - ph * N * N;
+    const int my = m / N, mx = m - my * N;
+    const int u = (f * my + ph / f) * F + f * mx + ph % f;
+    const float *T0 = fd.starlet + (long long)fd.J * F * F;
+    grad[fd.param_off + u] = (float)(s + (double)T0[u]);
+}
+
+// Per-field assembly of the loss and the small parameter blocks, in fixed order.
+__global__ void __launch_bounds__(kThreads)
+finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ chi_part,
+                const double *__restrict__ se_part, const double *__restrict__ l1_part,
+                const float *__restrict__ ps_da, const float *__restrict__ ps_du, float *__restrict__ grad,
+                double *__restrict__ losses) {
+    __shared__ double s_red[2][kThreads / 32];
+    const FieldDev &fd = fields[blockIdx.x];
+    const int E = fd.E, M = fd.M, F = fd.F, f = fd.f;
+    double chi = 0.0, l1 = 0.0;
+    const long long nt = (long long)E * fd.n_tiles;
+    for (long long s = threadIdx.x; s < nt; s += blockDim.x) chi += chi_part[fd.tile_slot + s];
+    const long long nl = (long long)(fd.J - 1) * fd.n_chunks;
+    for (long long s = threadIdx.x; s < nl; s += blockDim.x) l1 += l1_part[fd.l1_slot + s];
+    block_sum2(chi, l1, s_red);
+    if (threadIdx.x == 0) losses[blockIdx.x] = chi + l1;
+    float *g = grad + fd.param_off + (long long)F * F;  // a block
+    for (int s = threadIdx.x; s < E * M; s += blockDim.x) g[s] = ps_da[fd.ps_slot + s];
+    float *gc = g + (long long)E * M;
+    for (int s = threadIdx.x; s < 2 * M; s += blockDim.x) {
+        const int k = s >> 1, ax = s & 1;
+        double acc = 0.0;
+        for (int i = 0; i < E; ++i) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
+        gc[s] = (float)(f * acc);
+    }
+    float *gd = gc + 2 * M;
+    for (int s = threadIdx.x; s < 2 * E; s += blockDim.x) {
+        const int i = s >> 1, ax = s & 1;
+        double acc = 0.0;
+        for (int k = 0; k < M; ++k) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
+        gd[s] = (float)(f * acc);
+    }
+    float *gg = gd + 2 * E;
+    for (int i = threadIdx.x; i < E; i += blockDim.x) {
+        double acc = 0.0;
+        for (int tt = 0; tt < fd.n_tiles; ++tt) acc += se_part[fd.tile_slot + (long long)i * fd.n_tiles + tt];
+        gg[i] = (float)((double)(f * f) * acc);
+    }
+}
+
+__global__ void total_kernel(const double *__restrict__ losses, int n, double *__restrict__ total) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += losses[i];
+        *total = s;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------------
+static int fwd_smem_bytes_item(const TileItem &t, int Tk, bool fwd) {
+    const int xrows = t.h + Tk - 1;
+    const int xpitch = (t.w + Tk) | 1;
+    const int kpitch = (Tk + 3) & ~3;
+    const int xs = fwd ? t.pg * xrows * xpitch : xrows * xpitch;
+    int red = 0;
+    if (fwd && t.pg > 1) red = (t.pg - 1) * t.h * t.w;
+    int xpart = ((xs + 3) & ~3);
+    if (red > xpart) xpart = (red + 3) & ~3;
+    return (xpart + t.pg * Tk * kpitch) * (int)sizeof(float);
+}
+
+int tile_smem_bytes(const TileItem &t, int Tk, bool fwd) { return fwd_smem_bytes_item(t, Tk, fwd); }
+
+sr_status configure_tile_kernels(int smem_fwd, int smem_adj) {
+    SR_CUDA(cudaFuncSetAttribute(fwd_kernel<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_fwd));
+    SR_CUDA(cudaFuncSetAttribute(adj_kernel<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_adj));
+    return SR_OK;
+}
+
+sr_status occupancy_tile_kernels(int smem_fwd, int smem_adj, int *blocks_fwd, int *blocks_adj) {
+    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_fwd, fwd_kernel<kR>, kThreads, smem_fwd));
+    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_adj, adj_kernel<kR>, kThreads, smem_adj));
+    return SR_OK;
+}
+
+void launch_fwd(const FieldDev *fields, const TileItem *items, int n_items, int *counter, const float *params,
+                float *ebuf, double *chi_part, double *se_part, int grid, int smem, cudaStream_t st) {
+    fwd_kernel<kR><<<grid, kThreads, smem, st>>>(fields, items, n_items, counter, params, ebuf, chi_part, se_part);
+}
+
+void launch_adj(const FieldDev *fields, const TileItem *items, int n_items, int *counter, const float *ebuf,
+                float *gbuf, int grid, int smem, cudaStream_t st) {
+    adj_kernel<kR><<<grid, kThreads, smem, st>>>(fields, items, n_items, counter, ebuf, gbuf);
+}
+
+void launch_psgrad(const FieldDev *fields, const int4 *ps_items, int n, const float *params, const float *gbuf,
+                   float *ps_da, float *ps_du, cudaStream_t st) {
+    if (n <= 0) return;
+    const int warps_per_block = 8;
+    psgrad_kernel<<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+        fields, ps_items, n, params, gbuf, ps_da, ps_du);
+}
+
+void launch_hgrad(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, const float *gbuf, float *grad,
+                  cudaStream_t st) {
+    hgrad_kernel<<<n_chunks, 256, 0, st>>>(fields, chunks, n_chunks, gbuf, grad);
+}
+
+void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_part, const double *se_part,
+                     const double *l1_part, const float *ps_da, const float *ps_du, float *grad, double *losses,
+                     double *total, cudaStream_t st) {
+    finalize_kernel<<<n_fields, kThreads, 0, st>>>(fields, chi_part, se_part, l1_part, ps_da, ps_du, grad, losses);
+    total_kernel<<<1, 32, 0, st>>>(losses, n_fields, total);
+}
+
+}  // namespace sr

@@ -1,0 +1,74 @@
+// Host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace sr {
+
+// Outputs per thread of the register-blocked correlation (a compile-time width).
+constexpr int kR = 16;
+
+// --- deconvolution (deconv.cu) ---
+void launch_kappa_prep(const float *s, float *kappa, int E, int K, int f, int Tk, int tau_lo, cudaStream_t st);
+int tile_smem_bytes(const TileItem &t, int Tk, bool fwd);
+sr_status configure_tile_kernels(int smem_fwd, int smem_adj);
+sr_status occupancy_tile_kernels(int smem_fwd, int smem_adj, int *blocks_fwd, int *blocks_adj);
+void launch_fwd(const FieldDev *fields, const TileItem *items, int n_items, int *counter, const float *params,
+                float *ebuf, double *chi_part, double *se_part, int grid, int smem, cudaStream_t st);
+void launch_adj(const FieldDev *fields, const TileItem *items, int n_items, int *counter, const float *ebuf,
+                float *gbuf, int grid, int smem, cudaStream_t st);
+void launch_psgrad(const FieldDev *fields, const int4 *ps_items, int n, const float *params, const float *gbuf,
+                   float *ps_da, float *ps_du, cudaStream_t st);
+void launch_hgrad(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, const float *gbuf, float *grad,
+                  cudaStream_t st);
+void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_part, const double *se_part,
+                     const double *l1_part, const float *ps_da, const float *ps_du, float *grad, double *losses,
+                     double *total, cudaStream_t st);
+
+// --- starlet prior (starlet.cu) ---
+// Forward levels then adjoint levels for every field of the table; writes the
+// per-(level, chunk) prior partial sums and leaves T0 = dP/dh in plane J of
+// each field's starlet scratch.  Returns the number of launches issued.
+int launch_starlet(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, int Jmax, const float *params,
+                   double *l1_part, cudaStream_t st);
+
+// --- PSF reconstruction (psf.cu) ---
+struct PsfBuffers {
+    float *ebuf;        // [S][N][N]
+    double *star_part;  // [S][n_dchunks][4]: chi2, da, dcx, dcy
+    double *ab_part;    // [n_chunks][2]: dalpha, dbeta partials
+    int n_dchunks;      // data-grid chunks per star
+};
+int launch_psf_eval(const FieldDev *fields, const FieldDev &host_field, const ChunkItem *chunks, int n_chunks,
+                    const float *params, float *grad, const PsfBuffers &pb, double *l1_part, double *losses,
+                    double *total, cudaStream_t st);
+
+// --- plain per-epoch form (plain.cu) ---
+struct PlainBuffers {
+    float *fimg;   // [F][F] rasterised fine image of the current epoch
+    float *conv;   // [F][F] S_i f_i on the fine grid
+    float *ey;     // [F][F] D^T e
+    float *gsum;   // [F][F] running sum over epochs of S_i^T D^T e_i
+    float *gi;     // [F][F] S_i^T D^T e_i of the current epoch
+};
+int launch_plain_eval(const FieldDev *fields, const FieldDev &hf, const float *s_raw, const ChunkItem *chunks,
+                      int n_chunks, const float *params, float *grad, const PlainBuffers &pb, float *ebuf,
+                      double *chi_part, double *se_part, float *ps_da, float *ps_du, const int4 *ps_items,
+                      double *l1_part, double *losses, double *total, cudaStream_t st);
+sr_status configure_plain_kernels(int K);
+
+// --- optimiser (optim.cu) ---
+struct OptimArgs {
+    int kind;
+    float beta1, beta2, eps;
+    float lr[SR_MAX_GROUPS];
+    float lo[SR_MAX_GROUPS];
+};
+void launch_opt_step(long long n, float *params, const float *grad, float *m, float *v, const uint8_t *group,
+                     const OptimArgs &a, long long *t_dev, float *bc_dev, cudaStream_t st);
+
+// --- input preparation (prep.cu) ---
+void launch_inv_var(const float *sigma, float *w, long long n, int *bad_flag, cudaStream_t st);
+void launch_check_finite(const float *x, long long n, int *bad_flag, cudaStream_t st);
+
+}  // namespace sr

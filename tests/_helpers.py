@@ -1,0 +1,89 @@
+"""Shared comparison helpers of the GPU parity tests (CUDA path vs FP64 oracle).
+
+Tolerances (stated per result): loss within 1e-6 relative, measured against
+max(L, 1e-3 * 0.5 * sum w d^2) so that a loss near zero is not held to a relative
+bound it cannot meet; gradient within 1e-4 relative L2 per parameter block.
+"""
+import numpy as np
+
+import oracle
+
+LOSS_RTOL = 1e-6
+GRAD_RTOL = 1e-4
+
+DECONV_BLOCKS = ("h", "a", "c", "delta", "Gamma")
+PSF_BLOCKS = ("b", "moffat", "a", "c")
+
+
+def loss_scale(L_ref, d, sigma):
+    d = np.asarray(d, dtype=np.float64)
+    s = np.asarray(sigma, dtype=np.float64)
+    w = np.where(np.isinf(s), 0.0, 1.0 / (s * s))
+    return max(abs(L_ref), 1e-3 * 0.5 * float(np.sum(w * d * d)))
+
+
+def deconv_blocks(E, N, f, M):
+    F = f * N
+    sizes = [F * F, E * M, 2 * M, 2 * E, E]
+    out, o = {}, 0
+    for name, n in zip(DECONV_BLOCKS, sizes):
+        out[name] = slice(o, o + n)
+        o += n
+    return out
+
+
+def psf_blocks(S, N, f):
+    F = f * N
+    sizes = [F * F, 2, S, 2 * S]
+    out, o = {}, 0
+    for name, n in zip(PSF_BLOCKS, sizes):
+        out[name] = slice(o, o + n)
+        o += n
+    return out
+
+
+def rel_l2(g, ref):
+    g = np.asarray(g, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    nr = np.linalg.norm(ref)
+    if nr == 0.0:
+        return float(np.linalg.norm(g))
+    return float(np.linalg.norm(g - ref) / nr)
+
+
+def oracle_deconv(fd, params=None, **kw):
+    P = fd.params if params is None else params
+    return oracle.deconv_loss_grad(fd.E, fd.N, fd.f, fd.K, fd.M, fd.J, fd.lam, fd.d, fd.sigma, fd.s, fd.W, P, **kw)
+
+
+def check_deconv(fd, loss, grad, params=None, report=None):
+    L_ref, _, g_ref, _ = oracle_deconv(fd, params)
+    scale = loss_scale(L_ref, fd.d, fd.sigma)
+    err = abs(loss - L_ref) / scale
+    res = {"loss": loss, "loss_ref": L_ref, "loss_rel": err}
+    g = np.asarray(grad, dtype=np.float64)
+    for name, sl in deconv_blocks(fd.E, fd.N, fd.f, fd.M).items():
+        if sl.stop > sl.start:
+            res[name] = rel_l2(g[sl], g_ref[sl])
+    if report is not None:
+        report.update(res)
+    assert err <= LOSS_RTOL, res
+    for name in DECONV_BLOCKS:
+        if name in res:
+            assert res[name] <= GRAD_RTOL, (name, res)
+    return res
+
+
+def check_psf(pb, loss, grad, params=None):
+    P = pb.params if params is None else params
+    L_ref, _, g_ref = oracle.psf_loss_grad(pb.S, pb.N, pb.f, pb.J, pb.lam, pb.t, pb.sigma, pb.W, P)
+    scale = loss_scale(L_ref, pb.t, pb.sigma)
+    err = abs(loss - L_ref) / scale
+    res = {"loss": loss, "loss_ref": L_ref, "loss_rel": err}
+    g = np.asarray(grad, dtype=np.float64)
+    for name, sl in psf_blocks(pb.S, pb.N, pb.f).items():
+        res[name] = rel_l2(g[sl], g_ref[sl])
+    assert err <= LOSS_RTOL, res
+    for name in PSF_BLOCKS:
+        assert res[name] <= GRAD_RTOL, (name, res)
+    return res

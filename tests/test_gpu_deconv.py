@@ -1,0 +1,186 @@
+"""GPU parity of the joint-deconvolution loss and gradient (fused D-folded path and
+the plain per-epoch path) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2402_08725_gb300 import synthetic as syn  # noqa: E402
+from tests._helpers import check_deconv, deconv_blocks  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_08725_gb300 import _native
+    _native.load()
+    yield
+
+
+def _run(fd, params=None, conv_mode="auto"):
+    from paper_2402_08725_gb300.binding import Problem
+    prob = Problem.from_field(fd, conv_mode=conv_mode)
+    P = fd.params if params is None else params
+    p = torch.from_numpy(np.ascontiguousarray(P, dtype=np.float32)).cuda()
+    loss, grad = prob.loss_and_grad(p)
+    g = grad.cpu().numpy()
+    prob.close()
+    return loss, g
+
+
+# (E, N, f, K, M, J): tiles of 64 plus ragged tails, odd/even K, f = 1, 2, 3, M = 0
+SMALL = [
+    (3, 24, 2, 15, 2, 3),
+    (2, 80, 2, 21, 3, 4),
+    (2, 20, 3, 17, 1, 3),
+    (2, 16, 1, 9, 2, 3),
+    (2, 30, 2, 64, 2, 4),
+    (3, 37, 2, 12, 0, 3),
+    (1, 8, 2, 5, 1, 2),
+    (2, 70, 3, 30, 2, 5),
+]
+
+
+@pytest.mark.parametrize("E,N,f,K,M,J", SMALL)
+@pytest.mark.parametrize("mode", ["direct", "plain"])
+def test_small_cases_match_oracle(E, N, f, K, M, J, mode):
+    fd = syn.small_deconv(seed=100 + N + K, E=E, N=N, f=f, K=K, M=M, J=J, lam=1.5)
+    loss, g = _run(fd, conv_mode=mode)
+    check_deconv(fd, loss, g)
+
+
+def test_masked_pixels_background_and_edge_source():
+    fd = syn.small_deconv(seed=5, E=3, N=28, f=2, K=13, M=2, J=3, lam=0.8)
+    fd.sigma[0, 3:9, 4:11] = np.inf
+    fd.sigma[2, :, 0] = np.inf
+    h, a, c, dl, gm = syn.unpack_deconv(fd.params.copy(), fd.E, fd.N, fd.f, fd.M)
+    c[1] = (13.2, -13.4)   # near the corner: window clipped by the grid
+    gm = np.array([0.3, -0.2, 0.1])
+    P = syn.pack_deconv(h, a, c, dl, gm)
+    for mode in ("direct", "plain"):
+        loss, g = _run(fd, P, conv_mode=mode)
+        check_deconv(fd, loss, g, params=P)
+
+
+def test_lambda_zero_and_large():
+    for lam in (0.0, 20.0):
+        fd = syn.small_deconv(seed=9, E=2, N=32, f=2, K=17, M=1, J=4, lam=lam)
+        loss, g = _run(fd)
+        check_deconv(fd, loss, g)
+
+
+def test_config1_full_size():
+    fd = syn.config1()
+    for mode in ("direct", "plain"):
+        loss, g = _run(fd, conv_mode=mode)
+        r = check_deconv(fd, loss, g)
+        print("config1", mode, r)
+
+
+def test_config3_full_size():
+    """300 epochs of 64x64, f=2, K=64, 4 sources: all epochs in one persistent launch."""
+    fd = syn.config3()
+    loss, g = _run(fd)
+    r = check_deconv(fd, loss, g)
+    print("config3", r)
+
+
+def test_repeatable_bitwise():
+    fd = syn.small_deconv(seed=4, E=5, N=48, f=2, K=21, M=2, J=4, lam=1.0)
+    from paper_2402_08725_gb300.binding import Problem
+    prob = Problem.from_field(fd)
+    p = torch.from_numpy(fd.params).cuda()
+    l1, g1 = prob.loss_and_grad(p)
+    g1 = g1.clone()
+    l2, g2 = prob.loss_and_grad(p)
+    assert l1 == l2
+    assert torch.equal(g1, g2)
+    prob.close()
+
+
+def test_batch_equals_single_fields_bitwise():
+    """An uneven batch (sizes, epoch counts, starlet depths) gives each field exactly
+    the loss and gradient of its own single-problem evaluation."""
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    shapes = [(3, 32, 4), (5, 48, 5), (2, 64, 4), (4, 96, 6), (1, 20, 3)]
+    fields = [syn.small_deconv(seed=50 + i, E=E, N=N, f=2, K=17, M=1, J=J, lam=1.0)
+              for i, (E, N, J) in enumerate(shapes)]
+    probs = [Problem.from_field(fd) for fd in fields]
+    batch = Batch(probs)
+    P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
+    losses = torch.empty(len(fields), dtype=torch.float64, device="cuda")
+    total, grad = batch.loss_and_grad(P, losses=losses)
+    for i, (fd, pr) in enumerate(zip(fields, probs)):
+        l_i, g_i = pr.loss_and_grad(torch.from_numpy(fd.params).cuda())
+        o = batch.offsets[i]
+        assert losses[i].item() == l_i
+        assert torch.equal(grad[o:o + fd.n_params], g_i)
+    assert abs(total - losses.sum().item()) <= 1e-12 * abs(total)
+    batch.close()
+    for pr in probs:
+        pr.close()
+
+
+def test_config4_full_batch_sampled_fields():
+    """The full uneven batch of 256 fields in one evaluation; fields the oracle
+    evaluates in seconds are checked against it (loss and gradient segments)."""
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    shapes = syn.config4_shapes()
+    fields = syn.config4()
+    probs = [Problem.from_field(fd) for fd in fields]
+    batch = Batch(probs)
+    P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
+    losses = torch.empty(len(fields), dtype=torch.float64, device="cuda")
+    total, grad = batch.loss_and_grad(P, losses=losses)
+    assert np.isfinite(total)
+    cost = [E * N * N for (N, E, J) in shapes]
+    order = np.argsort(cost)
+    picks = list(order[:3]) + [order[len(order) // 4]]
+    g_all = grad.cpu().numpy()
+    ls = losses.cpu().numpy()
+    for i in picks:
+        fd = fields[i]
+        o = batch.offsets[i]
+        r = check_deconv(fd, float(ls[i]), g_all[o:o + fd.n_params])
+        print("config4 field", i, shapes[i], r)
+    batch.close()
+    for pr in probs:
+        pr.close()
+
+
+def test_autograd_function():
+    from paper_2402_08725_gb300.binding import Problem
+    from paper_2402_08725_gb300.torch_ops import starred_loss
+    fd = syn.small_deconv(seed=8, E=2, N=24, f=2, K=11, M=1, J=3, lam=1.0)
+    prob = Problem.from_field(fd)
+    p = torch.from_numpy(fd.params).cuda().requires_grad_(True)
+    L = starred_loss(p, prob)
+    (2.0 * L).backward()
+    loss, g = prob.loss_and_grad(p.detach())
+    assert abs(L.item() - loss) == 0.0
+    assert torch.allclose(p.grad, 2.0 * g, rtol=0, atol=0)
+    prob.close()
+
+
+def test_host_buffer_entry_point_matches_device():
+    from paper_2402_08725_gb300.binding import Problem
+    fd = syn.small_deconv(seed=12, E=3, N=32, f=2, K=13, M=2, J=3, lam=1.0)
+    prob = Problem.from_field(fd)
+    l_h, g_h = prob.loss_and_grad_host(fd.params)
+    l_d, g_d = prob.loss_and_grad(torch.from_numpy(fd.params).cuda())
+    assert l_h == l_d
+    np.testing.assert_array_equal(g_h, g_d.cpu().numpy())
+    prob.close()
+
+
+def test_gradient_blocks_layout_matches_library():
+    from paper_2402_08725_gb300.binding import Problem
+    fd = syn.small_deconv(seed=1, E=3, N=16, f=2, K=7, M=2, J=3)
+    prob = Problem.from_field(fd)
+    lay = prob.layout()
+    blocks = deconv_blocks(fd.E, fd.N, fd.f, fd.M)
+    assert [(s.start, s.stop - s.start) for s in blocks.values()] == lay
+    prob.close()
