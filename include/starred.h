@@ -243,6 +243,37 @@ sr_status sr_batch_profile(sr_batch *b, int enable);
  * forward and adjoint tile kernels.  Synchronises the batch's stream. */
 sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms);
 
+/* Loss and gradient of one deconvolution field, allocating nothing.
+ *
+ * The paper has no counterpart to this call: it exists for callers that cannot
+ * allocate device memory, neither themselves nor through this library, e.g.
+ * code running inside a device-memory pool that was sized once at start-up,
+ * a loop that must never block on the allocator, or a host runtime that owns
+ * all device memory.  It computes what sr_create_problem + set_* +
+ * sr_loss_and_grad compute (folded direct form), but every intermediate buffer
+ * (weights, folded PSF kernels, residual and adjoint images, partial sums,
+ * starlet planes, work lists) lives in one file-scope device array of
+ * SR_NOALLOC_SCRATCH_BYTES (64 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ *
+ * Arguments: desc (DECONV; data_n <= 256; conv_mode AUTO or DIRECT), device
+ * pointers d [E][N][N], sigma [E][N][N], psf [E][K][K] and params (packed
+ * DECONV layout), host pointer W [J-1]; outputs loss_dev (one device double)
+ * and grad_dev (sr_param_count floats, device); cuda_stream orders the work.
+ * Sizes whose scratch would exceed SR_NOALLOC_SCRATCH_BYTES are rejected with
+ * SR_ERR_SHAPE (the message gives the bytes needed); for config-3-sized fields
+ * (300 epochs of 64x64, f = 2, K = 64) about 35 MB are used.
+ * The call does not synchronise and does not validate the values of its
+ * inputs (NaN data give a NaN loss).  The first call on a device looks up the
+ * array's device address and configures the kernels; make that first call
+ * before any stream capture.  Every call uses the same array and leaves the
+ * previous call's contents in it; calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller. */
+#define SR_NOALLOC_SCRATCH_BYTES (64u << 20)
+sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const float *d_dev, const float *sigma_dev,
+                                   const float *psf_dev, const float *W_host, const float *params_dev,
+                                   double *loss_dev, float *grad_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
