@@ -561,7 +561,7 @@ static sr_status run_steps(Plan *pl, cudaStream_t st, float *params, int n_steps
     SR_CUDA(cudaMemcpyAsync(pl->d_hist_ptr, &losses_dev, sizeof(double *), cudaMemcpyHostToDevice, st));
     SR_CUDA(cudaMemcpyAsync(pl->d_hist_base, pl->d_t, sizeof(long long), cudaMemcpyDeviceToDevice, st));
     auto enqueue_one = [&](cudaStream_t s2) {
-        run_eval(pl, params, pl->grad_int, s2, s_raw);
+        pl->launches = run_eval(pl, params, pl->grad_int, s2, s_raw);
         record_loss_kernel<<<1, 32, 0, s2>>>(pl->total, pl->d_hist_ptr, pl->d_t, pl->d_hist_base);
         launch_opt_step((long long)pl->n_params, params, pl->grad_int, pl->opt_m, pl->opt_v, pl->d_group, oa, pl->d_t,
                         pl->d_bc, s2);

@@ -20,7 +20,7 @@
 //   adj_kernel<R>       persistent over (field, epoch, tile): stage the e tile once, correlate
 //                       with each phase's kernel, write G_{i,phi} (per-epoch images)
 //   psgrad_kernel       per (epoch, source): <G_i, g>, <G_i, grad g> on the source window
-//   hgrad_kernel        dL/dh = sum_i G_i + starlet prior gradient (fixed epoch order, FP64)
+//   hgrad_kernel        dL/dh = sum_i G_i + starlet prior gradient (fixed epoch order)
 //   finalize_kernel     loss, dGamma, da, dc, ddelta per field in fixed order
 #include <math.h>
 
@@ -133,18 +133,23 @@ __device__ __forceinline__ float2 source_centre(const float *__restrict__ c, con
     return make_float2(u0 + (float)f * (c[2 * k] + dl[0]), u0 + (float)f * (c[2 * k + 1] + dl[1]));
 }
 
+// Up to this many point sources are added while the tile is staged; more are scattered after it.
+constexpr int kFusedSources = 8;
+
 __device__ __forceinline__ float gauss_at(float dx, float dy) {
     return kGaussNorm * exp2f(-(dx * dx + dy * dy));
 }
 
 template <int R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ items, int n_items,
            int *__restrict__ counter, const float *__restrict__ params, float *__restrict__ ebuf,
            double *__restrict__ chi_part, double *__restrict__ se_part) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_item;
     __shared__ double s_red[2][kThreads / 32];
+    __shared__ float4 s_src[kFusedSources];
+    __shared__ int2 s_win[kFusedSources];
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -166,39 +171,68 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
         const float gam = cpar[2 * M + 2 * E + t.epoch];
         const int my0 = t.y0 - thi, mx0 = t.x0 - thi;  // data-grid origin of the staged tiles
 
+        // point sources of this epoch: fine centre, amplitude and window origin (Eq. 9)
+        if (tid < M && tid < kFusedSources) {
+            const float2 cen = source_centre(cpar, dpar, tid, F, f);
+            s_src[tid] = make_float4(cen.x, cen.y, apar[tid], 0.f);
+            s_win[tid] = make_int2((int)floorf(cen.x) - kWinLo, (int)floorf(cen.y) - kWinLo);
+        }
+        __syncthreads();
+        const bool fused_sources = M <= kFusedSources;
+        const int warp = tid >> 5, lane = tid & 31;
+
         float acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0.f;
 
         for (int iter = 0; iter < nph / G.PG; ++iter) {
-            // stage F_phi = h[f m + phi] (zero outside the grid) for every group's phase
-            const int per = G.xrows * G.xcols;
-            for (int idx = tid; idx < G.PG * per; idx += kThreads) {
-                const int grp = idx / per;
-                const int rr = idx - grp * per;
-                const int i = rr / G.xcols, j = rr - i * G.xcols;
+            // stage F_phi = f_i[f m + phi] = h + point sources (zero outside the grid), one row per warp
+            for (int rr = warp; rr < G.PG * G.xrows; rr += kThreads / 32) {
+                const int grp = rr / G.xrows;
+                const int i = rr - grp * G.xrows;
                 const int ph = iter * G.PG + grp;
                 const int phy = ph / f, phx = ph - phy * f;
-                const int my = my0 + i, mx = mx0 + j;
-                float v = 0.f;
-                if (my >= 0 && my < N && mx >= 0 && mx < N) v = __ldg(hpar + (long long)(f * my + phy) * F + f * mx + phx);
-                smem[grp * xsize + i * G.xpitch + j] = v;
+                const int my = my0 + i;
+                float *dst = smem + grp * xsize + i * G.xpitch;
+                if (my < 0 || my >= N) {
+                    for (int j = lane; j < G.xcols; j += 32) dst[j] = 0.f;
+                    continue;
+                }
+                const int uy = f * my + phy;
+                unsigned rowmask = 0u;
+                if (fused_sources)
+                    for (int k = 0; k < M; ++k)
+                        if ((unsigned)(uy - s_win[k].y) < (unsigned)kWin) rowmask |= 1u << k;
+                const float *src = hpar + (long long)uy * F + phx;
+                for (int j = lane; j < G.xcols; j += 32) {
+                    const int mx = mx0 + j;
+                    float v = 0.f;
+                    if (mx >= 0 && mx < N) {
+                        v = __ldg(src + f * mx);
+                        const int ux = f * mx + phx;
+                        for (unsigned m = rowmask; m; m &= m - 1) {
+                            const int k = __ffs(m) - 1;
+                            if ((unsigned)(ux - s_win[k].x) < (unsigned)kWin)
+                                v += s_src[k].z * gauss_at((float)ux - s_src[k].x, (float)uy - s_src[k].y);
+                        }
+                    }
+                    dst[j] = v;
+                }
             }
-            // flipped folded kernels: Kp[jy][jx] = kappa_phi(thi - jy, thi - jx)
+            // flipped folded kernels: Kp[jy][jx] = kappa_phi(thi - jy, thi - jx), one row per warp
             const int ksz = Tk * G.kpitch;
             const float *kap = fd.kappa + (long long)t.epoch * nph * Tk * Tk;
-            for (int idx = tid; idx < G.PG * ksz; idx += kThreads) {
-                const int grp = idx / ksz;
-                const int rr = idx - grp * ksz;
-                const int jy = rr / G.kpitch, jx = rr - jy * G.kpitch;
+            for (int rr = warp; rr < G.PG * Tk; rr += kThreads / 32) {
+                const int grp = rr / Tk;
+                const int jy = rr - grp * Tk;
                 const int ph = iter * G.PG + grp;
-                float v = 0.f;
-                if (jx < Tk) v = __ldg(kap + ((long long)ph * Tk + (Tk - 1 - jy)) * Tk + (Tk - 1 - jx));
-                Kall[idx] = v;
+                const float *srow = kap + ((long long)ph * Tk + (Tk - 1 - jy)) * Tk + (Tk - 1);
+                float *dst = Kall + grp * ksz + jy * G.kpitch;
+                for (int jx = lane; jx < G.kpitch; jx += 32) dst[jx] = jx < Tk ? __ldg(srow - jx) : 0.f;
             }
             __syncthreads();
-            // point-source channel (Eq. 9): add a_ki g(u - centre) on the window pixels of this phase
-            if (M > 0) {
+            // many point sources: scatter them onto the staged tiles instead
+            if (M > 0 && !fused_sources) {
                 const int nw = kWin / f + 1;
                 const int work = G.PG * M * nw * nw;
                 for (int idx = tid; idx < work; idx += kThreads) {
@@ -294,24 +328,29 @@ adj_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
         float *Kall = smem + align4(ysize);
         const int my0 = t.y0 + tlo, mx0 = t.x0 + tlo;
         const float *ep = ebuf + fd.ebuf_off + (long long)t.epoch * N * N;
-        // stage e on the tile plus halo (zero outside the data grid)
-        for (int idx = tid; idx < G.xrows * G.xcols; idx += kThreads) {
-            const int i = idx / G.xcols, j = idx - i * G.xcols;
-            const int my = my0 + i, mx = mx0 + j;
-            float v = 0.f;
-            if (my >= 0 && my < N && mx >= 0 && mx < N) v = ep[(long long)my * N + mx];
-            smem[i * G.xpitch + j] = v;
+        // stage e on the tile plus halo (zero outside the data grid), one row per warp
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int i = warp; i < G.xrows; i += kThreads / 32) {
+            const int my = my0 + i;
+            float *dst = smem + i * G.xpitch;
+            const bool row_in = my >= 0 && my < N;
+            const float *src = ep + (long long)my * N;
+            for (int j = lane; j < G.xcols; j += 32) {
+                const int mx = mx0 + j;
+                dst[j] = (row_in && mx >= 0 && mx < N) ? src[mx] : 0.f;
+            }
         }
         const int ksz = Tk * G.kpitch;
         const float *kap = fd.kappa + (long long)t.epoch * nph * Tk * Tk;
         float *gout = gbuf + fd.gbuf_off + (long long)t.epoch * nph * N * N;
         for (int iter = 0; iter < nph / G.PG; ++iter) {
-            for (int idx = tid; idx < G.PG * ksz; idx += kThreads) {
-                const int grp = idx / ksz;
-                const int rr = idx - grp * ksz;
-                const int jy = rr / G.kpitch, jx = rr - jy * G.kpitch;
+            for (int rr = warp; rr < G.PG * Tk; rr += kThreads / 32) {
+                const int grp = rr / Tk;
+                const int jy = rr - grp * Tk;
                 const int ph = iter * G.PG + grp;
-                Kall[idx] = (jx < Tk) ? __ldg(kap + ((long long)ph * Tk + jy) * Tk + jx) : 0.f;
+                const float *srow = kap + ((long long)ph * Tk + jy) * Tk;
+                float *dst = Kall + grp * ksz + jy * G.kpitch;
+                for (int jx = lane; jx < G.kpitch; jx += 32) dst[jx] = jx < Tk ? __ldg(srow + jx) : 0.f;
             }
             __syncthreads();
             if (G.g < G.PG) {
@@ -395,13 +434,22 @@ __global__ void hgrad_kernel(const FieldDev *__restrict__ fields, const ChunkIte
     if (q >= F * F) return;
     const long long plane = (long long)f * f * N * N;
     const float *G = gbuf + fd.gbuf_off + q;
-    double s = 0.0;
-    for (int i = 0; i < fd.E; ++i) s += (double)G[(long long)i * plane];
+    // four interleaved FP32 partial sums over the epochs, combined in a fixed order
+    // (the FP64 pipe of this GPU is far narrower than the FP32 one)
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int i = 0;
+    for (; i + 4 <= fd.E; i += 4) {
+        s0 += G[(long long)i * plane];
+        s1 += G[(long long)(i + 1) * plane];
+        s2 += G[(long long)(i + 2) * plane];
+        s3 += G[(long long)(i + 3) * plane];
+    }
+    for (; i < fd.E; ++i) s0 += G[(long long)i * plane];
     const int ph = q / (N * N), m = q - ph * N * N;
     const int my = m / N, mx = m - my * N;
     const int u = (f * my + ph / f) * F + f * mx + ph % f;
     const float *T0 = fd.starlet + (long long)fd.J * F * F;
-    grad[fd.param_off + u] = (float)(s + (double)T0[u]);
+    grad[fd.param_off + u] = ((s0 + s1) + (s2 + s3)) + T0[u];
 }
 
 // Per-field assembly of the loss and the small parameter blocks, in fixed order.
