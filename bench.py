@@ -117,6 +117,60 @@ def fwd_bytes(fields):
     return b
 
 
+def fft_size(N, K, f):
+    """Transform size of the frequency-domain form (the library's rule): the smallest even
+    L >= N + max(tau_hi, -tau_lo) with prime factors 2, 3, 5."""
+    o = K // 2
+    t_lo, t_hi = -o - f + 1, K - 1 - o
+    tau_lo = -((-t_lo) // f)
+    tau_hi = (t_hi + f - 1) // f
+    L = N + max(tau_hi, -tau_lo)
+    while True:
+        m = L
+        for q in (2, 3, 5):
+            while m % q == 0:
+                m //= q
+        if m == 1 and L % 2 == 0:
+            return L
+        L += 1
+
+
+def uses_fft(fd):
+    """Whether the library runs this field in the frequency domain (AUTO: where the
+    per-epoch transform buffers fit in 227 KB of shared memory)."""
+    L = fft_size(fd.N, fd.K, fd.f)
+    H = L // 2 + 1
+    return (2 * L * H + L + fd.M * fd.f * (H + L)) * 8 <= 232448 - 1024
+
+
+def fft_bytes(fields):
+    """Algorithmic DRAM bytes of one evaluation's transform kernels: each epoch reads its
+    f^2 folded-kernel spectra (L x (L/2+1) complex), its data and weights, and writes its f^2
+    adjoint images; each field's h spectra are written and read once."""
+    b = 0
+    for fd in fields:
+        L = fft_size(fd.N, fd.K, fd.f)
+        H = L // 2 + 1
+        nph = fd.f * fd.f
+        b += fd.E * (nph * L * H * 8 + 8 * fd.N * fd.N + 4 * nph * fd.N * fd.N) + 2 * nph * L * H * 8 + 4 * fd.F ** 2
+    return b
+
+
+def fft_flops(fields):
+    """Nominal FLOPs of the transform kernels: 5 n log2 n per complex transform of n points
+    (a real L x L transform counted as L^2/2 complex points), 2 + f^2 per epoch, plus the
+    complex products of the spectra."""
+    import math
+    fl = 0.0
+    for fd in fields:
+        L = fft_size(fd.N, fd.K, fd.f)
+        nph = fd.f * fd.f
+        n = L * L / 2
+        per = (2 + nph) * 5 * n * math.log2(n) + 2 * nph * (L * (L // 2 + 1)) * 8
+        fl += fd.E * per + nph * 5 * n * math.log2(n)
+    return fl
+
+
 def lr_groups(fd):
     amp = float(np.mean(np.abs(fd.params[fd.F ** 2:fd.F ** 2 + fd.E * fd.M]))) if fd.M else 1.0
     return (1e-2 * max(float(np.max(np.abs(fd.params[:fd.F ** 2]))), 1.0) / 100.0, 1e-2 * amp, 1e-3, 1e-3, 1e-2)
@@ -285,7 +339,7 @@ def run_ours(args):
             dist.barrier()
         ms = e0.elapsed_time(e1)
         clk = clocks.stop()
-        n_ev, fwd_ms, adj_ms = batch.profile_read() if batch is not None else (0, 0.0, 0.0)
+        n_ev, fwd_ms, adj_ms, fft_ms = batch.profile_read() if batch is not None else (0, 0.0, 0.0, 0.0)
         if batch is not None:
             batch.profile(False)
         launches = 0
@@ -325,16 +379,36 @@ def run_ours(args):
     roof = None
     kernels = None
     if batch is not None and n_ev > 0:
-        fl = fwd_flops(fields)
-        avg_f, avg_a = fwd_ms / n_ev, adj_ms / n_ev
-        dom_ms, dom = (avg_f, "fwd") if avg_f >= avg_a else (avg_a, "adj")
-        achieved = fl / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": None, "kernel": f"{dom}_kernel<16>",
-                "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_src} max clock)"}
-        kernels = {"fwd_ms": round(avg_f, 4), "adj_ms": round(avg_a, 4), "fwd_tflops": round(fl / avg_f / 1e9, 3),
-                   "adj_tflops": round(fl / avg_a / 1e9, 3), "flops_per_launch": fl,
-                   "evals_profiled": n_ev}
+        direct_fields = [fd for fd in fields if not uses_fft(fd)]
+        fft_fields = [fd for fd in fields if uses_fft(fd)]
+        avg_f, avg_a, avg_t = fwd_ms / n_ev, adj_ms / n_ev, fft_ms / n_ev
+        kernels = {"fwd_ms": round(avg_f, 4), "adj_ms": round(avg_a, 4), "fft_ms": round(avg_t, 4),
+                   "evals_profiled": n_ev, "fields_direct": len(direct_fields), "fields_fft": len(fft_fields)}
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        if direct_fields:
+            fl = fwd_flops(direct_fields)
+            kernels.update({"fwd_tflops": round(fl / avg_f / 1e9, 3) if avg_f > 0 else None,
+                            "adj_tflops": round(fl / avg_a / 1e9, 3) if avg_a > 0 else None,
+                            "direct_flops_per_launch": fl})
+        if fft_fields:
+            tb = fft_bytes(fft_fields)
+            tf = fft_flops(fft_fields)
+            kernels.update({"fft_bytes_per_launch": tb, "fft_flops_per_launch": tf,
+                            "fft_gbs": round(tb / (avg_t / 1e3) / 1e9, 1), "fft_tflops": round(tf / (avg_t / 1e3) / 1e12, 3)})
+        if avg_t >= max(avg_f, avg_a):
+            ach = fft_bytes(fft_fields) / (avg_t / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "traffic": None,
+                    "kernel": "fft_hhat_kernel + fft_epoch_kernel",
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+        else:
+            fl = fwd_flops(direct_fields)
+            dom_ms, dom = (avg_f, "fwd") if avg_f >= avg_a else (avg_a, "adj")
+            achieved = fl / (dom_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                    "frac": round(achieved / fp32_peak, 4), "traffic": None, "kernel": f"{dom}_kernel<16>",
+                    "peak_source": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                   f"({peak_src} max clock)"}
 
     plain = None
     if not args.no_plain and fields and rank == 0:

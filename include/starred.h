@@ -82,11 +82,15 @@ typedef enum {
 
 typedef enum { SR_DECONV = 0, SR_PSF = 1 } sr_kind;
 
-/* How S (and D) are evaluated.  AUTO lets the library choose.  DIRECT is the
- * fused D-folded direct form.  PLAIN is the literal per-epoch form (fine-grid
+/* How S (and D) are evaluated.  DIRECT is the fused D-folded direct form
+ * (shared-memory tiles).  FFT evaluates the same folded form with circular
+ * transforms whose size leaves the N x N output free of wrap-around (exact up
+ * to rounding); it needs the transform buffers of one epoch to fit in shared
+ * memory (SR_ERR_UNSUPPORTED at create otherwise).  AUTO uses FFT where it
+ * fits, else DIRECT.  PLAIN is the literal per-epoch form (fine-grid
  * convolution, then D, residual, D^T, correlation, each a separate launch per
  * epoch), kept as the measured baseline. */
-typedef enum { SR_CONV_AUTO = 0, SR_CONV_DIRECT = 1, SR_CONV_PLAIN = 2 } sr_conv_mode;
+typedef enum { SR_CONV_AUTO = 0, SR_CONV_DIRECT = 1, SR_CONV_PLAIN = 2, SR_CONV_FFT = 3 } sr_conv_mode;
 
 typedef struct {
     int kind;            /* sr_kind */
@@ -234,14 +238,16 @@ int sr_launches_per_eval(const sr_problem *p);
 int sr_batch_launches_per_eval(const sr_batch *b);
 
 /* Kernel timing: while enabled, every evaluation of the batch records CUDA
- * events on the batch's stream before the forward tile kernel, between it and
- * the adjoint tile kernel, and after the adjoint (a ring of the last 512
- * evaluations); sr_batch_step runs without graph capture meanwhile.
- * enable = 1 also clears the record. */
+ * events on the batch's stream around its hot kernels — the forward and the
+ * adjoint tile kernels of the fields in the direct form, and the transform
+ * kernels (h spectra and the per-epoch kernel) of the fields in the FFT form
+ * (a ring of the last 512 evaluations); sr_batch_step runs without graph
+ * capture meanwhile.  enable = 1 also clears the record. */
 sr_status sr_batch_profile(sr_batch *b, int enable);
 /* Evaluations recorded and the summed durations in milliseconds of the
- * forward and adjoint tile kernels.  Synchronises the batch's stream. */
-sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms);
+ * forward tile kernel, the adjoint tile kernel and the transform kernels.
+ * Synchronises the batch's stream. */
+sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms, double *fft_ms);
 
 /* Loss and gradient of one deconvolution field, allocating nothing.
  *

@@ -20,7 +20,7 @@ SR_MAX_GROUPS = 8
 STATUS = {0: "SR_OK", 1: "SR_ERR_ARG", 2: "SR_ERR_SHAPE", 3: "SR_ERR_STATE", 4: "SR_ERR_CUDA", 5: "SR_ERR_OOM",
           6: "SR_ERR_NONFINITE", 7: "SR_ERR_TIMEOUT", 8: "SR_ERR_UNSUPPORTED"}
 SR_DECONV, SR_PSF = 0, 1
-SR_CONV_AUTO, SR_CONV_DIRECT, SR_CONV_PLAIN = 0, 1, 2
+SR_CONV_AUTO, SR_CONV_DIRECT, SR_CONV_PLAIN, SR_CONV_FFT = 0, 1, 2, 3
 SR_ADABELIEF, SR_ADAM = 0, 1
 
 
@@ -71,7 +71,7 @@ PROTOTYPES = {
     "sr_launches_per_eval": ([c_void_p], c_int),
     "sr_batch_launches_per_eval": ([c_void_p], c_int),
     "sr_batch_profile": ([c_void_p, c_int], c_int),
-    "sr_batch_profile_read": ([c_void_p, ctypes.POINTER(c_int), P_double, P_double], c_int),
+    "sr_batch_profile_read": ([c_void_p, ctypes.POINTER(c_int), P_double, P_double, P_double], c_int),
     "sr_loss_and_grad_noalloc": ([ctypes.POINTER(ProblemDesc), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p], c_int),
 }

@@ -69,7 +69,8 @@ class Problem:
         d = nat.ProblemDesc()
         d.kind, d.n_epochs, d.data_n, d.supersampling = self.kind, E, N, f
         d.psf_k, d.n_sources, d.n_scales, d.lam = K, M, J, lam
-        d.conv_mode = {"auto": nat.SR_CONV_AUTO, "direct": nat.SR_CONV_DIRECT, "plain": nat.SR_CONV_PLAIN}[conv_mode]
+        d.conv_mode = {"auto": nat.SR_CONV_AUTO, "direct": nat.SR_CONV_DIRECT, "plain": nat.SR_CONV_PLAIN,
+                       "fft": nat.SR_CONV_FFT}[conv_mode]
         self._stream = stream
         h = ctypes.c_void_p()
         nat.check(self.lib.sr_create_problem(ctypes.byref(d), _stream_ptr(stream), ctypes.byref(h)), "sr_create_problem")
@@ -264,11 +265,12 @@ class Batch:
         nat.check(self.lib.sr_batch_profile(self.handle, 1 if enable else 0), "sr_batch_profile")
 
     def profile_read(self):
-        """(evaluations recorded, summed forward-kernel ms, summed adjoint-kernel ms)."""
-        n, fm, am = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
-        nat.check(self.lib.sr_batch_profile_read(self.handle, ctypes.byref(n), ctypes.byref(fm), ctypes.byref(am)),
-                  "sr_batch_profile_read")
-        return n.value, fm.value, am.value
+        """(evaluations recorded, summed ms of the forward tile kernel, of the adjoint tile
+        kernel, and of the transform kernels)."""
+        n, fm, am, tm = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        nat.check(self.lib.sr_batch_profile_read(self.handle, ctypes.byref(n), ctypes.byref(fm), ctypes.byref(am),
+                                                 ctypes.byref(tm)), "sr_batch_profile_read")
+        return n.value, fm.value, am.value, tm.value
 
     def close(self):
         if getattr(self, "handle", None):

@@ -75,7 +75,32 @@ static sr_status device_limits() {
     const int dyn = g_smem_optin - 1024;
     sr_status s = configure_tile_kernels(dyn, dyn);
     if (s != SR_OK) return s;
+    s = configure_fft_kernels(dyn);
+    if (s != SR_OK) return s;
     return SR_OK;
+}
+
+// Transform size for the frequency-domain form: the smallest even L >= N + max(tau_hi, -tau_lo)
+// whose prime factors are 2, 3 and 5, and its radix sequence (4s first, then 2, 3, 5).
+static bool fft_size(int N, int Tk, int tau_lo, int *L_out, int *nst, int *rad) {
+    const int tau_hi = tau_lo + Tk - 1;
+    int L = N + std::max(tau_hi, -tau_lo);
+    for (;; ++L) {
+        if (L % 2) continue;
+        int m = L;
+        for (int q : {2, 3, 5})
+            while (m % q == 0) m /= q;
+        if (m == 1) break;
+    }
+    int m = L, n = 0;
+    while (m % 4 == 0 && n < kFftMaxStages) { rad[n++] = 4; m /= 4; }
+    while (m % 2 == 0 && n < kFftMaxStages) { rad[n++] = 2; m /= 2; }
+    while (m % 3 == 0 && n < kFftMaxStages) { rad[n++] = 3; m /= 3; }
+    while (m % 5 == 0 && n < kFftMaxStages) { rad[n++] = 5; m /= 5; }
+    if (m != 1) return false;
+    *L_out = L;
+    *nst = n;
+    return true;
 }
 
 // Polyphase extent of the folded kernels: tau in [tau_lo, tau_lo + Tk).
@@ -117,6 +142,12 @@ struct Plan {
     int Jmax = 0;
     float *ebuf = nullptr, *gbuf = nullptr, *ps_da = nullptr, *ps_du = nullptr;
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
+    // frequency-domain form
+    int n_fft_items = 0, n_fft_fields = 0, max_nph = 1, smem_fft = 0, grid_fft = 0;
+    int4 *d_fft_items = nullptr;
+    int *d_fft_fields = nullptr;
+    float2 *hhat = nullptr, *ehat = nullptr;
+    long long ehat_stride = 0;
     // PSF
     PsfBuffers psf{};
     // plain form
@@ -151,6 +182,11 @@ struct sr_problem {
     int F = 0, Tk = 0, tau_lo = 0;
     float *d = nullptr, *w = nullptr, *s = nullptr, *kappa = nullptr, *Wd = nullptr, *starlet = nullptr;
     float *psf_s = nullptr, *psf_tmp = nullptr, *psf_gs = nullptr;
+    // frequency-domain form: transform geometry, twiddles, kernel spectra
+    bool fft_ok = false;
+    int fft_L = 0, fft_nst = 0;
+    int fft_rad[kFftMaxStages] = {0};
+    float2 *fft_tw = nullptr, *khat = nullptr;
     int *d_flag = nullptr;
     float W_host[kMaxScales] = {0};
     bool has_data = false, has_noise = false, has_psfs = false, has_weights = false;
@@ -181,7 +217,9 @@ static sr_status validate_desc(const sr_problem_desc *d) {
         if (d->psf_k < 1 || d->psf_k > 511) return fail(SR_ERR_SHAPE, "psf_k %d out of range", d->psf_k);
         if (d->n_sources < 0 || d->n_sources > 64) return fail(SR_ERR_SHAPE, "n_sources %d out of range", d->n_sources);
     }
-    if (d->conv_mode < SR_CONV_AUTO || d->conv_mode > SR_CONV_PLAIN) return fail(SR_ERR_ARG, "unknown conv_mode");
+    if (d->conv_mode < SR_CONV_AUTO || d->conv_mode > SR_CONV_FFT) return fail(SR_ERR_ARG, "unknown conv_mode");
+    if (d->kind == SR_PSF && d->conv_mode == SR_CONV_FFT)
+        return fail(SR_ERR_UNSUPPORTED, "the transform form exists for deconvolution problems only");
     if (d->kind == SR_PSF && d->conv_mode == SR_CONV_PLAIN)
         return fail(SR_ERR_UNSUPPORTED, "the plain form exists for deconvolution problems only");
     return SR_OK;
@@ -252,6 +290,17 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
     fd.psf_tmp = p->psf_tmp;
     fd.psf_gs = p->psf_gs;
     fd.n_chunks = (fd.F * fd.F + 255) / 256;
+    fd.mode = 0;
+    fd.fft_L = p->fft_L;
+    fd.fft_nst = p->fft_nst;
+    for (int s = 0; s < kFftMaxStages; ++s) fd.fft_rad[s] = p->fft_rad[s];
+    fd.fft_tw = p->fft_tw;
+    fd.fft_khat = p->khat;
+}
+
+// Whether a field of a plan runs in the frequency domain.
+static bool use_fft(const sr_problem *p) {
+    return p->fft_ok && (p->desc.conv_mode == SR_CONV_FFT || p->desc.conv_mode == SR_CONV_AUTO);
 }
 
 static int choose_pg(int nph, int threads_per_group) {
@@ -277,7 +326,10 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     long long ebuf = 0, gbuf = 0, tslot = 0, psslot = 0, l1slot = 0;
     size_t poff = 0;
     int Jmax = 0;
-    int smem_fwd = 0, smem_adj = 0;
+    int smem_fwd = 0, smem_adj = 0, smem_fft = 0;
+    std::vector<int4> fft_items;
+    std::vector<int> fft_fields;
+    long long hhat_len = 0, max_LH = 0;
     for (int i = 0; i < n; ++i) {
         sr_problem *p = probs[i];
         if (p->desc.kind != pl->kind) return fail(SR_ERR_ARG, "a batch mixes problem kinds");
@@ -305,7 +357,25 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         l1slot += (long long)(fd.J - 1) * fd.n_chunks;
         for (int c = 0; c < fd.n_chunks; ++c) chunks.push_back(ChunkItem{i, c * 256, c});
         Jmax = std::max(Jmax, fd.J);
-        if (pl->kind == SR_DECONV && !plain) {
+        if (pl->kind == SR_DECONV && !plain && use_fft(p)) {
+            gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
+            fd.mode = 1;
+            fd.n_tiles = 1;
+            fd.tile_slot = tslot;
+            for (int e = 0; e < fd.E; ++e) fft_items.push_back(make_int4(i, e, (int)(tslot + e), 0));
+            tslot += fd.E;
+            fd.ps_slot = psslot;
+            for (int e = 0; e < fd.E; ++e)
+                for (int k = 0; k < fd.M; ++k) ps.push_back(make_int4(i, e, k, 0));
+            psslot += (long long)fd.E * fd.M;
+            const int L = fd.fft_L, H = L / 2 + 1;
+            fd.fft_hhat_off = hhat_len;
+            hhat_len += (long long)fd.f * fd.f * L * H;
+            fft_fields.push_back(i);
+            pl->max_nph = std::max(pl->max_nph, fd.f * fd.f);
+            smem_fft = std::max(smem_fft, fft_smem_bytes(L, fd.M, fd.f));
+            max_LH = std::max<long long>(max_LH, (long long)L * H);
+        } else if (pl->kind == SR_DECONV && !plain) {
             gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
             const int nph = fd.f * fd.f;
             std::vector<TileItem> tiles;
@@ -357,6 +427,14 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         const double cb = (double)b.h * b.w * fb.Tk * fb.Tk * fb.f * fb.f;
         return ca > cb;
     });
+    std::stable_sort(fft_items.begin(), fft_items.end(), [&](const int4 &a, const int4 &b) {
+        const FieldDev &fa = pl->h_fields[a.x], &fb = pl->h_fields[b.x];
+        const double ca = (double)fa.fft_L * fa.fft_L * (2 + fa.f * fa.f);
+        const double cb = (double)fb.fft_L * fb.fft_L * (2 + fb.f * fb.f);
+        return ca > cb;
+    });
+    pl->n_fft_items = (int)fft_items.size();
+    pl->n_fft_fields = (int)fft_fields.size();
     pl->n_items = (int)items.size();
     pl->n_ps = (int)ps.size();
     pl->n_chunks = (int)chunks.size();
@@ -410,7 +488,22 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     if (!ps.empty()) SR_CUDA(cudaMemcpy(pl->d_ps, ps.data(), sizeof(int4) * ps.size(), cudaMemcpyHostToDevice));
     if (!chunks.empty()) SR_CUDA(cudaMemcpy(pl->d_chunks, chunks.data(), sizeof(ChunkItem) * chunks.size(), cudaMemcpyHostToDevice));
     SR_CUDA(cudaMemcpy(pl->d_group, groups.data(), groups.size(), cudaMemcpyHostToDevice));
-    if (pl->kind == SR_DECONV && !plain) {
+    if (pl->n_fft_items > 0) {
+        const int limit = g_smem_optin - 1024;
+        if (smem_fft > limit) return fail(SR_ERR_UNSUPPORTED, "transform form needs %d bytes of shared memory", smem_fft);
+        pl->smem_fft = smem_fft;
+        int bfft = 0;
+        if ((st = occupancy_fft_kernel(smem_fft, &bfft)) != SR_OK) return st;
+        pl->grid_fft = std::max(1, std::min(pl->n_fft_items, std::max(bfft, 1) * g_num_sms));
+        pl->ehat_stride = max_LH;
+        if ((st = A.alloc(&pl->d_fft_items, fft_items.size())) != SR_OK) return st;
+        if ((st = A.alloc(&pl->d_fft_fields, fft_fields.size())) != SR_OK) return st;
+        if ((st = A.alloc(&pl->hhat, (size_t)hhat_len)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->ehat, (size_t)(max_LH * pl->grid_fft))) != SR_OK) return st;
+        SR_CUDA(cudaMemcpy(pl->d_fft_items, fft_items.data(), sizeof(int4) * fft_items.size(), cudaMemcpyHostToDevice));
+        SR_CUDA(cudaMemcpy(pl->d_fft_fields, fft_fields.data(), sizeof(int) * fft_fields.size(), cudaMemcpyHostToDevice));
+    }
+    if (pl->kind == SR_DECONV && !plain && pl->n_items > 0) {
         const int limit = g_smem_optin - 1024;
         if (smem_fwd > limit || smem_adj > limit)
             return fail(SR_ERR_UNSUPPORTED, "PSF size needs %d bytes of shared memory per block (limit %d)",
@@ -445,18 +538,31 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
     cudaMemsetAsync(pl->d_counters, 0, 4 * sizeof(int), st);
     cudaEvent_t *ev = nullptr;
     if (pl->profiling && !pl->prof_ev.empty()) {
-        const int ring = (int)pl->prof_ev.size() / 3;
-        ev = &pl->prof_ev[3 * (pl->prof_count % ring)];
+        const int ring = (int)pl->prof_ev.size() / 4;
+        ev = &pl->prof_ev[4 * (pl->prof_count % ring)];
         ++pl->prof_count;
         cudaEventRecord(ev[0], st);
     }
-    launch_fwd(pl->d_fields, pl->d_items, pl->n_items, pl->d_counters, params, pl->ebuf, pl->chi_part, pl->se_part,
-               pl->grid_fwd, pl->smem_fwd, st);
-    if (ev) cudaEventRecord(ev[1], st);
-    launch_adj(pl->d_fields, pl->d_items, pl->n_items, pl->d_counters + 1, pl->ebuf, pl->gbuf, pl->grid_adj,
-               pl->smem_adj, st);
+    if (pl->n_items > 0) {
+        launch_fwd(pl->d_fields, pl->d_items, pl->n_items, pl->d_counters, params, pl->ebuf, pl->chi_part,
+                   pl->se_part, pl->grid_fwd, pl->smem_fwd, st);
+        if (ev) cudaEventRecord(ev[1], st);
+        launch_adj(pl->d_fields, pl->d_items, pl->n_items, pl->d_counters + 1, pl->ebuf, pl->gbuf, pl->grid_adj,
+                   pl->smem_adj, st);
+        n += 2;
+    } else if (ev) {
+        cudaEventRecord(ev[1], st);
+    }
     if (ev) cudaEventRecord(ev[2], st);
-    n += 2;
+    if (pl->n_fft_items > 0) {
+        launch_fft_hhat(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_nph, pl->smem_fft, params, pl->hhat,
+                        st);
+        launch_fft_epochs(pl->d_fields, pl->d_fft_items, pl->n_fft_items, pl->d_counters + 2, params, pl->hhat,
+                          pl->ehat, pl->ehat_stride, pl->gbuf, pl->chi_part, pl->se_part, pl->grid_fft, pl->smem_fft,
+                          st);
+        n += 2;
+    }
+    if (ev) cudaEventRecord(ev[3], st);
     if (pl->n_ps > 0) {
         launch_psgrad(pl->d_fields, pl->d_ps, pl->n_ps, params, pl->gbuf, pl->ps_da, pl->ps_du, st);
         ++n;
@@ -634,6 +740,30 @@ sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_p
         if ((st = A.alloc(&p->s, E * K * K)) != SR_OK) return bail(st);
         if ((st = A.alloc(&p->kappa, E * d.supersampling * d.supersampling * (size_t)p->Tk * p->Tk)) != SR_OK)
             return bail(st);
+        if (d.conv_mode == SR_CONV_FFT || d.conv_mode == SR_CONV_AUTO) {
+            if ((st = device_limits()) != SR_OK) return bail(st);
+            int L = 0, nst = 0;
+            const bool ok = fft_size(d.data_n, p->Tk, p->tau_lo, &L, &nst, p->fft_rad) &&
+                            fft_smem_bytes(L, d.n_sources, d.supersampling) <= g_smem_optin - 1024;
+            if (!ok && d.conv_mode == SR_CONV_FFT)
+                return bail(fail(SR_ERR_UNSUPPORTED, "the transform form does not fit this size in shared memory"));
+            if (ok) {
+                p->fft_ok = true;
+                p->fft_L = L;
+                p->fft_nst = nst;
+                const size_t H = L / 2 + 1;
+                if ((st = A.alloc(&p->khat, E * d.supersampling * d.supersampling * (size_t)L * H)) != SR_OK)
+                    return bail(st);
+                if ((st = A.alloc(&p->fft_tw, (size_t)L)) != SR_OK) return bail(st);
+                std::vector<float2> tw(L);
+                for (int n = 0; n < L; ++n) {
+                    const double a = -2.0 * M_PI * (double)n / (double)L;
+                    tw[n] = make_float2((float)cos(a), (float)sin(a));
+                }
+                if (cudaMemcpy(p->fft_tw, tw.data(), sizeof(float2) * L, cudaMemcpyHostToDevice) != cudaSuccess)
+                    return bail(fail(SR_ERR_CUDA, "twiddle upload failed"));
+            }
+        }
     } else {
         if ((st = A.alloc(&p->psf_s, F * F)) != SR_OK) return bail(st);
         if ((st = A.alloc(&p->psf_tmp, 3 * E * F * F)) != SR_OK) return bail(st);
@@ -690,6 +820,11 @@ sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device) {
     if (st != SR_OK) return st;
     launch_check_finite(p->s, (long long)n, p->d_flag, p->stream);
     launch_kappa_prep(p->s, p->kappa, d.n_epochs, d.psf_k, d.supersampling, p->Tk, p->tau_lo, p->stream);
+    if (p->khat) {
+        FieldDev fd;
+        fill_field_common(fd, p);
+        launch_fft_kappa(fd, p->kappa, p->khat, p->stream);
+    }
     SR_CUDA(cudaGetLastError());
     p->pending_check = true;
     p->has_psfs = true;
@@ -945,7 +1080,7 @@ sr_status sr_batch_profile(sr_batch *b, int enable) {
     if (!b) return fail(SR_ERR_ARG, "NULL batch");
     Plan *pl = b->plan;
     if (enable && pl->prof_ev.empty()) {
-        pl->prof_ev.resize(3 * 512);
+        pl->prof_ev.resize(4 * 512);
         for (cudaEvent_t &e : pl->prof_ev) SR_CUDA(cudaEventCreate(&e));
     }
     pl->profiling = enable != 0;
@@ -953,21 +1088,23 @@ sr_status sr_batch_profile(sr_batch *b, int enable) {
     return SR_OK;
 }
 
-sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms) {
-    if (!b || !n_evals || !fwd_ms || !adj_ms) return fail(SR_ERR_ARG, "NULL argument");
+sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms, double *fft_ms) {
+    if (!b || !n_evals || !fwd_ms || !adj_ms || !fft_ms) return fail(SR_ERR_ARG, "NULL argument");
     Plan *pl = b->plan;
     *n_evals = 0;
-    *fwd_ms = *adj_ms = 0.0;
+    *fwd_ms = *adj_ms = *fft_ms = 0.0;
     if (pl->prof_ev.empty()) return SR_OK;
     SR_CUDA(cudaStreamSynchronize(b->stream));
-    const int ring = (int)pl->prof_ev.size() / 3;
+    const int ring = (int)pl->prof_ev.size() / 4;
     const int n = std::min(pl->prof_count, ring);
     for (int i = 0; i < n; ++i) {
-        float a = 0.f, c = 0.f;
-        SR_CUDA(cudaEventElapsedTime(&a, pl->prof_ev[3 * i], pl->prof_ev[3 * i + 1]));
-        SR_CUDA(cudaEventElapsedTime(&c, pl->prof_ev[3 * i + 1], pl->prof_ev[3 * i + 2]));
+        float a = 0.f, c = 0.f, d = 0.f;
+        SR_CUDA(cudaEventElapsedTime(&a, pl->prof_ev[4 * i], pl->prof_ev[4 * i + 1]));
+        SR_CUDA(cudaEventElapsedTime(&c, pl->prof_ev[4 * i + 1], pl->prof_ev[4 * i + 2]));
+        SR_CUDA(cudaEventElapsedTime(&d, pl->prof_ev[4 * i + 2], pl->prof_ev[4 * i + 3]));
         *fwd_ms += a;
         *adj_ms += c;
+        *fft_ms += d;
     }
     *n_evals = n;
     return SR_OK;

@@ -22,6 +22,7 @@ constexpr int kWinLo = 7;
 constexpr int kBlurHalf = 8;
 
 constexpr int kMaxScales = 8;
+constexpr int kFftMaxStages = 8;
 constexpr int kThreads = 256;
 
 struct FieldDev {
@@ -45,6 +46,13 @@ struct FieldDev {
     float *psf_s;          // PSF kind: [F][F] narrow PSF s = m + b
     float *psf_tmp;        // PSF kind: [S][3][F][F] row-pass planes (value, d/dx) and adjoint plane
     float *psf_gs;         // PSF kind: [S][F][F] per-star gradient wrt s
+    // frequency-domain form (fft.cu); mode 0 = direct tiles, 1 = transforms
+    int mode;
+    int fft_L, fft_nst;
+    int fft_rad[kFftMaxStages];
+    const float2 *fft_tw;     // [L] exp(-2 pi i n / L)
+    const float2 *fft_khat;   // [E][f*f][L][L/2+1] transforms of the folded kernels
+    long long fft_hhat_off;   // offset of the field's [f*f][L][L/2+1] h spectra in the plan buffer
 };
 
 // One output tile of one epoch: rows [y0, y0+h), cols [x0, x0+w) of the data

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "corr.cuh"
+#include "reduce.cuh"
 
 namespace sr {
 
@@ -69,33 +70,6 @@ void launch_kappa_prep(const float *s, float *kappa, int E, int K, int f, int Tk
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 32) grid = 152 * 32;
     kappa_prep_kernel<<<grid, 256, 0, st>>>(s, kappa, E, K, f, Tk, tau_lo);
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Deterministic block sum of two doubles (fixed shuffle tree, warps summed in order).
-__device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[kThreads / 32]) {
-    a = warp_sum(a);
-    b = warp_sum(b);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][wid] = a;
-        red[1][wid] = b;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            sa += red[0][i];
-            sb += red[1][i];
-        }
-        a = sa;
-        b = sb;
-    }
 }
 
 struct TileGeom {

@@ -1,0 +1,430 @@
+// Frequency-domain form of the deconvolution loss and gradient (sm_103a).
+//
+// The D-folded polyphase model (deconv.cu) is a sum over phases phi of ordinary 2-D
+// convolutions on the data grid, M_i = sum_phi kappa_{i,phi} * F_phi, and the adjoint is a
+// correlation per phase, G_{i,phi} = kappa_{i,phi} (corr) e_i.  With circular transforms of size
+// L x L, L >= N + max(tau_hi, -tau_lo), the wrap-around never reaches the N x N output, so
+//     M_i = IDFT( sum_phi Khat_{i,phi} . (Hhat_phi + Phat_{i,phi}) ) on [0,N)^2,
+//     G_{i,phi} = IDFT( conj(Khat_{i,phi}) . ehat_i ) on [0,N)^2,
+// exactly (up to rounding).  Khat (the transforms of the folded kernels placed at tau mod L) are
+// computed once per set_psfs; Hhat (the phase images of h) once per evaluation and field; the
+// point sources' transforms are outer products of 1-D DFTs (the truncated, sampled Gaussian is
+// separable).  Per epoch that is 2 + f^2 real 2-D transforms instead of (K+f-1)^2 taps per data
+// pixel and direction.
+//
+// Transforms: Stockham auto-sort mixed-radix FFT (radices 4, 2, 3, 5), ping-ponging between two
+// shared-memory buffers, twiddles from a table exp(-2 pi i n / L).  A real L x L image is
+// transformed as L/2 complex rows (two real rows per complex row), split into the half spectrum
+// (L rows x L/2+1 columns), then L/2+1 complex column transforms; the inverse runs the same steps
+// backwards.  Rows that are known to be zero are skipped.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "reduce.cuh"
+
+namespace sr {
+
+struct FftGeom {
+    int L, H, Lp;      // transform size, half-spectrum width L/2+1, pitch of the row-pair layout (L+1)
+    int nst;
+    int rad[kFftMaxStages];
+    const float2 *tw;  // exp(-2 pi i n / L), n < L (shared memory)
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// y_q = sum_r v_r exp(-+ 2 pi i q r / R) for R in {2, 3, 4, 5}; s = -1 forward, +1 inverse.
+__device__ __forceinline__ void small_dft(float2 *v, int R, float s) {
+    if (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        const float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        const float2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        // multiplying d by s*i: (x, y) -> (-s y, s x)
+        const float2 di = make_float2(-s * d.y, s * d.x);
+        v[0] = cadd(a, c);
+        v[2] = csub(a, c);
+        v[1] = cadd(b, di);
+        v[3] = csub(b, di);
+    } else if (R == 3) {
+        const float c1 = -0.5f, s1 = s * 0.866025403784438647f;  // cos, +-sin of 2 pi / 3
+        const float2 a = v[0], b = v[1], c = v[2];
+        const float2 t = cadd(b, c), u = csub(b, c);
+        v[0] = cadd(a, t);
+        const float2 m = make_float2(a.x + c1 * t.x, a.y + c1 * t.y);
+        const float2 n = make_float2(-s1 * u.y, s1 * u.x);
+        v[1] = cadd(m, n);
+        v[2] = csub(m, n);
+    } else {  // R == 5
+        const float c1 = 0.309016994374947424f, c2 = -0.809016994374947424f;  // cos 2pi/5, cos 4pi/5
+        const float s1 = s * 0.951056516295153572f, s2 = s * 0.587785252292473129f;  // sin 2pi/5, sin 4pi/5
+        const float2 a = v[0];
+        const float2 t1 = cadd(v[1], v[4]), u1 = csub(v[1], v[4]);
+        const float2 t2 = cadd(v[2], v[3]), u2 = csub(v[2], v[3]);
+        v[0] = make_float2(a.x + t1.x + t2.x, a.y + t1.y + t2.y);
+        const float2 m1 = make_float2(a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y);
+        const float2 m2 = make_float2(a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y);
+        // i*(s1 u1 + s2 u2) and i*(s2 u1 - s1 u2)
+        const float2 n1 = make_float2(-(s1 * u1.y + s2 * u2.y), s1 * u1.x + s2 * u2.x);
+        const float2 n2 = make_float2(-(s2 * u1.y - s1 * u2.y), s2 * u1.x - s1 * u2.x);
+        v[1] = cadd(m1, n1);
+        v[4] = csub(m1, n1);
+        v[2] = cadd(m2, n2);
+        v[3] = csub(m2, n2);
+    }
+}
+
+// ntr independent length-L transforms; element n of transform t at base + t*tstride + n*estride.
+// Returns the buffer that holds the result (src or dst).  Warps take butterflies, lanes take
+// transforms, so the twiddles of a butterfly are loaded once per warp.
+__device__ float2 *stockham(float2 *src, float2 *dst, int ntr, int tstride, int estride, const FftGeom &g, bool inv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float s = inv ? 1.f : -1.f;
+    int Ns = 1;
+    for (int st = 0; st < g.nst; ++st) {
+        const int R = g.rad[st];
+        const int nb = g.L / R;
+        const int step = g.L / (Ns * R);
+        for (int j = warp; j < nb; j += nw) {
+            const int k = j % Ns;
+            const int obase = (j / Ns) * Ns * R + k;
+            float2 w[5];
+#pragma unroll
+            for (int r = 1; r < 5; ++r) {
+                if (r < R) {
+                    const float2 t = g.tw[r * k * step];  // r k step < L
+                    w[r] = inv ? conjf2(t) : t;
+                }
+            }
+            for (int t = lane; t < ntr; t += 32) {
+                const float2 *sp = src + t * tstride;
+                float2 *dp = dst + t * tstride;
+                float2 v[5];
+                v[0] = sp[j * estride];
+#pragma unroll
+                for (int r = 1; r < 5; ++r)
+                    if (r < R) v[r] = cmul(sp[(j + r * nb) * estride], w[r]);
+                small_dft(v, R, s);
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    if (q < R) dp[(obase + q * Ns) * estride] = v[q];
+            }
+        }
+        __syncthreads();
+        float2 *x = src;
+        src = dst;
+        dst = x;
+        Ns *= R;
+    }
+    return src;
+}
+
+// Forward real 2-D transform.  `in` holds np row pairs (row 2p in .x, row 2p+1 in .y), pitch
+// Lp; rows >= 2 np are zero.  Returns the buffer with the half spectrum (pitch H).
+__device__ float2 *fwd2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
+    float2 *r = stockham(in, tmp, np, g.Lp, 1, g, false);
+    float2 *o = (r == in) ? tmp : in;
+    const int L = g.L, H = g.H;
+    for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) {
+        const int y = idx / H, kx = idx - y * H;
+        float2 v = make_float2(0.f, 0.f);
+        if (y < 2 * np) {
+            const float2 *row = r + (y >> 1) * g.Lp;
+            const float2 a = row[kx];
+            const float2 b = conjf2(row[kx == 0 ? 0 : L - kx]);
+            v = (y & 1) ? make_float2(0.5f * (a.y - b.y), -0.5f * (a.x - b.x))   // (a - b) / (2i)
+                        : make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));   // (a + b) / 2
+        }
+        o[idx] = v;
+    }
+    __syncthreads();
+    return stockham(o, r, H, 1, H, g, false);
+}
+
+// Inverse real 2-D transform of the half spectrum in `in` (pitch H).  Returns the buffer with
+// np row pairs (pitch Lp) of the unscaled real image (multiply by 1/L^2).
+__device__ float2 *inv2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
+    float2 *c = stockham(in, tmp, g.H, 1, g.H, g, true);
+    float2 *o = (c == in) ? tmp : in;
+    const int L = g.L, H = g.H;
+    for (int idx = threadIdx.x; idx < np * L; idx += blockDim.x) {
+        const int p = idx / L, kx = idx - p * L;
+        const float2 *r1 = c + (2 * p) * H, *r2 = c + (2 * p + 1) * H;
+        float2 z;
+        if (kx < H) {
+            const float2 a = r1[kx], b = r2[kx];
+            z = make_float2(a.x - b.y, a.y + b.x);           // a + i b
+        } else {
+            const float2 a = r1[L - kx], b = r2[L - kx];
+            z = make_float2(a.x + b.y, -a.y + b.x);          // conj(a) + i conj(b)
+        }
+        o[p * g.Lp + kx] = z;
+    }
+    __syncthreads();
+    return stockham(o, c, np, g.Lp, 1, g, true);
+}
+
+__device__ __forceinline__ void load_geom(FftGeom &g, const FieldDev &fd, float2 *tw_smem) {
+    g.L = fd.fft_L;
+    g.H = fd.fft_L / 2 + 1;
+    g.Lp = fd.fft_L + 1;
+    g.nst = fd.fft_nst;
+    for (int s = 0; s < kFftMaxStages; ++s) g.rad[s] = fd.fft_rad[s];
+    for (int n = threadIdx.x; n < g.L; n += blockDim.x) tw_smem[n] = fd.fft_tw[n];
+    g.tw = tw_smem;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Khat_{i,phi}: transforms of the folded kernels placed at tau mod L.  One block per (epoch, phi).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+fft_kappa_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restrict__ khat) {
+    extern __shared__ __align__(16) float2 fsm[];
+    const int L = fd.fft_L, H = L / 2 + 1;
+    const int nph = fd.f * fd.f;
+    const int item = blockIdx.x;
+    const int i = item / nph, ph = item - i * nph;
+    float2 *A = fsm, *B = fsm + L * H, *tw = fsm + 2 * L * H;
+    FftGeom g;
+    load_geom(g, fd, tw);
+    const int Tk = fd.Tk, tlo = fd.tau_lo, thi = tlo + Tk - 1;
+    const float *kap = kappa + ((long long)i * nph + ph) * Tk * Tk;
+    for (int idx = threadIdx.x; idx < (L / 2) * L; idx += blockDim.x) {
+        const int p = idx / L, x = idx - p * L;
+        float v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int y = 2 * p + q;
+            const int ty = y <= thi ? y : y - L;
+            const int tx = x <= thi ? x : x - L;
+            v[q] = (ty >= tlo && ty <= thi && tx >= tlo && tx <= thi) ? kap[(ty - tlo) * Tk + (tx - tlo)] : 0.f;
+        }
+        A[p * g.Lp + x] = make_float2(v[0], v[1]);
+    }
+    __syncthreads();
+    float2 *S = fwd2d(A, B, g, L / 2);
+    float2 *out = khat + ((long long)i * nph + ph) * L * H;
+    for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) out[idx] = S[idx];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Hhat_phi: transforms of the phase images of h, F_phi[m] = h[f m + phi].  One block per
+// (fft field, phi); blockIdx.x indexes fft_fields[].
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+fft_hhat_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
+                const float *__restrict__ params, float2 *__restrict__ hhat_all) {
+    extern __shared__ __align__(16) float2 fsm[];
+    const FieldDev &fd = fields[fft_fields[blockIdx.x]];
+    const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
+    const int ph = blockIdx.y;
+    if (ph >= nph) return;
+    const int L = fd.fft_L, H = L / 2 + 1;
+    float2 *A = fsm, *B = fsm + L * H, *tw = fsm + 2 * L * H;
+    FftGeom g;
+    load_geom(g, fd, tw);
+    const int phy = ph / f, phx = ph - phy * f;
+    const float *h = params + fd.param_off;
+    const int np = (N + 1) / 2;
+    for (int idx = threadIdx.x; idx < np * L; idx += blockDim.x) {
+        const int p = idx / L, x = idx - p * L;
+        float v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int y = 2 * p + q;
+            v[q] = (y < N && x < N) ? h[(long long)(f * y + phy) * F + f * x + phx] : 0.f;
+        }
+        A[p * g.Lp + x] = make_float2(v[0], v[1]);
+    }
+    __syncthreads();
+    float2 *S = fwd2d(A, B, g, np);
+    float2 *out = hhat_all + fd.fft_hhat_off + (long long)ph * L * H;
+    for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) out[idx] = S[idx];
+}
+
+// ---------------------------------------------------------------------------------------------
+// One epoch per item: forward model, residual, chi^2, and the per-phase adjoint images.
+// items[] = (field, epoch, slot) for the fft fields; ehat_scratch: one L*H spectrum per block.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+fft_epoch_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ items, int n_items,
+                 int *__restrict__ counter, const float *__restrict__ params, const float2 *__restrict__ hhat_all,
+                 float2 *__restrict__ ehat_scratch, long long ehat_stride, float *__restrict__ gbuf,
+                 double *__restrict__ chi_part, double *__restrict__ se_part) {
+    extern __shared__ __align__(16) float2 fsm[];
+    __shared__ int s_item;
+    __shared__ double s_red[2][kThreads / 32];
+    const int tid = threadIdx.x;
+    float2 *ehat_g = ehat_scratch + (long long)blockIdx.x * ehat_stride;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int4 item = items[it];
+        const FieldDev &fd = fields[item.x];
+        const int i = item.y;
+        const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E, nph = f * f;
+        const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1;
+        float2 *A = fsm, *B = fsm + L * H, *tw = fsm + 2 * L * H;
+        float2 *gsp = tw + L;  // point-source 1-D spectra: [M][f][H] (x) then [M][f][L] (y)
+        FftGeom g;
+        load_geom(g, fd, tw);
+        const float *hpar = params + fd.param_off;
+        const float *apar = hpar + (long long)F * F + (long long)i * M;
+        const float *cpar = hpar + (long long)F * F + (long long)E * M;
+        const float *dpar = cpar + 2 * M + 2 * i;
+        const float gam = cpar[2 * M + 2 * E + i];
+        __syncthreads();
+        // 1-D transforms of the point sources' window profiles, per axis and phase:
+        // gx[k][phx][kx] = sum_m g1(f m + phx - cx) W^(kx m) over the window columns (likewise y)
+        const float u0 = 0.5f * (float)(F - 1);
+        const int nx = M * f * H, ny = M * f * L;
+        for (int idx = tid; idx < nx + ny; idx += blockDim.x) {
+            const bool isx = idx < nx;
+            const int r = isx ? idx : idx - nx;
+            const int len = isx ? H : L;
+            const int kf = r / len, kk = r - kf * len;
+            const int k = kf / f, phs = kf - k * f;
+            const float cc = u0 + (float)f * (cpar[2 * k + (isx ? 0 : 1)] + dpar[isx ? 0 : 1]);
+            const int lo = (int)floorf(cc) - kWinLo;
+            int m0 = lo - phs;
+            m0 = m0 >= 0 ? (m0 + f - 1) / f : -((-m0) / f);
+            float2 acc = make_float2(0.f, 0.f);
+            for (int m = m0;; ++m) {
+                const int u = f * m + phs;
+                if (u >= lo + kWin) break;
+                if (u < 0 || u >= F) continue;
+                const float t = (float)u - cc;
+                const float gv = kGauss1Norm * exp2f(-t * t);
+                const float2 w = tw[(int)(((long long)kk * m) % L)];
+                acc.x += gv * w.x;
+                acc.y += gv * w.y;
+            }
+            gsp[idx] = acc;
+        }
+        __syncthreads();
+        // forward model spectrum: sum_phi Khat_phi (Hhat_phi + sum_k a_k gx gy)
+        const float2 *kh = fd.fft_khat + (long long)i * nph * L * H;
+        const float2 *hh = hhat_all + fd.fft_hhat_off;
+        for (int idx = tid; idx < L * H; idx += blockDim.x) {
+            const int ky = idx / H, kx = idx - ky * H;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int ph = 0; ph < nph; ++ph) {
+                const int phy = ph / f, phx = ph - phy * f;
+                float2 sp = hh[(long long)ph * L * H + idx];
+                for (int k = 0; k < M; ++k) {
+                    const float2 gxv = gsp[(k * f + phx) * H + kx];
+                    const float2 gyv = gsp[nx + (k * f + phy) * L + ky];
+                    const float2 pr = cmul(gxv, gyv);
+                    sp.x += apar[k] * pr.x;
+                    sp.y += apar[k] * pr.y;
+                }
+                acc = cadd(acc, cmul(kh[(long long)ph * L * H + idx], sp));
+            }
+            A[idx] = acc;
+        }
+        __syncthreads();
+        const int np = (N + 1) / 2;
+        float2 *Mp = inv2d(A, B, g, np);
+        // residual on [0,N)^2; the pairs become e (zero outside), ready for the forward transform
+        const float scale = 1.f / ((float)L * (float)L);
+        const float bg = (float)(f * f) * gam;
+        double chi = 0.0, se = 0.0;
+        const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
+        for (int idx = tid; idx < np * L; idx += blockDim.x) {
+            const int p = idx / L, x = idx - p * L;
+            const float2 mv = Mp[p * Lp + x];
+            float e2[2] = {0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int y = 2 * p + q;
+                if (y < N && x < N) {
+                    const float Mv = (q ? mv.y : mv.x) * scale + bg;
+                    const float res = __ldg(dd + y * N + x) - Mv;
+                    const float wv = __ldg(ww + y * N + x);
+                    chi += (double)(0.5f * wv * res * res);
+                    e2[q] = -wv * res;
+                    se += (double)e2[q];
+                }
+            }
+            Mp[p * Lp + x] = make_float2(e2[0], e2[1]);
+        }
+        __syncthreads();
+        float2 *other = (Mp == A) ? B : A;
+        float2 *Eh = fwd2d(Mp, other, g, np);
+        for (int idx = tid; idx < L * H; idx += blockDim.x) ehat_g[idx] = Eh[idx];
+        __syncthreads();
+        // adjoint images G_phi = IDFT(conj(Khat_phi) ehat) on [0,N)^2
+        float *gout = gbuf + fd.gbuf_off + (long long)i * nph * N * N;
+        for (int ph = 0; ph < nph; ++ph) {
+            for (int idx = tid; idx < L * H; idx += blockDim.x) A[idx] = cmulc(ehat_g[idx], kh[(long long)ph * L * H + idx]);
+            __syncthreads();
+            float2 *Gp = inv2d(A, B, g, np);
+            for (int idx = tid; idx < np * L; idx += blockDim.x) {
+                const int p = idx / L, x = idx - p * L;
+                if (x >= N) continue;
+                const float2 v = Gp[p * Lp + x];
+                const int y = 2 * p;
+                gout[((long long)ph * N + y) * N + x] = v.x * scale;
+                if (y + 1 < N) gout[((long long)ph * N + y + 1) * N + x] = v.y * scale;
+            }
+            __syncthreads();
+        }
+        block_sum2(chi, se, s_red);
+        if (tid == 0) {
+            chi_part[item.z] = chi;
+            se_part[item.z] = se;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+int fft_smem_bytes(int L, int M, int f) {
+    const int H = L / 2 + 1;
+    return (2 * L * H + L + M * f * (H + L)) * (int)sizeof(float2);
+}
+
+sr_status configure_fft_kernels(int smem) {
+    SR_CUDA(cudaFuncSetAttribute(fft_epoch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SR_CUDA(cudaFuncSetAttribute(fft_hhat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SR_CUDA(cudaFuncSetAttribute(fft_kappa_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return SR_OK;
+}
+
+sr_status occupancy_fft_kernel(int smem, int *blocks) {
+    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fft_epoch_kernel, kThreads, smem));
+    return SR_OK;
+}
+
+void launch_fft_kappa(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st) {
+    const int L = fd.fft_L;
+    const int smem = fft_smem_bytes(L, 0, fd.f);
+    fft_kappa_kernel<<<fd.E * fd.f * fd.f, kThreads, smem, st>>>(fd, kappa, khat);
+}
+
+void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
+                     const float *params, float2 *hhat, cudaStream_t st) {
+    fft_hhat_kernel<<<dim3(n_fft_fields, max_nph), kThreads, smem, st>>>(fields, fft_fields, params, hhat);
+}
+
+void launch_fft_epochs(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
+                       const float2 *hhat, float2 *ehat_scratch, long long ehat_stride, float *gbuf, double *chi_part,
+                       double *se_part, int grid, int smem, cudaStream_t st) {
+    fft_epoch_kernel<<<grid, kThreads, smem, st>>>(fields, items, n_items, counter, params, hhat, ehat_scratch,
+                                                   ehat_stride, gbuf, chi_part, se_part);
+}
+
+}  // namespace sr

@@ -25,6 +25,17 @@ void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_par
                      const double *l1_part, const float *ps_da, const float *ps_du, float *grad, double *losses,
                      double *total, cudaStream_t st);
 
+// --- frequency-domain form (fft.cu) ---
+int fft_smem_bytes(int L, int M, int f);
+sr_status configure_fft_kernels(int smem);
+sr_status occupancy_fft_kernel(int smem, int *blocks);
+void launch_fft_kappa(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st);
+void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
+                     const float *params, float2 *hhat, cudaStream_t st);
+void launch_fft_epochs(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
+                       const float2 *hhat, float2 *ehat_scratch, long long ehat_stride, float *gbuf, double *chi_part,
+                       double *se_part, int grid, int smem, cudaStream_t st);
+
 // --- starlet prior (starlet.cu) ---
 // Forward levels then adjoint levels for every field of the table; writes the
 // per-(level, chunk) prior partial sums and leaves T0 = dP/dh in plane J of

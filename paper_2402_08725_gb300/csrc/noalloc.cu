@@ -83,7 +83,7 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
         return noalloc_fail(SR_ERR_ARG, "sr_loss_and_grad_noalloc: NULL argument");
     const sr_problem_desc &D = *desc;
     if (D.kind != SR_DECONV) return noalloc_fail(SR_ERR_UNSUPPORTED, "sr_loss_and_grad_noalloc: deconvolution only");
-    if (D.conv_mode == SR_CONV_PLAIN)
+    if (D.conv_mode == SR_CONV_PLAIN || D.conv_mode == SR_CONV_FFT)
         return noalloc_fail(SR_ERR_UNSUPPORTED, "sr_loss_and_grad_noalloc: the folded direct form only");
     if (D.n_epochs < 1 || D.data_n < 1 || D.data_n > 256 || D.supersampling < 1 || D.supersampling > 8 ||
         D.psf_k < 1 || D.psf_k > 511 || D.n_sources < 0 || D.n_sources > 64 || D.n_scales < 2 ||

@@ -1,0 +1,35 @@
+// Deterministic block reductions (internal, device code).
+#pragma once
+
+#include "common.cuh"
+
+namespace sr {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum of two doubles (fixed shuffle tree, warps summed in order).
+__device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[kThreads / 32]) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = a;
+        red[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            sa += red[0][i];
+            sb += red[1][i];
+        }
+        a = sa;
+        b = sb;
+    }
+}
+
+}  // namespace sr

@@ -45,7 +45,7 @@ SMALL = [
 
 
 @pytest.mark.parametrize("E,N,f,K,M,J", SMALL)
-@pytest.mark.parametrize("mode", ["direct", "plain"])
+@pytest.mark.parametrize("mode", ["direct", "plain", "fft"])
 def test_small_cases_match_oracle(E, N, f, K, M, J, mode):
     fd = syn.small_deconv(seed=100 + N + K, E=E, N=N, f=f, K=K, M=M, J=J, lam=1.5)
     loss, g = _run(fd, conv_mode=mode)
@@ -60,7 +60,7 @@ def test_masked_pixels_background_and_edge_source():
     c[1] = (13.2, -13.4)   # near the corner: window clipped by the grid
     gm = np.array([0.3, -0.2, 0.1])
     P = syn.pack_deconv(h, a, c, dl, gm)
-    for mode in ("direct", "plain"):
+    for mode in ("direct", "plain", "fft"):
         loss, g = _run(fd, P, conv_mode=mode)
         check_deconv(fd, loss, g, params=P)
 
@@ -68,30 +68,33 @@ def test_masked_pixels_background_and_edge_source():
 def test_lambda_zero_and_large():
     for lam in (0.0, 20.0):
         fd = syn.small_deconv(seed=9, E=2, N=32, f=2, K=17, M=1, J=4, lam=lam)
-        loss, g = _run(fd)
-        check_deconv(fd, loss, g)
+        for mode in ("direct", "fft"):
+            loss, g = _run(fd, conv_mode=mode)
+            check_deconv(fd, loss, g)
 
 
 def test_config1_full_size():
     fd = syn.config1()
-    for mode in ("direct", "plain"):
+    for mode in ("direct", "plain", "fft"):
         loss, g = _run(fd, conv_mode=mode)
         r = check_deconv(fd, loss, g)
         print("config1", mode, r)
 
 
-def test_config3_full_size():
+@pytest.mark.parametrize("mode", ["direct", "fft"])
+def test_config3_full_size(mode):
     """300 epochs of 64x64, f=2, K=64, 4 sources: all epochs in one persistent launch."""
     fd = syn.config3()
-    loss, g = _run(fd)
+    loss, g = _run(fd, conv_mode=mode)
     r = check_deconv(fd, loss, g)
-    print("config3", r)
+    print("config3", mode, r)
 
 
-def test_repeatable_bitwise():
+@pytest.mark.parametrize("mode", ["direct", "fft"])
+def test_repeatable_bitwise(mode):
     fd = syn.small_deconv(seed=4, E=5, N=48, f=2, K=21, M=2, J=4, lam=1.0)
     from paper_2402_08725_gb300.binding import Problem
-    prob = Problem.from_field(fd)
+    prob = Problem.from_field(fd, conv_mode=mode)
     p = torch.from_numpy(fd.params).cuda()
     l1, g1 = prob.loss_and_grad(p)
     g1 = g1.clone()
@@ -102,13 +105,14 @@ def test_repeatable_bitwise():
 
 
 def test_batch_equals_single_fields_bitwise():
-    """An uneven batch (sizes, epoch counts, starlet depths) gives each field exactly
-    the loss and gradient of its own single-problem evaluation."""
+    """An uneven batch (sizes, epoch counts, starlet depths, and both the direct and the
+    transform form) gives each field exactly the loss and gradient of its own
+    single-problem evaluation."""
     from paper_2402_08725_gb300.binding import Batch, Problem
     shapes = [(3, 32, 4), (5, 48, 5), (2, 64, 4), (4, 96, 6), (1, 20, 3)]
     fields = [syn.small_deconv(seed=50 + i, E=E, N=N, f=2, K=17, M=1, J=J, lam=1.0)
               for i, (E, N, J) in enumerate(shapes)]
-    probs = [Problem.from_field(fd) for fd in fields]
+    probs = [Problem.from_field(fd, conv_mode=("fft" if i % 2 else "direct")) for i, fd in enumerate(fields)]
     batch = Batch(probs)
     P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
     losses = torch.empty(len(fields), dtype=torch.float64, device="cuda")
