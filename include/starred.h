@@ -55,7 +55,10 @@
  * sr_last_error() gives a message for the calling thread's last failure.
  * Calls that need data not yet set return SR_ERR_STATE.  Non-finite inputs
  * (NaN data, NaN or non-positive sigma, non-finite PSF values) are rejected
- * with SR_ERR_NONFINITE by the first call after them that returns a host value.  A problem is not thread-safe: use one per thread or
+ * with SR_ERR_NONFINITE by the first call after them that returns a host value.
+ * Debugging aid: with the environment variable SR_GUARD=1 set when buffers are
+ * allocated, every device buffer of the library carries a guard tail, and the
+ * calls that return a host value fail with SR_ERR_STATE if a tail was written.  A problem is not thread-safe: use one per thread or
  * serialise calls.
  */
 #ifndef STARRED_H
@@ -231,6 +234,14 @@ sr_status sr_batch_loss_and_grad_host(sr_batch *b, const float *params_host, dou
 sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_optim_cfg *cfg,
                         double *last_total_host);
 sr_status sr_batch_reset_optimizer(sr_batch *b);
+
+/* Which form evaluates field i of the batch: SR_CONV_DIRECT or SR_CONV_FFT
+ * (AUTO fields are resolved by the autotuner when the batch is created: both
+ * forms are timed on the field's shape and the faster one is kept; the
+ * choices are cached per shape in memory, and in the JSON file named by the
+ * environment variable SR_AUTOTUNE_CACHE when it is set).  -1 for a bad
+ * argument. */
+int sr_batch_field_form(const sr_batch *b, int i);
 
 /* Launch statistics of the last evaluation on this problem/batch: number of
  * kernel launches one loss_and_grad issues. */

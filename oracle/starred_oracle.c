@@ -39,6 +39,8 @@
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+#else
+static int omp_in_parallel(void) { return 1; }
 #endif
 
 #define ORC_OK 0
@@ -87,10 +89,13 @@ int orc_max_threads(void) {
 /* S: narrow-PSF convolution on the fine grid (Eq. 8 and Eq. 10, sec. 2.2).  */
 /* ------------------------------------------------------------------------- */
 
-/* out[u] = sum_q s[q] * x[u - q + o], zero outside [0,F)^2, o = K/2. */
+/* out[u] = sum_q s[q] * x[u - q + o], zero outside [0,F)^2, o = K/2.
+ * Output rows are independent; when not already inside a parallel region they are
+ * shared among threads (each pixel's sum keeps its order, so results do not change). */
 int orc_conv_same(int F, int K, const double *x, const double *s, double *out) {
     if (F <= 0 || K <= 0) return ORC_ERR_SHAPE;
     int o = K / 2;
+#pragma omp parallel for schedule(static) if (!omp_in_parallel() && (long)F * F * K * K > 100000000L)
     for (int uy = 0; uy < F; ++uy)
         for (int ux = 0; ux < F; ++ux) {
             double acc = 0.0;
@@ -108,13 +113,10 @@ int orc_conv_same(int F, int K, const double *x, const double *s, double *out) {
     return ORC_OK;
 }
 
-/* Transpose of orc_conv_same, written as the scatter of each forward term:
- * every term s[q]*x[u-q+o] of out[u] sends s[q]*y[u] to position u-q+o. */
-int orc_conv_same_adjoint(int F, int K, const double *y, const double *s, double *out) {
-    if (F <= 0 || K <= 0) return ORC_ERR_SHAPE;
+/* Scatter of the rows [uy0, uy1) of y into out (added). */
+static void conv_adjoint_rows(int F, int K, int uy0, int uy1, const double *y, const double *s, double *out) {
     int o = K / 2;
-    memset(out, 0, sizeof(double) * (size_t)F * F);
-    for (int uy = 0; uy < F; ++uy)
+    for (int uy = uy0; uy < uy1; ++uy)
         for (int ux = 0; ux < F; ++ux) {
             double yu = y[uy * F + ux];
             if (yu == 0.0) continue;
@@ -128,6 +130,29 @@ int orc_conv_same_adjoint(int F, int K, const double *y, const double *s, double
                 }
             }
         }
+}
+
+/* Transpose of orc_conv_same, written as the scatter of each forward term:
+ * every term s[q]*x[u-q+o] of out[u] sends s[q]*y[u] to position u-q+o.
+ * Large sizes scatter a fixed number of row bands into private images, summed in band
+ * order (the same result for any number of threads). */
+int orc_conv_same_adjoint(int F, int K, const double *y, const double *s, double *out) {
+    if (F <= 0 || K <= 0) return ORC_ERR_SHAPE;
+    memset(out, 0, sizeof(double) * (size_t)F * F);
+    const int bands = 16;
+    size_t n = (size_t)F * F;
+    if (omp_in_parallel() || (long)F * F * K * K <= 100000000L || F < bands) {
+        conv_adjoint_rows(F, K, 0, F, y, s, out);
+        return ORC_OK;
+    }
+    double *part = calloc(n * bands, sizeof(double));
+    if (!part) return ORC_ERR_OOM;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < bands; ++b)
+        conv_adjoint_rows(F, K, (int)((long)F * b / bands), (int)((long)F * (b + 1) / bands), y, s, part + n * b);
+    for (int b = 0; b < bands; ++b)
+        for (size_t k = 0; k < n; ++k) out[k] += part[n * b + k];
+    free(part);
     return ORC_OK;
 }
 
@@ -342,7 +367,9 @@ int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const d
     deconv_offsets(E, N, f, M, &oh, &oa, &oc, &od, &og, &tot);
     size_t n = (size_t)F * F;
     int err = 0;
-#pragma omp parallel
+    int nt = orc_threads(0);
+    if (nt > E) nt = E;
+#pragma omp parallel num_threads(nt)
     {
         double *fimg = malloc(sizeof(double) * n), *conv = malloc(sizeof(double) * n);
         if (!fimg || !conv) {
@@ -374,6 +401,7 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
     deconv_offsets(E, N, f, M, &oh, &oa, &oc, &od, &og, &tot);
     size_t n = (size_t)F * F;
     int nt = orc_threads(nthreads);
+    if (nt > E) nt = E; /* fewer epochs than threads: the convolutions share the rest */
     double *chi = calloc((size_t)E, sizeof(double));
     /* per-epoch gradient wrt the fine image f_i, summed into dh afterwards in epoch order */
     double *gfine = grad ? malloc(sizeof(double) * n * (size_t)E) : NULL;

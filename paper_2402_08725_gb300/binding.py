@@ -261,6 +261,11 @@ class Batch:
     def launches_per_eval(self) -> int:
         return int(self.lib.sr_batch_launches_per_eval(self.handle))
 
+    def field_forms(self):
+        """'direct' or 'fft' for each field, as chosen when the batch was created."""
+        return ["fft" if self.lib.sr_batch_field_form(self.handle, i) == nat.SR_CONV_FFT else "direct"
+                for i in range(len(self.problems))]
+
     def profile(self, enable: bool = True):
         nat.check(self.lib.sr_batch_profile(self.handle, 1 if enable else 0), "sr_batch_profile")
 

@@ -4,7 +4,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -41,29 +44,62 @@ static sr_status fail(sr_status s, const char *fmt, ...) {
     return s;
 }
 
+// Guard-band debug mode (environment variable SR_GUARD=1 when a buffer is allocated): every
+// device buffer gets a tail of kGuardBytes filled with kGuardByte, and calls that return a host
+// value verify that no tail was written (an overrun fails them with SR_ERR_STATE).
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
+
+static bool guard_mode() {
+    const char *v = getenv("SR_GUARD");
+    return v && v[0] == '1';
+}
+
 // Device allocations owned by one object, freed together.
 struct DevArena {
     std::vector<void *> ptrs;
+    std::vector<std::pair<unsigned char *, size_t>> guards;  // (tail start, bytes) when guarded
     template <typename T>
     sr_status alloc(T **p, size_t n) {
         *p = nullptr;
         if (n == 0) n = 1;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        const bool guard = guard_mode();
+        const size_t bytes = n * sizeof(T);
+        cudaError_t e = cudaMalloc(&q, bytes + (guard ? kGuardBytes : 0));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         ptrs.push_back(q);
+        if (guard) {
+            unsigned char *tail = static_cast<unsigned char *>(q) + bytes;
+            e = cudaMemset(tail, kGuardByte, kGuardBytes);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+            guards.emplace_back(tail, kGuardBytes);
+        }
         *p = static_cast<T *>(q);
+        return SR_OK;
+    }
+    // SR_OK if every guard tail still holds the pattern (synchronous).
+    sr_status check_guards() const {
+        std::vector<unsigned char> buf(kGuardBytes);
+        for (const auto &g : guards) {
+            cudaError_t e = cudaMemcpy(buf.data(), g.first, g.second, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "guard check");
+            for (size_t k = 0; k < g.second; ++k)
+                if (buf[k] != kGuardByte) return fail(SR_ERR_STATE, "a device buffer was written past its end");
+        }
         return SR_OK;
     }
     void release() {
         for (void *q : ptrs) cudaFree(q);
         ptrs.clear();
+        guards.clear();
     }
     ~DevArena() { release(); }
 };
 
 static int g_smem_optin = -1;
 static int g_num_sms = 0;
+static int g_fft_smem_limit = 0;  // dynamic shared memory the transform kernels can take
 
 static sr_status device_limits() {
     if (g_smem_optin >= 0) return SR_OK;
@@ -75,7 +111,7 @@ static sr_status device_limits() {
     const int dyn = g_smem_optin - 1024;
     sr_status s = configure_tile_kernels(dyn, dyn);
     if (s != SR_OK) return s;
-    s = configure_fft_kernels(dyn);
+    s = configure_fft_kernels(g_smem_optin, &g_fft_smem_limit);
     if (s != SR_OK) return s;
     return SR_OK;
 }
@@ -146,8 +182,7 @@ struct Plan {
     int n_fft_items = 0, n_fft_fields = 0, max_nph = 1, smem_fft = 0, grid_fft = 0;
     int4 *d_fft_items = nullptr;
     int *d_fft_fields = nullptr;
-    float2 *hhat = nullptr, *ehat = nullptr;
-    long long ehat_stride = 0;
+    float2 *hhat = nullptr, *fft_acc = nullptr;
     // PSF
     PsfBuffers psf{};
     // plain form
@@ -298,20 +333,86 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
     fd.fft_khat = p->khat;
 }
 
-// Whether a field of a plan runs in the frequency domain.
-static bool use_fft(const sr_problem *p) {
-    return p->fft_ok && (p->desc.conv_mode == SR_CONV_FFT || p->desc.conv_mode == SR_CONV_AUTO);
-}
+// Epochs per work item of the frequency-domain form (one accumulator per item).
+static const int kFftChunk = 8;
 
-static int choose_pg(int nph, int threads_per_group) {
+// Phase groups of a tile: the most phases at once that fit in the block's threads and in
+// shared memory (one group always).
+static int choose_pg(int nph, TileItem t, int Tk) {
     int best = 1;
-    for (int pg = 1; pg <= nph; ++pg)
-        if (nph % pg == 0 && pg * threads_per_group <= kThreads) best = pg;
+    const int threads_per_group = t.h * (t.w / kR);
+    for (int pg = 1; pg <= nph; ++pg) {
+        if (nph % pg != 0 || pg * threads_per_group > kThreads) continue;
+        t.pg = pg;
+        if (tile_smem_bytes(t, Tk, true) > g_smem_optin - 1024) continue;
+        best = pg;
+    }
     return best;
 }
 
+// ------------------------------------------------------------------------------------------
+// Autotuner: which form (direct tiles or transforms) evaluates a field shape faster per epoch.
+// ------------------------------------------------------------------------------------------
+static std::mutex g_tune_mutex;
+static std::map<std::string, int> g_tune;  // "N,f,K,M" -> 0 direct, 1 transforms
+static bool g_tune_loaded = false;
+
+static std::string tune_key(const sr_problem_desc &d) {
+    char buf[96];
+    snprintf(buf, sizeof buf, "%d,%d,%d,%d", d.data_n, d.supersampling, d.psf_k, d.n_sources);
+    return buf;
+}
+
+// Cache file named by SR_AUTOTUNE_CACHE: one JSON object {"N,f,K,M": mode, ...}.
+static void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("SR_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return;
+    char key[96];
+    int mode;
+    int c;
+    while ((c = fgetc(fp)) != EOF) {
+        if (c != '"') continue;
+        if (fscanf(fp, "%95[^\"]\": %d", key, &mode) == 2 && (mode == 0 || mode == 1)) g_tune[key] = mode;
+    }
+    fclose(fp);
+}
+
+static void tune_save() {
+    const char *path = getenv("SR_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *fp = fopen(path, "w");
+    if (!fp) return;
+    fprintf(fp, "{");
+    bool first = true;
+    for (const auto &kv : g_tune) {
+        fprintf(fp, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
+        first = false;
+    }
+    fprintf(fp, "\n}\n");
+    fclose(fp);
+}
+
+struct PlanOptions;
+static sr_status time_form(sr_problem *p, int mode, float *ms);
+
+static bool field_uses_fft(sr_problem *p, const PlanOptions &opt);
+
+// Options of the single-field plans the autotuner times.
+struct PlanOptions {
+    int mode_override = -1;  // -1: the problem's own choice, 0: direct tiles, 1: transforms
+    int epoch_limit = 0;     // > 0: evaluate only the first epochs
+    int grid_limit = 0;      // > 0: at most this many blocks in the persistent kernels
+};
+
+static bool field_uses_fft(sr_problem *p, const PlanOptions &opt);
+
 // Build the evaluation plan of `n` problems of the same kind.
-static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plain) {
+static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plain,
+                            const PlanOptions &opt = PlanOptions()) {
     sr_status st = device_limits();
     if (st != SR_OK) return st;
     pl->kind = probs[0]->desc.kind;
@@ -329,12 +430,13 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     int smem_fwd = 0, smem_adj = 0, smem_fft = 0;
     std::vector<int4> fft_items;
     std::vector<int> fft_fields;
-    long long hhat_len = 0, max_LH = 0;
+    long long hhat_len = 0, acc_len = 0;
     for (int i = 0; i < n; ++i) {
         sr_problem *p = probs[i];
         if (p->desc.kind != pl->kind) return fail(SR_ERR_ARG, "a batch mixes problem kinds");
         FieldDev &fd = pl->h_fields[i];
         fill_field_common(fd, p);
+        if (opt.epoch_limit > 0) fd.E = std::min(fd.E, opt.epoch_limit);
         fd.param_off = (long long)poff;
         pl->param_off[i] = poff;
         const size_t np = param_count(p->desc);
@@ -357,24 +459,26 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         l1slot += (long long)(fd.J - 1) * fd.n_chunks;
         for (int c = 0; c < fd.n_chunks; ++c) chunks.push_back(ChunkItem{i, c * 256, c});
         Jmax = std::max(Jmax, fd.J);
-        if (pl->kind == SR_DECONV && !plain && use_fft(p)) {
-            gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
+        if (pl->kind == SR_DECONV && !plain && field_uses_fft(p, opt)) {
+            // frequency-domain form: chunks of consecutive epochs, one accumulator per chunk
             fd.mode = 1;
             fd.n_tiles = 1;
             fd.tile_slot = tslot;
-            for (int e = 0; e < fd.E; ++e) fft_items.push_back(make_int4(i, e, (int)(tslot + e), 0));
             tslot += fd.E;
             fd.ps_slot = psslot;
-            for (int e = 0; e < fd.E; ++e)
-                for (int k = 0; k < fd.M; ++k) ps.push_back(make_int4(i, e, k, 0));
             psslot += (long long)fd.E * fd.M;
             const int L = fd.fft_L, H = L / 2 + 1;
+            const int nph = fd.f * fd.f;
+            fd.fft_acc_off = acc_len;
+            fd.fft_n_chunks = (fd.E + kFftChunk - 1) / kFftChunk;
+            for (int c = 0; c < fd.fft_n_chunks; ++c)
+                fft_items.push_back(make_int4(i, c * kFftChunk, std::min(fd.E, (c + 1) * kFftChunk), c));
+            acc_len += (long long)fd.fft_n_chunks * nph * L * H;
             fd.fft_hhat_off = hhat_len;
-            hhat_len += (long long)fd.f * fd.f * L * H;
+            hhat_len += (long long)nph * L * H;
             fft_fields.push_back(i);
-            pl->max_nph = std::max(pl->max_nph, fd.f * fd.f);
+            pl->max_nph = std::max(pl->max_nph, nph);
             smem_fft = std::max(smem_fft, fft_smem_bytes(L, fd.M, fd.f));
-            max_LH = std::max<long long>(max_LH, (long long)L * H);
         } else if (pl->kind == SR_DECONV && !plain) {
             gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
             const int nph = fd.f * fd.f;
@@ -387,7 +491,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
                     t.x0 = (short)x0;
                     t.h = (short)std::min(64, fd.N - y0);
                     t.w = (short)(((std::min(64, fd.N - x0)) + kR - 1) / kR * kR);
-                    t.pg = choose_pg(nph, t.h * (t.w / kR));
+                    t.pg = choose_pg(nph, t, fd.Tk);
                     tiles.push_back(t);
                 }
             fd.n_tiles = (int)tiles.size();
@@ -429,8 +533,8 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     });
     std::stable_sort(fft_items.begin(), fft_items.end(), [&](const int4 &a, const int4 &b) {
         const FieldDev &fa = pl->h_fields[a.x], &fb = pl->h_fields[b.x];
-        const double ca = (double)fa.fft_L * fa.fft_L * (2 + fa.f * fa.f);
-        const double cb = (double)fb.fft_L * fb.fft_L * (2 + fb.f * fb.f);
+        const double ca = (double)fa.fft_L * fa.fft_L * (2 + fa.f * fa.f) * (a.z - a.y);
+        const double cb = (double)fb.fft_L * fb.fft_L * (2 + fb.f * fb.f) * (b.z - b.y);
         return ca > cb;
     });
     pl->n_fft_items = (int)fft_items.size();
@@ -489,17 +593,17 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     if (!chunks.empty()) SR_CUDA(cudaMemcpy(pl->d_chunks, chunks.data(), sizeof(ChunkItem) * chunks.size(), cudaMemcpyHostToDevice));
     SR_CUDA(cudaMemcpy(pl->d_group, groups.data(), groups.size(), cudaMemcpyHostToDevice));
     if (pl->n_fft_items > 0) {
-        const int limit = g_smem_optin - 1024;
-        if (smem_fft > limit) return fail(SR_ERR_UNSUPPORTED, "transform form needs %d bytes of shared memory", smem_fft);
+        if (smem_fft > g_fft_smem_limit)
+            return fail(SR_ERR_UNSUPPORTED, "transform form needs %d bytes of shared memory", smem_fft);
         pl->smem_fft = smem_fft;
         int bfft = 0;
         if ((st = occupancy_fft_kernel(smem_fft, &bfft)) != SR_OK) return st;
         pl->grid_fft = std::max(1, std::min(pl->n_fft_items, std::max(bfft, 1) * g_num_sms));
-        pl->ehat_stride = max_LH;
+        if (opt.grid_limit > 0) pl->grid_fft = std::min(pl->grid_fft, opt.grid_limit);
         if ((st = A.alloc(&pl->d_fft_items, fft_items.size())) != SR_OK) return st;
         if ((st = A.alloc(&pl->d_fft_fields, fft_fields.size())) != SR_OK) return st;
         if ((st = A.alloc(&pl->hhat, (size_t)hhat_len)) != SR_OK) return st;
-        if ((st = A.alloc(&pl->ehat, (size_t)(max_LH * pl->grid_fft))) != SR_OK) return st;
+        if ((st = A.alloc(&pl->fft_acc, (size_t)acc_len)) != SR_OK) return st;
         SR_CUDA(cudaMemcpy(pl->d_fft_items, fft_items.data(), sizeof(int4) * fft_items.size(), cudaMemcpyHostToDevice));
         SR_CUDA(cudaMemcpy(pl->d_fft_fields, fft_fields.data(), sizeof(int) * fft_fields.size(), cudaMemcpyHostToDevice));
     }
@@ -516,6 +620,10 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         ba = std::max(ba, 1);
         pl->grid_fwd = std::max(1, std::min(pl->n_items, bf * g_num_sms));
         pl->grid_adj = std::max(1, std::min(pl->n_items, ba * g_num_sms));
+        if (opt.grid_limit > 0) {
+            pl->grid_fwd = std::min(pl->grid_fwd, opt.grid_limit);
+            pl->grid_adj = std::min(pl->grid_adj, opt.grid_limit);
+        }
     }
     return SR_OK;
 }
@@ -557,9 +665,8 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
     if (pl->n_fft_items > 0) {
         launch_fft_hhat(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_nph, pl->smem_fft, params, pl->hhat,
                         st);
-        launch_fft_epochs(pl->d_fields, pl->d_fft_items, pl->n_fft_items, pl->d_counters + 2, params, pl->hhat,
-                          pl->ehat, pl->ehat_stride, pl->gbuf, pl->chi_part, pl->se_part, pl->grid_fft, pl->smem_fft,
-                          st);
+        launch_fft_chunks(pl->d_fields, pl->d_fft_items, pl->n_fft_items, pl->d_counters + 2, params, pl->hhat,
+                          pl->fft_acc, pl->chi_part, pl->se_part, pl->ps_da, pl->ps_du, pl->grid_fft, pl->smem_fft, st);
         n += 2;
     }
     if (ev) cudaEventRecord(ev[3], st);
@@ -568,12 +675,74 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
         ++n;
     }
     n += launch_starlet(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->Jmax, params, pl->l1_part, st);
-    launch_hgrad(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->gbuf, grad, st);
-    ++n;
+    if (pl->n_items > 0) {
+        launch_hgrad(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->gbuf, grad, st);
+        ++n;
+    }
+    if (pl->n_fft_items > 0) {
+        launch_fft_hgrad(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_nph, pl->smem_fft, pl->fft_acc,
+                         grad, st);
+        ++n;
+    }
     launch_finalize(pl->d_fields, pl->n_fields, pl->chi_part, pl->se_part, pl->l1_part, pl->ps_da, pl->ps_du, grad,
                     pl->losses, pl->total, st);
     n += 2;
     return n;
+}
+
+// Time one loss-and-gradient evaluation of a problem in a given form on its first <= 16
+// epochs with the persistent kernels on a single block: the cost per epoch on one SM, which is
+// what decides a batch that fills the GPU either way.  Parameters are all zero (the kernels'
+// work does not depend on the values).
+static sr_status time_form(sr_problem *p, int mode, float *ms) {
+    Plan pl;
+    PlanOptions opt;
+    opt.mode_override = mode;
+    opt.epoch_limit = 16;
+    opt.grid_limit = 1;
+    sr_problem *arr[1] = {p};
+    sr_status st = build_plan(&pl, arr, 1, false, opt);
+    if (st != SR_OK) return st;
+    float *params = nullptr, *grad = nullptr;
+    if ((st = pl.arena.alloc(&params, pl.n_params)) != SR_OK) return st;
+    if ((st = pl.arena.alloc(&grad, pl.n_params)) != SR_OK) return st;
+    SR_CUDA(cudaMemsetAsync(params, 0, sizeof(float) * pl.n_params, p->stream));
+    cudaEvent_t e0, e1;
+    SR_CUDA(cudaEventCreate(&e0));
+    SR_CUDA(cudaEventCreate(&e1));
+    run_eval(&pl, params, grad, p->stream, nullptr);
+    cudaEventRecord(e0, p->stream);
+    for (int r = 0; r < 3; ++r) run_eval(&pl, params, grad, p->stream, nullptr);
+    cudaEventRecord(e1, p->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+    *ms = t / 3.f;
+    return SR_OK;
+}
+
+static bool field_uses_fft(sr_problem *p, const PlanOptions &opt) {
+    if (opt.mode_override >= 0) return opt.mode_override == 1 && p->fft_ok;
+    if (!p->fft_ok) return false;
+    if (p->desc.conv_mode == SR_CONV_FFT) return true;
+    if (p->desc.conv_mode != SR_CONV_AUTO) return false;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_load();
+    const std::string key = tune_key(p->desc);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second == 1;
+    float t_direct = 0.f, t_fft = 0.f;
+    if (time_form(p, 0, &t_direct) != SR_OK || time_form(p, 1, &t_fft) != SR_OK) {
+        cudaGetLastError();
+        return true;  // the transform form fits; keep it when timing is not possible
+    }
+    const int mode = t_fft <= t_direct ? 1 : 0;
+    g_tune[key] = mode;
+    tune_save();
+    return mode == 1;
 }
 
 static sr_status check_ready(sr_problem *p) {
@@ -743,8 +912,8 @@ sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_p
         if (d.conv_mode == SR_CONV_FFT || d.conv_mode == SR_CONV_AUTO) {
             if ((st = device_limits()) != SR_OK) return bail(st);
             int L = 0, nst = 0;
-            const bool ok = fft_size(d.data_n, p->Tk, p->tau_lo, &L, &nst, p->fft_rad) &&
-                            fft_smem_bytes(L, d.n_sources, d.supersampling) <= g_smem_optin - 1024;
+            const bool ok = d.n_sources <= kFftMaxSources && fft_size(d.data_n, p->Tk, p->tau_lo, &L, &nst, p->fft_rad) &&
+                            fft_smem_bytes(L, d.n_sources, d.supersampling) <= g_fft_smem_limit;
             if (!ok && d.conv_mode == SR_CONV_FFT)
                 return bail(fail(SR_ERR_UNSUPPORTED, "the transform form does not fit this size in shared memory"));
             if (ok) {
@@ -867,6 +1036,7 @@ sr_status sr_loss_and_grad(sr_problem *p, const float *params_dev, double *loss_
         SR_CUDA(cudaMemcpyAsync(loss_host, pl->total, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
         SR_CUDA(cudaStreamSynchronize(p->stream));
         if (p->pending_check && (st = check_flag(p)) != SR_OK) return st;
+        if ((st = p->arena.check_guards()) != SR_OK || (st = pl->arena.check_guards()) != SR_OK) return st;
         if (!std::isfinite(*loss_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
     }
     return SR_OK;
@@ -1030,6 +1200,9 @@ sr_status sr_batch_loss_and_grad(sr_batch *b, const float *params_dev, double *l
         SR_CUDA(cudaStreamSynchronize(b->stream));
         sr_status st = batch_check(b);
         if (st != SR_OK) return st;
+        if ((st = pl->arena.check_guards()) != SR_OK) return st;
+        for (sr_problem *p : b->probs)
+            if ((st = p->arena.check_guards()) != SR_OK) return st;
         if (!std::isfinite(*total_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
     }
     return SR_OK;
@@ -1075,6 +1248,11 @@ sr_status sr_batch_reset_optimizer(sr_batch *b) {
 }
 
 int sr_batch_launches_per_eval(const sr_batch *b) { return b ? b->plan->launches : 0; }
+
+int sr_batch_field_form(const sr_batch *b, int i) {
+    if (!b || i < 0 || i >= b->plan->n_fields) return -1;
+    return b->plan->h_fields[i].mode == 1 ? SR_CONV_FFT : SR_CONV_DIRECT;
+}
 
 sr_status sr_batch_profile(sr_batch *b, int enable) {
     if (!b) return fail(SR_ERR_ARG, "NULL batch");

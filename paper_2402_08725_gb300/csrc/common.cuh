@@ -23,6 +23,8 @@ constexpr int kBlurHalf = 8;
 
 constexpr int kMaxScales = 8;
 constexpr int kFftMaxStages = 8;
+constexpr int kFftThreads = 512;
+constexpr int kFftMaxSources = 8;  // point sources per field in the frequency-domain form
 constexpr int kThreads = 256;
 
 struct FieldDev {
@@ -53,6 +55,8 @@ struct FieldDev {
     const float2 *fft_tw;     // [L] exp(-2 pi i n / L)
     const float2 *fft_khat;   // [E][f*f][L][L/2+1] transforms of the folded kernels
     long long fft_hhat_off;   // offset of the field's [f*f][L][L/2+1] h spectra in the plan buffer
+    long long fft_acc_off;    // float2 offset of the field's chunk accumulators ([f*f][L][L/2+1] each)
+    int fft_n_chunks;         // epoch chunks of the field
 };
 
 // One output tile of one epoch: rows [y0, y0+h), cols [x0, x0+w) of the data
@@ -70,6 +74,15 @@ struct ChunkItem {
     int start;     // first pixel (row-major F*F index) of the chunk
     int chunk;     // chunk index within the field
 };
+
+// Offset u - centre of fine pixel u from a point source whose fine centre is
+// (F-1)/2 + f (c + delta).  The centre can be hundreds of pixels from the origin while the
+// offset is a few pixels, so the offset is formed from small quantities: u - (F-1)/2 is exact,
+// and each product f*c, f*delta is rounded only together with the small running difference.
+__device__ __forceinline__ float src_offset(int u, int F, int f, float c, float delta) {
+    const float t = (float)u - 0.5f * (float)(F - 1);
+    return fmaf(-(float)f, delta, fmaf(-(float)f, c, t));
+}
 
 }  // namespace sr
 

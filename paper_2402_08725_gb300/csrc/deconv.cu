@@ -148,7 +148,7 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
         // point sources of this epoch: fine centre, amplitude and window origin (Eq. 9)
         if (tid < M && tid < kFusedSources) {
             const float2 cen = source_centre(cpar, dpar, tid, F, f);
-            s_src[tid] = make_float4(cen.x, cen.y, apar[tid], 0.f);
+            s_src[tid] = make_float4(cpar[2 * tid], cpar[2 * tid + 1], apar[tid], 0.f);
             s_win[tid] = make_int2((int)floorf(cen.x) - kWinLo, (int)floorf(cen.y) - kWinLo);
         }
         __syncthreads();
@@ -187,7 +187,8 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                         for (unsigned m = rowmask; m; m &= m - 1) {
                             const int k = __ffs(m) - 1;
                             if ((unsigned)(ux - s_win[k].x) < (unsigned)kWin)
-                                v += s_src[k].z * gauss_at((float)ux - s_src[k].x, (float)uy - s_src[k].y);
+                                v += s_src[k].z * gauss_at(src_offset(ux, F, f, s_src[k].x, dpar[0]),
+                                                           src_offset(uy, F, f, s_src[k].y, dpar[1]));
                         }
                     }
                     dst[j] = v;
@@ -227,7 +228,8 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                     if (uy < 0 || uy >= F || ux < 0 || ux >= F) continue;
                     const int i = my - my0, j = mx - mx0;
                     if (i < 0 || i >= G.xrows || j < 0 || j >= G.xcols) continue;
-                    const float val = apar[k] * gauss_at((float)ux - cen.x, (float)uy - cen.y);
+                    const float val = apar[k] * gauss_at(src_offset(ux, F, f, cpar[2 * k], dpar[0]),
+                                                         src_offset(uy, F, f, cpar[2 * k + 1], dpar[1]));
                     atomicAdd(&smem[grp * xsize + i * G.xpitch + j], val);
                 }
                 __syncthreads();
@@ -376,7 +378,8 @@ __global__ void psgrad_kernel(const FieldDev *__restrict__ fields, const int4 *_
         const int my = uy / f, mx = ux / f;
         const int ph = (uy - my * f) * f + (ux - mx * f);
         const float gv = G[((long long)ph * N + my) * N + mx];
-        const float dx = (float)ux - cen.x, dy = (float)uy - cen.y;
+        const float dx = src_offset(ux, F, f, cpar[2 * k], dpar[0]);
+        const float dy = src_offset(uy, F, f, cpar[2 * k + 1], dpar[1]);
         const float gg = gv * gauss_at(dx, dy);
         sa += gg;
         sx += gg * dx;
@@ -403,6 +406,7 @@ __global__ void hgrad_kernel(const FieldDev *__restrict__ fields, const ChunkIte
     if (c >= n_chunks) return;
     const ChunkItem ch = chunks[c];
     const FieldDev &fd = fields[ch.field];
+    if (fd.mode != 0) return;  // fields in the frequency-domain form get dL/dh from fft_hgrad_kernel
     const int q = ch.start + threadIdx.x;
     const int f = fd.f, N = fd.N, F = fd.F;
     if (q >= F * F) return;

@@ -12,12 +12,20 @@
 // separable).  Per epoch that is 2 + f^2 real 2-D transforms instead of (K+f-1)^2 taps per data
 // pixel and direction.
 //
+// The adjoint is not transformed back per epoch: dL/dh_phi = IDFT( sum_i conj(Khat_{i,phi}) ehat_i )
+// is accumulated in the frequency domain (per chunk of epochs, then per field in a fixed order)
+// and transformed once per field and phase.  The point sources' gradients come from Parseval's
+// identity, <G_{i,phi}, g> = L^-2 sum_k Ghat(k) conj(ghat(k)), with the separable spectra of the
+// window profile and of its shift derivatives.  Per epoch that is 2 real 2-D transforms.
+//
 // Transforms: Stockham auto-sort mixed-radix FFT (radices 4, 2, 3, 5), ping-ponging between two
 // shared-memory buffers, twiddles from a table exp(-2 pi i n / L).  A real L x L image is
 // transformed as L/2 complex rows (two real rows per complex row), split into the half spectrum
 // (L rows x L/2+1 columns), then L/2+1 complex column transforms; the inverse runs the same steps
 // backwards.  Rows that are known to be zero are skipped.
 #include <math.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -136,17 +144,21 @@ __device__ float2 *fwd2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
     float2 *r = stockham(in, tmp, np, g.Lp, 1, g, false);
     float2 *o = (r == in) ? tmp : in;
     const int L = g.L, H = g.H;
-    for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) {
-        const int y = idx / H, kx = idx - y * H;
-        float2 v = make_float2(0.f, 0.f);
-        if (y < 2 * np) {
-            const float2 *row = r + (y >> 1) * g.Lp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int y = warp; y < L; y += nw) {
+        float2 *orow = o + y * H;
+        if (y >= 2 * np) {
+            for (int kx = lane; kx < H; kx += 32) orow[kx] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const float2 *row = r + (y >> 1) * g.Lp;
+        const bool odd = y & 1;
+        for (int kx = lane; kx < H; kx += 32) {
             const float2 a = row[kx];
             const float2 b = conjf2(row[kx == 0 ? 0 : L - kx]);
-            v = (y & 1) ? make_float2(0.5f * (a.y - b.y), -0.5f * (a.x - b.x))   // (a - b) / (2i)
-                        : make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));   // (a + b) / 2
+            orow[kx] = odd ? make_float2(0.5f * (a.y - b.y), -0.5f * (a.x - b.x))   // (a - b) / (2i)
+                           : make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));   // (a + b) / 2
         }
-        o[idx] = v;
     }
     __syncthreads();
     return stockham(o, r, H, 1, H, g, false);
@@ -158,18 +170,21 @@ __device__ float2 *inv2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
     float2 *c = stockham(in, tmp, g.H, 1, g.H, g, true);
     float2 *o = (c == in) ? tmp : in;
     const int L = g.L, H = g.H;
-    for (int idx = threadIdx.x; idx < np * L; idx += blockDim.x) {
-        const int p = idx / L, kx = idx - p * L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < np; p += nw) {
         const float2 *r1 = c + (2 * p) * H, *r2 = c + (2 * p + 1) * H;
-        float2 z;
-        if (kx < H) {
-            const float2 a = r1[kx], b = r2[kx];
-            z = make_float2(a.x - b.y, a.y + b.x);           // a + i b
-        } else {
-            const float2 a = r1[L - kx], b = r2[L - kx];
-            z = make_float2(a.x + b.y, -a.y + b.x);          // conj(a) + i conj(b)
+        float2 *orow = o + p * g.Lp;
+        for (int kx = lane; kx < L; kx += 32) {
+            float2 z;
+            if (kx < H) {
+                const float2 a = r1[kx], b = r2[kx];
+                z = make_float2(a.x - b.y, a.y + b.x);           // a + i b
+            } else {
+                const float2 a = r1[L - kx], b = r2[L - kx];
+                z = make_float2(a.x + b.y, -a.y + b.x);          // conj(a) + i conj(b)
+            }
+            orow[kx] = z;
         }
-        o[p * g.Lp + kx] = z;
     }
     __syncthreads();
     return stockham(o, c, np, g.Lp, 1, g, true);
@@ -188,10 +203,10 @@ __device__ __forceinline__ void load_geom(FftGeom &g, const FieldDev &fd, float2
 // ---------------------------------------------------------------------------------------------
 // Khat_{i,phi}: transforms of the folded kernels placed at tau mod L.  One block per (epoch, phi).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFftThreads)
 fft_kappa_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restrict__ khat) {
     extern __shared__ __align__(16) float2 fsm[];
-    const int L = fd.fft_L, H = L / 2 + 1;
+    const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1;
     const int nph = fd.f * fd.f;
     const int item = blockIdx.x;
     const int i = item / nph, ph = item - i * nph;
@@ -200,17 +215,19 @@ fft_kappa_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restric
     load_geom(g, fd, tw);
     const int Tk = fd.Tk, tlo = fd.tau_lo, thi = tlo + Tk - 1;
     const float *kap = kappa + ((long long)i * nph + ph) * Tk * Tk;
-    for (int idx = threadIdx.x; idx < (L / 2) * L; idx += blockDim.x) {
-        const int p = idx / L, x = idx - p * L;
-        float v[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < L / 2; p += nw) {
+        for (int x = lane; x < L; x += 32) {
+            float v[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int y = 2 * p + q;
-            const int ty = y <= thi ? y : y - L;
-            const int tx = x <= thi ? x : x - L;
-            v[q] = (ty >= tlo && ty <= thi && tx >= tlo && tx <= thi) ? kap[(ty - tlo) * Tk + (tx - tlo)] : 0.f;
+            for (int q = 0; q < 2; ++q) {
+                const int y = 2 * p + q;
+                const int ty = y <= thi ? y : y - L;
+                const int tx = x <= thi ? x : x - L;
+                v[q] = (ty >= tlo && ty <= thi && tx >= tlo && tx <= thi) ? kap[(ty - tlo) * Tk + (tx - tlo)] : 0.f;
+            }
+            A[p * Lp + x] = make_float2(v[0], v[1]);
         }
-        A[p * g.Lp + x] = make_float2(v[0], v[1]);
     }
     __syncthreads();
     float2 *S = fwd2d(A, B, g, L / 2);
@@ -222,7 +239,7 @@ fft_kappa_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restric
 // Hhat_phi: transforms of the phase images of h, F_phi[m] = h[f m + phi].  One block per
 // (fft field, phi); blockIdx.x indexes fft_fields[].
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFftThreads)
 fft_hhat_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
                 const float *__restrict__ params, float2 *__restrict__ hhat_all) {
     extern __shared__ __align__(16) float2 fsm[];
@@ -230,22 +247,24 @@ fft_hhat_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft
     const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
     const int ph = blockIdx.y;
     if (ph >= nph) return;
-    const int L = fd.fft_L, H = L / 2 + 1;
+    const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1;
     float2 *A = fsm, *B = fsm + L * H, *tw = fsm + 2 * L * H;
     FftGeom g;
     load_geom(g, fd, tw);
     const int phy = ph / f, phx = ph - phy * f;
     const float *h = params + fd.param_off;
     const int np = (N + 1) / 2;
-    for (int idx = threadIdx.x; idx < np * L; idx += blockDim.x) {
-        const int p = idx / L, x = idx - p * L;
-        float v[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < np; p += nw) {
+        for (int x = lane; x < L; x += 32) {
+            float v[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int y = 2 * p + q;
-            v[q] = (y < N && x < N) ? h[(long long)(f * y + phy) * F + f * x + phx] : 0.f;
+            for (int q = 0; q < 2; ++q) {
+                const int y = 2 * p + q;
+                v[q] = (y < N && x < N) ? h[(long long)(f * y + phy) * F + f * x + phx] : 0.f;
+            }
+            A[p * Lp + x] = make_float2(v[0], v[1]);
         }
-        A[p * g.Lp + x] = make_float2(v[0], v[1]);
     }
     __syncthreads();
     float2 *S = fwd2d(A, B, g, np);
@@ -254,19 +273,21 @@ fft_hhat_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft
 }
 
 // ---------------------------------------------------------------------------------------------
-// One epoch per item: forward model, residual, chi^2, and the per-phase adjoint images.
-// items[] = (field, epoch, slot) for the fft fields; ehat_scratch: one L*H spectrum per block.
+// A chunk of consecutive epochs of one field per item (x = field, y = first epoch, z = end,
+// w = chunk index within the field): for each epoch, the forward model, residual, chi^2, ehat, the
+// Parseval products of the point sources, and conj(Khat_phi) ehat added into the chunk's
+// accumulator acc[slot][phi][L][H].
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
-fft_epoch_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ items, int n_items,
                  int *__restrict__ counter, const float *__restrict__ params, const float2 *__restrict__ hhat_all,
-                 float2 *__restrict__ ehat_scratch, long long ehat_stride, float *__restrict__ gbuf,
-                 double *__restrict__ chi_part, double *__restrict__ se_part) {
+                 float2 *__restrict__ acc_all, double *__restrict__ chi_part, double *__restrict__ se_part,
+                 float *__restrict__ ps_da, float *__restrict__ ps_du) {
     extern __shared__ __align__(16) float2 fsm[];
     __shared__ int s_item;
-    __shared__ double s_red[2][kThreads / 32];
+    __shared__ double s_red[2 + 3 * kFftMaxSources][kFftThreads / 32];
     const int tid = threadIdx.x;
-    float2 *ehat_g = ehat_scratch + (long long)blockIdx.x * ehat_stride;
+    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -274,157 +295,280 @@ fft_epoch_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ i
         if (it >= n_items) break;
         const int4 item = items[it];
         const FieldDev &fd = fields[item.x];
-        const int i = item.y;
         const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E, nph = f * f;
-        const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1;
-        float2 *A = fsm, *B = fsm + L * H, *tw = fsm + 2 * L * H;
-        float2 *gsp = tw + L;  // point-source 1-D spectra: [M][f][H] (x) then [M][f][L] (y)
+        const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1, LH = L * H;
+        float2 *A = fsm, *B = fsm + LH, *tw = fsm + 2 * LH;
+        // point-source 1-D spectra: [M][f] x-profiles and x-derivatives (H each), then y (L each)
+        float2 *gsx = tw + L;                // [M][f][H]
+        float2 *gsxd = gsx + M * f * H;      // [M][f][H]
+        float2 *gsy = gsxd + M * f * H;      // [M][f][L]
+        float2 *gsyd = gsy + M * f * L;      // [M][f][L]
         FftGeom g;
         load_geom(g, fd, tw);
         const float *hpar = params + fd.param_off;
-        const float *apar = hpar + (long long)F * F + (long long)i * M;
         const float *cpar = hpar + (long long)F * F + (long long)E * M;
-        const float *dpar = cpar + 2 * M + 2 * i;
-        const float gam = cpar[2 * M + 2 * E + i];
-        __syncthreads();
-        // 1-D transforms of the point sources' window profiles, per axis and phase:
-        // gx[k][phx][kx] = sum_m g1(f m + phx - cx) W^(kx m) over the window columns (likewise y)
-        const float u0 = 0.5f * (float)(F - 1);
-        const int nx = M * f * H, ny = M * f * L;
-        for (int idx = tid; idx < nx + ny; idx += blockDim.x) {
-            const bool isx = idx < nx;
-            const int r = isx ? idx : idx - nx;
-            const int len = isx ? H : L;
-            const int kf = r / len, kk = r - kf * len;
-            const int k = kf / f, phs = kf - k * f;
-            const float cc = u0 + (float)f * (cpar[2 * k + (isx ? 0 : 1)] + dpar[isx ? 0 : 1]);
-            const int lo = (int)floorf(cc) - kWinLo;
-            int m0 = lo - phs;
-            m0 = m0 >= 0 ? (m0 + f - 1) / f : -((-m0) / f);
-            float2 acc = make_float2(0.f, 0.f);
-            for (int m = m0;; ++m) {
-                const int u = f * m + phs;
-                if (u >= lo + kWin) break;
-                if (u < 0 || u >= F) continue;
-                const float t = (float)u - cc;
-                const float gv = kGauss1Norm * exp2f(-t * t);
-                const float2 w = tw[(int)(((long long)kk * m) % L)];
-                acc.x += gv * w.x;
-                acc.y += gv * w.y;
-            }
-            gsp[idx] = acc;
-        }
-        __syncthreads();
-        // forward model spectrum: sum_phi Khat_phi (Hhat_phi + sum_k a_k gx gy)
-        const float2 *kh = fd.fft_khat + (long long)i * nph * L * H;
         const float2 *hh = hhat_all + fd.fft_hhat_off;
-        for (int idx = tid; idx < L * H; idx += blockDim.x) {
-            const int ky = idx / H, kx = idx - ky * H;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int ph = 0; ph < nph; ++ph) {
-                const int phy = ph / f, phx = ph - phy * f;
-                float2 sp = hh[(long long)ph * L * H + idx];
-                for (int k = 0; k < M; ++k) {
-                    const float2 gxv = gsp[(k * f + phx) * H + kx];
-                    const float2 gyv = gsp[nx + (k * f + phy) * L + ky];
-                    const float2 pr = cmul(gxv, gyv);
-                    sp.x += apar[k] * pr.x;
-                    sp.y += apar[k] * pr.y;
-                }
-                acc = cadd(acc, cmul(kh[(long long)ph * L * H + idx], sp));
-            }
-            A[idx] = acc;
-        }
-        __syncthreads();
-        const int np = (N + 1) / 2;
-        float2 *Mp = inv2d(A, B, g, np);
-        // residual on [0,N)^2; the pairs become e (zero outside), ready for the forward transform
+        float2 *acc = acc_all + fd.fft_acc_off + (long long)item.w * nph * LH;
+        const float u0 = 0.5f * (float)(F - 1);
         const float scale = 1.f / ((float)L * (float)L);
-        const float bg = (float)(f * f) * gam;
-        double chi = 0.0, se = 0.0;
-        const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
-        for (int idx = tid; idx < np * L; idx += blockDim.x) {
-            const int p = idx / L, x = idx - p * L;
-            const float2 mv = Mp[p * Lp + x];
-            float e2[2] = {0.f, 0.f};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int y = 2 * p + q;
-                if (y < N && x < N) {
-                    const float Mv = (q ? mv.y : mv.x) * scale + bg;
-                    const float res = __ldg(dd + y * N + x) - Mv;
-                    const float wv = __ldg(ww + y * N + x);
-                    chi += (double)(0.5f * wv * res * res);
-                    e2[q] = -wv * res;
-                    se += (double)e2[q];
+        const int np = (N + 1) / 2;
+        for (int i = item.y; i < item.z; ++i) {
+            const float *apar = hpar + (long long)F * F + (long long)i * M;
+            const float *dpar = cpar + 2 * M + 2 * i;
+            const float gam = cpar[2 * M + 2 * E + i];
+            const float2 *kh = fd.fft_khat + (long long)i * nph * LH;
+            __syncthreads();
+            // 1-D transforms of the window profiles g1(u - c) and g1(u - c) (u - c) / sigma^2
+            const int nx = M * f * H, ny = M * f * L;
+            for (int idx = tid; idx < nx + ny; idx += blockDim.x) {
+                const bool isx = idx < nx;
+                const int r = isx ? idx : idx - nx;
+                const int len = isx ? H : L;
+                const int kf = r / len, kk = r - kf * len;
+                const int k = kf / f, phs = kf - k * f;
+                const float cc = u0 + (float)f * (cpar[2 * k + (isx ? 0 : 1)] + dpar[isx ? 0 : 1]);
+                const int lo = (int)floorf(cc) - kWinLo;
+                int m0 = lo - phs;
+                m0 = m0 >= 0 ? (m0 + f - 1) / f : -((-m0) / f);
+                float2 v = make_float2(0.f, 0.f), vd = make_float2(0.f, 0.f);
+                for (int m = m0;; ++m) {
+                    const int u = f * m + phs;
+                    if (u >= lo + kWin) break;
+                    if (u < 0 || u >= F) continue;
+                    const float t = src_offset(u, F, f, cpar[2 * k + (isx ? 0 : 1)], dpar[isx ? 0 : 1]);
+                    const float gv = kGauss1Norm * exp2f(-t * t);
+                    const float gd = gv * t * kGaussInvSig2;
+                    const float2 w = tw[(int)(((long long)kk * m) % L)];
+                    v.x += gv * w.x;
+                    v.y += gv * w.y;
+                    vd.x += gd * w.x;
+                    vd.y += gd * w.y;
+                }
+                if (isx) {
+                    gsx[r] = v;
+                    gsxd[r] = vd;
+                } else {
+                    gsy[r] = v;
+                    gsyd[r] = vd;
                 }
             }
-            Mp[p * Lp + x] = make_float2(e2[0], e2[1]);
-        }
-        __syncthreads();
-        float2 *other = (Mp == A) ? B : A;
-        float2 *Eh = fwd2d(Mp, other, g, np);
-        for (int idx = tid; idx < L * H; idx += blockDim.x) ehat_g[idx] = Eh[idx];
-        __syncthreads();
-        // adjoint images G_phi = IDFT(conj(Khat_phi) ehat) on [0,N)^2
-        float *gout = gbuf + fd.gbuf_off + (long long)i * nph * N * N;
-        for (int ph = 0; ph < nph; ++ph) {
-            for (int idx = tid; idx < L * H; idx += blockDim.x) A[idx] = cmulc(ehat_g[idx], kh[(long long)ph * L * H + idx]);
             __syncthreads();
-            float2 *Gp = inv2d(A, B, g, np);
-            for (int idx = tid; idx < np * L; idx += blockDim.x) {
-                const int p = idx / L, x = idx - p * L;
-                if (x >= N) continue;
-                const float2 v = Gp[p * Lp + x];
-                const int y = 2 * p;
-                gout[((long long)ph * N + y) * N + x] = v.x * scale;
-                if (y + 1 < N) gout[((long long)ph * N + y + 1) * N + x] = v.y * scale;
+            // forward model spectrum: sum_phi Khat_phi (Hhat_phi + sum_k a_k gx gy)
+            for (int ky = warp; ky < L; ky += nw) {
+                for (int kx = lane; kx < H; kx += 32) {
+                    const int idx = ky * H + kx;
+                    float2 m = make_float2(0.f, 0.f);
+                    for (int ph = 0; ph < nph; ++ph) {
+                        const int phy = ph / f, phx = ph - phy * f;
+                        float2 sp = hh[(long long)ph * LH + idx];
+                        for (int k = 0; k < M; ++k) {
+                            const float2 pr = cmul(gsx[(k * f + phx) * H + kx], gsy[(k * f + phy) * L + ky]);
+                            sp.x += apar[k] * pr.x;
+                            sp.y += apar[k] * pr.y;
+                        }
+                        m = cadd(m, cmul(__ldg(&kh[(long long)ph * LH + idx]), sp));
+                    }
+                    A[idx] = m;
+                }
             }
             __syncthreads();
-        }
-        block_sum2(chi, se, s_red);
-        if (tid == 0) {
-            chi_part[item.z] = chi;
-            se_part[item.z] = se;
+            float2 *Mp = inv2d(A, B, g, np);
+            // residual on [0,N)^2; the pairs become e (zero outside), ready for the forward transform
+            const float bg = (float)(f * f) * gam;
+            double chi = 0.0, se = 0.0;
+            const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
+            for (int p = warp; p < np; p += nw) {
+                float2 *row = Mp + p * Lp;
+                for (int x = lane; x < L; x += 32) {
+                    const float2 mv = row[x];
+                    float e2[2] = {0.f, 0.f};
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int y = 2 * p + q;
+                        if (y < N && x < N) {
+                            const float Mv = (q ? mv.y : mv.x) * scale + bg;
+                            const float res = __ldg(dd + y * N + x) - Mv;
+                            const float wv = __ldg(ww + y * N + x);
+                            chi += (double)(0.5f * wv * res * res);
+                            e2[q] = -wv * res;
+                            se += (double)e2[q];
+                        }
+                    }
+                    row[x] = make_float2(e2[0], e2[1]);
+                }
+            }
+            __syncthreads();
+            float2 *other = (Mp == A) ? B : A;
+            const float2 *Eh = fwd2d(Mp, other, g, np);
+            // adjoint spectra conj(Khat_phi) ehat: into the chunk accumulator, and Parseval
+            // products with the sources' spectra (weights 1 at kx = 0 and L/2, 2 elsewhere)
+            float pa[kFftMaxSources], px[kFftMaxSources], py[kFftMaxSources];
+#pragma unroll
+            for (int k = 0; k < kFftMaxSources; ++k) pa[k] = px[k] = py[k] = 0.f;
+            const bool first = i == item.y;
+            for (int ky = warp; ky < L; ky += nw) {
+                for (int kx = lane; kx < H; kx += 32) {
+                    const int idx = ky * H + kx;
+                    const float2 ev = Eh[idx];
+                    const float wgt = (kx == 0 || 2 * kx == L) ? 1.f : 2.f;
+                    for (int ph = 0; ph < nph; ++ph) {
+                        const int phy = ph / f, phx = ph - phy * f;
+                        const float2 G = cmulc(ev, __ldg(&kh[(long long)ph * LH + idx]));
+                        float2 *ap = acc + (long long)ph * LH + idx;
+                        *ap = first ? G : cadd(*ap, G);
+#pragma unroll
+                        for (int k = 0; k < kFftMaxSources; ++k) {
+                            if (k < M) {
+                                const float2 gx = gsx[(k * f + phx) * H + kx], gy = gsy[(k * f + phy) * L + ky];
+                                const float2 gxd = gsxd[(k * f + phx) * H + kx], gyd = gsyd[(k * f + phy) * L + ky];
+                                // Re(G conj(a b)) for the profile and its two shift derivatives
+                                const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
+                                pa[k] += wgt * (G.x * s0.x + G.y * s0.y);
+                                px[k] += wgt * (G.x * s1.x + G.y * s1.y);
+                                py[k] += wgt * (G.x * s2.x + G.y * s2.y);
+                            }
+                        }
+                    }
+                }
+            }
+            // block sums (fixed order): chi, se, and the 3 M source products
+            double v[2 + 3 * kFftMaxSources];
+            v[0] = chi;
+            v[1] = se;
+#pragma unroll
+            for (int k = 0; k < kFftMaxSources; ++k) {
+                v[2 + 3 * k] = pa[k];
+                v[3 + 3 * k] = px[k];
+                v[4 + 3 * k] = py[k];
+            }
+            const int nv = 2 + 3 * M;
+            for (int q = 0; q < nv; ++q) {
+                double x = v[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) s_red[q][warp] = x;
+            }
+            __syncthreads();
+            if (tid < nv) {
+                double sum = 0.0;
+                for (int q = 0; q < nw; ++q) sum += s_red[tid][q];
+                const long long slot = fd.tile_slot + i;
+                if (tid == 0) {
+                    chi_part[slot] = sum;
+                } else if (tid == 1) {
+                    se_part[slot] = sum;
+                } else {
+                    const int k = (tid - 2) / 3, which = (tid - 2) - 3 * k;
+                    const long long ps = fd.ps_slot + (long long)i * M + k;
+                    const float sc = (float)(sum / ((double)L * (double)L));
+                    if (which == 0) ps_da[ps] = sc;
+                    else ps_du[2 * ps + which - 1] = apar[k] * sc;
+                }
+            }
         }
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------------------------
-int fft_smem_bytes(int L, int M, int f) {
-    const int H = L / 2 + 1;
-    return (2 * L * H + L + M * f * (H + L)) * (int)sizeof(float2);
+// dL/dh for the fft fields: sum the chunk accumulators of the field in a fixed order, transform
+// back, and add the prior's gradient.  One block per (fft field, phi).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kFftThreads)
+fft_hgrad_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
+                 const float2 *__restrict__ acc_all, float *__restrict__ grad) {
+    extern __shared__ __align__(16) float2 fsm[];
+    const FieldDev &fd = fields[fft_fields[blockIdx.x]];
+    const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
+    const int ph = blockIdx.y;
+    if (ph >= nph) return;
+    const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1, LH = L * H;
+    float2 *A = fsm, *B = fsm + LH, *tw = fsm + 2 * LH;
+    FftGeom g;
+    load_geom(g, fd, tw);
+    const int n_chunks = fd.fft_n_chunks;
+    for (int idx = threadIdx.x; idx < LH; idx += blockDim.x) {
+        float2 s = make_float2(0.f, 0.f);
+        const float2 *ac = acc_all + fd.fft_acc_off + (long long)ph * LH + idx;
+        for (int c = 0; c < n_chunks; ++c) s = cadd(s, ac[(long long)c * nph * LH]);
+        A[idx] = s;
+    }
+    __syncthreads();
+    const int np = (N + 1) / 2;
+    const float2 *Gp = inv2d(A, B, g, np);
+    const float scale = 1.f / ((float)L * (float)L);
+    const int phy = ph / f, phx = ph - phy * f;
+    const float *T0 = fd.starlet + (long long)fd.J * F * F;
+    float *gh = grad + fd.param_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = warp; p < np; p += nw) {
+        for (int x = lane; x < N; x += 32) {
+            const float2 v = Gp[p * Lp + x];
+            const int y = 2 * p;
+            const long long u0 = (long long)(f * y + phy) * F + f * x + phx;
+            gh[u0] = v.x * scale + T0[u0];
+            if (y + 1 < N) {
+                const long long u1 = u0 + (long long)f * F;
+                gh[u1] = v.y * scale + T0[u1];
+            }
+        }
+    }
 }
 
-sr_status configure_fft_kernels(int smem) {
-    SR_CUDA(cudaFuncSetAttribute(fft_epoch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    SR_CUDA(cudaFuncSetAttribute(fft_hhat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    SR_CUDA(cudaFuncSetAttribute(fft_kappa_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+// ---------------------------------------------------------------------------------------------
+int fft_smem_bytes(int L, int M, int f) {
+    const int H = L / 2 + 1;
+    return (2 * L * H + L + 2 * M * f * (H + L)) * (int)sizeof(float2);
+}
+
+template <typename K>
+static sr_status set_dyn_smem(K kernel, int optin, int *limit) {
+    cudaFuncAttributes a;
+    SR_CUDA(cudaFuncGetAttributes(&a, kernel));
+    const int dyn = optin - (int)a.sharedSizeBytes;
+    SR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    *limit = std::min(*limit, dyn);
+    return SR_OK;
+}
+
+// Opens the largest dynamic shared memory each transform kernel can take (the opt-in limit
+// less its static shared memory) and returns the smallest of these in *limit.
+sr_status configure_fft_kernels(int optin, int *limit) {
+    *limit = optin;
+    sr_status s;
+    if ((s = set_dyn_smem(fft_chunk_kernel, optin, limit)) != SR_OK) return s;
+    if ((s = set_dyn_smem(fft_hhat_kernel, optin, limit)) != SR_OK) return s;
+    if ((s = set_dyn_smem(fft_kappa_kernel, optin, limit)) != SR_OK) return s;
+    if ((s = set_dyn_smem(fft_hgrad_kernel, optin, limit)) != SR_OK) return s;
     return SR_OK;
 }
 
 sr_status occupancy_fft_kernel(int smem, int *blocks) {
-    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fft_epoch_kernel, kThreads, smem));
+    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fft_chunk_kernel, kFftThreads, smem));
     return SR_OK;
 }
 
 void launch_fft_kappa(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st) {
     const int L = fd.fft_L;
     const int smem = fft_smem_bytes(L, 0, fd.f);
-    fft_kappa_kernel<<<fd.E * fd.f * fd.f, kThreads, smem, st>>>(fd, kappa, khat);
+    fft_kappa_kernel<<<fd.E * fd.f * fd.f, kFftThreads, smem, st>>>(fd, kappa, khat);
 }
 
 void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
                      const float *params, float2 *hhat, cudaStream_t st) {
-    fft_hhat_kernel<<<dim3(n_fft_fields, max_nph), kThreads, smem, st>>>(fields, fft_fields, params, hhat);
+    fft_hhat_kernel<<<dim3(n_fft_fields, max_nph), kFftThreads, smem, st>>>(fields, fft_fields, params, hhat);
 }
 
-void launch_fft_epochs(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
-                       const float2 *hhat, float2 *ehat_scratch, long long ehat_stride, float *gbuf, double *chi_part,
-                       double *se_part, int grid, int smem, cudaStream_t st) {
-    fft_epoch_kernel<<<grid, kThreads, smem, st>>>(fields, items, n_items, counter, params, hhat, ehat_scratch,
-                                                   ehat_stride, gbuf, chi_part, se_part);
+void launch_fft_chunks(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
+                       const float2 *hhat, float2 *acc, double *chi_part, double *se_part, float *ps_da, float *ps_du,
+                       int grid, int smem, cudaStream_t st) {
+    fft_chunk_kernel<<<grid, kFftThreads, smem, st>>>(fields, items, n_items, counter, params, hhat, acc, chi_part,
+                                                      se_part, ps_da, ps_du);
+}
+
+void launch_fft_hgrad(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
+                      const float2 *acc, float *grad, cudaStream_t st) {
+    fft_hgrad_kernel<<<dim3(n_fft_fields, max_nph), kFftThreads, smem, st>>>(fields, fft_fields, acc, grad);
 }
 
 }  // namespace sr

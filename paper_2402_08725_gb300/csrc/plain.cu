@@ -37,7 +37,8 @@ __global__ void plain_raster_kernel(const FieldDev *__restrict__ fields, const f
         const float cy = u0 + (float)f * (cpar[2 * k + 1] + dpar[1]);
         const int lx = (int)floorf(cx) - kWinLo, ly = (int)floorf(cy) - kWinLo;
         if (ux >= lx && ux < lx + kWin && uy >= ly && uy < ly + kWin) {
-            const float dx = (float)ux - cx, dy = (float)uy - cy;
+            const float dx = src_offset(ux, F, f, cpar[2 * k], dpar[0]);
+            const float dy = src_offset(uy, F, f, cpar[2 * k + 1], dpar[1]);
             v += apar[k] * (kGaussNorm * exp2f(-(dx * dx + dy * dy)));
         }
     }
@@ -166,7 +167,8 @@ __global__ void plain_psgrad_kernel(const FieldDev *__restrict__ fields, const f
     for (int idx = lane; idx < kWin * kWin; idx += 32) {
         const int uy = ly + idx / kWin, ux = lx + idx % kWin;
         if (uy < 0 || uy >= F || ux < 0 || ux >= F) continue;
-        const float dx = (float)ux - cx, dy = (float)uy - cy;
+        const float dx = src_offset(ux, F, f, cpar[2 * k], dpar[0]);
+        const float dy = src_offset(uy, F, f, cpar[2 * k + 1], dpar[1]);
         const float gg = gi[(long long)uy * F + ux] * (kGaussNorm * exp2f(-(dx * dx + dy * dy)));
         sa += gg;
         sx += gg * dx;

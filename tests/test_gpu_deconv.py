@@ -188,3 +188,86 @@ def test_gradient_blocks_layout_matches_library():
     blocks = deconv_blocks(fd.E, fd.N, fd.f, fd.M)
     assert [(s.start, s.stop - s.start) for s in blocks.values()] == lay
     prob.close()
+
+
+def test_config5_one_full_frame_matches_oracle():
+    """JWST-like frame at full size: 512x512 data, f = 3 (1536x1536 model grid), 255x255 PSF,
+    40 clumps, 6 starlet scales, one frame (the oracle evaluates it in about a minute)."""
+    fd = syn.config5(E=1)
+    loss, g = _run(fd)
+    r = check_deconv(fd, loss, g)
+    print("config5 frame", r)
+
+
+def test_config5_six_frames_add_up():
+    """All 6 frames in one evaluation (the benchmarked launch configuration): with the prior
+    off, the loss and the shared-parameter gradients are the sums over single-frame
+    evaluations — a property that holds at any size."""
+    fd = syn.config5()
+    fd.lam = 0.0
+    loss6, g6 = _run(fd)
+    h, a, c, dl, gm = syn.unpack_deconv(fd.params, fd.E, fd.N, fd.f, fd.M)
+    F = fd.F
+    tot, gh, gc = 0.0, np.zeros(F * F), np.zeros(2 * fd.M)
+    for i in range(fd.E):
+        one = syn.DeconvField(1, fd.N, fd.f, fd.K, fd.M, fd.J, 0.0, fd.d[i:i + 1], fd.sigma[i:i + 1],
+                              fd.s[i:i + 1], fd.W, syn.pack_deconv(h, a[i:i + 1], c, dl[i:i + 1], gm[i:i + 1]))
+        l1, g1 = _run(one)
+        tot += l1
+        gh += g1[:F * F]
+        gc += g1[F * F + fd.M:F * F + 3 * fd.M]
+    assert abs(loss6 - tot) <= 1e-9 * abs(tot)
+    from tests._helpers import rel_l2
+    assert rel_l2(g6[:F * F], gh) <= 1e-6
+    oc = F * F + fd.E * fd.M
+    assert rel_l2(g6[oc:oc + 2 * fd.M], gc) <= 1e-6
+
+
+def test_autotuner_resolves_auto_fields_and_caches(tmp_path, monkeypatch):
+    """AUTO fields whose shape fits both forms are timed once per shape; the choice is
+    reported per field and written to the SR_AUTOTUNE_CACHE file."""
+    import json
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("SR_AUTOTUNE_CACHE", str(cache))
+    fd = syn.small_deconv(seed=91, E=6, N=44, f=2, K=19, M=1, J=3, lam=1.0)
+    probs = [Problem.from_field(fd), Problem.from_field(fd, conv_mode="direct")]
+    batch = Batch(probs)
+    forms = batch.field_forms()
+    assert forms[0] in ("direct", "fft") and forms[1] == "direct"
+    data = json.loads(cache.read_text())
+    assert data["44,2,19,1"] == (1 if forms[0] == "fft" else 0)
+    P = torch.from_numpy(batch.pack([fd.params, fd.params])).cuda()
+    losses = torch.empty(2, dtype=torch.float64, device="cuda")
+    batch.loss_and_grad(P, losses=losses)
+    l = losses.cpu().numpy()
+    assert abs(l[0] - l[1]) <= 1e-6 * abs(l[1])
+    batch.close()
+    for p in probs:
+        p.close()
+
+
+def test_guard_bands_uneven_batch_both_forms(monkeypatch):
+    """With guard tails on every device buffer, an uneven batch mixing both forms, several
+    transform sizes and several epoch chunks per field writes nothing past any buffer, and
+    each field still equals its single-problem evaluation."""
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    monkeypatch.setenv("SR_GUARD", "1")
+    shapes = [(20, 32, "fft"), (9, 96, "fft"), (3, 48, "direct"), (17, 64, "fft"), (11, 128, "fft"),
+              (5, 40, "direct")]
+    fields = [syn.small_deconv(seed=300 + i, E=E, N=N, f=2, K=17, M=1, J=4, lam=1.0)
+              for i, (E, N, _) in enumerate(shapes)]
+    probs = [Problem.from_field(fd, conv_mode=m) for fd, (_, _, m) in zip(fields, shapes)]
+    batch = Batch(probs)
+    assert batch.field_forms() == [m for (_, _, m) in shapes]
+    P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
+    losses = torch.empty(len(fields), dtype=torch.float64, device="cuda")
+    total, grad = batch.loss_and_grad(P, losses=losses)
+    for i, (fd, pr) in enumerate(zip(fields, probs)):
+        l_i, g_i = pr.loss_and_grad(torch.from_numpy(fd.params).cuda())
+        o = batch.offsets[i]
+        assert losses[i].item() == l_i
+        assert torch.equal(grad[o:o + fd.n_params], g_i)
+    batch.close()
+    for pr in probs:
+        pr.close()
