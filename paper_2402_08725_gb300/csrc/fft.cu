@@ -190,6 +190,16 @@ __device__ float2 *inv2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
     return stockham(o, c, np, g.Lp, 1, g, true);
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (a hint; p and bytes multiples of 16, range inside
+// one allocation), issued in pieces of at most 64 KB.
+__device__ __forceinline__ void prefetch_l2(const void *p, long long bytes) {
+    const char *c = static_cast<const char *>(p);
+    for (long long off = 0; off < bytes; off += 65536) {
+        const unsigned n = (unsigned)((bytes - off) < 65536 ? (bytes - off) : 65536);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(n) : "memory");
+    }
+}
+
 __device__ __forceinline__ void load_geom(FftGeom &g, const FieldDev &fd, float2 *tw_smem) {
     g.L = fd.fft_L;
     g.H = fd.fft_L / 2 + 1;
@@ -317,6 +327,15 @@ fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ i
             const float *dpar = cpar + 2 * M + 2 * i;
             const float gam = cpar[2 * M + 2 * E + i];
             const float2 *kh = fd.fft_khat + (long long)i * nph * LH;
+            // the next epoch's kernel spectra, data and weights go to L2 while this one computes
+            // (all sizes are multiples of 16 bytes: L*H is even, and N*N*4 when N is even)
+            if (tid == 0 && i + 1 < item.z) {
+                prefetch_l2(kh + (long long)nph * LH, (long long)nph * LH * (long long)sizeof(float2));
+                if ((N & 1) == 0) {
+                    prefetch_l2(fd.d + (long long)(i + 1) * N * N, (long long)N * N * 4);
+                    prefetch_l2(fd.w + (long long)(i + 1) * N * N, (long long)N * N * 4);
+                }
+            }
             __syncthreads();
             // 1-D transforms of the window profiles g1(u - c) and g1(u - c) (u - c) / sigma^2
             const int nx = M * f * H, ny = M * f * L;
@@ -354,9 +373,9 @@ fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ i
             }
             __syncthreads();
             // forward model spectrum: sum_phi Khat_phi (Hhat_phi + sum_k a_k gx gy)
-            for (int ky = warp; ky < L; ky += nw) {
-                for (int kx = lane; kx < H; kx += 32) {
-                    const int idx = ky * H + kx;
+            for (int idx = tid; idx < LH; idx += blockDim.x) {
+                {
+                    const int ky = idx / H, kx = idx - ky * H;
                     float2 m = make_float2(0.f, 0.f);
                     for (int ph = 0; ph < nph; ++ph) {
                         const int phy = ph / f, phx = ph - phy * f;
@@ -406,9 +425,9 @@ fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ i
 #pragma unroll
             for (int k = 0; k < kFftMaxSources; ++k) pa[k] = px[k] = py[k] = 0.f;
             const bool first = i == item.y;
-            for (int ky = warp; ky < L; ky += nw) {
-                for (int kx = lane; kx < H; kx += 32) {
-                    const int idx = ky * H + kx;
+            for (int idx = tid; idx < LH; idx += blockDim.x) {
+                {
+                    const int ky = idx / H, kx = idx - ky * H;
                     const float2 ev = Eh[idx];
                     const float wgt = (kx == 0 || 2 * kx == L) ? 1.f : 2.f;
                     for (int ph = 0; ph < nph; ++ph) {
