@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--conv-mode", choices=["auto", "direct", "fft"], default="auto",
+                    help="convolution form of every field (auto: timed per shape on first use)")
     ap.add_argument("--fields", type=int, default=0,
                     help="config4 only: evaluate the first FIELDS fields (a smaller case for profiling)")
     return ap.parse_args()
@@ -298,7 +300,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     units = units_of(fields, pb)
     with torch.cuda.stream(stream):
-        probs = [Problem.from_field(fd, stream=stream) for fd in fields]
+        probs = [Problem.from_field(fd, conv_mode=args.conv_mode, stream=stream) for fd in fields]
         batch = Batch(probs, stream=stream) if probs else None
         psf = Problem.from_psf(pb, stream=stream) if pb is not None else None
         P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda() if batch else None
@@ -426,6 +428,7 @@ def run_ours(args):
             "config": {"workload": args.workload + (f" (first {args.fields} fields)" if args.fields else ""),
                        "description": WORKLOADS[args.workload],
                        "epoch_pixels_per_step": units, "fields": len(fields), "psf_stars": pb.S if pb else 0,
+                       "conv_mode": args.conv_mode,
                        "l2": "inputs larger than L2" if units * 12 > 129e6 else "inputs smaller than L2 (no flush)",
                        "generation_s": round(t_gen, 1)},
             "graph_ms_per_step": graph_ms,

@@ -33,10 +33,12 @@
 
 namespace sr {
 
+// Passed by value: the radices are packed 4 bits per stage so that nothing here is indexed at
+// run time (a runtime-indexed array would put the whole struct in local memory).
 struct FftGeom {
     int L, H, Lp;      // transform size, half-spectrum width L/2+1, pitch of the row-pair layout (L+1)
     int nst;
-    int rad[kFftMaxStages];
+    unsigned rad;      // radix of stage s in bits [4s, 4s+4)
     const float2 *tw;  // exp(-2 pi i n / L), n < L (shared memory)
 };
 
@@ -96,12 +98,12 @@ __device__ __forceinline__ void small_dft(float2 *v, int R, float s) {
 // ntr independent length-L transforms; element n of transform t at base + t*tstride + n*estride.
 // Returns the buffer that holds the result (src or dst).  Warps take butterflies, lanes take
 // transforms, so the twiddles of a butterfly are loaded once per warp.
-__device__ float2 *stockham(float2 *src, float2 *dst, int ntr, int tstride, int estride, const FftGeom &g, bool inv) {
+__device__ float2 *stockham(float2 *src, float2 *dst, int ntr, int tstride, int estride, const FftGeom g, bool inv) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const float s = inv ? 1.f : -1.f;
     int Ns = 1;
     for (int st = 0; st < g.nst; ++st) {
-        const int R = g.rad[st];
+        const int R = (int)((g.rad >> (4 * st)) & 15u);
         const int nb = g.L / R;
         const int step = g.L / (Ns * R);
         for (int j = warp; j < nb; j += nw) {
@@ -140,7 +142,7 @@ __device__ float2 *stockham(float2 *src, float2 *dst, int ntr, int tstride, int 
 
 // Forward real 2-D transform.  `in` holds np row pairs (row 2p in .x, row 2p+1 in .y), pitch
 // Lp; rows >= 2 np are zero.  Returns the buffer with the half spectrum (pitch H).
-__device__ float2 *fwd2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
+__device__ float2 *fwd2d(float2 *in, float2 *tmp, const FftGeom g, int np) {
     float2 *r = stockham(in, tmp, np, g.Lp, 1, g, false);
     float2 *o = (r == in) ? tmp : in;
     const int L = g.L, H = g.H;
@@ -166,7 +168,7 @@ __device__ float2 *fwd2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
 
 // Inverse real 2-D transform of the half spectrum in `in` (pitch H).  Returns the buffer with
 // np row pairs (pitch Lp) of the unscaled real image (multiply by 1/L^2).
-__device__ float2 *inv2d(float2 *in, float2 *tmp, const FftGeom &g, int np) {
+__device__ float2 *inv2d(float2 *in, float2 *tmp, const FftGeom g, int np) {
     float2 *c = stockham(in, tmp, g.H, 1, g.H, g, true);
     float2 *o = (c == in) ? tmp : in;
     const int L = g.L, H = g.H;
@@ -205,7 +207,9 @@ __device__ __forceinline__ void load_geom(FftGeom &g, const FieldDev &fd, float2
     g.H = fd.fft_L / 2 + 1;
     g.Lp = fd.fft_L + 1;
     g.nst = fd.fft_nst;
-    for (int s = 0; s < kFftMaxStages; ++s) g.rad[s] = fd.fft_rad[s];
+    g.rad = 0u;
+#pragma unroll
+    for (int s = 0; s < kFftMaxStages; ++s) g.rad |= (unsigned)(fd.fft_rad[s] & 15) << (4 * s);
     for (int n = threadIdx.x; n < g.L; n += blockDim.x) tw_smem[n] = fd.fft_tw[n];
     g.tw = tw_smem;
 }
@@ -394,10 +398,13 @@ fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ i
             float2 *Mp = inv2d(A, B, g, np);
             // residual on [0,N)^2; the pairs become e (zero outside), ready for the forward transform
             const float bg = (float)(f * f) * gam;
+            // per-thread partials in FP32 over one row pair (at most 2 ceil(L/32) terms), summed
+            // in FP64 across row pairs, lanes and warps
             double chi = 0.0, se = 0.0;
             const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
             for (int p = warp; p < np; p += nw) {
                 float2 *row = Mp + p * Lp;
+                float chi_r = 0.f, se_r = 0.f;
                 for (int x = lane; x < L; x += 32) {
                     const float2 mv = row[x];
                     float e2[2] = {0.f, 0.f};
@@ -408,13 +415,15 @@ fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ i
                             const float Mv = (q ? mv.y : mv.x) * scale + bg;
                             const float res = __ldg(dd + y * N + x) - Mv;
                             const float wv = __ldg(ww + y * N + x);
-                            chi += (double)(0.5f * wv * res * res);
+                            chi_r += 0.5f * wv * res * res;
                             e2[q] = -wv * res;
-                            se += (double)e2[q];
+                            se_r += e2[q];
                         }
                     }
                     row[x] = make_float2(e2[0], e2[1]);
                 }
+                chi += (double)chi_r;
+                se += (double)se_r;
             }
             __syncthreads();
             float2 *other = (Mp == A) ? B : A;
@@ -450,23 +459,37 @@ fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ i
                     }
                 }
             }
-            // block sums (fixed order): chi, se, and the 3 M source products
-            double v[2 + 3 * kFftMaxSources];
-            v[0] = chi;
-            v[1] = se;
+            // block sums (fixed order): chi and se in FP64; the 3 M source products as FP32 warp
+            // sums, then FP64 across warps
+            {
 #pragma unroll
-            for (int k = 0; k < kFftMaxSources; ++k) {
-                v[2 + 3 * k] = pa[k];
-                v[3 + 3 * k] = px[k];
-                v[4 + 3 * k] = py[k];
+                for (int o = 16; o > 0; o >>= 1) {
+                    chi += __shfl_down_sync(0xffffffffu, chi, o);
+                    se += __shfl_down_sync(0xffffffffu, se, o);
+                }
+                if (lane == 0) {
+                    s_red[0][warp] = chi;
+                    s_red[1][warp] = se;
+                }
+#pragma unroll
+                for (int k = 0; k < kFftMaxSources; ++k) {
+                    if (k < M) {
+                        float a = pa[k], bx = px[k], by = py[k];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            a += __shfl_down_sync(0xffffffffu, a, o);
+                            bx += __shfl_down_sync(0xffffffffu, bx, o);
+                            by += __shfl_down_sync(0xffffffffu, by, o);
+                        }
+                        if (lane == 0) {
+                            s_red[2 + 3 * k][warp] = (double)a;
+                            s_red[3 + 3 * k][warp] = (double)bx;
+                            s_red[4 + 3 * k][warp] = (double)by;
+                        }
+                    }
+                }
             }
             const int nv = 2 + 3 * M;
-            for (int q = 0; q < nv; ++q) {
-                double x = v[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                if (lane == 0) s_red[q][warp] = x;
-            }
             __syncthreads();
             if (tid < nv) {
                 double sum = 0.0;
