@@ -100,6 +100,7 @@ struct DevArena {
 static int g_smem_optin = -1;
 static int g_num_sms = 0;
 static int g_fft_smem_limit = 0;  // dynamic shared memory the transform kernels can take
+static int g_fx_smem_limit = 0;   // ... and the per-epoch chunk kernel
 
 static sr_status device_limits() {
     if (g_smem_optin >= 0) return SR_OK;
@@ -113,21 +114,18 @@ static sr_status device_limits() {
     if (s != SR_OK) return s;
     s = configure_fft_kernels(g_smem_optin, &g_fft_smem_limit);
     if (s != SR_OK) return s;
+    s = configure_fft_fixed(g_smem_optin, &g_fx_smem_limit);
+    if (s != SR_OK) return s;
     return SR_OK;
 }
 
-// Transform size for the frequency-domain form: the smallest even L >= N + max(tau_hi, -tau_lo)
-// whose prime factors are 2, 3 and 5, and its radix sequence (4s first, then 2, 3, 5).
+// Transform size for the frequency-domain form: the smallest listed L >= N + max(tau_hi, -tau_lo)
+// (the sizes the per-epoch chunk kernel is compiled for), and its radix sequence for the
+// runtime-size transforms of the per-field kernels (4s first, then 2, 3, 5).
 static bool fft_size(int N, int Tk, int tau_lo, int *L_out, int *nst, int *rad) {
     const int tau_hi = tau_lo + Tk - 1;
-    int L = N + std::max(tau_hi, -tau_lo);
-    for (;; ++L) {
-        if (L % 2) continue;
-        int m = L;
-        for (int q : {2, 3, 5})
-            while (m % q == 0) m /= q;
-        if (m == 1) break;
-    }
+    const int L = fft_fixed_next(N + std::max(tau_hi, -tau_lo));
+    if (L == 0) return false;
     int m = L, n = 0;
     while (m % 4 == 0 && n < kFftMaxStages) { rad[n++] = 4; m /= 4; }
     while (m % 2 == 0 && n < kFftMaxStages) { rad[n++] = 2; m /= 2; }
@@ -179,7 +177,7 @@ struct Plan {
     float *ebuf = nullptr, *gbuf = nullptr, *ps_da = nullptr, *ps_du = nullptr;
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
     // frequency-domain form
-    int n_fft_items = 0, n_fft_fields = 0, max_nph = 1, smem_fft = 0, grid_fft = 0;
+    int n_fft_items = 0, n_fft_fields = 0, max_nph = 1, smem_fft = 0, smem_fx = 0, grid_fft = 0;
     int4 *d_fft_items = nullptr;
     int *d_fft_fields = nullptr;
     float2 *hhat = nullptr, *fft_acc = nullptr;
@@ -427,7 +425,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     long long ebuf = 0, gbuf = 0, tslot = 0, psslot = 0, l1slot = 0;
     size_t poff = 0;
     int Jmax = 0;
-    int smem_fwd = 0, smem_adj = 0, smem_fft = 0;
+    int smem_fwd = 0, smem_adj = 0, smem_fft = 0, smem_fx = 0;
     std::vector<int4> fft_items;
     std::vector<int> fft_fields;
     long long hhat_len = 0, acc_len = 0;
@@ -478,7 +476,14 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             hhat_len += (long long)nph * L * H;
             fft_fields.push_back(i);
             pl->max_nph = std::max(pl->max_nph, nph);
-            smem_fft = std::max(smem_fft, fft_smem_bytes(L, fd.M, fd.f));
+            smem_fft = std::max(smem_fft, fft_smem_bytes(L, 0, fd.f));
+            // epochs side by side: the most (up to 4; only with at most one source) whose buffers fit
+            int G = fd.M <= 1 ? 4 : 1;
+            while (G > 1 && fft_fixed_smem_bytes(L, fd.N, fd.M, fd.f, G) > g_fx_smem_limit)
+                G >>= 1;
+            fd.fft_G = G;
+            fd.fft_EB = fft_fixed_epoch_buffer(L, fd.N);
+            smem_fx = std::max(smem_fx, fft_fixed_smem_bytes(L, fd.N, fd.M, fd.f, G));
         } else if (pl->kind == SR_DECONV && !plain) {
             gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
             const int nph = fd.f * fd.f;
@@ -593,11 +598,12 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     if (!chunks.empty()) SR_CUDA(cudaMemcpy(pl->d_chunks, chunks.data(), sizeof(ChunkItem) * chunks.size(), cudaMemcpyHostToDevice));
     SR_CUDA(cudaMemcpy(pl->d_group, groups.data(), groups.size(), cudaMemcpyHostToDevice));
     if (pl->n_fft_items > 0) {
-        if (smem_fft > g_fft_smem_limit)
-            return fail(SR_ERR_UNSUPPORTED, "transform form needs %d bytes of shared memory", smem_fft);
+        if (smem_fft > g_fft_smem_limit || smem_fx > g_fx_smem_limit)
+            return fail(SR_ERR_UNSUPPORTED, "transform form needs %d + %d bytes of shared memory", smem_fft, smem_fx);
         pl->smem_fft = smem_fft;
+        pl->smem_fx = smem_fx;
         int bfft = 0;
-        if ((st = occupancy_fft_kernel(smem_fft, &bfft)) != SR_OK) return st;
+        if ((st = occupancy_fft_fixed(smem_fx, &bfft)) != SR_OK) return st;
         pl->grid_fft = std::max(1, std::min(pl->n_fft_items, std::max(bfft, 1) * g_num_sms));
         if (opt.grid_limit > 0) pl->grid_fft = std::min(pl->grid_fft, opt.grid_limit);
         if ((st = A.alloc(&pl->d_fft_items, fft_items.size())) != SR_OK) return st;
@@ -665,8 +671,9 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
     if (pl->n_fft_items > 0) {
         launch_fft_hhat(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_nph, pl->smem_fft, params, pl->hhat,
                         st);
-        launch_fft_chunks(pl->d_fields, pl->d_fft_items, pl->n_fft_items, pl->d_counters + 2, params, pl->hhat,
-                          pl->fft_acc, pl->chi_part, pl->se_part, pl->ps_da, pl->ps_du, pl->grid_fft, pl->smem_fft, st);
+        launch_fft_chunks_fixed(pl->d_fields, pl->d_fft_items, pl->n_fft_items, pl->d_counters + 2, params, pl->hhat,
+                                pl->fft_acc, pl->chi_part, pl->se_part, pl->ps_da, pl->ps_du, pl->grid_fft, pl->smem_fx,
+                                st);
         n += 2;
     }
     if (ev) cudaEventRecord(ev[3], st);
@@ -913,7 +920,8 @@ sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_p
             if ((st = device_limits()) != SR_OK) return bail(st);
             int L = 0, nst = 0;
             const bool ok = d.n_sources <= kFftMaxSources && fft_size(d.data_n, p->Tk, p->tau_lo, &L, &nst, p->fft_rad) &&
-                            fft_smem_bytes(L, d.n_sources, d.supersampling) <= g_fft_smem_limit;
+                            fft_smem_bytes(L, 0, d.supersampling) <= g_fft_smem_limit &&
+                            fft_fixed_smem_bytes(L, d.data_n, d.n_sources, d.supersampling, 1) <= g_fx_smem_limit;
             if (!ok && d.conv_mode == SR_CONV_FFT)
                 return bail(fail(SR_ERR_UNSUPPORTED, "the transform form does not fit this size in shared memory"));
             if (ok) {

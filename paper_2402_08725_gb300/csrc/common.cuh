@@ -24,7 +24,7 @@ constexpr int kBlurHalf = 8;
 constexpr int kMaxScales = 8;
 constexpr int kFftMaxStages = 8;
 constexpr int kFftThreads = 512;
-constexpr int kFftMaxSources = 8;  // point sources per field in the frequency-domain form
+constexpr int kFftMaxSources = 4;  // point sources per field in the frequency-domain form
 constexpr int kThreads = 256;
 
 struct FieldDev {
@@ -57,6 +57,8 @@ struct FieldDev {
     long long fft_hhat_off;   // offset of the field's [f*f][L][L/2+1] h spectra in the plan buffer
     long long fft_acc_off;    // float2 offset of the field's chunk accumulators ([f*f][L][L/2+1] each)
     int fft_n_chunks;         // epoch chunks of the field
+    int fft_G;                // epochs transformed side by side by the chunk kernel (1, 2 or 4)
+    int fft_EB;               // float2 elements of each per-epoch transform buffer (fft_fixed.cu)
 };
 
 // One output tile of one epoch: rows [y0, y0+h), cols [x0, x0+w) of the data

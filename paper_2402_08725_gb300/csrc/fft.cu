@@ -18,8 +18,11 @@
 // identity, <G_{i,phi}, g> = L^-2 sum_k Ghat(k) conj(ghat(k)), with the separable spectra of the
 // window profile and of its shift derivatives.  Per epoch that is 2 real 2-D transforms.
 //
-// Transforms: Stockham auto-sort mixed-radix FFT (radices 4, 2, 3, 5), ping-ponging between two
-// shared-memory buffers, twiddles from a table exp(-2 pi i n / L).  A real L x L image is
+// This file holds the per-field and per-PSF kernels (Khat, Hhat, and the final dL/dh); the
+// per-epoch chunk kernel, where the time goes, is in fft_fixed.cu (compile-time sizes).
+//
+// Transforms here: Stockham auto-sort mixed-radix FFT (radices 4, 2, 3, 5), ping-ponging between
+// two shared-memory buffers, twiddles from a table exp(-2 pi i n / L).  A real L x L image is
 // transformed as L/2 complex rows (two real rows per complex row), split into the half spectrum
 // (L rows x L/2+1 columns), then L/2+1 complex column transforms; the inverse runs the same steps
 // backwards.  Rows that are known to be zero are skipped.
@@ -28,6 +31,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "cplx.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
 
@@ -41,16 +45,6 @@ struct FftGeom {
     unsigned rad;      // radix of stage s in bits [4s, 4s+4)
     const float2 *tw;  // exp(-2 pi i n / L), n < L (shared memory)
 };
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
 // y_q = sum_r v_r exp(-+ 2 pi i q r / R) for R in {2, 3, 4, 5}; s = -1 forward, +1 inverse.
 __device__ __forceinline__ void small_dft(float2 *v, int R, float s) {
@@ -192,16 +186,6 @@ __device__ float2 *inv2d(float2 *in, float2 *tmp, const FftGeom g, int np) {
     return stockham(o, c, np, g.Lp, 1, g, true);
 }
 
-// Bulk prefetch of [p, p + bytes) into L2 (a hint; p and bytes multiples of 16, range inside
-// one allocation), issued in pieces of at most 64 KB.
-__device__ __forceinline__ void prefetch_l2(const void *p, long long bytes) {
-    const char *c = static_cast<const char *>(p);
-    for (long long off = 0; off < bytes; off += 65536) {
-        const unsigned n = (unsigned)((bytes - off) < 65536 ? (bytes - off) : 65536);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(n) : "memory");
-    }
-}
-
 __device__ __forceinline__ void load_geom(FftGeom &g, const FieldDev &fd, float2 *tw_smem) {
     g.L = fd.fft_L;
     g.H = fd.fft_L / 2 + 1;
@@ -287,232 +271,6 @@ fft_hhat_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft
 }
 
 // ---------------------------------------------------------------------------------------------
-// A chunk of consecutive epochs of one field per item (x = field, y = first epoch, z = end,
-// w = chunk index within the field): for each epoch, the forward model, residual, chi^2, ehat, the
-// Parseval products of the point sources, and conj(Khat_phi) ehat added into the chunk's
-// accumulator acc[slot][phi][L][H].
-// ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFftThreads, 1)
-fft_chunk_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ items, int n_items,
-                 int *__restrict__ counter, const float *__restrict__ params, const float2 *__restrict__ hhat_all,
-                 float2 *__restrict__ acc_all, double *__restrict__ chi_part, double *__restrict__ se_part,
-                 float *__restrict__ ps_da, float *__restrict__ ps_du) {
-    extern __shared__ __align__(16) float2 fsm[];
-    __shared__ int s_item;
-    __shared__ double s_red[2 + 3 * kFftMaxSources][kFftThreads / 32];
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= n_items) break;
-        const int4 item = items[it];
-        const FieldDev &fd = fields[item.x];
-        const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E, nph = f * f;
-        const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1, LH = L * H;
-        float2 *A = fsm, *B = fsm + LH, *tw = fsm + 2 * LH;
-        // point-source 1-D spectra: [M][f] x-profiles and x-derivatives (H each), then y (L each)
-        float2 *gsx = tw + L;                // [M][f][H]
-        float2 *gsxd = gsx + M * f * H;      // [M][f][H]
-        float2 *gsy = gsxd + M * f * H;      // [M][f][L]
-        float2 *gsyd = gsy + M * f * L;      // [M][f][L]
-        FftGeom g;
-        load_geom(g, fd, tw);
-        const float *hpar = params + fd.param_off;
-        const float *cpar = hpar + (long long)F * F + (long long)E * M;
-        const float2 *hh = hhat_all + fd.fft_hhat_off;
-        float2 *acc = acc_all + fd.fft_acc_off + (long long)item.w * nph * LH;
-        const float u0 = 0.5f * (float)(F - 1);
-        const float scale = 1.f / ((float)L * (float)L);
-        const int np = (N + 1) / 2;
-        for (int i = item.y; i < item.z; ++i) {
-            const float *apar = hpar + (long long)F * F + (long long)i * M;
-            const float *dpar = cpar + 2 * M + 2 * i;
-            const float gam = cpar[2 * M + 2 * E + i];
-            const float2 *kh = fd.fft_khat + (long long)i * nph * LH;
-            // the next epoch's kernel spectra, data and weights go to L2 while this one computes
-            // (all sizes are multiples of 16 bytes: L*H is even, and N*N*4 when N is even)
-            if (tid == 0 && i + 1 < item.z) {
-                prefetch_l2(kh + (long long)nph * LH, (long long)nph * LH * (long long)sizeof(float2));
-                if ((N & 1) == 0) {
-                    prefetch_l2(fd.d + (long long)(i + 1) * N * N, (long long)N * N * 4);
-                    prefetch_l2(fd.w + (long long)(i + 1) * N * N, (long long)N * N * 4);
-                }
-            }
-            __syncthreads();
-            // 1-D transforms of the window profiles g1(u - c) and g1(u - c) (u - c) / sigma^2
-            const int nx = M * f * H, ny = M * f * L;
-            for (int idx = tid; idx < nx + ny; idx += blockDim.x) {
-                const bool isx = idx < nx;
-                const int r = isx ? idx : idx - nx;
-                const int len = isx ? H : L;
-                const int kf = r / len, kk = r - kf * len;
-                const int k = kf / f, phs = kf - k * f;
-                const float cc = u0 + (float)f * (cpar[2 * k + (isx ? 0 : 1)] + dpar[isx ? 0 : 1]);
-                const int lo = (int)floorf(cc) - kWinLo;
-                int m0 = lo - phs;
-                m0 = m0 >= 0 ? (m0 + f - 1) / f : -((-m0) / f);
-                float2 v = make_float2(0.f, 0.f), vd = make_float2(0.f, 0.f);
-                for (int m = m0;; ++m) {
-                    const int u = f * m + phs;
-                    if (u >= lo + kWin) break;
-                    if (u < 0 || u >= F) continue;
-                    const float t = src_offset(u, F, f, cpar[2 * k + (isx ? 0 : 1)], dpar[isx ? 0 : 1]);
-                    const float gv = kGauss1Norm * exp2f(-t * t);
-                    const float gd = gv * t * kGaussInvSig2;
-                    const float2 w = tw[(int)(((long long)kk * m) % L)];
-                    v.x += gv * w.x;
-                    v.y += gv * w.y;
-                    vd.x += gd * w.x;
-                    vd.y += gd * w.y;
-                }
-                if (isx) {
-                    gsx[r] = v;
-                    gsxd[r] = vd;
-                } else {
-                    gsy[r] = v;
-                    gsyd[r] = vd;
-                }
-            }
-            __syncthreads();
-            // forward model spectrum: sum_phi Khat_phi (Hhat_phi + sum_k a_k gx gy)
-            for (int idx = tid; idx < LH; idx += blockDim.x) {
-                {
-                    const int ky = idx / H, kx = idx - ky * H;
-                    float2 m = make_float2(0.f, 0.f);
-                    for (int ph = 0; ph < nph; ++ph) {
-                        const int phy = ph / f, phx = ph - phy * f;
-                        float2 sp = hh[(long long)ph * LH + idx];
-                        for (int k = 0; k < M; ++k) {
-                            const float2 pr = cmul(gsx[(k * f + phx) * H + kx], gsy[(k * f + phy) * L + ky]);
-                            sp.x += apar[k] * pr.x;
-                            sp.y += apar[k] * pr.y;
-                        }
-                        m = cadd(m, cmul(__ldg(&kh[(long long)ph * LH + idx]), sp));
-                    }
-                    A[idx] = m;
-                }
-            }
-            __syncthreads();
-            float2 *Mp = inv2d(A, B, g, np);
-            // residual on [0,N)^2; the pairs become e (zero outside), ready for the forward transform
-            const float bg = (float)(f * f) * gam;
-            // per-thread partials in FP32 over one row pair (at most 2 ceil(L/32) terms), summed
-            // in FP64 across row pairs, lanes and warps
-            double chi = 0.0, se = 0.0;
-            const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
-            for (int p = warp; p < np; p += nw) {
-                float2 *row = Mp + p * Lp;
-                float chi_r = 0.f, se_r = 0.f;
-                for (int x = lane; x < L; x += 32) {
-                    const float2 mv = row[x];
-                    float e2[2] = {0.f, 0.f};
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int y = 2 * p + q;
-                        if (y < N && x < N) {
-                            const float Mv = (q ? mv.y : mv.x) * scale + bg;
-                            const float res = __ldg(dd + y * N + x) - Mv;
-                            const float wv = __ldg(ww + y * N + x);
-                            chi_r += 0.5f * wv * res * res;
-                            e2[q] = -wv * res;
-                            se_r += e2[q];
-                        }
-                    }
-                    row[x] = make_float2(e2[0], e2[1]);
-                }
-                chi += (double)chi_r;
-                se += (double)se_r;
-            }
-            __syncthreads();
-            float2 *other = (Mp == A) ? B : A;
-            const float2 *Eh = fwd2d(Mp, other, g, np);
-            // adjoint spectra conj(Khat_phi) ehat: into the chunk accumulator, and Parseval
-            // products with the sources' spectra (weights 1 at kx = 0 and L/2, 2 elsewhere)
-            float pa[kFftMaxSources], px[kFftMaxSources], py[kFftMaxSources];
-#pragma unroll
-            for (int k = 0; k < kFftMaxSources; ++k) pa[k] = px[k] = py[k] = 0.f;
-            const bool first = i == item.y;
-            for (int idx = tid; idx < LH; idx += blockDim.x) {
-                {
-                    const int ky = idx / H, kx = idx - ky * H;
-                    const float2 ev = Eh[idx];
-                    const float wgt = (kx == 0 || 2 * kx == L) ? 1.f : 2.f;
-                    for (int ph = 0; ph < nph; ++ph) {
-                        const int phy = ph / f, phx = ph - phy * f;
-                        const float2 G = cmulc(ev, __ldg(&kh[(long long)ph * LH + idx]));
-                        float2 *ap = acc + (long long)ph * LH + idx;
-                        *ap = first ? G : cadd(*ap, G);
-#pragma unroll
-                        for (int k = 0; k < kFftMaxSources; ++k) {
-                            if (k < M) {
-                                const float2 gx = gsx[(k * f + phx) * H + kx], gy = gsy[(k * f + phy) * L + ky];
-                                const float2 gxd = gsxd[(k * f + phx) * H + kx], gyd = gsyd[(k * f + phy) * L + ky];
-                                // Re(G conj(a b)) for the profile and its two shift derivatives
-                                const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
-                                pa[k] += wgt * (G.x * s0.x + G.y * s0.y);
-                                px[k] += wgt * (G.x * s1.x + G.y * s1.y);
-                                py[k] += wgt * (G.x * s2.x + G.y * s2.y);
-                            }
-                        }
-                    }
-                }
-            }
-            // block sums (fixed order): chi and se in FP64; the 3 M source products as FP32 warp
-            // sums, then FP64 across warps
-            {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    chi += __shfl_down_sync(0xffffffffu, chi, o);
-                    se += __shfl_down_sync(0xffffffffu, se, o);
-                }
-                if (lane == 0) {
-                    s_red[0][warp] = chi;
-                    s_red[1][warp] = se;
-                }
-#pragma unroll
-                for (int k = 0; k < kFftMaxSources; ++k) {
-                    if (k < M) {
-                        float a = pa[k], bx = px[k], by = py[k];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            a += __shfl_down_sync(0xffffffffu, a, o);
-                            bx += __shfl_down_sync(0xffffffffu, bx, o);
-                            by += __shfl_down_sync(0xffffffffu, by, o);
-                        }
-                        if (lane == 0) {
-                            s_red[2 + 3 * k][warp] = (double)a;
-                            s_red[3 + 3 * k][warp] = (double)bx;
-                            s_red[4 + 3 * k][warp] = (double)by;
-                        }
-                    }
-                }
-            }
-            const int nv = 2 + 3 * M;
-            __syncthreads();
-            if (tid < nv) {
-                double sum = 0.0;
-                for (int q = 0; q < nw; ++q) sum += s_red[tid][q];
-                const long long slot = fd.tile_slot + i;
-                if (tid == 0) {
-                    chi_part[slot] = sum;
-                } else if (tid == 1) {
-                    se_part[slot] = sum;
-                } else {
-                    const int k = (tid - 2) / 3, which = (tid - 2) - 3 * k;
-                    const long long ps = fd.ps_slot + (long long)i * M + k;
-                    const float sc = (float)(sum / ((double)L * (double)L));
-                    if (which == 0) ps_da[ps] = sc;
-                    else ps_du[2 * ps + which - 1] = apar[k] * sc;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
 // dL/dh for the fft fields: sum the chunk accumulators of the field in a fixed order, transform
 // back, and add the prior's gradient.  One block per (fft field, phi).
 // ---------------------------------------------------------------------------------------------
@@ -578,15 +336,9 @@ static sr_status set_dyn_smem(K kernel, int optin, int *limit) {
 sr_status configure_fft_kernels(int optin, int *limit) {
     *limit = optin;
     sr_status s;
-    if ((s = set_dyn_smem(fft_chunk_kernel, optin, limit)) != SR_OK) return s;
     if ((s = set_dyn_smem(fft_hhat_kernel, optin, limit)) != SR_OK) return s;
     if ((s = set_dyn_smem(fft_kappa_kernel, optin, limit)) != SR_OK) return s;
     if ((s = set_dyn_smem(fft_hgrad_kernel, optin, limit)) != SR_OK) return s;
-    return SR_OK;
-}
-
-sr_status occupancy_fft_kernel(int smem, int *blocks) {
-    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fft_chunk_kernel, kFftThreads, smem));
     return SR_OK;
 }
 
@@ -599,13 +351,6 @@ void launch_fft_kappa(const FieldDev &fd, const float *kappa, float2 *khat, cuda
 void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
                      const float *params, float2 *hhat, cudaStream_t st) {
     fft_hhat_kernel<<<dim3(n_fft_fields, max_nph), kFftThreads, smem, st>>>(fields, fft_fields, params, hhat);
-}
-
-void launch_fft_chunks(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
-                       const float2 *hhat, float2 *acc, double *chi_part, double *se_part, float *ps_da, float *ps_du,
-                       int grid, int smem, cudaStream_t st) {
-    fft_chunk_kernel<<<grid, kFftThreads, smem, st>>>(fields, items, n_items, counter, params, hhat, acc, chi_part,
-                                                      se_part, ps_da, ps_du);
 }
 
 void launch_fft_hgrad(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,

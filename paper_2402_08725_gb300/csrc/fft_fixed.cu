@@ -1,0 +1,743 @@
+// Frequency-domain chunk kernel for transform sizes known at compile time (sm_103a).
+//
+// Computes per epoch exactly what the frequency-domain form defines (fft.cu): the model spectrum
+// sum_phi Khat_phi (Hhat_phi + Phat_phi), its inverse real transform, the weighted residual and
+// chi^2, the forward transform of e, the adjoint spectra conj(Khat_phi) ehat accumulated per chunk,
+// and the point sources' Parseval products.  What differs is how the transforms run:
+//
+//  * L = R1 R2 is a template parameter taken from a fixed list (multiples of 4, 16..144).  A
+//    length-L transform is two passes of in-register DFTs: R2 threads per transform each take
+//    an R1-point DFT of the elements n2 + R2 n1 and multiply by W_L^(n2 k1); then R1 threads
+//    each take an R2-point DFT of the results k1 and write X[k1 + R1 k2].  A real L x L image
+//    is transformed as row pairs (two real rows in one complex row), split into the half
+//    spectrum, then columns, so one 2-D transform is four passes with a barrier after each.
+//  * G epochs of a chunk run side by side (G = 1, 2 or 4, chosen on the host so that their
+//    buffers fit in shared memory; G > 1 only for fields with at most one point source): small
+//    transforms fill the block, and the chunk accumulator is read and written once per group
+//    instead of once per epoch.
+//  * the spectral loops take 4 (point, epoch) pairs per thread per batch, so that their global
+//    loads (kernel spectra, h spectra, accumulator) are in flight together.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "cplx.cuh"
+#include "kernels.cuh"
+
+namespace sr {
+namespace {
+
+// --- in-register DFTs -----------------------------------------------------------------------
+// W_R^m = exp(-2 pi i m / R), m < R, for the composite sizes 6, 8, 9, 10, 12, 16.
+constexpr int kDtwTotal = 61;
+__constant__ float2 c_dtw[kDtwTotal];
+__host__ __device__ constexpr int dtw_off(int R) { return R == 6 ? 0 : R == 8 ? 6 : R == 9 ? 14 : R == 10 ? 23 : R == 12 ? 33 : 45; }
+
+// v * W_R^m (forward) or v * W_R^-m (inverse), exact for multiples of a quarter turn.
+template <int R, bool INV>
+__device__ __forceinline__ float2 twiddle(float2 v, int m) {
+    if (m == 0) return v;
+    if ((4 * m) % R == 0) {
+        const int q = (4 * m) / R;  // W^m = (-i)^q
+        if (q == 2) return make_float2(-v.x, -v.y);
+        const bool minus_i = (q == 1) != INV;
+        return minus_i ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);
+    }
+    const float2 w = c_dtw[dtw_off(R) + m];
+    return INV ? cmulc(v, w) : cmul(v, w);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2 *v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2 *v) {
+    const float s1 = INV ? 0.866025403784438647f : -0.866025403784438647f;  // sin(-+2 pi / 3)
+    const float2 a = v[0], t = cadd(v[1], v[2]), u = csub(v[1], v[2]);
+    v[0] = cadd(a, t);
+    const float2 m = make_float2(a.x - 0.5f * t.x, a.y - 0.5f * t.y);
+    const float2 n = make_float2(-s1 * u.y, s1 * u.x);  // i s1 u
+    v[1] = cadd(m, n);
+    v[2] = csub(m, n);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 *v) {
+    const float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    const float2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    const float2 di = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);  // +-i d
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = cadd(b, di);
+    v[3] = csub(b, di);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft5(float2 *v) {
+    const float c1 = 0.309016994374947424f, c2 = -0.809016994374947424f;  // cos 2pi/5, cos 4pi/5
+    const float s1 = INV ? 0.951056516295153572f : -0.951056516295153572f;  // sin(-+2pi/5)
+    const float s2 = INV ? 0.587785252292473129f : -0.587785252292473129f;  // sin(-+4pi/5)
+    const float2 a = v[0];
+    const float2 t1 = cadd(v[1], v[4]), u1 = csub(v[1], v[4]);
+    const float2 t2 = cadd(v[2], v[3]), u2 = csub(v[2], v[3]);
+    v[0] = make_float2(a.x + t1.x + t2.x, a.y + t1.y + t2.y);
+    const float2 m1 = make_float2(a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y);
+    const float2 m2 = make_float2(a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y);
+    const float2 n1 = make_float2(-(s1 * u1.y + s2 * u2.y), s1 * u1.x + s2 * u2.x);
+    const float2 n2 = make_float2(-(s2 * u1.y - s1 * u2.y), s2 * u1.x - s1 * u2.x);
+    v[1] = cadd(m1, n1);
+    v[4] = csub(m1, n1);
+    v[2] = cadd(m2, n2);
+    v[3] = csub(m2, n2);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 *v);
+
+// R = P Q: P-point DFTs of v[Q n1 + n2] over n1, twiddles W_R^(n2 k1), Q-point DFTs over n2;
+// X[k1 + P k2] lands in v.
+template <int P, int Q, bool INV>
+__device__ __forceinline__ void dft_pq(float2 *v) {
+    constexpr int R = P * Q;
+    float2 a[R];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+        float2 t[P];
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) t[n1] = v[Q * n1 + n2];
+        dft<P, INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) a[k1 * Q + n2] = twiddle<R, INV>(t[k1], n2 * k1);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+        float2 t[Q];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) t[n2] = a[k1 * Q + n2];
+        dft<Q, INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = t[k2];
+    }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 *v) {
+    if constexpr (R == 2) dft2<INV>(v);
+    else if constexpr (R == 3) dft3<INV>(v);
+    else if constexpr (R == 4) dft4<INV>(v);
+    else if constexpr (R == 5) dft5<INV>(v);
+    else if constexpr (R == 6) dft_pq<2, 3, INV>(v);
+    else if constexpr (R == 8) dft_pq<2, 4, INV>(v);
+    else if constexpr (R == 9) dft_pq<3, 3, INV>(v);
+    else if constexpr (R == 10) dft_pq<2, 5, INV>(v);
+    else if constexpr (R == 12) dft_pq<4, 3, INV>(v);
+    else if constexpr (R == 16) dft_pq<4, 4, INV>(v);
+    else static_assert(R == 2, "unsupported in-register DFT size");
+}
+
+// --- transform geometry -----------------------------------------------------------------------
+__host__ __device__ constexpr int fx_r1(int L) {
+    return L == 16 ? 4 : L == 20 ? 5 : L == 24 ? 6 : L == 32 ? 8 : L == 36 ? 6 : L == 40 ? 8 : L == 48 ? 8
+         : L == 60 ? 10 : L == 64 ? 8 : L == 72 ? 9 : L == 80 ? 10 : L == 96 ? 12 : L == 100 ? 10
+         : L == 108 ? 12 : L == 120 ? 12 : L == 128 ? 16 : L == 144 ? 12 : 0;
+}
+
+// Buffer layouts (float2 units), per epoch, each of the two buffers:
+//   row pairs       p * PX + x                 (p < np, x < L)
+//   row pass 1 out  p * PY + k1 * S + n2       (S odd: the R2-point loads of pass 2 are conflict-free)
+//   half spectrum   ky * H + kx                (H = L/2 + 1, odd since L % 4 == 0)
+template <int L>
+struct Fx {
+    static constexpr int R1 = fx_r1(L), R2 = L / R1, H = L / 2 + 1, LH = L * H;
+    static constexpr int S = (R2 & 1) ? R2 : R2 + 1, PX = L, PY = R1 * S;
+    static_assert(R1 > 0 && R1 * R2 == L && L % 4 == 0, "transform size not in the list");
+};
+
+// floor(r / d) for 0 <= r < 1024 d and d <= 1024: (r + 0.5) / d is at least 0.5 / d away from an
+// integer, far more than the rounding error of the float product.
+__device__ __forceinline__ int fdivq(int r, float inv_d) { return __float2int_rd(((float)r + 0.5f) * inv_d); }
+
+// Forward real 2-D transform of G epochs.  A[g]: np row pairs (pitch PX), columns >= N read as
+// zero; result: the half spectrum in A[g] (pitch H).  TWL[k1 R2 + n2] = W_L^(n2 k1).
+template <int L>
+__device__ void fx_fwd2d(float2 *A, float2 *B, int EB, int G, int np, float inv_np, int N, const float2 *TWL) {
+    using P = Fx<L>;
+    constexpr int R1 = P::R1, R2 = P::R2, H = P::H, S = P::S, PX = P::PX, PY = P::PY;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < G * np * R2; t += nt) {  // rows, pass 1
+        const int n2 = t % R2, r = t / R2;
+        const int g = fdivq(r, inv_np), p = r - g * np;
+        const float2 *src = A + g * EB + p * PX;
+        float2 v[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            const int x = R2 * n1 + n2;
+            v[n1] = x < N ? src[x] : make_float2(0.f, 0.f);
+        }
+        dft<R1, false>(v);
+        float2 *dst = B + g * EB + p * PY + n2;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * S] = k1 == 0 ? v[0] : cmul(v[k1], TWL[k1 * R2 + n2]);
+    }
+    __syncthreads();
+    for (int t = tid; t < G * np * R1; t += nt) {  // rows, pass 2
+        const int k1 = t % R1, r = t / R1;
+        const int g = fdivq(r, inv_np), p = r - g * np;
+        const float2 *src = B + g * EB + p * PY + k1 * S;
+        float2 v[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2];
+        dft<R2, false>(v);
+        float2 *dst = A + g * EB + p * PX + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) dst[R1 * k2] = v[k2];
+    }
+    __syncthreads();
+    for (int t = tid; t < G * H * R2; t += nt) {  // split into row spectra, columns pass 1
+        const int kx = t % H, r = t / H;
+        const int n2 = r % R2, g = r / R2;
+        const float2 *src = A + g * EB;
+        const int kxm = kx == 0 ? 0 : L - kx;
+        float2 v[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            const int y = R2 * n1 + n2;
+            float2 o = make_float2(0.f, 0.f);
+            if (y < 2 * np) {
+                const float2 *row = src + (y >> 1) * PX;
+                const float2 a = row[kx], b = conjf2(row[kxm]);
+                o = (y & 1) ? make_float2(0.5f * (a.y - b.y), -0.5f * (a.x - b.x))   // (a - b) / (2i)
+                            : make_float2(0.5f * (a.x + b.x), 0.5f * (a.y + b.y));   // (a + b) / 2
+            }
+            v[n1] = o;
+        }
+        dft<R1, false>(v);
+        float2 *dst = B + g * EB + n2 * H + kx;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * R2 * H] = k1 == 0 ? v[0] : cmul(v[k1], TWL[k1 * R2 + n2]);
+    }
+    __syncthreads();
+    for (int t = tid; t < G * H * R1; t += nt) {  // columns, pass 2
+        const int kx = t % H, r = t / H;
+        const int k1 = r % R1, g = r / R1;
+        const float2 *src = B + g * EB + k1 * R2 * H + kx;
+        float2 v[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2 * H];
+        dft<R2, false>(v);
+        float2 *dst = A + g * EB + k1 * H + kx;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) dst[R1 * k2 * H] = v[k2];
+    }
+    __syncthreads();
+}
+
+// Inverse real 2-D transform of G epochs: the half spectrum in A[g] (pitch H) becomes np row
+// pairs of the unscaled image (times L^2) in A[g] (pitch PX), columns < N written.
+template <int L>
+__device__ void fx_inv2d(float2 *A, float2 *B, int EB, int G, int np, float inv_np, int N, const float2 *TWL) {
+    using P = Fx<L>;
+    constexpr int R1 = P::R1, R2 = P::R2, H = P::H, S = P::S, PX = P::PX, PY = P::PY;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < G * H * R2; t += nt) {  // columns, pass 1
+        const int kx = t % H, r = t / H;
+        const int n2 = r % R2, g = r / R2;
+        const float2 *src = A + g * EB + n2 * H + kx;
+        float2 v[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[n1 * R2 * H];
+        dft<R1, true>(v);
+        float2 *dst = B + g * EB + n2 * H + kx;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * R2 * H] = k1 == 0 ? v[0] : cmulc(v[k1], TWL[k1 * R2 + n2]);
+    }
+    __syncthreads();
+    for (int t = tid; t < G * H * R1; t += nt) {  // columns, pass 2: rows y < 2 np only
+        const int kx = t % H, r = t / H;
+        const int k1 = r % R1, g = r / R1;
+        const float2 *src = B + g * EB + k1 * R2 * H + kx;
+        float2 v[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2 * H];
+        dft<R2, true>(v);
+        float2 *dst = A + g * EB + k1 * H + kx;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+            if (k1 + R1 * k2 < 2 * np) dst[R1 * k2 * H] = v[k2];
+    }
+    __syncthreads();
+    for (int t = tid; t < G * np * R2; t += nt) {  // merge rows 2p, 2p+1; rows pass 1
+        const int n2 = t % R2, r = t / R2;
+        const int g = fdivq(r, inv_np), p = r - g * np;
+        const float2 *r1 = A + g * EB + (2 * p) * H, *r2 = r1 + H;
+        float2 v[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            const int x = R2 * n1 + n2;
+            if (x < H) {
+                const float2 a = r1[x], b = r2[x];
+                v[n1] = make_float2(a.x - b.y, a.y + b.x);   // a + i b
+            } else {
+                const float2 a = r1[L - x], b = r2[L - x];
+                v[n1] = make_float2(a.x + b.y, -a.y + b.x);  // conj(a) + i conj(b)
+            }
+        }
+        dft<R1, true>(v);
+        float2 *dst = B + g * EB + p * PY + n2;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * S] = k1 == 0 ? v[0] : cmulc(v[k1], TWL[k1 * R2 + n2]);
+    }
+    __syncthreads();
+    for (int t = tid; t < G * np * R1; t += nt) {  // rows, pass 2: columns x < N only
+        const int k1 = t % R1, r = t / R1;
+        const int g = fdivq(r, inv_np), p = r - g * np;
+        const float2 *src = B + g * EB + p * PY + k1 * S;
+        float2 v[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2];
+        dft<R2, true>(v);
+        float2 *dst = A + g * EB + p * PX + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+            if (k1 + R1 * k2 < N) dst[R1 * k2] = v[k2];
+    }
+    __syncthreads();
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (a hint; p and bytes multiples of 16, range inside
+// one allocation), issued in pieces of at most 64 KB.
+__device__ __forceinline__ void prefetch_l2(const void *p, long long bytes) {
+    const char *c = static_cast<const char *>(p);
+    for (long long off = 0; off < bytes; off += 65536) {
+        const unsigned n = (unsigned)((bytes - off) < 65536 ? (bytes - off) : 65536);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(n) : "memory");
+    }
+}
+
+constexpr int kBatch = 4;  // (spectral point, epoch) pairs per thread per batch of loads
+constexpr int kMaxG = 4;   // epochs per group (<= kBatch: a batch holds every epoch of its points)
+// reduced values per group: G (2 + 3 M) with G > 1 only when M <= 1
+constexpr int kRedVals = (kMaxG * 5 > 2 + 3 * kFftMaxSources) ? kMaxG * 5 : 2 + 3 * kFftMaxSources;
+static_assert(kMaxG <= kBatch && kFftMaxSources <= kBatch, "accumulators are indexed by batch element");
+
+struct FxShared {
+    double red[kRedVals][kFftThreads / 32];
+    float apar[kFftMaxSources];
+    int item;
+};
+
+// One item (x = field, y = first epoch, z = end, w = chunk index within the field), in groups
+// of G epochs.  Not inlined: each size is register-allocated on its own (one call per item).
+template <int L>
+__device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 item, const float *__restrict__ params,
+                                 const float2 *__restrict__ hhat_all, float2 *__restrict__ acc_all,
+                                 double *__restrict__ chi_part, double *__restrict__ se_part,
+                                 float *__restrict__ ps_da, float *__restrict__ ps_du, float2 *fsm, FxShared &sh) {
+    using P = Fx<L>;
+    constexpr int H = P::H, LH = P::LH, R2 = P::R2;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E, nph = f * f;
+    const int G = fd.fft_G, lgG = G == 4 ? 2 : G == 2 ? 1 : 0;
+    const int EB = fd.fft_EB;
+    const int np = (N + 1) / 2;
+    const float inv_np = 1.f / (float)np;
+    float2 *A = fsm, *B = fsm + G * EB, *TWL = B + G * EB, *tw = TWL + L;
+    // point-source 1-D spectra per epoch of the group: [G][M][f][H] x-profiles, x-derivatives,
+    // then [G][M][f][L] y-profiles, y-derivatives
+    const int MfH = M * f * H, MfL = M * f * L;
+    float2 *gsx = tw + L, *gsxd = gsx + G * MfH, *gsy = gsxd + G * MfH, *gsyd = gsy + G * MfL;
+    for (int n = tid; n < L; n += nt) {
+        tw[n] = fd.fft_tw[n];
+        TWL[n] = fd.fft_tw[(n % R2) * (n / R2)];
+    }
+    __syncthreads();
+    const float *hpar = params + fd.param_off;
+    const float *cpar = hpar + (long long)F * F + (long long)E * M;
+    const float2 *hh = hhat_all + fd.fft_hhat_off;
+    float2 *acc = acc_all + fd.fft_acc_off + (long long)item.w * nph * LH;
+    const float u0 = 0.5f * (float)(F - 1);
+    const float scale = 1.f / ((float)L * (float)L);
+    const int nsub = nw >> lgG;  // warps per epoch in the residual
+    const int nv = 2 + 3 * M;    // reduced values per epoch
+    for (int i0 = item.y; i0 < item.z; i0 += G) {
+        const int Ge = min(G, item.z - i0);
+        const float2 *kh = fd.fft_khat + (long long)i0 * nph * LH;  // [g][phi][LH]
+        if (tid < Ge * M) sh.apar[tid] = hpar[(long long)F * F + (long long)i0 * M + tid];
+        // the next group's kernel spectra, data and weights go to L2 while this one computes
+        // (sizes are multiples of 16 bytes: L*H is even, and N*N*4 when N is even)
+        if (tid == 0 && i0 + G < item.z) {
+            const int Gn = min(G, item.z - i0 - G);
+            prefetch_l2(kh + (long long)G * nph * LH, (long long)Gn * nph * LH * (long long)sizeof(float2));
+            if ((N & 1) == 0) {
+                prefetch_l2(fd.d + (long long)(i0 + G) * N * N, (long long)Gn * N * N * 4);
+                prefetch_l2(fd.w + (long long)(i0 + G) * N * N, (long long)Gn * N * N * 4);
+            }
+        }
+        // 1-D transforms of the window profiles g1(u - c) and g1(u - c) (u - c) / sigma^2
+        {
+            const int nx = MfH, ny = MfL, per = nx + ny;
+            for (int idx = tid; idx < Ge * per; idx += nt) {
+                const int g = idx / per, rr = idx - g * per;
+                const bool isx = rr < nx;
+                const int r = isx ? rr : rr - nx;
+                const int len = isx ? H : L;
+                const int kf = r / len, kk = r - kf * len;
+                const int k = kf / f, phs = kf - k * f;
+                const float *dpar = cpar + 2 * M + 2 * (i0 + g);
+                const float cpos = cpar[2 * k + (isx ? 0 : 1)], dl = dpar[isx ? 0 : 1];
+                const float cc = u0 + (float)f * (cpos + dl);
+                const int lo = (int)floorf(cc) - kWinLo;
+                int m0 = lo - phs;
+                m0 = m0 >= 0 ? (m0 + f - 1) / f : -((-m0) / f);
+                float2 v = make_float2(0.f, 0.f), vd = make_float2(0.f, 0.f);
+                for (int m = m0;; ++m) {
+                    const int u = f * m + phs;
+                    if (u >= lo + kWin) break;
+                    if (u < 0 || u >= F) continue;
+                    const float t = src_offset(u, F, f, cpos, dl);
+                    const float gv = kGauss1Norm * exp2f(-t * t);
+                    const float gd = gv * t * kGaussInvSig2;
+                    const float2 w = tw[(int)(((long long)kk * m) % L)];
+                    v.x += gv * w.x;
+                    v.y += gv * w.y;
+                    vd.x += gd * w.x;
+                    vd.y += gd * w.y;
+                }
+                if (isx) {
+                    gsx[g * MfH + r] = v;
+                    gsxd[g * MfH + r] = vd;
+                } else {
+                    gsy[g * MfL + r] = v;
+                    gsyd[g * MfL + r] = vd;
+                }
+            }
+        }
+        __syncthreads();
+        // model spectra: sum_phi Khat_{g,phi} (Hhat_phi + sum_k a_{g,k} gx gy); batch element
+        // j takes epoch j mod G of spectral point base + (j / G) nt
+        for (int base = tid; base < LH; base += (kBatch >> lgG) * nt) {
+            float2 m[kBatch];
+#pragma unroll
+            for (int j = 0; j < kBatch; ++j) m[j] = make_float2(0.f, 0.f);
+            for (int ph = 0; ph < nph; ++ph) {
+                const int phy = ph / f, phx = ph - phy * f;
+                float2 kv[kBatch], sv[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
+                    const bool ok = idx < LH && g < Ge;
+                    kv[j] = ok ? __ldg(&kh[((long long)g * nph + ph) * LH + idx]) : make_float2(0.f, 0.f);
+                    sv[j] = ok ? __ldg(&hh[(long long)ph * LH + idx]) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
+                    if (idx < LH && g < Ge) {
+                        const int ky = idx / H, kx = idx - ky * H;
+                        for (int k = 0; k < M; ++k) {
+                            const float2 pr = cmul(gsx[g * MfH + (k * f + phx) * H + kx],
+                                                   gsy[g * MfL + (k * f + phy) * L + ky]);
+                            const float a = sh.apar[g * M + k];
+                            sv[j].x += a * pr.x;
+                            sv[j].y += a * pr.y;
+                        }
+                    }
+                    m[j] = cadd(m[j], cmul(kv[j], sv[j]));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kBatch; ++j) {
+                const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
+                if (idx < LH && g < Ge) A[g * EB + idx] = m[j];
+            }
+        }
+        __syncthreads();
+        fx_inv2d<L>(A, B, EB, Ge, np, inv_np, N, TWL);
+        // residual on [0,N)^2 in place (e for the forward transform), chi^2 and sum e: the warps
+        // w with w mod G = g take the row pairs of epoch g
+        {
+            const int g = warp & (G - 1), sub = warp >> lgG;
+            double chi = 0.0, se = 0.0;
+            if (g < Ge) {
+                const int i = i0 + g;
+                const float gam = cpar[2 * M + 2 * E + i];
+                const float bg = (float)(f * f) * gam;
+                const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
+                for (int p = sub; p < np; p += nsub) {
+                    float2 *row = A + g * EB + p * P::PX;
+                    float chi_r = 0.f, se_r = 0.f;
+                    for (int x0 = 0; x0 < N; x0 += 128) {
+                        float dv[4][2], wv[4][2];
+#pragma unroll
+                        for (int jx = 0; jx < 4; ++jx) {
+                            const int x = x0 + 32 * jx + lane;
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const int y = 2 * p + q;
+                                const bool in = y < N && x < N;
+                                dv[jx][q] = in ? __ldg(dd + y * N + x) : 0.f;
+                                wv[jx][q] = in ? __ldg(ww + y * N + x) : 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int jx = 0; jx < 4; ++jx) {
+                            const int x = x0 + 32 * jx + lane;
+                            if (x < N) {
+                                const float2 mv = row[x];
+                                float e2[2] = {0.f, 0.f};
+#pragma unroll
+                                for (int q = 0; q < 2; ++q) {
+                                    if (2 * p + q < N) {
+                                        const float Mv = (q ? mv.y : mv.x) * scale + bg;
+                                        const float res = dv[jx][q] - Mv;
+                                        chi_r += 0.5f * wv[jx][q] * res * res;
+                                        e2[q] = -wv[jx][q] * res;
+                                        se_r += e2[q];
+                                    }
+                                }
+                                row[x] = make_float2(e2[0], e2[1]);
+                            }
+                        }
+                    }
+                    chi += (double)chi_r;
+                    se += (double)se_r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                chi += __shfl_down_sync(0xffffffffu, chi, o);
+                se += __shfl_down_sync(0xffffffffu, se, o);
+            }
+            if (lane == 0 && g < Ge) {
+                sh.red[g * nv + 0][sub] = chi;
+                sh.red[g * nv + 1][sub] = se;
+            }
+        }
+        __syncthreads();
+        fx_fwd2d<L>(A, B, EB, Ge, np, inv_np, N, TWL);
+        // adjoint spectra: acc_phi += sum_g conj(Khat_{g,phi}) ehat_g (epochs in order), and the
+        // Parseval products of the sources (weights 1 at kx = 0 and L/2, 2 elsewhere).  With
+        // G > 1 (then M <= 1) the products are kept per batch element and folded per epoch
+        // below; with G = 1 per source (M <= kFftMaxSources <= kBatch).
+        const bool first = i0 == item.y;
+        float pa[kBatch], px[kBatch], py[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) pa[j] = px[j] = py[j] = 0.f;
+        for (int base = tid; base < LH; base += (kBatch >> lgG) * nt) {
+            for (int ph = 0; ph < nph; ++ph) {
+                const int phy = ph / f, phx = ph - phy * f;
+                float2 *ap = acc + (long long)ph * LH;
+                float2 kv[kBatch], av[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
+                    const bool ok = idx < LH && g < Ge;
+                    kv[j] = ok ? __ldg(&kh[((long long)g * nph + ph) * LH + idx]) : make_float2(0.f, 0.f);
+                    av[j] = (ok && g == 0 && !first) ? ap[idx] : make_float2(0.f, 0.f);
+                }
+                float2 run = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
+                    if (idx < LH && g < Ge) {
+                        const int ky = idx / H, kx = idx - ky * H;
+                        const float wgt = (kx == 0 || 2 * kx == L) ? 1.f : 2.f;
+                        const float2 Gv = cmulc(A[g * EB + idx], kv[j]);
+                        run = cadd(g == 0 ? av[j] : run, Gv);
+                        if (g == Ge - 1) ap[idx] = run;
+                        if (G > 1) {
+                            if (M == 1) {
+                                const float2 gx = gsx[g * MfH + phx * H + kx], gy = gsy[g * MfL + phy * L + ky];
+                                const float2 gxd = gsxd[g * MfH + phx * H + kx], gyd = gsyd[g * MfL + phy * L + ky];
+                                const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
+                                pa[j] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
+                                px[j] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
+                                py[j] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < kFftMaxSources; ++k) {
+                                if (k < M) {
+                                    const float2 gx = gsx[(k * f + phx) * H + kx], gy = gsy[(k * f + phy) * L + ky];
+                                    const float2 gxd = gsxd[(k * f + phx) * H + kx], gyd = gsyd[(k * f + phy) * L + ky];
+                                    // Re(G conj(a b)) for the profile and its two shift derivatives
+                                    const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
+                                    pa[k] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
+                                    px[k] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
+                                    py[k] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // fold per epoch (G > 1: batch element j belongs to epoch j mod G) and reduce over the
+        // warp in FP32, then across warps in FP64 below
+        if (M > 0) {
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q) {
+                // q indexes the epoch (G > 1) or the source (G = 1)
+                float a = 0.f, bx = 0.f, by = 0.f;
+                if (G > 1) {
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        if ((j & (G - 1)) == q) {
+                            a += pa[j];
+                            bx += px[j];
+                            by += py[j];
+                        }
+                    }
+                } else {
+                    a = pa[q];
+                    bx = px[q];
+                    by = py[q];
+                }
+                const bool live = G > 1 ? q < Ge : q < M;
+                if (live) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        a += __shfl_down_sync(0xffffffffu, a, o);
+                        bx += __shfl_down_sync(0xffffffffu, bx, o);
+                        by += __shfl_down_sync(0xffffffffu, by, o);
+                    }
+                    if (lane == 0) {
+                        const int g = G > 1 ? q : 0, k = G > 1 ? 0 : q;
+                        sh.red[g * nv + 2 + 3 * k][warp] = (double)a;
+                        sh.red[g * nv + 3 + 3 * k][warp] = (double)bx;
+                        sh.red[g * nv + 4 + 3 * k][warp] = (double)by;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < Ge * nv) {
+            const int g = tid / nv, q = tid - g * nv;
+            const int cnt = q < 2 ? nsub : nw;
+            double sum = 0.0;
+            for (int w = 0; w < cnt; ++w) sum += sh.red[tid][w];
+            const int i = i0 + g;
+            if (q == 0) {
+                chi_part[fd.tile_slot + i] = sum;
+            } else if (q == 1) {
+                se_part[fd.tile_slot + i] = sum;
+            } else {
+                const int k = (q - 2) / 3, which = (q - 2) - 3 * k;
+                const long long ps = fd.ps_slot + (long long)i * M + k;
+                const float sc = (float)(sum / ((double)L * (double)L));
+                if (which == 0) ps_da[ps] = sc;
+                else ps_du[2 * ps + which - 1] = sh.apar[g * M + k] * sc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+#define SR_FX_SIZES(X) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(60) X(64) X(72) X(80) X(96) X(100) X(108) X(120) X(128) X(144)
+
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_chunk_fixed_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ items, int n_items,
+                       int *__restrict__ counter, const float *__restrict__ params,
+                       const float2 *__restrict__ hhat_all, float2 *__restrict__ acc_all,
+                       double *__restrict__ chi_part, double *__restrict__ se_part, float *__restrict__ ps_da,
+                       float *__restrict__ ps_du) {
+    extern __shared__ __align__(16) float2 fsm[];
+    __shared__ FxShared sh;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = sh.item;
+        if (it >= n_items) break;
+        const int4 item = items[it];
+        const FieldDev &fd = fields[item.x];
+        switch (fd.fft_L) {
+#define SR_FX_CASE(LL)                                                                                          \
+    case LL:                                                                                                    \
+        chunk_item_fixed<LL>(fd, item, params, hhat_all, acc_all, chi_part, se_part, ps_da, ps_du, fsm, sh); \
+        break;
+            SR_FX_SIZES(SR_FX_CASE)
+#undef SR_FX_CASE
+            default:
+                break;  // not reached: the host only builds items for sizes in the list
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+bool fft_fixed_size(int L) {
+    switch (L) {
+#define SR_FX_OK(LL) case LL:
+        SR_FX_SIZES(SR_FX_OK)
+#undef SR_FX_OK
+        return true;
+        default:
+            return false;
+    }
+}
+
+int fft_fixed_next(int need) {
+    static const int sizes[] = {
+#define SR_FX_LIST(LL) LL,
+        SR_FX_SIZES(SR_FX_LIST)
+#undef SR_FX_LIST
+    };
+    for (int L : sizes)
+        if (L >= need) return L;
+    return 0;
+}
+
+// Elements (float2) of each of the two per-epoch buffers: the largest of the three layouts.
+int fft_fixed_epoch_buffer(int L, int N) {
+    const int R1 = fx_r1(L), R2 = L / R1;
+    const int S = (R2 & 1) ? R2 : R2 + 1;
+    const int np = (N + 1) / 2;
+    int eb = std::max(np * L, np * R1 * S);
+    eb = std::max(eb, L * (L / 2 + 1));
+    return (eb + 1) & ~1;  // keeps every buffer 16-byte aligned
+}
+
+int fft_fixed_smem_bytes(int L, int N, int M, int f, int G) {
+    const int H = L / 2 + 1;
+    return (2 * G * fft_fixed_epoch_buffer(L, N) + 2 * L + 2 * G * M * f * (H + L)) * (int)sizeof(float2);
+}
+
+sr_status configure_fft_fixed(int optin, int *limit) {
+    float2 tw[kDtwTotal];
+    for (int R : {6, 8, 9, 10, 12, 16})
+        for (int m = 0; m < R; ++m) {
+            const double a = -2.0 * M_PI * (double)m / (double)R;
+            tw[dtw_off(R) + m] = make_float2((float)cos(a), (float)sin(a));
+        }
+    SR_CUDA(cudaMemcpyToSymbol(c_dtw, tw, sizeof(tw)));
+    cudaFuncAttributes a;
+    SR_CUDA(cudaFuncGetAttributes(&a, fft_chunk_fixed_kernel));
+    const int dyn = optin - (int)a.sharedSizeBytes;
+    SR_CUDA(cudaFuncSetAttribute(fft_chunk_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    *limit = dyn;
+    return SR_OK;
+}
+
+sr_status occupancy_fft_fixed(int smem, int *blocks) {
+    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fft_chunk_fixed_kernel, kFftThreads, smem));
+    return SR_OK;
+}
+
+void launch_fft_chunks_fixed(const FieldDev *fields, const int4 *items, int n_items, int *counter,
+                             const float *params, const float2 *hhat, float2 *acc, double *chi_part,
+                             double *se_part, float *ps_da, float *ps_du, int grid, int smem, cudaStream_t st) {
+    fft_chunk_fixed_kernel<<<grid, kFftThreads, smem, st>>>(fields, items, n_items, counter, params, hhat, acc,
+                                                            chi_part, se_part, ps_da, ps_du);
+}
+
+}  // namespace sr

@@ -28,15 +28,22 @@ void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_par
 // --- frequency-domain form (fft.cu) ---
 int fft_smem_bytes(int L, int M, int f);
 sr_status configure_fft_kernels(int optin, int *limit);
-sr_status occupancy_fft_kernel(int smem, int *blocks);
 void launch_fft_kappa(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st);
 void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
                      const float *params, float2 *hhat, cudaStream_t st);
-void launch_fft_chunks(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
-                       const float2 *hhat, float2 *acc, double *chi_part, double *se_part, float *ps_da, float *ps_du,
-                       int grid, int smem, cudaStream_t st);
 void launch_fft_hgrad(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
                       const float2 *acc, float *grad, cudaStream_t st);
+
+// --- per-epoch chunk kernel for the transform sizes of a fixed list (fft_fixed.cu) ---
+bool fft_fixed_size(int L);
+int fft_fixed_next(int need);  // smallest listed size >= need, 0 if none
+int fft_fixed_epoch_buffer(int L, int N);
+int fft_fixed_smem_bytes(int L, int N, int M, int f, int G);
+sr_status configure_fft_fixed(int optin, int *limit);
+sr_status occupancy_fft_fixed(int smem, int *blocks);
+void launch_fft_chunks_fixed(const FieldDev *fields, const int4 *items, int n_items, int *counter,
+                             const float *params, const float2 *hhat, float2 *acc, double *chi_part,
+                             double *se_part, float *ps_da, float *ps_du, int grid, int smem, cudaStream_t st);
 
 // --- starlet prior (starlet.cu) ---
 // Forward levels then adjoint levels for every field of the table; writes the
