@@ -16,7 +16,8 @@
 //    transforms fill the block, and the chunk accumulator is read and written once per group
 //    instead of once per epoch.
 //  * the spectral loops take 4 (point, epoch) pairs per thread per batch, so that their global
-//    loads (kernel spectra, h spectra, accumulator) are in flight together.
+//    loads (kernel spectra, h spectra, accumulator) are in flight together; L2 eviction
+//    priorities keep the chunk accumulator and the epoch's kernel spectra resident.
 #include <math.h>
 
 #include <algorithm>
@@ -319,6 +320,41 @@ __device__ __forceinline__ void prefetch_l2(const void *p, long long bytes) {
     }
 }
 
+// L2 eviction priorities.  Per SM a large-L work item keeps its chunk accumulator (f^2 L (L/2+1)
+// complex) and the current epoch's kernel spectra live across the epoch, while the data,
+// weights and last reads of the spectra stream through: without hints the streamed lines
+// evict the accumulator between its read-modify-writes.
+__device__ __forceinline__ unsigned long long l2_policy_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// read-only loads (data not written during the kernel)
+__device__ __forceinline__ float2 ldg_hint(const float2 *p, unsigned long long pol) {
+    float2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ldg_hint(const float *p, unsigned long long pol) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+// the accumulator: ordered with its stores (volatile, memory clobber)
+__device__ __forceinline__ float2 ld_hint(const float2 *p, unsigned long long pol) {
+    float2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_hint(float2 *p, float2 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
+
 constexpr int kBatch = 4;  // (spectral point, epoch) pairs per thread per batch of loads
 constexpr int kMaxG = 4;   // epochs per group (<= kBatch: a batch holds every epoch of its points)
 // reduced values per group: G (2 + 3 M) with G > 1 only when M <= 1
@@ -364,16 +400,17 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     const float u0 = 0.5f * (float)(F - 1);
     const float scale = 1.f / ((float)L * (float)L);
     const int nsub = nw >> lgG;  // warps per epoch in the residual
+    const unsigned long long pol_last = l2_policy_last(), pol_first = l2_policy_first();
     const int nv = 2 + 3 * M;    // reduced values per epoch
     for (int i0 = item.y; i0 < item.z; i0 += G) {
         const int Ge = min(G, item.z - i0);
         const float2 *kh = fd.fft_khat + (long long)i0 * nph * LH;  // [g][phi][LH]
         if (tid < Ge * M) sh.apar[tid] = hpar[(long long)F * F + (long long)i0 * M + tid];
-        // the next group's kernel spectra, data and weights go to L2 while this one computes
-        // (sizes are multiples of 16 bytes: L*H is even, and N*N*4 when N is even)
+        // the next group's data and weights go to L2 while this one computes (N*N*4 is a
+        // multiple of 16 bytes when N is even).  Its kernel spectra are not prefetched: with every
+        // SM holding a large-L item, one more epoch of spectra per SM overflows L2.
         if (tid == 0 && i0 + G < item.z) {
             const int Gn = min(G, item.z - i0 - G);
-            prefetch_l2(kh + (long long)G * nph * LH, (long long)Gn * nph * LH * (long long)sizeof(float2));
             if ((N & 1) == 0) {
                 prefetch_l2(fd.d + (long long)(i0 + G) * N * N, (long long)Gn * N * N * 4);
                 prefetch_l2(fd.w + (long long)(i0 + G) * N * N, (long long)Gn * N * N * 4);
@@ -432,8 +469,8 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                 for (int j = 0; j < kBatch; ++j) {
                     const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
                     const bool ok = idx < LH && g < Ge;
-                    kv[j] = ok ? __ldg(&kh[((long long)g * nph + ph) * LH + idx]) : make_float2(0.f, 0.f);
-                    sv[j] = ok ? __ldg(&hh[(long long)ph * LH + idx]) : make_float2(0.f, 0.f);
+                    kv[j] = ok ? ldg_hint(&kh[((long long)g * nph + ph) * LH + idx], pol_last) : make_float2(0.f, 0.f);
+                    sv[j] = ok ? ldg_hint(&hh[(long long)ph * LH + idx], pol_last) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
@@ -481,8 +518,8 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                             for (int q = 0; q < 2; ++q) {
                                 const int y = 2 * p + q;
                                 const bool in = y < N && x < N;
-                                dv[jx][q] = in ? __ldg(dd + y * N + x) : 0.f;
-                                wv[jx][q] = in ? __ldg(ww + y * N + x) : 0.f;
+                                dv[jx][q] = in ? ldg_hint(dd + y * N + x, pol_first) : 0.f;
+                                wv[jx][q] = in ? ldg_hint(ww + y * N + x, pol_first) : 0.f;
                             }
                         }
 #pragma unroll
@@ -525,7 +562,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         // Parseval products of the sources (weights 1 at kx = 0 and L/2, 2 elsewhere).  With
         // G > 1 (then M <= 1) the products are kept per batch element and folded per epoch
         // below; with G = 1 per source (M <= kFftMaxSources <= kBatch).
-        const bool first = i0 == item.y;
+        const bool first = i0 == item.y, last = i0 + G >= item.z;
         float pa[kBatch], px[kBatch], py[kBatch];
 #pragma unroll
         for (int j = 0; j < kBatch; ++j) pa[j] = px[j] = py[j] = 0.f;
@@ -538,8 +575,8 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                 for (int j = 0; j < kBatch; ++j) {
                     const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
                     const bool ok = idx < LH && g < Ge;
-                    kv[j] = ok ? __ldg(&kh[((long long)g * nph + ph) * LH + idx]) : make_float2(0.f, 0.f);
-                    av[j] = (ok && g == 0 && !first) ? ap[idx] : make_float2(0.f, 0.f);
+                    kv[j] = ok ? ldg_hint(&kh[((long long)g * nph + ph) * LH + idx], pol_first) : make_float2(0.f, 0.f);
+                    av[j] = (ok && g == 0 && !first) ? ld_hint(&ap[idx], pol_last) : make_float2(0.f, 0.f);
                 }
                 float2 run = make_float2(0.f, 0.f);
 #pragma unroll
@@ -550,7 +587,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                         const float wgt = (kx == 0 || 2 * kx == L) ? 1.f : 2.f;
                         const float2 Gv = cmulc(A[g * EB + idx], kv[j]);
                         run = cadd(g == 0 ? av[j] : run, Gv);
-                        if (g == Ge - 1) ap[idx] = run;
+                        if (g == Ge - 1) st_hint(&ap[idx], run, last ? pol_first : pol_last);
                         if (G > 1) {
                             if (M == 1) {
                                 const float2 gx = gsx[g * MfH + phx * H + kx], gy = gsy[g * MfL + phy * L + ky];
