@@ -366,6 +366,10 @@ struct FxShared {
     float apar[kFftMaxSources];
     int item;
 };
+// Declared here rather than passed down, so that the per-size bodies (not inlined) still address
+// them as shared memory.
+extern __shared__ __align__(16) float2 fx_dyn[];
+__shared__ FxShared fx_sh;
 
 // One item (x = field, y = first epoch, z = end, w = chunk index within the field), in groups
 // of G epochs.  Not inlined: each size is register-allocated on its own (one call per item).
@@ -373,7 +377,9 @@ template <int L>
 __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 item, const float *__restrict__ params,
                                  const float2 *__restrict__ hhat_all, float2 *__restrict__ acc_all,
                                  double *__restrict__ chi_part, double *__restrict__ se_part,
-                                 float *__restrict__ ps_da, float *__restrict__ ps_du, float2 *fsm, FxShared &sh) {
+                                 float *__restrict__ ps_da, float *__restrict__ ps_du) {
+    float2 *const fsm = fx_dyn;
+    FxShared &sh = fx_sh;
     using P = Fx<L>;
     constexpr int H = P::H, LH = P::LH, R2 = P::R2;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -400,6 +406,11 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     const float u0 = 0.5f * (float)(F - 1);
     const float scale = 1.f / ((float)L * (float)L);
     const int nsub = nw >> lgG;  // warps per epoch in the residual
+    // spectral loops: thread (ty, tx) takes column tx and rows ty + RP r
+    constexpr int RP = kFftThreads / H;
+    const int tx = tid % H, ty = tid / H;
+    const int rstep = (kBatch >> lgG) * RP;
+    const float wgt = (tx == 0 || 2 * tx == L) ? 1.f : 2.f;  // Parseval weight of column tx
     const unsigned long long pol_last = l2_policy_last(), pol_first = l2_policy_first();
     const int nv = 2 + 3 * M;    // reduced values per epoch
     for (int i0 = item.y; i0 < item.z; i0 += G) {
@@ -440,7 +451,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                     const float t = src_offset(u, F, f, cpos, dl);
                     const float gv = kGauss1Norm * exp2f(-t * t);
                     const float gd = gv * t * kGaussInvSig2;
-                    const float2 w = tw[(int)(((long long)kk * m) % L)];
+                    const float2 w = tw[(kk * m) % L];  // kk < L, 0 <= m <= N + 1: no overflow
                     v.x += gv * w.x;
                     v.y += gv * w.y;
                     vd.x += gd * w.x;
@@ -456,42 +467,45 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
             }
         }
         __syncthreads();
-        // model spectra: sum_phi Khat_{g,phi} (Hhat_phi + sum_k a_{g,k} gx gy); batch element
-        // j takes epoch j mod G of spectral point base + (j / G) nt
-        for (int base = tid; base < LH; base += (kBatch >> lgG) * nt) {
-            float2 m[kBatch];
+        // model spectra: sum_phi Khat_{g,phi} (Hhat_phi + sum_k a_{g,k} gx gy).  Thread
+        // (ty, tx) = (tid / H, tid mod H) takes column kx = tx and rows ty + RP r, so there is no
+        // per-point index division; batch element j takes epoch j mod G of row row0 + (j / G) RP
+        if (ty < RP) {
+            for (int row0 = ty; row0 < L; row0 += rstep) {
+                float2 m[kBatch];
 #pragma unroll
-            for (int j = 0; j < kBatch; ++j) m[j] = make_float2(0.f, 0.f);
-            for (int ph = 0; ph < nph; ++ph) {
-                const int phy = ph / f, phx = ph - phy * f;
-                float2 kv[kBatch], sv[kBatch];
+                for (int j = 0; j < kBatch; ++j) m[j] = make_float2(0.f, 0.f);
+                for (int ph = 0; ph < nph; ++ph) {
+                    const int phy = ph / f, phx = ph - phy * f;
+                    float2 kv[kBatch], sv[kBatch];
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
-                    const bool ok = idx < LH && g < Ge;
-                    kv[j] = ok ? ldg_hint(&kh[((long long)g * nph + ph) * LH + idx], pol_last) : make_float2(0.f, 0.f);
-                    sv[j] = ok ? ldg_hint(&hh[(long long)ph * LH + idx], pol_last) : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
-                    if (idx < LH && g < Ge) {
-                        const int ky = idx / H, kx = idx - ky * H;
-                        for (int k = 0; k < M; ++k) {
-                            const float2 pr = cmul(gsx[g * MfH + (k * f + phx) * H + kx],
-                                                   gsy[g * MfL + (k * f + phy) * L + ky]);
-                            const float a = sh.apar[g * M + k];
-                            sv[j].x += a * pr.x;
-                            sv[j].y += a * pr.y;
-                        }
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
+                        const bool ok = row < L && g < Ge;
+                        const int off = row * H + tx;
+                        kv[j] = ok ? ldg_hint(kh + (g * nph + ph) * LH + off, pol_last) : make_float2(0.f, 0.f);
+                        sv[j] = ok ? ldg_hint(hh + ph * LH + off, pol_last) : make_float2(0.f, 0.f);
                     }
-                    m[j] = cadd(m[j], cmul(kv[j], sv[j]));
-                }
-            }
 #pragma unroll
-            for (int j = 0; j < kBatch; ++j) {
-                const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
-                if (idx < LH && g < Ge) A[g * EB + idx] = m[j];
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
+                        if (row < L && g < Ge) {
+                            for (int k = 0; k < M; ++k) {
+                                const float2 pr = cmul(gsx[g * MfH + (k * f + phx) * H + tx],
+                                                       gsy[g * MfL + (k * f + phy) * L + row]);
+                                const float a = sh.apar[g * M + k];
+                                sv[j].x += a * pr.x;
+                                sv[j].y += a * pr.y;
+                            }
+                        }
+                        m[j] = cadd(m[j], cmul(kv[j], sv[j]));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
+                    if (row < L && g < Ge) A[g * EB + row * H + tx] = m[j];
+                }
             }
         }
         __syncthreads();
@@ -566,48 +580,49 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         float pa[kBatch], px[kBatch], py[kBatch];
 #pragma unroll
         for (int j = 0; j < kBatch; ++j) pa[j] = px[j] = py[j] = 0.f;
-        for (int base = tid; base < LH; base += (kBatch >> lgG) * nt) {
-            for (int ph = 0; ph < nph; ++ph) {
-                const int phy = ph / f, phx = ph - phy * f;
-                float2 *ap = acc + (long long)ph * LH;
-                float2 kv[kBatch], av[kBatch];
+        if (ty < RP) {
+            for (int row0 = ty; row0 < L; row0 += rstep) {
+                for (int ph = 0; ph < nph; ++ph) {
+                    const int phy = ph / f, phx = ph - phy * f;
+                    float2 *ap = acc + ph * LH + tx;
+                    float2 kv[kBatch], av[kBatch];
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
-                    const bool ok = idx < LH && g < Ge;
-                    kv[j] = ok ? ldg_hint(&kh[((long long)g * nph + ph) * LH + idx], pol_first) : make_float2(0.f, 0.f);
-                    av[j] = (ok && g == 0 && !first) ? ld_hint(&ap[idx], pol_last) : make_float2(0.f, 0.f);
-                }
-                float2 run = make_float2(0.f, 0.f);
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
+                        const bool ok = row < L && g < Ge;
+                        kv[j] = ok ? ldg_hint(kh + (g * nph + ph) * LH + row * H + tx, pol_first) : make_float2(0.f, 0.f);
+                        av[j] = (ok && g == 0 && !first) ? ld_hint(ap + row * H, pol_last) : make_float2(0.f, 0.f);
+                    }
+                    float2 run = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const int g = j & (G - 1), idx = base + (j >> lgG) * nt;
-                    if (idx < LH && g < Ge) {
-                        const int ky = idx / H, kx = idx - ky * H;
-                        const float wgt = (kx == 0 || 2 * kx == L) ? 1.f : 2.f;
-                        const float2 Gv = cmulc(A[g * EB + idx], kv[j]);
-                        run = cadd(g == 0 ? av[j] : run, Gv);
-                        if (g == Ge - 1) st_hint(&ap[idx], run, last ? pol_first : pol_last);
-                        if (G > 1) {
-                            if (M == 1) {
-                                const float2 gx = gsx[g * MfH + phx * H + kx], gy = gsy[g * MfL + phy * L + ky];
-                                const float2 gxd = gsxd[g * MfH + phx * H + kx], gyd = gsyd[g * MfL + phy * L + ky];
-                                const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
-                                pa[j] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
-                                px[j] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
-                                py[j] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
-                            }
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < kFftMaxSources; ++k) {
-                                if (k < M) {
-                                    const float2 gx = gsx[(k * f + phx) * H + kx], gy = gsy[(k * f + phy) * L + ky];
-                                    const float2 gxd = gsxd[(k * f + phx) * H + kx], gyd = gsyd[(k * f + phy) * L + ky];
-                                    // Re(G conj(a b)) for the profile and its two shift derivatives
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
+                        if (row < L && g < Ge) {
+                            const float2 Gv = cmulc(A[g * EB + row * H + tx], kv[j]);
+                            run = cadd(g == 0 ? av[j] : run, Gv);
+                            if (g == Ge - 1) st_hint(ap + row * H, run, last ? pol_first : pol_last);
+                            if (G > 1) {
+                                if (M == 1) {
+                                    const float2 gx = gsx[g * MfH + phx * H + tx], gy = gsy[g * MfL + phy * L + row];
+                                    const float2 gxd = gsxd[g * MfH + phx * H + tx], gyd = gsyd[g * MfL + phy * L + row];
                                     const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
-                                    pa[k] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
-                                    px[k] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
-                                    py[k] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
+                                    pa[j] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
+                                    px[j] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
+                                    py[j] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
+                                }
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < kFftMaxSources; ++k) {
+                                    if (k < M) {
+                                        const float2 gx = gsx[(k * f + phx) * H + tx], gy = gsy[(k * f + phy) * L + row];
+                                        const float2 gxd = gsxd[(k * f + phx) * H + tx];
+                                        const float2 gyd = gsyd[(k * f + phy) * L + row];
+                                        // Re(G conj(a b)) for the profile and its two shift derivatives
+                                        const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
+                                        pa[k] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
+                                        px[k] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
+                                        py[k] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
+                                    }
                                 }
                             }
                         }
@@ -684,19 +699,17 @@ fft_chunk_fixed_kernel(const FieldDev *__restrict__ fields, const int4 *__restri
                        const float2 *__restrict__ hhat_all, float2 *__restrict__ acc_all,
                        double *__restrict__ chi_part, double *__restrict__ se_part, float *__restrict__ ps_da,
                        float *__restrict__ ps_du) {
-    extern __shared__ __align__(16) float2 fsm[];
-    __shared__ FxShared sh;
     for (;;) {
-        if (threadIdx.x == 0) sh.item = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) fx_sh.item = atomicAdd(counter, 1);
         __syncthreads();
-        const int it = sh.item;
+        const int it = fx_sh.item;
         if (it >= n_items) break;
         const int4 item = items[it];
         const FieldDev &fd = fields[item.x];
         switch (fd.fft_L) {
 #define SR_FX_CASE(LL)                                                                                          \
     case LL:                                                                                                    \
-        chunk_item_fixed<LL>(fd, item, params, hhat_all, acc_all, chi_part, se_part, ps_da, ps_du, fsm, sh); \
+        chunk_item_fixed<LL>(fd, item, params, hhat_all, acc_all, chi_part, se_part, ps_da, ps_du);          \
         break;
             SR_FX_SIZES(SR_FX_CASE)
 #undef SR_FX_CASE
