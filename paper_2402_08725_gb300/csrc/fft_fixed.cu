@@ -417,9 +417,12 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         const int Ge = min(G, item.z - i0);
         const float2 *kh = fd.fft_khat + (long long)i0 * nph * LH;  // [g][phi][LH]
         if (tid < Ge * M) sh.apar[tid] = hpar[(long long)F * F + (long long)i0 * M + tid];
-        // the next group's data and weights go to L2 while this one computes (N*N*4 is a
-        // multiple of 16 bytes when N is even).  Its kernel spectra are not prefetched: with every
-        // SM holding a large-L item, one more epoch of spectra per SM overflows L2.
+        // This group's kernel spectra go to L2 while the window spectra are computed, and the
+        // next group's data and weights while this one computes (sizes are multiples of 16
+        // bytes: L*H is even, and N*N*4 when N is even).  The next group's kernel spectra are not
+        // prefetched: with every SM holding a large-L item, one more epoch of spectra per SM
+        // overflows L2.
+        if (tid == 0) prefetch_l2(kh, (long long)Ge * nph * LH * (long long)sizeof(float2));
         if (tid == 0 && i0 + G < item.z) {
             const int Gn = min(G, item.z - i0 - G);
             if ((N & 1) == 0) {

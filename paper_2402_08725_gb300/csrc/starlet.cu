@@ -50,94 +50,106 @@ __device__ __forceinline__ float adj_1d(const float *__restrict__ y, int n, int 
     return acc;
 }
 
+// Chunk items (256 pixels each) per block: their loads are in flight together, and the block's
+// set-up (item, field) is paid once per 1024 pixels.
+constexpr int kStarletChunks = 4;
+
 // pass = 0: forward row pass; 1: forward column pass (+ detail plane, L1 partial);
 //        2: adjoint column pass; 3: adjoint row pass (+ gamma).
 __global__ void __launch_bounds__(256)
 starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__restrict__ chunks, int n_chunks,
                     const float *__restrict__ params, double *__restrict__ l1_part, int j, int pass) {
-    __shared__ double s_red[8];
-    const int c = blockIdx.x;
-    const ChunkItem ch = chunks[c];
-    const FieldDev &fd = fields[ch.field];
-    if (j > fd.J - 2) return;  // whole block exits together
-    const int F = fd.F;
+    __shared__ double s_red[kStarletChunks][8];
     const int step = 1 << j;
-    const int px = ch.start + threadIdx.x;
-    const bool valid = px < F * F;
-    const int y = valid ? px / F : 0, x = valid ? px - y * F : 0;
-    const float lw = fd.lambda * fd.Wd[j];
-    double l1 = 0.0;
-    if (pass == 0) {
-        if (valid) {
-            const float *cj = c_plane(fd, params, j) + (long long)y * F;
-            float acc = 0.f;
 #pragma unroll
-            for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * cj[mirror_at(x + n * step, F)];
-            pass_plane(fd)[px] = acc;
-        }
-    } else if (pass == 1) {
-        if (valid) {
-            const float *tmp = pass_plane(fd);
-            float acc = 0.f;
+    for (int q = 0; q < kStarletChunks; ++q) {
+        const int c = blockIdx.x * kStarletChunks + q;
+        if (c >= n_chunks) break;  // uniform over the block
+        const ChunkItem ch = chunks[c];
+        const FieldDev &fd = fields[ch.field];
+        if (j > fd.J - 2) continue;  // the field has no level j: the whole block skips this item
+        const int F = fd.F;
+        const int px = ch.start + threadIdx.x;
+        const bool valid = px < F * F;
+        const int y = valid ? px / F : 0, x = valid ? px - y * F : 0;
+        const float lw = fd.lambda * fd.Wd[j];
+        double l1 = 0.0;
+        if (pass == 0) {
+            if (valid) {
+                const float *cj = c_plane(fd, params, j) + (long long)y * F;
+                float acc = 0.f;
 #pragma unroll
-            for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * tmp[(long long)mirror_at(y + m * step, F) * F + x];
-            float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
-            cn[px] = acc;
-            const float wv = c_plane(fd, params, j)[px] - acc;
-            l1 = (double)fabsf(wv);
-        }
-    } else if (pass == 2) {
-        if (valid) {
-            // v = T_{j+1} - gamma_{j+1}; tmp = Col^T v (gather over rows)
-            const float *cj = c_plane(fd, params, j);
-            const float *cn = fd.starlet + (long long)j * F * F;
-            const bool has_t = (j + 1) < (fd.J - 1);
-            const float *Tn = t_plane(fd, j + 1);
-            float acc = 0.f;
+                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * cj[mirror_at(x + n * step, F)];
+                pass_plane(fd)[px] = acc;
+            }
+        } else if (pass == 1) {
+            if (valid) {
+                const float *tmp = pass_plane(fd);
+                float acc = 0.f;
 #pragma unroll
-            for (int m = -2; m <= 2; ++m) {
-                const float b = kB3[m + 2];
-                int ks[3];
-                int nk = 0;
-                const int k1 = y - m * step;
-                if (k1 >= 0 && k1 < F) ks[nk++] = k1;
-                if (y > 0) {
-                    const int k2 = -y - m * step;
-                    if (k2 >= 0 && k2 < F) ks[nk++] = k2;
-                }
-                if (y < F - 1) {
-                    const int k3 = 2 * (F - 1) - y - m * step;
-                    if (k3 >= 0 && k3 < F) ks[nk++] = k3;
-                }
-                for (int q = 0; q < nk; ++q) {
-                    const long long o = (long long)ks[q] * F + x;
+                for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * tmp[(long long)mirror_at(y + m * step, F) * F + x];
+                float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
+                cn[px] = acc;
+                const float wv = c_plane(fd, params, j)[px] - acc;
+                l1 = (double)fabsf(wv);
+            }
+        } else if (pass == 2) {
+            if (valid) {
+                // v = T_{j+1} - gamma_{j+1}; tmp = Col^T v, gathered over the (up to three) rows k
+                // whose mirrored taps land on row y
+                const float *cj = c_plane(fd, params, j);
+                const float *cn = fd.starlet + (long long)j * F * F;
+                const bool has_t = (j + 1) < (fd.J - 1);
+                const float *Tn = t_plane(fd, j + 1);
+                auto v = [&](int k) {
+                    const long long o = (long long)k * F + x;
                     const float wv = cj[o] - cn[o];
                     const float g = wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f);
-                    const float v = (has_t ? Tn[o] : 0.f) - g;
-                    acc += b * v;
+                    return (has_t ? Tn[o] : 0.f) - g;
+                };
+                float acc = 0.f;
+#pragma unroll
+                for (int m = -2; m <= 2; ++m) {
+                    const float b = kB3[m + 2];
+                    const int k1 = y - m * step;
+                    if (k1 >= 0 && k1 < F) acc += b * v(k1);
+                    const int k2 = -y - m * step;
+                    if (y > 0 && k2 >= 0 && k2 < F) acc += b * v(k2);
+                    const int k3 = 2 * (F - 1) - y - m * step;
+                    if (y < F - 1 && k3 >= 0 && k3 < F) acc += b * v(k3);
                 }
+                pass_plane(fd)[px] = acc;
             }
-            pass_plane(fd)[px] = acc;
+        } else {
+            if (valid) {
+                const float *tmp = pass_plane(fd) + (long long)y * F;
+                const float acc = adj_1d(tmp, x, F, step, 1);
+                const float wv = c_plane(fd, params, j)[px] - fd.starlet[(long long)j * F * F + px];
+                const float g = wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f);
+                t_plane(fd, j)[px] = g + acc;
+            }
         }
-    } else {
-        if (valid) {
-            const float *tmp = pass_plane(fd) + (long long)y * F;
-            const float acc = adj_1d(tmp, x, F, step, 1);
-            const float wv = c_plane(fd, params, j)[px] - fd.starlet[(long long)j * F * F + px];
-            const float g = wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f);
-            t_plane(fd, j)[px] = g + acc;
+        if (pass == 1) {
+            // deterministic reduction of |w| over the item's 256 pixels
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) l1 += __shfl_down_sync(0xffffffffu, l1, o);
+            if ((threadIdx.x & 31) == 0) s_red[q][threadIdx.x >> 5] = l1;
         }
     }
     if (pass == 1) {
-        // deterministic block reduction of |w|
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_down_sync(0xffffffffu, l1, o);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = l1;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < 8; ++i) s += s_red[i];
-            l1_part[fd.l1_slot + (long long)j * fd.n_chunks + ch.chunk] = (double)fd.lambda * (double)fd.Wd[j] * s;
+        if (threadIdx.x < kStarletChunks) {
+            const int c = blockIdx.x * kStarletChunks + threadIdx.x;
+            if (c < n_chunks) {
+                const ChunkItem ch = chunks[c];
+                const FieldDev &fd = fields[ch.field];
+                if (j <= fd.J - 2) {
+                    double s = 0.0;
+                    for (int i = 0; i < 8; ++i) s += s_red[threadIdx.x][i];
+                    l1_part[fd.l1_slot + (long long)j * fd.n_chunks + ch.chunk] =
+                        (double)fd.lambda * (double)fd.Wd[j] * s;
+                }
+            }
         }
     }
 }
@@ -145,14 +157,15 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
 int launch_starlet(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, int Jmax, const float *params,
                    double *l1_part, cudaStream_t st) {
     int n = 0;
+    const int grid = (n_chunks + kStarletChunks - 1) / kStarletChunks;
     for (int j = 0; j <= Jmax - 2; ++j) {
-        starlet_pass_kernel<<<n_chunks, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 0);
-        starlet_pass_kernel<<<n_chunks, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 1);
+        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 0);
+        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 1);
         n += 2;
     }
     for (int j = Jmax - 2; j >= 0; --j) {
-        starlet_pass_kernel<<<n_chunks, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
-        starlet_pass_kernel<<<n_chunks, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 3);
+        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
+        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 3);
         n += 2;
     }
     return n;
