@@ -473,7 +473,47 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         // model spectra: sum_phi Khat_{g,phi} (Hhat_phi + sum_k a_{g,k} gx gy).  Thread
         // (ty, tx) = (tid / H, tid mod H) takes column kx = tx and rows ty + RP r, so there is no
         // per-point index division; batch element j takes epoch j mod G of row row0 + (j / G) RP
-        if (ty < RP) {
+        // One epoch per group (the large transforms): batch element j is row row0 + j RP, and the
+        // sources' column profiles a_k gx_k(tx) are loaded once per step.
+        if (G == 1 && ty < RP) {
+            for (int row0 = ty; row0 < L; row0 += kBatch * RP) {
+                float2 m[kBatch];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) m[j] = make_float2(0.f, 0.f);
+                for (int ph = 0; ph < nph; ++ph) {
+                    const int phy = ph / f, phx = ph - phy * f;
+                    float2 kv[kBatch], sv[kBatch];
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int row = row0 + j * RP;
+                        const int off = row * H + tx;
+                        kv[j] = row < L ? ldg_hint(kh + ph * LH + off, pol_last) : make_float2(0.f, 0.f);
+                        sv[j] = row < L ? ldg_hint(hh + ph * LH + off, pol_last) : make_float2(0.f, 0.f);
+                    }
+                    for (int k = 0; k < M; ++k) {
+                        const float a = sh.apar[k];
+                        const float2 gx = gsx[(k * f + phx) * H + tx];
+                        const float2 agx = make_float2(a * gx.x, a * gx.y);
+                        const float2 *gy = gsy + (k * f + phy) * L;
+#pragma unroll
+                        for (int j = 0; j < kBatch; ++j) {
+                            const int row = row0 + j * RP;
+                            if (row < L) sv[j] = cadd(sv[j], cmul(agx, gy[row]));
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) m[j] = cadd(m[j], cmul(kv[j], sv[j]));
+                }
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
+                    const int row = row0 + j * RP;
+                    if (row < L) A[row * H + tx] = m[j];
+                }
+            }
+        }
+        // Several epochs per group (then at most one source): batch element j takes epoch
+        // j mod G of row row0 + (j / G) RP.
+        if (G > 1 && ty < RP) {
             for (int row0 = ty; row0 < L; row0 += rstep) {
                 float2 m[kBatch];
 #pragma unroll
@@ -583,7 +623,53 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         float pa[kBatch], px[kBatch], py[kBatch];
 #pragma unroll
         for (int j = 0; j < kBatch; ++j) pa[j] = px[j] = py[j] = 0.f;
-        if (ty < RP) {
+        // One epoch per group: batch element j is row row0 + j RP.  With the column tx fixed,
+        // the Parseval sums factor: sum_rows w Re(G conj(gx gy)) = w Re(conj(gx) U) with
+        // U = sum_rows G conj(gy) (and V with the y-derivative profile), so per point only U and V
+        // are accumulated and the column profiles are applied once per step.
+        if (G == 1 && ty < RP) {
+            for (int row0 = ty; row0 < L; row0 += kBatch * RP) {
+                for (int ph = 0; ph < nph; ++ph) {
+                    const int phy = ph / f, phx = ph - phy * f;
+                    float2 *ap = acc + ph * LH + tx;
+                    float2 kv[kBatch], av[kBatch];
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int row = row0 + j * RP;
+                        kv[j] = row < L ? ldg_hint(kh + ph * LH + row * H + tx, pol_first) : make_float2(0.f, 0.f);
+                        av[j] = (row < L && !first) ? ld_hint(ap + row * H, pol_last) : make_float2(0.f, 0.f);
+                    }
+                    float2 U[kFftMaxSources], V[kFftMaxSources];
+#pragma unroll
+                    for (int k = 0; k < kFftMaxSources; ++k) U[k] = V[k] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < kBatch; ++j) {
+                        const int row = row0 + j * RP;
+                        if (row < L) {
+                            const float2 Gv = cmulc(A[row * H + tx], kv[j]);
+                            st_hint(ap + row * H, cadd(av[j], Gv), last ? pol_first : pol_last);
+#pragma unroll
+                            for (int k = 0; k < kFftMaxSources; ++k) {
+                                if (k < M) {
+                                    U[k] = cadd(U[k], cmulc(Gv, gsy[(k * f + phy) * L + row]));
+                                    V[k] = cadd(V[k], cmulc(Gv, gsyd[(k * f + phy) * L + row]));
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < kFftMaxSources; ++k) {
+                        if (k < M) {
+                            const float2 gx = gsx[(k * f + phx) * H + tx], gxd = gsxd[(k * f + phx) * H + tx];
+                            pa[k] += wgt * (U[k].x * gx.x + U[k].y * gx.y);
+                            px[k] += wgt * (U[k].x * gxd.x + U[k].y * gxd.y);
+                            py[k] += wgt * (V[k].x * gx.x + V[k].y * gx.y);
+                        }
+                    }
+                }
+            }
+        }
+        if (G > 1 && ty < RP) {
             for (int row0 = ty; row0 < L; row0 += rstep) {
                 for (int ph = 0; ph < nph; ++ph) {
                     const int phy = ph / f, phx = ph - phy * f;
@@ -604,29 +690,13 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                             const float2 Gv = cmulc(A[g * EB + row * H + tx], kv[j]);
                             run = cadd(g == 0 ? av[j] : run, Gv);
                             if (g == Ge - 1) st_hint(ap + row * H, run, last ? pol_first : pol_last);
-                            if (G > 1) {
-                                if (M == 1) {
-                                    const float2 gx = gsx[g * MfH + phx * H + tx], gy = gsy[g * MfL + phy * L + row];
-                                    const float2 gxd = gsxd[g * MfH + phx * H + tx], gyd = gsyd[g * MfL + phy * L + row];
-                                    const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
-                                    pa[j] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
-                                    px[j] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
-                                    py[j] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
-                                }
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < kFftMaxSources; ++k) {
-                                    if (k < M) {
-                                        const float2 gx = gsx[(k * f + phx) * H + tx], gy = gsy[(k * f + phy) * L + row];
-                                        const float2 gxd = gsxd[(k * f + phx) * H + tx];
-                                        const float2 gyd = gsyd[(k * f + phy) * L + row];
-                                        // Re(G conj(a b)) for the profile and its two shift derivatives
-                                        const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
-                                        pa[k] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
-                                        px[k] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
-                                        py[k] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
-                                    }
-                                }
+                            if (M == 1) {
+                                const float2 gx = gsx[g * MfH + phx * H + tx], gy = gsy[g * MfL + phy * L + row];
+                                const float2 gxd = gsxd[g * MfH + phx * H + tx], gyd = gsyd[g * MfL + phy * L + row];
+                                const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
+                                pa[j] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
+                                px[j] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
+                                py[j] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
                             }
                         }
                     }
