@@ -345,14 +345,17 @@ __device__ __forceinline__ float ldg_hint(const float *p, unsigned long long pol
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
     return v;
 }
-// the accumulator: ordered with its stores (volatile, memory clobber)
+// The accumulator: volatile, so that its loads and stores keep their program order among
+// themselves and against the block barriers; no memory clobber, so that the shared-memory reads
+// and the spectra loads around them can still be scheduled freely (a store's value depends on the
+// load of the same element, and different elements never alias).
 __device__ __forceinline__ float2 ld_hint(const float2 *p, unsigned long long pol) {
     float2 v;
-    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol) : "memory");
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
     return v;
 }
 __device__ __forceinline__ void st_hint(float2 *p, float2 v, unsigned long long pol) {
-    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol));
 }
 
 constexpr int kBatch = 4;  // (spectral point, epoch) pairs per thread per batch of loads
@@ -563,39 +566,51 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                 const float gam = cpar[2 * M + 2 * E + i];
                 const float bg = (float)(f * f) * gam;
                 const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
-                for (int p = sub; p < np; p += nsub) {
-                    float2 *row = A + g * EB + p * P::PX;
+                // two row pairs per iteration, so that 32 data and weight loads per lane are in
+                // flight together
+                for (int p0 = sub; p0 < np; p0 += 2 * nsub) {
                     float chi_r = 0.f, se_r = 0.f;
                     for (int x0 = 0; x0 < N; x0 += 128) {
-                        float dv[4][2], wv[4][2];
+                        float dv[2][4][2], wv[2][4][2];
 #pragma unroll
-                        for (int jx = 0; jx < 4; ++jx) {
-                            const int x = x0 + 32 * jx + lane;
+                        for (int rp = 0; rp < 2; ++rp) {
+                            const int p = p0 + rp * nsub;
 #pragma unroll
-                            for (int q = 0; q < 2; ++q) {
-                                const int y = 2 * p + q;
-                                const bool in = y < N && x < N;
-                                dv[jx][q] = in ? ldg_hint(dd + y * N + x, pol_first) : 0.f;
-                                wv[jx][q] = in ? ldg_hint(ww + y * N + x, pol_first) : 0.f;
+                            for (int jx = 0; jx < 4; ++jx) {
+                                const int x = x0 + 32 * jx + lane;
+#pragma unroll
+                                for (int q = 0; q < 2; ++q) {
+                                    const int y = 2 * p + q;
+                                    const bool in = p < np && y < N && x < N;
+                                    dv[rp][jx][q] = in ? ldg_hint(dd + y * N + x, pol_first) : 0.f;
+                                    wv[rp][jx][q] = in ? ldg_hint(ww + y * N + x, pol_first) : 0.f;
+                                }
                             }
                         }
 #pragma unroll
-                        for (int jx = 0; jx < 4; ++jx) {
-                            const int x = x0 + 32 * jx + lane;
-                            if (x < N) {
-                                const float2 mv = row[x];
-                                float e2[2] = {0.f, 0.f};
+                        for (int rp = 0; rp < 2; ++rp) {
+                            const int p = p0 + rp * nsub;
+                            if (p < np) {
+                                float2 *row = A + g * EB + p * P::PX;
 #pragma unroll
-                                for (int q = 0; q < 2; ++q) {
-                                    if (2 * p + q < N) {
-                                        const float Mv = (q ? mv.y : mv.x) * scale + bg;
-                                        const float res = dv[jx][q] - Mv;
-                                        chi_r += 0.5f * wv[jx][q] * res * res;
-                                        e2[q] = -wv[jx][q] * res;
-                                        se_r += e2[q];
+                                for (int jx = 0; jx < 4; ++jx) {
+                                    const int x = x0 + 32 * jx + lane;
+                                    if (x < N) {
+                                        const float2 mv = row[x];
+                                        float e2[2] = {0.f, 0.f};
+#pragma unroll
+                                        for (int q = 0; q < 2; ++q) {
+                                            if (2 * p + q < N) {
+                                                const float Mv = (q ? mv.y : mv.x) * scale + bg;
+                                                const float res = dv[rp][jx][q] - Mv;
+                                                chi_r += 0.5f * wv[rp][jx][q] * res * res;
+                                                e2[q] = -wv[rp][jx][q] * res;
+                                                se_r += e2[q];
+                                            }
+                                        }
+                                        row[x] = make_float2(e2[0], e2[1]);
                                     }
                                 }
-                                row[x] = make_float2(e2[0], e2[1]);
                             }
                         }
                     }
