@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "cplx.cuh"
@@ -642,7 +643,9 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         // the Parseval sums factor: sum_rows w Re(G conj(gx gy)) = w Re(conj(gx) U) with
         // U = sum_rows G conj(gy) (and V with the y-derivative profile), so per point only U and V
         // are accumulated and the column profiles are applied once per step.
-        if (G == 1 && ty < RP) {
+        // (compiled for at most one source, the common case, and for up to kFftMaxSources)
+        auto adj_one_epoch = [&](auto ms_tag) {
+            constexpr int MS = decltype(ms_tag)::value;
             for (int row0 = ty; row0 < L; row0 += kBatch * RP) {
                 for (int ph = 0; ph < nph; ++ph) {
                     const int phy = ph / f, phx = ph - phy * f;
@@ -654,9 +657,9 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                         kv[j] = row < L ? ldg_hint(kh + ph * LH + row * H + tx, pol_first) : make_float2(0.f, 0.f);
                         av[j] = (row < L && !first) ? ld_hint(ap + row * H, pol_last) : make_float2(0.f, 0.f);
                     }
-                    float2 U[kFftMaxSources], V[kFftMaxSources];
+                    float2 U[MS], V[MS];
 #pragma unroll
-                    for (int k = 0; k < kFftMaxSources; ++k) U[k] = V[k] = make_float2(0.f, 0.f);
+                    for (int k = 0; k < MS; ++k) U[k] = V[k] = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int j = 0; j < kBatch; ++j) {
                         const int row = row0 + j * RP;
@@ -664,7 +667,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                             const float2 Gv = cmulc(A[row * H + tx], kv[j]);
                             st_hint(ap + row * H, cadd(av[j], Gv), last ? pol_first : pol_last);
 #pragma unroll
-                            for (int k = 0; k < kFftMaxSources; ++k) {
+                            for (int k = 0; k < MS; ++k) {
                                 if (k < M) {
                                     U[k] = cadd(U[k], cmulc(Gv, gsy[(k * f + phy) * L + row]));
                                     V[k] = cadd(V[k], cmulc(Gv, gsyd[(k * f + phy) * L + row]));
@@ -673,7 +676,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < kFftMaxSources; ++k) {
+                    for (int k = 0; k < MS; ++k) {
                         if (k < M) {
                             const float2 gx = gsx[(k * f + phx) * H + tx], gxd = gsxd[(k * f + phx) * H + tx];
                             pa[k] += wgt * (U[k].x * gx.x + U[k].y * gx.y);
@@ -683,6 +686,10 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                     }
                 }
             }
+        };
+        if (G == 1 && ty < RP) {
+            if (M <= 1) adj_one_epoch(std::integral_constant<int, 1>{});
+            else adj_one_epoch(std::integral_constant<int, kFftMaxSources>{});
         }
         if (G > 1 && ty < RP) {
             for (int row0 = ty; row0 < L; row0 += rstep) {
