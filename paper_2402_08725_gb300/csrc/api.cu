@@ -471,9 +471,9 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             fd.fft_n_chunks = (fd.E + kFftChunk - 1) / kFftChunk;
             for (int c = 0; c < fd.fft_n_chunks; ++c)
                 fft_items.push_back(make_int4(i, c * kFftChunk, std::min(fd.E, (c + 1) * kFftChunk), c));
-            acc_len += (long long)fd.fft_n_chunks * nph * L * H;
+            acc_len += (long long)fd.fft_n_chunks * nph * L * (H + 1);  // rows padded to H + 1
             fd.fft_hhat_off = hhat_len;
-            hhat_len += (long long)nph * L * H;
+            hhat_len += (long long)nph * L * (H + 1);
             fft_fields.push_back(i);
             pl->max_nph = std::max(pl->max_nph, nph);
             smem_fft = std::max(smem_fft, fft_smem_bytes(L, 0, fd.f));
@@ -929,7 +929,8 @@ sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_p
                 p->fft_L = L;
                 p->fft_nst = nst;
                 const size_t H = L / 2 + 1;
-                if ((st = A.alloc(&p->khat, E * d.supersampling * d.supersampling * (size_t)L * H)) != SR_OK)
+                // rows padded to H + 1 (even), so that column pairs are 16-byte aligned
+                if ((st = A.alloc(&p->khat, E * d.supersampling * d.supersampling * (size_t)L * (H + 1))) != SR_OK)
                     return bail(st);
                 if ((st = A.alloc(&p->fft_tw, (size_t)L)) != SR_OK) return bail(st);
                 std::vector<float2> tw(L);

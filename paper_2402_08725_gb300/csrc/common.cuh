@@ -53,9 +53,11 @@ struct FieldDev {
     int fft_L, fft_nst;
     int fft_rad[kFftMaxStages];
     const float2 *fft_tw;     // [L] exp(-2 pi i n / L)
-    const float2 *fft_khat;   // [E][f*f][L][L/2+1] transforms of the folded kernels
-    long long fft_hhat_off;   // offset of the field's [f*f][L][L/2+1] h spectra in the plan buffer
-    long long fft_acc_off;    // float2 offset of the field's chunk accumulators ([f*f][L][L/2+1] each)
+    // spectra in global memory are rows of L/2+2 (the last column a zero pad, so that column
+    // pairs are 16-byte aligned)
+    const float2 *fft_khat;   // [E][f*f][L][L/2+2] transforms of the folded kernels
+    long long fft_hhat_off;   // offset of the field's [f*f][L][L/2+2] h spectra in the plan buffer
+    long long fft_acc_off;    // float2 offset of the field's chunk accumulators ([f*f][L][L/2+2] each)
     int fft_n_chunks;         // epoch chunks of the field
     int fft_G;                // epochs transformed side by side by the chunk kernel (1, 2 or 4)
     int fft_EB;               // float2 elements of each per-epoch transform buffer (fft_fixed.cu)

@@ -229,8 +229,13 @@ fft_kappa_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restric
     }
     __syncthreads();
     float2 *S = fwd2d(A, B, g, L / 2);
-    float2 *out = khat + ((long long)i * nph + ph) * L * H;
-    for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) out[idx] = S[idx];
+    // global layout: rows of Hp = H + 1 (even, for 16-byte column pairs), the pad column zero
+    const int Hp = H + 1;
+    float2 *out = khat + ((long long)i * nph + ph) * L * Hp;
+    for (int idx = threadIdx.x; idx < L * Hp; idx += blockDim.x) {
+        const int ky = idx / Hp, kx = idx - ky * Hp;
+        out[idx] = kx < H ? S[ky * H + kx] : make_float2(0.f, 0.f);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -266,8 +271,12 @@ fft_hhat_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft
     }
     __syncthreads();
     float2 *S = fwd2d(A, B, g, np);
-    float2 *out = hhat_all + fd.fft_hhat_off + (long long)ph * L * H;
-    for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) out[idx] = S[idx];
+    const int Hp = H + 1;  // global row pitch (pad column zero)
+    float2 *out = hhat_all + fd.fft_hhat_off + (long long)ph * L * Hp;
+    for (int idx = threadIdx.x; idx < L * Hp; idx += blockDim.x) {
+        const int ky = idx / Hp, kx = idx - ky * Hp;
+        out[idx] = kx < H ? S[ky * H + kx] : make_float2(0.f, 0.f);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -287,10 +296,12 @@ fft_hgrad_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ ff
     FftGeom g;
     load_geom(g, fd, tw);
     const int n_chunks = fd.fft_n_chunks;
+    const int Hp = H + 1, LHp = L * Hp;  // global row pitch of the accumulators
     for (int idx = threadIdx.x; idx < LH; idx += blockDim.x) {
+        const int ky = idx / H, kx = idx - ky * H;
         float2 s = make_float2(0.f, 0.f);
-        const float2 *ac = acc_all + fd.fft_acc_off + (long long)ph * LH + idx;
-        for (int c = 0; c < n_chunks; ++c) s = cadd(s, ac[(long long)c * nph * LH]);
+        const float2 *ac = acc_all + fd.fft_acc_off + (long long)ph * LHp + ky * Hp + kx;
+        for (int c = 0; c < n_chunks; ++c) s = cadd(s, ac[(long long)c * nph * LHp]);
         A[idx] = s;
     }
     __syncthreads();

@@ -156,6 +156,7 @@ __host__ __device__ constexpr int fx_r1(int L) {
 template <int L>
 struct Fx {
     static constexpr int R1 = fx_r1(L), R2 = L / R1, H = L / 2 + 1, LH = L * H;
+    static constexpr int HP = H + 1, LHP = L * HP;  // global spectra: row pitch HP (zero pad column)
     static constexpr int S = (R2 & 1) ? R2 : R2 + 1, PX = L, PY = R1 * S;
     static_assert(R1 > 0 && R1 * R2 == L && L % 4 == 0, "transform size not in the list");
 };
@@ -346,6 +347,14 @@ __device__ __forceinline__ float ldg_hint(const float *p, unsigned long long pol
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
     return v;
 }
+// two complex values (16 bytes: a column pair of a padded spectrum row)
+__device__ __forceinline__ float4 ldg4_hint(const float2 *p, unsigned long long pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
 // The accumulator: volatile, so that its loads and stores keep their program order among
 // themselves and against the block barriers; no memory clobber, so that the shared-memory reads
 // and the spectra loads around them can still be scheduled freely (a store's value depends on the
@@ -358,8 +367,22 @@ __device__ __forceinline__ float2 ld_hint(const float2 *p, unsigned long long po
 __device__ __forceinline__ void st_hint(float2 *p, float2 v, unsigned long long pol) {
     asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol));
 }
+__device__ __forceinline__ float4 ld4_hint(const float2 *p, unsigned long long pol) {
+    float4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st4_hint(float2 *p, float4 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol));
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
 constexpr int kBatch = 4;  // (spectral point, epoch) pairs per thread per batch of loads
+constexpr int kPairRows = 2;  // rows per step of the one-epoch loops (two columns per row)
 constexpr int kMaxG = 4;   // epochs per group (<= kBatch: a batch holds every epoch of its points)
 // reduced values per group: G (2 + 3 M) with G > 1 only when M <= 1
 constexpr int kRedVals = (kMaxG * 5 > 2 + 3 * kFftMaxSources) ? kMaxG * 5 : 2 + 3 * kFftMaxSources;
@@ -385,7 +408,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     float2 *const fsm = fx_dyn;
     FxShared &sh = fx_sh;
     using P = Fx<L>;
-    constexpr int H = P::H, LH = P::LH, R2 = P::R2;
+    constexpr int H = P::H, R2 = P::R2, HP = P::HP, LHP = P::LHP;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E, nph = f * f;
@@ -406,7 +429,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     const float *hpar = params + fd.param_off;
     const float *cpar = hpar + (long long)F * F + (long long)E * M;
     const float2 *hh = hhat_all + fd.fft_hhat_off;
-    float2 *acc = acc_all + fd.fft_acc_off + (long long)item.w * nph * LH;
+    float2 *acc = acc_all + fd.fft_acc_off + (long long)item.w * nph * LHP;
     const float u0 = 0.5f * (float)(F - 1);
     const float scale = 1.f / ((float)L * (float)L);
     const int nsub = nw >> lgG;  // warps per epoch in the residual
@@ -415,18 +438,24 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     const int tx = tid % H, ty = tid / H;
     const int rstep = (kBatch >> lgG) * RP;
     const float wgt = (tx == 0 || 2 * tx == L) ? 1.f : 2.f;  // Parseval weight of column tx
+    // one-epoch loops: thread (ty2, cp) = (tid / HH, tid mod HH) takes the column pair
+    // (c0, c1) = (2 cp, 2 cp + 1) (c1 = H is the zero pad column) of rows ty2 + RP2 r
+    constexpr int HH = HP / 2, RP2 = kFftThreads / HH;
+    const int cp = tid % HH, ty2 = tid / HH, c0 = 2 * cp, c1 = c0 + 1;
+    const bool has1 = c1 < H;
+    const float wgt0 = (c0 == 0 || 2 * c0 == L) ? 1.f : 2.f, wgt1 = has1 ? (2 * c1 == L ? 1.f : 2.f) : 0.f;
     const unsigned long long pol_last = l2_policy_last(), pol_first = l2_policy_first();
     const int nv = 2 + 3 * M;    // reduced values per epoch
     for (int i0 = item.y; i0 < item.z; i0 += G) {
         const int Ge = min(G, item.z - i0);
-        const float2 *kh = fd.fft_khat + (long long)i0 * nph * LH;  // [g][phi][LH]
+        const float2 *kh = fd.fft_khat + (long long)i0 * nph * LHP;  // [g][phi][L][HP]
         if (tid < Ge * M) sh.apar[tid] = hpar[(long long)F * F + (long long)i0 * M + tid];
         // This group's kernel spectra go to L2 while the window spectra are computed, and the
         // next group's data and weights while this one computes (sizes are multiples of 16
         // bytes: L*H is even, and N*N*4 when N is even).  The next group's kernel spectra are not
         // prefetched: with every SM holding a large-L item, one more epoch of spectra per SM
         // overflows L2.
-        if (tid == 0) prefetch_l2(kh, (long long)Ge * nph * LH * (long long)sizeof(float2));
+        if (tid == 0) prefetch_l2(kh, (long long)Ge * nph * LHP * (long long)sizeof(float2));
         if (tid == 0 && i0 + G < item.z) {
             const int Gn = min(G, item.z - i0 - G);
             if ((N & 1) == 0) {
@@ -477,41 +506,51 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         // model spectra: sum_phi Khat_{g,phi} (Hhat_phi + sum_k a_{g,k} gx gy).  Thread
         // (ty, tx) = (tid / H, tid mod H) takes column kx = tx and rows ty + RP r, so there is no
         // per-point index division; batch element j takes epoch j mod G of row row0 + (j / G) RP
-        // One epoch per group (the large transforms): batch element j is row row0 + j RP, and the
-        // sources' column profiles a_k gx_k(tx) are loaded once per step.
-        if (G == 1 && ty < RP) {
-            for (int row0 = ty; row0 < L; row0 += kBatch * RP) {
-                float2 m[kBatch];
+        // One epoch per group (the large transforms): the column pairs of kPairRows rows per step,
+        // with 16-byte loads; the sources' column profiles a_k gx_k are loaded once per step.
+        if (G == 1 && ty2 < RP2) {
+            for (int row0 = ty2; row0 < L; row0 += kPairRows * RP2) {
+                float2 m0[kPairRows], m1[kPairRows];
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) m[j] = make_float2(0.f, 0.f);
+                for (int j = 0; j < kPairRows; ++j) m0[j] = m1[j] = make_float2(0.f, 0.f);
                 for (int ph = 0; ph < nph; ++ph) {
                     const int phy = ph / f, phx = ph - phy * f;
-                    float2 kv[kBatch], sv[kBatch];
+                    float4 kv[kPairRows], sv[kPairRows];
 #pragma unroll
-                    for (int j = 0; j < kBatch; ++j) {
-                        const int row = row0 + j * RP;
-                        const int off = row * H + tx;
-                        kv[j] = row < L ? ldg_hint(kh + ph * LH + off, pol_last) : make_float2(0.f, 0.f);
-                        sv[j] = row < L ? ldg_hint(hh + ph * LH + off, pol_last) : make_float2(0.f, 0.f);
+                    for (int j = 0; j < kPairRows; ++j) {
+                        const int row = row0 + j * RP2;
+                        const int off = row * HP + c0;
+                        kv[j] = row < L ? ldg4_hint(kh + ph * LHP + off, pol_last) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        sv[j] = row < L ? ldg4_hint(hh + ph * LHP + off, pol_last) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                     for (int k = 0; k < M; ++k) {
                         const float a = sh.apar[k];
-                        const float2 gx = gsx[(k * f + phx) * H + tx];
-                        const float2 agx = make_float2(a * gx.x, a * gx.y);
+                        const float2 *gxk = gsx + (k * f + phx) * H;
+                        const float2 gx0 = gxk[c0], gx1 = has1 ? gxk[c1] : make_float2(0.f, 0.f);
+                        const float2 agx0 = make_float2(a * gx0.x, a * gx0.y), agx1 = make_float2(a * gx1.x, a * gx1.y);
                         const float2 *gy = gsy + (k * f + phy) * L;
 #pragma unroll
-                        for (int j = 0; j < kBatch; ++j) {
-                            const int row = row0 + j * RP;
-                            if (row < L) sv[j] = cadd(sv[j], cmul(agx, gy[row]));
+                        for (int j = 0; j < kPairRows; ++j) {
+                            const int row = row0 + j * RP2;
+                            if (row < L) {
+                                const float2 g = gy[row], p0 = cmul(agx0, g), p1 = cmul(agx1, g);
+                                sv[j] = make_float4(sv[j].x + p0.x, sv[j].y + p0.y, sv[j].z + p1.x, sv[j].w + p1.y);
+                            }
                         }
                     }
 #pragma unroll
-                    for (int j = 0; j < kBatch; ++j) m[j] = cadd(m[j], cmul(kv[j], sv[j]));
+                    for (int j = 0; j < kPairRows; ++j) {
+                        m0[j] = cadd(m0[j], cmul(lo2(kv[j]), lo2(sv[j])));
+                        m1[j] = cadd(m1[j], cmul(hi2(kv[j]), hi2(sv[j])));
+                    }
                 }
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const int row = row0 + j * RP;
-                    if (row < L) A[row * H + tx] = m[j];
+                for (int j = 0; j < kPairRows; ++j) {
+                    const int row = row0 + j * RP2;
+                    if (row < L) {
+                        A[row * H + c0] = m0[j];
+                        if (has1) A[row * H + c1] = m1[j];
+                    }
                 }
             }
         }
@@ -529,9 +568,9 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                     for (int j = 0; j < kBatch; ++j) {
                         const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
                         const bool ok = row < L && g < Ge;
-                        const int off = row * H + tx;
-                        kv[j] = ok ? ldg_hint(kh + (g * nph + ph) * LH + off, pol_last) : make_float2(0.f, 0.f);
-                        sv[j] = ok ? ldg_hint(hh + ph * LH + off, pol_last) : make_float2(0.f, 0.f);
+                        const int off = row * HP + tx;
+                        kv[j] = ok ? ldg_hint(kh + (g * nph + ph) * LHP + off, pol_last) : make_float2(0.f, 0.f);
+                        sv[j] = ok ? ldg_hint(hh + ph * LHP + off, pol_last) : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int j = 0; j < kBatch; ++j) {
@@ -646,31 +685,40 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         // (compiled for at most one source, the common case, and for up to kFftMaxSources)
         auto adj_one_epoch = [&](auto ms_tag) {
             constexpr int MS = decltype(ms_tag)::value;
-            for (int row0 = ty; row0 < L; row0 += kBatch * RP) {
+            for (int row0 = ty2; row0 < L; row0 += kPairRows * RP2) {
                 for (int ph = 0; ph < nph; ++ph) {
                     const int phy = ph / f, phx = ph - phy * f;
-                    float2 *ap = acc + ph * LH + tx;
-                    float2 kv[kBatch], av[kBatch];
+                    float2 *ap = acc + ph * LHP + c0;
+                    float4 kv[kPairRows], av[kPairRows];
 #pragma unroll
-                    for (int j = 0; j < kBatch; ++j) {
-                        const int row = row0 + j * RP;
-                        kv[j] = row < L ? ldg_hint(kh + ph * LH + row * H + tx, pol_first) : make_float2(0.f, 0.f);
-                        av[j] = (row < L && !first) ? ld_hint(ap + row * H, pol_last) : make_float2(0.f, 0.f);
+                    for (int j = 0; j < kPairRows; ++j) {
+                        const int row = row0 + j * RP2;
+                        kv[j] = row < L ? ldg4_hint(kh + ph * LHP + row * HP + c0, pol_first)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                        av[j] = (row < L && !first) ? ld4_hint(ap + row * HP, pol_last) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    float2 U[MS], V[MS];
+                    float2 U0[MS], U1[MS], V0[MS], V1[MS];
 #pragma unroll
-                    for (int k = 0; k < MS; ++k) U[k] = V[k] = make_float2(0.f, 0.f);
+                    for (int k = 0; k < MS; ++k) U0[k] = U1[k] = V0[k] = V1[k] = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int j = 0; j < kBatch; ++j) {
-                        const int row = row0 + j * RP;
+                    for (int j = 0; j < kPairRows; ++j) {
+                        const int row = row0 + j * RP2;
                         if (row < L) {
-                            const float2 Gv = cmulc(A[row * H + tx], kv[j]);
-                            st_hint(ap + row * H, cadd(av[j], Gv), last ? pol_first : pol_last);
+                            const float2 e0 = A[row * H + c0], e1 = has1 ? A[row * H + c1] : make_float2(0.f, 0.f);
+                            const float2 G0 = cmulc(e0, lo2(kv[j])), G1 = cmulc(e1, hi2(kv[j]));
+                            // the pad column of the accumulator stays zero
+                            st4_hint(ap + row * HP,
+                                     make_float4(av[j].x + G0.x, av[j].y + G0.y, has1 ? av[j].z + G1.x : 0.f,
+                                                 has1 ? av[j].w + G1.y : 0.f),
+                                     last ? pol_first : pol_last);
 #pragma unroll
                             for (int k = 0; k < MS; ++k) {
                                 if (k < M) {
-                                    U[k] = cadd(U[k], cmulc(Gv, gsy[(k * f + phy) * L + row]));
-                                    V[k] = cadd(V[k], cmulc(Gv, gsyd[(k * f + phy) * L + row]));
+                                    const float2 gy = gsy[(k * f + phy) * L + row], gyd = gsyd[(k * f + phy) * L + row];
+                                    U0[k] = cadd(U0[k], cmulc(G0, gy));
+                                    U1[k] = cadd(U1[k], cmulc(G1, gy));
+                                    V0[k] = cadd(V0[k], cmulc(G0, gyd));
+                                    V1[k] = cadd(V1[k], cmulc(G1, gyd));
                                 }
                             }
                         }
@@ -678,16 +726,20 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
 #pragma unroll
                     for (int k = 0; k < MS; ++k) {
                         if (k < M) {
-                            const float2 gx = gsx[(k * f + phx) * H + tx], gxd = gsxd[(k * f + phx) * H + tx];
-                            pa[k] += wgt * (U[k].x * gx.x + U[k].y * gx.y);
-                            px[k] += wgt * (U[k].x * gxd.x + U[k].y * gxd.y);
-                            py[k] += wgt * (V[k].x * gx.x + V[k].y * gx.y);
+                            const float2 *gxk = gsx + (k * f + phx) * H, *gxdk = gsxd + (k * f + phx) * H;
+                            const float2 gx0 = gxk[c0], gxd0 = gxdk[c0];
+                            const float2 gx1 = has1 ? gxk[c1] : make_float2(0.f, 0.f);
+                            const float2 gxd1 = has1 ? gxdk[c1] : make_float2(0.f, 0.f);
+                            pa[k] += wgt0 * (U0[k].x * gx0.x + U0[k].y * gx0.y) + wgt1 * (U1[k].x * gx1.x + U1[k].y * gx1.y);
+                            px[k] += wgt0 * (U0[k].x * gxd0.x + U0[k].y * gxd0.y) +
+                                     wgt1 * (U1[k].x * gxd1.x + U1[k].y * gxd1.y);
+                            py[k] += wgt0 * (V0[k].x * gx0.x + V0[k].y * gx0.y) + wgt1 * (V1[k].x * gx1.x + V1[k].y * gx1.y);
                         }
                     }
                 }
             }
         };
-        if (G == 1 && ty < RP) {
+        if (G == 1 && ty2 < RP2) {
             if (M <= 1) adj_one_epoch(std::integral_constant<int, 1>{});
             else adj_one_epoch(std::integral_constant<int, kFftMaxSources>{});
         }
@@ -695,14 +747,14 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
             for (int row0 = ty; row0 < L; row0 += rstep) {
                 for (int ph = 0; ph < nph; ++ph) {
                     const int phy = ph / f, phx = ph - phy * f;
-                    float2 *ap = acc + ph * LH + tx;
+                    float2 *ap = acc + ph * LHP + tx;
                     float2 kv[kBatch], av[kBatch];
 #pragma unroll
                     for (int j = 0; j < kBatch; ++j) {
                         const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
                         const bool ok = row < L && g < Ge;
-                        kv[j] = ok ? ldg_hint(kh + (g * nph + ph) * LH + row * H + tx, pol_first) : make_float2(0.f, 0.f);
-                        av[j] = (ok && g == 0 && !first) ? ld_hint(ap + row * H, pol_last) : make_float2(0.f, 0.f);
+                        kv[j] = ok ? ldg_hint(kh + (g * nph + ph) * LHP + row * HP + tx, pol_first) : make_float2(0.f, 0.f);
+                        av[j] = (ok && g == 0 && !first) ? ld_hint(ap + row * HP, pol_last) : make_float2(0.f, 0.f);
                     }
                     float2 run = make_float2(0.f, 0.f);
 #pragma unroll
@@ -711,7 +763,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                         if (row < L && g < Ge) {
                             const float2 Gv = cmulc(A[g * EB + row * H + tx], kv[j]);
                             run = cadd(g == 0 ? av[j] : run, Gv);
-                            if (g == Ge - 1) st_hint(ap + row * H, run, last ? pol_first : pol_last);
+                            if (g == Ge - 1) st_hint(ap + row * HP, run, last ? pol_first : pol_last);
                             if (M == 1) {
                                 const float2 gx = gsx[g * MfH + phx * H + tx], gy = gsy[g * MfL + phy * L + row];
                                 const float2 gxd = gsxd[g * MfH + phx * H + tx], gyd = gsyd[g * MfL + phy * L + row];
