@@ -167,21 +167,29 @@ def fft_flops(fields):
     return fl
 
 
-CHUNK_SRC = os.path.join(ROOT, "paper_2402_08725_gb300", "csrc", "fft_fixed.cu")
+CHUNK_SRCS = [os.path.join(ROOT, "paper_2402_08725_gb300", "csrc", n) for n in ("fft_fixed.cu", "common.cuh", "cplx.cuh")]
 CHUNK_PROFILE = os.path.join(ROOT, "profiles", "fft_chunk_fixed_kernel_config4.md")
+
+
+def chunk_source_hash():
+    """First 16 hex digits of the sha256 of the transform chunk kernel's source files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for path in CHUNK_SRCS:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():
     """DRAM bytes (read + write) of one full-size config-4 launch of the transform chunk kernel,
     from the committed ncu summary, or None if that summary was taken on another version of the
     kernel's source (its recorded hash differs)."""
-    import hashlib
     import re
     try:
         txt = open(CHUNK_PROFILE).read()
         want = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt).group(1)
-        have = hashlib.sha256(open(CHUNK_SRC, "rb").read()).hexdigest()[:16]
-        if want != have:
+        if want != chunk_source_hash():
             return None
         return float(re.search(r"dram_bytes_per_launch_full:\s*(\d+)", txt).group(1))
     except (OSError, AttributeError, ValueError):

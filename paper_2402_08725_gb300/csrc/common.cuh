@@ -23,7 +23,7 @@ constexpr int kBlurHalf = 8;
 
 constexpr int kMaxScales = 8;
 constexpr int kFftMaxStages = 8;
-constexpr int kFftThreads = 512;
+constexpr int kFftThreads = 768;
 constexpr int kFftMaxSources = 4;  // point sources per field in the frequency-domain form
 constexpr int kThreads = 256;
 
