@@ -174,6 +174,8 @@ struct Plan {
     int n_chunks = 0;
     ChunkItem *d_chunks = nullptr;
     int Jmax = 0;
+    int Fmax = 0;               // widest fine grid of the table (the starlet band grid)
+    bool any_unbanded = false;  // some field's starlet runs as passes rather than bands
     float *ebuf = nullptr, *gbuf = nullptr, *ps_da = nullptr, *ps_du = nullptr;
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
     // frequency-domain form
@@ -457,6 +459,8 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         l1slot += (long long)(fd.J - 1) * fd.n_chunks;
         for (int c = 0; c < fd.n_chunks; ++c) chunks.push_back(ChunkItem{i, c * 256, c});
         Jmax = std::max(Jmax, fd.J);
+        pl->Fmax = std::max(pl->Fmax, fd.F);
+        if (!starlet_field_banded(fd.F, fd.J)) pl->any_unbanded = true;
         if (pl->kind == SR_DECONV && !plain && field_uses_fft(p, opt)) {
             // frequency-domain form: chunks of consecutive epochs, one accumulator per chunk
             fd.mode = 1;
@@ -681,7 +685,8 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
         launch_psgrad(pl->d_fields, pl->d_ps, pl->n_ps, params, pl->gbuf, pl->ps_da, pl->ps_du, st);
         ++n;
     }
-    n += launch_starlet(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->Jmax, params, pl->l1_part, st);
+    n += launch_starlet(pl->d_fields, pl->n_fields, pl->Fmax, pl->any_unbanded, pl->d_chunks, pl->n_chunks, pl->Jmax,
+                        params, pl->l1_part, st);
     if (pl->n_items > 0) {
         launch_hgrad(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->gbuf, grad, st);
         ++n;

@@ -46,11 +46,14 @@ void launch_fft_chunks_fixed(const FieldDev *fields, const int4 *items, int n_it
                              double *se_part, float *ps_da, float *ps_du, int grid, int smem, cudaStream_t st);
 
 // --- starlet prior (starlet.cu) ---
-// Forward levels then adjoint levels for every field of the table; writes the
-// per-(level, chunk) prior partial sums and leaves T0 = dP/dh in plane J of
-// each field's starlet scratch.  Returns the number of launches issued.
-int launch_starlet(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, int Jmax, const float *params,
-                   double *l1_part, cudaStream_t st);
+// Forward levels then adjoint levels for every field of the table (n_fields of them, grids at
+// most Fmax wide); writes the per-(level, chunk) prior partial sums and leaves T0 = dP/dh in
+// plane J of each field's starlet scratch.  Fields for which starlet_field_banded(F, J) holds
+// run as row bands; any_unbanded says whether the table has others (they run as passes over
+// the 256-pixel chunks).  Returns the number of launches issued.
+bool starlet_field_banded(int F, int J);
+int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unbanded, const ChunkItem *chunks,
+                   int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st);
 
 // --- PSF reconstruction (psf.cu) ---
 struct PsfBuffers {

@@ -10,13 +10,32 @@
 //
 // Scratch per field (planes of F*F floats): c_1..c_{J-1} (planes 0..J-2), a pass buffer (J-1),
 // and two T planes (J, J+1) used alternately; T_0 ends in plane J.
-// One launch per pass covers every field of the table (fields deeper than a level skip it).
+//
+// Two ways to run a level, chosen per field (starlet_banded):
+//  * bands: one launch per level; a block takes 16 output rows of one field, filters the rows it
+//    needs (with their 2 * 2^j-row halo) along x into shared memory, then along y.  The adjoint
+//    propagates V_j = T_j - gamma_j instead of T_j (V_{J-1} = -gamma_{J-1} is formed while
+//    loading), so that its column pass reads one plane per tap; the signs are taken from the c
+//    planes once per output pixel.  Same arithmetic, in the same order, as the passes below.
+//  * passes (fields too wide for the shared-memory budget): one launch per pass and level,
+//    every field of the table in 256-pixel chunks.
+// Fields deeper than a level skip it.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace sr {
 
 __constant__ float kB3[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
+
+constexpr int kBandRows = 16;                  // output rows per block in the band kernels
+constexpr int kBandSmemBytes = 100 * 1024;     // shared memory of a band block (two per SM)
+
+// Whether a field runs its levels as bands: the deepest level's adjoint (2 * 16 + 4 * 2^(J-2)
+// rows of F floats) fits the budget.
+__host__ __device__ inline bool starlet_banded(int F, int J) {
+    const long long s = 1LL << (J - 2);
+    return (2LL * kBandRows + 4 * s) * F * (long long)sizeof(float) <= kBandSmemBytes;
+}
 
 __device__ __forceinline__ int mirror_at(int t, int F) { return t < 0 ? -t : (t > F - 1 ? 2 * (F - 1) - t : t); }
 
@@ -67,7 +86,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
         if (c >= n_chunks) break;  // uniform over the block
         const ChunkItem ch = chunks[c];
         const FieldDev &fd = fields[ch.field];
-        if (j > fd.J - 2) continue;  // the field has no level j: the whole block skips this item
+        if (j > fd.J - 2 || starlet_banded(fd.F, fd.J)) continue;  // no level j here, or run as bands
         const int F = fd.F;
         const int px = ch.start + threadIdx.x;
         const bool valid = px < F * F;
@@ -143,7 +162,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
             if (c < n_chunks) {
                 const ChunkItem ch = chunks[c];
                 const FieldDev &fd = fields[ch.field];
-                if (j <= fd.J - 2) {
+                if (j <= fd.J - 2 && !starlet_banded(fd.F, fd.J)) {
                     double s = 0.0;
                     for (int i = 0; i < 8; ++i) s += s_red[threadIdx.x][i];
                     l1_part[fd.l1_slot + (long long)j * fd.n_chunks + ch.chunk] =
@@ -154,19 +173,151 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
     }
 }
 
-int launch_starlet(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, int Jmax, const float *params,
-                   double *l1_part, cudaStream_t st) {
+// Forward level j as bands: c_{j+1} = Col_j Row_j c_j on rows [y0, y0 + 16) and the prior
+// partial lambda W_j sum |c_j - c_{j+1}| of the band.  Block (b, field).
+__global__ void __launch_bounds__(256)
+starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
+                        double *__restrict__ l1_part, int j) {
+    extern __shared__ float sb[];
+    __shared__ double s_red[8];
+    const FieldDev &fd = fields[blockIdx.y];
+    const int F = fd.F, J = fd.J;
+    if (j > J - 2 || !starlet_banded(F, J)) return;
+    const int b = blockIdx.x, y0 = b * kBandRows;
+    if (y0 >= F) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int s = 1 << j, Tr = min(kBandRows, F - y0), r0 = y0 - 2 * s;
+    // rows r0 .. y0 + Tr - 1 + 2s (mirrored: one reflection, as 2 s <= F - 1), filtered along x
+    const int R = Tr + 4 * s;
+    const float *cj = c_plane(fd, params, j);
+    for (int i = warp; i < R; i += nwarp) {
+        const float *row = cj + (long long)mirror_at(r0 + i, F) * F;
+        float *dst = sb + (long long)i * F;
+        for (int x = lane; x < F; x += 32) {
+            float acc = 0.f;
+#pragma unroll
+            for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+            dst[x] = acc;
+        }
+    }
+    __syncthreads();
+    float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
+    double l1 = 0.0;
+    for (int yy = warp; yy < Tr; yy += nwarp) {
+        const long long ro = (long long)(y0 + yy) * F;
+        for (int x = lane; x < F; x += 32) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(yy + 2 * s + m * s) * F + x];
+            cn[ro + x] = acc;
+            l1 += (double)fabsf(cj[ro + x] - acc);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l1 += __shfl_down_sync(0xffffffffu, l1, o);
+    if (lane == 0) s_red[warp] = l1;
+    __syncthreads();
+    const long long base = fd.l1_slot + (long long)j * fd.n_chunks;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nwarp; ++w) t += s_red[w];
+        l1_part[base + b] = (double)fd.lambda * (double)fd.Wd[j] * t;
+    }
+    if (b == 0) {  // the level's remaining partial-sum slots (one per 256-pixel chunk) stay zero
+        const int nb = (F + kBandRows - 1) / kBandRows;
+        for (int c = nb + threadIdx.x; c < fd.n_chunks; c += blockDim.x) l1_part[base + c] = 0.0;
+    }
+}
+
+__device__ __forceinline__ float gamma_of(float wv, float lw) { return wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f); }
+
+// Adjoint level j as bands: T_j = gamma_{j+1} + Row_j^T Col_j^T V_{j+1} on rows [y0, y0 + 16),
+// written as V_j = T_j - gamma_j (j >= 1) or T_0 (j = 0) into plane J + (j & 1).
+__global__ void __launch_bounds__(256)
+starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
+    extern __shared__ float sb[];
+    const FieldDev &fd = fields[blockIdx.y];
+    const int F = fd.F, J = fd.J;
+    if (j > J - 2 || !starlet_banded(F, J)) return;
+    const int b = blockIdx.x, y0 = b * kBandRows;
+    if (y0 >= F) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int s = 1 << j, Tr = min(kBandRows, F - y0);
+    // every row the column gather below can reach (mirror preimages included)
+    const int vlo = max(0, y0 - 2 * s), vhi = min(F, y0 + Tr + 2 * s);
+    float *vb = sb, *tb = sb + (long long)(kBandRows + 4 * s) * F;
+    const float lw1 = fd.lambda * fd.Wd[j];
+    const float *cj = c_plane(fd, params, j), *cn = fd.starlet + (long long)j * F * F;  // c_j, c_{j+1}
+    const bool top = j + 1 == J - 1;
+    const float *Vn = fd.starlet + (long long)(J + ((j + 1) & 1)) * F * F;
+    for (int i = warp; i < vhi - vlo; i += nwarp) {
+        const long long ro = (long long)(vlo + i) * F;
+        for (int x = lane; x < F; x += 32)
+            vb[(long long)i * F + x] = top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1) : Vn[ro + x];
+    }
+    __syncthreads();
+    for (int yy = warp; yy < Tr; yy += nwarp) {
+        const int y = y0 + yy;
+        for (int x = lane; x < F; x += 32) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = -2; m <= 2; ++m) {
+                const float bm = kB3[m + 2];
+                const int k1 = y - m * s;
+                if (k1 >= 0 && k1 < F) acc += bm * vb[(long long)(k1 - vlo) * F + x];
+                const int k2 = -y - m * s;
+                if (y > 0 && k2 >= 0 && k2 < F) acc += bm * vb[(long long)(k2 - vlo) * F + x];
+                const int k3 = 2 * (F - 1) - y - m * s;
+                if (y < F - 1 && k3 >= 0 && k3 < F) acc += bm * vb[(long long)(k3 - vlo) * F + x];
+            }
+            tb[(long long)yy * F + x] = acc;
+        }
+    }
+    __syncthreads();
+    const float lw0 = j >= 1 ? fd.lambda * fd.Wd[j - 1] : 0.f;
+    const float *cjm = j >= 1 ? c_plane(fd, params, j - 1) : cj;  // c_{j-1}
+    float *out = fd.starlet + (long long)(J + (j & 1)) * F * F;
+    for (int yy = warp; yy < Tr; yy += nwarp) {
+        const long long ro = (long long)(y0 + yy) * F;
+        const float *trow = tb + (long long)yy * F;
+        for (int x = lane; x < F; x += 32) {
+            const float acc = adj_1d(trow, x, F, s, 1);
+            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1) + acc;
+            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0) : tj;
+        }
+    }
+}
+
+bool starlet_field_banded(int F, int J) { return starlet_banded(F, J); }
+
+int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unbanded, const ChunkItem *chunks,
+                   int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {  // the band kernels take kBandSmemBytes of dynamic shared memory
+        cudaFuncSetAttribute(starlet_band_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_band_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        configured = true;
+    }
     int n = 0;
     const int grid = (n_chunks + kStarletChunks - 1) / kStarletChunks;
+    const dim3 bgrid((Fmax + kBandRows - 1) / kBandRows, n_fields);
     for (int j = 0; j <= Jmax - 2; ++j) {
-        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 0);
-        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 1);
-        n += 2;
+        starlet_band_fwd_kernel<<<bgrid, 256, kBandSmemBytes, st>>>(fields, params, l1_part, j);
+        ++n;
+        if (any_unbanded) {
+            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 0);
+            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 1);
+            n += 2;
+        }
     }
     for (int j = Jmax - 2; j >= 0; --j) {
-        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
-        starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 3);
-        n += 2;
+        starlet_band_adj_kernel<<<bgrid, 256, kBandSmemBytes, st>>>(fields, params, j);
+        ++n;
+        if (any_unbanded) {
+            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
+            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 3);
+            n += 2;
+        }
     }
     return n;
 }
