@@ -20,6 +20,8 @@
 //  * passes (fields too wide for the shared-memory budget): one launch per pass and level,
 //    every field of the table in 256-pixel chunks.
 // Fields deeper than a level skip it.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -301,8 +303,14 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unba
     int n = 0;
     const int grid = (n_chunks + kStarletChunks - 1) / kStarletChunks;
     const dim3 bgrid((Fmax + kBandRows - 1) / kBandRows, n_fields);
+    // shared memory of level j: (2 * 16 + 4 * 2^j) rows of the widest grid, at most the budget
+    // (which every banded field's deepest level fits, so its shallower levels fit too)
+    auto band_smem = [&](int j) {
+        const long long b = (2LL * kBandRows + 4LL * (1 << j)) * Fmax * (long long)sizeof(float);
+        return (int)std::min<long long>(b, kBandSmemBytes);
+    };
     for (int j = 0; j <= Jmax - 2; ++j) {
-        starlet_band_fwd_kernel<<<bgrid, 256, kBandSmemBytes, st>>>(fields, params, l1_part, j);
+        starlet_band_fwd_kernel<<<bgrid, 256, band_smem(j), st>>>(fields, params, l1_part, j);
         ++n;
         if (any_unbanded) {
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 0);
@@ -311,7 +319,7 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unba
         }
     }
     for (int j = Jmax - 2; j >= 0; --j) {
-        starlet_band_adj_kernel<<<bgrid, 256, kBandSmemBytes, st>>>(fields, params, j);
+        starlet_band_adj_kernel<<<bgrid, 256, band_smem(j), st>>>(fields, params, j);
         ++n;
         if (any_unbanded) {
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
