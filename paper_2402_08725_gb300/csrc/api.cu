@@ -334,7 +334,6 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
 }
 
 // Epochs per work item of the frequency-domain form (one accumulator per item).
-static const int kFftChunk = 8;
 
 // Phase groups of a tile: the most phases at once that fit in the block's threads and in
 // shared memory (one group always).

@@ -387,10 +387,16 @@ constexpr int kMaxG = 4;   // epochs per group (<= kBatch: a batch holds every e
 // reduced values per group: G (2 + 3 M) with G > 1 only when M <= 1
 constexpr int kRedVals = (kMaxG * 5 > 2 + 3 * kFftMaxSources) ? kMaxG * 5 : 2 + 3 * kFftMaxSources;
 static_assert(kMaxG <= kBatch && kFftMaxSources <= kBatch, "accumulators are indexed by batch element");
+static_assert(kRedVals <= kFftThreads / 32 && kFftThreads / 32 <= 32, "one warp per reduced value, one lane per warp");
 
 struct FxShared {
     double red[kRedVals][kFftThreads / 32];
-    float apar[kFftMaxSources];
+    // the work item's parameters: amplitudes a_{i,k}, epoch shifts delta_i, backgrounds gamma_i
+    // of its epochs, and the source positions c_k (loaded once per item)
+    float ia[kFftChunk * kFftMaxSources];
+    float id[2 * kFftChunk];
+    float ig[kFftChunk];
+    float ic[2 * kFftMaxSources];
     int item;
 };
 // Declared here rather than passed down, so that the per-size bodies (not inlined) still address
@@ -421,13 +427,20 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     // then [G][M][f][L] y-profiles, y-derivatives
     const int MfH = M * f * H, MfL = M * f * L;
     float2 *gsx = tw + L, *gsxd = gsx + G * MfH, *gsy = gsxd + G * MfH, *gsyd = gsy + G * MfL;
+    const float *hpar = params + fd.param_off;
+    const float *cpar = hpar + (long long)F * F + (long long)E * M;
     for (int n = tid; n < L; n += nt) {
         tw[n] = fd.fft_tw[n];
         TWL[n] = fd.fft_tw[(n % R2) * (n / R2)];
     }
+    {
+        const int n_ep = item.z - item.y;
+        for (int t = tid; t < n_ep * M; t += nt) sh.ia[t] = hpar[(long long)F * F + (long long)item.y * M + t];
+        for (int t = tid; t < 2 * n_ep; t += nt) sh.id[t] = cpar[2 * M + 2 * item.y + t];
+        for (int t = tid; t < n_ep; t += nt) sh.ig[t] = cpar[2 * M + 2 * E + item.y + t];
+        for (int t = tid; t < 2 * M; t += nt) sh.ic[t] = cpar[t];
+    }
     __syncthreads();
-    const float *hpar = params + fd.param_off;
-    const float *cpar = hpar + (long long)F * F + (long long)E * M;
     const float2 *hh = hhat_all + fd.fft_hhat_off;
     float2 *acc = acc_all + fd.fft_acc_off + (long long)item.w * nph * LHP;
     const float u0 = 0.5f * (float)(F - 1);
@@ -449,7 +462,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     for (int i0 = item.y; i0 < item.z; i0 += G) {
         const int Ge = min(G, item.z - i0);
         const float2 *kh = fd.fft_khat + (long long)i0 * nph * LHP;  // [g][phi][L][HP]
-        if (tid < Ge * M) sh.apar[tid] = hpar[(long long)F * F + (long long)i0 * M + tid];
+        const float *apar = sh.ia + (i0 - item.y) * M;  // a_{i0 + g, k} at g M + k
         // This group's kernel spectra go to L2 while the window spectra are computed, and the
         // next group's data and weights while this one computes (sizes are multiples of 16
         // bytes: L*H is even, and N*N*4 when N is even).  The next group's kernel spectra are not
@@ -473,8 +486,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                 const int len = isx ? H : L;
                 const int kf = r / len, kk = r - kf * len;
                 const int k = kf / f, phs = kf - k * f;
-                const float *dpar = cpar + 2 * M + 2 * (i0 + g);
-                const float cpos = cpar[2 * k + (isx ? 0 : 1)], dl = dpar[isx ? 0 : 1];
+                const float cpos = sh.ic[2 * k + (isx ? 0 : 1)], dl = sh.id[2 * (i0 - item.y + g) + (isx ? 0 : 1)];
                 const float cc = u0 + (float)f * (cpos + dl);
                 const int lo = (int)floorf(cc) - kWinLo;
                 int m0 = lo - phs;
@@ -524,7 +536,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                         sv[j] = row < L ? ldg4_hint(hh + ph * LHP + off, pol_last) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                     for (int k = 0; k < M; ++k) {
-                        const float a = sh.apar[k];
+                        const float a = apar[k];
                         const float2 *gxk = gsx + (k * f + phx) * H;
                         const float2 gx0 = gxk[c0], gx1 = has1 ? gxk[c1] : make_float2(0.f, 0.f);
                         const float2 agx0 = make_float2(a * gx0.x, a * gx0.y), agx1 = make_float2(a * gx1.x, a * gx1.y);
@@ -579,7 +591,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                             for (int k = 0; k < M; ++k) {
                                 const float2 pr = cmul(gsx[g * MfH + (k * f + phx) * H + tx],
                                                        gsy[g * MfL + (k * f + phy) * L + row]);
-                                const float a = sh.apar[g * M + k];
+                                const float a = apar[g * M + k];
                                 sv[j].x += a * pr.x;
                                 sv[j].y += a * pr.y;
                             }
@@ -603,7 +615,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
             double chi = 0.0, se = 0.0;
             if (g < Ge) {
                 const int i = i0 + g;
-                const float gam = cpar[2 * M + 2 * E + i];
+                const float gam = sh.ig[i - item.y];
                 const float bg = (float)(f * f) * gam;
                 const float *dd = fd.d + (long long)i * N * N, *ww = fd.w + (long long)i * N * N;
                 // two row pairs per iteration, so that 32 data and weight loads per lane are in
@@ -816,22 +828,27 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
             }
         }
         __syncthreads();
-        if (tid < Ge * nv) {
-            const int g = tid / nv, q = tid - g * nv;
+        // warp v (< Ge nv) sums value v's per-warp partials in a fixed shuffle tree
+        if (warp < Ge * nv) {
+            const int g = warp / nv, q = warp - g * nv;
             const int cnt = q < 2 ? nsub : nw;
-            double sum = 0.0;
-            for (int w = 0; w < cnt; ++w) sum += sh.red[tid][w];
-            const int i = i0 + g;
-            if (q == 0) {
-                chi_part[fd.tile_slot + i] = sum;
-            } else if (q == 1) {
-                se_part[fd.tile_slot + i] = sum;
-            } else {
-                const int k = (q - 2) / 3, which = (q - 2) - 3 * k;
-                const long long ps = fd.ps_slot + (long long)i * M + k;
-                const float sc = (float)(sum / ((double)L * (double)L));
-                if (which == 0) ps_da[ps] = sc;
-                else ps_du[2 * ps + which - 1] = sh.apar[g * M + k] * sc;
+            double sum = lane < cnt ? sh.red[warp][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+            if (lane == 0) {
+                const int i = i0 + g;
+                if (q == 0) {
+                    chi_part[fd.tile_slot + i] = sum;
+                } else if (q == 1) {
+                    se_part[fd.tile_slot + i] = sum;
+                } else {
+                    constexpr double kInvL2 = 1.0 / ((double)L * (double)L);
+                    const int k = (q - 2) / 3, which = (q - 2) - 3 * k;
+                    const long long ps = fd.ps_slot + (long long)i * M + k;
+                    const float sc = (float)(sum * kInvL2);
+                    if (which == 0) ps_da[ps] = sc;
+                    else ps_du[2 * ps + which - 1] = apar[g * M + k] * sc;
+                }
             }
         }
         __syncthreads();
