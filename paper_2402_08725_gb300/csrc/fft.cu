@@ -299,10 +299,22 @@ fft_hgrad_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ ff
     const int Hp = H + 1, LHp = L * Hp;  // global row pitch of the accumulators
     for (int idx = threadIdx.x; idx < LH; idx += blockDim.x) {
         const int ky = idx / H, kx = idx - ky * H;
-        float2 s = make_float2(0.f, 0.f);
+        // eight interleaved partial sums (chunk c into c mod 8), combined in a fixed order: eight
+        // loads in flight instead of one dependent chain
         const float2 *ac = acc_all + fd.fft_acc_off + (long long)ph * LHp + ky * Hp + kx;
-        for (int c = 0; c < n_chunks; ++c) s = cadd(s, ac[(long long)c * nph * LHp]);
-        A[idx] = s;
+        const long long cs = (long long)nph * LHp;
+        float2 p[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[q] = make_float2(0.f, 0.f);
+        int c = 0;
+        for (; c + 8 <= n_chunks; c += 8) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) p[q] = cadd(p[q], __ldg(&ac[(c + q) * cs]));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (c + q < n_chunks) p[q] = cadd(p[q], __ldg(&ac[(c + q) * cs]));
+        A[idx] = cadd(cadd(cadd(p[0], p[1]), cadd(p[2], p[3])), cadd(cadd(p[4], p[5]), cadd(p[6], p[7])));
     }
     __syncthreads();
     const int np = (N + 1) / 2;

@@ -152,7 +152,8 @@ __host__ __device__ constexpr int fx_r1(int L) {
 // Buffer layouts (float2 units), per epoch, each of the two buffers:
 //   row pairs       p * PX + x                 (p < np, x < L)
 //   row pass 1 out  p * PY + k1 * S + n2       (S odd: the R2-point loads of pass 2 are conflict-free)
-//   half spectrum   ky * H + kx                (H = L/2 + 1, odd since L % 4 == 0)
+//   half spectrum   ky * HP + kx               (kx < H = L/2 + 1; HP = H + 1 even, as in global
+//                                               memory, so that column pairs are 16-byte aligned)
 template <int L>
 struct Fx {
     static constexpr int R1 = fx_r1(L), R2 = L / R1, H = L / 2 + 1, LH = L * H;
@@ -170,7 +171,7 @@ __device__ __forceinline__ int fdivq(int r, float inv_d) { return __float2int_rd
 template <int L>
 __device__ void fx_fwd2d(float2 *A, float2 *B, int EB, int G, int np, float inv_np, int N, const float2 *TWL) {
     using P = Fx<L>;
-    constexpr int R1 = P::R1, R2 = P::R2, H = P::H, S = P::S, PX = P::PX, PY = P::PY;
+    constexpr int R1 = P::R1, R2 = P::R2, H = P::H, HP = P::HP, S = P::S, PX = P::PX, PY = P::PY;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int t = tid; t < G * np * R2; t += nt) {  // rows, pass 1
         const int n2 = t % R2, r = t / R2;
@@ -220,22 +221,22 @@ __device__ void fx_fwd2d(float2 *A, float2 *B, int EB, int G, int np, float inv_
             v[n1] = o;
         }
         dft<R1, false>(v);
-        float2 *dst = B + g * EB + n2 * H + kx;
+        float2 *dst = B + g * EB + n2 * HP + kx;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * R2 * H] = k1 == 0 ? v[0] : cmul(v[k1], TWL[k1 * R2 + n2]);
+        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * R2 * HP] = k1 == 0 ? v[0] : cmul(v[k1], TWL[k1 * R2 + n2]);
     }
     __syncthreads();
     for (int t = tid; t < G * H * R1; t += nt) {  // columns, pass 2
         const int kx = t % H, r = t / H;
         const int k1 = r % R1, g = r / R1;
-        const float2 *src = B + g * EB + k1 * R2 * H + kx;
+        const float2 *src = B + g * EB + k1 * R2 * HP + kx;
         float2 v[R2];
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2 * H];
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2 * HP];
         dft<R2, false>(v);
-        float2 *dst = A + g * EB + k1 * H + kx;
+        float2 *dst = A + g * EB + k1 * HP + kx;
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) dst[R1 * k2 * H] = v[k2];
+        for (int k2 = 0; k2 < R2; ++k2) dst[R1 * k2 * HP] = v[k2];
     }
     __syncthreads();
 }
@@ -245,39 +246,39 @@ __device__ void fx_fwd2d(float2 *A, float2 *B, int EB, int G, int np, float inv_
 template <int L>
 __device__ void fx_inv2d(float2 *A, float2 *B, int EB, int G, int np, float inv_np, int N, const float2 *TWL) {
     using P = Fx<L>;
-    constexpr int R1 = P::R1, R2 = P::R2, H = P::H, S = P::S, PX = P::PX, PY = P::PY;
+    constexpr int R1 = P::R1, R2 = P::R2, H = P::H, HP = P::HP, S = P::S, PX = P::PX, PY = P::PY;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int t = tid; t < G * H * R2; t += nt) {  // columns, pass 1
         const int kx = t % H, r = t / H;
         const int n2 = r % R2, g = r / R2;
-        const float2 *src = A + g * EB + n2 * H + kx;
+        const float2 *src = A + g * EB + n2 * HP + kx;
         float2 v[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[n1 * R2 * H];
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = src[n1 * R2 * HP];
         dft<R1, true>(v);
-        float2 *dst = B + g * EB + n2 * H + kx;
+        float2 *dst = B + g * EB + n2 * HP + kx;
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * R2 * H] = k1 == 0 ? v[0] : cmulc(v[k1], TWL[k1 * R2 + n2]);
+        for (int k1 = 0; k1 < R1; ++k1) dst[k1 * R2 * HP] = k1 == 0 ? v[0] : cmulc(v[k1], TWL[k1 * R2 + n2]);
     }
     __syncthreads();
     for (int t = tid; t < G * H * R1; t += nt) {  // columns, pass 2: rows y < 2 np only
         const int kx = t % H, r = t / H;
         const int k1 = r % R1, g = r / R1;
-        const float2 *src = B + g * EB + k1 * R2 * H + kx;
+        const float2 *src = B + g * EB + k1 * R2 * HP + kx;
         float2 v[R2];
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2 * H];
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = src[n2 * HP];
         dft<R2, true>(v);
-        float2 *dst = A + g * EB + k1 * H + kx;
+        float2 *dst = A + g * EB + k1 * HP + kx;
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2)
-            if (k1 + R1 * k2 < 2 * np) dst[R1 * k2 * H] = v[k2];
+            if (k1 + R1 * k2 < 2 * np) dst[R1 * k2 * HP] = v[k2];
     }
     __syncthreads();
     for (int t = tid; t < G * np * R2; t += nt) {  // merge rows 2p, 2p+1; rows pass 1
         const int n2 = t % R2, r = t / R2;
         const int g = fdivq(r, inv_np), p = r - g * np;
-        const float2 *r1 = A + g * EB + (2 * p) * H, *r2 = r1 + H;
+        const float2 *r1 = A + g * EB + (2 * p) * HP, *r2 = r1 + HP;
         float2 v[R1];
 #pragma unroll
         for (int n1 = 0; n1 < R1; ++n1) {
@@ -560,8 +561,8 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                 for (int j = 0; j < kPairRows; ++j) {
                     const int row = row0 + j * RP2;
                     if (row < L) {
-                        A[row * H + c0] = m0[j];
-                        if (has1) A[row * H + c1] = m1[j];
+                        // one 16-byte store of the pair (the pad column's value is zero)
+                        *reinterpret_cast<float4 *>(A + row * HP + c0) = make_float4(m0[j].x, m0[j].y, m1[j].x, m1[j].y);
                     }
                 }
             }
@@ -602,7 +603,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
 #pragma unroll
                 for (int j = 0; j < kBatch; ++j) {
                     const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
-                    if (row < L && g < Ge) A[g * EB + row * H + tx] = m[j];
+                    if (row < L && g < Ge) A[g * EB + row * HP + tx] = m[j];
                 }
             }
         }
@@ -716,7 +717,9 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                     for (int j = 0; j < kPairRows; ++j) {
                         const int row = row0 + j * RP2;
                         if (row < L) {
-                            const float2 e0 = A[row * H + c0], e1 = has1 ? A[row * H + c1] : make_float2(0.f, 0.f);
+                            // one 16-byte load of the pair; the pad slot holds no transform output
+                            const float4 e = *reinterpret_cast<const float4 *>(A + row * HP + c0);
+                            const float2 e0 = lo2(e), e1 = has1 ? hi2(e) : make_float2(0.f, 0.f);
                             const float2 G0 = cmulc(e0, lo2(kv[j])), G1 = cmulc(e1, hi2(kv[j]));
                             // the pad column of the accumulator stays zero
                             st4_hint(ap + row * HP,
@@ -773,7 +776,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                     for (int j = 0; j < kBatch; ++j) {
                         const int g = j & (G - 1), row = row0 + (j >> lgG) * RP;
                         if (row < L && g < Ge) {
-                            const float2 Gv = cmulc(A[g * EB + row * H + tx], kv[j]);
+                            const float2 Gv = cmulc(A[g * EB + row * HP + tx], kv[j]);
                             run = cadd(g == 0 ? av[j] : run, Gv);
                             if (g == Ge - 1) st_hint(ap + row * HP, run, last ? pol_first : pol_last);
                             if (M == 1) {
@@ -917,7 +920,7 @@ int fft_fixed_epoch_buffer(int L, int N) {
     const int S = (R2 & 1) ? R2 : R2 + 1;
     const int np = (N + 1) / 2;
     int eb = std::max(np * L, np * R1 * S);
-    eb = std::max(eb, L * (L / 2 + 1));
+    eb = std::max(eb, L * (L / 2 + 2));  // the spectrum, rows padded to an even pitch
     return (eb + 1) & ~1;  // keeps every buffer 16-byte aligned
 }
 
