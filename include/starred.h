@@ -260,6 +260,13 @@ sr_status sr_batch_profile(sr_batch *b, int enable);
  * Synchronises the batch's stream. */
 sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, double *adj_ms, double *fft_ms);
 
+/* Diagnostic, not from the paper: measured FP32 fused-multiply-add throughput of the current
+ * CUDA device in TFLOP/s (a register-resident FMA kernel on the legacy default stream, timed
+ * with events after a warm-up; synchronises the device's default stream).  It is the
+ * denominator of the direct form's roofline, whose tile kernels are bound by FP32 FMA issue.
+ * *tflops receives the figure; SR_ERR_CUDA if a CUDA call fails. */
+sr_status sr_measure_fp32_peak(double *tflops);
+
 /* Loss and gradient of one deconvolution field, allocating nothing.
  *
  * The paper has no counterpart to this call: it exists for callers that cannot

@@ -69,6 +69,7 @@ def _load():
         sig = {
             "orc_version": ([], i),
             "orc_max_threads": ([], i),
+            "orc_set_threads": ([i], None),
             "orc_conv_same": ([i, i, _dp, _dp, _dp], i),
             "orc_conv_same_adjoint": ([i, i, _dp, _dp, _dp], i),
             "orc_downsample": ([i, i, _dp, _dp], i),
@@ -112,6 +113,11 @@ def _check(rc: int, what: str):
 
 def max_threads() -> int:
     return int(_load().orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of later oracle calls (timing only; results do not depend on it)."""
+    _load().orc_set_threads(int(n))
 
 
 # --- building blocks -------------------------------------------------------

@@ -85,6 +85,16 @@ int orc_max_threads(void) {
 #endif
 }
 
+/* Threads of later calls (timing only: every reduction runs in a fixed order, so the results do
+   not depend on it). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* S: narrow-PSF convolution on the fine grid (Eq. 8 and Eq. 10, sec. 2.2).  */
 /* ------------------------------------------------------------------------- */

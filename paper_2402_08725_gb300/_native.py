@@ -73,6 +73,7 @@ PROTOTYPES = {
     "sr_batch_field_form": ([c_void_p, c_int], c_int),
     "sr_batch_profile": ([c_void_p, c_int], c_int),
     "sr_batch_profile_read": ([c_void_p, ctypes.POINTER(c_int), P_double, P_double, P_double], c_int),
+    "sr_measure_fp32_peak": ([P_double], c_int),
     "sr_loss_and_grad_noalloc": ([ctypes.POINTER(ProblemDesc), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p], c_int),
 }

@@ -287,3 +287,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp32_peak() -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s (sr_measure_fp32_peak)."""
+    lib = nat.load()
+    t = ctypes.c_double()
+    nat.check(lib.sr_measure_fp32_peak(ctypes.byref(t)), "sr_measure_fp32_peak")
+    return float(t.value)

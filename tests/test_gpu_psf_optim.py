@@ -205,3 +205,22 @@ def test_state_and_input_errors():
     assert ei.value.status == "SR_ERR_STATE"
     psf_prob.close()
     prob.close()
+
+
+@pytest.mark.gpu
+def test_measured_fp32_peak_is_physical():
+    """The FMA microbenchmark (the direct form's roofline denominator) lands between a quarter of
+    the nominal FP32 rate and just above it (SMs x 128 lanes x 2 FLOP x maximum SM clock)."""
+    import torch
+    from paper_2402_08725_gb300.binding import measure_fp32_peak
+    props = torch.cuda.get_device_properties(0)
+    clock_mhz = 2070.0
+    try:
+        import json, os
+        with open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "MEASURED_PEAKS.json")) as fh:
+            clock_mhz = float(json.load(fh).get("sm_max_mhz", clock_mhz))
+    except OSError:
+        pass
+    nominal = props.multi_processor_count * 128 * 2 * clock_mhz * 1e6 / 1e12
+    t = measure_fp32_peak()
+    assert 0.25 * nominal < t < 1.05 * nominal, (t, nominal)
