@@ -87,6 +87,10 @@ def _load():
             "orc_psf_model": ([i, i, i, _dp, _dp], i),
             "orc_psf_loss_grad": ([i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
             "orc_optim_step": ([i, ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.c_long, _dp, d, d, d, _dp, _dp], i),
+            "orc_philox4x64": ([ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64)], None),
+            "orc_normal": ([ctypes.c_uint64, ctypes.c_uint64], d),
+            "orc_noise_weights": ([i, i, i, i, i, _dp, _dp, i, ctypes.c_uint64, _dp, _dp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -264,3 +268,33 @@ def optim_step(kind, theta, g, m, v, t, lr, beta1, beta2, eps, lo, hi):
     rc = _load().orc_optim_step(int(kind), theta.size, _ptr(theta), _ptr(g), _ptr(m), _ptr(v), int(t), _ptr(lr),
                                 float(beta1), float(beta2), float(eps), _ptr(lo), _ptr(hi))
     _check(rc, "optim_step")
+
+
+# --- noise propagation (sec. 2.3, App. B) ------------------------------------
+
+def philox4x64(counter, key):
+    """One Philox4x64-10 block (Salmon et al. 2011): four 64-bit words."""
+    c = (ctypes.c_uint64 * 4)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in counter])
+    k = (ctypes.c_uint64 * 2)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in key])
+    out = (ctypes.c_uint64 * 4)()
+    _load().orc_philox4x64(c, k, out)
+    return [int(v) for v in out]
+
+
+def normal(seed: int, n: int) -> float:
+    """Standard normal number n of stream `seed` (Philox4x64-10 + Box-Muller on 24-bit uniforms)."""
+    return float(_load().orc_normal(int(seed), int(n)))
+
+
+def noise_weights(N, f, K, J, sigma, s1, n_real, seed):
+    """Monte Carlo starlet weights of sec. 2.3 from n_real realisations of S_1^T (C^)^-1 dd:
+    (W_scale [J-1], the pooled standard deviation of each detail scale, and W_map [J-1][fN][fN],
+    the standard deviation of each coefficient)."""
+    sigma = _f64(sigma).reshape(-1, N, N)
+    s1 = _f64(s1).reshape(K, K)
+    F = f * N
+    W = np.empty((J - 1, F, F))
+    Ws = np.empty(J - 1)
+    _check(_load().orc_noise_weights(int(N), int(f), int(K), int(J), int(sigma.shape[0]), _ptr(sigma), _ptr(s1),
+                                     int(n_real), ctypes.c_uint64(int(seed)), _ptr(W), _ptr(Ws)), "noise_weights")
+    return Ws, W

@@ -35,6 +35,7 @@
  *   Noise: w = 1/sigma^2 (Eq. 10: C diagonal); sigma = +inf masks a pixel (w = 0).
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -759,5 +760,114 @@ int orc_optim_step(int kind, long n, double *theta, const double *g, double *m, 
         if (th > hi[k]) th = hi[k];
         theta[k] = th;
     }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Noise propagation to the starlet coefficients (sec. 2.3, App. B).          */
+/* ------------------------------------------------------------------------- */
+
+/* Philox4x64-10 (Salmon, Moraes, Dror & Shaw 2011, "Parallel random numbers:
+ * as easy as 1, 2, 3"): ten rounds of two 64 x 64 -> 128-bit products on a
+ * four-word counter, the two-word key bumped by the Weyl constants between
+ * rounds.  One block: counter ctr, key key -> four 64-bit words. */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        const unsigned __int128 p0 = (unsigned __int128)M0 * c0, p1 = (unsigned __int128)M1 * c2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Standard normal number n of stream `seed`: block b = n / 4 of Philox4x64-10
+ * with counter (b, 0, 0, 0) and key (seed, 0); words (0, 1) and (2, 3) give
+ * two Box-Muller pairs from the uniforms u = ((w >> 40) + 1) 2^-24 in (0, 1]:
+ * z = sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b) for n mod 4 = (0, 1) and
+ * (2, 3).  (24-bit uniforms: every single-precision implementation of the
+ * same stream draws the same u exactly.) */
+double orc_normal(uint64_t seed, uint64_t n) {
+    const uint64_t ctr[4] = {n >> 2, 0, 0, 0}, key[2] = {seed, 0};
+    uint64_t w[4];
+    orc_philox4x64(ctr, key, w);
+    const int q = (int)(n & 3), pair = q >> 1;
+    const double ua = (double)((w[2 * pair] >> 40) + 1) * 0x1p-24;
+    const double ub = (double)((w[2 * pair + 1] >> 40) + 1) * 0x1p-24;
+    const double r = sqrt(-2.0 * log(ua));
+    return (q & 1) ? r * sin(2.0 * M_PI * ub) : r * cos(2.0 * M_PI * ub);
+}
+
+/* Starlet weights by Monte Carlo noise propagation (sec. 2.3): realisation r
+ * draws z_r on the fine grid (normal number r F^2 + u of the stream `seed`),
+ * forms (C^)^-1 dd = z / sigma^ with sigma^ the effective noise of the
+ * co-added epochs, sigma_eff(p)^-2 = sum_i sigma_i(p)^-2, replicated onto the
+ * f x f fine pixels of data pixel p (sigma = +inf masks a pixel), propagates it
+ * with S_1^T (the correlation with epoch 1's narrow PSF) and the starlet
+ * analysis.  Outputs, for each detail plane w_{j+1}, j = 0..J-2:
+ *   W_map [J-1][F][F]: the sample standard deviation (n - 1) over the n_real
+ *                      realisations of each coefficient;
+ *   W_scale [J-1]:     the sample standard deviation (n F^2 - 1) of all the
+ *                      plane's coefficients of all realisations, the one number
+ *                      per scale the prior of Eq. 6 takes.
+ * Either output may be NULL. */
+int orc_noise_weights(int N, int f, int K, int J, int E, const double *sigma, const double *s1, int n_real,
+                      uint64_t seed, double *W_map, double *W_scale) {
+    const int F = f * N;
+    if (N < 1 || f < 1 || K < 1 || !orc_starlet_valid(F, J) || n_real < 2 || E < 1) return ORC_ERR_SHAPE;
+    const size_t n = (size_t)F * F, nd = (size_t)(J - 1) * n;
+    double *isig = malloc(sizeof(double) * n), *x = malloc(sizeof(double) * n), *y = malloc(sizeof(double) * n);
+    double *planes = malloc(sizeof(double) * (size_t)J * n), *s1sum = calloc(nd, sizeof(double)),
+           *s2sum = calloc(nd, sizeof(double));
+    if (!isig || !x || !y || !planes || !s1sum || !s2sum) {
+        free(isig); free(x); free(y); free(planes); free(s1sum); free(s2sum);
+        return ORC_ERR_OOM;
+    }
+    for (int p = 0; p < N * N; ++p) {
+        double iv = 0.0;
+        for (int i = 0; i < E; ++i) {
+            const double sg = sigma[(size_t)i * N * N + p];
+            if (isfinite(sg)) iv += 1.0 / (sg * sg);
+        }
+        const double v = sqrt(iv);  /* 1 / sigma_eff */
+        const int py = p / N, px = p % N;
+        for (int a = 0; a < f; ++a)
+            for (int b = 0; b < f; ++b) isig[(size_t)(f * py + a) * F + (f * px + b)] = v;
+    }
+    for (int r = 0; r < n_real; ++r) {
+        for (size_t u = 0; u < n; ++u) x[u] = orc_normal(seed, (uint64_t)r * n + u) * isig[u];
+        orc_conv_same_adjoint(F, K, x, s1, y);
+        orc_starlet_analysis(F, J, y, planes);
+        for (size_t k = 0; k < nd; ++k) {
+            s1sum[k] += planes[k];
+            s2sum[k] += planes[k] * planes[k];
+        }
+    }
+    for (int j = 0; j < J - 1; ++j) {
+        double t1 = 0.0, t2 = 0.0;
+        for (size_t u = 0; u < n; ++u) {
+            const size_t k = (size_t)j * n + u;
+            t1 += s1sum[k];
+            t2 += s2sum[k];
+            if (W_map) {
+                const double mean = s1sum[k] / n_real;
+                const double var = (s2sum[k] - n_real * mean * mean) / (n_real - 1);
+                W_map[k] = sqrt(var > 0.0 ? var : 0.0);
+            }
+        }
+        if (W_scale) {
+            const double m = (double)n_real * (double)n, mean = t1 / m, var = (t2 - m * mean * mean) / (m - 1.0);
+            W_scale[j] = sqrt(var > 0.0 ? var : 0.0);
+        }
+    }
+    free(isig); free(x); free(y); free(planes); free(s1sum); free(s2sum);
     return ORC_OK;
 }
