@@ -267,6 +267,47 @@ sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, doubl
  * *tflops receives the figure; SR_ERR_CUDA if a CUDA call fails. */
 sr_status sr_measure_fp32_peak(double *tflops);
 
+/* Phase timings of one sr_noise_weights call: CUDA-event durations on its stream, summed over
+ * the batches of realisations. */
+typedef struct {
+    double draw_ms;     /* normal draws divided by sigma_eff */
+    double corr_ms;     /* the S_1^T correlation, the dominant kernel */
+    double starlet_ms;  /* starlet analysis with the per-coefficient sums */
+    double final_ms;    /* the final reductions */
+    int launches;       /* kernels the call launched */
+    int batch;          /* realisations per batch */
+} sr_noise_timing;
+
+/* Prior weights W by Monte Carlo noise propagation (sec. 2.3 and App. B): realisation r draws a
+ * standard normal field z_r on the F x F fine grid (F = f N), forms (C^)^-1 dd = z_r / sigma_eff
+ * with sigma_eff^-2 = sum_i sigma_i^-2 the co-added noise of the E epochs replicated over each
+ * f x f block (sigma = +inf masks a pixel of an epoch), applies S_1^T (the transpose of the
+ * zero-padded convolution with epoch 1's narrow PSF, i.e. a correlation) and the starlet
+ * analysis with J planes.
+ *   sigma_dev  float32 [E][N][N], device; each value > 0 or +inf;
+ *   s1_dev     float32 [K][K], device, origin (K/2, K/2), the narrow PSF of epoch 1 (or, for a
+ *              PSF fit, the kernel the pixel grid is convolved with);
+ *   n_real     realisations (>= 2; the paper uses 5000); seed selects the random stream:
+ *              normal number n is Philox4x64-10 block n/4 (counter (n/4, 0, 0, 0), key
+ *              (seed, 0)), words (0,1) and (2,3) giving two Box-Muller pairs (cos, sin) from the
+ *              24-bit uniforms ((w >> 40) + 1) 2^-24; realisation r takes numbers r F^2 ..
+ *              r F^2 + F^2 - 1 in row-major pixel order;
+ *   W_host     float32 [J-1], host, or NULL: per detail scale, the sample standard deviation of
+ *              all its coefficients of all realisations (the weights sr_set_weights takes);
+ *   W_map_dev  float32 [J-1][F][F], device, or NULL: per coefficient, the sample standard
+ *              deviation over the realisations; at least one of the two outputs is required;
+ *   timing     NULL, or receives the phase timings (the call then synchronises every batch).
+ * Arithmetic is FP32; the moments are accumulated in FP64 in a fixed order, so the result does
+ * not depend on the run.  The call allocates and frees its workspace (two F x F float buffers
+ * per realisation of a batch, at most 64 MB, plus 2 x S x (J-1) x F^2 doubles with S <= 16),
+ * orders its work on cuda_stream and synchronises it.  SR_ERR_SHAPE for bad sizes,
+ * SR_ERR_UNSUPPORTED for a K whose staging does not fit shared memory (K above about 500),
+ * SR_ERR_NONFINITE for a NaN or non-positive sigma or a non-finite s1, SR_ERR_OOM,
+ * SR_ERR_CUDA. */
+sr_status sr_noise_weights(int N, int f, int K, int J, int E, const float *sigma_dev, const float *s1_dev,
+                           int n_real, uint64_t seed, float *W_host, float *W_map_dev, sr_noise_timing *timing,
+                           void *cuda_stream);
+
 /* Loss and gradient of one deconvolution field, allocating nothing.
  *
  * The paper has no counterpart to this call: it exists for callers that cannot

@@ -824,11 +824,14 @@ int orc_noise_weights(int N, int f, int K, int J, int E, const double *sigma, co
     const int F = f * N;
     if (N < 1 || f < 1 || K < 1 || !orc_starlet_valid(F, J) || n_real < 2 || E < 1) return ORC_ERR_SHAPE;
     const size_t n = (size_t)F * F, nd = (size_t)(J - 1) * n;
-    double *isig = malloc(sizeof(double) * n), *x = malloc(sizeof(double) * n), *y = malloc(sizeof(double) * n);
-    double *planes = malloc(sizeof(double) * (size_t)J * n), *s1sum = calloc(nd, sizeof(double)),
-           *s2sum = calloc(nd, sizeof(double));
-    if (!isig || !x || !y || !planes || !s1sum || !s2sum) {
-        free(isig); free(x); free(y); free(planes); free(s1sum); free(s2sum);
+    /* realisations split into contiguous per-thread ranges with private sums, added in thread order */
+    int nt = omp_in_parallel() ? 1 : omp_get_max_threads();
+    if (nt > n_real) nt = n_real;
+    double *isig = malloc(sizeof(double) * n), *work = malloc(sizeof(double) * (size_t)nt * (2 + J) * n);
+    double *part1 = calloc((size_t)nt * nd, sizeof(double)), *part2 = calloc((size_t)nt * nd, sizeof(double));
+    double *s1sum = calloc(nd, sizeof(double)), *s2sum = calloc(nd, sizeof(double));
+    if (!isig || !work || !part1 || !part2 || !s1sum || !s2sum) {
+        free(isig); free(work); free(part1); free(part2); free(s1sum); free(s2sum);
         return ORC_ERR_OOM;
     }
     for (int p = 0; p < N * N; ++p) {
@@ -842,15 +845,27 @@ int orc_noise_weights(int N, int f, int K, int J, int E, const double *sigma, co
         for (int a = 0; a < f; ++a)
             for (int b = 0; b < f; ++b) isig[(size_t)(f * py + a) * F + (f * px + b)] = v;
     }
-    for (int r = 0; r < n_real; ++r) {
-        for (size_t u = 0; u < n; ++u) x[u] = orc_normal(seed, (uint64_t)r * n + u) * isig[u];
-        orc_conv_same_adjoint(F, K, x, s1, y);
-        orc_starlet_analysis(F, J, y, planes);
-        for (size_t k = 0; k < nd; ++k) {
-            s1sum[k] += planes[k];
-            s2sum[k] += planes[k] * planes[k];
+#pragma omp parallel num_threads(nt)
+    {
+        const int t = omp_get_thread_num(), T = omp_get_num_threads();
+        double *x = work + (size_t)t * (2 + J) * n, *y = x + n, *planes = y + n;
+        double *p1 = part1 + (size_t)t * nd, *p2 = part2 + (size_t)t * nd;
+        const int r0 = (int)((long)n_real * t / T), r1 = (int)((long)n_real * (t + 1) / T);
+        for (int r = r0; r < r1; ++r) {
+            for (size_t u = 0; u < n; ++u) x[u] = orc_normal(seed, (uint64_t)r * n + u) * isig[u];
+            orc_conv_same_adjoint(F, K, x, s1, y);
+            orc_starlet_analysis(F, J, y, planes);
+            for (size_t k = 0; k < nd; ++k) {
+                p1[k] += planes[k];
+                p2[k] += planes[k] * planes[k];
+            }
         }
     }
+    for (int t = 0; t < nt; ++t)
+        for (size_t k = 0; k < nd; ++k) {
+            s1sum[k] += part1[(size_t)t * nd + k];
+            s2sum[k] += part2[(size_t)t * nd + k];
+        }
     for (int j = 0; j < J - 1; ++j) {
         double t1 = 0.0, t2 = 0.0;
         for (size_t u = 0; u < n; ++u) {
@@ -868,6 +883,6 @@ int orc_noise_weights(int N, int f, int K, int J, int E, const double *sigma, co
             W_scale[j] = sqrt(var > 0.0 ? var : 0.0);
         }
     }
-    free(isig); free(x); free(y); free(planes); free(s1sum); free(s2sum);
+    free(isig); free(work); free(part1); free(part2); free(s1sum); free(s2sum);
     return ORC_OK;
 }

@@ -35,6 +35,11 @@ class Layout(ctypes.Structure):
                 ("total", c_size_t)]
 
 
+class NoiseTiming(ctypes.Structure):
+    _fields_ = [("draw_ms", c_double), ("corr_ms", c_double), ("starlet_ms", c_double), ("final_ms", c_double),
+                ("launches", c_int), ("batch", c_int)]
+
+
 class OptimCfg(ctypes.Structure):
     _fields_ = [("kind", c_int), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
                 ("lr", c_float * SR_MAX_GROUPS)]
@@ -74,6 +79,8 @@ PROTOTYPES = {
     "sr_batch_profile": ([c_void_p, c_int], c_int),
     "sr_batch_profile_read": ([c_void_p, ctypes.POINTER(c_int), P_double, P_double, P_double], c_int),
     "sr_measure_fp32_peak": ([P_double], c_int),
+    "sr_noise_weights": ([c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int, ctypes.c_uint64, P_float,
+                          c_void_p, ctypes.POINTER(NoiseTiming), c_void_p], c_int),
     "sr_loss_and_grad_noalloc": ([ctypes.POINTER(ProblemDesc), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p], c_int),
 }

@@ -295,3 +295,27 @@ def measure_fp32_peak() -> float:
     t = ctypes.c_double()
     nat.check(lib.sr_measure_fp32_peak(ctypes.byref(t)), "sr_measure_fp32_peak")
     return float(t.value)
+
+
+def noise_weights(N: int, f: int, K: int, J: int, sigma: torch.Tensor, s1: torch.Tensor, n_real: int, seed: int,
+                  want_map: bool = True, timing: bool = False, stream=None):
+    """Monte Carlo prior weights of sec. 2.3 (sr_noise_weights) from sigma [E][N][N] and the
+    narrow PSF s1 [K][K], both float32 CUDA tensors.  Returns (W_scale as a numpy float32 [J-1],
+    W_map as a CUDA tensor [J-1][fN][fN] or None, the phase timings as a dict or None)."""
+    lib = nat.load()
+    E = sigma.numel() // (N * N)
+    sp = _cuda_f32(sigma, E * N * N, "sigma")
+    kp = _cuda_f32(s1, K * K, "s1")
+    F = f * N
+    W = np.zeros(J - 1, dtype=np.float32)
+    W_map = torch.empty((J - 1, F, F), dtype=torch.float32, device=sigma.device) if want_map else None
+    tm = nat.NoiseTiming() if timing else None
+    nat.check(lib.sr_noise_weights(N, f, K, J, E, sp, kp, int(n_real), ctypes.c_uint64(int(seed) & (2**64 - 1)),
+                                   W.ctypes.data_as(nat.P_float),
+                                   ctypes.c_void_p(W_map.data_ptr()) if W_map is not None else None,
+                                   ctypes.byref(tm) if tm is not None else None, _stream_ptr(stream)),
+              "sr_noise_weights")
+    times = None
+    if tm is not None:
+        times = {k: getattr(tm, k) for k, _ in nat.NoiseTiming._fields_}
+    return W, W_map, times

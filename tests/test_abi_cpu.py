@@ -74,6 +74,26 @@ def test_null_arguments(lib):
     assert lib.sr_loss_and_grad(None, None, None, None, None) == 1
 
 
+def test_noise_weights_checks_arguments_before_device_use(lib):
+    """sr_noise_weights validates pointers and sizes before any CUDA call (the dummy pointers
+    below are never dereferenced)."""
+    buf = (ctypes.c_float * 16)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    W = (ctypes.c_float * 8)()
+    Wp = ctypes.cast(W, nat.P_float)
+    call = lambda N, f, K, J, E, sg, s1, n, Wh, Wm: lib.sr_noise_weights(N, f, K, J, E, sg, s1, n, 0, Wh, Wm,
+                                                                          None, None)
+    assert call(16, 2, 5, 3, 1, None, p, 10, Wp, None) == 1          # no sigma
+    assert call(16, 2, 5, 3, 1, p, p, 10, None, None) == 1           # no output
+    assert call(16, 2, 5, 7, 1, p, p, 10, Wp, None) == 2             # 2 * 2^5 > F - 1
+    assert call(16, 2, 5, 1, 1, p, p, 10, Wp, None) == 2             # J < 2
+    assert call(16, 2, 5, 3, 1, p, p, 1, Wp, None) == 2              # one realisation
+    assert call(0, 2, 5, 3, 1, p, p, 10, Wp, None) == 2
+    assert call(16, 2, 0, 3, 1, p, p, 10, Wp, None) == 2
+    assert call(16, 2, 5, 3, 0, p, p, 10, Wp, None) == 2
+    assert b"sr_noise_weights" in lib.sr_last_error()
+
+
 def test_struct_layouts_match_c(tmp_path):
     """ctypes mirrors of the header's structs have the C compiler's sizes and offsets."""
     src = tmp_path / "layout.c"
@@ -82,8 +102,9 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "starred.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sr_problem_desc), offsetof(sr_problem_desc, lambda),
-         offsetof(sr_problem_desc, conv_mode), sizeof(sr_layout), offsetof(sr_layout, total), sizeof(sr_optim_cfg));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sr_problem_desc), offsetof(sr_problem_desc, lambda),
+         offsetof(sr_problem_desc, conv_mode), sizeof(sr_layout), offsetof(sr_layout, total), sizeof(sr_optim_cfg),
+         sizeof(sr_noise_timing), offsetof(sr_noise_timing, batch));
   return 0;
 }
 """)
@@ -91,4 +112,5 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [ctypes.sizeof(nat.ProblemDesc), nat.ProblemDesc.lam.offset, nat.ProblemDesc.conv_mode.offset,
-                    ctypes.sizeof(nat.Layout), nat.Layout.total.offset, ctypes.sizeof(nat.OptimCfg)]
+                    ctypes.sizeof(nat.Layout), nat.Layout.total.offset, ctypes.sizeof(nat.OptimCfg),
+                    ctypes.sizeof(nat.NoiseTiming), nat.NoiseTiming.batch.offset]
