@@ -94,39 +94,73 @@ __global__ void __launch_bounds__(256) noise_draw_kernel(const float *__restrict
 //
 // y[v] = sum_{qy,qx} s[qy][qx] x[vy + qy - o][vx + qx - o]   (o = K/2; x = 0 outside the grid)
 //
-// A block of kCorrWarps warps computes a TY x TX tile of one realisation; lane l of warp w owns
-// rows w*RY .. w*RY+RY-1 and columns 4l .. 4l+3.  The kernel rows are taken KC at a time: the x
-// rows the chunk needs ((TY + KC - 1) x (TX + KP), zero-filled outside the grid) and the chunk's
-// kernel rows, padded by RY - 1 zero rows on both sides, are staged in shared memory.  For x row
-// r of the thread's window, output row i uses kernel row r - i: one float4 of x (conflict-free,
-// consecutive lanes read consecutive 16 bytes) and RY broadcast float4s of s feed 16 RY FMAs.
+// A block of kCorrWarps warps computes a TY x TX tile of one realisation.  Lane l of warp w
+// owns output rows w*2*RY + (l/16)*RY + i (i < RY) and the two column groups 4(l%16) + j and
+// 64 + 4(l%16) + j (j < 4).  The kernel rows are taken KC at a time (KC >= RY): the x rows the
+// chunk needs ((TY + KC - 1) x (TX + KP), zero-filled outside the grid) and the chunk's kernel
+// rows (zero beyond K) are staged in shared memory.  For x row r of the thread's window, output
+// row i uses kernel row r - i, so rows r < RY - 1 and r >= KC feed only part of the RY outputs:
+// corr_row takes the range of i as template arguments and no FMA is spent on a missing row.
+// Per group of four kernel columns, two float4 of x (a quarter-warp reads 128 consecutive
+// bytes: no bank conflict) and one broadcast float4 of s per output row feed 32 FMAs per row;
+// the FMAs are ordered by kernel column so that consecutive ones share their s operand.
 
-constexpr int kCorrRY = 8;
+constexpr int kCorrRY = 4;
 constexpr int kCorrWarps = 4;
-constexpr int kCorrTY = kCorrRY * kCorrWarps;  // 32 output rows per block
-constexpr int kCorrTX = 128;                   // 32 lanes x 4 columns
+constexpr int kCorrTY = 2 * kCorrRY * kCorrWarps;  // 32 output rows per block
+constexpr int kCorrTX = 128;                       // 16 column groups x 2 x 4 columns
 constexpr int kCorrThreads = 32 * kCorrWarps;
+constexpr int kCorrMinBlocks = 3;                  // blocks per SM the chunk size aims for
 
 size_t corr_smem_bytes(int KP, int KC) {
-    return sizeof(float) * ((size_t)(kCorrTY + KC - 1) * (kCorrTX + KP) + (size_t)(KC + 2 * (kCorrRY - 1)) * KP);
+    return sizeof(float) * ((size_t)(kCorrTY + KC - 1) * (kCorrTX + KP) + (size_t)KC * KP);
 }
 
-__global__ void __launch_bounds__(kCorrThreads, 2)
+// x row r of the window against kernel rows r - i for i in [ILO, IHI)
+template <int ILO, int IHI>
+__device__ __forceinline__ void corr_row(float (&acc)[kCorrRY][2][4], const float4 *__restrict__ xp,
+                                         const float *__restrict__ ss, int r, int KP) {
+    const int G = KP / 4;
+    float4 A0 = xp[0], A1 = xp[16];
+#pragma unroll 2
+    for (int g = 0; g < G; ++g) {
+        const float4 B0 = xp[g + 1], B1 = xp[g + 17];
+        const float xa[2][8] = {{A0.x, A0.y, A0.z, A0.w, B0.x, B0.y, B0.z, B0.w},
+                                {A1.x, A1.y, A1.z, A1.w, B1.x, B1.y, B1.z, B1.w}};
+#pragma unroll
+        for (int i = ILO; i < IHI; ++i) {
+            const float4 sv = reinterpret_cast<const float4 *>(ss + (size_t)(r - i) * KP)[g];
+            const float se[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][h][j] = fmaf(se[e], xa[h][j + e], acc[i][h][j]);
+        }
+        A0 = B0;
+        A1 = B1;
+    }
+}
+
+__global__ void __launch_bounds__(kCorrThreads, kCorrMinBlocks)
     noise_corr_kernel(const float *__restrict__ x, const float *__restrict__ s, int F, int K, int KP, int KC,
                       float *__restrict__ y) {
+    static_assert(kCorrRY == 4, "the head and tail rows below are written out for RY = 4");
     extern __shared__ float4 corr_sm4[];
-    const int XR = kCorrTY + KC - 1, XW = kCorrTX + KP, SR = KC + 2 * (kCorrRY - 1);
+    const int XR = kCorrTY + KC - 1, XW = kCorrTX + KP;
     float *xs = reinterpret_cast<float *>(corr_sm4);
     float *ss = xs + (size_t)XR * XW;
     const int b = blockIdx.z, ty0 = blockIdx.y * kCorrTY, tx0 = blockIdx.x * kCorrTX;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, o = K / 2;
+    const int row0 = warp * 2 * kCorrRY + (lane >> 4) * kCorrRY, col0 = 4 * (lane & 15);
     const float *xb = x + (size_t)b * F * F;
 
-    float acc[kCorrRY][4];
+    float acc[kCorrRY][2][4];
 #pragma unroll
     for (int i = 0; i < kCorrRY; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc[i][0][j] = acc[i][1][j] = 0.f;
 
     for (int q0 = 0; q0 < K; q0 += KC) {
         __syncthreads();
@@ -135,54 +169,33 @@ __global__ void __launch_bounds__(kCorrThreads, 2)
             const int gy = ty0 - o + q0 + t, gx = tx0 - o + c;
             xs[idx] = (gy >= 0 && gy < F && gx >= 0 && gx < F) ? xb[(size_t)gy * F + gx] : 0.f;
         }
-        for (int idx = threadIdx.x; idx < SR * KP; idx += kCorrThreads) {
-            const int p = idx / KP, qx = idx - p * KP, qy = p - (kCorrRY - 1), q = q0 + qy;
-            ss[idx] = (qy >= 0 && qy < KC && q < K && qx < K) ? s[(size_t)q * K + qx] : 0.f;
+        for (int idx = threadIdx.x; idx < KC * KP; idx += kCorrThreads) {
+            const int qy = idx / KP, qx = idx - qy * KP, q = q0 + qy;
+            ss[idx] = (q < K && qx < K) ? s[(size_t)q * K + qx] : 0.f;
         }
         __syncthreads();
-        const int G = KP / 4;
-        const float *xrow = xs + (size_t)warp * kCorrRY * XW + 4 * lane;
-        for (int r = 0; r < kCorrRY + KC - 1; ++r) {
-            const float4 *xp = reinterpret_cast<const float4 *>(xrow + (size_t)r * XW);
-            const float4 *sp = reinterpret_cast<const float4 *>(ss + (size_t)(r + kCorrRY - 1) * KP);
-            float4 A = xp[0];
-#pragma unroll 2
-            for (int g = 0; g < G; ++g) {
-                const float4 Bv = xp[g + 1];
-#pragma unroll
-                for (int i = 0; i < kCorrRY; ++i) {
-                    const float4 sv = sp[g - i * G];
-                    acc[i][0] = fmaf(sv.x, A.x, acc[i][0]);
-                    acc[i][0] = fmaf(sv.y, A.y, acc[i][0]);
-                    acc[i][0] = fmaf(sv.z, A.z, acc[i][0]);
-                    acc[i][0] = fmaf(sv.w, A.w, acc[i][0]);
-                    acc[i][1] = fmaf(sv.x, A.y, acc[i][1]);
-                    acc[i][1] = fmaf(sv.y, A.z, acc[i][1]);
-                    acc[i][1] = fmaf(sv.z, A.w, acc[i][1]);
-                    acc[i][1] = fmaf(sv.w, Bv.x, acc[i][1]);
-                    acc[i][2] = fmaf(sv.x, A.z, acc[i][2]);
-                    acc[i][2] = fmaf(sv.y, A.w, acc[i][2]);
-                    acc[i][2] = fmaf(sv.z, Bv.x, acc[i][2]);
-                    acc[i][2] = fmaf(sv.w, Bv.y, acc[i][2]);
-                    acc[i][3] = fmaf(sv.x, A.w, acc[i][3]);
-                    acc[i][3] = fmaf(sv.y, Bv.x, acc[i][3]);
-                    acc[i][3] = fmaf(sv.z, Bv.y, acc[i][3]);
-                    acc[i][3] = fmaf(sv.w, Bv.z, acc[i][3]);
-                }
-                A = Bv;
-            }
-        }
+        const float *xrow = xs + (size_t)row0 * XW + col0;
+        auto xp = [&](int r) { return reinterpret_cast<const float4 *>(xrow + (size_t)r * XW); };
+        corr_row<0, 1>(acc, xp(0), ss, 0, KP);
+        corr_row<0, 2>(acc, xp(1), ss, 1, KP);
+        corr_row<0, 3>(acc, xp(2), ss, 2, KP);
+        for (int r = kCorrRY - 1; r < KC; ++r) corr_row<0, kCorrRY>(acc, xp(r), ss, r, KP);
+        corr_row<1, 4>(acc, xp(KC), ss, KC, KP);
+        corr_row<2, 4>(acc, xp(KC + 1), ss, KC + 1, KP);
+        corr_row<3, 4>(acc, xp(KC + 2), ss, KC + 2, KP);
     }
     float *yb = y + (size_t)b * F * F;
 #pragma unroll
     for (int i = 0; i < kCorrRY; ++i) {
-        const int vy = ty0 + warp * kCorrRY + i;
+        const int vy = ty0 + row0 + i;
         if (vy >= F) break;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int vx = tx0 + 4 * lane + j;
-            if (vx < F) yb[(size_t)vy * F + vx] = acc[i][j];
-        }
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int vx = tx0 + 64 * h + col0 + j;
+                if (vx < F) yb[(size_t)vy * F + vx] = acc[i][h][j];
+            }
     }
 }
 
@@ -220,7 +233,29 @@ __global__ void __launch_bounds__(256) noise_col_stats_kernel(float *__restrict_
     const long long o_m2 = (long long)reflect(yy - 2 * step, F) * F + xx, o_p2 = (long long)reflect(yy + 2 * step, F) * F + xx;
     const long long o_m1 = (long long)reflect(yy - step, F) * F + xx, o_p1 = (long long)reflect(yy + step, F) * F + xx;
     double s1 = 0.0, s2 = 0.0;
-    for (int b = b0; b < b1; ++b) {
+    int b = b0;
+    for (; b + 4 <= b1; b += 4) {  // four realisations' loads issued before their arithmetic
+        float tv[4][5], cv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float *tb = t + (b + k) * FF;
+            tv[k][0] = tb[o_m2];
+            tv[k][1] = tb[o_m1];
+            tv[k][2] = tb[u];
+            tv[k][3] = tb[o_p1];
+            tv[k][4] = tb[o_p2];
+            cv[k] = c[(b + k) * FF + u];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float cn = kH0 * (tv[k][0] + tv[k][4]) + kH1 * (tv[k][1] + tv[k][3]) + kH2 * tv[k][2];
+            const float w = cv[k] - cn;
+            c[(b + k) * FF + u] = cn;
+            s1 += (double)w;
+            s2 += (double)w * (double)w;
+        }
+    }
+    for (; b < b1; ++b) {
         const float *tb = t + b * FF;
         const float cn = kH0 * (tb[o_m2] + tb[o_p2]) + kH1 * (tb[o_m1] + tb[o_p1]) + kH2 * tb[u];
         float *cb = c + b * FF + u;
@@ -349,18 +384,18 @@ extern "C" sr_status sr_noise_weights(int N, int f, int K, int J, int E, const f
     SR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     SR_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    // kernel rows per chunk: the largest that lets two blocks share an SM (1 KB reserved per
-    // block), else the largest that fits one block
+    // kernel rows per chunk (at least RY; rows beyond K are zero): the largest that lets
+    // kCorrMinBlocks blocks share an SM (1 KB reserved per block), else the largest that fits one
     int KC = 0;
     for (int kc : {64, 32, 16, 8})
-        if (2 * (corr_smem_bytes(KP, std::min(kc, K)) + 1024) <= (size_t)per_sm) {
-            KC = std::min(kc, K);
+        if (kCorrMinBlocks * (corr_smem_bytes(KP, std::max(std::min(kc, K), kCorrRY)) + 1024) <= (size_t)per_sm) {
+            KC = std::max(std::min(kc, K), kCorrRY);
             break;
         }
     if (!KC)
-        for (int kc : {16, 8})
-            if (corr_smem_bytes(KP, std::min(kc, K)) <= (size_t)optin) {
-                KC = std::min(kc, K);
+        for (int kc : {32, 16, 8})
+            if (corr_smem_bytes(KP, std::max(std::min(kc, K), kCorrRY)) <= (size_t)optin) {
+                KC = std::max(std::min(kc, K), kCorrRY);
                 break;
             }
     if (!KC) {
