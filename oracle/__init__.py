@@ -87,6 +87,8 @@ def _load():
             "orc_psf_model": ([i, i, i, _dp, _dp], i),
             "orc_psf_loss_grad": ([i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
             "orc_optim_step": ([i, ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.c_long, _dp, d, d, d, _dp, _dp], i),
+            "orc_pts_prior": ([i, i, i, i, i, d, _dp, _dp, _dp, _dp], i),
+            "orc_lambda_pts_estimate": ([i, i, i, i, i, d, _dp, _dp, _dp], i),
             "orc_philox4x64": ([ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64)], None),
             "orc_normal": ([ctypes.c_uint64, ctypes.c_uint64], d),
@@ -224,6 +226,26 @@ def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, n
 
 
 # --- PSF reconstruction (Eq. 2-4, 7) ----------------------------------------
+
+def pts_prior(E, N, f, M, J, lam_pts, W, params, grad=True):
+    """Point-source prior of Eq. 11 (third term): (value, gradient over the packed deconvolution
+    parameters, zero outside the a and c blocks)."""
+    P = _f64(params)
+    Wv = _f64(W)
+    v = ctypes.c_double()
+    g = np.zeros_like(P) if grad else None
+    _check(_load().orc_pts_prior(int(E), int(N), int(f), int(M), int(J), float(lam_pts), _ptr(Wv), _ptr(P),
+                                 ctypes.byref(v), _ptr(g) if grad else None), "pts_prior")
+    return v.value, g
+
+
+def lambda_pts_estimate(E, N, f, M, J, lam, W, params) -> float:
+    """lambda_pts from a model by the ratio of App. C."""
+    out = ctypes.c_double()
+    _check(_load().orc_lambda_pts_estimate(int(E), int(N), int(f), int(M), int(J), float(lam), _ptr(_f64(W)),
+                                           _ptr(_f64(params)), ctypes.byref(out)), "lambda_pts_estimate")
+    return out.value
+
 
 def moffat(F: int, alpha: float, beta: float):
     m, da, db = np.empty((F, F)), np.empty((F, F)), np.empty((F, F))

@@ -507,6 +507,101 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
     return rc;
 }
 
+/* Point-source prior, the third term of Eq. 11 (sec. 2.2):
+ *   lambda_pts || W o Phi^T sum_k <a_k> r_k ||_1,   <a_k> = (1/E) sum_i a_ki,
+ * with r_k the unit Gaussian of Eq. 1 at the source's centre c_k (no per-epoch shift: the
+ * term regularises the mean point-source image).  *value receives the term; when grad is not
+ * NULL its gradient is ADDED to the a and c blocks of grad (packed deconvolution layout):
+ *   d/da_ki = (1/E) sum_u G[u] r_k[u],
+ *   d/dc_k  = <a_k> sum_u G[u] d r_k[u] / d c_k,  d r_k / d c_k = f (u - centre_k) / s^2 r_k,
+ * G = Phi (lambda_pts W o sign(Phi^T P)) the prior's gradient with respect to the image P. */
+int orc_pts_prior(int E, int N, int f, int M, int J, double lam_pts, const double *W, const double *params,
+                  double *value, double *grad) {
+    if (E <= 0 || N <= 0 || f <= 0 || M < 0) return ORC_ERR_SHAPE;
+    const int F = f * N;
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t oh, oa, oc, od, og, tot;
+    deconv_offsets(E, N, f, M, &oh, &oa, &oc, &od, &og, &tot);
+    const size_t n = (size_t)F * F;
+    double *P = calloc(n, sizeof(double)), *G = malloc(sizeof(double) * n), *abar = calloc((size_t)M + 1, sizeof(double));
+    double *zero = calloc(2, sizeof(double));
+    if (!P || !G || !abar || !zero) { free(P); free(G); free(abar); free(zero); return ORC_ERR_OOM; }
+    for (int k = 0; k < M; ++k) {
+        for (int i = 0; i < E; ++i) abar[k] += params[oa + (size_t)i * M + k];
+        abar[k] /= E;
+        double ux, uy;
+        source_centre(F, f, params + oc, zero, k, 0, &ux, &uy);
+        orc_add_gaussian(F, abar[k], ux, uy, P);
+    }
+    int rc = orc_starlet_prior(F, J, lam_pts, W, P, value, grad ? G : NULL);
+    if (rc == ORC_OK && grad) {
+        const double s2 = gauss_sigma() * gauss_sigma();
+        for (int k = 0; k < M; ++k) {
+            double ux, uy;
+            source_centre(F, f, params + oc, zero, k, 0, &ux, &uy);
+            double sa = 0.0, sx = 0.0, sy = 0.0;
+            for (int vy = 0; vy < F; ++vy)
+                for (int vx = 0; vx < F; ++vx) {
+                    const double g = gauss2(vx - ux, vy - uy), Gv = G[(size_t)vy * F + vx];
+                    sa += Gv * g;
+                    sx += Gv * g * (vx - ux) / s2;
+                    sy += Gv * g * (vy - uy) / s2;
+                }
+            for (int i = 0; i < E; ++i) grad[oa + (size_t)i * M + k] += sa / E;
+            grad[oc + 2 * k + 0] += abar[k] * f * sx;
+            grad[oc + 2 * k + 1] += abar[k] * f * sy;
+        }
+    }
+    free(P); free(G); free(abar); free(zero);
+    return rc;
+}
+
+/* Weighted L1 norm of the detail planes, sum_j W_j || (Phi^T x)_j ||_1. */
+static int wl1(int F, int J, const double *W, const double *x, double *out) {
+    return orc_starlet_prior(F, J, 1.0, W, x, out, NULL);
+}
+
+/* Estimate of lambda_pts from a model (App. C):
+ *   lambda_pts = lambda (|| W o Phi^T fbar ||_1 - || W o Phi^T h ||_1) / sum_k <a_k> || W o Phi^T r_k ||_1,
+ * fbar = (1/E) sum_i f_i the mean of the epochs' fine images f_i = h + sum_k a_ki r_k(c_k + delta_i)
+ * (Eq. 9), r_k in the denominator the unit Gaussian at c_k.  The printed formula also multiplies
+ * the second norm by lambda, which leaves the difference without a consistent unit; it is read
+ * without that factor.  A zero denominator (no point-source flux) gives 0. */
+int orc_lambda_pts_estimate(int E, int N, int f, int M, int J, double lam, const double *W, const double *params,
+                            double *out) {
+    if (E <= 0 || N <= 0 || f <= 0 || M < 0) return ORC_ERR_SHAPE;
+    const int F = f * N;
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t oh, oa, oc, od, og, tot;
+    deconv_offsets(E, N, f, M, &oh, &oa, &oc, &od, &og, &tot);
+    const size_t n = (size_t)F * F;
+    double *fbar = malloc(sizeof(double) * n), *r = malloc(sizeof(double) * n), *zero = calloc(2, sizeof(double));
+    if (!fbar || !r || !zero) { free(fbar); free(r); free(zero); return ORC_ERR_OOM; }
+    memcpy(fbar, params + oh, sizeof(double) * n);
+    for (int i = 0; i < E; ++i)
+        for (int k = 0; k < M; ++k) {
+            double ux, uy;
+            source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
+            orc_add_gaussian(F, params[oa + (size_t)i * M + k] / E, ux, uy, fbar);
+        }
+    double l1_f = 0.0, l1_h = 0.0, den = 0.0;
+    int rc = wl1(F, J, W, fbar, &l1_f);
+    if (!rc) rc = wl1(F, J, W, params + oh, &l1_h);
+    for (int k = 0; k < M && !rc; ++k) {
+        double abar = 0.0, l1_r = 0.0, ux, uy;
+        for (int i = 0; i < E; ++i) abar += params[oa + (size_t)i * M + k];
+        abar /= E;
+        memset(r, 0, sizeof(double) * n);
+        source_centre(F, f, params + oc, zero, k, 0, &ux, &uy);
+        orc_add_gaussian(F, 1.0, ux, uy, r);
+        rc = wl1(F, J, W, r, &l1_r);
+        den += abar * l1_r;
+    }
+    if (!rc) *out = den != 0.0 ? lam * (l1_f - l1_h) / den : 0.0;
+    free(fbar); free(r); free(zero);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------- */
 /* PSF reconstruction: Eq. 2 (Moffat + pixel grid), Eq. 3, Eq. 4, Eq. 7      */
 /* ------------------------------------------------------------------------- */
