@@ -174,6 +174,29 @@ sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device);
  * SR_ERR_NONFINITE otherwise); the array may be reused when the call returns. */
 sr_status sr_set_weights(sr_problem *p, const float *W);
 
+/* Point-source prior, the third term of Eq. 11 (sec. 2.2):
+ *   lambda_pts || W o Phi^T sum_k <a_k> r_k ||_1,
+ * <a_k> = (1/E) sum_i a_ki the mean amplitude of source k over the epochs, r_k the unit Gaussian
+ * of Eq. 1 at its centre c_k (no per-epoch shift), W the prior weights of sr_set_weights.  DECONV
+ * only (SR_ERR_STATE otherwise); lambda_pts finite and >= 0 (SR_ERR_ARG).  The default is 0 and
+ * the term is then not evaluated.  The first non-zero value allocates the term's buffers and adds
+ * it to the problem's evaluation (an existing optimiser state carries over); later values, zero
+ * included, only change its weights, also inside captured optimiser steps.  A batch created
+ * before a member's first non-zero value returns SR_ERR_STATE until it is re-created.  The plain
+ * form (SR_CONV_PLAIN) evaluates lambda_pts = 0 only (SR_ERR_UNSUPPORTED at its next evaluation). */
+sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts);
+
+/* lambda_pts from a model, by the ratio of App. C:
+ *   lambda (|| W o Phi^T fbar ||_1 - || W o Phi^T h ||_1) / sum_k <a_k> || W o Phi^T r_k ||_1,
+ * fbar = (1/E) sum_i (h + sum_k a_ki r_k(c_k + delta_i)) the mean of the epochs' fine images,
+ * h and r_k (unit Gaussian at c_k) as above, lambda the problem's.  (The printed ratio also
+ * multiplies the second norm by lambda; it is read without that factor, which would leave the
+ * difference without a consistent unit.)  0 when the denominator is 0.  The paper starts from
+ * 0.5 lambda and refines the value from each best fit until it settles.  params_dev: the packed
+ * DECONV vector (device); *lambda_pts receives the value; synchronises the stream; allocates and
+ * frees a workspace of 2 (M + 2) F^2 floats.  SR_ERR_STATE without weights or for PSF problems. */
+sr_status sr_estimate_lambda_pts(sr_problem *p, const float *params_dev, double *lambda_pts);
+
 /* Number of float32 values in the packed parameter vector, and its layout. */
 size_t sr_param_count(const sr_problem *p);
 sr_status sr_param_layout(const sr_problem *p, sr_layout *out);

@@ -120,6 +120,17 @@ class Problem:
             raise ValueError(f"expected {self.J - 1} weights")
         nat.check(self.lib.sr_set_weights(self.handle, ctypes.c_void_p(a.ctypes.data)), "sr_set_weights")
 
+    def set_lambda_pts(self, lambda_pts: float):
+        """Strength of the point-source prior (Eq. 11, third term); sr_set_lambda_pts."""
+        nat.check(self.lib.sr_set_lambda_pts(self.handle, float(lambda_pts)), "sr_set_lambda_pts")
+
+    def estimate_lambda_pts(self, params: torch.Tensor) -> float:
+        """lambda_pts from the model `params` by the ratio of App. C; sr_estimate_lambda_pts."""
+        out = ctypes.c_double()
+        nat.check(self.lib.sr_estimate_lambda_pts(self.handle, _cuda_f32(params, self.n_params, "params"),
+                                                  ctypes.byref(out)), "sr_estimate_lambda_pts")
+        return float(out.value)
+
     def layout(self):
         L = nat.Layout()
         nat.check(self.lib.sr_param_layout(self.handle, ctypes.byref(L)), "sr_param_layout")

@@ -183,6 +183,13 @@ struct Plan {
     int4 *d_fft_items = nullptr;
     int *d_fft_fields = nullptr;
     float2 *hhat = nullptr, *fft_acc = nullptr;
+    // point-source prior (Eq. 11, third term): shadow entries of the fields that have it
+    int n_sh = 0, sh_Fmax = 0, sh_Jmax = 0, sh_Mmax = 0, n_sh_chunks = 0;
+    bool sh_any_unbanded = false;
+    FieldDev *d_sh = nullptr;
+    ChunkItem *d_sh_chunks = nullptr;
+    float *pbar = nullptr, *abar = nullptr, *pts_g = nullptr;
+    double *l1_pts = nullptr;
     // PSF
     PsfBuffers psf{};
     // plain form
@@ -224,6 +231,13 @@ struct sr_problem {
     float2 *fft_tw = nullptr, *khat = nullptr;
     int *d_flag = nullptr;
     float W_host[kMaxScales] = {0};
+    // point-source prior: lambda_pts, its weights lambda_pts W_j (device, and the host copy they
+    // are sent from) and the starlet scratch of the mean point-source image; pts_enabled once a
+    // non-zero lambda_pts was set (the evaluation then carries the term)
+    double lam_pts = 0.0;
+    bool pts_enabled = false;
+    float Wpts_host[kMaxScales] = {0};
+    float *Wpts = nullptr, *pts_starlet = nullptr;
     bool has_data = false, has_noise = false, has_psfs = false, has_weights = false;
     bool pending_check = false;
     Plan *plan = nullptr;
@@ -233,6 +247,7 @@ struct sr_problem {
 struct sr_batch {
     cudaStream_t stream = nullptr;
     std::vector<sr_problem *> probs;
+    std::vector<char> pts_enabled;  // each problem's point-source prior state when the plan was built
     Plan *plan = nullptr;
 };
 
@@ -430,6 +445,9 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     std::vector<int4> fft_items;
     std::vector<int> fft_fields;
     long long hhat_len = 0, acc_len = 0;
+    std::vector<FieldDev> sh;
+    std::vector<ChunkItem> sh_chunks;
+    long long pbar_len = 0, l1pts = 0, ptsslot = 0;
     for (int i = 0; i < n; ++i) {
         sr_problem *p = probs[i];
         if (p->desc.kind != pl->kind) return fail(SR_ERR_ARG, "a batch mixes problem kinds");
@@ -527,6 +545,28 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             fd.ps_slot = psslot;
             psslot += (long long)fd.E * fd.M;
         }
+        if (pl->kind == SR_DECONV && p->pts_enabled && fd.M > 0) {
+            if (plain) return fail(SR_ERR_UNSUPPORTED, "the plain form evaluates lambda_pts = 0 only");
+            // shadow entry: the same field with c_0 = the mean point-source image
+            FieldDev sd = fd;
+            sd.lambda = 1.0f;
+            sd.Wd = p->Wpts;
+            sd.starlet = p->pts_starlet;
+            sd.param_off = pbar_len;
+            pbar_len += (long long)fd.F * fd.F;
+            sd.l1_slot = l1pts;
+            l1pts += (long long)(fd.J - 1) * fd.n_chunks;
+            sd.ps_slot = ptsslot;
+            ptsslot += fd.M;
+            sd.pts = i + 1;
+            fd.pts = (int)sh.size() + 1;
+            for (int c = 0; c < fd.n_chunks; ++c) sh_chunks.push_back(ChunkItem{(int)sh.size(), c * 256, c});
+            pl->sh_Fmax = std::max(pl->sh_Fmax, fd.F);
+            pl->sh_Jmax = std::max(pl->sh_Jmax, fd.J);
+            pl->sh_Mmax = std::max(pl->sh_Mmax, fd.M);
+            if (!starlet_field_banded(fd.F, fd.J)) pl->sh_any_unbanded = true;
+            sh.push_back(sd);
+        }
     }
     if (tslot > 0x7fffffff) return fail(SR_ERR_SHAPE, "too many tiles");
     pl->Jmax = Jmax;
@@ -596,6 +636,19 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         if ((st = configure_plain_kernels(K)) != SR_OK) return st;
     }
     SR_CUDA(cudaMemcpy(pl->d_fields, pl->h_fields.data(), sizeof(FieldDev) * n, cudaMemcpyHostToDevice));
+    if (!sh.empty()) {
+        pl->n_sh = (int)sh.size();
+        pl->n_sh_chunks = (int)sh_chunks.size();
+        if ((st = A.alloc(&pl->d_sh, sh.size())) != SR_OK) return st;
+        if ((st = A.alloc(&pl->d_sh_chunks, sh_chunks.size())) != SR_OK) return st;
+        if ((st = A.alloc(&pl->pbar, (size_t)pbar_len)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->l1_pts, (size_t)l1pts)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->abar, (size_t)ptsslot)) != SR_OK) return st;
+        if ((st = A.alloc(&pl->pts_g, 3 * (size_t)ptsslot)) != SR_OK) return st;
+        SR_CUDA(cudaMemcpy(pl->d_sh, sh.data(), sizeof(FieldDev) * sh.size(), cudaMemcpyHostToDevice));
+        SR_CUDA(cudaMemcpy(pl->d_sh_chunks, sh_chunks.data(), sizeof(ChunkItem) * sh_chunks.size(),
+                           cudaMemcpyHostToDevice));
+    }
     if (!items.empty()) SR_CUDA(cudaMemcpy(pl->d_items, items.data(), sizeof(TileItem) * items.size(), cudaMemcpyHostToDevice));
     if (!ps.empty()) SR_CUDA(cudaMemcpy(pl->d_ps, ps.data(), sizeof(int4) * ps.size(), cudaMemcpyHostToDevice));
     if (!chunks.empty()) SR_CUDA(cudaMemcpy(pl->d_chunks, chunks.data(), sizeof(ChunkItem) * chunks.size(), cudaMemcpyHostToDevice));
@@ -695,8 +748,12 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
                          grad, st);
         ++n;
     }
+    if (pl->n_sh > 0)
+        n += launch_pts_prior(pl->d_sh, pl->d_fields, pl->n_sh, pl->sh_Fmax, pl->sh_Mmax, pl->sh_any_unbanded,
+                              pl->d_sh_chunks, pl->n_sh_chunks, pl->sh_Jmax, params, pl->abar, pl->pbar, pl->l1_pts,
+                              pl->pts_g, st);
     launch_finalize(pl->d_fields, pl->n_fields, pl->chi_part, pl->se_part, pl->l1_part, pl->ps_da, pl->ps_du, grad,
-                    pl->losses, pl->total, st);
+                    pl->losses, pl->total, st, pl->n_sh > 0 ? pl->d_sh : nullptr, pl->l1_pts, pl->pts_g);
     n += 2;
     return n;
 }
@@ -1024,7 +1081,61 @@ sr_status sr_set_weights(sr_problem *p, const float *W) {
     memcpy(p->W_host, tmp, sizeof tmp);
     SR_CUDA(cudaMemcpyAsync(p->Wd, p->W_host, sizeof tmp, cudaMemcpyHostToDevice, p->stream));
     p->has_weights = true;
+    if (p->Wpts) {
+        for (int j = 0; j < kMaxScales; ++j) p->Wpts_host[j] = (float)(p->lam_pts * p->W_host[j]);
+        SR_CUDA(cudaMemcpyAsync(p->Wpts, p->Wpts_host, sizeof p->Wpts_host, cudaMemcpyHostToDevice, p->stream));
+    }
     return SR_OK;
+}
+
+sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts) {
+    if (!p) return fail(SR_ERR_ARG, "problem is NULL");
+    if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "lambda_pts belongs to deconvolution problems");
+    if (!(lambda_pts >= 0.0) || !std::isfinite(lambda_pts)) return fail(SR_ERR_ARG, "lambda_pts must be finite and >= 0");
+    sr_status st;
+    if (!p->Wpts && lambda_pts > 0.0) {
+        // first non-zero value: the term's buffers, and a plan that carries it
+        const size_t F2 = (size_t)p->F * p->F;
+        if ((st = p->arena.alloc(&p->Wpts, kMaxScales)) != SR_OK) return st;
+        if ((st = p->arena.alloc(&p->pts_starlet, (size_t)(p->desc.n_scales + 2) * F2)) != SR_OK) return st;
+        p->pts_enabled = true;
+        if (p->plan) {
+            Plan *old = p->plan;
+            SR_CUDA(cudaStreamSynchronize(p->stream));
+            p->plan = nullptr;
+            if ((st = ensure_plan(p)) != SR_OK) {
+                p->plan = old;
+                return st;
+            }
+            if (old->opt_m) {  // the optimiser's state carries over
+                if ((st = ensure_opt_buffers(p->plan)) != SR_OK) return st;
+                Plan *pl = p->plan;
+                SR_CUDA(cudaMemcpyAsync(pl->opt_m, old->opt_m, sizeof(float) * pl->n_params, cudaMemcpyDeviceToDevice,
+                                        p->stream));
+                SR_CUDA(cudaMemcpyAsync(pl->opt_v, old->opt_v, sizeof(float) * pl->n_params, cudaMemcpyDeviceToDevice,
+                                        p->stream));
+                SR_CUDA(cudaMemcpyAsync(pl->d_t, old->d_t, sizeof(long long), cudaMemcpyDeviceToDevice, p->stream));
+                SR_CUDA(cudaStreamSynchronize(p->stream));
+            }
+            delete old;
+        }
+    }
+    p->lam_pts = lambda_pts;
+    if (p->Wpts) {
+        for (int j = 0; j < kMaxScales; ++j) p->Wpts_host[j] = (float)(lambda_pts * p->W_host[j]);
+        SR_CUDA(cudaMemcpyAsync(p->Wpts, p->Wpts_host, sizeof p->Wpts_host, cudaMemcpyHostToDevice, p->stream));
+    }
+    return SR_OK;
+}
+
+sr_status sr_estimate_lambda_pts(sr_problem *p, const float *params_dev, double *lambda_pts) {
+    if (!p || !params_dev || !lambda_pts) return fail(SR_ERR_ARG, "NULL argument");
+    if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "lambda_pts belongs to deconvolution problems");
+    if (!p->has_weights) return fail(SR_ERR_STATE, "weights not set");
+    FieldDev fd;
+    fill_field_common(fd, p);
+    fd.param_off = 0;
+    return pts_estimate(fd, params_dev, p->Wd, (float)p->desc.lambda, lambda_pts, p->stream);
 }
 
 size_t sr_param_count(const sr_problem *p) { return p ? param_count(p->desc) : 0; }
@@ -1157,6 +1268,7 @@ sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream,
     if (!b) return fail(SR_ERR_OOM, "host allocation failed");
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     b->probs.assign(problems, problems + n);
+    for (int i = 0; i < n; ++i) b->pts_enabled.push_back(problems[i]->pts_enabled ? 1 : 0);
     b->plan = new (std::nothrow) Plan();
     if (!b->plan) {
         delete b;
@@ -1189,7 +1301,17 @@ sr_status sr_batch_param_offset(const sr_batch *b, int i, size_t *offset) {
     return SR_OK;
 }
 
+// A problem whose point-source prior was switched on after the batch was built is not in the
+// batch's plan: the batch must be re-created.
+static sr_status batch_pts_check(const sr_batch *b) {
+    for (size_t i = 0; i < b->probs.size(); ++i)
+        if ((b->probs[i]->pts_enabled ? 1 : 0) != b->pts_enabled[i])
+            return fail(SR_ERR_STATE, "field %zu got a non-zero lambda_pts after sr_batch_create: re-create the batch", i);
+    return SR_OK;
+}
+
 static sr_status batch_check(sr_batch *b) {
+    if (sr_status st = batch_pts_check(b)) return st;
     for (sr_problem *p : b->probs) {
         if (p->pending_check) {
             sr_status st = check_flag(p);
@@ -1202,6 +1324,7 @@ static sr_status batch_check(sr_batch *b) {
 sr_status sr_batch_loss_and_grad(sr_batch *b, const float *params_dev, double *losses_dev, double *total_dev,
                                  double *total_host, float *grad_dev) {
     if (!b || !params_dev || !grad_dev) return fail(SR_ERR_ARG, "NULL argument");
+    if (sr_status st = batch_pts_check(b)) return st;
     Plan *pl = b->plan;
     pl->launches = run_eval(pl, params_dev, grad_dev, b->stream, nullptr);
     SR_CUDA(cudaGetLastError());
@@ -1239,6 +1362,7 @@ sr_status sr_batch_loss_and_grad_host(sr_batch *b, const float *params_host, dou
 
 sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_optim_cfg *cfg, double *last_total_host) {
     if (!b || !params_dev || !cfg || n_steps < 0) return fail(SR_ERR_ARG, "bad argument");
+    if (sr_status st0 = batch_pts_check(b)) return st0;
     sr_status st = run_steps(b->plan, b->stream, params_dev, n_steps, cfg, nullptr, nullptr);
     if (st != SR_OK) return st;
     if (last_total_host) {

@@ -62,6 +62,9 @@ struct FieldDev {
     int fft_n_chunks;         // epoch chunks of the field
     int fft_G;                // epochs transformed side by side by the chunk kernel (1, 2 or 4)
     int fft_EB;               // float2 elements of each per-epoch transform buffer (fft_fixed.cu)
+    // point-source prior (Eq. 11, third term): 1 + index of the partner entry (a field's shadow
+    // entry in the plan's point-source table, or a shadow entry's field), 0 for none
+    int pts;
 };
 
 // One output tile of one epoch: rows [y0, y0+h), cols [x0, x0+w) of the data

@@ -435,25 +435,31 @@ __global__ void __launch_bounds__(kThreads)
 finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ chi_part,
                 const double *__restrict__ se_part, const double *__restrict__ l1_part,
                 const float *__restrict__ ps_da, const float *__restrict__ ps_du, float *__restrict__ grad,
-                double *__restrict__ losses) {
+                double *__restrict__ losses, const FieldDev *__restrict__ pts_fields,
+                const double *__restrict__ l1_pts, const float *__restrict__ pts_g) {
     __shared__ double s_red[2][kThreads / 32];
     const FieldDev &fd = fields[blockIdx.x];
     const int E = fd.E, M = fd.M, F = fd.F, f = fd.f;
+    // point-source prior of the field (Eq. 11, third term), if it has one
+    const FieldDev *sd = (pts_fields && fd.pts > 0) ? &pts_fields[fd.pts - 1] : nullptr;
     double chi = 0.0, l1 = 0.0;
     const long long nt = (long long)E * fd.n_tiles;
     for (long long s = threadIdx.x; s < nt; s += blockDim.x) chi += chi_part[fd.tile_slot + s];
     const long long nl = (long long)(fd.J - 1) * fd.n_chunks;
     for (long long s = threadIdx.x; s < nl; s += blockDim.x) l1 += l1_part[fd.l1_slot + s];
+    if (sd)
+        for (long long s = threadIdx.x; s < nl; s += blockDim.x) l1 += l1_pts[sd->l1_slot + s];
     block_sum2(chi, l1, s_red);
     if (threadIdx.x == 0) losses[blockIdx.x] = chi + l1;
     float *g = grad + fd.param_off + (long long)F * F;  // a block
-    for (int s = threadIdx.x; s < E * M; s += blockDim.x) g[s] = ps_da[fd.ps_slot + s];
+    for (int s = threadIdx.x; s < E * M; s += blockDim.x)
+        g[s] = sd ? ps_da[fd.ps_slot + s] + pts_g[3 * (sd->ps_slot + s % M)] / (float)E : ps_da[fd.ps_slot + s];
     float *gc = g + (long long)E * M;
     for (int s = threadIdx.x; s < 2 * M; s += blockDim.x) {
         const int k = s >> 1, ax = s & 1;
         double acc = 0.0;
         for (int i = 0; i < E; ++i) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
-        gc[s] = (float)(f * acc);
+        gc[s] = sd ? (float)(f * acc + (double)pts_g[3 * (sd->ps_slot + k) + 1 + ax]) : (float)(f * acc);
     }
     float *gd = gc + 2 * M;
     for (int s = threadIdx.x; s < 2 * E; s += blockDim.x) {
@@ -532,8 +538,10 @@ void launch_hgrad(const FieldDev *fields, const ChunkItem *chunks, int n_chunks,
 
 void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_part, const double *se_part,
                      const double *l1_part, const float *ps_da, const float *ps_du, float *grad, double *losses,
-                     double *total, cudaStream_t st) {
-    finalize_kernel<<<n_fields, kThreads, 0, st>>>(fields, chi_part, se_part, l1_part, ps_da, ps_du, grad, losses);
+                     double *total, cudaStream_t st, const FieldDev *pts_fields, const double *l1_pts,
+                     const float *pts_g) {
+    finalize_kernel<<<n_fields, kThreads, 0, st>>>(fields, chi_part, se_part, l1_part, ps_da, ps_du, grad, losses,
+                                                   pts_fields, l1_pts, pts_g);
     total_kernel<<<1, 32, 0, st>>>(losses, n_fields, total);
 }
 

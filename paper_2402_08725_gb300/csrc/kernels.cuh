@@ -21,9 +21,12 @@ void launch_psgrad(const FieldDev *fields, const int4 *ps_items, int n, const fl
                    float *ps_da, float *ps_du, cudaStream_t st);
 void launch_hgrad(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, const float *gbuf, float *grad,
                   cudaStream_t st);
+// pts_fields / l1_pts / pts_g: the point-source prior's table and outputs (launch_pts_prior), or
+// nullptr when no field of the table has the term
 void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_part, const double *se_part,
                      const double *l1_part, const float *ps_da, const float *ps_du, float *grad, double *losses,
-                     double *total, cudaStream_t st);
+                     double *total, cudaStream_t st, const FieldDev *pts_fields = nullptr,
+                     const double *l1_pts = nullptr, const float *pts_g = nullptr);
 
 // --- frequency-domain form (fft.cu) ---
 int fft_smem_bytes(int L, int M, int f);
@@ -54,6 +57,18 @@ void launch_fft_chunks_fixed(const FieldDev *fields, const int4 *items, int n_it
 bool starlet_field_banded(int F, int J);
 int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unbanded, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st);
+
+// --- point-source prior and lambda_pts estimate (pts.cu) ---
+// Shadow entries sh[0..n_sh) (each a copy of its field's entry with c_0 = the mean point-source
+// image at param_off in pbar, lambda 1, weights lambda_pts W_j, its own starlet scratch, l1 slots
+// in l1_pts and source slots ps_slot in abar / pts_g): value partial sums in l1_pts and per source
+// (sum G r, d/dc_x, d/dc_y) in pts_g.  Returns the number of launches.
+int launch_pts_prior(const FieldDev *sh, const FieldDev *fields, int n_sh, int Fmax, int Mmax, bool any_unbanded,
+                     const ChunkItem *chunks, int n_chunks, int Jmax, const float *params, float *abar, float *pbar,
+                     double *l1_pts, float *pts_g, cudaStream_t st);
+// The App. C ratio for one field (fd.param_off into params); synchronises st.
+sr_status pts_estimate(const FieldDev &fd, const float *params, const float *Wd, float lambda, double *out_host,
+                       cudaStream_t st);
 
 // --- PSF reconstruction (psf.cu) ---
 struct PsfBuffers {

@@ -56,8 +56,14 @@ def oracle_deconv(fd, params=None, **kw):
     return oracle.deconv_loss_grad(fd.E, fd.N, fd.f, fd.K, fd.M, fd.J, fd.lam, fd.d, fd.sigma, fd.s, fd.W, P, **kw)
 
 
-def check_deconv(fd, loss, grad, params=None, report=None):
+def check_deconv(fd, loss, grad, params=None, report=None, lam_pts=0.0):
+    """lam_pts > 0 adds the point-source prior of Eq. 11 to the reference."""
     L_ref, _, g_ref, _ = oracle_deconv(fd, params)
+    if lam_pts > 0.0:
+        P = fd.params if params is None else params
+        v, gp = oracle.pts_prior(fd.E, fd.N, fd.f, fd.M, fd.J, lam_pts, fd.W, P)
+        L_ref += v
+        g_ref = g_ref + gp
     scale = loss_scale(L_ref, fd.d, fd.sigma)
     err = abs(loss - L_ref) / scale
     res = {"loss": loss, "loss_ref": L_ref, "loss_rel": err}

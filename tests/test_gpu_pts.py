@@ -1,0 +1,171 @@
+"""GPU parity of the point-source prior (Eq. 11, third term) and of the lambda_pts estimate
+(App. C) through the C ABI, against the FP64 oracle, with the tolerances of the other parity
+tests (loss 1e-6 relative, gradient 1e-4 relative L2 per parameter block)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2402_08725_gb300 import synthetic as syn  # noqa: E402
+from tests._helpers import check_deconv  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_08725_gb300 import _native
+    _native.load()
+    yield
+
+
+def _prob(fd, mode="auto", lam_pts=None):
+    from paper_2402_08725_gb300.binding import Problem
+    p = Problem.from_field(fd, conv_mode=mode)
+    if lam_pts is not None:
+        p.set_lambda_pts(lam_pts)
+    return p
+
+
+def _eval(p, P):
+    loss, g = p.loss_and_grad(torch.from_numpy(np.ascontiguousarray(P, dtype=np.float32)).cuda())
+    return loss, g.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["direct", "fft"])
+@pytest.mark.parametrize("seed,N,M,J", [(1, 16, 2, 3), (2, 24, 1, 4), (3, 20, 3, 3)])
+def test_pts_prior_matches_oracle(mode, seed, N, M, J):
+    fd = syn.small_deconv(seed, E=3, N=N, f=2, K=13, M=M, J=J, lam=0.5)
+    p = _prob(fd, mode, lam_pts=0.8)
+    loss, g = _eval(p, fd.params)
+    check_deconv(fd, loss, g, lam_pts=0.8)
+    p.close()
+
+
+def test_lambda_pts_zero_and_changes_without_new_plan():
+    fd = syn.small_deconv(4, E=4, N=16, f=2, K=11, M=2, J=3, lam=0.5)
+    p = _prob(fd)
+    loss0, g0 = _eval(p, fd.params)
+    check_deconv(fd, loss0, g0)
+    p.set_lambda_pts(1.3)  # first non-zero value: the plan is rebuilt with the term
+    loss1, g1 = _eval(p, fd.params)
+    check_deconv(fd, loss1, g1, lam_pts=1.3)
+    p.set_lambda_pts(0.4)  # later values only change the weights
+    loss2, g2 = _eval(p, fd.params)
+    check_deconv(fd, loss2, g2, lam_pts=0.4)
+    p.set_lambda_pts(0.0)
+    loss3, g3 = _eval(p, fd.params)
+    assert abs(loss3 - loss0) <= 1e-9 * abs(loss0) and np.array_equal(g3, g0)
+    p.close()
+
+
+def test_lambda_pts_inside_captured_steps_and_state_carried_over():
+    from paper_2402_08725_gb300.binding import optim_cfg
+    fd = syn.small_deconv(5, E=3, N=16, f=2, K=11, M=1, J=3, lam=0.5)
+    p = _prob(fd)
+    P = torch.from_numpy(np.ascontiguousarray(fd.params, dtype=np.float32)).cuda()
+    cfg = optim_cfg("adabelief", lr=(1e-3, 1e-2, 1e-3, 1e-3, 1e-3))
+    p.step(P, 3, cfg)
+    m0, v0, t0 = p.get_state()
+    p.set_lambda_pts(0.9)  # rebuilds the plan; the optimiser state carries over
+    m1, v1, t1 = p.get_state()
+    assert t1 == t0 == 3 and torch.equal(m0, m1) and torch.equal(v0, v1)
+    p.step(P, 2, cfg)
+    p.set_lambda_pts(0.2)  # replayed steps read the new weights
+    p.step(P, 1, cfg)
+    Pn = P.cpu().numpy().astype(np.float64)
+    loss, g = _eval(p, Pn)
+    check_deconv(fd, loss, g, params=Pn, lam_pts=0.2)
+    p.close()
+
+
+def test_batch_with_the_term_equals_single_problems():
+    from paper_2402_08725_gb300.binding import Batch
+    fields = [syn.small_deconv(10 + i, E=2 + i, N=16 + 4 * (i % 2), f=2, K=11, M=i % 3, J=3, lam=0.5)
+              for i in range(5)]
+    lam_pts = [0.7, 0.0, 1.1, 0.5, None]
+    probs = [_prob(fd, lam_pts=lp) for fd, lp in zip(fields, lam_pts)]
+    b = Batch(probs)
+    P = torch.from_numpy(b.pack([fd.params for fd in fields])).cuda()
+    lt = torch.empty(len(fields), dtype=torch.float64, device="cuda")
+    _, g = b.loss_and_grad(P, losses=lt)
+    losses = lt.cpu().numpy()
+    g = g.cpu().numpy()
+    for i, (fd, lp) in enumerate(zip(fields, lam_pts)):
+        o = b.offsets[i]
+        n = fd.params.size
+        single = _prob(fd, lam_pts=lp)
+        ls, gs = _eval(single, fd.params)
+        assert float(losses[i]) == ls and np.array_equal(g[o:o + n], gs)
+        check_deconv(fd, ls, gs, lam_pts=lp or 0.0)
+        single.close()
+    b.close()
+    for p in probs:
+        p.close()
+
+
+def test_batch_built_before_the_term_must_be_recreated():
+    from paper_2402_08725_gb300.binding import Batch
+    fields = [syn.small_deconv(20 + i, E=2, N=16, f=2, K=11, M=1, J=3, lam=0.5) for i in range(2)]
+    probs = [_prob(fd) for fd in fields]
+    b = Batch(probs)
+    P = torch.from_numpy(b.pack([fd.params for fd in fields])).cuda()
+    b.loss_and_grad(P)
+    probs[1].set_lambda_pts(0.5)
+    with pytest.raises(RuntimeError, match="SR_ERR_STATE"):
+        b.loss_and_grad(P)
+    b.close()
+    b2 = Batch(probs)
+    lt = torch.empty(2, dtype=torch.float64, device="cuda")
+    _, g = b2.loss_and_grad(P, losses=lt)
+    o = b2.offsets[1]
+    check_deconv(fields[1], float(lt[1]), g.cpu().numpy()[o:o + fields[1].params.size], lam_pts=0.5)
+    b2.close()
+    for p in probs:
+        p.close()
+
+
+def test_plain_form_and_psf_problems_reject_the_term():
+    from paper_2402_08725_gb300.binding import Problem
+    fd = syn.small_deconv(6, E=2, N=16, f=2, K=11, M=1, J=3, lam=0.5)
+    p = _prob(fd, "plain", lam_pts=0.5)
+    with pytest.raises(RuntimeError, match="SR_ERR_UNSUPPORTED"):
+        _eval(p, fd.params)
+    p.close()
+    q = Problem.from_psf(syn.small_psf(7, S=2, N=12, f=2, J=3))
+    with pytest.raises(RuntimeError, match="SR_ERR_STATE"):
+        q.set_lambda_pts(0.5)
+    with pytest.raises(RuntimeError, match="SR_ERR_ARG"):
+        _prob(fd).set_lambda_pts(float("nan"))
+    q.close()
+
+
+@pytest.mark.parametrize("seed,N,M,J,shift", [(30, 24, 1, 4, 0.0), (31, 20, 2, 3, 0.4), (32, 32, 3, 4, 0.8)])
+def test_lambda_pts_estimate_matches_oracle(seed, N, M, J, shift):
+    fd = syn.small_deconv(seed, E=4, N=N, f=2, K=11, M=M, J=J, lam=1.5)
+    P = fd.params.astype(np.float64).copy()
+    F = fd.F
+    od = F * F + fd.E * M + 2 * M
+    P[od:od + 2 * fd.E] = np.random.default_rng(seed).normal(0, shift, 2 * fd.E) if shift else 0.0
+    P = P.astype(np.float32).astype(np.float64)
+    ref = oracle.lambda_pts_estimate(fd.E, N, 2, M, J, fd.lam, fd.W, P)
+    p = _prob(fd)
+    est = p.estimate_lambda_pts(torch.from_numpy(P.astype(np.float32)).cuda())
+    assert abs(est - ref) <= 1e-4 * abs(fd.lam), (est, ref)
+    p.close()
+
+
+def test_lambda_pts_estimate_closed_form_on_gpu():
+    """One source, no extended flux and no per-epoch shifts: the ratio is lambda."""
+    fd = syn.small_deconv(33, E=3, N=24, f=2, K=11, M=1, J=4, lam=2.0)
+    P = fd.params.astype(np.float32).copy()
+    P[:fd.F * fd.F] = 0.0
+    od = fd.F * fd.F + fd.E + 2
+    P[od:od + 2 * fd.E] = 0.0
+    p = _prob(fd)
+    est = p.estimate_lambda_pts(torch.from_numpy(P).cuda())
+    assert abs(est - 2.0) <= 1e-5 * 2.0
+    p.close()
