@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-noise", action="store_true", help="skip the Monte Carlo prior-weight measurement")
+    ap.add_argument("--no-noise", action="store_true",
+                    help="skip the Monte Carlo prior weights and point-source prior measurements")
     ap.add_argument("--conv-mode", choices=["auto", "direct", "fft"], default="auto",
                     help="convolution form of every field (auto: timed per shape on first use)")
     ap.add_argument("--fields", type=int, default=0,
@@ -382,6 +383,49 @@ def measure_noise(stream, fp32_peak, with_cpu, reps=3, cpu_sample=256):
     return out
 
 
+def measure_pts(stream, evals=10, warm=3):
+    """Point-source prior (Eq. 11, third term) on the config-3 lensed quasar (E = 300, N = 64,
+    f = 2, M = 4, J = 4), where blending makes the term necessary: one loss-and-gradient
+    evaluation without and with the term (lambda_pts = 0.5 lambda, the starting value of App. C),
+    and the App. C estimate."""
+    import torch
+    from paper_2402_08725_gb300 import synthetic as syn
+    from paper_2402_08725_gb300.binding import Problem
+    fd = syn.config3()
+    with torch.cuda.stream(stream):
+        prob = Problem.from_field(fd, stream=stream)
+        P = torch.from_numpy(np.ascontiguousarray(fd.params, dtype=np.float32)).cuda()
+        g = torch.empty_like(P)
+        stream.synchronize()
+
+        def timed():
+            for _ in range(warm):
+                prob.loss_and_grad(P, g, sync=False)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(evals):
+                prob.loss_and_grad(P, g, sync=False)
+            e1.record(stream)
+            stream.synchronize()
+            return e0.elapsed_time(e1) / evals
+
+        ms0, n0 = timed(), prob.launches_per_eval()
+        prob.set_lambda_pts(0.5 * fd.lam)
+        ms1, n1 = timed(), prob.launches_per_eval()
+        t0 = time.perf_counter()
+        est = prob.estimate_lambda_pts(P)
+        est_ms = (time.perf_counter() - t0) * 1e3
+        prob.close()
+    return {"workload": f"config-3 field: E={fd.E}, N={fd.N}, f={fd.f}, K={fd.K}, M={fd.M}, J={fd.J}, "
+                        f"lambda={fd.lam}",
+            "eval_ms_without": round(ms0, 4), "eval_ms_with": round(ms1, 4),
+            "overhead_ms": round(ms1 - ms0, 4), "launches_without": n0, "launches_with": n1,
+            "lambda_pts": 0.5 * fd.lam, "estimate_app_c": round(est, 6), "estimate_call_ms": round(est_ms, 3),
+            "timing": f"CUDA events over {evals} evaluations after {warm} warm-up ones (per evaluation); "
+                      "the estimate call by the host clock (it allocates, runs and synchronises)"}
+
+
 def run_ours(args):
     import torch
     rank, world, local_rank = dist_env()
@@ -527,6 +571,7 @@ def run_ours(args):
     noise = None
     if not args.no_noise and rank == 0:
         noise = measure_noise(stream, fp32_peak, with_cpu=not args.no_cpu and world == 1)
+    pts = measure_pts(stream) if not args.no_noise and rank == 0 else None
 
     if rank == 0:
         line = {
@@ -549,6 +594,7 @@ def run_ours(args):
             "plain": plain,
             "cpu_baseline": cpu,
             "noise_weights": noise,
+            "pts_prior": pts,
         }
         print(json.dumps(line))
     if dist is not None:
