@@ -329,6 +329,23 @@ def config4_field(index, N, E, J, seed=None) -> DeconvField:
                              host=host, sky=(3.0, 10.0), light_curve=lc[:, None], positions=pos, texture=0.1)
 
 
+def point_source_field(seed, E, N, M, light_curve=None, positions=None, J=4) -> DeconvField:
+    """Point sources on the sky background only (no extended source), f = 2, K = 64, Moffat PSFs
+    of FWHM U[4, 10] fine px: the data then differ from the model only by how the point sources
+    are sampled, so the extracted light curves measure the photometry itself.  light_curve [E][M]
+    (default: log-uniform base fluxes with 10 % scatter), positions [M][2] in data pixels from the
+    stamp centre (default: uniform within N/6)."""
+    rng = np.random.default_rng(seed)
+    return make_deconv_field(rng, E=E, N=N, f=2, K=64, M=M, J=J, lam=2.0, psf_fwhm=(4.0, 10.0), host=[],
+                             sky=(3.0, 10.0), light_curve=light_curve, positions=positions, pos_half=N / 6)
+
+
+def supernova_light_curve(E, peak_epoch, peak=1e4, width=20.0, floor=50.0):
+    """Gaussian-pulse light curve [E][1] (the shape of the config-4 supernovae)."""
+    t = np.arange(E)
+    return (peak * np.exp(-0.5 * ((t - peak_epoch) / width) ** 2) + floor)[:, None]
+
+
 def config4(seed=None, n_fields=256, fields=None) -> list[DeconvField]:
     shapes = config4_shapes(seed, n_fields)
     idx = range(len(shapes)) if fields is None else fields
