@@ -290,6 +290,39 @@ sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, doubl
  * *tflops receives the figure; SR_ERR_CUDA if a CUDA call fails. */
 sr_status sr_measure_fp32_peak(double *tflops);
 
+/* L-BFGS-B, the paper's second optimiser (sec. 2.4; the algorithm of Byrd, Lu, Nocedal & Zhu 1995:
+ * compact limited-memory matrix, generalised Cauchy point, subspace minimisation, strong-Wolfe
+ * line search by bracketing and bisection with c1 = 1e-3, c2 = 0.9, steps in (0, 1]).  Bounds:
+ * the same lower bounds as the sr_step projection (amplitudes >= 0; for a PSF fit also
+ * alpha >= 1e-3 and beta >= 1.001), no others. */
+typedef struct {
+    int m;          /* stored correction pairs, 1..10 (10 when <= 0) */
+    int max_iter;   /* iterations, >= 0 */
+    int max_ls;     /* loss evaluations per line search (20 when <= 0) */
+    double pgtol;   /* stop when the largest entry of the projected gradient is <= pgtol (>= 0) */
+    double factr;   /* stop when the loss decreases by <= factr * 2.2e-16 relative (>= 0) */
+} sr_lbfgsb_cfg;
+
+enum { SR_LBFGSB_PGTOL = 0, SR_LBFGSB_FACTR = 1, SR_LBFGSB_MAX_ITER = 2, SR_LBFGSB_LINE_SEARCH = 3 };
+
+typedef struct {
+    int iterations;   /* accepted steps */
+    int evaluations;  /* loss-and-gradient evaluations, the first included */
+    int status;       /* SR_LBFGSB_*: why it stopped (LINE_SEARCH: no strong-Wolfe step within max_ls) */
+    double f;         /* loss at the returned parameters */
+    double pg_norm;   /* largest entry of the projected gradient there */
+} sr_lbfgsb_info;
+
+/* Minimise the problem's loss from params_dev (device, sr_param_count floats; overwritten with the
+ * last accepted iterate, the bounded entries first clipped into their bounds).  f_history: NULL,
+ * or a host array of max_iter + 1 doubles receiving the loss of the start and of every iterate.
+ * info may be NULL.  Every n-long vector operation runs on the device; the 2m x 2m algebra and
+ * the breakpoints of the bounded range (a few thousand values at most) run on the host in FP64.
+ * Allocates and frees 2 (m + 1) + 4 vectors of sr_param_count floats; synchronises the stream.
+ * Errors as sr_loss_and_grad, SR_ERR_ARG for a bad configuration. */
+sr_status sr_lbfgsb(sr_problem *p, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
+                    sr_lbfgsb_info *info);
+
 /* Phase timings of one sr_noise_weights call: CUDA-event durations on its stream, summed over
  * the batches of realisations. */
 typedef struct {

@@ -40,6 +40,18 @@ class NoiseTiming(ctypes.Structure):
                 ("launches", c_int), ("batch", c_int)]
 
 
+class LbfgsbCfg(ctypes.Structure):
+    _fields_ = [("m", c_int), ("max_iter", c_int), ("max_ls", c_int), ("pgtol", c_double), ("factr", c_double)]
+
+
+class LbfgsbInfo(ctypes.Structure):
+    _fields_ = [("iterations", c_int), ("evaluations", c_int), ("status", c_int), ("f", c_double),
+                ("pg_norm", c_double)]
+
+
+LBFGSB_STATUS = {0: "pgtol", 1: "factr", 2: "max_iter", 3: "line_search"}
+
+
 class OptimCfg(ctypes.Structure):
     _fields_ = [("kind", c_int), ("beta1", c_float), ("beta2", c_float), ("eps", c_float),
                 ("lr", c_float * SR_MAX_GROUPS)]
@@ -80,6 +92,7 @@ PROTOTYPES = {
     "sr_batch_profile_read": ([c_void_p, ctypes.POINTER(c_int), P_double, P_double, P_double], c_int),
     "sr_measure_fp32_peak": ([P_double], c_int),
     "sr_set_lambda_pts": ([c_void_p, c_double], c_int),
+    "sr_lbfgsb": ([c_void_p, c_void_p, ctypes.POINTER(LbfgsbCfg), P_double, ctypes.POINTER(LbfgsbInfo)], c_int),
     "sr_estimate_lambda_pts": ([c_void_p, c_void_p, P_double], c_int),
     "sr_noise_weights": ([c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int, ctypes.c_uint64, P_float,
                           c_void_p, ctypes.POINTER(NoiseTiming), c_void_p], c_int),

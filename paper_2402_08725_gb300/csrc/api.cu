@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "lbfgsb.cuh"
 
 namespace sr {
 
@@ -1126,6 +1127,33 @@ sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts) {
         SR_CUDA(cudaMemcpyAsync(p->Wpts, p->Wpts_host, sizeof p->Wpts_host, cudaMemcpyHostToDevice, p->stream));
     }
     return SR_OK;
+}
+
+sr_status sr_lbfgsb(sr_problem *p, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
+                    sr_lbfgsb_info *info) {
+    if (!p || !params_dev || !cfg) return fail(SR_ERR_ARG, "NULL argument");
+    sr_status st = check_ready(p);
+    if (st != SR_OK) return st;
+    sr_lbfgsb_cfg c = *cfg;
+    if (c.m <= 0) c.m = kLbfgsMaxMemory;
+    if (c.max_ls <= 0) c.max_ls = 20;
+    if (c.m > kLbfgsMaxMemory || c.max_iter < 0 || !(c.pgtol >= 0.0) || !(c.factr >= 0.0))
+        return fail(SR_ERR_ARG, "sr_lbfgsb: need m <= %d, max_iter >= 0, pgtol >= 0, factr >= 0", kLbfgsMaxMemory);
+    const sr_problem_desc &d = p->desc;
+    LbfgsbProblem P;
+    P.n = (long long)param_count(d);
+    P.r0 = (long long)p->F * p->F;
+    if (d.kind == SR_DECONV) {
+        P.r1 = P.r0 + (long long)d.n_epochs * d.n_sources;
+        P.lo.assign((size_t)(P.r1 - P.r0), 0.0f);  // a >= 0
+    } else {
+        P.r1 = P.r0 + 2 + d.n_epochs;
+        P.lo.assign((size_t)(P.r1 - P.r0), 0.0f);  // a >= 0
+        P.lo[0] = 1e-3f;                           // alpha
+        P.lo[1] = 1.001f;                          // beta
+    }
+    P.eval = [p](const float *x, float *g, double *f) { return sr_loss_and_grad(p, x, f, nullptr, g); };
+    return lbfgsb_run(P, params_dev, c, f_history, info, p->stream);
 }
 
 sr_status sr_estimate_lambda_pts(sr_problem *p, const float *params_dev, double *lambda_pts) {
