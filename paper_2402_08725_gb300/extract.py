@@ -10,6 +10,9 @@ that extended image in the box around c0_k, clipped at 0; delta = 0; Gamma = 0. 
 per parameter group (h, a, c, delta, Gamma): 0.1 % of the brightest data pixel spread over f^2
 fine pixels, 1 % of the mean starting amplitude, and fixed steps of 5e-3, 2e-3 and 1e-2.
 
+The optimiser is AdaBelief with these rates, or L-BFGS-B (sr_lbfgsb, no rates), which may stop
+before its iteration budget when its line search finds no step.
+
 Point-source prior (App. C): lambda_pts starts at 0.5 lambda; the steps run in rounds, and after
 each round lambda_pts is re-estimated from the current model (sr_estimate_lambda_pts, clipped at
 0).  lambda_pts = a number fixes it instead; 0 leaves the term out.
@@ -53,11 +56,13 @@ def default_lr(fd, p0):
     return (1e-3 * float(np.max(fd.d)) / (f * f), 1e-2 * max(float(np.mean(np.abs(a0))), 1.0), 5e-3, 2e-3, 1e-2)
 
 
-def extract(fd, c0, n_steps: int = 200, lr=None, lambda_pts="app_c", rounds: int = 4, stream=None):
-    """Run n_steps optimiser steps from initial_params(fd, c0), in `rounds` rounds when
-    lambda_pts is refined.  Returns a dict with the final packed parameters, the light curves
-    a [E][M], the positions c [M][2], the loss of every step, the lambda_pts of each round and
-    the device time of the steps and estimates (CUDA events on the problem's stream, ms)."""
+def extract(fd, c0, n_steps: int = 200, lr=None, lambda_pts="app_c", rounds: int = 4, stream=None,
+            optimizer: str = "adabelief"):
+    """Run n_steps optimiser steps (AdaBelief; or L-BFGS-B iterations with optimizer="lbfgsb")
+    from initial_params(fd, c0), in `rounds` rounds when lambda_pts is refined.  Returns a dict
+    with the final packed parameters, the light curves a [E][M], the positions c [M][2], the loss
+    of every step, the lambda_pts of each round and the device time of the steps and estimates
+    (CUDA events on the problem's stream, ms); for L-BFGS-B also its loss evaluations."""
     prob = Problem.from_field(fd, stream=stream)
     p0 = initial_params(fd, c0)
     P = torch.from_numpy(np.ascontiguousarray(p0, dtype=np.float32)).cuda()
@@ -72,10 +77,16 @@ def extract(fd, c0, n_steps: int = 200, lr=None, lambda_pts="app_c", rounds: int
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lps, done = [lp], 0
     e0.record(st)
+    evals, hist = 0, []
     for r in range(n_rounds):
         n = (n_steps * (r + 1)) // n_rounds - done
         if n > 0:
-            prob.step(P, n, cfg, losses[done:done + n])
+            if optimizer == "lbfgsb":
+                info = prob.lbfgsb(P, max_iter=n, pgtol=0.0, factr=0.0)
+                evals += info["evaluations"]
+                hist.extend(info["history"][1:])
+            else:
+                prob.step(P, n, cfg, losses[done:done + n])
             done += n
         if refine and r + 1 < n_rounds:
             lp = max(prob.estimate_lambda_pts(P), 0.0)
@@ -85,7 +96,8 @@ def extract(fd, c0, n_steps: int = 200, lr=None, lambda_pts="app_c", rounds: int
     e1.synchronize()
     out = P.cpu().numpy().astype(np.float64)
     _, a, c, _, _ = syn.unpack_deconv(out, fd.E, fd.N, fd.f, fd.M)
-    res = {"params": out, "a": a, "c": c, "losses": losses[:n_steps].cpu().numpy(), "lambda_pts": lps,
-           "ms": e0.elapsed_time(e1)}
+    L = np.asarray(hist) if optimizer == "lbfgsb" else losses[:n_steps].cpu().numpy()
+    res = {"params": out, "a": a, "c": c, "losses": L, "lambda_pts": lps, "ms": e0.elapsed_time(e1),
+           "evaluations": evals if optimizer == "lbfgsb" else n_steps}
     prob.close()
     return res

@@ -105,6 +105,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sr_problem_desc), offsetof(sr_problem_desc, lambda),
          offsetof(sr_problem_desc, conv_mode), sizeof(sr_layout), offsetof(sr_layout, total), sizeof(sr_optim_cfg),
          sizeof(sr_noise_timing), offsetof(sr_noise_timing, batch));
+  printf("%zu %zu %zu %zu\\n", sizeof(sr_lbfgsb_cfg), offsetof(sr_lbfgsb_cfg, factr), sizeof(sr_lbfgsb_info),
+         offsetof(sr_lbfgsb_info, pg_norm));
   return 0;
 }
 """)
@@ -113,4 +115,6 @@ int main(void) {
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [ctypes.sizeof(nat.ProblemDesc), nat.ProblemDesc.lam.offset, nat.ProblemDesc.conv_mode.offset,
                     ctypes.sizeof(nat.Layout), nat.Layout.total.offset, ctypes.sizeof(nat.OptimCfg),
-                    ctypes.sizeof(nat.NoiseTiming), nat.NoiseTiming.batch.offset]
+                    ctypes.sizeof(nat.NoiseTiming), nat.NoiseTiming.batch.offset,
+                    ctypes.sizeof(nat.LbfgsbCfg), nat.LbfgsbCfg.factr.offset, ctypes.sizeof(nat.LbfgsbInfo),
+                    nat.LbfgsbInfo.pg_norm.offset]
