@@ -290,6 +290,12 @@ sr_status sr_batch_profile_read(sr_batch *b, int *n_evals, double *fwd_ms, doubl
  * *tflops receives the figure; SR_ERR_CUDA if a CUDA call fails. */
 sr_status sr_measure_fp32_peak(double *tflops);
 
+/* The reconstructed narrow PSF of a PSF fit (sec. 2.1, Eq. 2): s = Moffat(alpha, beta) + b on the
+ * F x F fine grid, the Moffat part centred on fine pixel (F/2, F/2) with unit analytic flux.
+ * params_dev: the packed PSF vector (device); s_dev: F*F floats (device), written on the
+ * problem's stream (no synchronisation).  SR_ERR_STATE for a deconvolution problem. */
+sr_status sr_psf_model(sr_problem *p, const float *params_dev, float *s_dev);
+
 /* L-BFGS-B, the paper's second optimiser (sec. 2.4; the algorithm of Byrd, Lu, Nocedal & Zhu 1995:
  * compact limited-memory matrix, generalised Cauchy point, subspace minimisation, strong-Wolfe
  * line search by bracketing and bisection with c1 = 1e-3, c2 = 0.9, steps in (0, 1]).  Bounds:

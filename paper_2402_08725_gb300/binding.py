@@ -177,6 +177,14 @@ class Problem:
                                    ctypes.byref(cfg), lp, ctypes.byref(last)), "sr_step")
         return last.value
 
+    def psf_model(self, params: torch.Tensor) -> torch.Tensor:
+        """The narrow PSF s = Moffat + b of a PSF fit's parameters, [F][F] on the device; sr_psf_model."""
+        F = self.f * self.N
+        out = torch.empty((F, F), dtype=torch.float32, device=params.device)
+        nat.check(self.lib.sr_psf_model(self.handle, _cuda_f32(params, self.n_params, "params"),
+                                        ctypes.c_void_p(out.data_ptr())), "sr_psf_model")
+        return out
+
     def lbfgsb(self, params: torch.Tensor, max_iter: int = 100, m: int = 10, max_ls: int = 20, pgtol: float = 1e-5,
                factr: float = 1e7):
         """L-BFGS-B from `params` (overwritten); sr_lbfgsb.  Returns a dict: iterations,

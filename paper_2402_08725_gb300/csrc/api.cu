@@ -465,7 +465,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         groups.resize(g0 + np);
         for (int g = 0; g < L.n_groups; ++g) {
             uint8_t gid = (uint8_t)g;
-            if (pl->kind == SR_PSF) gid = (uint8_t)(g == 0 ? 0 : g + 1);  // 0 b, 1 alpha, 2 beta, 3 a, 4 c
+            if (pl->kind == SR_PSF) gid = (uint8_t)(g <= 1 ? g : g + 1);  // 0 b, 1 alpha, 2 beta, 3 a, 4 c
             for (size_t k = 0; k < L.count[g]; ++k) groups[g0 + L.offset[g] + k] = gid;
         }
         if (pl->kind == SR_PSF) groups[g0 + L.offset[1] + 1] = 2;  // beta
@@ -1126,6 +1126,18 @@ sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts) {
         for (int j = 0; j < kMaxScales; ++j) p->Wpts_host[j] = (float)(lambda_pts * p->W_host[j]);
         SR_CUDA(cudaMemcpyAsync(p->Wpts, p->Wpts_host, sizeof p->Wpts_host, cudaMemcpyHostToDevice, p->stream));
     }
+    return SR_OK;
+}
+
+sr_status sr_psf_model(sr_problem *p, const float *params_dev, float *s_dev) {
+    if (!p || !params_dev || !s_dev) return fail(SR_ERR_ARG, "NULL argument");
+    if (p->desc.kind != SR_PSF) return fail(SR_ERR_STATE, "sr_psf_model needs a PSF problem");
+    sr_status st;
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    launch_psf_model(p->plan->d_fields, p->F, params_dev, p->stream);
+    SR_CUDA(cudaGetLastError());
+    SR_CUDA(cudaMemcpyAsync(s_dev, p->psf_s, sizeof(float) * (size_t)p->F * p->F, cudaMemcpyDeviceToDevice,
+                            p->stream));
     return SR_OK;
 }
 

@@ -81,6 +81,9 @@ int launch_psf_eval(const FieldDev *fields, const FieldDev &host_field, const Ch
                     const float *params, float *grad, const PsfBuffers &pb, double *l1_part, double *losses,
                     double *total, cudaStream_t st);
 
+// The narrow PSF s = Moffat(alpha, beta) + b of the parameters, into fields[0].psf_s.
+void launch_psf_model(const FieldDev *fields, int F, const float *params, cudaStream_t st);
+
 // --- plain per-epoch form (plain.cu) ---
 struct PlainBuffers {
     float *fimg;   // [F][F] rasterised fine image of the current epoch

@@ -254,6 +254,10 @@ __global__ void psf_finalize_kernel(const FieldDev *__restrict__ fields, const f
     }
 }
 
+void launch_psf_model(const FieldDev *fields, int F, const float *params, cudaStream_t st) {
+    psf_build_s_kernel<<<(F * F + 255) / 256, 256, 0, st>>>(fields, params);
+}
+
 int launch_psf_eval(const FieldDev *fields, const FieldDev &hf, const ChunkItem *chunks, int n_chunks,
                     const float *params, float *grad, const PsfBuffers &pb, double *l1_part, double *losses,
                     double *total, cudaStream_t st) {

@@ -162,6 +162,41 @@ def test_psf_optimiser_projection():
     prob.close()
 
 
+def test_psf_optimiser_groups_move_separately():
+    """Learning rate on one group of the layout at a time (b, Moffat alpha and beta, a, c): Adam's
+    first step moves each variable by lr sign(g), so only the chosen group changes, by exactly
+    its rate; and alpha keeps its own lower bound (1e-3), not beta's."""
+    from paper_2402_08725_gb300.binding import Problem, optim_cfg
+    pb = syn.small_psf(seed=6, S=2, N=12, f=2, J=3)
+    F = pb.f * pb.N
+    spans = [slice(0, F * F), slice(F * F, F * F + 2), slice(F * F + 2, F * F + 2 + pb.S),
+             slice(F * F + 2 + pb.S, F * F + 2 + 3 * pb.S)]
+    for gsel, sl in enumerate(spans):
+        prob = Problem.from_psf(pb)
+        p0 = pb.params.astype(np.float32)
+        p = torch.from_numpy(p0.copy()).cuda()
+        lr = [0.0] * 4
+        lr[gsel] = 1e-3
+        prob.step(p, 1, optim_cfg("adam", lr=tuple(lr)))
+        moved = np.abs(p.cpu().numpy() - p0)
+        others = np.ones(p0.size, dtype=bool)
+        others[sl] = False
+        assert np.all(moved[others] == 0.0), gsel
+        mv, tol = moved[sl], 1e-6 + 2.0 * np.spacing(np.abs(p0[sl]))  # float32 rounding of x +- lr
+        assert np.any(mv > 0) and np.all(np.abs(mv[mv > 0] - 1e-3) <= tol[mv > 0]), gsel
+        prob.close()
+    # alpha pushed below 1.001 stays there (its bound is 1e-3); beta is held at 1.001
+    prob = Problem.from_psf(pb)
+    q = pb.params.astype(np.float32).copy()
+    q[F * F] = 1.0005
+    q[F * F + 1] = 1.0015
+    p = torch.from_numpy(q).cuda()
+    prob.step(p, 1, optim_cfg("adam", lr=(0.0, 0.01, 0.0, 0.0)))
+    out = p.cpu().numpy()
+    assert out[F * F + 1] >= 1.001 - 1e-7 and abs(out[F * F] - 1.0005) == pytest.approx(0.01, rel=1e-3)
+    prob.close()
+
+
 # --- errors -------------------------------------------------------------------------------
 
 def test_state_and_input_errors():
@@ -224,3 +259,17 @@ def test_measured_fp32_peak_is_physical():
     nominal = props.multi_processor_count * 128 * 2 * clock_mhz * 1e6 / 1e12
     t = measure_fp32_peak()
     assert 0.25 * nominal < t < 1.05 * nominal, (t, nominal)
+
+
+def test_psf_model_matches_oracle_moffat_plus_grid():
+    """sr_psf_model: s = Moffat(alpha, beta) + b, against the oracle's Moffat (Eq. 2)."""
+    from paper_2402_08725_gb300.binding import Problem
+    pb = syn.small_psf(51, S=2, N=20, f=2, J=3)
+    F = pb.f * pb.N
+    p = Problem.from_psf(pb)
+    P = pb.params.astype(np.float64)
+    s = p.psf_model(torch.from_numpy(P.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
+    m, _, _ = oracle.moffat(F, float(np.float32(P[F * F])), float(np.float32(P[F * F + 1])))
+    ref = m + P[:F * F].astype(np.float32).reshape(F, F)
+    assert np.max(np.abs(s - ref)) <= 1e-6 * np.max(np.abs(ref))
+    p.close()
