@@ -169,3 +169,42 @@ def test_lambda_pts_estimate_closed_form_on_gpu():
     est = p.estimate_lambda_pts(torch.from_numpy(P).cuda())
     assert abs(est - 2.0) <= 1e-5 * 2.0
     p.close()
+
+
+def test_pts_prior_on_the_full_config4_batch():
+    """All 256 fields of the uneven batch (the benchmark's launch configuration), with
+    lambda_pts = 0.5 lambda on every field: the evaluation with the term minus the one without
+    (the chi^2 and the prior on h are bitwise the same in both) equals the oracle's term for every
+    field, value and a/c gradient, and leaves the h, delta and Gamma gradients unchanged."""
+    from paper_2402_08725_gb300.binding import Batch
+    fields = syn.config4()
+    probs = [_prob(fd) for fd in fields]
+
+    def run():
+        b = Batch(probs)
+        P = torch.from_numpy(b.pack([fd.params for fd in fields])).cuda()
+        lt = torch.empty(len(fields), dtype=torch.float64, device="cuda")
+        _, g = b.loss_and_grad(P, losses=lt)
+        out = (lt.cpu().numpy(), g.cpu().numpy(), list(b.offsets))
+        b.close()
+        return out
+
+    l0, g0, offs = run()
+    for fd, p in zip(fields, probs):
+        p.set_lambda_pts(0.5 * fd.lam)
+    l1, g1, offs1 = run()
+    assert offs1 == offs
+    for i, fd in enumerate(fields):
+        F, E, M = fd.F, fd.E, fd.M
+        v, gp = oracle.pts_prior(E, fd.N, fd.f, M, fd.J, 0.5 * fd.lam, fd.W, fd.params)
+        o = offs[i]
+        dg = g1[o:o + fd.params.size].astype(np.float64) - g0[o:o + fd.params.size]
+        assert abs((l1[i] - l0[i]) - v) <= 1e-5 * v + 1e-9 * abs(l0[i]), (i, l1[i] - l0[i], v)
+        ac = slice(F * F, F * F + E * M + 2 * M)
+        # dg is a difference of two float32 gradients whose chi^2 parts can be large: allow their
+        # rounding (two float32 spacings of the larger entry) besides the usual 1e-4 relative
+        ulp = 2.0 * np.spacing(np.maximum(np.abs(g0[o:o + fd.params.size][ac]), np.abs(g1[o:o + fd.params.size][ac])))
+        assert np.all(np.abs(dg[ac] - gp[ac]) <= 1e-4 * np.max(np.abs(gp[ac])) + ulp), i
+        assert np.all(dg[:F * F] == 0.0) and np.all(dg[F * F + E * M + 2 * M:] == 0.0), i
+    for p in probs:
+        p.close()
