@@ -329,6 +329,12 @@ typedef struct {
 sr_status sr_lbfgsb(sr_problem *p, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
                     sr_lbfgsb_info *info);
 
+/* The same over a batch: L-BFGS-B on the batch's total loss (the sum of its fields' losses) over
+ * the packed parameters of sr_batch_param_offset, each field with its own bounds; one batched
+ * evaluation per line-search trial.  Arguments and errors as sr_lbfgsb, on the batch's stream. */
+sr_status sr_batch_lbfgsb(sr_batch *b, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
+                          sr_lbfgsb_info *info);
+
 /* Phase timings of one sr_noise_weights call: CUDA-event durations on its stream, summed over
  * the batches of realisations. */
 typedef struct {

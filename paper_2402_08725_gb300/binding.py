@@ -287,6 +287,18 @@ class Batch:
                                          ctypes.byref(cfg), ctypes.byref(last)), "sr_batch_step")
         return last.value
 
+    def lbfgsb(self, params: torch.Tensor, max_iter: int = 100, m: int = 10, max_ls: int = 20, pgtol: float = 1e-5,
+               factr: float = 1e7):
+        """L-BFGS-B on the batch's total loss from `params` (overwritten); sr_batch_lbfgsb."""
+        cfg = nat.LbfgsbCfg(int(m), int(max_iter), int(max_ls), float(pgtol), float(factr))
+        info = nat.LbfgsbInfo()
+        hist = np.zeros(int(max_iter) + 1)
+        nat.check(self.lib.sr_batch_lbfgsb(self.handle, _cuda_f32(params, self.n_params, "params"), ctypes.byref(cfg),
+                                           hist.ctypes.data_as(nat.P_double), ctypes.byref(info)), "sr_batch_lbfgsb")
+        return {"iterations": info.iterations, "evaluations": info.evaluations,
+                "status": nat.LBFGSB_STATUS.get(info.status, str(info.status)), "f": info.f, "pg_norm": info.pg_norm,
+                "history": hist[:info.iterations + 1]}
+
     def reset_optimizer(self):
         nat.check(self.lib.sr_batch_reset_optimizer(self.handle), "sr_batch_reset_optimizer")
 

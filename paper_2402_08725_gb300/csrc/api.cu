@@ -1141,29 +1141,42 @@ sr_status sr_psf_model(sr_problem *p, const float *params_dev, float *s_dev) {
     return SR_OK;
 }
 
+// The bounds of one problem's parameters at offset `off`: the lower bounds of the sr_step projection.
+static void add_bounds(LbfgsbProblem &P, const sr_problem_desc &d, int F, long long off) {
+    const long long r0 = off + (long long)F * F;
+    if (d.kind == SR_DECONV) {
+        const long long r1 = r0 + (long long)d.n_epochs * d.n_sources;
+        P.ranges.push_back({r0, r1});
+        P.lo.insert(P.lo.end(), (size_t)(r1 - r0), 0.0f);  // a >= 0
+    } else {
+        const long long r1 = r0 + 2 + d.n_epochs;
+        P.ranges.push_back({r0, r1});
+        P.lo.push_back(1e-3f);                                  // alpha
+        P.lo.push_back(1.001f);                                 // beta
+        P.lo.insert(P.lo.end(), (size_t)(r1 - r0 - 2), 0.0f);  // a >= 0
+    }
+}
+
+static sr_status lbfgsb_config(const sr_lbfgsb_cfg *cfg, sr_lbfgsb_cfg *c) {
+    *c = *cfg;
+    if (c->m <= 0) c->m = kLbfgsMaxMemory;
+    if (c->max_ls <= 0) c->max_ls = 20;
+    if (c->m > kLbfgsMaxMemory || c->max_iter < 0 || !(c->pgtol >= 0.0) || !(c->factr >= 0.0))
+        return fail(SR_ERR_ARG, "sr_lbfgsb: need m <= %d, max_iter >= 0, pgtol >= 0, factr >= 0", kLbfgsMaxMemory);
+    return SR_OK;
+}
+
 sr_status sr_lbfgsb(sr_problem *p, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
                     sr_lbfgsb_info *info) {
     if (!p || !params_dev || !cfg) return fail(SR_ERR_ARG, "NULL argument");
     sr_status st = check_ready(p);
     if (st != SR_OK) return st;
-    sr_lbfgsb_cfg c = *cfg;
-    if (c.m <= 0) c.m = kLbfgsMaxMemory;
-    if (c.max_ls <= 0) c.max_ls = 20;
-    if (c.m > kLbfgsMaxMemory || c.max_iter < 0 || !(c.pgtol >= 0.0) || !(c.factr >= 0.0))
-        return fail(SR_ERR_ARG, "sr_lbfgsb: need m <= %d, max_iter >= 0, pgtol >= 0, factr >= 0", kLbfgsMaxMemory);
+    sr_lbfgsb_cfg c;
+    if ((st = lbfgsb_config(cfg, &c)) != SR_OK) return st;
     const sr_problem_desc &d = p->desc;
     LbfgsbProblem P;
     P.n = (long long)param_count(d);
-    P.r0 = (long long)p->F * p->F;
-    if (d.kind == SR_DECONV) {
-        P.r1 = P.r0 + (long long)d.n_epochs * d.n_sources;
-        P.lo.assign((size_t)(P.r1 - P.r0), 0.0f);  // a >= 0
-    } else {
-        P.r1 = P.r0 + 2 + d.n_epochs;
-        P.lo.assign((size_t)(P.r1 - P.r0), 0.0f);  // a >= 0
-        P.lo[0] = 1e-3f;                           // alpha
-        P.lo[1] = 1.001f;                          // beta
-    }
+    add_bounds(P, d, p->F, 0);
     P.eval = [p](const float *x, float *g, double *f) { return sr_loss_and_grad(p, x, f, nullptr, g); };
     return lbfgsb_run(P, params_dev, c, f_history, info, p->stream);
 }
@@ -1411,6 +1424,23 @@ sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_op
         if ((st = batch_check(b)) != SR_OK) return st;
     }
     return SR_OK;
+}
+
+sr_status sr_batch_lbfgsb(sr_batch *b, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
+                          sr_lbfgsb_info *info) {
+    if (!b || !params_dev || !cfg) return fail(SR_ERR_ARG, "NULL argument");
+    sr_status st;
+    if ((st = batch_check(b)) != SR_OK) return st;
+    sr_lbfgsb_cfg c;
+    if ((st = lbfgsb_config(cfg, &c)) != SR_OK) return st;
+    LbfgsbProblem P;
+    P.n = (long long)b->plan->n_params;
+    for (size_t i = 0; i < b->probs.size(); ++i)
+        add_bounds(P, b->probs[i]->desc, b->probs[i]->F, (long long)b->plan->param_off[i]);
+    P.eval = [b](const float *x, float *g, double *f) {
+        return sr_batch_loss_and_grad(b, x, nullptr, nullptr, f, g);
+    };
+    return lbfgsb_run(P, params_dev, c, f_history, info, b->stream);
 }
 
 sr_status sr_batch_reset_optimizer(sr_batch *b) {

@@ -6,11 +6,11 @@
 // The device holds the n-vectors: the parameters, the gradient, the trial point and gradient,
 // the search direction and the pairs S, Y (column j at offset j n of a set of m + 1 columns).
 // Everything n-long runs in the kernels below; the small algebra (2k x 2k) runs on the host in
-// FP64.  The bounds of the problems this library optimises are lower bounds on one contiguous
-// range of the parameter vector (the amplitudes; for a PSF fit also the Moffat alpha and beta),
-// so the breakpoints of the generalised Cauchy point are those of that range: the host copies the
-// range (x, g and the rows of W) each iteration, sorts its breakpoints and walks them in order, and
-// corrects the all-variable reductions for the variables it fixes at their bounds.
+// FP64.  The bounds of the problems this library optimises are lower bounds on a few contiguous
+// ranges of the parameter vector (the amplitudes of each field; for a PSF fit also the Moffat alpha
+// and beta), so the breakpoints of the generalised Cauchy point are those of the bounded set: a
+// gather kernel packs its x, g and rows of W, the host sorts its breakpoints and walks them in
+// order, and corrects the all-variable reductions for the variables it fixes at their bounds.
 //
 // Per iteration:
 //   lbfgs_coldots_kernel   W^T g and g^T g (the Cauchy path's p = W^T d and f' = -d^T d)
@@ -83,7 +83,6 @@ struct DirArgs {
     double theta, told, alpha;
     double u[2 * kLbfgsMaxMemory];  // M c
     double v[2 * kLbfgsMaxMemory];  // the subspace solution
-    long long r0, r1;   // the bounded range
 };
 
 // d_i = x^c_i - x_i + alpha* du_i (free) or x^c_i - x_i (fixed); outside the bounded range
@@ -91,14 +90,15 @@ struct DirArgs {
 __global__ void __launch_bounds__(kLbThreads) lbfgs_dir_kernel(DirArgs a, const float *__restrict__ x,
                                                                const float *__restrict__ g, const float *__restrict__ S,
                                                                const float *__restrict__ Y, long long n,
+                                                               const int *__restrict__ ridx,
                                                                const float *__restrict__ xcR,
                                                                const unsigned char *__restrict__ fixR,
                                                                float *__restrict__ d) {
     for (long long i = blockIdx.x * (long long)kLbThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kLbThreads) {
-        const bool inR = i >= a.r0 && i < a.r1;
+        const int r = ridx[i];  // slot in the bounded set, -1 for an unbounded variable
         const double xi = x[i], gi = g[i];
-        const double xci = inR ? (double)xcR[i - a.r0] : xi - a.told * gi;
-        if (inR && fixR[i - a.r0]) {
+        const double xci = r >= 0 ? (double)xcR[r] : xi - a.told * gi;
+        if (r >= 0 && fixR[r]) {
             d[i] = (float)(xci - xi);
             continue;
         }
@@ -114,6 +114,29 @@ __global__ void __launch_bounds__(kLbThreads) lbfgs_dir_kernel(DirArgs a, const 
     }
 }
 
+// the bounded set packed: x, g and the k stored columns of Y then of S at its variables
+__global__ void lbfgs_gather_kernel(const long long *__restrict__ rsrc, long long nR, const float *__restrict__ x,
+                                    const float *__restrict__ g, const float *__restrict__ S,
+                                    const float *__restrict__ Y, long long n, DirArgs a, float *__restrict__ ox,
+                                    float *__restrict__ og, float *__restrict__ oW) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nR; j += (long long)gridDim.x * blockDim.x) {
+        const long long i = rsrc[j];
+        ox[j] = x[i];
+        og[j] = g[i];
+        for (int c = 0; c < a.k; ++c) {
+            oW[(long long)c * nR + j] = Y[(long long)a.slot[c] * n + i];
+            oW[(long long)(a.k + c) * nR + j] = S[(long long)a.slot[c] * n + i];
+        }
+    }
+}
+
+// bounded variables clipped into their bounds
+__global__ void lbfgs_clip_kernel(const long long *__restrict__ rsrc, long long nR, const float *__restrict__ loR,
+                                  float *__restrict__ x) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nR; j += (long long)gridDim.x * blockDim.x)
+        x[rsrc[j]] = fmaxf(x[rsrc[j]], loR[j]);
+}
+
 // s = xn - x and y = gn - g into ring column `col`
 __global__ void lbfgs_pair_kernel(const float *__restrict__ x, const float *__restrict__ xn, const float *__restrict__ g,
                                   const float *__restrict__ gn, long long n, float *__restrict__ s,
@@ -126,14 +149,14 @@ __global__ void lbfgs_pair_kernel(const float *__restrict__ x, const float *__re
 
 __global__ void __launch_bounds__(kLbThreads) lbfgs_pgnorm_kernel(const float *__restrict__ x,
                                                                   const float *__restrict__ g, long long n,
-                                                                  long long r0, long long r1,
+                                                                  const int *__restrict__ ridx,
                                                                   const float *__restrict__ loR,
                                                                   float *__restrict__ part) {
     __shared__ float red[kLbThreads];
     float m = 0.f;
     for (long long i = blockIdx.x * (long long)kLbThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kLbThreads) {
         float t = x[i] - g[i];
-        if (i >= r0 && i < r1) t = fmaxf(t, loR[i - r0]);
+        if (ridx[i] >= 0) t = fmaxf(t, loR[ridx[i]]);
         m = fmaxf(m, fabsf(t - x[i]));
     }
     red[threadIdx.x] = m;
@@ -201,16 +224,18 @@ struct Dev {
 
 sr_status lbfgsb_run(const LbfgsbProblem &P, float *x, const sr_lbfgsb_cfg &cfg, double *f_hist, sr_lbfgsb_info *info,
                      cudaStream_t st) {
-    const long long n = P.n, r0 = P.r0, r1 = P.r1, nR = r1 - r0;
+    const long long n = P.n, nR = (long long)P.lo.size();
     const int m = cfg.m;
     int sms = 0, dev = 0;
     SR_CUDA(cudaGetDevice(&dev));
     SR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int nblk = (int)std::max(1LL, std::min<long long>((n + kLbThreads - 1) / kLbThreads, 2LL * sms));
     Dev D;
-    float *g, *xt, *gt, *d, *S, *Y, *xcR, *loR, *pgpart;
+    float *g, *xt, *gt, *d, *S, *Y, *xcR, *loR, *pgpart, *gx, *gg_, *gW;
     unsigned char *fixR;
     double *part;
+    int *ridx;
+    long long *rsrc;
     cudaError_t e = D.alloc(&g, n);
     if (!e) e = D.alloc(&xt, n);
     if (!e) e = D.alloc(&gt, n);
@@ -220,6 +245,11 @@ sr_status lbfgsb_run(const LbfgsbProblem &P, float *x, const sr_lbfgsb_cfg &cfg,
     if (!e) e = D.alloc(&xcR, nR);
     if (!e) e = D.alloc(&loR, nR);
     if (!e) e = D.alloc(&fixR, nR);
+    if (!e) e = D.alloc(&ridx, n);
+    if (!e) e = D.alloc(&rsrc, nR);
+    if (!e) e = D.alloc(&gx, nR);
+    if (!e) e = D.alloc(&gg_, nR);
+    if (!e) e = D.alloc(&gW, (size_t)2 * m * nR);
     if (!e) e = D.alloc(&pgpart, nblk);
     if (!e) e = D.alloc(&part, (size_t)nblk * kLbMaxDots);
     if (e) {
@@ -228,12 +258,27 @@ sr_status lbfgsb_run(const LbfgsbProblem &P, float *x, const sr_lbfgsb_cfg &cfg,
         return SR_ERR_OOM;
     }
     std::vector<float> hx(nR), hg(nR), hlo(P.lo.begin(), P.lo.end());
-    SR_CUDA(cudaMemcpyAsync(loR, hlo.data(), sizeof(float) * nR, cudaMemcpyHostToDevice, st));
-    // clip the bounded range into the box
-    SR_CUDA(cudaMemcpyAsync(hx.data(), x + r0, sizeof(float) * nR, cudaMemcpyDeviceToHost, st));
-    SR_CUDA(cudaStreamSynchronize(st));
-    for (long long i = 0; i < nR; ++i) hx[i] = std::max(hx[i], hlo[i]);
-    SR_CUDA(cudaMemcpyAsync(x + r0, hx.data(), sizeof(float) * nR, cudaMemcpyHostToDevice, st));
+    // the bounded set: slot of each variable (-1 outside), variable of each slot
+    {
+        std::vector<int> hr((size_t)n, -1);
+        std::vector<long long> hs;
+        hs.reserve((size_t)nR);
+        for (const auto &rg : P.ranges)
+            for (long long i = rg.first; i < rg.second; ++i) {
+                hr[(size_t)i] = (int)hs.size();
+                hs.push_back(i);
+            }
+        if ((long long)hs.size() != nR) {
+            set_error("sr_lbfgsb: %lld bounds for %zu bounded variables", nR, hs.size());
+            return SR_ERR_ARG;
+        }
+        SR_CUDA(cudaMemcpyAsync(ridx, hr.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+        SR_CUDA(cudaMemcpyAsync(rsrc, hs.data(), sizeof(long long) * nR, cudaMemcpyHostToDevice, st));
+        SR_CUDA(cudaMemcpyAsync(loR, hlo.data(), sizeof(float) * nR, cudaMemcpyHostToDevice, st));
+        SR_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    }
+    const int gR = (int)std::max(1LL, std::min<long long>((nR + 255) / 256, 8LL * sms));
+    if (nR > 0) lbfgs_clip_kernel<<<gR, 256, 0, st>>>(rsrc, nR, loR, x);
 
     auto dots = [&](const std::vector<std::pair<const float *, const float *>> &pr, std::vector<double> &out) -> sr_status {
         ColPtrs cp{};
@@ -262,7 +307,7 @@ sr_status lbfgsb_run(const LbfgsbProblem &P, float *x, const sr_lbfgsb_cfg &cfg,
     std::vector<std::vector<double>> SS, SY, YY;  // SY[i][j] = s_i . y_j
     double theta = 1.0, pg = 0.0;
     auto pgnorm = [&](double *out) -> sr_status {
-        lbfgs_pgnorm_kernel<<<nblk, kLbThreads, 0, st>>>(x, g, n, r0, r1, loR, pgpart);
+        lbfgs_pgnorm_kernel<<<nblk, kLbThreads, 0, st>>>(x, g, n, ridx, loR, pgpart);
         std::vector<float> hp(nblk);
         SR_CUDA(cudaMemcpyAsync(hp.data(), pgpart, sizeof(float) * nblk, cudaMemcpyDeviceToHost, st));
         SR_CUDA(cudaStreamSynchronize(st));
@@ -318,17 +363,18 @@ sr_status lbfgsb_run(const LbfgsbProblem &P, float *x, const sr_lbfgsb_cfg &cfg,
             Wg[k + j] = theta * dv[k + j];
         }
         const double gg = dv[k2];
-        // the bounded range on the host: x, g and the rows of W
-        SR_CUDA(cudaMemcpyAsync(hx.data(), x + r0, sizeof(float) * nR, cudaMemcpyDeviceToHost, st));
-        SR_CUDA(cudaMemcpyAsync(hg.data(), g + r0, sizeof(float) * nR, cudaMemcpyDeviceToHost, st));
+        // the bounded set on the host: x, g and the rows of W
         std::vector<float> hW((size_t)k2 * nR);
-        for (int j = 0; j < k; ++j) {
-            SR_CUDA(cudaMemcpyAsync(hW.data() + (size_t)j * nR, Y + (long long)slots[j] * n + r0, sizeof(float) * nR,
-                                    cudaMemcpyDeviceToHost, st));
-            SR_CUDA(cudaMemcpyAsync(hW.data() + (size_t)(k + j) * nR, S + (long long)slots[j] * n + r0,
-                                    sizeof(float) * nR, cudaMemcpyDeviceToHost, st));
+        if (nR > 0) {
+            DirArgs ga{};
+            ga.k = k;
+            for (int j = 0; j < k; ++j) ga.slot[j] = slots[j];
+            lbfgs_gather_kernel<<<gR, 256, 0, st>>>(rsrc, nR, x, g, S, Y, n, ga, gx, gg_, gW);
+            SR_CUDA(cudaMemcpyAsync(hx.data(), gx, sizeof(float) * nR, cudaMemcpyDeviceToHost, st));
+            SR_CUDA(cudaMemcpyAsync(hg.data(), gg_, sizeof(float) * nR, cudaMemcpyDeviceToHost, st));
+            if (k2) SR_CUDA(cudaMemcpyAsync(hW.data(), gW, sizeof(float) * k2 * nR, cudaMemcpyDeviceToHost, st));
+            SR_CUDA(cudaStreamSynchronize(st));
         }
-        SR_CUDA(cudaStreamSynchronize(st));
         auto wrow = [&](long long i, std::vector<double> &w) {
             w.resize(k2);
             for (int j = 0; j < k; ++j) {
@@ -399,8 +445,6 @@ sr_status lbfgsb_run(const LbfgsbProblem &P, float *x, const sr_lbfgsb_cfg &cfg,
         for (int j = 0; j < k; ++j) da.slot[j] = slots[j];
         da.theta = theta;
         da.told = told;
-        da.r0 = r0;
-        da.r1 = r1;
         std::vector<double> u(k2, 0.0), v(k2, 0.0);
         double alpha = 1.0;
         if (k) {
@@ -472,7 +516,7 @@ sr_status lbfgsb_run(const LbfgsbProblem &P, float *x, const sr_lbfgsb_cfg &cfg,
         for (long long i = 0; i < nR; ++i) xcR_f[i] = (float)xcR_h[i];
         SR_CUDA(cudaMemcpyAsync(xcR, xcR_f.data(), sizeof(float) * nR, cudaMemcpyHostToDevice, st));
         SR_CUDA(cudaMemcpyAsync(fixR, fix.data(), nR, cudaMemcpyHostToDevice, st));
-        lbfgs_dir_kernel<<<nblk, kLbThreads, 0, st>>>(da, x, g, S, Y, n, xcR, fixR, d);
+        lbfgs_dir_kernel<<<nblk, kLbThreads, 0, st>>>(da, x, g, S, Y, n, ridx, xcR, fixR, d);
         // line search along d
         std::vector<double> dd;
         if ((rs = dots({{d, d}, {g, d}}, dd)) != SR_OK) return rs;

@@ -10,10 +10,12 @@ namespace sr {
 
 constexpr int kLbfgsMaxMemory = 10;
 
-// One bound-constrained problem: n variables, lower bounds lo[i - r0] on the range [r0, r1)
-// (no other bounds), and eval(x, g, &f) = the loss and its gradient at the device vector x.
+// One bound-constrained problem: n variables, lower bounds on the variables of `ranges` ([begin,
+// end) index pairs, disjoint; lo holds their bounds in the order of the ranges), no other bounds,
+// and eval(x, g, &f) = the loss and its gradient at the device vector x.
 struct LbfgsbProblem {
-    long long n = 0, r0 = 0, r1 = 0;
+    long long n = 0;
+    std::vector<std::pair<long long, long long>> ranges;
     std::vector<float> lo;
     std::function<sr_status(const float *x, float *g, double *f)> eval;
 };

@@ -136,3 +136,40 @@ def test_lbfgsb_stops_on_its_criteria_and_rejects_bad_configurations():
     with pytest.raises(RuntimeError, match="SR_ERR_ARG"):
         p.lbfgsb(P, pgtol=-1.0)
     p.close()
+
+
+def test_batch_lbfgsb_matches_oracle_on_the_sum_of_fields():
+    """sr_batch_lbfgsb: L-BFGS-B on the total loss of three fields of different shapes (one
+    without point sources), each with its own amplitude bounds, against the oracle L-BFGS-B on
+    the concatenated problem."""
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    fields = [syn.small_deconv(60, E=3, N=12, f=2, K=9, M=2, J=3, lam=0.5),
+              syn.small_deconv(61, E=2, N=16, f=2, K=9, M=0, J=3, lam=0.5),
+              syn.small_deconv(62, E=4, N=12, f=2, K=9, M=1, J=3, lam=0.5)]
+    probs = [Problem.from_field(fd) for fd in fields]
+    b = Batch(probs)
+    starts = []
+    for fd in fields:
+        h, a, c, dl, gm = syn.unpack_deconv(fd.params.astype(np.float64), fd.E, fd.N, fd.f, fd.M)
+        starts.append(syn.pack_deconv(0.7 * h, 1.3 * a, c + 0.15, dl, gm))
+    x0 = b.pack(starts).astype(np.float64)
+    lo = np.full(x0.size, -np.inf)
+    for fd, o in zip(fields, b.offsets):
+        lo[o + fd.F ** 2:o + fd.F ** 2 + fd.E * fd.M] = 0.0
+    funs = [_deconv_fun(fd) for fd in fields]
+
+    def total(x):
+        L, g = 0.0, np.zeros_like(x)
+        for fd, o, fn in zip(fields, b.offsets, funs):
+            n = fd.params.size
+            Li, gi = fn(x[o:o + n])
+            L += Li
+            g[o:o + n] = gi
+        return L, g
+    ref = olb.lbfgsb(total, x0, lo, np.full(x0.size, np.inf), m=5, max_iter=5, pgtol=0.0, factr=0.0)
+    P = torch.from_numpy(x0.astype(np.float32)).cuda()
+    gpu = b.lbfgsb(P, max_iter=5, m=5, pgtol=0.0, factr=0.0)
+    _compare(ref, gpu, P.cpu().numpy().astype(np.float64))
+    b.close()
+    for p in probs:
+        p.close()
