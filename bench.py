@@ -557,7 +557,12 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     units = units_of(fields, pb)
     with torch.cuda.stream(stream):
-        probs = [Problem.from_field(fd, conv_mode=args.conv_mode, stream=stream) for fd in fields]
+        # each field's uploads and set-up run on one of a few side streams (they overlap on the
+        # GPU); the batch evaluates on `stream` after waiting for them
+        side = [torch.cuda.Stream() for _ in range(SIDE_STREAMS)]
+        probs = [Problem.from_field(fd, conv_mode=args.conv_mode, stream=side[i % SIDE_STREAMS])
+                 for i, fd in enumerate(fields)]
+        torch.cuda.synchronize()
         batch = Batch(probs, stream=stream) if probs else None
         psf = Problem.from_psf(pb, stream=stream) if pb is not None else None
         P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda() if batch else None
@@ -629,7 +634,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e and batch is not None:
-        e2e = measure_e2e(fields, probs, batch, psf, pb, max(1, min(args.steps, 3)), stream)
+        e2e = measure_e2e(fields, probs, batch, psf, pb, max(1, min(args.steps, 3)), stream, side)
 
     peaks, peak_src = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -737,10 +742,16 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def measure_e2e(fields, probs, batch, psf, pb, steps, stream):
+SIDE_STREAMS = 8
+
+
+def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
     """Host arrays in page-locked memory; each step copies data, noise, PSFs and
     parameters to the device through the C ABI, evaluates, and reads back the
-    gradient and the loss."""
+    gradient and the loss.  The fields' set-up calls run on their problems' side streams
+    (round-robin), so that uploads and kernel set-up of different fields overlap; the batch's
+    stream waits for all of them before the evaluation, which returns to the host (so the next
+    step's uploads never overwrite inputs still in use)."""
     import torch
 
     def pinned(a):
@@ -765,6 +776,10 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream):
             pr.set_data(d)
             pr.set_noise(s)
             pr.set_psfs(p)
+        for sd in side:
+            ev = torch.cuda.Event()
+            ev.record(sd)
+            stream.wait_event(ev)
         batch.loss_and_grad_host(params, grad)
         if psf is not None:
             psf.set_data(qd)

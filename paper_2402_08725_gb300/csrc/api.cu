@@ -1063,7 +1063,7 @@ sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device) {
     if (p->khat) {
         FieldDev fd;
         fill_field_common(fd, p);
-        launch_fft_kappa(fd, p->kappa, p->khat, p->stream);
+        launch_fft_kappa_fixed(fd, p->kappa, p->khat, p->stream);
     }
     SR_CUDA(cudaGetLastError());
     p->pending_check = true;

@@ -199,46 +199,6 @@ __device__ __forceinline__ void load_geom(FftGeom &g, const FieldDev &fd, float2
 }
 
 // ---------------------------------------------------------------------------------------------
-// Khat_{i,phi}: transforms of the folded kernels placed at tau mod L.  One block per (epoch, phi).
-// ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFftThreads)
-fft_kappa_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restrict__ khat) {
-    extern __shared__ __align__(16) float2 fsm[];
-    const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1;
-    const int nph = fd.f * fd.f;
-    const int item = blockIdx.x;
-    const int i = item / nph, ph = item - i * nph;
-    float2 *A = fsm, *B = fsm + L * H, *tw = fsm + 2 * L * H;
-    FftGeom g;
-    load_geom(g, fd, tw);
-    const int Tk = fd.Tk, tlo = fd.tau_lo, thi = tlo + Tk - 1;
-    const float *kap = kappa + ((long long)i * nph + ph) * Tk * Tk;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int p = warp; p < L / 2; p += nw) {
-        for (int x = lane; x < L; x += 32) {
-            float v[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int y = 2 * p + q;
-                const int ty = y <= thi ? y : y - L;
-                const int tx = x <= thi ? x : x - L;
-                v[q] = (ty >= tlo && ty <= thi && tx >= tlo && tx <= thi) ? kap[(ty - tlo) * Tk + (tx - tlo)] : 0.f;
-            }
-            A[p * Lp + x] = make_float2(v[0], v[1]);
-        }
-    }
-    __syncthreads();
-    float2 *S = fwd2d(A, B, g, L / 2);
-    // global layout: rows of Hp = H + 1 (even, for 16-byte column pairs), the pad column zero
-    const int Hp = H + 1;
-    float2 *out = khat + ((long long)i * nph + ph) * L * Hp;
-    for (int idx = threadIdx.x; idx < L * Hp; idx += blockDim.x) {
-        const int ky = idx / Hp, kx = idx - ky * Hp;
-        out[idx] = kx < H ? S[ky * H + kx] : make_float2(0.f, 0.f);
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
 // Hhat_phi: transforms of the phase images of h, F_phi[m] = h[f m + phi].  One block per
 // (fft field, phi); blockIdx.x indexes fft_fields[].
 // ---------------------------------------------------------------------------------------------
@@ -360,15 +320,8 @@ sr_status configure_fft_kernels(int optin, int *limit) {
     *limit = optin;
     sr_status s;
     if ((s = set_dyn_smem(fft_hhat_kernel, optin, limit)) != SR_OK) return s;
-    if ((s = set_dyn_smem(fft_kappa_kernel, optin, limit)) != SR_OK) return s;
     if ((s = set_dyn_smem(fft_hgrad_kernel, optin, limit)) != SR_OK) return s;
     return SR_OK;
-}
-
-void launch_fft_kappa(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st) {
-    const int L = fd.fft_L;
-    const int smem = fft_smem_bytes(L, 0, fd.f);
-    fft_kappa_kernel<<<fd.E * fd.f * fd.f, kFftThreads, smem, st>>>(fd, kappa, khat);
 }
 
 void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,

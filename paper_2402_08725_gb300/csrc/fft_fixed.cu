@@ -159,6 +159,9 @@ struct Fx {
     static constexpr int R1 = fx_r1(L), R2 = L / R1, H = L / 2 + 1, LH = L * H;
     static constexpr int HP = H + 1, LHP = L * HP;  // global spectra: row pitch HP (zero pad column)
     static constexpr int S = (R2 & 1) ? R2 : R2 + 1, PX = L, PY = R1 * S;
+    // per-buffer float2 count of a full-width transform (L/2 row pairs, every column), even
+    static constexpr int EBF0 = (L / 2) * (PY > PX ? PY : PX) > LHP ? (L / 2) * (PY > PX ? PY : PX) : LHP;
+    static constexpr int EBF = (EBF0 + 1) & ~1;
     static_assert(R1 > 0 && R1 * R2 == L && L % 4 == 0, "transform size not in the list");
 };
 
@@ -858,7 +861,62 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
     }
 }
 
+// Spectra of the folded PSF kernels (computed at set_psfs): item = epoch * f^2 + phase.  The
+// phase kernel kappa_phi (Tk x Tk, taps tau_lo .. tau_lo + Tk - 1 on each axis) belongs on the
+// L x L circle with tap tau at tau mod L.  It is placed instead at tau - tau_lo (rows and columns
+// 0 .. Tk - 1), so that the row passes of fx_fwd2d touch only its ceil(Tk/2) row pairs and Tk
+// columns, and the shift is restored on the spectrum (shift theorem):
+//   Khat[ky][kx] = W_L^((ky + kx) tau_lo) Khat'[ky][kx],   W_L = exp(-2 pi i / L).
+// Written as L rows of pitch HP with the pad column zero.
+template <int L>
+__device__ __noinline__ void kappa_item_fixed(const FieldDev &fd, const float *__restrict__ kappa,
+                                              float2 *__restrict__ khat, int item) {
+    using P = Fx<L>;
+    constexpr int R2 = P::R2, H = P::H, HP = P::HP, PX = P::PX, EB = P::EBF;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float2 *A = fx_dyn, *B = fx_dyn + EB, *TWL = B + EB, *tw = TWL + L;
+    for (int n = tid; n < L; n += nt) {
+        tw[n] = fd.fft_tw[n];
+        TWL[n] = fd.fft_tw[(n % R2) * (n / R2)];
+    }
+    const int nph = fd.f * fd.f, i = item / nph, ph = item - i * nph;
+    const int Tk = fd.Tk, np = (Tk + 1) / 2;
+    const float *kap = kappa + ((long long)i * nph + ph) * Tk * Tk;
+    for (int t = tid; t < np * Tk; t += nt) {
+        const int pr = t / Tk, x = t - pr * Tk;
+        const float v0 = kap[(2 * pr) * Tk + x];
+        const float v1 = 2 * pr + 1 < Tk ? kap[(2 * pr + 1) * Tk + x] : 0.f;
+        A[pr * PX + x] = make_float2(v0, v1);
+    }
+    __syncthreads();
+    fx_fwd2d<L>(A, B, EB, 1, np, 1.f / (float)np, Tk, TWL);
+    const int sh = ((fd.tau_lo % L) + L) % L;  // tau_lo mod L
+    float2 *out = khat + ((long long)i * nph + ph) * L * HP;
+    for (int idx = tid; idx < L * HP; idx += nt) {
+        const int ky = idx / HP, kx = idx - ky * HP;
+        out[idx] = kx < H ? cmul(A[idx], tw[((ky + kx) * sh) % L]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+}
+
 #define SR_FX_SIZES(X) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(60) X(64) X(72) X(80) X(96) X(100) X(108) X(120) X(128) X(144)
+
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_kappa_fixed_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restrict__ khat) {
+    const int n_items = fd.E * fd.f * fd.f;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        switch (fd.fft_L) {
+#define SR_FX_KCASE(LL)                                  \
+    case LL:                                             \
+        kappa_item_fixed<LL>(fd, kappa, khat, item);     \
+        break;
+            SR_FX_SIZES(SR_FX_KCASE)
+#undef SR_FX_KCASE
+            default:
+                break;  // not reached: transform sizes come from the list
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kFftThreads, 1)
 fft_chunk_fixed_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ items, int n_items,
@@ -942,7 +1000,27 @@ sr_status configure_fft_fixed(int optin, int *limit) {
     const int dyn = optin - (int)a.sharedSizeBytes;
     SR_CUDA(cudaFuncSetAttribute(fft_chunk_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
     *limit = dyn;
+    SR_CUDA(cudaFuncGetAttributes(&a, fft_kappa_fixed_kernel));
+    SR_CUDA(cudaFuncSetAttribute(fft_kappa_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)a.sharedSizeBytes));
     return SR_OK;
+}
+
+static int kappa_fixed_smem(int L) {
+    switch (L) {
+#define SR_FX_KSMEM(LL) \
+    case LL:            \
+        return (2 * Fx<LL>::EBF + 2 * LL) * (int)sizeof(float2);
+        SR_FX_SIZES(SR_FX_KSMEM)
+#undef SR_FX_KSMEM
+        default:
+            return 0;
+    }
+}
+
+void launch_fft_kappa_fixed(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st) {
+    const int n_items = fd.E * fd.f * fd.f;
+    fft_kappa_fixed_kernel<<<n_items, kFftThreads, kappa_fixed_smem(fd.fft_L), st>>>(fd, kappa, khat);
 }
 
 sr_status occupancy_fft_fixed(int smem, int *blocks) {

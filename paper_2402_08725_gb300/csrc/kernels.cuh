@@ -31,7 +31,7 @@ void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_par
 // --- frequency-domain form (fft.cu) ---
 int fft_smem_bytes(int L, int M, int f);
 sr_status configure_fft_kernels(int optin, int *limit);
-void launch_fft_kappa(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st);
+
 void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
                      const float *params, float2 *hhat, cudaStream_t st);
 void launch_fft_hgrad(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
@@ -43,6 +43,8 @@ int fft_fixed_next(int need);  // smallest listed size >= need, 0 if none
 int fft_fixed_epoch_buffer(int L, int N);
 int fft_fixed_smem_bytes(int L, int N, int M, int f, int G);
 sr_status configure_fft_fixed(int optin, int *limit);
+// spectra of a problem's folded kernels (set_psfs): [E][f*f][L][L/2+2], the pad column zero
+void launch_fft_kappa_fixed(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st);
 sr_status occupancy_fft_fixed(int smem, int *blocks);
 void launch_fft_chunks_fixed(const FieldDev *fields, const int4 *items, int n_items, int *counter,
                              const float *params, const float2 *hhat, float2 *acc, double *chi_part,
