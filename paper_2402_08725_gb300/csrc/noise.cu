@@ -122,7 +122,7 @@ __device__ __forceinline__ void corr_row(float (&acc)[kCorrRY][2][4], const floa
                                          const float *__restrict__ ss, int r, int KP) {
     const int G = KP / 4;
     float4 A0 = xp[0], A1 = xp[16];
-#pragma unroll 2
+#pragma unroll 4
     for (int g = 0; g < G; ++g) {
         const float4 B0 = xp[g + 1], B1 = xp[g + 17];
         const float xa[2][8] = {{A0.x, A0.y, A0.z, A0.w, B0.x, B0.y, B0.z, B0.w},
