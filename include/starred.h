@@ -242,6 +242,22 @@ sr_status sr_set_state(sr_problem *p, const float *m_dev, const float *v_dev, in
  * parameter vector is the concatenation of the fields' packed vectors;
  * sr_batch_param_offset gives field i's offset. */
 sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream, sr_batch **out);
+
+/* The inputs of every member at once: the arrays of the members' sr_set_data / sr_set_noise /
+ * sr_set_psfs calls concatenated in batch order (float32, host or device as on_device says;
+ * page-locked host memory makes the single copy asynchronous).  The same effect as those calls on
+ * each member, with one host-to-device copy and a few launches for the whole batch (the PSFs'
+ * folding and, for members of the transform form, their kernel spectra included), ordered on the
+ * batch's stream; the members' own streams must have no set-up or evaluation of these members in
+ * flight.  From host memory each kind is staged by a copy on an internal stream that overlaps
+ * the set-up of the other kinds (calling sr_batch_set_psfs first lets its folding and spectra run
+ * under the data and noise copies); the host array must stay valid until the batch's stream has
+ * passed the call.  Checks and errors as the per-member calls (reported by the next call that
+ * returns a host value).  The first call allocates a table of the members and one staging buffer
+ * per kind (the packed data, noise and PSF sizes). */
+sr_status sr_batch_set_data(sr_batch *b, const float *d, int on_device);
+sr_status sr_batch_set_noise(sr_batch *b, const float *sigma, int on_device);
+sr_status sr_batch_set_psfs(sr_batch *b, const float *s, int on_device);
 sr_status sr_batch_destroy(sr_batch *b);
 size_t sr_batch_param_count(const sr_batch *b);
 sr_status sr_batch_param_offset(const sr_batch *b, int i, size_t *offset);

@@ -246,6 +246,25 @@ class Batch:
             nat.check(self.lib.sr_batch_param_offset(h, i, ctypes.byref(o)), "sr_batch_param_offset")
             self.offsets.append(int(o.value))
 
+    def _set(self, fn, name, x):
+        if isinstance(x, torch.Tensor):
+            t = x.detach().float().contiguous()
+            nat.check(fn(self.handle, ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0), name)
+            return t
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+        nat.check(fn(self.handle, ctypes.c_void_p(a.ctypes.data), 0), name)
+        return a
+
+    def set_data(self, d):
+        """Every member's data, concatenated in batch order (sr_batch_set_data)."""
+        return self._set(self.lib.sr_batch_set_data, "sr_batch_set_data", d)
+
+    def set_noise(self, sigma):
+        return self._set(self.lib.sr_batch_set_noise, "sr_batch_set_noise", sigma)
+
+    def set_psfs(self, s):
+        return self._set(self.lib.sr_batch_set_psfs, "sr_batch_set_psfs", s)
+
     def pack(self, vectors):
         """Concatenate per-field parameter vectors (numpy or torch) in batch order."""
         if isinstance(vectors[0], torch.Tensor):

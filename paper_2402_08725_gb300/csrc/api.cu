@@ -1,6 +1,7 @@
 // Host side of the C ABI (include/starred.h): problem and batch objects, input validation,
 // work-list construction, the evaluation launch sequence, and optimiser graphs.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -249,6 +250,26 @@ struct sr_batch {
     cudaStream_t stream = nullptr;
     std::vector<sr_problem *> probs;
     std::vector<char> pts_enabled;  // each problem's point-source prior state when the plan was built
+    // batched input set-up (sr_batch_set_*), built at its first use
+    DevArena bio_arena;
+    BioEntry *bio_tab = nullptr;
+    long long *bio_off_d = nullptr, *bio_off_s = nullptr, *bio_off_k = nullptr;
+    long long bio_total_d = 0, bio_total_s = 0, bio_total_k = 0;
+    int2 *bio_items = nullptr;
+    std::vector<std::array<int, 3>> bio_ranges;  // (transform size L, first item, items) per size
+    // host inputs are staged per kind (0 data, 1 noise, 2 PSFs) by copies on an internal stream:
+    // a kind's copy waits until the launches that read its previous contents are done (free), the
+    // batch's stream waits for the copy (copied), so copies overlap the set-up of other kinds
+    float *bio_stage[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t bio_io = nullptr;
+    cudaEvent_t bio_free[3] = {nullptr, nullptr, nullptr}, bio_copied[3] = {nullptr, nullptr, nullptr};
+    ~sr_batch() {
+        if (bio_io) cudaStreamDestroy(bio_io);
+        for (int k = 0; k < 3; ++k) {
+            if (bio_free[k]) cudaEventDestroy(bio_free[k]);
+            if (bio_copied[k]) cudaEventDestroy(bio_copied[k]);
+        }
+    }
     Plan *plan = nullptr;
 };
 
@@ -1423,6 +1444,132 @@ sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_op
         SR_CUDA(cudaStreamSynchronize(b->stream));
         if ((st = batch_check(b)) != SR_OK) return st;
     }
+    return SR_OK;
+}
+
+// The table of the batched set-up: each member's buffers and shape, prefix offsets of the packed
+// inputs, the kernel-spectra items, and a staging buffer for inputs that come from the host.
+static sr_status batch_io_prepare(sr_batch *b) {
+    if (b->bio_tab) return SR_OK;
+    const int n = (int)b->probs.size();
+    std::vector<BioEntry> tab(n);
+    std::vector<long long> od(n + 1, 0), os(n + 1, 0), ok(n + 1, 0);
+    std::vector<int2> items;
+    for (int i = 0; i < n; ++i) {
+        sr_problem *p = b->probs[i];
+        const sr_problem_desc &d = p->desc;
+        BioEntry &e = tab[i];
+        e.d = p->d;
+        e.w = p->w;
+        e.s = p->s;
+        e.kappa = p->kappa;
+        e.flag = p->d_flag;
+        e.E = d.n_epochs;
+        e.N = d.data_n;
+        e.K = d.psf_k;
+        e.f = d.supersampling;
+        e.Tk = p->Tk;
+        e.tau_lo = p->tau_lo;
+        od[i + 1] = od[i] + (long long)e.E * e.N * e.N;
+        os[i + 1] = os[i] + (long long)e.E * e.K * e.K;
+        ok[i + 1] = ok[i] + (long long)e.E * e.f * e.f * e.Tk * e.Tk;
+        if (p->khat)
+            for (int j = 0; j < e.E * e.f * e.f; ++j) items.push_back(make_int2(i, j));
+    }
+    // items grouped by transform size: one launch per size with that size's block
+    std::stable_sort(items.begin(), items.end(), [&](const int2 &a, const int2 &c) {
+        return b->probs[a.x]->fft_L < b->probs[c.x]->fft_L;
+    });
+    for (size_t j = 0; j < items.size(); ++j) {
+        const int L = b->probs[items[j].x]->fft_L;
+        if (b->bio_ranges.empty() || b->bio_ranges.back()[0] != L) b->bio_ranges.push_back({L, (int)j, 0});
+        ++b->bio_ranges.back()[2];
+    }
+    DevArena &A = b->bio_arena;
+    sr_status st;
+    if ((st = A.alloc(&b->bio_tab, (size_t)n)) != SR_OK) return st;
+    if ((st = A.alloc(&b->bio_off_d, (size_t)n + 1)) != SR_OK) return st;
+    if ((st = A.alloc(&b->bio_off_s, (size_t)n + 1)) != SR_OK) return st;
+    if ((st = A.alloc(&b->bio_off_k, (size_t)n + 1)) != SR_OK) return st;
+    if ((st = A.alloc(&b->bio_items, items.size())) != SR_OK) return st;
+    const size_t stage_len[3] = {(size_t)od[n], (size_t)od[n], (size_t)os[n]};
+    for (int k = 0; k < 3; ++k)
+        if ((st = A.alloc(&b->bio_stage[k], stage_len[k])) != SR_OK) return st;
+    SR_CUDA(cudaStreamCreateWithFlags(&b->bio_io, cudaStreamNonBlocking));
+    for (int k = 0; k < 3; ++k) {
+        SR_CUDA(cudaEventCreateWithFlags(&b->bio_free[k], cudaEventDisableTiming));
+        SR_CUDA(cudaEventCreateWithFlags(&b->bio_copied[k], cudaEventDisableTiming));
+        SR_CUDA(cudaEventRecord(b->bio_free[k], b->stream));
+    }
+    SR_CUDA(cudaMemcpy(b->bio_tab, tab.data(), sizeof(BioEntry) * n, cudaMemcpyHostToDevice));
+    SR_CUDA(cudaMemcpy(b->bio_off_d, od.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    SR_CUDA(cudaMemcpy(b->bio_off_s, os.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    SR_CUDA(cudaMemcpy(b->bio_off_k, ok.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    if (!items.empty())
+        SR_CUDA(cudaMemcpy(b->bio_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+    b->bio_total_d = od[n];
+    b->bio_total_s = os[n];
+    b->bio_total_k = ok[n];
+    return SR_OK;
+}
+
+// The packed input of kind k on the device: the caller's device array, or the kind's staging
+// buffer after one copy on the internal stream (ordered as described at bio_stage).
+static sr_status batch_io_source(sr_batch *b, int k, const float *src, long long count, int on_device,
+                                 const float **out) {
+    if (on_device) {
+        *out = src;
+        return SR_OK;
+    }
+    SR_CUDA(cudaStreamWaitEvent(b->bio_io, b->bio_free[k], 0));
+    SR_CUDA(cudaMemcpyAsync(b->bio_stage[k], src, sizeof(float) * count, cudaMemcpyHostToDevice, b->bio_io));
+    SR_CUDA(cudaEventRecord(b->bio_copied[k], b->bio_io));
+    SR_CUDA(cudaStreamWaitEvent(b->stream, b->bio_copied[k], 0));
+    *out = b->bio_stage[k];
+    return SR_OK;
+}
+
+sr_status sr_batch_set_data(sr_batch *b, const float *d, int on_device) {
+    if (!b || !d) return fail(SR_ERR_ARG, "NULL argument");
+    sr_status st;
+    const float *src;
+    if ((st = batch_io_prepare(b)) != SR_OK) return st;
+    if ((st = batch_io_source(b, 0, d, b->bio_total_d, on_device, &src)) != SR_OK) return st;
+    launch_bio_data(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d, b->stream);
+    SR_CUDA(cudaGetLastError());
+    SR_CUDA(cudaEventRecord(b->bio_free[0], b->stream));
+    for (sr_problem *p : b->probs) p->pending_check = true;
+    return SR_OK;
+}
+
+sr_status sr_batch_set_noise(sr_batch *b, const float *sigma, int on_device) {
+    if (!b || !sigma) return fail(SR_ERR_ARG, "NULL argument");
+    sr_status st;
+    const float *src;
+    if ((st = batch_io_prepare(b)) != SR_OK) return st;
+    if ((st = batch_io_source(b, 1, sigma, b->bio_total_d, on_device, &src)) != SR_OK) return st;
+    launch_bio_noise(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d, b->stream);
+    SR_CUDA(cudaGetLastError());
+    SR_CUDA(cudaEventRecord(b->bio_free[1], b->stream));
+    for (sr_problem *p : b->probs) p->pending_check = true;
+    return SR_OK;
+}
+
+sr_status sr_batch_set_psfs(sr_batch *b, const float *s, int on_device) {
+    if (!b || !s) return fail(SR_ERR_ARG, "NULL argument");
+    sr_status st;
+    const float *src;
+    if ((st = batch_io_prepare(b)) != SR_OK) return st;
+    if ((st = batch_io_source(b, 2, s, b->bio_total_s, on_device, &src)) != SR_OK) return st;
+    launch_bio_psfs(b->bio_tab, b->bio_off_s, b->bio_off_k, (int)b->probs.size(), src, b->bio_total_s,
+                    b->bio_total_k, b->stream);
+    SR_CUDA(cudaEventRecord(b->bio_free[2], b->stream));  // the staged PSFs are read by the copy kernel only
+    for (const auto &r : b->bio_ranges)
+        if ((st = launch_fft_kappa_fixed_batch(b->plan->d_fields, b->bio_items + r[1], r[2], r[0], g_num_sms,
+                                               b->stream)) != SR_OK)
+            return st;
+    SR_CUDA(cudaGetLastError());
+    for (sr_problem *p : b->probs) p->pending_check = true;
     return SR_OK;
 }
 

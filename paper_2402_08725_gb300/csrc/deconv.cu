@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "corr.cuh"
+#include "fold.cuh"
 #include "reduce.cuh"
 
 namespace sr {
@@ -37,31 +38,11 @@ namespace sr {
 // ---------------------------------------------------------------------------------------
 __global__ void kappa_prep_kernel(const float *__restrict__ s, float *__restrict__ kappa, int E, int K, int f,
                                   int Tk, int tau_lo) {
-    const long long total = (long long)E * f * f * Tk * Tk;
-    const int o = K / 2;
+    const long long per = (long long)f * f * Tk * Tk, total = (long long)E * per;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        long long r = idx;
-        const int tx = (int)(r % Tk); r /= Tk;
-        const int ty = (int)(r % Tk); r /= Tk;
-        const int ph = (int)(r % (f * f)); r /= (f * f);
-        const int i = (int)r;
-        const int phy = ph / f, phx = ph - phy * f;
-        // kappa(t) with t = f*tau - phi; kappa(t) = sum_{a,b<f} s[t + (a,b) + o]
-        const int t_y = f * (tau_lo + ty) - phy;
-        const int t_x = f * (tau_lo + tx) - phx;
-        double acc = 0.0;
-        const float *si = s + (long long)i * K * K;
-        for (int a = 0; a < f; ++a) {
-            const int qy = t_y + a + o;
-            if (qy < 0 || qy >= K) continue;
-            for (int b = 0; b < f; ++b) {
-                const int qx = t_x + b + o;
-                if (qx < 0 || qx >= K) continue;
-                acc += (double)si[qy * K + qx];
-            }
-        }
-        kappa[idx] = (float)acc;
+        const long long i = idx / per;
+        kappa[idx] = kappa_fold(s + i * K * K, K, f, Tk, tau_lo, idx - i * per);
     }
 }
 

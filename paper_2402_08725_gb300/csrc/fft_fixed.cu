@@ -918,6 +918,27 @@ fft_kappa_fixed_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__r
     }
 }
 
+// The kernel spectra of many problems in one launch: items[j] = (table entry, epoch * f^2 + phase);
+// every block takes items in turn (the spectra live at each entry's fft_khat).
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_kappa_fixed_batch_kernel(const FieldDev *__restrict__ fields, const int2 *__restrict__ items, int n_items) {
+    for (int j = blockIdx.x; j < n_items; j += gridDim.x) {
+        const int2 it = items[j];
+        const FieldDev &fd = fields[it.x];
+        float2 *khat = const_cast<float2 *>(fd.fft_khat);
+        switch (fd.fft_L) {
+#define SR_FX_BCASE(LL)                                      \
+    case LL:                                                 \
+        kappa_item_fixed<LL>(fd, fd.kappa, khat, it.y);      \
+        break;
+            SR_FX_SIZES(SR_FX_BCASE)
+#undef SR_FX_BCASE
+            default:
+                break;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kFftThreads, 1)
 fft_chunk_fixed_kernel(const FieldDev *__restrict__ fields, const int4 *__restrict__ items, int n_items,
                        int *__restrict__ counter, const float *__restrict__ params,
@@ -1003,6 +1024,9 @@ sr_status configure_fft_fixed(int optin, int *limit) {
     SR_CUDA(cudaFuncGetAttributes(&a, fft_kappa_fixed_kernel));
     SR_CUDA(cudaFuncSetAttribute(fft_kappa_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)a.sharedSizeBytes));
+    SR_CUDA(cudaFuncGetAttributes(&a, fft_kappa_fixed_batch_kernel));
+    SR_CUDA(cudaFuncSetAttribute(fft_kappa_fixed_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)a.sharedSizeBytes));
     return SR_OK;
 }
 
@@ -1018,9 +1042,38 @@ static int kappa_fixed_smem(int L) {
     }
 }
 
+// Threads of a kernel-spectra block: one per work item of the widest pass (the column passes,
+// H * max(R1, R2)), in whole warps, at most kFftThreads: small transforms then pack several
+// blocks per SM instead of leaving most of a full-size block idle.
+static int kappa_fixed_threads(int L) {
+    switch (L) {
+#define SR_FX_KTHR(LL)                                                                       \
+    case LL: {                                                                               \
+        const int w = Fx<LL>::H * (Fx<LL>::R1 > Fx<LL>::R2 ? Fx<LL>::R1 : Fx<LL>::R2);      \
+        return std::min(kFftThreads, (w + 31) / 32 * 32);                                    \
+    }
+        SR_FX_SIZES(SR_FX_KTHR)
+#undef SR_FX_KTHR
+        default:
+            return kFftThreads;
+    }
+}
+
+sr_status launch_fft_kappa_fixed_batch(const FieldDev *fields, const int2 *items, int n_items, int L, int n_sms,
+                                       cudaStream_t st) {
+    if (n_items <= 0) return SR_OK;
+    const int threads = kappa_fixed_threads(L), smem = kappa_fixed_smem(L);
+    int occ = 0;
+    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fft_kappa_fixed_batch_kernel, threads, smem));
+    const int grid = std::min(n_items, std::max(occ, 1) * n_sms);
+    fft_kappa_fixed_batch_kernel<<<grid, threads, smem, st>>>(fields, items, n_items);
+    return SR_OK;
+}
+
 void launch_fft_kappa_fixed(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st) {
     const int n_items = fd.E * fd.f * fd.f;
-    fft_kappa_fixed_kernel<<<n_items, kFftThreads, kappa_fixed_smem(fd.fft_L), st>>>(fd, kappa, khat);
+    fft_kappa_fixed_kernel<<<n_items, kappa_fixed_threads(fd.fft_L), kappa_fixed_smem(fd.fft_L), st>>>(fd, kappa,
+                                                                                                     khat);
 }
 
 sr_status occupancy_fft_fixed(int smem, int *blocks) {

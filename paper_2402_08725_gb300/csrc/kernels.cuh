@@ -45,6 +45,25 @@ int fft_fixed_smem_bytes(int L, int N, int M, int f, int G);
 sr_status configure_fft_fixed(int optin, int *limit);
 // spectra of a problem's folded kernels (set_psfs): [E][f*f][L][L/2+2], the pad column zero
 void launch_fft_kappa_fixed(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st);
+// the same for (entry, epoch * f^2 + phase) items of a table whose entries all have transform size L
+// (each entry's kappa and fft_khat), a persistent grid of as many blocks as fit on n_sms SMs
+sr_status launch_fft_kappa_fixed_batch(const FieldDev *fields, const int2 *items, int n_items, int L, int n_sms,
+                                       cudaStream_t st);
+
+// --- batched input set-up (batch_io.cu) ---
+// One entry per problem of a batch: its device buffers and shape, for the packed inputs of
+// sr_batch_set_data / _noise / _psfs (each problem's block at its prefix offset).
+struct BioEntry {
+    float *d, *w, *s, *kappa;
+    int *flag;
+    int E, N, K, f, Tk, tau_lo;
+};
+void launch_bio_data(const BioEntry *tab, const long long *off, int n, const float *src, long long total,
+                     cudaStream_t st);
+void launch_bio_noise(const BioEntry *tab, const long long *off, int n, const float *src, long long total,
+                      cudaStream_t st);
+void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long long *off_k, int n, const float *src,
+                     long long total_s, long long total_k, cudaStream_t st);
 sr_status occupancy_fft_fixed(int smem, int *blocks);
 void launch_fft_chunks_fixed(const FieldDev *fields, const int4 *items, int n_items, int *counter,
                              const float *params, const float2 *hhat, float2 *acc, double *chi_part,
