@@ -80,7 +80,7 @@ typedef enum {
     SR_ERR_OOM = 5,         /* device or host allocation failed */
     SR_ERR_NONFINITE = 6,   /* NaN/Inf input or non-finite loss */
     SR_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
-    SR_ERR_UNSUPPORTED = 8  /* valid request that this build does not support */
+    SR_ERR_UNSUPPORTED = 8  /* valid request that the library does not support */
 } sr_status;
 
 typedef enum { SR_DECONV = 0, SR_PSF = 1 } sr_kind;
