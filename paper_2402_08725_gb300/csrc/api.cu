@@ -261,6 +261,8 @@ struct sr_batch {
     // a kind's copy waits until the launches that read its previous contents are done (free), the
     // batch's stream waits for the copy (copied), so copies overlap the set-up of other kinds
     float *bio_stage[3] = {nullptr, nullptr, nullptr};
+    int *bio_flags = nullptr;   // the members' input flags gathered for one read-back
+    bool bio_pending = false;   // a batched set-up call since the last check
     cudaStream_t bio_io = nullptr;
     cudaEvent_t bio_free[3] = {nullptr, nullptr, nullptr}, bio_copied[3] = {nullptr, nullptr, nullptr};
     ~sr_batch() {
@@ -1392,6 +1394,18 @@ static sr_status batch_check(sr_batch *b) {
             if (st != SR_OK) return st;
         }
     }
+    if (b->bio_pending) {
+        // after batched set-up every flag write is ordered on the batch's stream (the members' own
+        // pending set-up was synchronised just above): one gather
+        const int n = (int)b->probs.size();
+        std::vector<int> fl(n);
+        launch_bio_flags(b->bio_tab, n, b->bio_flags, b->stream);
+        SR_CUDA(cudaMemcpyAsync(fl.data(), b->bio_flags, sizeof(int) * n, cudaMemcpyDeviceToHost, b->stream));
+        SR_CUDA(cudaStreamSynchronize(b->stream));
+        b->bio_pending = false;
+        for (int i = 0; i < n; ++i)
+            if (fl[i]) return fail(SR_ERR_NONFINITE, "a non-finite value (or sigma <= 0) was found in the inputs of field %d", i);
+    }
     return SR_OK;
 }
 
@@ -1492,6 +1506,7 @@ static sr_status batch_io_prepare(sr_batch *b) {
     if ((st = A.alloc(&b->bio_off_s, (size_t)n + 1)) != SR_OK) return st;
     if ((st = A.alloc(&b->bio_off_k, (size_t)n + 1)) != SR_OK) return st;
     if ((st = A.alloc(&b->bio_items, items.size())) != SR_OK) return st;
+    if ((st = A.alloc(&b->bio_flags, (size_t)n)) != SR_OK) return st;
     const size_t stage_len[3] = {(size_t)od[n], (size_t)od[n], (size_t)os[n]};
     for (int k = 0; k < 3; ++k)
         if ((st = A.alloc(&b->bio_stage[k], stage_len[k])) != SR_OK) return st;
@@ -1538,7 +1553,7 @@ sr_status sr_batch_set_data(sr_batch *b, const float *d, int on_device) {
     launch_bio_data(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d, b->stream);
     SR_CUDA(cudaGetLastError());
     SR_CUDA(cudaEventRecord(b->bio_free[0], b->stream));
-    for (sr_problem *p : b->probs) p->pending_check = true;
+    b->bio_pending = true;
     return SR_OK;
 }
 
@@ -1551,7 +1566,7 @@ sr_status sr_batch_set_noise(sr_batch *b, const float *sigma, int on_device) {
     launch_bio_noise(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d, b->stream);
     SR_CUDA(cudaGetLastError());
     SR_CUDA(cudaEventRecord(b->bio_free[1], b->stream));
-    for (sr_problem *p : b->probs) p->pending_check = true;
+    b->bio_pending = true;
     return SR_OK;
 }
 
@@ -1569,7 +1584,7 @@ sr_status sr_batch_set_psfs(sr_batch *b, const float *s, int on_device) {
                                                b->stream)) != SR_OK)
             return st;
     SR_CUDA(cudaGetLastError());
-    for (sr_problem *p : b->probs) p->pending_check = true;
+    b->bio_pending = true;
     return SR_OK;
 }
 

@@ -76,6 +76,14 @@ __global__ void bio_kappa_kernel(const BioEntry *__restrict__ tab, const long lo
     }
 }
 
+// every entry's input flag into out[] (then cleared): one read-back for the whole batch
+__global__ void bio_flags_kernel(const BioEntry *__restrict__ tab, int n, int *__restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        out[i] = *tab[i].flag;
+        *tab[i].flag = 0;
+    }
+}
+
 int grid_of(long long n) {
     long long g = (n + 255) / 256;
     if (g > 152LL * 16) g = 152LL * 16;
@@ -83,6 +91,10 @@ int grid_of(long long n) {
 }
 
 }  // namespace
+
+void launch_bio_flags(const BioEntry *tab, int n, int *out, cudaStream_t st) {
+    bio_flags_kernel<<<(n + 255) / 256, 256, 0, st>>>(tab, n, out);
+}
 
 void launch_bio_data(const BioEntry *tab, const long long *off, int n, const float *src, long long total,
                      cudaStream_t st) {

@@ -60,6 +60,7 @@ struct BioEntry {
 };
 void launch_bio_data(const BioEntry *tab, const long long *off, int n, const float *src, long long total,
                      cudaStream_t st);
+void launch_bio_flags(const BioEntry *tab, int n, int *out, cudaStream_t st);
 void launch_bio_noise(const BioEntry *tab, const long long *off, int n, const float *src, long long total,
                       cudaStream_t st);
 void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long long *off_k, int n, const float *src,
