@@ -1,0 +1,81 @@
+"""Stored values under tests/golden/: the published noise levels of the B3 starlet, and oracle
+regression values written by tests/golden/make_oracle_golden.py (oracle only)."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def starlet_table():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "starlet_b3_white_noise.txt")) if not l.startswith("#")]
+    return {int(j): float(v) for j, v in rows}
+
+
+def oracle_rows():
+    out = {}
+    for l in open(os.path.join(GOLDEN, "oracle_small_cases.txt")):
+        if l.startswith("#"):
+            continue
+        t = l.split()
+        out[t[0]] = (float(t[1]), [float(v) for v in t[2:]])
+    return out
+
+
+def _maker():
+    spec = importlib.util.spec_from_file_location("make_oracle_golden", os.path.join(GOLDEN, "make_oracle_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_oracle_starlet_reproduces_the_published_noise_levels():
+    """A centred delta's detail planes have the L2 norms of the white-noise levels per scale."""
+    F, J = 257, 8
+    h = np.zeros((F, F))
+    h[128, 128] = 1.0
+    planes = oracle.starlet_analysis(h, J)
+    for j, sigma in starlet_table().items():
+        got = float(np.sqrt(np.sum(planes[j - 1] ** 2)))
+        assert abs(got - sigma) <= 1.5e-4, (j, got, sigma)  # the table's last digit
+
+
+def test_oracle_matches_its_stored_regression_values():
+    stored = oracle_rows()
+    for name, L, norms in _maker().rows():
+        L0, n0 = stored[name]
+        assert abs(L - L0) <= 1e-10 * abs(L0), name
+        np.testing.assert_allclose(norms, n0, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.gpu
+def test_gpu_matches_the_stored_oracle_values():
+    """The library's loss (1e-6 relative) and per-block gradient norms (1e-4 relative) on the
+    stored cases, against the stored oracle values."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_08725_gb300 import synthetic as syn
+    from paper_2402_08725_gb300.binding import Problem
+    stored = oracle_rows()
+    for name, seed, E, N, f, K, M, J, lam, lp in _maker().CASES:
+        fd = syn.small_deconv(seed, E=E, N=N, f=f, K=K, M=M, J=J, lam=lam)
+        p = Problem.from_field(fd)
+        if lp > 0:
+            p.set_lambda_pts(lp)
+        L, g = p.loss_and_grad(torch.from_numpy(fd.params.astype(np.float32)).cuda())
+        g = g.cpu().numpy().astype(np.float64)
+        F = f * N
+        o, norms = 0, []
+        for n in (F * F, E * M, 2 * M, 2 * E, E):
+            norms.append(float(np.linalg.norm(g[o:o + n])))
+            o += n
+        L0, n0 = stored[name]
+        assert abs(L - L0) <= 1e-6 * abs(L0), name
+        for v, r in zip(norms, n0):
+            assert abs(v - r) <= 1e-4 * max(r, 1e-12 * max(n0)), (name, v, r)
+        p.close()

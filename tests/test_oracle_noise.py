@@ -57,7 +57,9 @@ def test_normal_streams_depend_on_seed_and_index():
 
 
 # published standard deviations of the B3 starlet detail scales under unit white noise
-STARLET_WHITE_NOISE = [0.8907, 0.2007, 0.0856, 0.0413]
+# (tests/golden/starlet_b3_white_noise.txt, with its citation)
+_GOLDEN = __file__.rsplit("/", 1)[0] + "/golden/starlet_b3_white_noise.txt"
+STARLET_WHITE_NOISE = [float(l.split()[1]) for l in open(_GOLDEN) if not l.startswith("#")]
 
 
 def test_weights_white_noise_match_published_starlet_norms():
