@@ -173,3 +173,17 @@ def test_batch_lbfgsb_matches_oracle_on_the_sum_of_fields():
     b.close()
     for p in probs:
         p.close()
+
+
+def test_lbfgsb_with_a_memory_of_one_pair():
+    from paper_2402_08725_gb300.binding import Problem
+    fd = syn.small_deconv(45, E=2, N=12, f=2, K=9, M=1, J=3, lam=0.5)
+    h, a, c, dl, gm = syn.unpack_deconv(fd.params.astype(np.float64), fd.E, fd.N, fd.f, fd.M)
+    start = syn.pack_deconv(0.8 * h, 1.2 * a, c - 0.1, dl, gm).astype(np.float32).astype(np.float64)
+    lo, hi = _bounds_deconv(fd)
+    ref = olb.lbfgsb(_deconv_fun(fd), start, lo, hi, m=1, max_iter=5, pgtol=0.0, factr=0.0)
+    p = Problem.from_field(fd)
+    P = torch.from_numpy(start.astype(np.float32)).cuda()
+    gpu = p.lbfgsb(P, max_iter=5, m=1, pgtol=0.0, factr=0.0)
+    _compare(ref, gpu, P.cpu().numpy().astype(np.float64))
+    p.close()
