@@ -61,7 +61,7 @@ def _compare(N, f, K, J, sigma, s1, n_real, seed):
     (75, 2, 71, 4, 2, 6),     # 2 x 5 tiles with ragged edges, two kernel-row chunks
     (20, 3, 1, 4, 4, 100),    # delta PSF, f = 3
     (8, 1, 15, 3, 2, 200),    # PSF wider than the grid (K > F): taps outside read zero
-    (16, 2, 5, 5, 1, 40),     # the deepest starlet the grid allows (2 * 2^(J-2) = F - 1 = 31 > 16 fails; J=5: 16 <= 31)
+    (16, 2, 5, 5, 1, 40),     # the deepest starlet of this grid: 2 * 2^(J-2) = 16 <= F - 1 = 31 (J = 6 needs 32)
 ])
 def test_noise_weights_match_oracle(N, f, K, J, E, n_real):
     rng = np.random.default_rng(N * 100 + K)
