@@ -169,7 +169,7 @@ def fft_flops(fields):
     return fl
 
 
-CHUNK_SRCS = [os.path.join(ROOT, "paper_2402_08725_gb300", "csrc", n) for n in ("fft_fixed.cu", "common.cuh", "cplx.cuh")]
+CHUNK_SRCS = [os.path.join(ROOT, "paper_2402_08725_gb300", "csrc", n) for n in ("fft_fixed.cu", "common.cuh", "cplx.cuh", "ffsum.cuh")]
 CHUNK_PROFILE = os.path.join(ROOT, "profiles", "fft_chunk_fixed_kernel_config4.md")
 
 

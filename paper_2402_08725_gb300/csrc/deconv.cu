@@ -102,7 +102,7 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
            double *__restrict__ chi_part, double *__restrict__ se_part) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_item;
-    __shared__ double s_red[2][kThreads / 32];
+    __shared__ float2 s_red[2][kThreads / 32];
     __shared__ float4 s_src[kFusedSources];
     __shared__ int2 s_win[kFusedSources];
     const int tid = threadIdx.x;
@@ -235,8 +235,9 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                 }
             }
         }
-        // residual, chi^2 (FP64 accumulation), e = -w r
-        double chi = 0.0, se = 0.0;
+        // residual, chi^2 and sum e (FP32 over the thread's R pixels, compensated across the
+        // block), e = -w r
+        float chi_r = 0.f, se_r = 0.f;
         const int py = t.y0 + G.row;
         if (G.g == 0 && py < N) {
             const float bg = (float)(f * f) * gam;
@@ -248,14 +249,15 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                     const float Mv = acc[r] + bg;
                     const float res = __ldg(fd.d + base + px) - Mv;
                     const float wv = __ldg(fd.w + base + px);
-                    chi += (double)(0.5f * wv * res * res);
+                    chi_r += 0.5f * wv * res * res;
                     const float e = -wv * res;
                     ebuf[fd.ebuf_off + base + px] = e;
-                    se += (double)e;
+                    se_r += e;
                 }
             }
         }
-        block_sum2(chi, se, s_red);
+        double chi = 0.0, se = 0.0;
+        block_fsum2(FSum{chi_r, 0.f}, FSum{se_r, 0.f}, s_red, chi, se);
         if (tid == 0) {
             chi_part[t.slot] = chi;
             se_part[t.slot] = se;

@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "cplx.cuh"
+#include "ffsum.cuh"
 #include "kernels.cuh"
 
 namespace sr {
@@ -394,7 +395,7 @@ static_assert(kMaxG <= kBatch && kFftMaxSources <= kBatch, "accumulators are ind
 static_assert(kRedVals <= kFftThreads / 32 && kFftThreads / 32 <= 32, "one warp per reduced value, one lane per warp");
 
 struct FxShared {
-    double red[kRedVals][kFftThreads / 32];
+    float2 red[kRedVals][kFftThreads / 32];  // compensated partial sums (hi, lo)
     // the work item's parameters: amplitudes a_{i,k}, epoch shifts delta_i, backgrounds gamma_i
     // of its epochs, and the source positions c_k (loaded once per item)
     float ia[kFftChunk * kFftMaxSources];
@@ -616,7 +617,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         // w with w mod G = g take the row pairs of epoch g
         {
             const int g = warp & (G - 1), sub = warp >> lgG;
-            double chi = 0.0, se = 0.0;
+            FSum chi = fsum_zero(), se = fsum_zero();
             if (g < Ge) {
                 const int i = i0 + g;
                 const float gam = sh.ig[i - item.y];
@@ -670,18 +671,15 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                             }
                         }
                     }
-                    chi += (double)chi_r;
-                    se += (double)se_r;
+                    chi = fsum_add(chi, chi_r);
+                    se = fsum_add(se, se_r);
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                chi += __shfl_down_sync(0xffffffffu, chi, o);
-                se += __shfl_down_sync(0xffffffffu, se, o);
-            }
+            chi = fsum_warp(chi);
+            se = fsum_warp(se);
             if (lane == 0 && g < Ge) {
-                sh.red[g * nv + 0][sub] = chi;
-                sh.red[g * nv + 1][sub] = se;
+                sh.red[g * nv + 0][sub] = make_float2(chi.hi, chi.lo);
+                sh.red[g * nv + 1][sub] = make_float2(se.hi, se.lo);
             }
         }
         __syncthreads();
@@ -796,7 +794,7 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
             }
         }
         // fold per epoch (G > 1: batch element j belongs to epoch j mod G) and reduce over the
-        // warp in FP32, then across warps in FP64 below
+        // warp in FP32, then across warps as compensated sums below
         if (M > 0) {
 #pragma unroll
             for (int q = 0; q < kBatch; ++q) {
@@ -826,9 +824,9 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
                     }
                     if (lane == 0) {
                         const int g = G > 1 ? q : 0, k = G > 1 ? 0 : q;
-                        sh.red[g * nv + 2 + 3 * k][warp] = (double)a;
-                        sh.red[g * nv + 3 + 3 * k][warp] = (double)bx;
-                        sh.red[g * nv + 4 + 3 * k][warp] = (double)by;
+                        sh.red[g * nv + 2 + 3 * k][warp] = make_float2(a, 0.f);
+                        sh.red[g * nv + 3 + 3 * k][warp] = make_float2(bx, 0.f);
+                        sh.red[g * nv + 4 + 3 * k][warp] = make_float2(by, 0.f);
                     }
                 }
             }
@@ -838,10 +836,10 @@ __device__ __noinline__ void chunk_item_fixed(const FieldDev &fd, const int4 ite
         if (warp < Ge * nv) {
             const int g = warp / nv, q = warp - g * nv;
             const int cnt = q < 2 ? nsub : nw;
-            double sum = lane < cnt ? sh.red[warp][lane] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+            const float2 part = lane < cnt ? sh.red[warp][lane] : make_float2(0.f, 0.f);
+            const FSum tot = fsum_warp(FSum{part.x, part.y});
             if (lane == 0) {
+                const double sum = fsum_value(tot);
                 const int i = i0 + g;
                 if (q == 0) {
                     chi_part[fd.tile_slot + i] = sum;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "ffsum.cuh"
 
 namespace sr {
 
@@ -29,6 +30,27 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[k
         }
         a = sa;
         b = sb;
+    }
+}
+
+// The same over compensated FP32 pairs (FP64 only for the two results, on thread 0).
+__device__ __forceinline__ void block_fsum2(FSum a, FSum b, float2 (*red)[kThreads / 32], double &oa, double &ob) {
+    a = fsum_warp(a);
+    b = fsum_warp(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = make_float2(a.hi, a.lo);
+        red[1][wid] = make_float2(b.hi, b.lo);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        FSum sa = fsum_zero(), sb = fsum_zero();
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            sa = fsum_add(sa, FSum{red[0][i].x, red[0][i].y});
+            sb = fsum_add(sb, FSum{red[1][i].x, red[1][i].y});
+        }
+        oa = fsum_value(sa);
+        ob = fsum_value(sb);
     }
 }
 

@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "ffsum.cuh"
 #include "kernels.cuh"
 
 namespace sr {
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256)
 starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
                         double *__restrict__ l1_part, int j) {
     extern __shared__ float sb[];
-    __shared__ double s_red[8];
+    __shared__ float2 s_red[8];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
     if (j > J - 2 || !starlet_banded(F, J)) return;
@@ -204,26 +205,28 @@ starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     }
     __syncthreads();
     float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
-    double l1 = 0.0;
+    // |w| summed in FP32 along a row, the rows as compensated sums
+    FSum l1 = fsum_zero();
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const long long ro = (long long)(y0 + yy) * F;
+        float l1_row = 0.f;
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
 #pragma unroll
             for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(yy + 2 * s + m * s) * F + x];
             cn[ro + x] = acc;
-            l1 += (double)fabsf(cj[ro + x] - acc);
+            l1_row += fabsf(cj[ro + x] - acc);
         }
+        l1 = fsum_add(l1, l1_row);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l1 += __shfl_down_sync(0xffffffffu, l1, o);
-    if (lane == 0) s_red[warp] = l1;
+    l1 = fsum_warp(l1);
+    if (lane == 0) s_red[warp] = make_float2(l1.hi, l1.lo);
     __syncthreads();
     const long long base = fd.l1_slot + (long long)j * fd.n_chunks;
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < nwarp; ++w) t += s_red[w];
-        l1_part[base + b] = (double)fd.lambda * (double)fd.Wd[j] * t;
+        FSum t = fsum_zero();
+        for (int w = 0; w < nwarp; ++w) t = fsum_add(t, FSum{s_red[w].x, s_red[w].y});
+        l1_part[base + b] = (double)fd.lambda * (double)fd.Wd[j] * fsum_value(t);
     }
     if (b == 0) {  // the level's remaining partial-sum slots (one per 256-pixel chunk) stay zero
         const int nb = (F + kBandRows - 1) / kBandRows;
