@@ -564,7 +564,11 @@ def run_ours(args):
                  for i, fd in enumerate(fields)]
         torch.cuda.synchronize()
         batch = Batch(probs, stream=stream) if probs else None
-        psf = Problem.from_psf(pb, stream=stream) if pb is not None else None
+        # the PSF fit is independent of the batch: it runs on its own stream, forked from and
+        # joined to `stream` in every step, so that its small launches overlap the batch's
+        psf_stream = torch.cuda.Stream()
+        psf = Problem.from_psf(pb, stream=psf_stream) if pb is not None else None
+        fork, join = torch.cuda.Event(), torch.cuda.Event()
         P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda() if batch else None
         P0 = P.clone() if P is not None else None
         Q = torch.from_numpy(pb.params).cuda() if psf else None
@@ -574,10 +578,17 @@ def run_ours(args):
         stream.synchronize()
 
         def one_step():
-            if batch is not None:
-                batch.step(P, 1, cfg)
+            # queued without host synchronisation; the step ends when `stream` has joined the
+            # PSF fit's stream
             if psf is not None:
-                psf.step(Q, 1, cfg_psf)
+                fork.record(stream)
+                psf_stream.wait_event(fork)
+                psf.step(Q, 1, cfg_psf, sync=False)
+                join.record(psf_stream)
+            if batch is not None:
+                batch.step(P, 1, cfg, sync=False)
+            if psf is not None:
+                stream.wait_event(join)
 
         for _ in range(args.warmup):
             one_step()

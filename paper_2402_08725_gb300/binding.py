@@ -166,7 +166,11 @@ class Problem:
                                                  ctypes.c_void_p(grad_host.ctypes.data)), "sr_loss_and_grad_host")
         return loss.value, grad_host
 
-    def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg, losses: torch.Tensor | None = None) -> float:
+    def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg, losses: torch.Tensor | None = None,
+             sync: bool = True) -> float | None:
+        """n_steps optimiser updates in place (sr_step).  Returns the last loss, read back with a
+        synchronisation of the problem's stream; with sync=False nothing is read back (None) and
+        the call returns once the steps are queued."""
         last = ctypes.c_double()
         lp = None
         if losses is not None:
@@ -174,8 +178,8 @@ class Problem:
                 raise TypeError("losses must be a float64 CUDA tensor with n_steps values")
             lp = ctypes.c_void_p(losses.data_ptr())
         nat.check(self.lib.sr_step(self.handle, _cuda_f32(params, self.n_params, "params"), int(n_steps),
-                                   ctypes.byref(cfg), lp, ctypes.byref(last)), "sr_step")
-        return last.value
+                                   ctypes.byref(cfg), lp, ctypes.byref(last) if sync else None), "sr_step")
+        return last.value if sync else None
 
     def psf_model(self, params: torch.Tensor) -> torch.Tensor:
         """The narrow PSF s = Moffat + b of a PSF fit's parameters, [F][F] on the device; sr_psf_model."""
@@ -300,11 +304,13 @@ class Batch:
                   "sr_batch_loss_and_grad_host")
         return tot.value, grad_host
 
-    def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg) -> float:
+    def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg, sync: bool = True) -> float | None:
+        """n_steps optimiser updates of every field (sr_batch_step).  Returns the last total loss
+        (synchronises the batch's stream), or None without reading it back when sync=False."""
         last = ctypes.c_double()
         nat.check(self.lib.sr_batch_step(self.handle, _cuda_f32(params, self.n_params, "params"), int(n_steps),
-                                         ctypes.byref(cfg), ctypes.byref(last)), "sr_batch_step")
-        return last.value
+                                         ctypes.byref(cfg), ctypes.byref(last) if sync else None), "sr_batch_step")
+        return last.value if sync else None
 
     def lbfgsb(self, params: torch.Tensor, max_iter: int = 100, m: int = 10, max_ls: int = 20, pgtol: float = 1e-5,
                factr: float = 1e7):
