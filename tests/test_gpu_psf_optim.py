@@ -130,6 +130,42 @@ def test_graph_replay_equals_eager_and_checkpoint_resume():
     prob2.close()
 
 
+def test_steps_queued_without_read_back_on_two_streams():
+    """step(sync=False) queues the steps without reading the loss back: a PSF fit and a batch
+    stepped on two streams, forked from and joined to one stream by events, end bitwise where
+    the synchronising calls end."""
+    from paper_2402_08725_gb300.binding import Batch, Problem, optim_cfg
+    fd = syn.small_deconv(seed=34, E=3, N=32, f=2, K=15, M=1, J=3, lam=1.0)
+    pb = syn.small_psf(seed=35, S=3, N=16, f=2, J=3, lam=1.0)
+    cfg = optim_cfg("adabelief", lr=_lr(fd))
+    cfg_psf = optim_cfg("adabelief", lr=(1e-5, 1e-3, 10.0, 1e-3))
+    main, side = torch.cuda.Stream(), torch.cuda.Stream()
+    results = []
+    for sync in (True, False):
+        with torch.cuda.stream(main):
+            prob = Problem.from_field(fd, stream=main)
+            batch = Batch([prob], stream=main)
+            psf = Problem.from_psf(pb, stream=side)
+            P = torch.from_numpy(batch.pack([fd.params])).cuda()
+            Q = torch.from_numpy(pb.params).cuda()
+            torch.cuda.synchronize()
+            fork, join = torch.cuda.Event(), torch.cuda.Event()
+            for _ in range(4):
+                fork.record(main)
+                side.wait_event(fork)
+                r_psf = psf.step(Q, 1, cfg_psf, sync=sync)
+                join.record(side)
+                r_b = batch.step(P, 1, cfg, sync=sync)
+                main.wait_event(join)
+                assert (r_psf is None and r_b is None) if not sync else np.isfinite(r_psf + r_b)
+            main.synchronize()
+            results.append((P.clone(), Q.clone()))
+            batch.close()
+            prob.close()
+            psf.close()
+    assert torch.equal(results[0][0], results[1][0]) and torch.equal(results[0][1], results[1][1])
+
+
 def test_noiseless_recovery_on_gpu():
     """Data made by the oracle's model at known truth (no noise, lambda = 0):
     AdaBelief on (a, c) with h and delta held fixed recovers the truth."""
