@@ -25,7 +25,7 @@ constexpr int kMaxScales = 8;
 constexpr int kFftMaxStages = 8;
 constexpr int kFftThreads = 768;
 constexpr int kFftMaxSources = 4;  // point sources per field in the frequency-domain form
-constexpr int kFftChunk = 8;       // epochs per work item of the frequency-domain form
+constexpr int kFftChunk = 16;      // epochs per work item of the frequency-domain form
 constexpr int kThreads = 256;
 
 struct FieldDev {
