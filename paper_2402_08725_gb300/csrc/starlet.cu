@@ -238,7 +238,7 @@ __device__ __forceinline__ float gamma_of(float wv, float lw) { return wv > 0.f 
 
 // Adjoint level j as bands: T_j = gamma_{j+1} + Row_j^T Col_j^T V_{j+1} on rows [y0, y0 + 16),
 // written as V_j = T_j - gamma_j (j >= 1) or T_0 (j = 0) into plane J + (j & 1).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)  // at most 64 registers: four blocks per SM
 starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
     extern __shared__ float sb[];
     const FieldDev &fd = fields[blockIdx.y];
