@@ -240,7 +240,8 @@ sr_status sr_set_state(sr_problem *p, const float *m_dev, const float *v_dev, in
  * The problems must be fully set (data, noise, PSFs, weights) and must outlive
  * the batch; later set_* calls on them are seen by the batch.  The batch's
  * parameter vector is the concatenation of the fields' packed vectors;
- * sr_batch_param_offset gives field i's offset. */
+ * sr_batch_param_offset gives field i's offset.  1 <= n <= 65535 (fields index a
+ * grid dimension); otherwise SR_ERR_ARG. */
 sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream, sr_batch **out);
 
 /* The inputs of every member at once: the arrays of the members' sr_set_data / sr_set_noise /

@@ -609,6 +609,14 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         const double cb = (double)fb.fft_L * fb.fft_L * (2 + fb.f * fb.f) * (b.z - b.y);
         return ca > cb;
     });
+    // the per-field transform kernels (h spectra, h gradient) take the costliest fields first, so
+    // that their longest blocks start in the first wave; each block writes only its own field
+    std::stable_sort(fft_fields.begin(), fft_fields.end(), [&](int a, int b) {
+        const FieldDev &fa = pl->h_fields[a], &fb = pl->h_fields[b];
+        const double ca = (double)fa.fft_L * fa.fft_L * (fa.fft_n_chunks + 1);
+        const double cb = (double)fb.fft_L * fb.fft_L * (fb.fft_n_chunks + 1);
+        return ca > cb;
+    });
     pl->n_fft_items = (int)fft_items.size();
     pl->n_fft_fields = (int)fft_fields.size();
     pl->n_items = (int)items.size();
@@ -1334,6 +1342,7 @@ sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream,
     if (!out) return fail(SR_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!problems || n < 1) return fail(SR_ERR_ARG, "empty batch");
+    if (n > 65535) return fail(SR_ERR_ARG, "%d fields: a batch holds at most 65535", n);
     for (int i = 0; i < n; ++i) {
         sr_status st = check_ready(problems[i]);
         if (st != SR_OK) return st;

@@ -200,15 +200,15 @@ __device__ __forceinline__ void load_geom(FftGeom &g, const FieldDev &fd, float2
 
 // ---------------------------------------------------------------------------------------------
 // Hhat_phi: transforms of the phase images of h, F_phi[m] = h[f m + phi].  One block per
-// (fft field, phi); blockIdx.x indexes fft_fields[].
+// (fft field, phi): blockIdx.y indexes fft_fields[] (costliest fields first), blockIdx.x is phi.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kFftThreads)
 fft_hhat_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
                 const float *__restrict__ params, float2 *__restrict__ hhat_all) {
     extern __shared__ __align__(16) float2 fsm[];
-    const FieldDev &fd = fields[fft_fields[blockIdx.x]];
+    const FieldDev &fd = fields[fft_fields[blockIdx.y]];
     const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
-    const int ph = blockIdx.y;
+    const int ph = blockIdx.x;
     if (ph >= nph) return;
     const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1;
     float2 *A = fsm, *B = fsm + L * H, *tw = fsm + 2 * L * H;
@@ -247,9 +247,9 @@ __global__ void __launch_bounds__(kFftThreads)
 fft_hgrad_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
                  const float2 *__restrict__ acc_all, float *__restrict__ grad) {
     extern __shared__ __align__(16) float2 fsm[];
-    const FieldDev &fd = fields[fft_fields[blockIdx.x]];
+    const FieldDev &fd = fields[fft_fields[blockIdx.y]];
     const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
-    const int ph = blockIdx.y;
+    const int ph = blockIdx.x;
     if (ph >= nph) return;
     const int L = fd.fft_L, H = L / 2 + 1, Lp = L + 1, LH = L * H;
     float2 *A = fsm, *B = fsm + LH, *tw = fsm + 2 * LH;
@@ -326,12 +326,12 @@ sr_status configure_fft_kernels(int optin, int *limit) {
 
 void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
                      const float *params, float2 *hhat, cudaStream_t st) {
-    fft_hhat_kernel<<<dim3(n_fft_fields, max_nph), kFftThreads, smem, st>>>(fields, fft_fields, params, hhat);
+    fft_hhat_kernel<<<dim3(max_nph, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, params, hhat);
 }
 
 void launch_fft_hgrad(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
                       const float2 *acc, float *grad, cudaStream_t st) {
-    fft_hgrad_kernel<<<dim3(n_fft_fields, max_nph), kFftThreads, smem, st>>>(fields, fft_fields, acc, grad);
+    fft_hgrad_kernel<<<dim3(max_nph, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, acc, grad);
 }
 
 }  // namespace sr

@@ -74,6 +74,17 @@ def test_null_arguments(lib):
     assert lib.sr_loss_and_grad(None, None, None, None, None) == 1
 
 
+def test_batch_size_checked_before_its_members(lib):
+    """sr_batch_create rejects an empty batch and one of more than 65535 fields (a grid
+    dimension) before it reads any member (the dummy handles below are never dereferenced)."""
+    n = 65536
+    arr = (ctypes.c_void_p * n)(*([1] * n))
+    h = ctypes.c_void_p()
+    assert lib.sr_batch_create(arr, n, None, ctypes.byref(h)) == 1 and h.value is None
+    assert b"65535" in lib.sr_last_error()
+    assert lib.sr_batch_create(arr, 0, None, ctypes.byref(h)) == 1
+
+
 def test_noise_weights_checks_arguments_before_device_use(lib):
     """sr_noise_weights validates pointers and sizes before any CUDA call (the dummy pointers
     below are never dereferenced)."""
