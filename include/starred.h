@@ -413,10 +413,14 @@ sr_status sr_noise_weights(int N, int f, int K, int J, int E, const float *sigma
  * Sizes whose scratch would exceed SR_NOALLOC_SCRATCH_BYTES are rejected with
  * SR_ERR_SHAPE (the message gives the bytes needed); for config-3-sized fields
  * (300 epochs of 64x64, f = 2, K = 64) about 35 MB are used.
- * The call does not synchronise and does not validate the values of its
- * inputs (NaN data give a NaN loss).  The first call on a device looks up the
- * array's device address and configures the kernels; make that first call
- * before any stream capture.  Every call uses the same array and leaves the
+ * The call does not synchronise and returns no input check: NaN data give a
+ * NaN loss, and so does any sigma that is NaN or <= 0 (sigma = +inf masks the
+ * pixel as elsewhere).  The tile layout (phase groups per output tile) follows
+ * the same shared-memory rule as a created problem, so both accept the same
+ * shapes.  The first call on a device looks up the
+ * array's device address and configures the kernels (under a lock, so first
+ * calls from several host threads are safe); make that first call before any
+ * stream capture.  Every call uses the same array and leaves the
  * previous call's contents in it; calls whose work overlaps on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller. */
 #define SR_NOALLOC_SCRATCH_BYTES (64u << 20)

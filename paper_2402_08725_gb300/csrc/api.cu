@@ -376,17 +376,7 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
 
 // Phase groups of a tile: the most phases at once that fit in the block's threads and in
 // shared memory (one group always).
-static int choose_pg(int nph, TileItem t, int Tk) {
-    int best = 1;
-    const int threads_per_group = t.h * (t.w / kR);
-    for (int pg = 1; pg <= nph; ++pg) {
-        if (nph % pg != 0 || pg * threads_per_group > kThreads) continue;
-        t.pg = pg;
-        if (tile_smem_bytes(t, Tk, true) > g_smem_optin - 1024) continue;
-        best = pg;
-    }
-    return best;
-}
+static int choose_pg(int nph, TileItem t, int Tk) { return choose_tile_pg(nph, t, Tk, g_smem_optin - 1024); }
 
 // ------------------------------------------------------------------------------------------
 // Autotuner: which form (direct tiles or transforms) evaluates a field shape faster per epoch.

@@ -484,6 +484,20 @@ static int fwd_smem_bytes_item(const TileItem &t, int Tk, bool fwd) {
 
 int tile_smem_bytes(const TileItem &t, int Tk, bool fwd) { return fwd_smem_bytes_item(t, Tk, fwd); }
 
+// The most phase groups (a divisor of f^2) whose threads fit in one block and whose forward
+// tile fits in smem_limit bytes of shared memory; 1 if none does.
+int choose_tile_pg(int nph, TileItem t, int Tk, int smem_limit) {
+    int best = 1;
+    const int threads_per_group = t.h * (t.w / kR);
+    for (int pg = 1; pg <= nph; ++pg) {
+        if (nph % pg != 0 || pg * threads_per_group > kThreads) continue;
+        t.pg = pg;
+        if (tile_smem_bytes(t, Tk, true) > smem_limit) continue;
+        best = pg;
+    }
+    return best;
+}
+
 sr_status configure_tile_kernels(int smem_fwd, int smem_adj) {
     SR_CUDA(cudaFuncSetAttribute(fwd_kernel<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_fwd));
     SR_CUDA(cudaFuncSetAttribute(adj_kernel<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_adj));

@@ -11,6 +11,8 @@ constexpr int kR = 16;
 // --- deconvolution (deconv.cu) ---
 void launch_kappa_prep(const float *s, float *kappa, int E, int K, int f, int Tk, int tau_lo, cudaStream_t st);
 int tile_smem_bytes(const TileItem &t, int Tk, bool fwd);
+// phase groups of a tile: the most (a divisor of f^2) that fit one block and smem_limit bytes
+int choose_tile_pg(int nph, TileItem t, int Tk, int smem_limit);
 sr_status configure_tile_kernels(int smem_fwd, int smem_adj);
 sr_status occupancy_tile_kernels(int smem_fwd, int smem_adj, int *blocks_fwd, int *blocks_adj);
 void launch_fwd(const FieldDev *fields, const TileItem *items, int n_items, int *counter, const float *params,
@@ -133,5 +135,7 @@ void launch_opt_step(long long n, float *params, const float *grad, float *m, fl
 // --- input preparation (prep.cu) ---
 void launch_inv_var(const float *sigma, float *w, long long n, int *bad_flag, cudaStream_t st);
 void launch_check_finite(const float *x, long long n, int *bad_flag, cudaStream_t st);
+// *loss = NaN if *flag is set (an input the weights could not be formed from)
+void launch_flag_to_nan(const int *flag, double *loss, cudaStream_t st);
 
 }  // namespace sr

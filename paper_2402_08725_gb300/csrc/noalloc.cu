@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -23,7 +24,9 @@ constexpr int kNoallocMaxDevices = 64;
 constexpr int kNoallocMaxTiles = 16;  // N <= 256: at most 4 x 4 output tiles of 64 per epoch
 
 // Device address of the array on each device, looked up once per device (host code cannot use the
-// symbol's host-side name as a device address).
+// symbol's host-side name as a device address).  The mutex makes the first call on a device safe
+// from several host threads: one of them does the set-up, the others wait for it.
+static std::mutex g_scratch_mutex;
 static void *g_scratch_addr[kNoallocMaxDevices];
 static bool g_scratch_ready[kNoallocMaxDevices];
 
@@ -96,6 +99,29 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
         if (!(W_host[j] >= 0.f)) return noalloc_fail(SR_ERR_NONFINITE, "sr_loss_and_grad_noalloc: weight < 0 or NaN");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
+    // set-up, once per device, with that device current
+    int dev = 0;
+    SR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return noalloc_fail(SR_ERR_UNSUPPORTED, "device index too large");
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_ready[dev]) {
+            void *ptr = nullptr;
+            SR_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            int optin_dev = 0;
+            SR_CUDA(cudaDeviceGetAttribute(&optin_dev, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            sr_status s = configure_tile_kernels(optin_dev - 1024, optin_dev - 1024);
+            if (s != SR_OK) return s;
+            g_scratch_addr[dev] = ptr;
+            g_scratch_ready[dev] = true;
+        }
+        base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    }
+    int optin = 0, n_sm = 0;
+    SR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    SR_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+
     // geometry of the folded kernels and of the output tiles (the same rules as a created problem)
     const int o = K / 2, t_lo = -o - f + 1, t_hi = K - 1 - o;
     const int tau_lo = t_lo >= 0 ? (t_lo + f - 1) / f : -((-t_lo) / f);
@@ -112,10 +138,7 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
             t.x0 = (short)x0;
             t.h = (short)std::min(64, N - y0);
             t.w = (short)((std::min(64, N - x0) + kR - 1) / kR * kR);
-            int pg = 1;
-            for (int c = 1; c <= nph; ++c)
-                if (nph % c == 0 && c * t.h * (t.w / kR) <= kThreads) pg = c;
-            t.pg = pg;
+            t.pg = choose_tile_pg(nph, t, Tk, optin - 1024);
             tt.t[tt.n++] = t;
             smem_fwd = std::max(smem_fwd, tile_smem_bytes(t, Tk, true));
             smem_adj = std::max(smem_adj, tile_smem_bytes(t, Tk, false));
@@ -139,24 +162,6 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
         return noalloc_fail(SR_ERR_SHAPE, msg);
     }
 
-    // set-up, once per device, with that device current
-    int dev = 0;
-    SR_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoallocMaxDevices) return noalloc_fail(SR_ERR_UNSUPPORTED, "device index too large");
-    if (!g_scratch_ready[dev]) {
-        void *ptr = nullptr;
-        SR_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        int optin = 0;
-        SR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        sr_status s = configure_tile_kernels(optin - 1024, optin - 1024);
-        if (s != SR_OK) return s;
-        g_scratch_addr[dev] = ptr;
-        g_scratch_ready[dev] = true;
-    }
-    unsigned char *base = static_cast<unsigned char *>(g_scratch_addr[dev]);
-    int optin = 0, n_sm = 0;
-    SR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    SR_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     if (smem_fwd > optin - 1024 || smem_adj > optin - 1024)
         return noalloc_fail(SR_ERR_UNSUPPORTED, "sr_loss_and_grad_noalloc: PSF too large for shared memory");
     int bf = 1, ba = 1;
@@ -221,6 +226,8 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
     launch_starlet(d_fd, 1, F, !starlet_field_banded(F, J), chunks, n_chunks, J, params_dev, l1, st);
     launch_hgrad(d_fd, chunks, n_chunks, gbuf, grad_dev, st);
     launch_finalize(d_fd, 1, chi, se, l1, da, du, grad_dev, loss_field, loss_dev, st);
+    // a sigma that is NaN or <= 0 has no inverse variance: the loss reports it as NaN
+    launch_flag_to_nan(flag, loss_dev, st);
     SR_CUDA(cudaGetLastError());
     return SR_OK;
 }

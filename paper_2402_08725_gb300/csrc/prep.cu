@@ -31,6 +31,10 @@ __global__ void check_finite_kernel(const float *__restrict__ x, long long n, in
     }
 }
 
+__global__ void flag_to_nan_kernel(const int *flag, double *loss) {
+    if (*flag) *loss = __longlong_as_double(0x7ff8000000000000LL);
+}
+
 static int grid_for(long long n) {
     long long g = (n + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -44,5 +48,7 @@ void launch_inv_var(const float *sigma, float *w, long long n, int *bad_flag, cu
 void launch_check_finite(const float *x, long long n, int *bad_flag, cudaStream_t st) {
     check_finite_kernel<<<grid_for(n), 256, 0, st>>>(x, n, bad_flag);
 }
+
+void launch_flag_to_nan(const int *flag, double *loss, cudaStream_t st) { flag_to_nan_kernel<<<1, 1, 0, st>>>(flag, loss); }
 
 }  // namespace sr

@@ -1,5 +1,8 @@
 """Writes oracle_small_cases.txt: loss and per-block gradient norms of small seeded cases,
-computed by the FP64 oracle only (regression values for the oracle; no GPU, no library).
+computed by the FP64 oracle only (regression values for the oracle; no GPU, no library), and
+oracle_small_cases_inputs.txt: the float32 inputs of those cases (data, sigma, PSFs, weights,
+parameters), so that the stored values are reproduced from the very same inputs on every
+machine, whatever the last bits of the seeded generator there.
 
     python tests/golden/make_oracle_golden.py
 """
@@ -22,10 +25,41 @@ CASES = [  # (name, seed, E, N, f, K, M, J, lam, lam_pts)
 BLOCKS = ("h", "a", "c", "delta", "Gamma")
 
 
-def rows():
+ARRAYS = ("d", "sigma", "s", "W", "params")
+INPUTS = os.path.join(HERE, "oracle_small_cases_inputs.txt")
+
+
+def generated_inputs():
+    """{case: {array: float32 array}} from the seeded generator (used when writing)."""
+    out = {}
+    for name, seed, E, N, f, K, M, J, lam, lp in CASES:
+        fd = syn.small_deconv(seed, E=E, N=N, f=f, K=K, M=M, J=J, lam=lam)
+        out[name] = {a: np.asarray(getattr(fd, a), dtype=np.float32) for a in ARRAYS}
+    return out
+
+
+def stored_inputs():
+    """{case: {array: float32 array}} read back from oracle_small_cases_inputs.txt."""
+    out = {}
+    for line in open(INPUTS):
+        if line.startswith("#"):
+            continue
+        t = line.split()
+        name, arr, ndim = t[0], t[1], int(t[2])
+        shape = tuple(int(v) for v in t[3:3 + ndim])
+        vals = np.array([float(v) for v in t[3 + ndim:]], dtype=np.float32)
+        out.setdefault(name, {})[arr] = vals.reshape(shape)
+    return out
+
+
+def rows(inputs=None):
+    """Oracle values of every case, on the given inputs (default: the stored ones)."""
+    inputs = stored_inputs() if inputs is None else inputs
     out = []
     for name, seed, E, N, f, K, M, J, lam, lp in CASES:
         fd = syn.small_deconv(seed, E=E, N=N, f=f, K=K, M=M, J=J, lam=lam)
+        for a in ARRAYS:
+            setattr(fd, a, inputs[name][a])
         P = fd.params.astype(np.float64)
         L, _, g, _ = oracle.deconv_loss_grad(fd.E, fd.N, fd.f, fd.K, fd.M, fd.J, fd.lam, fd.d, fd.sigma, fd.s,
                                              fd.W, P)
@@ -43,6 +77,16 @@ def rows():
 
 
 if __name__ == "__main__":
+    gen = generated_inputs()
+    with open(INPUTS, "w") as fh:
+        fh.write("# Written by tests/golden/make_oracle_golden.py: float32 inputs of its cases, one array per line:\n")
+        fh.write("# case, array, ndim, shape, values (9 significant digits: exact float32 round trip)\n")
+        for name, arrs in gen.items():
+            for a in ARRAYS:
+                v = arrs[a]
+                fh.write(f"{name} {a} {v.ndim} " + " ".join(str(n) for n in v.shape) + " " +
+                         " ".join(f"{x:.9g}" for x in v.ravel()) + "\n")
+    assert all(np.array_equal(stored_inputs()[n][a], gen[n][a]) for n in gen for a in ARRAYS)
     with open(os.path.join(HERE, "oracle_small_cases.txt"), "w") as fh:
         fh.write("# Written by tests/golden/make_oracle_golden.py from the FP64 oracle (small_deconv cases of\n")
         fh.write("# that script, lambda_pts as listed there): case, loss, gradient L2 norm per block (h a c delta Gamma)\n")

@@ -5,6 +5,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_2402_08725_gb300 import synthetic as syn  # noqa: E402
 from tests._helpers import check_deconv, deconv_blocks  # noqa: E402
 
@@ -50,6 +51,38 @@ def test_small_cases_match_oracle(E, N, f, K, M, J, mode):
     fd = syn.small_deconv(seed=100 + N + K, E=E, N=N, f=f, K=K, M=M, J=J, lam=1.5)
     loss, g = _run(fd, conv_mode=mode)
     check_deconv(fd, loss, g)
+
+
+# The transform sizes that carry most of the config-4 epoch-pixels: L = 80 / 120 / 144 for
+# N = 64 / 96 / 128 with K = 64, f = 2.  M = 1 takes the one-source paths (and epochs side by
+# side where their buffers fit), M = 4 the up-to-four-source path.  E = 19: one full 16-epoch
+# work item and a 3-epoch item whose last group is partial.
+HEADLINE = [(64, 1), (64, 4), (96, 1), (96, 4), (128, 1), (128, 4)]
+
+
+@pytest.mark.parametrize("N,M", HEADLINE)
+def test_headline_transform_sizes_match_oracle(N, M):
+    fd = syn.small_deconv(seed=700 + N + M, E=19, N=N, f=2, K=64, M=M, J=4, lam=1.5)
+    loss, g = _run(fd, conv_mode="fft")
+    r = check_deconv(fd, loss, g)
+    print("headline fft", N, M, r)
+
+
+def test_near_truth_config3_field_against_loss_itself():
+    """A config-3 field (64x64, K = 64, 4 sources) whose data are the oracle's model at the
+    evaluation point plus Gaussian noise of the field's sigma: the loss sits near its expected
+    value 0.5 * npix, far below 0.5 * sum w d^2, and is checked against L itself."""
+    fd = syn.config3(E=40)
+    rng = np.random.default_rng(31)
+    P = fd.params.astype(np.float32).astype(np.float64)
+    model = oracle.deconv_model(fd.E, fd.N, fd.f, fd.K, fd.M, fd.s, P)
+    fd.d = (model + fd.sigma * rng.standard_normal(model.shape)).astype(np.float32)
+    for mode in ("direct", "fft"):
+        loss, g = _run(fd, conv_mode=mode)
+        r = check_deconv(fd, loss, g)
+        npix = fd.E * fd.N * fd.N
+        assert abs(2.0 * r["loss_ref"] / npix - 1.0) < 0.5, r
+        print("near-truth config3", mode, r)
 
 
 def test_masked_pixels_background_and_edge_source():
@@ -143,6 +176,13 @@ def test_config4_full_batch_sampled_fields():
     cost = [E * N * N for (N, E, J) in shapes]
     order = np.argsort(cost)
     picks = list(order[:3]) + [order[len(order) // 4]]
+    # the two largest stamp sizes (transform sizes 120 and 144): the cheapest field of each,
+    # and the N = 128 field of median epoch count
+    for n in (96, 128):
+        ids = sorted((shapes[i][1], i) for i in range(len(shapes)) if shapes[i][0] == n)
+        picks.append(ids[0][1])
+        if n == 128:
+            picks.append(ids[len(ids) // 2][1])
     g_all = grad.cpu().numpy()
     ls = losses.cpu().numpy()
     for i in picks:

@@ -27,7 +27,7 @@ def _desc(nat, fd):
     return d
 
 
-@pytest.mark.parametrize("case", ["small", "config1", "ragged_f3"])
+@pytest.mark.parametrize("case", ["small", "config1", "ragged_f3", "wide_psf_f8"])
 def test_noalloc_matches_allocating_entry_point_twice(case):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -38,8 +38,12 @@ def test_noalloc_matches_allocating_entry_point_twice(case):
         fd = syn.small_deconv(seed=61, E=3, N=40, f=2, K=15, M=2, J=3, lam=1.2)
     elif case == "config1":
         fd = syn.config1()
-    else:
+    elif case == "ragged_f3":
         fd = syn.small_deconv(seed=62, E=2, N=70, f=3, K=21, M=1, J=4, lam=0.7)
+    else:
+        # f = 8 with a 255-pixel PSF on an 8x8 stamp: many phases per tile, each needing a
+        # wide kernel in shared memory; both entry points must pick phase groups that fit
+        fd = syn.small_deconv(seed=63, E=2, N=8, f=8, K=255, M=1, J=3, lam=0.5)
     ref = Problem.from_field(fd)
     P = torch.from_numpy(fd.params).cuda()
     L_ref, g_ref = ref.loss_and_grad(P)
@@ -85,3 +89,33 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rc = lib.sr_loss_and_grad_noalloc(ctypes.byref(d), p, p, p, ctypes.c_void_p(W.ctypes.data), p, p, p, None)
     assert rc == 2
     assert b"scratch" in lib.sr_last_error()
+
+
+def test_noalloc_invalid_sigma_gives_nan_loss():
+    """A sigma that is NaN or <= 0 has no inverse variance: the call, which returns no input
+    check, reports it as a NaN loss (sigma = +inf still masks its pixel)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2402_08725_gb300 import _native as nat
+    lib = nat.load()
+    fd = syn.small_deconv(seed=64, E=2, N=24, f=2, K=11, M=1, J=3, lam=1.0)
+    desc = _desc(nat, fd)
+    P = torch.from_numpy(fd.params).cuda()
+    d = torch.from_numpy(fd.d).cuda()
+    psf = torch.from_numpy(fd.s).cuda()
+    W = np.ascontiguousarray(fd.W, dtype=np.float32)
+    stream = torch.cuda.current_stream()
+    for bad, expect_nan in ((0.0, True), (-1.0, True), (float("nan"), True), (float("inf"), False)):
+        sig_h = fd.sigma.copy()
+        sig_h[1, 5, 7] = bad
+        sig = torch.from_numpy(sig_h).cuda()
+        loss = torch.zeros((), dtype=torch.float64, device="cuda")
+        grad = torch.zeros((fd.n_params,), dtype=torch.float32, device="cuda")
+        rc = lib.sr_loss_and_grad_noalloc(ctypes.byref(desc), ctypes.c_void_p(d.data_ptr()),
+                                          ctypes.c_void_p(sig.data_ptr()), ctypes.c_void_p(psf.data_ptr()),
+                                          ctypes.c_void_p(W.ctypes.data), ctypes.c_void_p(P.data_ptr()),
+                                          ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                          ctypes.c_void_p(stream.cuda_stream))
+        nat.check(rc, "sr_loss_and_grad_noalloc")
+        torch.cuda.synchronize()
+        assert np.isnan(loss.item()) == expect_nan, (bad, loss.item())
