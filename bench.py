@@ -121,21 +121,22 @@ def fwd_bytes(fields):
     return b
 
 
-FFT_SIZES = (16, 20, 24, 32, 36, 40, 48, 60, 64, 72, 80, 96, 100, 108, 120, 128, 144)
+FFT_SIZES = (24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 144)
 
 
 def fft_size(N, K, f):
     """Transform size of the frequency-domain form (the library's rule): the smallest listed
-    L >= N + max(tau_hi, -tau_lo) (the sizes its per-epoch kernel is compiled for)."""
+    L >= N + max(tau_hi, -tau_lo) that also holds the folded kernel (L >= Tk); the listed sizes
+    are those its transform kernels are compiled for."""
     o = K // 2
     t_lo, t_hi = -o - f + 1, K - 1 - o
     tau_lo = -((-t_lo) // f)
     tau_hi = (t_hi + f - 1) // f
-    need = N + max(tau_hi, -tau_lo)
+    need = max(N + max(tau_hi, -tau_lo), tau_hi - tau_lo + 1)
     return next(L for L in FFT_SIZES if L >= need)
 
 
-FFT_CHUNK = 8  # epochs per work item of the frequency-domain form (the library's value)
+FFT_CHUNK = 16  # epochs per work item of the frequency-domain form (the library's value)
 
 
 def fft_bytes(fields):
@@ -169,8 +170,9 @@ def fft_flops(fields):
     return fl
 
 
-CHUNK_SRCS = [os.path.join(ROOT, "paper_2402_08725_gb300", "csrc", n) for n in ("fft_fixed.cu", "common.cuh", "cplx.cuh", "ffsum.cuh")]
-CHUNK_PROFILE = os.path.join(ROOT, "profiles", "fft_chunk_fixed_kernel_config4.md")
+CHUNK_SRCS = [os.path.join(ROOT, "paper_2402_08725_gb300", "csrc", n)
+              for n in ("fft_pair.cu", "fft_pair.cuh", "common.cuh", "cplx.cuh", "ffsum.cuh")]
+CHUNK_PROFILE = os.path.join(ROOT, "profiles", "fft_chunk_pair_kernel_config4.md")
 
 
 def chunk_source_hash():
@@ -680,7 +682,7 @@ def run_ours(args):
             full = args.workload == "config4" and not args.fields and not direct_fields
             roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(ach / hbm, 4), "traffic": profiled_traffic() if full else None,
-                    "kernel": "fft_hhat_kernel + fft_chunk_fixed_kernel",
+                    "kernel": "fft_hhat_pair_kernel + fft_chunk_pair_kernel",
                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
         else:
             fl = fwd_flops(direct_fields)

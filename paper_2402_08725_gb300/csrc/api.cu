@@ -110,32 +110,23 @@ static sr_status device_limits() {
     SR_CUDA(cudaGetDevice(&dev));
     SR_CUDA(cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     SR_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-    // reserve the static shared memory of the kernels (a few hundred bytes)
-    const int dyn = g_smem_optin - 1024;
+    // reserve the static shared memory of the tile kernels
+    const int dyn = g_smem_optin - kTileStaticReserve;
     sr_status s = configure_tile_kernels(dyn, dyn);
     if (s != SR_OK) return s;
-    s = configure_fft_kernels(g_smem_optin, &g_fft_smem_limit);
-    if (s != SR_OK) return s;
-    s = configure_fft_fixed(g_smem_optin, &g_fx_smem_limit);
+    s = configure_fft_pair(g_smem_optin, &g_fx_smem_limit, &g_fft_smem_limit);
     if (s != SR_OK) return s;
     return SR_OK;
 }
 
-// Transform size for the frequency-domain form: the smallest listed L >= N + max(tau_hi, -tau_lo)
-// (the sizes the per-epoch chunk kernel is compiled for), and its radix sequence for the
-// runtime-size transforms of the per-field kernels (4s first, then 2, 3, 5).
-static bool fft_size(int N, int Tk, int tau_lo, int *L_out, int *nst, int *rad) {
+// Transform size for the frequency-domain form: the smallest listed L (the sizes the transform
+// kernels are compiled for) that keeps the N x N output free of wrap-around,
+// L >= N + max(tau_hi, -tau_lo), and holds the folded kernel, L >= Tk.
+static bool fft_size(int N, int Tk, int tau_lo, int *L_out) {
     const int tau_hi = tau_lo + Tk - 1;
-    const int L = fft_fixed_next(N + std::max(tau_hi, -tau_lo));
+    const int L = fft_pair_next(std::max(N + std::max(tau_hi, -tau_lo), Tk));
     if (L == 0) return false;
-    int m = L, n = 0;
-    while (m % 4 == 0 && n < kFftMaxStages) { rad[n++] = 4; m /= 4; }
-    while (m % 2 == 0 && n < kFftMaxStages) { rad[n++] = 2; m /= 2; }
-    while (m % 3 == 0 && n < kFftMaxStages) { rad[n++] = 3; m /= 3; }
-    while (m % 5 == 0 && n < kFftMaxStages) { rad[n++] = 5; m /= 5; }
-    if (m != 1) return false;
     *L_out = L;
-    *nst = n;
     return true;
 }
 
@@ -181,7 +172,7 @@ struct Plan {
     float *ebuf = nullptr, *gbuf = nullptr, *ps_da = nullptr, *ps_du = nullptr;
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
     // frequency-domain form
-    int n_fft_items = 0, n_fft_fields = 0, max_nph = 1, smem_fft = 0, smem_fx = 0, grid_fft = 0;
+    int n_fft_items = 0, n_fft_fields = 0, max_pairs = 1, smem_fft = 0, smem_fx = 0, grid_fft = 0;
     int4 *d_fft_items = nullptr;
     int *d_fft_fields = nullptr;
     float2 *hhat = nullptr, *fft_acc = nullptr;
@@ -228,8 +219,7 @@ struct sr_problem {
     float *psf_s = nullptr, *psf_tmp = nullptr, *psf_gs = nullptr;
     // frequency-domain form: transform geometry, twiddles, kernel spectra
     bool fft_ok = false;
-    int fft_L = 0, fft_nst = 0;
-    int fft_rad[kFftMaxStages] = {0};
+    int fft_L = 0;
     float2 *fft_tw = nullptr, *khat = nullptr;
     int *d_flag = nullptr;
     float W_host[kMaxScales] = {0};
@@ -366,8 +356,6 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
     fd.n_chunks = (fd.F * fd.F + 255) / 256;
     fd.mode = 0;
     fd.fft_L = p->fft_L;
-    fd.fft_nst = p->fft_nst;
-    for (int s = 0; s < kFftMaxStages; ++s) fd.fft_rad[s] = p->fft_rad[s];
     fd.fft_tw = p->fft_tw;
     fd.fft_khat = p->khat;
 }
@@ -376,7 +364,9 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
 
 // Phase groups of a tile: the most phases at once that fit in the block's threads and in
 // shared memory (one group always).
-static int choose_pg(int nph, TileItem t, int Tk) { return choose_tile_pg(nph, t, Tk, g_smem_optin - 1024); }
+static int choose_pg(int nph, TileItem t, int Tk) {
+    return choose_tile_pg(nph, t, Tk, g_smem_optin - kTileStaticReserve);
+}
 
 // ------------------------------------------------------------------------------------------
 // Autotuner: which form (direct tiles or transforms) evaluates a field shape faster per epoch.
@@ -510,15 +500,15 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             fd.fft_hhat_off = hhat_len;
             hhat_len += (long long)nph * L * (H + 1);
             fft_fields.push_back(i);
-            pl->max_nph = std::max(pl->max_nph, nph);
-            smem_fft = std::max(smem_fft, fft_smem_bytes(L, 0, fd.f));
-            // epochs side by side: the most (up to 4; only with at most one source) whose buffers fit
-            int G = fd.M <= 1 ? 4 : 1;
-            while (G > 1 && fft_fixed_smem_bytes(L, fd.N, fd.M, fd.f, G) > g_fx_smem_limit)
-                G >>= 1;
+            pl->max_pairs = std::max(pl->max_pairs, (nph + 1) / 2);
+            smem_fft = std::max(smem_fft, fft_pair_field_smem(L));
+            // epoch pairs side by side: the widest group the kernel is compiled for at this size
+            // (more than one pair only with at most one source) if its buffers fit, else one pair
+            int G = fd.M <= 1 ? fft_pair_gpmax(L) : 1;
+            if (G > 1 && fft_pair_smem_bytes(L, fd.M, fd.f, G) > g_fx_smem_limit) G = 1;
             fd.fft_G = G;
-            fd.fft_EB = fft_fixed_epoch_buffer(L, fd.N);
-            smem_fx = std::max(smem_fx, fft_fixed_smem_bytes(L, fd.N, fd.M, fd.f, G));
+            fd.fft_EB = fft_pair_zn(L);
+            smem_fx = std::max(smem_fx, fft_pair_smem_bytes(L, fd.M, fd.f, G));
         } else if (pl->kind == SR_DECONV && !plain) {
             gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
             const int nph = fd.f * fd.f;
@@ -653,7 +643,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         const int K = fd.K;
         const int T = 64;
         const long long need = (((long long)(T + K - 1) * ((T + K) | 1) + 3) / 4 * 4 + (long long)K * ((K + 3) & ~3)) * 4;
-        if (need > g_smem_optin - 1024)
+        if (need > g_smem_optin - kTileStaticReserve)
             return fail(SR_ERR_UNSUPPORTED, "plain form: PSF size %d needs %lld bytes of shared memory", K, need);
         if ((st = configure_plain_kernels(K)) != SR_OK) return st;
     }
@@ -681,7 +671,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         pl->smem_fft = smem_fft;
         pl->smem_fx = smem_fx;
         int bfft = 0;
-        if ((st = occupancy_fft_fixed(smem_fx, &bfft)) != SR_OK) return st;
+        if ((st = occupancy_fft_pair(smem_fx, &bfft)) != SR_OK) return st;
         pl->grid_fft = std::max(1, std::min(pl->n_fft_items, std::max(bfft, 1) * g_num_sms));
         if (opt.grid_limit > 0) pl->grid_fft = std::min(pl->grid_fft, opt.grid_limit);
         if ((st = A.alloc(&pl->d_fft_items, fft_items.size())) != SR_OK) return st;
@@ -692,7 +682,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         SR_CUDA(cudaMemcpy(pl->d_fft_fields, fft_fields.data(), sizeof(int) * fft_fields.size(), cudaMemcpyHostToDevice));
     }
     if (pl->kind == SR_DECONV && !plain && pl->n_items > 0) {
-        const int limit = g_smem_optin - 1024;
+        const int limit = g_smem_optin - kTileStaticReserve;
         if (smem_fwd > limit || smem_adj > limit)
             return fail(SR_ERR_UNSUPPORTED, "PSF size needs %d bytes of shared memory per block (limit %d)",
                         std::max(smem_fwd, smem_adj), limit);
@@ -747,11 +737,11 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
     }
     if (ev) cudaEventRecord(ev[2], st);
     if (pl->n_fft_items > 0) {
-        launch_fft_hhat(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_nph, pl->smem_fft, params, pl->hhat,
-                        st);
-        launch_fft_chunks_fixed(pl->d_fields, pl->d_fft_items, pl->n_fft_items, pl->d_counters + 2, params, pl->hhat,
-                                pl->fft_acc, pl->chi_part, pl->se_part, pl->ps_da, pl->ps_du, pl->grid_fft, pl->smem_fx,
-                                st);
+        launch_fft_hhat_pair(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_pairs, pl->smem_fft, params,
+                             pl->hhat, st);
+        launch_fft_chunks_pair(pl->d_fields, pl->d_fft_items, pl->n_fft_items, pl->d_counters + 2, params, pl->hhat,
+                               pl->fft_acc, pl->chi_part, pl->se_part, pl->ps_da, pl->ps_du, pl->grid_fft, pl->smem_fx,
+                               st);
         n += 2;
     }
     if (ev) cudaEventRecord(ev[3], st);
@@ -766,8 +756,8 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
         ++n;
     }
     if (pl->n_fft_items > 0) {
-        launch_fft_hgrad(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_nph, pl->smem_fft, pl->fft_acc,
-                         grad, st);
+        launch_fft_hgrad_pair(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_pairs, pl->smem_fft,
+                              pl->fft_acc, grad, st);
         ++n;
     }
     if (pl->n_sh > 0)
@@ -1001,16 +991,15 @@ sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_p
             return bail(st);
         if (d.conv_mode == SR_CONV_FFT || d.conv_mode == SR_CONV_AUTO) {
             if ((st = device_limits()) != SR_OK) return bail(st);
-            int L = 0, nst = 0;
-            const bool ok = d.n_sources <= kFftMaxSources && fft_size(d.data_n, p->Tk, p->tau_lo, &L, &nst, p->fft_rad) &&
-                            fft_smem_bytes(L, 0, d.supersampling) <= g_fft_smem_limit &&
-                            fft_fixed_smem_bytes(L, d.data_n, d.n_sources, d.supersampling, 1) <= g_fx_smem_limit;
+            int L = 0;
+            const bool ok = d.n_sources <= kFftMaxSources && fft_size(d.data_n, p->Tk, p->tau_lo, &L) &&
+                            fft_pair_field_smem(L) <= g_fft_smem_limit && fft_pair_variant(L, d.n_sources, 1) &&
+                            fft_pair_smem_bytes(L, d.n_sources, d.supersampling, 1) <= g_fx_smem_limit;
             if (!ok && d.conv_mode == SR_CONV_FFT)
                 return bail(fail(SR_ERR_UNSUPPORTED, "the transform form does not fit this size in shared memory"));
             if (ok) {
                 p->fft_ok = true;
                 p->fft_L = L;
-                p->fft_nst = nst;
                 const size_t H = L / 2 + 1;
                 // rows padded to H + 1 (even), so that column pairs are 16-byte aligned
                 if ((st = A.alloc(&p->khat, E * d.supersampling * d.supersampling * (size_t)L * (H + 1))) != SR_OK)
@@ -1084,7 +1073,7 @@ sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device) {
     if (p->khat) {
         FieldDev fd;
         fill_field_common(fd, p);
-        launch_fft_kappa_fixed(fd, p->kappa, p->khat, p->stream);
+        launch_fft_kappa_pair(fd, p->kappa, p->khat, p->stream);
     }
     SR_CUDA(cudaGetLastError());
     p->pending_check = true;
@@ -1487,7 +1476,7 @@ static sr_status batch_io_prepare(sr_batch *b) {
         os[i + 1] = os[i] + (long long)e.E * e.K * e.K;
         ok[i + 1] = ok[i] + (long long)e.E * e.f * e.f * e.Tk * e.Tk;
         if (p->khat)
-            for (int j = 0; j < e.E * e.f * e.f; ++j) items.push_back(make_int2(i, j));
+            for (int j = 0; j < e.E * ((e.f * e.f + 1) / 2); ++j) items.push_back(make_int2(i, j));
     }
     // items grouped by transform size: one launch per size with that size's block
     std::stable_sort(items.begin(), items.end(), [&](const int2 &a, const int2 &c) {
@@ -1579,8 +1568,8 @@ sr_status sr_batch_set_psfs(sr_batch *b, const float *s, int on_device) {
                     b->bio_total_k, b->stream);
     SR_CUDA(cudaEventRecord(b->bio_free[2], b->stream));  // the staged PSFs are read by the copy kernel only
     for (const auto &r : b->bio_ranges)
-        if ((st = launch_fft_kappa_fixed_batch(b->plan->d_fields, b->bio_items + r[1], r[2], r[0], g_num_sms,
-                                               b->stream)) != SR_OK)
+        if ((st = launch_fft_kappa_pair_batch(b->plan->d_fields, b->bio_items + r[1], r[2], r[0], g_num_sms,
+                                              b->stream)) != SR_OK)
             return st;
     SR_CUDA(cudaGetLastError());
     b->bio_pending = true;

@@ -22,8 +22,7 @@ constexpr int kWinLo = 7;
 constexpr int kBlurHalf = 8;
 
 constexpr int kMaxScales = 8;
-constexpr int kFftMaxStages = 8;
-constexpr int kFftThreads = 768;
+constexpr int kFftThreads = 512;
 constexpr int kFftMaxSources = 4;  // point sources per field in the frequency-domain form
 constexpr int kFftChunk = 16;      // epochs per work item of the frequency-domain form
 constexpr int kThreads = 256;
@@ -49,10 +48,9 @@ struct FieldDev {
     float *psf_s;          // PSF kind: [F][F] narrow PSF s = m + b
     float *psf_tmp;        // PSF kind: [S][3][F][F] row-pass planes (value, d/dx) and adjoint plane
     float *psf_gs;         // PSF kind: [S][F][F] per-star gradient wrt s
-    // frequency-domain form (fft.cu); mode 0 = direct tiles, 1 = transforms
+    // frequency-domain form (fft_pair.cu); mode 0 = direct tiles, 1 = transforms
     int mode;
-    int fft_L, fft_nst;
-    int fft_rad[kFftMaxStages];
+    int fft_L;
     const float2 *fft_tw;     // [L] exp(-2 pi i n / L)
     // spectra in global memory are rows of L/2+2 (the last column a zero pad, so that column
     // pairs are 16-byte aligned)
@@ -60,8 +58,8 @@ struct FieldDev {
     long long fft_hhat_off;   // offset of the field's [f*f][L][L/2+2] h spectra in the plan buffer
     long long fft_acc_off;    // float2 offset of the field's chunk accumulators ([f*f][L][L/2+2] each)
     int fft_n_chunks;         // epoch chunks of the field
-    int fft_G;                // epochs transformed side by side by the chunk kernel (1, 2 or 4)
-    int fft_EB;               // float2 elements of each per-epoch transform buffer (fft_fixed.cu)
+    int fft_G;                // epoch pairs transformed side by side by the chunk kernel (1, 2 or 4)
+    int fft_EB;               // float2 elements of one pair array of the transform kernels
     // point-source prior (Eq. 11, third term): 1 + index of the partner entry (a field's shadow
     // entry in the plan's point-source table, or a shadow entry's field), 0 for none
     int pts;

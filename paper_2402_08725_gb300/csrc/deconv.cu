@@ -88,8 +88,9 @@ __device__ __forceinline__ float2 source_centre(const float *__restrict__ c, con
     return make_float2(u0 + (float)f * (c[2 * k] + dl[0]), u0 + (float)f * (c[2 * k + 1] + dl[1]));
 }
 
-// Up to this many point sources are added while the tile is staged; more are scattered after it.
-constexpr int kFusedSources = 8;
+// Point sources are added while the tile is staged, each pixel summing the sources whose window
+// holds it in index order (a fixed order for any M: the result does not depend on the schedule).
+constexpr int kStagedSources = 64;  // the most point sources a problem may have
 
 __device__ __forceinline__ float gauss_at(float dx, float dy) {
     return kGaussNorm * exp2f(-(dx * dx + dy * dy));
@@ -103,8 +104,8 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_item;
     __shared__ float2 s_red[2][kThreads / 32];
-    __shared__ float4 s_src[kFusedSources];
-    __shared__ int2 s_win[kFusedSources];
+    __shared__ float4 s_src[kStagedSources];
+    __shared__ int2 s_win[kStagedSources];
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -127,13 +128,12 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
         const int my0 = t.y0 - thi, mx0 = t.x0 - thi;  // data-grid origin of the staged tiles
 
         // point sources of this epoch: fine centre, amplitude and window origin (Eq. 9)
-        if (tid < M && tid < kFusedSources) {
+        if (tid < M) {
             const float2 cen = source_centre(cpar, dpar, tid, F, f);
             s_src[tid] = make_float4(cpar[2 * tid], cpar[2 * tid + 1], apar[tid], 0.f);
             s_win[tid] = make_int2((int)floorf(cen.x) - kWinLo, (int)floorf(cen.y) - kWinLo);
         }
         __syncthreads();
-        const bool fused_sources = M <= kFusedSources;
         const int warp = tid >> 5, lane = tid & 31;
 
         float acc[R];
@@ -154,10 +154,12 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                     continue;
                 }
                 const int uy = f * my + phy;
-                unsigned rowmask = 0u;
-                if (fused_sources)
-                    for (int k = 0; k < M; ++k)
-                        if ((unsigned)(uy - s_win[k].y) < (unsigned)kWin) rowmask |= 1u << k;
+                // sources whose window holds this row: two ballots over the (at most 64) windows
+                const bool in0 = lane < M && (unsigned)(uy - s_win[lane].y) < (unsigned)kWin;
+                const bool in1 = lane + 32 < M && (unsigned)(uy - s_win[lane + 32].y) < (unsigned)kWin;
+                const unsigned long long rowmask =
+                    (unsigned long long)__ballot_sync(0xffffffffu, in0) |
+                    ((unsigned long long)__ballot_sync(0xffffffffu, in1) << 32);
                 const float *src = hpar + (long long)uy * F + phx;
                 for (int j = lane; j < G.xcols; j += 32) {
                     const int mx = mx0 + j;
@@ -165,8 +167,8 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                     if (mx >= 0 && mx < N) {
                         v = __ldg(src + f * mx);
                         const int ux = f * mx + phx;
-                        for (unsigned m = rowmask; m; m &= m - 1) {
-                            const int k = __ffs(m) - 1;
+                        for (unsigned long long m = rowmask; m; m &= m - 1) {
+                            const int k = __ffsll((long long)m) - 1;
                             if ((unsigned)(ux - s_win[k].x) < (unsigned)kWin)
                                 v += s_src[k].z * gauss_at(src_offset(ux, F, f, s_src[k].x, dpar[0]),
                                                            src_offset(uy, F, f, s_src[k].y, dpar[1]));
@@ -187,34 +189,6 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                 for (int jx = lane; jx < G.kpitch; jx += 32) dst[jx] = jx < Tk ? __ldg(srow - jx) : 0.f;
             }
             __syncthreads();
-            // many point sources: scatter them onto the staged tiles instead
-            if (M > 0 && !fused_sources) {
-                const int nw = kWin / f + 1;
-                const int work = G.PG * M * nw * nw;
-                for (int idx = tid; idx < work; idx += kThreads) {
-                    int rr = idx;
-                    const int b = rr % nw; rr /= nw;
-                    const int a = rr % nw; rr /= nw;
-                    const int k = rr % M; rr /= M;
-                    const int grp = rr;
-                    const int ph = iter * G.PG + grp;
-                    const int phy = ph / f, phx = ph - phy * f;
-                    const float2 cen = source_centre(cpar, dpar, k, F, f);
-                    const int uy_lo = (int)floorf(cen.y) - kWinLo, ux_lo = (int)floorf(cen.x) - kWinLo;
-                    // data rows/cols m whose phase pixel f m + phi lies in the window
-                    const int my = ceil_div(uy_lo - phy, f) + a;
-                    const int mx = ceil_div(ux_lo - phx, f) + b;
-                    const int uy = f * my + phy, ux = f * mx + phx;
-                    if (uy < uy_lo || uy >= uy_lo + kWin || ux < ux_lo || ux >= ux_lo + kWin) continue;
-                    if (uy < 0 || uy >= F || ux < 0 || ux >= F) continue;
-                    const int i = my - my0, j = mx - mx0;
-                    if (i < 0 || i >= G.xrows || j < 0 || j >= G.xcols) continue;
-                    const float val = apar[k] * gauss_at(src_offset(ux, F, f, cpar[2 * k], dpar[0]),
-                                                         src_offset(uy, F, f, cpar[2 * k + 1], dpar[1]));
-                    atomicAdd(&smem[grp * xsize + i * G.xpitch + j], val);
-                }
-                __syncthreads();
-            }
             if (G.g < G.PG)
                 corr_accumulate<R>(acc, smem + G.g * xsize + G.row * G.xpitch + G.chunk * R, G.xpitch,
                                    Kall + G.g * ksz, G.kpitch, Tk);

@@ -1,0 +1,294 @@
+// Per-PSF and per-field transforms of the frequency-domain form (sm_103a): the spectra of the
+// folded PSF kernels (at set_psfs), the spectra of the phase images of h (once per evaluation and
+// field) and the transform back of the accumulated adjoint spectra (dL/dh).  Each block transforms
+// two phases at once as one complex image (fft_pair.cuh).
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "cplx.cuh"
+#include "fft_pair.cuh"
+#include "kernels.cuh"
+
+namespace sr {
+namespace {
+
+// --- per-PSF and per-field transforms (two phases per block) ---------------------------------
+// Half spectra of the pair in Z: X_a at out_a, X_b at out_b (if any), rows of pitch HP with the pad
+// column zero; each value times W_L^((ky + kx) sh) (sh = 0: no shift).
+template <int L>
+__device__ void split_store(const float2 *Z, float2 *out_a, float2 *out_b, int sh, const float2 *tw) {
+    using G = Pr<L>;
+    constexpr int H = G::H, HP = G::HP, P = G::P;
+    for (int idx = threadIdx.x; idx < L * HP; idx += blockDim.x) {
+        const int ky = idx / HP, kx = idx - ky * HP;
+        float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
+        if (kx < H) {
+            const float2 A = Z[krow<L>(ky) * P + kcol<L>(kx)];
+            const float2 B = Z[krow<L>(neg_mod(ky, L)) * P + kcol<L>(neg_mod(kx, L))];
+            xa = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+            xb = make_float2(0.5f * (A.y + B.y), 0.5f * (B.x - A.x));
+            if (sh) {
+                const float2 w = tw[((ky + kx) * sh) % L];
+                xa = cmul(xa, w);
+                xb = cmul(xb, w);
+            }
+        }
+        out_a[idx] = xa;
+        if (out_b) out_b[idx] = xb;
+    }
+}
+
+// Spectra of the folded PSF kernels (at set_psfs): item = epoch * n_pairs + pair of phases.  The
+// phase kernel kappa_phi (Tk x Tk, taps tau_lo .. tau_lo + Tk - 1 on each axis, Tk <= L) belongs on
+// the L x L circle with tap tau at tau mod L.  It is placed instead at tau - tau_lo, so that the
+// row passes touch only its Tk rows, and the shift is restored on the spectrum (shift theorem):
+//   Khat[ky][kx] = W_L^((ky + kx) tau_lo) Khat'[ky][kx],   W_L = exp(-2 pi i / L).
+template <int L>
+__device__ __noinline__ void kappa_item_pair(const FieldDev &fd, const float *__restrict__ kappa,
+                                             float2 *__restrict__ khat, int item) {
+    using G = Pr<L>;
+    constexpr int P = G::P, HP = G::HP;
+    float2 *Z = pr_dyn, *TWL = Z + G::ZN;
+    load_twl<L>(TWL, fd.fft_tw);
+    const int nph = fd.f * fd.f, npr = (nph + 1) / 2;
+    const int i = item / npr, q = item - i * npr;
+    const int pa = 2 * q, pb = 2 * q + 1;
+    const int Tk = fd.Tk;
+    const float *ka = kappa + ((long long)i * nph + pa) * Tk * Tk;
+    const float *kb = pb < nph ? ka + Tk * Tk : nullptr;
+    for (int t = threadIdx.x; t < Tk * Tk; t += blockDim.x) {
+        const int y = t / Tk, x = t - y * Tk;
+        Z[y * P + pcol<L>(x)] = make_float2(ka[t], kb ? kb[t] : 0.f);
+    }
+    __syncthreads();
+    rows_fwd<L>(Z, 1, Tk, Tk, TWL);
+    cols_fwd<L>(Z, 1, Tk, TWL);
+    const int sh = ((fd.tau_lo % L) + L) % L;  // tau_lo mod L
+    float2 *out = khat + ((long long)i * nph + pa) * L * HP;
+    split_store<L>(Z, out, kb ? out + L * HP : nullptr, sh, fd.fft_tw);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_kappa_pair_kernel(FieldDev fd, const float *__restrict__ kappa, float2 *__restrict__ khat) {
+    const int n_items = fd.E * ((fd.f * fd.f + 1) / 2);
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        switch (fd.fft_L) {
+#define SR_PR_KCASE(LL)                                 \
+    case LL:                                            \
+        kappa_item_pair<LL>(fd, kappa, khat, item);     \
+        break;
+            SR_PR_SIZES(SR_PR_KCASE)
+#undef SR_PR_KCASE
+            default:
+                break;  // not reached: transform sizes come from the list
+        }
+    }
+}
+
+// The kernel spectra of many problems in one launch: items[j] = (table entry, epoch * n_pairs +
+// pair); every block takes items in turn (the spectra live at each entry's fft_khat).
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_kappa_pair_batch_kernel(const FieldDev *__restrict__ fields, const int2 *__restrict__ items, int n_items) {
+    for (int j = blockIdx.x; j < n_items; j += gridDim.x) {
+        const int2 it = items[j];
+        const FieldDev &fd = fields[it.x];
+        float2 *khat = const_cast<float2 *>(fd.fft_khat);
+        switch (fd.fft_L) {
+#define SR_PR_BCASE(LL)                                     \
+    case LL:                                                \
+        kappa_item_pair<LL>(fd, fd.kappa, khat, it.y);      \
+        break;
+            SR_PR_SIZES(SR_PR_BCASE)
+#undef SR_PR_BCASE
+            default:
+                break;
+        }
+    }
+}
+
+// Hhat_phi: spectra of the phase images of h, F_phi[m] = h[f m + phi], two phases per block.
+template <int L>
+__device__ __noinline__ void hhat_pair(const FieldDev &fd, const float *__restrict__ params, float2 *__restrict__ hhat_all,
+                                       int q) {
+    using G = Pr<L>;
+    constexpr int P = G::P, HP = G::HP;
+    float2 *Z = pr_dyn, *TWL = Z + G::ZN;
+    load_twl<L>(TWL, fd.fft_tw);
+    const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
+    const int pa = 2 * q, pb = 2 * q + 1;
+    const bool hasb = pb < nph;
+    const int pay = pa / f, pax = pa - pay * f, pby = pb / f, pbx = pb - pby * f;
+    const float *h = params + fd.param_off;
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+        const int y = t / N, x = t - y * N;
+        const float va = h[(long long)(f * y + pay) * F + f * x + pax];
+        const float vb = hasb ? h[(long long)(f * y + pby) * F + f * x + pbx] : 0.f;
+        Z[y * P + pcol<L>(x)] = make_float2(va, vb);
+    }
+    __syncthreads();
+    rows_fwd<L>(Z, 1, N, N, TWL);
+    cols_fwd<L>(Z, 1, N, TWL);
+    float2 *out = hhat_all + fd.fft_hhat_off + (long long)pa * L * HP;
+    split_store<L>(Z, out, hasb ? out + L * HP : nullptr, 0, fd.fft_tw);
+}
+
+// dL/dh for the transform fields: the chunk accumulators of two phases summed in a fixed order,
+// joined as Z = A_a + i A_b on the whole plane (Hermitian extension of each half spectrum),
+// transformed back, plus the prior's gradient.
+template <int L>
+__device__ __noinline__ void hgrad_pair(const FieldDev &fd, const float2 *__restrict__ acc_all,
+                                        float *__restrict__ grad, int q) {
+    using G = Pr<L>;
+    constexpr int P = G::P, H = G::H, HP = G::HP, LHP = L * HP;
+    float2 *Z = pr_dyn, *TWL = Z + G::ZN;
+    load_twl<L>(TWL, fd.fft_tw);
+    const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
+    const int pa = 2 * q, pb = 2 * q + 1;
+    const bool hasb = pb < nph;
+    const int n_chunks = fd.fft_n_chunks;
+    const long long cs = (long long)nph * LHP;
+    const float2 *base = acc_all + fd.fft_acc_off;
+    for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) {
+        const int ky = idx / H, kx = idx - ky * H;
+        const bool selfcol = kx == 0 || 2 * kx == L;
+        if (selfcol && 2 * ky > L) continue;  // written by the partner at -ky
+        float2 s[2];
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            s[w] = make_float2(0.f, 0.f);
+            if (w == 1 && !hasb) continue;
+            // four interleaved partial sums (chunk c into c mod 4) combined in a fixed order
+            const float2 *ac = base + (long long)(w ? pb : pa) * LHP + ky * HP + kx;
+            float2 p4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p4[u] = make_float2(0.f, 0.f);
+            int c = 0;
+            for (; c + 4 <= n_chunks; c += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c + u < n_chunks) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
+            s[w] = cadd(cadd(p4[0], p4[1]), cadd(p4[2], p4[3]));
+        }
+        const float2 A = s[0], B = s[1];
+        const int r = krow<L>(ky), cx = kcol<L>(kx);
+        if (selfcol && (ky == 0 || 2 * ky == L)) {
+            Z[r * P + cx] = make_float2(A.x, B.x);
+        } else {
+            Z[r * P + cx] = make_float2(A.x - B.y, A.y + B.x);                                          // A + i B
+            Z[krow<L>(neg_mod(ky, L)) * P + kcol<L>(neg_mod(kx, L))] = make_float2(A.x + B.y, B.x - A.y);  // conj
+        }
+    }
+    __syncthreads();
+    cols_inv<L>(Z, 1, N, TWL);
+    rows_inv<L>(Z, 1, N, N, TWL);
+    const float scale = 1.f / ((float)L * (float)L);
+    const int pay = pa / f, pax = pa - pay * f, pby = pb / f, pbx = pb - pby * f;
+    const float *T0 = fd.starlet + (long long)fd.J * F * F;
+    float *gh = grad + fd.param_off;
+    for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+        const int y = t / N, x = t - y * N;
+        const float2 v = Z[y * P + pcol<L>(x)];
+        const long long ua = (long long)(f * y + pay) * F + f * x + pax;
+        gh[ua] = v.x * scale + T0[ua];
+        if (hasb) {
+            const long long ub = (long long)(f * y + pby) * F + f * x + pbx;
+            gh[ub] = v.y * scale + T0[ub];
+        }
+    }
+}
+
+// One block per (transform field, pair of phases): blockIdx.y indexes fft_fields[] (costliest
+// fields first), blockIdx.x the pair.
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_hhat_pair_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
+                     const float *__restrict__ params, float2 *__restrict__ hhat_all) {
+    const FieldDev &fd = fields[fft_fields[blockIdx.y]];
+    const int q = blockIdx.x;
+    if (2 * q >= fd.f * fd.f) return;
+    switch (fd.fft_L) {
+#define SR_PR_HCASE(LL)                              \
+    case LL:                                         \
+        hhat_pair<LL>(fd, params, hhat_all, q);      \
+        break;
+        SR_PR_SIZES(SR_PR_HCASE)
+#undef SR_PR_HCASE
+        default:
+            break;
+    }
+}
+
+__global__ void __launch_bounds__(kFftThreads, 1)
+fft_hgrad_pair_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
+                      const float2 *__restrict__ acc_all, float *__restrict__ grad) {
+    const FieldDev &fd = fields[fft_fields[blockIdx.y]];
+    const int q = blockIdx.x;
+    if (2 * q >= fd.f * fd.f) return;
+    switch (fd.fft_L) {
+#define SR_PR_GCASE(LL)                             \
+    case LL:                                        \
+        hgrad_pair<LL>(fd, acc_all, grad, q);       \
+        break;
+        SR_PR_SIZES(SR_PR_GCASE)
+#undef SR_PR_GCASE
+        default:
+            break;
+    }
+}
+
+}  // namespace
+
+template <typename K>
+static sr_status open_smem(K kernel, int optin, int *limit) {
+    cudaFuncAttributes a;
+    SR_CUDA(cudaFuncGetAttributes(&a, kernel));
+    const int dyn = optin - (int)a.sharedSizeBytes;
+    SR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    *limit = std::min(*limit, dyn);
+    return SR_OK;
+}
+
+// Opens the largest dynamic shared memory of the per-field kernels; *field_limit is the smallest.
+sr_status configure_fft_pair_field(int optin, int *field_limit) {
+    SR_CUDA(pr_fill_dtw());
+    *field_limit = optin;
+    sr_status s;
+    if ((s = open_smem(fft_kappa_pair_kernel, optin, field_limit)) != SR_OK) return s;
+    if ((s = open_smem(fft_kappa_pair_batch_kernel, optin, field_limit)) != SR_OK) return s;
+    if ((s = open_smem(fft_hhat_pair_kernel, optin, field_limit)) != SR_OK) return s;
+    if ((s = open_smem(fft_hgrad_pair_kernel, optin, field_limit)) != SR_OK) return s;
+    return SR_OK;
+}
+
+sr_status launch_fft_kappa_pair_batch(const FieldDev *fields, const int2 *items, int n_items, int L, int n_sms,
+                                      cudaStream_t st) {
+    if (n_items <= 0) return SR_OK;
+    const int smem = fft_pair_field_smem(L);
+    int occ = 0;
+    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fft_kappa_pair_batch_kernel, kFftThreads, smem));
+    const int grid = std::min(n_items, std::max(occ, 1) * n_sms);
+    fft_kappa_pair_batch_kernel<<<grid, kFftThreads, smem, st>>>(fields, items, n_items);
+    return SR_OK;
+}
+
+void launch_fft_kappa_pair(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st) {
+    const int n_items = fd.E * ((fd.f * fd.f + 1) / 2);
+    fft_kappa_pair_kernel<<<n_items, kFftThreads, fft_pair_field_smem(fd.fft_L), st>>>(fd, kappa, khat);
+}
+
+void launch_fft_hhat_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
+                          const float *params, float2 *hhat, cudaStream_t st) {
+    fft_hhat_pair_kernel<<<dim3(max_pairs, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, params, hhat);
+}
+
+void launch_fft_hgrad_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
+                           const float2 *acc, float *grad, cudaStream_t st) {
+    fft_hgrad_pair_kernel<<<dim3(max_pairs, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, acc, grad);
+}
+
+}  // namespace sr

@@ -7,6 +7,9 @@ namespace sr {
 
 // Outputs per thread of the register-blocked correlation (a compile-time width).
 constexpr int kR = 16;
+// Shared memory kept back from the opt-in limit for the static shared memory of the tile kernels
+// (the work item, reduction slots and the staged point sources: under 2 KB).
+constexpr int kTileStaticReserve = 2048;
 
 // --- deconvolution (deconv.cu) ---
 void launch_kappa_prep(const float *s, float *kappa, int E, int K, int f, int Tk, int tau_lo, cudaStream_t st);
@@ -30,27 +33,30 @@ void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_par
                      double *total, cudaStream_t st, const FieldDev *pts_fields = nullptr,
                      const double *l1_pts = nullptr, const float *pts_g = nullptr);
 
-// --- frequency-domain form (fft.cu) ---
-int fft_smem_bytes(int L, int M, int f);
-sr_status configure_fft_kernels(int optin, int *limit);
-
-void launch_fft_hhat(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
-                     const float *params, float2 *hhat, cudaStream_t st);
-void launch_fft_hgrad(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_nph, int smem,
-                      const float2 *acc, float *grad, cudaStream_t st);
-
-// --- per-epoch chunk kernel for the transform sizes of a fixed list (fft_fixed.cu) ---
-bool fft_fixed_size(int L);
-int fft_fixed_next(int need);  // smallest listed size >= need, 0 if none
-int fft_fixed_epoch_buffer(int L, int N);
-int fft_fixed_smem_bytes(int L, int N, int M, int f, int G);
-sr_status configure_fft_fixed(int optin, int *limit);
+// --- frequency-domain form (fft_pair.cu): in-place transforms of real image pairs ---
+bool fft_pair_size(int L);
+int fft_pair_next(int need);  // smallest listed size >= need, 0 if none
+int fft_pair_zn(int L);       // float2 elements of one pair array
+int fft_pair_smem_bytes(int L, int M, int f, int GP);  // chunk kernel, GP epoch pairs per group
+int fft_pair_field_smem(int L);                        // per-field and per-PSF kernels
+bool fft_pair_variant(int L, int M, int GP);           // the chunk kernel is compiled for it
+int fft_pair_gpmax(int L);                             // widest group of pairs (one source)
+sr_status configure_fft_pair(int optin, int *chunk_limit, int *field_limit);
+sr_status configure_fft_pair_field(int optin, int *field_limit);  // called by configure_fft_pair
 // spectra of a problem's folded kernels (set_psfs): [E][f*f][L][L/2+2], the pad column zero
-void launch_fft_kappa_fixed(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st);
-// the same for (entry, epoch * f^2 + phase) items of a table whose entries all have transform size L
-// (each entry's kappa and fft_khat), a persistent grid of as many blocks as fit on n_sms SMs
-sr_status launch_fft_kappa_fixed_batch(const FieldDev *fields, const int2 *items, int n_items, int L, int n_sms,
-                                       cudaStream_t st);
+void launch_fft_kappa_pair(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st);
+// the same for (entry, epoch * pairs + pair of phases) items of a table whose entries all have
+// transform size L (each entry's kappa and fft_khat), a persistent grid over n_sms SMs
+sr_status launch_fft_kappa_pair_batch(const FieldDev *fields, const int2 *items, int n_items, int L, int n_sms,
+                                      cudaStream_t st);
+void launch_fft_hhat_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
+                          const float *params, float2 *hhat, cudaStream_t st);
+void launch_fft_hgrad_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
+                           const float2 *acc, float *grad, cudaStream_t st);
+sr_status occupancy_fft_pair(int smem, int *blocks);
+void launch_fft_chunks_pair(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
+                            const float2 *hhat, float2 *acc, double *chi_part, double *se_part, float *ps_da,
+                            float *ps_du, int grid, int smem, cudaStream_t st);
 
 // --- batched input set-up (batch_io.cu) ---
 // One entry per problem of a batch: its device buffers and shape, for the packed inputs of
@@ -67,10 +73,6 @@ void launch_bio_noise(const BioEntry *tab, const long long *off, int n, const fl
                       cudaStream_t st);
 void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long long *off_k, int n, const float *src,
                      long long total_s, long long total_k, cudaStream_t st);
-sr_status occupancy_fft_fixed(int smem, int *blocks);
-void launch_fft_chunks_fixed(const FieldDev *fields, const int4 *items, int n_items, int *counter,
-                             const float *params, const float2 *hhat, float2 *acc, double *chi_part,
-                             double *se_part, float *ps_da, float *ps_du, int grid, int smem, cudaStream_t st);
 
 // --- starlet prior (starlet.cu) ---
 // Forward levels then adjoint levels for every field of the table (n_fields of them, grids at

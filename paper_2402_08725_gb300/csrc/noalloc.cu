@@ -111,7 +111,7 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
             SR_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
             int optin_dev = 0;
             SR_CUDA(cudaDeviceGetAttribute(&optin_dev, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-            sr_status s = configure_tile_kernels(optin_dev - 1024, optin_dev - 1024);
+            sr_status s = configure_tile_kernels(optin_dev - kTileStaticReserve, optin_dev - kTileStaticReserve);
             if (s != SR_OK) return s;
             g_scratch_addr[dev] = ptr;
             g_scratch_ready[dev] = true;
@@ -138,7 +138,7 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
             t.x0 = (short)x0;
             t.h = (short)std::min(64, N - y0);
             t.w = (short)((std::min(64, N - x0) + kR - 1) / kR * kR);
-            t.pg = choose_tile_pg(nph, t, Tk, optin - 1024);
+            t.pg = choose_tile_pg(nph, t, Tk, optin - kTileStaticReserve);
             tt.t[tt.n++] = t;
             smem_fwd = std::max(smem_fwd, tile_smem_bytes(t, Tk, true));
             smem_adj = std::max(smem_adj, tile_smem_bytes(t, Tk, false));
@@ -162,7 +162,7 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
         return noalloc_fail(SR_ERR_SHAPE, msg);
     }
 
-    if (smem_fwd > optin - 1024 || smem_adj > optin - 1024)
+    if (smem_fwd > optin - kTileStaticReserve || smem_adj > optin - kTileStaticReserve)
         return noalloc_fail(SR_ERR_UNSUPPORTED, "sr_loss_and_grad_noalloc: PSF too large for shared memory");
     int bf = 1, ba = 1;
     sr_status s = occupancy_tile_kernels(smem_fwd, smem_adj, &bf, &ba);

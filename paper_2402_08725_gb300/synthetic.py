@@ -429,7 +429,8 @@ def config2(seed=None, S=16, N=64) -> PsfProblem:
 def small_deconv(seed, E=3, N=16, f=2, K=13, M=2, J=3, lam=1.0, **kw) -> DeconvField:
     """Small generic case (sizes the oracle finishes in well under a second)."""
     rng = np.random.default_rng(seed)
-    return make_deconv_field(rng, E=E, N=N, f=f, K=K, M=M, J=J, lam=lam, pos_half=N / 6, **kw)
+    kw.setdefault("pos_half", N / 6)
+    return make_deconv_field(rng, E=E, N=N, f=f, K=K, M=M, J=J, lam=lam, **kw)
 
 
 def small_psf(seed, S=3, N=16, f=2, J=3, lam=1.0) -> PsfProblem:

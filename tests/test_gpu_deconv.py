@@ -137,6 +137,34 @@ def test_repeatable_bitwise(mode):
     prob.close()
 
 
+def test_many_overlapping_sources_direct_form_deterministic():
+    """40 point sources packed into a few pixels (their 16 x 16 windows overlap) in the direct
+    form: every staged pixel adds its sources in index order, so repeated evaluations and a batch
+    of copies give bitwise the single evaluation; the values match the oracle."""
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    fd = syn.small_deconv(seed=404, E=3, N=40, f=2, K=15, M=40, J=3, lam=1.0, pos_half=2.5)
+    prob = Problem.from_field(fd, conv_mode="direct")
+    p = torch.from_numpy(fd.params).cuda()
+    l1, g1 = prob.loss_and_grad(p)
+    g1 = g1.clone()
+    l2, g2 = prob.loss_and_grad(p)
+    assert l1 == l2 and torch.equal(g1, g2)
+    check_deconv(fd, l1, g1.cpu().numpy())
+    probs = [Problem.from_field(fd, conv_mode="direct") for _ in range(3)]
+    batch = Batch(probs)
+    P = torch.from_numpy(batch.pack([fd.params] * 3)).cuda()
+    losses = torch.empty(3, dtype=torch.float64, device="cuda")
+    batch.loss_and_grad(P, losses=losses)
+    grad = batch.loss_and_grad(P, losses=losses)[1]
+    for i in range(3):
+        assert losses[i].item() == l1
+        o = batch.offsets[i]
+        assert torch.equal(grad[o:o + fd.n_params], g1)
+    batch.close()
+    for q in probs + [prob]:
+        q.close()
+
+
 def test_batch_equals_single_fields_bitwise():
     """An uneven batch (sizes, epoch counts, starlet depths, and both the direct and the
     transform form) gives each field exactly the loss and gradient of its own
