@@ -67,7 +67,9 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
     using G = Pr<L>;
     constexpr int H = G::H, HP = G::HP, LHP = L * HP, ZN = G::ZN, P = G::P;
     constexpr int EG = 2 * GP;             // epochs per group
-    constexpr int RS = 4 / GP;             // rows per thread and step of the spectral loops
+    constexpr int RS = GP == 1 ? 2 : 1;    // rows per thread and step of the model loop
+    constexpr int PC = GP == 4 ? 2 : 4;    // phases whose model-loop loads are issued together
+    constexpr int RA = GP == 1 ? 4 : GP == 2 ? 2 : 1;  // rows per thread and step of the adjoint loop
     constexpr int RP = kFftThreads / H;    // rows in parallel
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -102,10 +104,9 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
         const int np = (ne + 1) / 2;
         const float2 *kh = fd.fft_khat + (long long)i0 * nph * LHP;  // [e][phi][L][HP]
         const float *apar = sh.ia + (i0 - item.y) * M;                 // a_{i0 + e, k} at e M + k
-        // This group's kernel spectra go to L2 while the window spectra are computed, and the next
-        // group's data and weights while this one computes (sizes are multiples of 16 bytes when N
-        // is even).
-        if (tid == 0) prefetch_l2(kh, (long long)ne * nph * LHP * (long long)sizeof(float2));
+        // The next group's data and weights go to L2 while this one computes (sizes are multiples of
+        // 16 bytes when N is even).  The kernel spectra are not prefetched: with every SM streaming
+        // its own group's spectra, an early copy in L2 is evicted before its use (measured slower).
         if (tid == 0 && i0 + EG < item.z && (N & 1) == 0) {
             const int nn = min(EG, item.z - i0 - EG);
             prefetch_l2(fd.d + (long long)(i0 + EG) * N * N, (long long)nn * N * N * 4);
@@ -146,7 +147,8 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
         }
         __syncthreads();
         // model spectra: M_e = sum_phi Khat_{e,phi} (Hhat_phi + sum_k a_{e,k} gx gy) on the half plane,
-        // written as Z = M_{2g} + i M_{2g+1} at k and its conjugate at -k
+        // written as Z = M_{2g} + i M_{2g+1} at k and its conjugate at -k.  Every load of PC phases
+        // of RS rows is issued before any is used (one round trip per PC phases).
         if (ty < RP) {
             for (int row0 = ty; row0 < L; row0 += RS * RP) {
                 float2 m[RS][EG];
@@ -154,42 +156,60 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
                 for (int j = 0; j < RS; ++j)
 #pragma unroll
                     for (int e = 0; e < EG; ++e) m[j][e] = make_float2(0.f, 0.f);
-                for (int ph = 0; ph < nph; ++ph) {
-                    const int phy = ph / f, phx = ph - phy * f;
-                    float2 hv[RS], kv[RS][EG];
+                for (int ph0 = 0; ph0 < nph; ph0 += PC) {
+                    float2 hv[PC][RS], kv[PC][RS][EG];
 #pragma unroll
-                    for (int j = 0; j < RS; ++j) {
-                        const int row = row0 + j * RP;
-                        const bool ok = row < L;
-                        const int off = row * HP + tx;
-                        hv[j] = ok ? ldg_hint(hh + ph * LHP + off, pol_last) : make_float2(0.f, 0.f);
+                    for (int q = 0; q < PC; ++q) {
+                        const int ph = ph0 + q;
 #pragma unroll
-                        for (int e = 0; e < EG; ++e)
-                            kv[j][e] = (ok && e < ne) ? ldg_hint(kh + (e * nph + ph) * LHP + off, pol_last)
-                                                      : make_float2(0.f, 0.f);
+                        for (int j = 0; j < RS; ++j) {
+                            const int row = row0 + j * RP;
+                            const bool ok = row < L && ph < nph;
+                            const int off = ph * LHP + row * HP + tx;
+                            hv[q][j] = ok ? ldg_hint(hh + off, pol_last) : make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int e = 0; e < EG; ++e)
+                                kv[q][j][e] = (ok && e < ne) ? ldg_hint(kh + e * nph * LHP + off, pol_last)
+                                                             : make_float2(0.f, 0.f);
+                        }
                     }
 #pragma unroll
-                    for (int j = 0; j < RS; ++j) {
-                        const int row = row0 + j * RP;
-                        const bool lowrow = 2 * row <= L;
-                        const int yr = lowrow ? row : L - row;
+                    for (int q = 0; q < PC; ++q) {
+                        const int ph = ph0 + q;
+                        if (ph >= nph) break;
+                        const int phy = ph / f, phx = ph - phy * f;
+                        // a_{e,k} gx(kx) of this column and phase, once for the thread's rows
+                        float2 agx[EG][MS];
 #pragma unroll
-                        for (int e = 0; e < EG; ++e) {
-                            if (e < ne && row < L) {
-                                float2 s = hv[j];
+                        for (int e = 0; e < EG; ++e)
 #pragma unroll
-                                for (int k = 0; k < MS; ++k) {
-                                    if (k < M) {
-                                        const float2 gx = prof[prof_at(e, k, phx, 0, M, f, H) + tx];
-                                        float2 gy = prof[prof_at(e, k, phy, 2, M, f, H) + yr];
-                                        if (!lowrow) gy.y = -gy.y;
-                                        const float2 pr = cmul(gx, gy);
-                                        const float a = apar[e * M + k];
-                                        s.x += a * pr.x;
-                                        s.y += a * pr.y;
-                                    }
+                            for (int k = 0; k < MS; ++k) {
+                                agx[e][k] = make_float2(0.f, 0.f);
+                                if (k < M && e < ne) {
+                                    const float2 gx = prof[prof_at(e, k, phx, 0, M, f, H) + tx];
+                                    const float a = apar[e * M + k];
+                                    agx[e][k] = make_float2(a * gx.x, a * gx.y);
                                 }
-                                m[j][e] = cadd(m[j][e], cmul(kv[j][e], s));
+                            }
+#pragma unroll
+                        for (int j = 0; j < RS; ++j) {
+                            const int row = row0 + j * RP;
+                            const bool lowrow = 2 * row <= L;
+                            const int yr = lowrow ? row : L - row;
+#pragma unroll
+                            for (int e = 0; e < EG; ++e) {
+                                if (e < ne && row < L) {
+                                    float2 sv = hv[q][j];
+#pragma unroll
+                                    for (int k = 0; k < MS; ++k) {
+                                        if (k < M) {
+                                            float2 gy = prof[prof_at(e, k, phy, 2, M, f, H) + yr];
+                                            if (!lowrow) gy.y = -gy.y;
+                                            sv = cadd(sv, cmul(agx[e][k], gy));
+                                        }
+                                    }
+                                    m[j][e] = cadd(m[j][e], cmul(kv[q][j][e], sv));
+                                }
                             }
                         }
                     }
@@ -232,33 +252,44 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
                 const float *d0 = fd.d + (long long)i * N * N, *w0 = fd.w + (long long)i * N * N;
                 const float *d1 = d0 + N * N, *w1 = w0 + N * N;
                 float2 *zg = Z + g * ZN;
-                for (int y = sub; y < N; y += nsub) {
+                // two rows per iteration: 32 data and weight loads per lane in flight together
+                for (int y0 = sub; y0 < N; y0 += 2 * nsub) {
                     float c0 = 0.f, c1 = 0.f, s0 = 0.f, s1 = 0.f;
                     for (int x0 = 0; x0 < N; x0 += 128) {
-                        float dv[4][2], wv[4][2];
+                        float dv[2][4][2], wv[2][4][2];
 #pragma unroll
-                        for (int jx = 0; jx < 4; ++jx) {
-                            const int x = x0 + 32 * jx + lane;
-                            const bool in = x < N;
-                            dv[jx][0] = in ? ldg_hint(d0 + y * N + x, pol_first) : 0.f;
-                            wv[jx][0] = in ? ldg_hint(w0 + y * N + x, pol_first) : 0.f;
-                            dv[jx][1] = (in && has1) ? ldg_hint(d1 + y * N + x, pol_first) : 0.f;
-                            wv[jx][1] = (in && has1) ? ldg_hint(w1 + y * N + x, pol_first) : 0.f;
+                        for (int ry = 0; ry < 2; ++ry) {
+                            const int y = y0 + ry * nsub;
+#pragma unroll
+                            for (int jx = 0; jx < 4; ++jx) {
+                                const int x = x0 + 32 * jx + lane;
+                                const bool in = x < N && y < N;
+                                const int o = y * N + x;
+                                dv[ry][jx][0] = in ? ldg_hint(d0 + o, pol_first) : 0.f;
+                                wv[ry][jx][0] = in ? ldg_hint(w0 + o, pol_first) : 0.f;
+                                dv[ry][jx][1] = (in && has1) ? ldg_hint(d1 + o, pol_first) : 0.f;
+                                wv[ry][jx][1] = (in && has1) ? ldg_hint(w1 + o, pol_first) : 0.f;
+                            }
                         }
 #pragma unroll
-                        for (int jx = 0; jx < 4; ++jx) {
-                            const int x = x0 + 32 * jx + lane;
-                            if (x < N) {
-                                float2 *zp = zg + y * P + pcol<L>(x);
-                                const float2 mv = *zp;
-                                const float r0 = dv[jx][0] - (mv.x * scale + bg0);
-                                const float r1 = dv[jx][1] - (mv.y * scale + bg1);
-                                c0 += 0.5f * wv[jx][0] * r0 * r0;
-                                c1 += 0.5f * wv[jx][1] * r1 * r1;
-                                const float ev0 = -wv[jx][0] * r0, ev1 = has1 ? -wv[jx][1] * r1 : 0.f;
-                                s0 += ev0;
-                                s1 += ev1;
-                                *zp = make_float2(ev0, ev1);
+                        for (int ry = 0; ry < 2; ++ry) {
+                            const int y = y0 + ry * nsub;
+                            if (y >= N) continue;
+#pragma unroll
+                            for (int jx = 0; jx < 4; ++jx) {
+                                const int x = x0 + 32 * jx + lane;
+                                if (x < N) {
+                                    float2 *zp = zg + y * P + pcol<L>(x);
+                                    const float2 mv = *zp;
+                                    const float r0 = dv[ry][jx][0] - (mv.x * scale + bg0);
+                                    const float r1 = dv[ry][jx][1] - (mv.y * scale + bg1);
+                                    c0 += 0.5f * wv[ry][jx][0] * r0 * r0;
+                                    c1 += 0.5f * wv[ry][jx][1] * r1 * r1;
+                                    const float ev0 = -wv[ry][jx][0] * r0, ev1 = has1 ? -wv[ry][jx][1] * r1 : 0.f;
+                                    s0 += ev0;
+                                    s1 += ev1;
+                                    *zp = make_float2(ev0, ev1);
+                                }
                             }
                         }
                     }
@@ -285,37 +316,41 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
         for (int e = 0; e < EG; ++e)
 #pragma unroll
             for (int k = 0; k < MS; ++k) pa[e][k] = px[e][k] = py[e][k] = 0.f;
+        // Phases outermost: with the column kx of the thread fixed, the Parseval sums factor as
+        // sum_rows w Re(G conj(gx gy)) = w Re(conj(gx) T1), T1 = sum_rows G conj(gy) (and T2 with the
+        // derivative profile gyd), so per point only T1 and T2 are accumulated.
         if (ty < RP) {
-            for (int row0 = ty; row0 < L; row0 += RS * RP) {
-                float2 eh[RS][EG];
+            for (int ph = 0; ph < nph; ++ph) {
+                const int phy = ph / f, phx = ph - phy * f;
+                float2 T1[EG][MS], T2[EG][MS];
 #pragma unroll
-                for (int j = 0; j < RS; ++j) {
-                    const int ky = row0 + j * RP;
-                    const int r = krow<L>(ky < L ? ky : 0), rm = krow<L>(neg_mod(ky < L ? ky : 0, L));
+                for (int e = 0; e < EG; ++e)
 #pragma unroll
-                    for (int g = 0; g < GP; ++g) {
-                        const float2 *zg = Z + g * ZN;
-                        const float2 A = zg[r * P + cx], B = zg[rm * P + cxm];
-                        eh[j][2 * g] = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));      // (A + conj B) / 2
-                        eh[j][2 * g + 1] = make_float2(0.5f * (A.y + B.y), 0.5f * (B.x - A.x));  // (A - conj B) / 2i
-                    }
-                }
-                for (int ph = 0; ph < nph; ++ph) {
-                    const int phy = ph / f, phx = ph - phy * f;
-                    float2 av[RS], kv[RS][EG];
+                    for (int k = 0; k < MS; ++k) T1[e][k] = T2[e][k] = make_float2(0.f, 0.f);
+                for (int row0 = ty; row0 < L; row0 += RA * RP) {
+                    float2 eh[RA][EG], av[RA], kv[RA][EG];
 #pragma unroll
-                    for (int j = 0; j < RS; ++j) {
+                    for (int j = 0; j < RA; ++j) {
                         const int row = row0 + j * RP;
                         const bool ok = row < L;
-                        const int off = row * HP + tx;
-                        av[j] = (ok && !first) ? ld_hint(acc + ph * LHP + off, pol_last) : make_float2(0.f, 0.f);
+                        const int off = ph * LHP + row * HP + tx;
+                        av[j] = (ok && !first) ? ld_hint(acc + off, pol_last) : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int e = 0; e < EG; ++e)
-                            kv[j][e] = (ok && e < ne) ? ldg_hint(kh + (e * nph + ph) * LHP + off, pol_first)
+                            kv[j][e] = (ok && e < ne) ? ldg_hint(kh + e * nph * LHP + off, pol_first)
                                                       : make_float2(0.f, 0.f);
+                        const int ky = ok ? row : 0;
+                        const int r = krow<L>(ky), rm = krow<L>(neg_mod(ky, L));
+#pragma unroll
+                        for (int g = 0; g < GP; ++g) {
+                            const float2 *zg = Z + g * ZN;
+                            const float2 A = zg[r * P + cx], B = zg[rm * P + cxm];
+                            eh[j][2 * g] = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));      // (A + conj B) / 2
+                            eh[j][2 * g + 1] = make_float2(0.5f * (A.y + B.y), 0.5f * (B.x - A.x));  // (A - conj B) / 2i
+                        }
                     }
 #pragma unroll
-                    for (int j = 0; j < RS; ++j) {
+                    for (int j = 0; j < RA; ++j) {
                         const int row = row0 + j * RP;
                         if (row >= L) continue;
                         const bool lowrow = 2 * row <= L;
@@ -329,18 +364,14 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
 #pragma unroll
                                 for (int k = 0; k < MS; ++k) {
                                     if (k < M) {
-                                        const float2 *pg = prof + prof_at(e, k, phx, 0, M, f, H);
-                                        const float2 *py_ = prof + prof_at(e, k, phy, 2, M, f, H);
-                                        const float2 gx = pg[tx], gxd = pg[H + tx];
-                                        float2 gy = py_[yr], gyd = py_[H + yr];
+                                        const float2 *pgy = prof + prof_at(e, k, phy, 2, M, f, H);
+                                        float2 gy = pgy[yr], gyd = pgy[H + yr];
                                         if (!lowrow) {
                                             gy.y = -gy.y;
                                             gyd.y = -gyd.y;
                                         }
-                                        const float2 s0 = cmul(gx, gy), s1 = cmul(gxd, gy), s2 = cmul(gx, gyd);
-                                        pa[e][k] += wgt * (Gv.x * s0.x + Gv.y * s0.y);
-                                        px[e][k] += wgt * (Gv.x * s1.x + Gv.y * s1.y);
-                                        py[e][k] += wgt * (Gv.x * s2.x + Gv.y * s2.y);
+                                        T1[e][k] = cadd(T1[e][k], cmulc(Gv, gy));
+                                        T2[e][k] = cadd(T2[e][k], cmulc(Gv, gyd));
                                     }
                                 }
                             }
@@ -348,6 +379,18 @@ __device__ __noinline__ void chunk_item_pair(const FieldDev &fd, const int4 item
                         st_hint(acc + ph * LHP + row * HP + tx, run, last ? pol_first : pol_last);
                     }
                 }
+#pragma unroll
+                for (int e = 0; e < EG; ++e)
+#pragma unroll
+                    for (int k = 0; k < MS; ++k) {
+                        if (k < M && e < ne) {
+                            const float2 *pgx = prof + prof_at(e, k, phx, 0, M, f, H);
+                            const float2 gx = pgx[tx], gxd = pgx[H + tx];
+                            pa[e][k] += wgt * (T1[e][k].x * gx.x + T1[e][k].y * gx.y);
+                            px[e][k] += wgt * (T1[e][k].x * gxd.x + T1[e][k].y * gxd.y);
+                            py[e][k] += wgt * (T2[e][k].x * gx.x + T2[e][k].y * gx.y);
+                        }
+                    }
             }
         }
         __syncthreads();  // every read of Z is done: its first values take the per-warp partials
