@@ -121,34 +121,42 @@ def fwd_bytes(fields):
     return b
 
 
-FFT_SIZES = (24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 144)
+FFT_SIZES = (24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 144)   # in shared memory
+BIG_SIZES = (192, 240, 288, 384, 576, 768)                          # through global memory
 
 
 def fft_size(N, K, f):
     """Transform size of the frequency-domain form (the library's rule): the smallest listed
-    L >= N + max(tau_hi, -tau_lo) that also holds the folded kernel (L >= Tk); the listed sizes
-    are those its transform kernels are compiled for."""
+    L >= N + max(tau_hi, -tau_lo) that also holds the folded kernel (L >= Tk); the in-shared-memory
+    sizes first, then the global-memory ones."""
     o = K // 2
     t_lo, t_hi = -o - f + 1, K - 1 - o
     tau_lo = -((-t_lo) // f)
     tau_hi = (t_hi + f - 1) // f
     need = max(N + max(tau_hi, -tau_lo), tau_hi - tau_lo + 1)
-    return next(L for L in FFT_SIZES if L >= need)
+    return next(L for L in FFT_SIZES + BIG_SIZES if L >= need)
 
 
 FFT_CHUNK = 16  # epochs per work item of the frequency-domain form (the library's value)
 
 
 def fft_bytes(fields):
-    """Algorithmic DRAM bytes of one evaluation's transform kernels: each epoch reads its
-    f^2 folded-kernel spectra (L x (L/2+1) complex) and its data and weights; each chunk of
-    epochs writes its f^2 accumulated adjoint spectra, read back once by the per-field
-    reduction; each field's h spectra are written and read once."""
+    """Algorithmic DRAM bytes of one evaluation's transform kernels.  In shared memory: each epoch
+    reads its f^2 folded-kernel spectra (L x (L/2+1) complex) and its data and weights; each chunk of
+    epochs writes its f^2 accumulated adjoint spectra, read back once by the per-field reduction;
+    each field's h spectra are written and read once.  Through global memory: each frame's kernel
+    spectra are read once and its image spectra written and read once, its data and weights read
+    and its residual written; the f^2 adjoint spectra are written and read once per pair of
+    frames; h is read and its gradient written."""
     b = 0
     for fd in fields:
         L = fft_size(fd.N, fd.K, fd.f)
         LH = L * (L // 2 + 1)
         nph = fd.f * fd.f
+        if L in BIG_SIZES:
+            pairs = -(-fd.E // 2)
+            b += fd.E * (3 * nph * LH * 8 + 12 * fd.N * fd.N) + pairs * nph * LH * 8 * 2 + 8 * fd.F ** 2
+            continue
         chunks = -(-fd.E // FFT_CHUNK)
         b += fd.E * (nph * LH * 8 + 8 * fd.N * fd.N) + chunks * nph * LH * 8 * 2 + 2 * nph * LH * 8 + 8 * fd.F ** 2
     return b

@@ -116,6 +116,8 @@ static sr_status device_limits() {
     if (s != SR_OK) return s;
     s = configure_fft_pair(g_smem_optin, &g_fx_smem_limit, &g_fft_smem_limit);
     if (s != SR_OK) return s;
+    s = configure_fft_big(g_smem_optin);
+    if (s != SR_OK) return s;
     return SR_OK;
 }
 
@@ -176,6 +178,9 @@ struct Plan {
     int4 *d_fft_items = nullptr;
     int *d_fft_fields = nullptr;
     float2 *hhat = nullptr, *fft_acc = nullptr;
+    // fields on the global-memory transforms: their table index and buffers
+    std::vector<int> big_fields;
+    std::vector<BigBuffers> big_buf;
     // point-source prior (Eq. 11, third term): shadow entries of the fields that have it
     int n_sh = 0, sh_Fmax = 0, sh_Jmax = 0, sh_Mmax = 0, n_sh_chunks = 0;
     bool sh_any_unbanded = false;
@@ -219,6 +224,10 @@ struct sr_problem {
     float *psf_s = nullptr, *psf_tmp = nullptr, *psf_gs = nullptr;
     // frequency-domain form: transform geometry, twiddles, kernel spectra
     bool fft_ok = false;
+    // the transform size is beyond shared memory: global-memory transforms (fft_big.cu), kernel
+    // spectra in the transposed layout [E][f^2][L/2+1][L], and their set-up scratch
+    bool fft_big = false;
+    float2 *big_zb = nullptr, *big_zt = nullptr;
     int fft_L = 0;
     float2 *fft_tw = nullptr, *khat = nullptr;
     int *d_flag = nullptr;
@@ -482,7 +491,23 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         Jmax = std::max(Jmax, fd.J);
         pl->Fmax = std::max(pl->Fmax, fd.F);
         if (!starlet_field_banded(fd.F, fd.J)) pl->any_unbanded = true;
-        if (pl->kind == SR_DECONV && !plain && field_uses_fft(p, opt)) {
+        if (pl->kind == SR_DECONV && !plain && p->fft_big && field_uses_fft(p, opt)) {
+            // global-memory transforms: one chi^2 / sum e slot per data row, the window adjoint
+            // images of the point sources in gbuf, and per (epoch, source) gradient slots
+            fd.mode = 2;
+            fd.n_tiles = fd.N;
+            fd.tile_slot = tslot;
+            tslot += (long long)fd.E * fd.N;
+            if (fd.M > 0) {
+                fd.gbuf_off = gbuf;
+                gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
+            }
+            fd.ps_slot = psslot;
+            for (int e = 0; e < fd.E; ++e)
+                for (int k = 0; k < fd.M; ++k) ps.push_back(make_int4(i, e, k, 0));
+            psslot += (long long)fd.E * fd.M;
+            pl->big_fields.push_back(i);
+        } else if (pl->kind == SR_DECONV && !plain && field_uses_fft(p, opt)) {
             // frequency-domain form: chunks of consecutive epochs, one accumulator per chunk
             fd.mode = 1;
             fd.n_tiles = 1;
@@ -681,6 +706,16 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         SR_CUDA(cudaMemcpy(pl->d_fft_items, fft_items.data(), sizeof(int4) * fft_items.size(), cudaMemcpyHostToDevice));
         SR_CUDA(cudaMemcpy(pl->d_fft_fields, fft_fields.data(), sizeof(int) * fft_fields.size(), cudaMemcpyHostToDevice));
     }
+    for (int i : pl->big_fields) {
+        const FieldDev &fd = pl->h_fields[i];
+        const size_t L = fd.fft_L, H = L / 2 + 1, nph = (size_t)fd.f * fd.f, npr = (nph + 1) / 2;
+        BigBuffers bb{};
+        if ((st = A.alloc(&bb.zb, (size_t)fd.E * npr * fd.N * L)) != SR_OK) return st;
+        if ((st = A.alloc(&bb.zt, (size_t)fd.E * npr * fd.N * L)) != SR_OK) return st;
+        if ((st = A.alloc(&bb.fhat, (size_t)fd.E * nph * H * L)) != SR_OK) return st;
+        if ((st = A.alloc(&bb.acc, nph * H * L)) != SR_OK) return st;
+        pl->big_buf.push_back(bb);
+    }
     if (pl->kind == SR_DECONV && !plain && pl->n_items > 0) {
         const int limit = g_smem_optin - kTileStaticReserve;
         if (smem_fwd > limit || smem_adj > limit)
@@ -744,6 +779,9 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
                                st);
         n += 2;
     }
+    for (size_t b = 0; b < pl->big_fields.size(); ++b)
+        n += launch_big_eval(pl->h_fields[pl->big_fields[b]], params, pl->big_buf[b], pl->ebuf, pl->gbuf, pl->chi_part,
+                             pl->se_part, st);
     if (ev) cudaEventRecord(ev[3], st);
     if (pl->n_ps > 0) {
         launch_psgrad(pl->d_fields, pl->d_ps, pl->n_ps, params, pl->gbuf, pl->ps_da, pl->ps_du, st);
@@ -760,6 +798,8 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
                               pl->fft_acc, grad, st);
         ++n;
     }
+    for (size_t b = 0; b < pl->big_fields.size(); ++b)
+        n += launch_big_hgrad(pl->h_fields[pl->big_fields[b]], pl->big_buf[b], grad, st);
     if (pl->n_sh > 0)
         n += launch_pts_prior(pl->d_sh, pl->d_fields, pl->n_sh, pl->sh_Fmax, pl->sh_Mmax, pl->sh_any_unbanded,
                               pl->d_sh_chunks, pl->n_sh_chunks, pl->sh_Jmax, params, pl->abar, pl->pbar, pl->l1_pts,
@@ -809,6 +849,16 @@ static bool field_uses_fft(sr_problem *p, const PlanOptions &opt) {
     if (!p->fft_ok) return false;
     if (p->desc.conv_mode == SR_CONV_FFT) return true;
     if (p->desc.conv_mode != SR_CONV_AUTO) return false;
+    if (p->fft_big) {
+        // The one-block timing below does not apply to the global-memory transforms (they take the
+        // whole GPU per launch); compare operation counts per epoch instead: the direct form's
+        // 4 N^2 Tk^2 f^2 multiply-adds (model and adjoint) against about 50 L^2 log2(L^2) (f^2 + 4)
+        // for the transforms and the spectral products.
+        const double N = p->desc.data_n, f = p->desc.supersampling, Tk = p->Tk, L = p->fft_L;
+        const double direct = 4.0 * N * N * Tk * Tk * f * f;
+        const double transform = 50.0 * L * L * std::log2(L * L) * (f * f + 4.0);
+        return transform < direct;
+    }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     tune_load();
     const std::string key = tune_key(p->desc);
@@ -995,15 +1045,28 @@ sr_status sr_create_problem(const sr_problem_desc *desc, void *cuda_stream, sr_p
             const bool ok = d.n_sources <= kFftMaxSources && fft_size(d.data_n, p->Tk, p->tau_lo, &L) &&
                             fft_pair_field_smem(L) <= g_fft_smem_limit && fft_pair_variant(L, d.n_sources, 1) &&
                             fft_pair_smem_bytes(L, d.n_sources, d.supersampling, 1) <= g_fx_smem_limit;
-            if (!ok && d.conv_mode == SR_CONV_FFT)
-                return bail(fail(SR_ERR_UNSUPPORTED, "the transform form does not fit this size in shared memory"));
-            if (ok) {
-                p->fft_ok = true;
-                p->fft_L = L;
+            // sizes beyond shared memory: the global-memory transforms of fft_big.cu
+            const int tau_hi = p->tau_lo + p->Tk - 1;
+            const int Lb = ok ? 0 : fft_big_next(std::max(d.data_n + std::max(tau_hi, -p->tau_lo), p->Tk));
+            const bool big = !ok && Lb > 0 && fft_big_window_smem(p->Tk, d.supersampling) <= g_smem_optin - 2048;
+            if (!ok && !big && d.conv_mode == SR_CONV_FFT)
+                return bail(fail(SR_ERR_UNSUPPORTED, "the transform form does not fit this size"));
+            if (big) {
+                L = Lb;
+                p->fft_big = true;
+                const size_t H = L / 2 + 1, nph = (size_t)d.supersampling * d.supersampling, npr = (nph + 1) / 2;
+                if ((st = A.alloc(&p->khat, E * nph * H * L)) != SR_OK) return bail(st);
+                if ((st = A.alloc(&p->big_zb, E * npr * (size_t)p->Tk * L)) != SR_OK) return bail(st);
+                if ((st = A.alloc(&p->big_zt, E * npr * (size_t)p->Tk * L)) != SR_OK) return bail(st);
+            } else if (ok) {
                 const size_t H = L / 2 + 1;
                 // rows padded to H + 1 (even), so that column pairs are 16-byte aligned
                 if ((st = A.alloc(&p->khat, E * d.supersampling * d.supersampling * (size_t)L * (H + 1))) != SR_OK)
                     return bail(st);
+            }
+            if (ok || big) {
+                p->fft_ok = true;
+                p->fft_L = L;
                 if ((st = A.alloc(&p->fft_tw, (size_t)L)) != SR_OK) return bail(st);
                 std::vector<float2> tw(L);
                 for (int n = 0; n < L; ++n) {
@@ -1073,7 +1136,8 @@ sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device) {
     if (p->khat) {
         FieldDev fd;
         fill_field_common(fd, p);
-        launch_fft_kappa_pair(fd, p->kappa, p->khat, p->stream);
+        if (p->fft_big) launch_big_kappa(fd, p->big_zb, p->big_zt, p->stream);
+        else launch_fft_kappa_pair(fd, p->kappa, p->khat, p->stream);
     }
     SR_CUDA(cudaGetLastError());
     p->pending_check = true;
@@ -1475,7 +1539,7 @@ static sr_status batch_io_prepare(sr_batch *b) {
         od[i + 1] = od[i] + (long long)e.E * e.N * e.N;
         os[i + 1] = os[i] + (long long)e.E * e.K * e.K;
         ok[i + 1] = ok[i] + (long long)e.E * e.f * e.f * e.Tk * e.Tk;
-        if (p->khat)
+        if (p->khat && !p->fft_big)
             for (int j = 0; j < e.E * ((e.f * e.f + 1) / 2); ++j) items.push_back(make_int2(i, j));
     }
     // items grouped by transform size: one launch per size with that size's block
@@ -1571,6 +1635,12 @@ sr_status sr_batch_set_psfs(sr_batch *b, const float *s, int on_device) {
         if ((st = launch_fft_kappa_pair_batch(b->plan->d_fields, b->bio_items + r[1], r[2], r[0], g_num_sms,
                                               b->stream)) != SR_OK)
             return st;
+    for (sr_problem *p : b->probs)
+        if (p->fft_big) {
+            FieldDev fd;
+            fill_field_common(fd, p);
+            launch_big_kappa(fd, p->big_zb, p->big_zt, b->stream);
+        }
     SR_CUDA(cudaGetLastError());
     b->bio_pending = true;
     return SR_OK;
@@ -1608,7 +1678,7 @@ int sr_batch_launches_per_eval(const sr_batch *b) { return b ? b->plan->launches
 
 int sr_batch_field_form(const sr_batch *b, int i) {
     if (!b || i < 0 || i >= b->plan->n_fields) return -1;
-    return b->plan->h_fields[i].mode == 1 ? SR_CONV_FFT : SR_CONV_DIRECT;
+    return b->plan->h_fields[i].mode != 0 ? SR_CONV_FFT : SR_CONV_DIRECT;
 }
 
 sr_status sr_batch_profile(sr_batch *b, int enable) {

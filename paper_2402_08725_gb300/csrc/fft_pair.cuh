@@ -19,11 +19,12 @@ namespace sr {
 namespace {
 
 // --- in-register DFTs -----------------------------------------------------------------------
-// W_R^m = exp(-2 pi i m / R), m < R, for the composite sizes 6, 8, 9, 10, 12, 15, 16.
-constexpr int kDtwTotal = 6 + 8 + 9 + 10 + 12 + 15 + 16;
+// W_R^m = exp(-2 pi i m / R), m < R, for the composite sizes 6, 8, 9, 10, 12, 15, 16, 24, 32.
+constexpr int kDtwTotal = 6 + 8 + 9 + 10 + 12 + 15 + 16 + 24 + 32;
 __constant__ float2 c_dtw[kDtwTotal];
 __host__ __device__ constexpr int dtw_off(int R) {
-    return R == 6 ? 0 : R == 8 ? 6 : R == 9 ? 14 : R == 10 ? 23 : R == 12 ? 33 : R == 15 ? 45 : 60;
+    return R == 6 ? 0 : R == 8 ? 6 : R == 9 ? 14 : R == 10 ? 23 : R == 12 ? 33 : R == 15 ? 45 : R == 16 ? 60
+         : R == 24 ? 76 : 100;
 }
 
 // v * W_R^m (forward) or v * W_R^-m (inverse), exact for multiples of a quarter turn.
@@ -160,6 +161,8 @@ __device__ __forceinline__ void dft(float2 *v) {
     else if constexpr (R == 12) dft_pq<4, 3, INV>(v);
     else if constexpr (R == 15) dft_pq<3, 5, INV>(v);
     else if constexpr (R == 16) dft_pq<4, 4, INV>(v);
+    else if constexpr (R == 24) dft_pq<8, 3, INV>(v);
+    else if constexpr (R == 32) dft_pq<8, 4, INV>(v);
     else static_assert(R == 2, "unsupported in-register DFT size");
 }
 
@@ -407,7 +410,7 @@ extern __shared__ __align__(16) float2 pr_dyn[];
 // Fills this translation unit's twiddle table.
 inline cudaError_t pr_fill_dtw() {
     float2 tw[kDtwTotal];
-    for (int R : {6, 8, 9, 10, 12, 15, 16})
+    for (int R : {6, 8, 9, 10, 12, 15, 16, 24, 32})
         for (int m = 0; m < R; ++m) {
             const double a = -2.0 * M_PI * (double)m / (double)R;
             tw[dtw_off(R) + m] = make_float2((float)cos(a), (float)sin(a));

@@ -58,6 +58,25 @@ void launch_fft_chunks_pair(const FieldDev *fields, const int4 *items, int n_ite
                             const float2 *hhat, float2 *acc, double *chi_part, double *se_part, float *ps_da,
                             float *ps_du, int grid, int smem, cudaStream_t st);
 
+// --- frequency-domain form through global memory (fft_big.cu): sizes beyond shared memory ---
+// Per field and evaluation: zb and zt (the images and their transposes, E * pairs-of-phases * N * L
+// complex each), fhat (the frames' spectra, E * f^2 * (L/2+1) * L) and acc (f^2 * (L/2+1) * L).
+struct BigBuffers {
+    float2 *zb, *zt, *fhat, *acc;
+};
+int fft_big_next(int need);                 // smallest size >= need of the global-memory list, 0 if none
+int fft_big_window_smem(int Tk, int f);     // shared memory of the source-window adjoint kernel
+sr_status configure_fft_big(int optin);
+// kernel spectra [E][f^2][L/2+1][L] (transposed half spectra) at fd.fft_khat, with scratch zb, zt of
+// E * pairs * Tk * L complex each
+int launch_big_kappa(const FieldDev &fd, float2 *zb, float2 *zt, cudaStream_t st);
+// the model, residual, chi^2 / sum e partial sums (n_tiles = N slots per epoch), the adjoint spectra
+// and the source windows' adjoint images (gbuf); returns the number of launches
+int launch_big_eval(const FieldDev &fd, const float *params, const BigBuffers &bb, float *ebuf, float *gbuf,
+                    double *chi_part, double *se_part, cudaStream_t st);
+// dL/dh of the field (after the starlet kernels, whose gradient it adds)
+int launch_big_hgrad(const FieldDev &fd, const BigBuffers &bb, float *grad, cudaStream_t st);
+
 // --- batched input set-up (batch_io.cu) ---
 // One entry per problem of a batch: its device buffers and shape, for the packed inputs of
 // sr_batch_set_data / _noise / _psfs (each problem's block at its prefix offset).

@@ -68,6 +68,44 @@ def test_headline_transform_sizes_match_oracle(N, M):
     print("headline fft", N, M, r)
 
 
+# Transform sizes beyond shared memory (global-memory transforms, the config-5 form): L = 192 for
+# N = 160, K = 63, f = 2, and for N = 140, K = 127, f = 3 (nine phases, odd pairing) with masked
+# pixels, backgrounds and more sources than the in-shared-memory form takes.
+@pytest.mark.parametrize("E,N,f,K,M,J", [(3, 160, 2, 63, 3, 4), (2, 140, 3, 127, 12, 4)])
+def test_global_memory_transforms_match_oracle(E, N, f, K, M, J):
+    fd = syn.small_deconv(seed=900 + N + K, E=E, N=N, f=f, K=K, M=M, J=J, lam=1.2, pos_half=N / 5)
+    fd.sigma[0, 10:20, 30:41] = np.inf
+    h, a, c, dl, gm = syn.unpack_deconv(fd.params.copy(), fd.E, fd.N, fd.f, fd.M)
+    gm = np.linspace(-0.3, 0.4, fd.E)
+    c[0] = (N / 2 - 1.3, -N / 2 + 1.7)   # window clipped by the grid
+    P = syn.pack_deconv(h, a, c, dl, gm)
+    loss, g = _run(fd, P, conv_mode="fft")
+    r = check_deconv(fd, loss, g, params=P)
+    print("global-memory transforms", (E, N, f, K, M), r)
+
+
+def test_global_memory_transforms_batch_equals_single():
+    """A batch with a global-memory field between in-shared-memory ones gives each field exactly
+    its own evaluation."""
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    fields = [syn.small_deconv(seed=950, E=3, N=48, f=2, K=17, M=1, J=3),
+              syn.small_deconv(seed=951, E=3, N=160, f=2, K=63, M=2, J=4),
+              syn.small_deconv(seed=952, E=5, N=32, f=2, K=64, M=1, J=4)]
+    probs = [Problem.from_field(fd, conv_mode="fft") for fd in fields]
+    batch = Batch(probs)
+    P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
+    losses = torch.empty(len(fields), dtype=torch.float64, device="cuda")
+    total, grad = batch.loss_and_grad(P, losses=losses)
+    for i, (fd, pr) in enumerate(zip(fields, probs)):
+        l_i, g_i = pr.loss_and_grad(torch.from_numpy(fd.params).cuda())
+        o = batch.offsets[i]
+        assert losses[i].item() == l_i
+        assert torch.equal(grad[o:o + fd.n_params], g_i)
+    batch.close()
+    for pr in probs:
+        pr.close()
+
+
 def test_near_truth_config3_field_against_loss_itself():
     """A config-3 field (64x64, K = 64, 4 sources) whose data are the oracle's model at the
     evaluation point plus Gaussian noise of the field's sigma: the loss sits near its expected
@@ -284,11 +322,13 @@ def test_config5_six_frames_add_up():
         tot += l1
         gh += g1[:F * F]
         gc += g1[F * F + fd.M:F * F + 3 * fd.M]
-    assert abs(loss6 - tot) <= 1e-9 * abs(tot)
+    # the transform form carries two frames in one complex transform, so a frame's rounding
+    # depends on the frame it is paired with: equal to FP32 rounding, far inside the parity bounds
+    assert abs(loss6 - tot) <= 1e-7 * abs(tot)
     from tests._helpers import rel_l2
-    assert rel_l2(g6[:F * F], gh) <= 1e-6
+    assert rel_l2(g6[:F * F], gh) <= 1e-5
     oc = F * F + fd.E * fd.M
-    assert rel_l2(g6[oc:oc + 2 * fd.M], gc) <= 1e-6
+    assert rel_l2(g6[oc:oc + 2 * fd.M], gc) <= 1e-5
 
 
 def test_autotuner_resolves_auto_fields_and_caches(tmp_path, monkeypatch):
