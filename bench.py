@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the per-configuration measurements (configs 1, 2, 3, 5 each on its own)")
     ap.add_argument("--no-noise", action="store_true",
                     help="skip the Monte Carlo prior weights, point-source prior and extraction measurements")
     ap.add_argument("--conv-mode", choices=["auto", "direct", "fft"], default="auto",
@@ -731,6 +733,10 @@ def run_ours(args):
     pts = measure_pts(stream) if not args.no_noise and rank == 0 else None
     extraction = measure_extraction(stream) if not args.no_noise and rank == 0 else None
     psf_fit = measure_psf_fit(stream) if not args.no_noise and rank == 0 else None
+    configs = None
+    if not args.no_configs and rank == 0 and args.workload == "config4" and not args.fields:
+        configs = measure_configs(stream, fp32_peak, float(peaks.get("hbm_gbs", 6800.0)),
+                                  with_cpu=not args.no_cpu and world == 1)
 
     if rank == 0:
         line = {
@@ -757,6 +763,7 @@ def run_ours(args):
             "lc_extraction": extraction,
             "psf_fit": psf_fit,
             "lbfgsb_batch": lbfgsb_batch,
+            "configs": configs,
         }
         print(json.dumps(line))
     if dist is not None:
@@ -764,6 +771,164 @@ def run_ours(args):
 
 
 SIDE_STREAMS = 8
+
+
+# --- each configuration on its own ------------------------------------------------------------
+
+L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2: written between timed steps
+
+
+def timed_steps(step, steps, warm, stream, flush):
+    """Mean ms of `step` over `steps` calls, each bracketed by CUDA events on `stream`, with the
+    L2 flushed (a 256 MB write) before each call, outside the events."""
+    import torch
+    for _ in range(warm):
+        step()
+    total = 0.0
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    stream.synchronize()
+    for e0, e1 in evs:
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def first_epochs(fd, k):
+    """The field restricted to its first k epochs (data, noise, PSFs and per-epoch parameters)."""
+    h, a, c, dl, gm = syn.unpack_deconv(fd.params, fd.E, fd.N, fd.f, fd.M)
+    return syn.DeconvField(k, fd.N, fd.f, fd.K, fd.M, fd.J, fd.lam, fd.d[:k], fd.sigma[:k], fd.s[:k], fd.W,
+                           syn.pack_deconv(h, a[:k], c, dl[:k], gm[:k]))
+
+
+def oracle_rate(fields, pb):
+    """epoch-px/s of one literal FP64 oracle evaluation of each field (and the PSF fit)."""
+    import oracle
+    t0 = time.perf_counter()
+    units = 0
+    for fd in fields:
+        oracle.deconv_loss_grad(fd.E, fd.N, fd.f, fd.K, fd.M, fd.J, fd.lam, fd.d, fd.sigma, fd.s, fd.W, fd.params)
+        units += fd.epoch_pixels
+    if pb is not None:
+        oracle.psf_loss_grad(pb.S, pb.N, pb.f, pb.J, pb.lam, pb.t, pb.sigma, pb.W, pb.params)
+        units += pb.epoch_pixels
+    dt = time.perf_counter() - t0
+    return units / dt, dt, oracle.max_threads()
+
+
+def measure_config(name, stream, fp32_peak, hbm, with_cpu, steps=10, warm=3):
+    """One configuration alone: loss + gradient + AdaBelief step per step, L2 flushed between steps;
+    the dominant kernel against its roof; the plain per-epoch form; the oracle on the host cores."""
+    import torch
+    from paper_2402_08725_gb300.binding import Batch, Problem, optim_cfg
+    fields, pb = make_workload(name, 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {"description": WORKLOADS[name], "unit": "epoch-px/s", "steps": steps, "warmup": warm,
+           "l2": "flushed between steps (256 MB write)"}
+    with torch.cuda.stream(stream):
+        if fields:
+            probs = [Problem.from_field(fd, stream=stream) for fd in fields]
+            batch = Batch(probs, stream=stream)
+            P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
+            cfg = optim_cfg("adabelief", lr=lr_groups(fields[0]))
+            ms = timed_steps(lambda: batch.step(P, 1, cfg, sync=False), steps, warm, stream, flush)
+            batch.profile(True)
+            for _ in range(3):
+                batch.loss_and_grad(P)
+            stream.synchronize()
+            n_ev, fwd_ms, adj_ms, fft_ms = batch.profile_read()
+            batch.profile(False)
+            forms = batch.field_forms()
+            f_ms, a_ms, t_ms = fwd_ms / n_ev, adj_ms / n_ev, fft_ms / n_ev
+            if t_ms >= max(f_ms, a_ms):
+                tb = fft_bytes(fields)
+                ach = tb / (t_ms / 1e3) / 1e9
+                L = fft_size(fields[0].N, fields[0].K, fields[0].f)
+                kern = ("fft_load_rows/cols/rows + big_window_adj (global-memory transforms, L = %d)" % L
+                        if L in BIG_SIZES else "fft_hhat_pair_kernel + fft_chunk_pair_kernel (L = %d)" % L)
+                out["roofline"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                                   "frac": round(ach / hbm, 4), "traffic": None, "kernel": kern,
+                                   "kernel_ms": round(t_ms, 4), "bytes_per_launch": tb,
+                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+            else:
+                fl = fwd_flops(fields)
+                dom_ms, dom = (f_ms, "fwd") if f_ms >= a_ms else (a_ms, "adj")
+                ach = fl / (dom_ms / 1e3) / 1e12
+                out["roofline"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
+                                   "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
+                                   "kernel": f"{dom}_kernel<16>", "kernel_ms": round(dom_ms, 4),
+                                   "peak_source": "measured FFMA microbenchmark"}
+            out["forms"] = sorted(set(forms))
+            units = units_of(fields, None)
+            # the plain per-epoch form on the same fields
+            if name == "config5":
+                # the plain form's kernels hold the whole PSF in shared memory (K = 255 does not fit):
+                # the direct D-folded form on the same frames instead
+                dp = [Problem.from_field(fd, conv_mode="direct", stream=stream) for fd in fields]
+                db = Batch(dp, stream=stream)
+                dms = timed_steps(lambda: db.step(P, 1, cfg, sync=False), 2, 1, stream, flush)
+                out["plain"] = None
+                out["direct"] = {"value": units / (dms / 1e3), "unit": "epoch-px/s", "ms_per_step": round(dms, 3),
+                                 "speedup_transform_over_direct": dms / ms}
+                db.close()
+                for pr in dp:
+                    pr.close()
+            else:
+                pp = [Problem.from_field(fd, conv_mode="plain", stream=stream) for fd in fields]
+                Pp = [torch.from_numpy(fd.params).cuda() for fd in fields]
+                Gp = [torch.empty_like(x) for x in Pp]
+
+                def plain_eval():
+                    for pr, x, g in zip(pp, Pp, Gp):
+                        pr.loss_and_grad(x, g, sync=False)
+                pms = timed_steps(plain_eval, 2, 1, stream, flush)
+                plain_v = units / (pms / 1e3)
+                out["plain"] = {"value": plain_v, "unit": "epoch-px/s", "ms_per_eval": round(pms, 3),
+                                "speedup_batched_over_plain": (units / (ms / 1e3)) / plain_v}
+                for pr in pp:
+                    pr.close()
+            batch.close()
+            for pr in probs:
+                pr.close()
+        else:
+            psf = Problem.from_psf(pb, stream=stream)
+            Q = torch.from_numpy(pb.params).cuda()
+            cfg_psf = optim_cfg("adabelief", lr=(1e-5, 1e-3, 10.0, 1e-3))
+            ms = timed_steps(lambda: psf.step(Q, 1, cfg_psf, sync=False), steps, warm, stream, flush)
+            units = units_of([], pb)
+            # algorithmic bytes of a PSF-fit step: stars and weights read, b read and its gradient
+            # written, the optimiser's 28 B per parameter
+            byts = pb.S * pb.N * pb.N * 8 + pb.F * pb.F * 8 + 28 * pb.n_params
+            ach = byts / (ms / 1e3) / 1e9
+            out["roofline"] = {"bound": "hbm", "achieved": round(ach, 2), "peak": hbm, "unit": "GB/s",
+                               "frac": round(ach / hbm, 5), "traffic": None,
+                               "kernel": "the whole PSF-fit step (9 launches; latency-bound at this size)",
+                               "bytes_per_step": byts, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+            out["plain"] = None
+            psf.close()
+    out["value"] = units / (ms / 1e3)
+    out["ms_per_step"] = round(ms, 4)
+    out["epoch_pixels_per_step"] = units
+    if with_cpu:
+        cf = fields if name != "config5" else [syn.config5(E=1, N=128)]
+        cs = "all of it" if name != "config5" else "one 128x128 frame of the config-5 kind (f = 3, K = 255, 40 sources)"
+        if name == "config3":   # a tenth of the epochs
+            cf = [first_epochs(fields[0], 30)]
+            cs = "the first 30 of the 300 epochs"
+        v, dt, cores = oracle_rate(cf, pb if not fields else None)
+        out["cpu_baseline"] = {"value": v, "unit": "epoch-px/s", "cores": cores, "kind": "oracle", "sample": cs,
+                               "seconds": round(dt, 2)}
+    return out
+
+
+def measure_configs(stream, fp32_peak, hbm, with_cpu):
+    return {name: measure_config(name, stream, fp32_peak, hbm, with_cpu, steps=5 if name == "config5" else 10)
+            for name in ("config1", "config2", "config3", "config5")}
 
 
 def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
