@@ -576,6 +576,8 @@ def run_ours(args):
                  for i, fd in enumerate(fields)]
         torch.cuda.synchronize()
         batch = Batch(probs, stream=stream) if probs else None
+        # the transform form's schedule (epochs per work item, pair cap), timed on the batch
+        schedule = batch.tune_schedule() if batch is not None else None
         # the PSF fit is independent of the batch: it runs on its own stream, forked from and
         # joined to `stream` in every step, so that its small launches overlap the batch's
         psf_stream = torch.cuda.Stream()
@@ -751,6 +753,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2" if units * 12 > 129e6 else "inputs smaller than L2 (no flush)",
                        "generation_s": round(t_gen, 1)},
             "graph_ms_per_step": graph_ms,
+            "schedule": schedule,
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": roof,
@@ -834,6 +837,7 @@ def measure_config(name, stream, fp32_peak, hbm, with_cpu, steps=10, warm=3):
         if fields:
             probs = [Problem.from_field(fd, stream=stream) for fd in fields]
             batch = Batch(probs, stream=stream)
+            out["schedule"] = batch.tune_schedule()
             P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
             cfg = optim_cfg("adabelief", lr=lr_groups(fields[0]))
             ms = timed_steps(lambda: batch.step(P, 1, cfg, sync=False), steps, warm, stream, flush)

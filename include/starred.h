@@ -283,6 +283,28 @@ sr_status sr_batch_reset_optimizer(sr_batch *b);
  * argument. */
 int sr_batch_field_form(const sr_batch *b, int i);
 
+/* Schedule of the transform form (the paper has no counterpart: it decides how
+ * the epochs of sec. 2.4's joint evaluation are spread over the GPU, not what is
+ * computed).  The per-epoch kernel takes work items of epochs_per_item
+ * consecutive epochs of one field (each with its own accumulator of adjoint
+ * spectra) and transforms pairs_per_group = 1 epoch pair at a time, or (0) the
+ * widest group of pairs compiled for the field's transform size.  By default a
+ * batch takes as many epochs per item as keep at least two items per SM (even,
+ * 2 .. 16).  sr_batch_set_schedule rebuilds the batch's plan with the given
+ * schedule (epochs_per_item 0 or even in 2 .. 16; pairs_per_group 0 or 1;
+ * SR_ERR_ARG otherwise); it synchronises the batch's stream and drops its
+ * captured optimiser graph.  Results differ between schedules only by the
+ * order of FP32 sums of the adjoint spectra.  sr_batch_get_schedule gives the
+ * schedule in use (epochs per item, pair cap).  sr_batch_tune_schedule times
+ * one warm-up and three evaluations of each candidate (2, 4, 8, 16 epochs per
+ * item, each with and without the pair cap) on zero parameters, keeps the
+ * fastest and caches it by a digest of the fields' shapes and forms (in memory,
+ * and in the SR_AUTOTUNE_CACHE file when set); a cached schedule is applied
+ * without timing (*ms_per_eval = -1).  Output pointers may be NULL. */
+sr_status sr_batch_set_schedule(sr_batch *b, int epochs_per_item, int pairs_per_group);
+sr_status sr_batch_get_schedule(const sr_batch *b, int *epochs_per_item, int *pairs_per_group);
+sr_status sr_batch_tune_schedule(sr_batch *b, int *epochs_per_item, int *pairs_per_group, float *ms_per_eval);
+
 /* Launch statistics of the last evaluation on this problem/batch: number of
  * kernel launches one loss_and_grad issues. */
 int sr_launches_per_eval(const sr_problem *p);

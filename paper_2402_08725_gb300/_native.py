@@ -88,6 +88,10 @@ PROTOTYPES = {
     "sr_launches_per_eval": ([c_void_p], c_int),
     "sr_batch_launches_per_eval": ([c_void_p], c_int),
     "sr_batch_field_form": ([c_void_p, c_int], c_int),
+    "sr_batch_set_schedule": ([c_void_p, c_int, c_int], c_int),
+    "sr_batch_get_schedule": ([c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)], c_int),
+    "sr_batch_tune_schedule": ([c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_float)],
+                               c_int),
     "sr_batch_profile": ([c_void_p, c_int], c_int),
     "sr_batch_profile_read": ([c_void_p, ctypes.POINTER(c_int), P_double, P_double, P_double], c_int),
     "sr_measure_fp32_peak": ([P_double], c_int),

@@ -335,6 +335,27 @@ class Batch:
         return ["fft" if self.lib.sr_batch_field_form(self.handle, i) == nat.SR_CONV_FFT else "direct"
                 for i in range(len(self.problems))]
 
+    def set_schedule(self, epochs_per_item: int = 0, pairs_per_group: int = 0):
+        """Schedule of the transform form (0 = automatic); rebuilds the batch's plan."""
+        nat.check(self.lib.sr_batch_set_schedule(self.handle, int(epochs_per_item), int(pairs_per_group)),
+                  "sr_batch_set_schedule")
+
+    def schedule(self):
+        """(epochs per work item, pair cap) of the plan in use."""
+        c, g = ctypes.c_int(), ctypes.c_int()
+        nat.check(self.lib.sr_batch_get_schedule(self.handle, ctypes.byref(c), ctypes.byref(g)),
+                  "sr_batch_get_schedule")
+        return c.value, g.value
+
+    def tune_schedule(self):
+        """Times the candidate schedules and keeps the fastest (or the cached choice):
+        {"epochs_per_item", "pairs_per_group", "ms_per_eval" (None when cached)}."""
+        c, g, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        nat.check(self.lib.sr_batch_tune_schedule(self.handle, ctypes.byref(c), ctypes.byref(g), ctypes.byref(ms)),
+                  "sr_batch_tune_schedule")
+        return {"epochs_per_item": c.value, "pairs_per_group": g.value,
+                "ms_per_eval": None if ms.value < 0 else float(ms.value)}
+
     def profile(self, enable: bool = True):
         nat.check(self.lib.sr_batch_profile(self.handle, 1 if enable else 0), "sr_batch_profile")
 

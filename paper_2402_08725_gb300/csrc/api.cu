@@ -175,6 +175,7 @@ struct Plan {
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
     // frequency-domain form
     int n_fft_items = 0, n_fft_fields = 0, max_pairs = 1, smem_fft = 0, smem_fx = 0, grid_fft = 0;
+    int chunk = kFftChunk, gp_cap = 0;  // the schedule the plan was built with (epochs per item, pair cap)
     int4 *d_fft_items = nullptr;
     int *d_fft_fields = nullptr;
     float2 *hhat = nullptr, *fft_acc = nullptr;
@@ -272,6 +273,7 @@ struct sr_batch {
         }
     }
     Plan *plan = nullptr;
+    int sched_chunk = 0, sched_gp = 0;  // requested schedule of the transform form (0: automatic)
 };
 
 // ------------------------------------------------------------------------------------------
@@ -433,6 +435,8 @@ struct PlanOptions {
     int mode_override = -1;  // -1: the problem's own choice, 0: direct tiles, 1: transforms
     int epoch_limit = 0;     // > 0: evaluate only the first epochs
     int grid_limit = 0;      // > 0: at most this many blocks in the persistent kernels
+    int chunk = 0;           // epochs per work item of the transform form (even, <= kFftChunk; 0: by rule)
+    int gp_cap = 0;          // 1: one epoch pair per group in the transform form (0: the widest compiled)
 };
 
 static bool field_uses_fft(sr_problem *p, const PlanOptions &opt);
@@ -461,6 +465,19 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     std::vector<FieldDev> sh;
     std::vector<ChunkItem> sh_chunks;
     long long pbar_len = 0, l1pts = 0, ptsslot = 0;
+    // epochs per work item of the transform form: by default as many as keep at least two items per
+    // SM (even, 2 .. kFftChunk), so that a single long field spreads over the GPU
+    int chunk = opt.chunk;
+    if (chunk <= 0) {
+        long long ep = 0;
+        for (int i = 0; i < n; ++i)
+            if (probs[i]->fft_ok && !probs[i]->fft_big)
+                ep += opt.epoch_limit > 0 ? std::min(probs[i]->desc.n_epochs, opt.epoch_limit) : probs[i]->desc.n_epochs;
+        chunk = (int)std::min<long long>(kFftChunk, std::max<long long>(2, ep / (2LL * std::max(g_num_sms, 1)))) & ~1;
+    }
+    chunk = std::max(2, std::min(kFftChunk, chunk)) & ~1;
+    pl->chunk = chunk;
+    pl->gp_cap = opt.gp_cap;
     for (int i = 0; i < n; ++i) {
         sr_problem *p = probs[i];
         if (p->desc.kind != pl->kind) return fail(SR_ERR_ARG, "a batch mixes problem kinds");
@@ -518,9 +535,9 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             const int L = fd.fft_L, H = L / 2 + 1;
             const int nph = fd.f * fd.f;
             fd.fft_acc_off = acc_len;
-            fd.fft_n_chunks = (fd.E + kFftChunk - 1) / kFftChunk;
+            fd.fft_n_chunks = (fd.E + chunk - 1) / chunk;
             for (int c = 0; c < fd.fft_n_chunks; ++c)
-                fft_items.push_back(make_int4(i, c * kFftChunk, std::min(fd.E, (c + 1) * kFftChunk), c));
+                fft_items.push_back(make_int4(i, c * chunk, std::min(fd.E, (c + 1) * chunk), c));
             acc_len += (long long)fd.fft_n_chunks * nph * L * (H + 1);  // rows padded to H + 1
             fd.fft_hhat_off = hhat_len;
             hhat_len += (long long)nph * L * (H + 1);
@@ -529,7 +546,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             smem_fft = std::max(smem_fft, fft_pair_field_smem(L));
             // epoch pairs side by side: the widest group the kernel is compiled for at this size
             // (more than one pair only with at most one source) if its buffers fit, else one pair
-            int G = fd.M <= 1 ? fft_pair_gpmax(L) : 1;
+            int G = fd.M <= 1 && opt.gp_cap != 1 ? fft_pair_gpmax(L) : 1;
             if (G > 1 && fft_pair_smem_bytes(L, fd.M, fd.f, G) > g_fx_smem_limit) G = 1;
             fd.fft_G = G;
             fd.fft_EB = fft_pair_zn(L);
@@ -1409,6 +1426,129 @@ sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream,
         return st;
     }
     *out = b;
+    return SR_OK;
+}
+
+// Rebuilds the batch's plan with a schedule of the transform form (0: automatic).
+static sr_status batch_replan(sr_batch *b, int chunk, int gp) {
+    if (b->stream) SR_CUDA(cudaStreamSynchronize(b->stream));
+    else SR_CUDA(cudaDeviceSynchronize());
+    Plan *pl = new (std::nothrow) Plan();
+    if (!pl) return fail(SR_ERR_OOM, "host allocation failed");
+    PlanOptions opt;
+    opt.chunk = chunk;
+    opt.gp_cap = gp;
+    sr_status st = build_plan(pl, b->probs.data(), (int)b->probs.size(), false, opt);
+    if (st != SR_OK) {
+        delete pl;
+        return st;
+    }
+    delete b->plan;
+    b->plan = pl;
+    b->sched_chunk = chunk;
+    b->sched_gp = gp;
+    return SR_OK;
+}
+
+sr_status sr_batch_set_schedule(sr_batch *b, int epochs_per_item, int pairs_per_group) {
+    if (!b) return fail(SR_ERR_ARG, "NULL batch");
+    if (epochs_per_item < 0 || epochs_per_item > kFftChunk || (epochs_per_item & 1) ||
+        (epochs_per_item > 0 && epochs_per_item < 2))
+        return fail(SR_ERR_ARG, "epochs per item must be 0 (automatic) or even in 2..%d", kFftChunk);
+    if (pairs_per_group != 0 && pairs_per_group != 1)
+        return fail(SR_ERR_ARG, "pairs per group must be 0 (the widest compiled) or 1");
+    return batch_replan(b, epochs_per_item, pairs_per_group);
+}
+
+sr_status sr_batch_get_schedule(const sr_batch *b, int *epochs_per_item, int *pairs_per_group) {
+    if (!b || !epochs_per_item || !pairs_per_group) return fail(SR_ERR_ARG, "NULL argument");
+    *epochs_per_item = b->plan->chunk;
+    *pairs_per_group = b->plan->gp_cap;
+    return SR_OK;
+}
+
+// Key of a batch's fields for the schedule cache: FNV-1a over each field's (N, E, f, K, M, form).
+static std::string schedule_key(const sr_batch *b) {
+    unsigned long long h = 1469598103934665603ULL;
+    auto mix = [&](long long v) {
+        for (int k = 0; k < 8; ++k) {
+            h ^= (unsigned long long)((v >> (8 * k)) & 0xff);
+            h *= 1099511628211ULL;
+        }
+    };
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        const sr_problem_desc &d = b->probs[i]->desc;
+        mix(d.data_n);
+        mix(d.n_epochs);
+        mix(d.supersampling);
+        mix(d.psf_k);
+        mix(d.n_sources);
+        mix(b->plan->h_fields[i].mode);
+    }
+    char buf[64];
+    snprintf(buf, sizeof buf, "schedule:%016llx", h);
+    return buf;
+}
+
+sr_status sr_batch_tune_schedule(sr_batch *b, int *epochs_per_item, int *pairs_per_group, float *ms_per_eval) {
+    if (!b) return fail(SR_ERR_ARG, "NULL batch");
+    sr_status st;
+    const std::string key = schedule_key(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            const int c = it->second & 0xff, g = (it->second >> 8) & 0xff;
+            if ((st = batch_replan(b, c, g)) != SR_OK) return st;
+            if (epochs_per_item) *epochs_per_item = b->plan->chunk;
+            if (pairs_per_group) *pairs_per_group = b->plan->gp_cap;
+            if (ms_per_eval) *ms_per_eval = -1.f;  // from the cache, not timed
+            return SR_OK;
+        }
+    }
+    // time each candidate on zero parameters: one evaluation to warm up, then three
+    float best_ms = 0.f;
+    int best_c = 0, best_g = 0;
+    cudaStream_t s = b->stream;
+    for (int c : {2, 4, 8, 16})
+        for (int g : {0, 1}) {
+            if ((st = batch_replan(b, c, g)) != SR_OK) return st;
+            Plan *pl = b->plan;
+            if (pl->n_fft_items == 0 && (c != 2 || g != 0)) continue;  // nothing to schedule
+            float *params = nullptr, *grad = nullptr;
+            if ((st = pl->arena.alloc(&params, pl->n_params)) != SR_OK) return st;
+            if ((st = pl->arena.alloc(&grad, pl->n_params)) != SR_OK) return st;
+            SR_CUDA(cudaMemsetAsync(params, 0, sizeof(float) * pl->n_params, s));
+            cudaEvent_t e0, e1;
+            SR_CUDA(cudaEventCreate(&e0));
+            SR_CUDA(cudaEventCreate(&e1));
+            run_eval(pl, params, grad, s, nullptr);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) run_eval(pl, params, grad, s, nullptr);
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (e != cudaSuccess) return cuda_fail(e, "schedule timing");
+            t /= 3.f;
+            if (best_c == 0 || t < best_ms) {
+                best_ms = t;
+                best_c = c;
+                best_g = g;
+            }
+        }
+    if ((st = batch_replan(b, best_c, best_g)) != SR_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune[key] = best_c | (best_g << 8);
+        tune_save();
+    }
+    if (epochs_per_item) *epochs_per_item = best_c;
+    if (pairs_per_group) *pairs_per_group = best_g;
+    if (ms_per_eval) *ms_per_eval = best_ms;
     return SR_OK;
 }
 

@@ -379,3 +379,49 @@ def test_guard_bands_uneven_batch_both_forms(monkeypatch):
     batch.close()
     for pr in probs:
         pr.close()
+
+
+def test_schedules_forced_and_tuned_agree(tmp_path, monkeypatch):
+    """Epochs per work item and the pair cap of the transform form change only the order of FP32
+    sums (the pair cap changes which rows share an FP32 partial of chi^2): every forced schedule
+    gives the losses within 1e-8 and the gradients within 1e-5 of each other, and the oracle's
+    parity; the tuner keeps one of the candidates and caches it."""
+    import json
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    monkeypatch.setenv("SR_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    fields = [syn.small_deconv(seed=970 + i, E=E, N=N, f=2, K=21, M=1, J=3, lam=1.0)
+              for i, (E, N) in enumerate([(21, 48), (9, 64), (34, 32), (5, 96)])]
+    probs = [Problem.from_field(fd, conv_mode="fft") for fd in fields]
+    batch = Batch(probs)
+    P = torch.from_numpy(batch.pack([fd.params for fd in fields])).cuda()
+    losses = torch.empty(len(fields), dtype=torch.float64, device="cuda")
+    batch.set_schedule(16, 0)
+    _, g_ref = batch.loss_and_grad(P, losses=losses)
+    l_ref, g_ref = losses.cpu().numpy().copy(), g_ref.cpu().numpy().copy()
+    for i, fd in enumerate(fields):
+        o = batch.offsets[i]
+        check_deconv(fd, float(l_ref[i]), g_ref[o:o + fd.n_params])
+    from tests._helpers import rel_l2
+    for c, g in [(2, 0), (4, 1), (8, 0), (16, 1), (6, 0)]:
+        batch.set_schedule(c, g)
+        assert batch.schedule() == (c, g)
+        _, gr = batch.loss_and_grad(P, losses=losses)
+        l = losses.cpu().numpy()
+        assert np.all(np.abs(l - l_ref) <= 1e-8 * np.abs(l_ref)), (c, g, l, l_ref)
+        assert rel_l2(gr.cpu().numpy(), g_ref) <= 1e-5, (c, g)
+    t = batch.tune_schedule()
+    assert t["epochs_per_item"] in (2, 4, 8, 16) and t["pairs_per_group"] in (0, 1) and t["ms_per_eval"] > 0
+    assert batch.schedule() == (t["epochs_per_item"], t["pairs_per_group"])
+    assert any(k.startswith("schedule:") for k in json.loads((tmp_path / "tune.json").read_text()))
+    _, gr = batch.loss_and_grad(P, losses=losses)
+    assert np.all(np.abs(losses.cpu().numpy() - l_ref) <= 1e-8 * np.abs(l_ref))
+    batch.close()
+    batch2 = Batch(probs)
+    t2 = batch2.tune_schedule()   # the cached choice, not timed again
+    assert t2["ms_per_eval"] is None
+    assert (t2["epochs_per_item"], t2["pairs_per_group"]) == (t["epochs_per_item"], t["pairs_per_group"])
+    with pytest.raises(Exception):
+        batch2.set_schedule(3, 0)
+    batch2.close()
+    for pr in probs:
+        pr.close()
