@@ -730,7 +730,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         if ((st = A.alloc(&bb.zb, (size_t)fd.E * npr * fd.N * L)) != SR_OK) return st;
         if ((st = A.alloc(&bb.zt, (size_t)fd.E * npr * fd.N * L)) != SR_OK) return st;
         if ((st = A.alloc(&bb.fhat, (size_t)fd.E * nph * H * L)) != SR_OK) return st;
-        if ((st = A.alloc(&bb.acc, nph * H * L)) != SR_OK) return st;
+        if ((st = A.alloc(&bb.acc, (size_t)((fd.E + 1) / 2) * nph * H * L)) != SR_OK) return st;
         pl->big_buf.push_back(bb);
     }
     if (pl->kind == SR_DECONV && !plain && pl->n_items > 0) {

@@ -41,8 +41,8 @@ struct Bg {
     static constexpr int H = L / 2 + 1;
     static_assert(R1 > 0 && R1 * R2 == L, "transform size not in the list");
 };
-constexpr int kBgRows = 16;       // rows per block of the row transforms
-constexpr int kBgThreads = 384;   // threads per block of the row transforms
+constexpr int kBgRows = 8;        // rows per block of the row transforms
+constexpr int kBgThreads = 192;   // threads per block of the row transforms (one per pass item)
 constexpr int kBgItems = kBgRows / 2;  // (kx, L - kx) row pairs per block of the transposed-row kernels
 constexpr int kBgMaxSources = 64;      // the most point sources a problem may have
 
@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(kBgThreads) big_load_rows_kernel(FieldDev fd, 
     float2 *Z = bsm, *TWL = bsm + kBgRows * G::RW;
     __shared__ float4 s_src[kBgMaxSources];
     __shared__ int2 s_win[kBgMaxSources];
+    __shared__ unsigned long long s_rowmask[kBgRows][2];  // sources whose window holds the fine row
     bg_twl<L>(TWL, fd.fft_tw);
     const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E, nph = f * f, npr = (nph + 1) / 2;
     const int j = blockIdx.y, e = j / npr, q = j - e * npr;
@@ -154,6 +155,16 @@ __global__ void __launch_bounds__(kBgThreads) big_load_rows_kernel(FieldDev fd, 
         const float cx = u0 + (float)f * (cpar[2 * k] + dpar[0]), cy = u0 + (float)f * (cpar[2 * k + 1] + dpar[1]);
         s_src[k] = make_float4(cpar[2 * k], cpar[2 * k + 1], hpar[(long long)F * F + (long long)e * M + k], 0.f);
         s_win[k] = make_int2((int)floorf(cx) - kWinLo, (int)floorf(cy) - kWinLo);
+    }
+    __syncthreads();
+    if (mode == 0 && threadIdx.x < 2 * kBgRows) {
+        const int r = threadIdx.x >> 1, w = threadIdx.x & 1;
+        const int ph = w ? pb : pa;
+        const int uy = f * (y0 + r) + ph / f;
+        unsigned long long m = 0ull;
+        for (int k = 0; k < M; ++k)
+            if ((unsigned)(uy - s_win[k].y) < (unsigned)kWin) m |= 1ull << k;
+        s_rowmask[r][w] = m;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < kBgRows * nx; t += blockDim.x) {
@@ -174,10 +185,12 @@ __global__ void __launch_bounds__(kBgThreads) big_load_rows_kernel(FieldDev fd, 
                     const int uy = f * y + phy, ux = f * x + phx;
                     float s = hpar[(long long)uy * F + ux];
                     // the sources whose window holds the pixel, in index order
-                    for (int k = 0; k < M; ++k)
-                        if ((unsigned)(uy - s_win[k].y) < (unsigned)kWin && (unsigned)(ux - s_win[k].x) < (unsigned)kWin)
+                    for (unsigned long long m = s_rowmask[r][w]; m; m &= m - 1) {
+                        const int k = __ffsll((long long)m) - 1;
+                        if ((unsigned)(ux - s_win[k].x) < (unsigned)kWin)
                             s += s_src[k].z * gauss2(src_offset(ux, F, f, s_src[k].x, dpar[0]),
                                                      src_offset(uy, F, f, s_src[k].y, dpar[1]));
+                    }
                     val[w] = s;
                 }
                 v = make_float2(val[0], val[1]);
@@ -225,10 +238,10 @@ struct BgArgs {
     float2 *spec;          // SPLIT: output spectra [E][nph][H][L]
     const float2 *khat;    // MODEL, ADJ: kernel spectra [E][nph][H][L]
     const float2 *fhat;    // MODEL: image spectra [E][nph][H][L]
-    float2 *acc;           // ADJ (read-modify-write), HJOIN (read): adjoint spectra [nph][H][L]
+    float2 *acc;           // ADJ (write), HJOIN (read): adjoint spectra of each frame pair [pairs][nph][H][L]
     int ny;                // SPLIT, ADJ: spatial extent of the input rows
     int shift;             // SPLIT: tau_lo mod L (0: none)
-    int pair;              // MODEL, ADJ: frames 2 pair and 2 pair + 1
+    int npairs;            // HJOIN: frame pairs whose adjoint spectra are added (in order)
 };
 
 template <int L, int MODE>
@@ -239,7 +252,7 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
     float2 *Z = bsm, *TWL = bsm + kBgRows * RW;
     bg_twl<L>(TWL, fd.fft_tw);
     const int f = fd.f, N = fd.N, E = fd.E, nph = f * f, npr = (nph + 1) / 2;
-    const int j = blockIdx.y;  // image (SPLIT: e * npr + q; HJOIN: q)
+    const int j = blockIdx.y;  // image (SPLIT: e * npr + q; MODEL, ADJ: frame pair; HJOIN: q)
     const int kx0 = blockIdx.x * kBgItems;
     const long long SL = (long long)H * L;  // one transposed half spectrum
     // load or build the rows
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
         __syncthreads();
         bg_fwd<L>(Z, kBgRows, ny, TWL);
     } else {
-        const int e0 = 2 * a.pair, e1 = e0 + 1;
+        const int e0 = 2 * j, e1 = e0 + 1;
         const bool has1 = MODE == BG_MODEL ? e1 < E : (2 * j + 1 < nph);
         for (int t = threadIdx.x; t < kBgItems * L; t += blockDim.x) {
             const int i = t / L, ky = t - i * L;
@@ -275,9 +288,12 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
                     if (has1)
                         B = cadd(B, cmul(a.khat[((long long)e1 * nph + ph) * SL + off], a.fhat[((long long)e1 * nph + ph) * SL + off]));
                 }
-            } else {  // HJOIN: phases 2j and 2j + 1
-                A = a.acc[(long long)(2 * j) * SL + off];
-                if (has1) B = a.acc[(long long)(2 * j + 1) * SL + off];
+            } else {  // HJOIN: phases 2j and 2j + 1, the frame pairs' adjoint spectra added in order
+                for (int p = 0; p < a.npairs; ++p) {
+                    const float2 *ap = a.acc + (long long)p * nph * SL;
+                    A = cadd(A, ap[(long long)(2 * j) * SL + off]);
+                    if (has1) B = cadd(B, ap[(long long)(2 * j + 1) * SL + off]);
+                }
             }
             const int kym = (L - ky) % L;
             float2 *r0 = Z + (2 * i) * RW, *r1 = Z + (selfrow ? 2 * i : 2 * i + 1) * RW;
@@ -293,7 +309,7 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
     }
     // use or store the rows
     if constexpr (MODE == BG_MODEL || MODE == BG_HJOIN) {
-        float2 *dst = a.zt_out + (long long)(MODE == BG_HJOIN ? j : 0) * L * N;
+        float2 *dst = a.zt_out + (long long)j * L * N;
         for (int t = threadIdx.x; t < kBgRows * N; t += blockDim.x) {
             const int s = t / N, y = t - s * N;
             const int kx = kx0 + (s >> 1);
@@ -324,14 +340,14 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
             }
             a.spec[((long long)e * nph + 2 * q) * SL + off] = va;
             if (2 * q + 1 < nph) a.spec[((long long)e * nph + 2 * q + 1) * SL + off] = vb;
-        } else {  // ADJ: acc_phi += conj(Khat_{e0,phi}) ehat_e0 + conj(Khat_{e1,phi}) ehat_e1
-            const int e0 = 2 * a.pair, e1 = e0 + 1;
+        } else {  // ADJ: the pair's acc_phi = conj(Khat_{e0,phi}) ehat_e0 + conj(Khat_{e1,phi}) ehat_e1
+            const int e0 = 2 * j, e1 = e0 + 1;
             const bool has1 = e1 < E;
+            float2 *ap = a.acc + (long long)j * nph * SL;
             for (int ph = 0; ph < nph; ++ph) {
-                float2 run = a.pair == 0 ? make_float2(0.f, 0.f) : a.acc[(long long)ph * SL + off];
-                run = cadd(run, cmulc(xa, a.khat[((long long)e0 * nph + ph) * SL + off]));
+                float2 run = cmulc(xa, a.khat[((long long)e0 * nph + ph) * SL + off]);
                 if (has1) run = cadd(run, cmulc(xb, a.khat[((long long)e1 * nph + ph) * SL + off]));
-                a.acc[(long long)ph * SL + off] = run;
+                ap[(long long)ph * SL + off] = run;
             }
         }
     }
@@ -347,7 +363,7 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
 // ---------------------------------------------------------------------------------------------
 template <int L, int MODE>
 __global__ void __launch_bounds__(kBgThreads) big_rows_kernel(FieldDev fd, float2 *__restrict__ zb,
-                                                              const float *__restrict__ params, int pair,
+                                                              const float *__restrict__ params,
                                                               float *__restrict__ ebuf, double *__restrict__ chi_part,
                                                               double *__restrict__ se_part, float *__restrict__ grad) {
     using G = Bg<L>;
@@ -358,7 +374,7 @@ __global__ void __launch_bounds__(kBgThreads) big_rows_kernel(FieldDev fd, float
     __shared__ float4 red[kBgRows][TPR];
     bg_twl<L>(TWL, fd.fft_tw);
     const int f = fd.f, N = fd.N, F = fd.F, E = fd.E, M = fd.M;
-    const int j = MODE == BG_RESID_ROWS ? 0 : blockIdx.y;
+    const int j = blockIdx.y;  // RESID: frame pair; HOUT: pair of phases
     float2 *img = zb + (long long)j * N * L;
     const int y0 = blockIdx.x * kBgRows;
     for (int t = threadIdx.x; t < kBgRows * L; t += blockDim.x) {
@@ -369,7 +385,7 @@ __global__ void __launch_bounds__(kBgThreads) big_rows_kernel(FieldDev fd, float
     bg_inv<L>(Z, kBgRows, N, TWL);
     const float scale = 1.f / ((float)L * (float)L);
     if constexpr (MODE == BG_RESID_ROWS) {
-        const int e0 = 2 * pair, e1 = e0 + 1;
+        const int e0 = 2 * j, e1 = e0 + 1;
         const bool has1 = e1 < E;
         const float *gam = params + fd.param_off + (long long)F * F + (long long)E * M + 2 * M + 2 * E;
         const float bg0 = (float)(f * f) * gam[e0], bg1 = has1 ? (float)(f * f) * gam[e1] : 0.f;
@@ -597,28 +613,24 @@ template <int L>
 static int big_eval_t(const FieldDev &fd, const float *params, const BigBuffers &bb, float *ebuf, float *gbuf,
                       double *chi_part, double *se_part, cudaStream_t st) {
     int n = big_spectra_t<L>(fd, params, 0, bb.zb, bb.zt, bb.fhat, st);
-    const int H = L / 2 + 1, N = fd.N;
-    const dim3 cgrid((H + kBgItems - 1) / kBgItems, 1), rgrid((N + kBgRows - 1) / kBgRows, 1);
-    for (int p = 0; 2 * p < fd.E; ++p) {
-        BgArgs a{};
-        a.zt_out = bb.zt;
-        a.khat = fd.fft_khat;
-        a.fhat = bb.fhat;
-        a.pair = p;
-        big_cols_kernel<L, BG_MODEL><<<cgrid, kBgThreads, bg_smem<L>(), st>>>(fd, a);
-        transpose(bb.zt, bb.zb, L, N, 1, st);
-        big_rows_kernel<L, BG_RESID_ROWS><<<rgrid, kBgThreads, bg_smem<L>(), st>>>(fd, bb.zb, params, p, ebuf, chi_part,
-                                                                                  se_part, nullptr);
-        transpose(bb.zb, bb.zt, N, L, 1, st);
-        BgArgs b{};
-        b.zt_in = bb.zt;
-        b.khat = fd.fft_khat;
-        b.acc = bb.acc;
-        b.ny = N;
-        b.pair = p;
-        big_cols_kernel<L, BG_ADJ><<<cgrid, kBgThreads, bg_smem<L>(), st>>>(fd, b);
-        n += 5;
-    }
+    const int H = L / 2 + 1, N = fd.N, np = (fd.E + 1) / 2;
+    const dim3 cgrid((H + kBgItems - 1) / kBgItems, np), rgrid((N + kBgRows - 1) / kBgRows, np);
+    BgArgs a{};
+    a.zt_out = bb.zt;
+    a.khat = fd.fft_khat;
+    a.fhat = bb.fhat;
+    big_cols_kernel<L, BG_MODEL><<<cgrid, kBgThreads, bg_smem<L>(), st>>>(fd, a);
+    transpose(bb.zt, bb.zb, L, N, np, st);
+    big_rows_kernel<L, BG_RESID_ROWS><<<rgrid, kBgThreads, bg_smem<L>(), st>>>(fd, bb.zb, params, ebuf, chi_part,
+                                                                              se_part, nullptr);
+    transpose(bb.zb, bb.zt, N, L, np, st);
+    BgArgs b{};
+    b.zt_in = bb.zt;
+    b.khat = fd.fft_khat;
+    b.acc = bb.acc;
+    b.ny = N;
+    big_cols_kernel<L, BG_ADJ><<<cgrid, kBgThreads, bg_smem<L>(), st>>>(fd, b);
+    n += 5;
     if (fd.M > 0) {
         const int nph = fd.f * fd.f;
         big_window_adj_kernel<<<fd.E * fd.M * nph, kWinThreads, fft_big_window_smem(fd.Tk, fd.f), st>>>(fd, params, ebuf,
@@ -634,10 +646,11 @@ static int big_hgrad_t(const FieldDev &fd, const BigBuffers &bb, float *grad, cu
     BgArgs a{};
     a.zt_out = bb.zt;
     a.acc = bb.acc;
+    a.npairs = (fd.E + 1) / 2;
     big_cols_kernel<L, BG_HJOIN><<<dim3((H + kBgItems - 1) / kBgItems, npr), kBgThreads, bg_smem<L>(), st>>>(fd, a);
     transpose(bb.zt, bb.zb, L, N, npr, st);
     big_rows_kernel<L, BG_HOUT_ROWS><<<dim3((N + kBgRows - 1) / kBgRows, npr), kBgThreads, bg_smem<L>(), st>>>(
-        fd, bb.zb, nullptr, 0, nullptr, nullptr, nullptr, grad);
+        fd, bb.zb, nullptr, nullptr, nullptr, nullptr, grad);
     return 3;
 }
 

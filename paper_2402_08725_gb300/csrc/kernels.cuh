@@ -60,7 +60,8 @@ void launch_fft_chunks_pair(const FieldDev *fields, const int4 *items, int n_ite
 
 // --- frequency-domain form through global memory (fft_big.cu): sizes beyond shared memory ---
 // Per field and evaluation: zb and zt (the images and their transposes, E * pairs-of-phases * N * L
-// complex each), fhat (the frames' spectra, E * f^2 * (L/2+1) * L) and acc (f^2 * (L/2+1) * L).
+// complex each), fhat (the frames' spectra, E * f^2 * (L/2+1) * L) and acc (the adjoint spectra of
+// each pair of frames, ceil(E/2) * f^2 * (L/2+1) * L).
 struct BigBuffers {
     float2 *zb, *zt, *fhat, *acc;
 };

@@ -18,7 +18,8 @@
 //    loading), so that its column pass reads one plane per tap; the signs are taken from the c
 //    planes once per output pixel.  Same arithmetic, in the same order, as the passes below.
 //  * passes (fields too wide for the shared-memory budget): one launch per pass and level,
-//    every field of the table in 256-pixel chunks.
+//    every field of the table in 256-pixel chunks; the adjoint first writes V_{j+1} = T_{j+1} -
+//    gamma_{j+1} over T_{j+1} in place (pass 4), so that its column pass reads one plane per tap.
 // Fields deeper than a level skip it.
 #include <algorithm>
 
@@ -77,11 +78,12 @@ __device__ __forceinline__ float adj_1d(const float *__restrict__ y, int n, int 
 constexpr int kStarletChunks = 4;
 
 // pass = 0: forward row pass; 1: forward column pass (+ detail plane, L1 partial);
-//        2: adjoint column pass; 3: adjoint row pass (+ gamma).
+//        4: V_{j+1} = T_{j+1} - gamma_{j+1} in place; 2: adjoint column pass of V_{j+1};
+//        3: adjoint row pass (+ gamma).
 __global__ void __launch_bounds__(256)
 starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__restrict__ chunks, int n_chunks,
                     const float *__restrict__ params, double *__restrict__ l1_part, int j, int pass) {
-    __shared__ double s_red[kStarletChunks][8];
+    __shared__ float2 s_red[kStarletChunks][8];
     const int step = 1 << j;
 #pragma unroll
     for (int q = 0; q < kStarletChunks; ++q) {
@@ -95,7 +97,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
         const bool valid = px < F * F;
         const int y = valid ? px / F : 0, x = valid ? px - y * F : 0;
         const float lw = fd.lambda * fd.Wd[j];
-        double l1 = 0.0;
+        FSum l1 = fsum_zero();
         if (pass == 0) {
             if (valid) {
                 const float *cj = c_plane(fd, params, j) + (long long)y * F;
@@ -113,34 +115,24 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
                 cn[px] = acc;
                 const float wv = c_plane(fd, params, j)[px] - acc;
-                l1 = (double)fabsf(wv);
+                l1 = FSum{fabsf(wv), 0.f};
             }
-        } else if (pass == 2) {
+        } else if (pass == 4) {
             if (valid) {
-                // v = T_{j+1} - gamma_{j+1}; tmp = Col^T v, gathered over the (up to three) rows k
-                // whose mirrored taps land on row y
+                // V_{j+1} = T_{j+1} - gamma_{j+1}, written over T_{j+1} (T_{J-1} = 0)
                 const float *cj = c_plane(fd, params, j);
                 const float *cn = fd.starlet + (long long)j * F * F;
                 const bool has_t = (j + 1) < (fd.J - 1);
-                const float *Tn = t_plane(fd, j + 1);
-                auto v = [&](int k) {
-                    const long long o = (long long)k * F + x;
-                    const float wv = cj[o] - cn[o];
-                    const float g = wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f);
-                    return (has_t ? Tn[o] : 0.f) - g;
-                };
-                float acc = 0.f;
-#pragma unroll
-                for (int m = -2; m <= 2; ++m) {
-                    const float b = kB3[m + 2];
-                    const int k1 = y - m * step;
-                    if (k1 >= 0 && k1 < F) acc += b * v(k1);
-                    const int k2 = -y - m * step;
-                    if (y > 0 && k2 >= 0 && k2 < F) acc += b * v(k2);
-                    const int k3 = 2 * (F - 1) - y - m * step;
-                    if (y < F - 1 && k3 >= 0 && k3 < F) acc += b * v(k3);
-                }
-                pass_plane(fd)[px] = acc;
+                float *Tn = t_plane(fd, j + 1);
+                const float wv = cj[px] - cn[px];
+                const float g = wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f);
+                Tn[px] = (has_t ? Tn[px] : 0.f) - g;
+            }
+        } else if (pass == 2) {
+            if (valid) {
+                // tmp = Col^T V_{j+1}, gathered over the (up to three) rows k whose mirrored taps
+                // land on row y
+                pass_plane(fd)[px] = adj_1d(t_plane(fd, j + 1) + x, y, F, step, F);
             }
         } else {
             if (valid) {
@@ -152,10 +144,9 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
             }
         }
         if (pass == 1) {
-            // deterministic reduction of |w| over the item's 256 pixels
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) l1 += __shfl_down_sync(0xffffffffu, l1, o);
-            if ((threadIdx.x & 31) == 0) s_red[q][threadIdx.x >> 5] = l1;
+            // deterministic reduction of |w| over the item's 256 pixels (compensated FP32 pairs)
+            l1 = fsum_warp(l1);
+            if ((threadIdx.x & 31) == 0) s_red[q][threadIdx.x >> 5] = make_float2(l1.hi, l1.lo);
         }
     }
     if (pass == 1) {
@@ -166,10 +157,10 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 const ChunkItem ch = chunks[c];
                 const FieldDev &fd = fields[ch.field];
                 if (j <= fd.J - 2 && !starlet_banded(fd.F, fd.J)) {
-                    double s = 0.0;
-                    for (int i = 0; i < 8; ++i) s += s_red[threadIdx.x][i];
+                    FSum s = fsum_zero();
+                    for (int i = 0; i < 8; ++i) s = fsum_add(s, FSum{s_red[threadIdx.x][i].x, s_red[threadIdx.x][i].y});
                     l1_part[fd.l1_slot + (long long)j * fd.n_chunks + ch.chunk] =
-                        (double)fd.lambda * (double)fd.Wd[j] * s;
+                        (double)fd.lambda * (double)fd.Wd[j] * fsum_value(s);
                 }
             }
         }
@@ -325,9 +316,10 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unba
         starlet_band_adj_kernel<<<bgrid, 256, band_smem(j), st>>>(fields, params, j);
         ++n;
         if (any_unbanded) {
+            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 4);
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 3);
-            n += 2;
+            n += 3;
         }
     }
     return n;
