@@ -16,6 +16,7 @@ Functions and the passages they follow:
   starlet_analysis / _adjoint     Phi^T, the starlet transform of the prior (Eq. 6)
   starlet_prior                   lambda ||W o Phi^T h||_1 and its subgradient (Eq. 6, Eq. 11)
   deconv_model / deconv_loss_grad the two-channel multi-epoch model and loss (Eq. 9-11)
+  translate / _adjoint            the extended channel moved with an epoch's shift (sec. 5; bilinear)
   moffat                          the analytic part of the narrow PSF (Eq. 2)
   psf_model / psf_loss_grad       PSF reconstruction (Eq. 2-4, Eq. 7)
   optim_step                      AdaBelief / Adam update used by the optimiser (sec. 2.4)
@@ -82,6 +83,9 @@ def _load():
             "orc_deconv_param_count": ([i, i, i, i], sz),
             "orc_deconv_model": ([i, i, i, i, i, _dp, _dp, _dp], i),
             "orc_deconv_loss_grad": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
+            "orc_deconv_loss_grad_shifted": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
+            "orc_translate": ([i, d, d, _dp, _dp], i),
+            "orc_translate_adjoint": ([i, d, d, _dp, _dp], i),
             "orc_moffat": ([i, d, d, _dp, _dp, _dp], i),
             "orc_psf_param_count": ([i, i, i], sz),
             "orc_psf_model": ([i, i, i, _dp, _dp], i),
@@ -142,6 +146,24 @@ def conv_same_adjoint(y, s):
     F, K = y.shape[0], s.shape[0]
     out = np.empty((F, F))
     _check(_load().orc_conv_same_adjoint(F, K, _ptr(y), _ptr(s), _ptr(out)), "conv_same_adjoint")
+    return out
+
+
+def translate(h, sx, sy):
+    """The fine image moved by (sx, sy) fine pixels: out(u) = h(u - s), bilinear, zero outside
+    (the extended channel moved with an epoch's shift, sec. 5; the interpolation is a reading)."""
+    h = _f64(h)
+    F = h.shape[0]
+    out = np.empty((F, F))
+    _check(_load().orc_translate(F, float(sx), float(sy), _ptr(h), _ptr(out)), "translate")
+    return out
+
+
+def translate_adjoint(g, sx, sy):
+    g = _f64(g)
+    F = g.shape[0]
+    out = np.empty((F, F))
+    _check(_load().orc_translate_adjoint(F, float(sx), float(sy), _ptr(g), _ptr(out)), "translate_adjoint")
     return out
 
 
@@ -210,8 +232,9 @@ def deconv_model(E, N, f, K, M, s, params):
     return out
 
 
-def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, nthreads=0):
-    """Return (loss, parts[chi2, prior], grad or None, chi2 per epoch)."""
+def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, nthreads=0, shifted=False):
+    """Return (loss, parts[chi2, prior], grad or None, chi2 per epoch).  shifted=True moves the
+    extended channel h by each epoch's shift f * delta_i (translate) before the convolution."""
     d, sigma, s, W, params = _f64(d), _f64(sigma), _f64(s), _f64(W), _f64(params)
     n = deconv_param_count(E, N, f, M)
     if params.size != n:
@@ -219,8 +242,9 @@ def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, n
     parts = np.zeros(2)
     g = np.empty(n) if grad else None
     chi = np.empty(E)
-    rc = _load().orc_deconv_loss_grad(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W),
-                                      _ptr(params), _ptr(parts), _ptr(g), _ptr(chi), int(nthreads))
+    fn = _load().orc_deconv_loss_grad_shifted if shifted else _load().orc_deconv_loss_grad
+    rc = fn(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W), _ptr(params), _ptr(parts), _ptr(g),
+            _ptr(chi), int(nthreads))
     _check(rc, "deconv_loss_grad")
     return float(parts.sum()), parts, g, chi
 

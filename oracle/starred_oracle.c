@@ -352,12 +352,79 @@ static void source_centre(int F, int f, const double *c, const double *dl, int k
     *uy = u0 + f * (c[2 * k + 1] + dl[2 * i + 1]);
 }
 
+/* Translation of the fine image h by (sx, sy) fine pixels (the extended channel moved with the
+ * epoch's shift, f * delta_i): out(u) = h(u - s) with bilinear interpolation between the four
+ * fine pixels around u - s and zero outside the grid.  The paper leaves the interpolation open
+ * (sec. 5 names shifts between frames); bilinear is the reading taken. */
+static double bilinear_at(int F, const double *h, double px, double py) {
+    double fx = floor(px), fy = floor(py);
+    int x0 = (int)fx, y0 = (int)fy;
+    double tx = px - fx, ty = py - fy, acc = 0.0;
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+            int x = x0 + a, y = y0 + b;
+            if (x < 0 || x >= F || y < 0 || y >= F) continue;
+            acc += (a ? tx : 1.0 - tx) * (b ? ty : 1.0 - ty) * h[(size_t)y * F + x];
+        }
+    return acc;
+}
+
+int orc_translate(int F, double sx, double sy, const double *h, double *out) {
+    if (F <= 0) return ORC_ERR_SHAPE;
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) out[(size_t)uy * F + ux] = bilinear_at(F, h, ux - sx, uy - sy);
+    return ORC_OK;
+}
+
+/* Transpose of orc_translate: every output pixel u scatters its value to the four pixels its
+ * interpolation read, with the same weights. */
+int orc_translate_adjoint(int F, double sx, double sy, const double *g, double *out) {
+    if (F <= 0) return ORC_ERR_SHAPE;
+    memset(out, 0, sizeof(double) * (size_t)F * F);
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double px = ux - sx, py = uy - sy, fx = floor(px), fy = floor(py);
+            int x0 = (int)fx, y0 = (int)fy;
+            double tx = px - fx, ty = py - fy, gv = g[(size_t)uy * F + ux];
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    int x = x0 + a, y = y0 + b;
+                    if (x < 0 || x >= F || y < 0 || y >= F) continue;
+                    out[(size_t)y * F + x] += (a ? tx : 1.0 - tx) * (b ? ty : 1.0 - ty) * gv;
+                }
+        }
+    return ORC_OK;
+}
+
+/* d out(u) / d sx and d out(u) / d sy of orc_translate (the derivative of the interpolant inside
+ * its cell: minus the weighted differences of the four pixels along each axis). */
+static void translate_dshift(int F, double sx, double sy, const double *h, double *dx, double *dy) {
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double px = ux - sx, py = uy - sy, fx = floor(px), fy = floor(py);
+            int x0 = (int)fx, y0 = (int)fy;
+            double tx = px - fx, ty = py - fy;
+            double v[2][2];
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    int x = x0 + a, y = y0 + b;
+                    v[b][a] = (x < 0 || x >= F || y < 0 || y >= F) ? 0.0 : h[(size_t)y * F + x];
+                }
+            dx[(size_t)uy * F + ux] = -((1.0 - ty) * (v[0][1] - v[0][0]) + ty * (v[1][1] - v[1][0]));
+            dy[(size_t)uy * F + ux] = -((1.0 - tx) * (v[1][0] - v[0][0]) + tx * (v[1][1] - v[0][1]));
+        }
+}
+
 /* Model of epoch i on the data grid: M_i = D S_i (h + sum_k a_ki r_k) + f^2 Gamma_i. */
 static void deconv_model_epoch(int i, int N, int f, int K, int M, const double *s_i, const double *params,
-                               size_t oa, size_t oc, size_t od, size_t og, double *fimg, double *conv, double *model) {
+                               size_t oa, size_t oc, size_t od, size_t og, double *fimg, double *conv, double *model,
+                               int translate) {
     int F = f * N;
     size_t n = (size_t)F * F;
-    memcpy(fimg, params, sizeof(double) * n); /* h */
+    if (translate) /* h moved by the epoch's shift f * delta_i */
+        orc_translate(F, f * params[od + 2 * (size_t)i], f * params[od + 2 * (size_t)i + 1], params, fimg);
+    else
+        memcpy(fimg, params, sizeof(double) * n); /* h */
     for (int k = 0; k < M; ++k) {
         double ux, uy;
         source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
@@ -390,7 +457,7 @@ int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const d
 #pragma omp for schedule(static)
             for (int i = 0; i < E; ++i)
                 deconv_model_epoch(i, N, f, K, M, s + (size_t)i * K * K, params, oa, oc, od, og, fimg, conv,
-                                   model_out + (size_t)i * N * N);
+                                   model_out + (size_t)i * N * N, 0);
         }
         free(fimg); free(conv);
     }
@@ -402,9 +469,9 @@ int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const d
  *   prior term), loss = parts[0] + parts[1].
  *   grad (nullable) is d loss / d params in the packed layout.
  *   chi2_epoch (nullable) receives the chi^2 of each epoch. */
-int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d, const double *sigma,
-                         const double *s, const double *W, const double *params, double *parts, double *grad,
-                         double *chi2_epoch, int nthreads) {
+static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d,
+                            const double *sigma, const double *s, const double *W, const double *params, double *parts,
+                            double *grad, double *chi2_epoch, int nthreads, int translate) {
     if (E <= 0 || N <= 0 || f <= 0 || K <= 0 || M < 0) return ORC_ERR_SHAPE;
     int F = f * N;
     if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
@@ -418,7 +485,11 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
     double *gfine = grad ? malloc(sizeof(double) * n * (size_t)E) : NULL;
     /* d loss / d (fine centre of source k in epoch i), reduced in fixed order below */
     double *dcen = grad ? calloc((size_t)E * M * 2 + 1, sizeof(double)) : NULL;
-    if (!chi || (grad && (!gfine || !dcen))) { free(chi); free(gfine); free(dcen); return ORC_ERR_OOM; }
+    double *dshift = grad ? calloc((size_t)E * 2, sizeof(double)) : NULL;
+    if (!chi || (grad && (!gfine || !dcen || !dshift))) {
+        free(chi); free(gfine); free(dcen); free(dshift);
+        return ORC_ERR_OOM;
+    }
     if (grad) memset(grad, 0, sizeof(double) * tot);
     const double sg = gauss_sigma();
     int err = 0;
@@ -434,7 +505,7 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
 #pragma omp for schedule(dynamic, 1)
             for (int i = 0; i < E; ++i) {
                 const double *s_i = s + (size_t)i * K * K;
-                deconv_model_epoch(i, N, f, K, M, s_i, params, oa, oc, od, og, fimg, conv, model);
+                deconv_model_epoch(i, N, f, K, M, s_i, params, oa, oc, od, og, fimg, conv, model, translate);
                 double c2 = 0.0;
                 for (int p = 0; p < N * N; ++p) {
                     size_t ip = (size_t)i * N * N + p;
@@ -472,11 +543,23 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
                     dcen[((size_t)i * M + k) * 2 + 0] = aki * gx;
                     dcen[((size_t)i * M + k) * 2 + 1] = aki * gy;
                 }
+                if (translate) {
+                    /* the moved h: d/d delta_i = f sum_u G(u) d(T h)(u)/d s (conv and ey as scratch) */
+                    const double sx = f * params[od + 2 * (size_t)i], sy = f * params[od + 2 * (size_t)i + 1];
+                    translate_dshift(F, sx, sy, params, conv, ey);
+                    double tx = 0.0, ty = 0.0;
+                    for (size_t u = 0; u < n; ++u) {
+                        tx += G[u] * conv[u];
+                        ty += G[u] * ey[u];
+                    }
+                    dshift[2 * (size_t)i + 0] = f * tx;
+                    dshift[2 * (size_t)i + 1] = f * ty;
+                }
             }
         }
         free(fimg); free(conv); free(model); free(e); free(ey);
     }
-    if (err) { free(chi); free(gfine); free(dcen); return ORC_ERR_OOM; }
+    if (err) { free(chi); free(gfine); free(dcen); free(dshift); return ORC_ERR_OOM; }
     if (grad) {
         /* fine centre = u0 + f (c_k + delta_i): both chain factors are f */
         for (int i = 0; i < E; ++i)
@@ -486,15 +569,29 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
                     grad[oc + 2 * k + ax] += v;
                     grad[od + 2 * i + ax] += v;
                 }
+        if (translate)
+            for (int i = 0; i < E; ++i)
+                for (int ax = 0; ax < 2; ++ax) grad[od + 2 * i + ax] += dshift[2 * i + ax];
     }
-    free(dcen);
+    free(dcen); free(dshift);
     double chi2 = 0.0;
     for (int i = 0; i < E; ++i) chi2 += chi[i];
     if (chi2_epoch) memcpy(chi2_epoch, chi, sizeof(double) * E);
     double prior = 0.0;
     double *gprior = grad ? malloc(sizeof(double) * n) : NULL;
     int rc = orc_starlet_prior(F, J, lam, W, params + oh, &prior, gprior);
-    if (grad && rc == ORC_OK) {
+    if (grad && rc == ORC_OK && translate) {
+        /* d/dh = sum_i T_i^T G_i (epochs in order), plus the prior's part */
+        double *tg = malloc(sizeof(double) * n);
+        if (!tg) rc = ORC_ERR_OOM;
+        for (size_t u = 0; tg && u < n; ++u) grad[oh + u] = gprior[u];
+        for (int i = 0; tg && i < E; ++i) {
+            orc_translate_adjoint(F, f * params[od + 2 * (size_t)i], f * params[od + 2 * (size_t)i + 1],
+                                  gfine + (size_t)i * n, tg);
+            for (size_t u = 0; u < n; ++u) grad[oh + u] += tg[u];
+        }
+        free(tg);
+    } else if (grad && rc == ORC_OK) {
         for (size_t u = 0; u < n; ++u) {
             double acc = gprior[u];
             for (int i = 0; i < E; ++i) acc += gfine[(size_t)i * n + u];
@@ -505,6 +602,20 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
     parts[1] = prior;
     free(gprior); free(chi); free(gfine);
     return rc;
+}
+
+int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d, const double *sigma,
+                         const double *s, const double *W, const double *params, double *parts, double *grad,
+                         double *chi2_epoch, int nthreads) {
+    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 0);
+}
+
+/* The same with the extended channel moved by each epoch's shift: f_i = T_{f delta_i} h + P_i
+ * (orc_translate); the gradient of delta_i then also has the moved h's part. */
+int orc_deconv_loss_grad_shifted(int E, int N, int f, int K, int M, int J, double lam, const double *d,
+                                 const double *sigma, const double *s, const double *W, const double *params,
+                                 double *parts, double *grad, double *chi2_epoch, int nthreads) {
+    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 1);
 }
 
 /* Point-source prior, the third term of Eq. 11 (sec. 2.2):
