@@ -186,6 +186,17 @@ sr_status sr_set_weights(sr_problem *p, const float *W);
  * form (SR_CONV_PLAIN) evaluates lambda_pts = 0 only (SR_ERR_UNSUPPORTED at its next evaluation). */
 sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts);
 
+/* Move the extended channel with each epoch's shift (sec. 5, the frame shifts of the data set):
+ * when enabled, epoch i sees h translated by f * delta_i fine pixels, delta_i the epoch's shift in
+ * the packed parameters, by bilinear interpolation with zero outside the fine grid (the paper does
+ * not fix the interpolant; this is the reading), and the gradient gains the shift derivative of
+ * that term.  Off (0) by default: the paper's Eq. 8 applies the shift to the point sources only.
+ * DECONV only (SR_ERR_STATE otherwise); SR_ERR_UNSUPPORTED with conv_mode FFT or PLAIN; under AUTO
+ * the problem is evaluated in the direct form while enabled.  A change drops the problem's plan
+ * and its optimiser state (synchronises the stream).  A batch created before a member's change
+ * returns SR_ERR_STATE until it is re-created. */
+sr_status sr_set_translate_h(sr_problem *p, int enable);
+
 /* lambda_pts from a model, by the ratio of App. C:
  *   lambda (|| W o Phi^T fbar ||_1 - || W o Phi^T h ||_1) / sum_k <a_k> || W o Phi^T r_k ||_1,
  * fbar = (1/E) sum_i (h + sum_k a_ki r_k(c_k + delta_i)) the mean of the epochs' fine images,

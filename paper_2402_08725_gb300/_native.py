@@ -96,6 +96,7 @@ PROTOTYPES = {
     "sr_batch_profile_read": ([c_void_p, ctypes.POINTER(c_int), P_double, P_double, P_double], c_int),
     "sr_measure_fp32_peak": ([P_double], c_int),
     "sr_set_lambda_pts": ([c_void_p, c_double], c_int),
+    "sr_set_translate_h": ([c_void_p, c_int], c_int),
     "sr_psf_model": ([c_void_p, c_void_p, c_void_p], c_int),
     "sr_batch_set_data": ([c_void_p, c_void_p, c_int], c_int),
     "sr_batch_set_noise": ([c_void_p, c_void_p, c_int], c_int),

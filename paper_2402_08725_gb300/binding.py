@@ -124,6 +124,11 @@ class Problem:
         """Strength of the point-source prior (Eq. 11, third term); sr_set_lambda_pts."""
         nat.check(self.lib.sr_set_lambda_pts(self.handle, float(lambda_pts)), "sr_set_lambda_pts")
 
+    def set_translate_h(self, enable: bool = True):
+        """Move the extended channel with each epoch's shift (sec. 5; bilinear, zero outside);
+        sr_set_translate_h.  Direct form only; drops the problem's plan and optimiser state."""
+        nat.check(self.lib.sr_set_translate_h(self.handle, 1 if enable else 0), "sr_set_translate_h")
+
     def estimate_lambda_pts(self, params: torch.Tensor) -> float:
         """lambda_pts from the model `params` by the ratio of App. C; sr_estimate_lambda_pts."""
         out = ctypes.c_double()

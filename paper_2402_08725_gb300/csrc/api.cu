@@ -182,6 +182,9 @@ struct Plan {
     // fields on the global-memory transforms: their table index and buffers
     std::vector<int> big_fields;
     std::vector<BigBuffers> big_buf;
+    // fields whose channel moves with the epoch shifts: their shift gradients (2 per epoch)
+    float *hs = nullptr;
+    int hs_Emax = 0;
     // point-source prior (Eq. 11, third term): shadow entries of the fields that have it
     int n_sh = 0, sh_Fmax = 0, sh_Jmax = 0, sh_Mmax = 0, n_sh_chunks = 0;
     bool sh_any_unbanded = false;
@@ -229,6 +232,8 @@ struct sr_problem {
     // spectra in the transposed layout [E][f^2][L/2+1][L], and their set-up scratch
     bool fft_big = false;
     float2 *big_zb = nullptr, *big_zt = nullptr;
+    // the extended channel moved with each epoch's shift (sr_set_translate_h; direct form only)
+    bool translate_h = false;
     int fft_L = 0;
     float2 *fft_tw = nullptr, *khat = nullptr;
     int *d_flag = nullptr;
@@ -250,6 +255,7 @@ struct sr_batch {
     cudaStream_t stream = nullptr;
     std::vector<sr_problem *> probs;
     std::vector<char> pts_enabled;  // each problem's point-source prior state when the plan was built
+    std::vector<char> translate;    // each problem's moved-channel state when the plan was built
     // batched input set-up (sr_batch_set_*), built at its first use
     DevArena bio_arena;
     BioEntry *bio_tab = nullptr;
@@ -369,6 +375,8 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
     fd.fft_L = p->fft_L;
     fd.fft_tw = p->fft_tw;
     fd.fft_khat = p->khat;
+    fd.translate = p->translate_h ? 1 : 0;
+    fd.hs_off = 0;
 }
 
 // Epochs per work item of the frequency-domain form (one accumulator per item).
@@ -465,6 +473,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     std::vector<FieldDev> sh;
     std::vector<ChunkItem> sh_chunks;
     long long pbar_len = 0, l1pts = 0, ptsslot = 0;
+    long long hs_len = 0;
     // epochs per work item of the transform form: by default as many as keep at least two items per
     // SM (even, 2 .. kFftChunk), so that a single long field spreads over the GPU
     int chunk = opt.chunk;
@@ -553,6 +562,11 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             smem_fx = std::max(smem_fx, fft_pair_smem_bytes(L, fd.M, fd.f, G));
         } else if (pl->kind == SR_DECONV && !plain) {
             gbuf += (long long)fd.E * fd.f * fd.f * fd.N * fd.N;
+            if (fd.translate) {
+                fd.hs_off = hs_len;
+                hs_len += 2LL * fd.E;
+                pl->hs_Emax = std::max(pl->hs_Emax, fd.E);
+            }
             const int nph = fd.f * fd.f;
             std::vector<TileItem> tiles;
             for (int y0 = 0; y0 < fd.N; y0 += 64)
@@ -583,6 +597,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
                 for (int k = 0; k < fd.M; ++k) ps.push_back(make_int4(i, e, k, 0));
             psslot += (long long)fd.E * fd.M;
         } else if (pl->kind == SR_DECONV) {
+            if (fd.translate) return fail(SR_ERR_UNSUPPORTED, "the plain form does not move the extended channel");
             // plain form: per-epoch partials of the residual kernel, one slot per 256 data px
             const int nb = (fd.N * fd.N + 255) / 256;
             fd.n_tiles = nb;
@@ -658,6 +673,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
     if ((st = A.alloc(&pl->ps_du, 2 * n_ps_slots)) != SR_OK) return st;
     if ((st = A.alloc(&pl->l1_part, (size_t)l1slot)) != SR_OK) return st;
     if ((st = A.alloc(&pl->losses, (size_t)n)) != SR_OK) return st;
+    if (hs_len > 0 && (st = A.alloc(&pl->hs, (size_t)hs_len)) != SR_OK) return st;
     if ((st = A.alloc(&pl->total, 1)) != SR_OK) return st;
     if ((st = A.alloc(&pl->d_group, poff)) != SR_OK) return st;
     if ((st = A.alloc(&pl->d_t, 1)) != SR_OK) return st;
@@ -807,8 +823,12 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
     n += launch_starlet(pl->d_fields, pl->n_fields, pl->Fmax, pl->any_unbanded, pl->d_chunks, pl->n_chunks, pl->Jmax,
                         params, pl->l1_part, st);
     if (pl->n_items > 0) {
-        launch_hgrad(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->gbuf, grad, st);
+        launch_hgrad(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->gbuf, grad, params, st);
         ++n;
+        if (pl->hs) {
+            launch_hshift_grad(pl->d_fields, pl->n_fields, pl->hs_Emax, params, pl->gbuf, pl->hs, st);
+            ++n;
+        }
     }
     if (pl->n_fft_items > 0) {
         launch_fft_hgrad_pair(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_pairs, pl->smem_fft,
@@ -822,7 +842,7 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
                               pl->d_sh_chunks, pl->n_sh_chunks, pl->sh_Jmax, params, pl->abar, pl->pbar, pl->l1_pts,
                               pl->pts_g, st);
     launch_finalize(pl->d_fields, pl->n_fields, pl->chi_part, pl->se_part, pl->l1_part, pl->ps_da, pl->ps_du, grad,
-                    pl->losses, pl->total, st, pl->n_sh > 0 ? pl->d_sh : nullptr, pl->l1_pts, pl->pts_g);
+                    pl->losses, pl->total, st, pl->n_sh > 0 ? pl->d_sh : nullptr, pl->l1_pts, pl->pts_g, pl->hs);
     n += 2;
     return n;
 }
@@ -862,6 +882,7 @@ static sr_status time_form(sr_problem *p, int mode, float *ms) {
 }
 
 static bool field_uses_fft(sr_problem *p, const PlanOptions &opt) {
+    if (p->translate_h) return false;  // the moved channel is evaluated in the direct form only
     if (opt.mode_override >= 0) return opt.mode_override == 1 && p->fft_ok;
     if (!p->fft_ok) return false;
     if (p->desc.conv_mode == SR_CONV_FFT) return true;
@@ -1180,6 +1201,22 @@ sr_status sr_set_weights(sr_problem *p, const float *W) {
     return SR_OK;
 }
 
+sr_status sr_set_translate_h(sr_problem *p, int enable) {
+    if (!p) return fail(SR_ERR_ARG, "problem is NULL");
+    if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "the moved channel belongs to deconvolution problems");
+    const bool on = enable != 0;
+    if (on && (p->desc.conv_mode == SR_CONV_FFT || p->desc.conv_mode == SR_CONV_PLAIN))
+        return fail(SR_ERR_UNSUPPORTED, "moving the extended channel needs conv_mode AUTO or DIRECT");
+    if (on == p->translate_h) return SR_OK;
+    p->translate_h = on;
+    if (p->plan) {  // the next evaluation builds a plan in the direct form (the optimiser state restarts)
+        SR_CUDA(cudaStreamSynchronize(p->stream));
+        delete p->plan;
+        p->plan = nullptr;
+    }
+    return SR_OK;
+}
+
 sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts) {
     if (!p) return fail(SR_ERR_ARG, "problem is NULL");
     if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "lambda_pts belongs to deconvolution problems");
@@ -1413,7 +1450,10 @@ sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream,
     if (!b) return fail(SR_ERR_OOM, "host allocation failed");
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     b->probs.assign(problems, problems + n);
-    for (int i = 0; i < n; ++i) b->pts_enabled.push_back(problems[i]->pts_enabled ? 1 : 0);
+    for (int i = 0; i < n; ++i) {
+        b->pts_enabled.push_back(problems[i]->pts_enabled ? 1 : 0);
+        b->translate.push_back(problems[i]->translate_h ? 1 : 0);
+    }
     b->plan = new (std::nothrow) Plan();
     if (!b->plan) {
         delete b;
@@ -1572,9 +1612,12 @@ sr_status sr_batch_param_offset(const sr_batch *b, int i, size_t *offset) {
 // A problem whose point-source prior was switched on after the batch was built is not in the
 // batch's plan: the batch must be re-created.
 static sr_status batch_pts_check(const sr_batch *b) {
-    for (size_t i = 0; i < b->probs.size(); ++i)
+    for (size_t i = 0; i < b->probs.size(); ++i) {
         if ((b->probs[i]->pts_enabled ? 1 : 0) != b->pts_enabled[i])
             return fail(SR_ERR_STATE, "field %zu got a non-zero lambda_pts after sr_batch_create: re-create the batch", i);
+        if ((b->probs[i]->translate_h ? 1 : 0) != b->translate[i])
+            return fail(SR_ERR_STATE, "field %zu changed sr_set_translate_h after sr_batch_create: re-create the batch", i);
+    }
     return SR_OK;
 }
 

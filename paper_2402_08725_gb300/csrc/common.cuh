@@ -63,7 +63,19 @@ struct FieldDev {
     // point-source prior (Eq. 11, third term): 1 + index of the partner entry (a field's shadow
     // entry in the plan's point-source table, or a shadow entry's field), 0 for none
     int pts;
+    // the extended channel moved with each epoch's shift (f_i = T_{f delta_i} h + P_i, bilinear,
+    // zero outside; direct form only) and the offset of its shift gradients (2 per epoch)
+    int translate;
+    long long hs_off;
 };
+
+// Whole and fractional parts of the bilinear read of a channel moved by s fine pixels: output u
+// reads u + n (weight 1 - t) and u + n + 1 (weight t), n = floor(-s), t = -s - n in [0, 1).
+__device__ __forceinline__ void shift_split(float s, int *n, float *t) {
+    const float fl = floorf(-s);
+    *n = (int)fl;
+    *t = -s - fl;
+}
 
 // One output tile of one epoch: rows [y0, y0+h), cols [x0, x0+w) of the data
 // grid.  pg = number of thread groups working on different phases at once.

@@ -126,6 +126,13 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
         const float *dpar = cpar + 2 * M + 2 * t.epoch;
         const float gam = cpar[2 * M + 2 * E + t.epoch];
         const int my0 = t.y0 - thi, mx0 = t.x0 - thi;  // data-grid origin of the staged tiles
+        // the moved channel (translate): output fine pixel u reads h bilinearly at u + n + (0 | 1)
+        int snx = 0, sny = 0;
+        float stx = 0.f, sty = 0.f;
+        if (fd.translate) {
+            shift_split((float)f * dpar[0], &snx, &stx);
+            shift_split((float)f * dpar[1], &sny, &sty);
+        }
 
         // point sources of this epoch: fine centre, amplitude and window origin (Eq. 9)
         if (tid < M) {
@@ -165,8 +172,25 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                     const int mx = mx0 + j;
                     float v = 0.f;
                     if (mx >= 0 && mx < N) {
-                        v = __ldg(src + f * mx);
                         const int ux = f * mx + phx;
+                        if (fd.translate) {
+                            // bilinear read at u - s, zero outside the grid
+                            v = 0.f;
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) {
+                                const int yy = uy + sny + b;
+                                if (yy < 0 || yy >= F) continue;
+                                const float wy = b ? sty : 1.f - sty;
+#pragma unroll
+                                for (int a = 0; a < 2; ++a) {
+                                    const int xx = ux + snx + a;
+                                    if (xx < 0 || xx >= F) continue;
+                                    v += wy * (a ? stx : 1.f - stx) * __ldg(hpar + (long long)yy * F + xx);
+                                }
+                            }
+                        } else {
+                            v = __ldg(src + f * mx);
+                        }
                         for (unsigned long long m = rowmask; m; m &= m - 1) {
                             const int k = __ffsll((long long)m) - 1;
                             if ((unsigned)(ux - s_win[k].x) < (unsigned)kWin)
@@ -358,7 +382,7 @@ __global__ void psgrad_kernel(const FieldDev *__restrict__ fields, const int4 *_
 
 // dL/dh[u] = T0[u] + sum_i G_i[u]: one thread per polyphase index q = phi*N*N + m.
 __global__ void hgrad_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__restrict__ chunks, int n_chunks,
-                             const float *__restrict__ gbuf, float *__restrict__ grad) {
+                             const float *__restrict__ gbuf, float *__restrict__ grad, const float *__restrict__ params) {
     const int c = blockIdx.x;
     if (c >= n_chunks) return;
     const ChunkItem ch = chunks[c];
@@ -368,6 +392,39 @@ __global__ void hgrad_kernel(const FieldDev *__restrict__ fields, const ChunkIte
     const int f = fd.f, N = fd.N, F = fd.F;
     if (q >= F * F) return;
     const long long plane = (long long)f * f * N * N;
+    if (fd.translate) {
+        // dL/dh = sum_i T_i^T G_i: pixel v gathers G_i(v - n - (0 | 1)) with the read's weights
+        const int ph = q / (N * N), m = q - ph * N * N;
+        const int vy = f * (m / N) + ph / f, vx = f * (m % N) + ph % f;
+        const float *cpar = params + fd.param_off + (long long)F * F + (long long)fd.E * fd.M + 2 * fd.M;
+        const float *Gb = gbuf + fd.gbuf_off;
+        float acc = 0.f;
+        for (int i = 0; i < fd.E; ++i) {
+            int nx, ny;
+            float tx, ty;
+            shift_split((float)f * cpar[2 * i], &nx, &tx);
+            shift_split((float)f * cpar[2 * i + 1], &ny, &ty);
+            float gi = 0.f;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int uy = vy - ny - b;
+                if (uy < 0 || uy >= F) continue;
+                const float wy = b ? ty : 1.f - ty;
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int ux = vx - nx - a;
+                    if (ux < 0 || ux >= F) continue;
+                    const int uph = (uy % f) * f + ux % f;
+                    gi += wy * (a ? tx : 1.f - tx) *
+                          Gb[(long long)i * plane + (long long)uph * N * N + (uy / f) * N + ux / f];
+                }
+            }
+            acc += gi;
+        }
+        const int u = vy * F + vx;
+        grad[fd.param_off + u] = acc + fd.starlet[(long long)fd.J * F * F + u];
+        return;
+    }
     const float *G = gbuf + fd.gbuf_off + q;
     // four interleaved FP32 partial sums over the epochs, combined in a fixed order
     // (the FP64 pipe of this GPU is far narrower than the FP32 one)
@@ -387,13 +444,59 @@ __global__ void hgrad_kernel(const FieldDev *__restrict__ fields, const ChunkIte
     grad[fd.param_off + u] = ((s0 + s1) + (s2 + s3)) + T0[u];
 }
 
+// The moved channel's part of dL/d delta_i = f sum_u G_i(u) d(T h)(u)/d s, with d(T h)/d s_x =
+// -[(1 - t_y)(h(y0, x0 + 1) - h(y0, x0)) + t_y (h(y0 + 1, x0 + 1) - h(y0 + 1, x0))] (and the same with
+// the axes swapped), (x0, y0) = u + n.  Block (epoch, field); compensated FP32 sums in fixed order.
+__global__ void __launch_bounds__(256)
+hshift_grad_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
+                   const float *__restrict__ gbuf, float *__restrict__ hs) {
+    __shared__ float4 s_red[8];
+    const FieldDev &fd = fields[blockIdx.y];
+    const int i = blockIdx.x;
+    if (!fd.translate || fd.mode != 0 || i >= fd.E) return;
+    const int f = fd.f, N = fd.N, F = fd.F;
+    const float *h = params + fd.param_off;
+    const float *cpar = h + (long long)F * F + (long long)fd.E * fd.M + 2 * fd.M;
+    int nx, ny;
+    float tx, ty;
+    shift_split((float)f * cpar[2 * i], &nx, &tx);
+    shift_split((float)f * cpar[2 * i + 1], &ny, &ty);
+    const float *Gi = gbuf + fd.gbuf_off + (long long)i * f * f * N * N;
+    auto hv = [&](int y, int x) { return (y < 0 || y >= F || x < 0 || x >= F) ? 0.f : h[(long long)y * F + x]; };
+    FSum sx = fsum_zero(), sy = fsum_zero();
+    for (int q = threadIdx.x; q < F * F; q += blockDim.x) {
+        const int ph = q / (N * N), m = q - ph * N * N;
+        const int uy = f * (m / N) + ph / f, ux = f * (m % N) + ph % f;
+        const float G = Gi[q];
+        const int x0 = ux + nx, y0 = uy + ny;
+        const float h00 = hv(y0, x0), h01 = hv(y0, x0 + 1), h10 = hv(y0 + 1, x0), h11 = hv(y0 + 1, x0 + 1);
+        const float dx = -((1.f - ty) * (h01 - h00) + ty * (h11 - h10));
+        const float dy = -((1.f - tx) * (h10 - h00) + tx * (h11 - h01));
+        sx = fsum_add(sx, G * dx);
+        sy = fsum_add(sy, G * dy);
+    }
+    sx = fsum_warp(sx);
+    sy = fsum_warp(sy);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        FSum ax = fsum_zero(), ay = fsum_zero();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ax = fsum_add(ax, FSum{s_red[w].x, s_red[w].y});
+            ay = fsum_add(ay, FSum{s_red[w].z, s_red[w].w});
+        }
+        hs[fd.hs_off + 2 * i] = (float)((double)f * fsum_value(ax));
+        hs[fd.hs_off + 2 * i + 1] = (float)((double)f * fsum_value(ay));
+    }
+}
+
 // Per-field assembly of the loss and the small parameter blocks, in fixed order.
 __global__ void __launch_bounds__(kThreads)
 finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ chi_part,
                 const double *__restrict__ se_part, const double *__restrict__ l1_part,
                 const float *__restrict__ ps_da, const float *__restrict__ ps_du, float *__restrict__ grad,
                 double *__restrict__ losses, const FieldDev *__restrict__ pts_fields,
-                const double *__restrict__ l1_pts, const float *__restrict__ pts_g) {
+                const double *__restrict__ l1_pts, const float *__restrict__ pts_g, const float *__restrict__ hs) {
     __shared__ double s_red[2][kThreads / 32];
     const FieldDev &fd = fields[blockIdx.x];
     const int E = fd.E, M = fd.M, F = fd.F, f = fd.f;
@@ -423,7 +526,7 @@ finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ 
         const int i = s >> 1, ax = s & 1;
         double acc = 0.0;
         for (int k = 0; k < M; ++k) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
-        gd[s] = (float)(f * acc);
+        gd[s] = (float)(f * acc) + ((hs && fd.translate) ? hs[fd.hs_off + s] : 0.f);
     }
     float *gg = gd + 2 * E;
     for (int i = threadIdx.x; i < E; i += blockDim.x) {
@@ -503,16 +606,21 @@ void launch_psgrad(const FieldDev *fields, const int4 *ps_items, int n, const fl
 }
 
 void launch_hgrad(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, const float *gbuf, float *grad,
-                  cudaStream_t st) {
-    hgrad_kernel<<<n_chunks, 256, 0, st>>>(fields, chunks, n_chunks, gbuf, grad);
+                  const float *params, cudaStream_t st) {
+    hgrad_kernel<<<n_chunks, 256, 0, st>>>(fields, chunks, n_chunks, gbuf, grad, params);
+}
+
+void launch_hshift_grad(const FieldDev *fields, int n_fields, int E_max, const float *params, const float *gbuf,
+                        float *hs, cudaStream_t st) {
+    hshift_grad_kernel<<<dim3(E_max, n_fields), 256, 0, st>>>(fields, params, gbuf, hs);
 }
 
 void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_part, const double *se_part,
                      const double *l1_part, const float *ps_da, const float *ps_du, float *grad, double *losses,
                      double *total, cudaStream_t st, const FieldDev *pts_fields, const double *l1_pts,
-                     const float *pts_g) {
+                     const float *pts_g, const float *hs) {
     finalize_kernel<<<n_fields, kThreads, 0, st>>>(fields, chi_part, se_part, l1_part, ps_da, ps_du, grad, losses,
-                                                   pts_fields, l1_pts, pts_g);
+                                                   pts_fields, l1_pts, pts_g, hs);
     total_kernel<<<1, 32, 0, st>>>(losses, n_fields, total);
 }
 

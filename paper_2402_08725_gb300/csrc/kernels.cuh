@@ -25,13 +25,16 @@ void launch_adj(const FieldDev *fields, const TileItem *items, int n_items, int 
 void launch_psgrad(const FieldDev *fields, const int4 *ps_items, int n, const float *params, const float *gbuf,
                    float *ps_da, float *ps_du, cudaStream_t st);
 void launch_hgrad(const FieldDev *fields, const ChunkItem *chunks, int n_chunks, const float *gbuf, float *grad,
-                  cudaStream_t st);
+                  const float *params, cudaStream_t st);
+// the moved extended channel's part of dL/d delta_i (fields with translate set; grid E_max x fields)
+void launch_hshift_grad(const FieldDev *fields, int n_fields, int E_max, const float *params, const float *gbuf,
+                        float *hs, cudaStream_t st);
 // pts_fields / l1_pts / pts_g: the point-source prior's table and outputs (launch_pts_prior), or
 // nullptr when no field of the table has the term
 void launch_finalize(const FieldDev *fields, int n_fields, const double *chi_part, const double *se_part,
                      const double *l1_part, const float *ps_da, const float *ps_du, float *grad, double *losses,
                      double *total, cudaStream_t st, const FieldDev *pts_fields = nullptr,
-                     const double *l1_pts = nullptr, const float *pts_g = nullptr);
+                     const double *l1_pts = nullptr, const float *pts_g = nullptr, const float *hs = nullptr);
 
 // --- frequency-domain form (fft_pair.cu): in-place transforms of real image pairs ---
 bool fft_pair_size(int L);
