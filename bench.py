@@ -487,8 +487,12 @@ def measure_psf_fit(stream, steps=300):
     and centres 0.1 px off, by AdaBelief (300 steps) and by L-BFGS-B (100 iterations) with the
     workload's synthetic weights, and by AdaBelief with the weights of the noise propagation of
     sec. 2.3 (sr_noise_weights, 1000 realisations, the 2-px Gaussian as the operator on b).  The stars
-    of config 2 are drawn from the Moffat profile alone (the grid texture b of its parameters is not
-    in the data), so the reference PSF is that Moffat; both PSFs are normalised to unit sum."""
+    of config 2 are drawn on the data grid from the Moffat profile of the effective width times a
+    faint copy of a random texture, not through the model, so no narrow PSF reproduces them exactly;
+    the reference PSF is the Moffat that drew them, both PSFs normalised to unit sum.  Beside each
+    MAE_PSF the fitted PSF's negative mass (the sum of its negative pixels at unit sum) is given: for
+    two non-negative unit-sum PSFs the L1 difference cannot exceed 2, so an MAE above 2 is carried by
+    negative lobes of the pixel grid b."""
     import torch
     from paper_2402_08725_gb300 import metrics as mt
     from paper_2402_08725_gb300 import synthetic as syn
@@ -540,7 +544,9 @@ def measure_psf_fit(stream, steps=300):
             stream.synchronize()
             info["wall_s"] = round(time.perf_counter() - t0, 3)
             fit = P.cpu().numpy().astype(np.float64)
-            info["mae_psf"] = round(mt.mae_psf(s_ref, unit(prob.psf_model(P))), 5)
+            s_fit = unit(prob.psf_model(P))
+            info["mae_psf"] = round(mt.mae_psf(s_ref, s_fit), 5)
+            info["negative_mass"] = round(float(-np.sum(np.minimum(s_fit, 0.0))), 5)
             info["alpha"], info["beta"] = round(fit[F * F], 4), round(fit[F * F + 1], 4)
             info["P_astro_px"] = round(mt.p_astro(truth[F * F + 2 + S:].reshape(S, 2),
                                                   fit[F * F + 2 + S:].reshape(S, 2)), 5)

@@ -416,12 +416,15 @@ def config2(seed=None, S=16, N=64) -> PsfProblem:
     envelope = moffat_stamp(F, fwhm, beta)      # unit-sum Moffat shape on the fine grid
     b = 0.05 * envelope * gaussian_random_field(rng, F, 3.0)
     # stars drawn at data resolution: Moffat of the effective width (narrow PSF
-    # widened by the 2-px Gaussian), plus a faint copy of the grid texture
+    # widened by the 2-px Gaussian) times a faint copy of the grid texture (the same
+    # 5 % random field of correlation length 1.5 data px on every stamp)
     fwhm_eff = np.sqrt(fwhm ** 2 + 4.0) / f
     pos = (N - 1) / 2.0 + c
+    texture = (1.0 + 0.05 * gaussian_random_field(rng, N, 1.5)).astype(np.float32)
     model = _data_stamp_sources(N, S, pos[:, None, :], a[:, None], np.full(S, fwhm_eff), np.full(S, beta))
+    model = model * texture[None]
     d, sigma = _noise(rng, model, np.full(S, 10.0))
-    W = starlet_weights(J, sigma, f, S) * 1e-3
+    W = starlet_weights(J, sigma, f, S)
     params = pack_psf(b, alpha, beta, a, c)
     return PsfProblem(S, N, f, J, 2.0, d, sigma, W, params, meta={"alpha": alpha, "beta": beta})
 
