@@ -17,6 +17,7 @@ Functions and the passages they follow:
   starlet_prior                   lambda ||W o Phi^T h||_1 and its subgradient (Eq. 6, Eq. 11)
   deconv_model / deconv_loss_grad the two-channel multi-epoch model and loss (Eq. 9-11)
   translate / _adjoint            the extended channel moved with an epoch's shift (sec. 5; bilinear)
+  warp / _adjoint                 an epoch's frame rotated about the grid centre and shifted (sec. 5)
   moffat                          the analytic part of the narrow PSF (Eq. 2)
   psf_model / psf_loss_grad       PSF reconstruction (Eq. 2-4, Eq. 7)
   optim_step                      AdaBelief / Adam update used by the optimiser (sec. 2.4)
@@ -85,6 +86,10 @@ def _load():
             "orc_deconv_loss_grad": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
             "orc_deconv_loss_grad_shifted": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
             "orc_translate": ([i, d, d, _dp, _dp], i),
+            "orc_warp": ([i, d, d, d, _dp, _dp], i),
+            "orc_warp_adjoint": ([i, d, d, d, _dp, _dp], i),
+            "orc_deconv_model_ex": ([i, i, i, i, i, _dp, _dp, _dp, i, _dp], i),
+            "orc_deconv_loss_grad_ex": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i, i, _dp], i),
             "orc_translate_adjoint": ([i, d, d, _dp, _dp], i),
             "orc_moffat": ([i, d, d, _dp, _dp, _dp], i),
             "orc_psf_param_count": ([i, i, i], sz),
@@ -159,6 +164,25 @@ def translate(h, sx, sy):
     return out
 
 
+def warp(h, theta, sx=0.0, sy=0.0):
+    """h seen in a frame rotated by theta (radians) about the grid centre and shifted by (sx, sy)
+    fine pixels: out(u) = h at u0 + R^T (u - u0 - s), bilinear, zero outside (orc_warp)."""
+    h = _f64(h)
+    F = h.shape[0]
+    out = np.empty_like(h)
+    _check(_load().orc_warp(F, float(theta), float(sx), float(sy), _ptr(h), _ptr(out)), "warp")
+    return out
+
+
+def warp_adjoint(g, theta, sx=0.0, sy=0.0):
+    """Transpose of warp."""
+    g = _f64(g)
+    F = g.shape[0]
+    out = np.empty_like(g)
+    _check(_load().orc_warp_adjoint(F, float(theta), float(sx), float(sy), _ptr(g), _ptr(out)), "warp_adjoint")
+    return out
+
+
 def translate_adjoint(g, sx, sy):
     g = _f64(g)
     F = g.shape[0]
@@ -225,16 +249,26 @@ def deconv_param_count(E: int, N: int, f: int, M: int) -> int:
     return int(_load().orc_deconv_param_count(E, N, f, M))
 
 
-def deconv_model(E, N, f, K, M, s, params):
+def deconv_model(E, N, f, K, M, s, params, shifted=False, theta=None):
+    """Model of every epoch; shifted / theta as in deconv_loss_grad."""
     s, params = _f64(s), _f64(params)
     out = np.empty((E, N, N))
-    _check(_load().orc_deconv_model(E, N, f, K, M, _ptr(s), _ptr(params), _ptr(out)), "deconv_model")
+    if not shifted and theta is None:
+        _check(_load().orc_deconv_model(E, N, f, K, M, _ptr(s), _ptr(params), _ptr(out)), "deconv_model")
+        return out
+    th = None if theta is None else _f64(theta)
+    if th is not None and th.size != E:
+        raise ValueError(f"theta has {th.size} values, expected {E}")
+    _check(_load().orc_deconv_model_ex(E, N, f, K, M, _ptr(s), _ptr(params), _ptr(out), int(bool(shifted)),
+                                       _ptr(th) if th is not None else None), "deconv_model")
     return out
 
 
-def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, nthreads=0, shifted=False):
+def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, nthreads=0, shifted=False,
+                     theta=None):
     """Return (loss, parts[chi2, prior], grad or None, chi2 per epoch).  shifted=True moves the
-    extended channel h by each epoch's shift f * delta_i (translate) before the convolution."""
+    extended channel h by each epoch's shift f * delta_i (translate) before the convolution;
+    theta (E angles in radians) rotates each epoch's frame about the grid centre (warp)."""
     d, sigma, s, W, params = _f64(d), _f64(sigma), _f64(s), _f64(W), _f64(params)
     n = deconv_param_count(E, N, f, M)
     if params.size != n:
@@ -242,9 +276,17 @@ def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, n
     parts = np.zeros(2)
     g = np.empty(n) if grad else None
     chi = np.empty(E)
-    fn = _load().orc_deconv_loss_grad_shifted if shifted else _load().orc_deconv_loss_grad
-    rc = fn(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W), _ptr(params), _ptr(parts), _ptr(g),
-            _ptr(chi), int(nthreads))
+    if theta is not None:
+        th = _f64(theta)
+        if th.size != E:
+            raise ValueError(f"theta has {th.size} values, expected {E}")
+        rc = _load().orc_deconv_loss_grad_ex(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W),
+                                             _ptr(params), _ptr(parts), _ptr(g), _ptr(chi), int(nthreads),
+                                             int(bool(shifted)), _ptr(th))
+    else:
+        fn = _load().orc_deconv_loss_grad_shifted if shifted else _load().orc_deconv_loss_grad
+        rc = fn(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W), _ptr(params), _ptr(parts),
+                _ptr(g), _ptr(chi), int(nthreads))
     _check(rc, "deconv_loss_grad")
     return float(parts.sum()), parts, g, chi
 

@@ -415,19 +415,102 @@ static void translate_dshift(int F, double sx, double sy, const double *h, doubl
         }
 }
 
+/* Rotation of an epoch's frame (sec. 5 names rotations between frames; no equation in the paper,
+ * so the reading here): the reference-frame point q lands at u = u0 + R (q - u0) + s in the epoch's
+ * fine grid, R = [[cos t, -sin t], [sin t, cos t]] acting on (x, y), u0 = (F - 1)/2 the grid centre
+ * and s the shift (f delta_i when the extended channel moves with the shifts, else 0).  The epoch
+ * sees out(u) = h at q(u) = u0 + R^T (u - u0 - s), bilinear between the four fine pixels around q
+ * and zero outside the grid; its point sources sit at u0 + f (R c_k + delta_i). */
+static void warp_point(int F, double ct, double st, double sx, double sy, int ux, int uy, double *qx, double *qy) {
+    const double u0 = 0.5 * (F - 1), dx = ux - u0 - sx, dy = uy - u0 - sy;
+    *qx = u0 + ct * dx + st * dy;
+    *qy = u0 - st * dx + ct * dy;
+}
+
+int orc_warp(int F, double theta, double sx, double sy, const double *h, double *out) {
+    if (F <= 0) return ORC_ERR_SHAPE;
+    const double ct = cos(theta), st = sin(theta);
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double qx, qy;
+            warp_point(F, ct, st, sx, sy, ux, uy, &qx, &qy);
+            out[(size_t)uy * F + ux] = bilinear_at(F, h, qx, qy);
+        }
+    return ORC_OK;
+}
+
+/* Transpose of orc_warp: every output pixel scatters its value to the four pixels it read. */
+int orc_warp_adjoint(int F, double theta, double sx, double sy, const double *g, double *out) {
+    if (F <= 0) return ORC_ERR_SHAPE;
+    const double ct = cos(theta), st = sin(theta);
+    memset(out, 0, sizeof(double) * (size_t)F * F);
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double qx, qy;
+            warp_point(F, ct, st, sx, sy, ux, uy, &qx, &qy);
+            const double fx = floor(qx), fy = floor(qy), tx = qx - fx, ty = qy - fy, gv = g[(size_t)uy * F + ux];
+            const int x0 = (int)fx, y0 = (int)fy;
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    const int x = x0 + a, y = y0 + b;
+                    if (x < 0 || x >= F || y < 0 || y >= F) continue;
+                    out[(size_t)y * F + x] += (a ? tx : 1.0 - tx) * (b ? ty : 1.0 - ty) * gv;
+                }
+        }
+    return ORC_OK;
+}
+
+/* d out(u) / d s of orc_warp: q moves by -R^T ds, so d out / d s = -R grad H(q), grad H the
+ * derivative of the interpolant inside its cell. */
+static void warp_dshift(int F, double theta, double sx, double sy, const double *h, double *dx, double *dy) {
+    const double ct = cos(theta), st = sin(theta);
+    for (int uy = 0; uy < F; ++uy)
+        for (int ux = 0; ux < F; ++ux) {
+            double qx, qy;
+            warp_point(F, ct, st, sx, sy, ux, uy, &qx, &qy);
+            const double fx = floor(qx), fy = floor(qy), tx = qx - fx, ty = qy - fy;
+            const int x0 = (int)fx, y0 = (int)fy;
+            double v[2][2];
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    const int x = x0 + a, y = y0 + b;
+                    v[b][a] = (x < 0 || x >= F || y < 0 || y >= F) ? 0.0 : h[(size_t)y * F + x];
+                }
+            const double hx = (1.0 - ty) * (v[0][1] - v[0][0]) + ty * (v[1][1] - v[1][0]);
+            const double hy = (1.0 - tx) * (v[1][0] - v[0][0]) + tx * (v[1][1] - v[0][1]);
+            dx[(size_t)uy * F + ux] = -(ct * hx - st * hy);
+            dy[(size_t)uy * F + ux] = -(st * hx + ct * hy);
+        }
+}
+
+/* Fine centre of point source k in epoch i of a rotated frame: u0 + f (R c_k + delta_i). */
+static void source_centre_rot(int F, int f, const double *c, const double *dl, int k, int i, double theta, double *ux,
+                              double *uy) {
+    const double u0 = 0.5 * (F - 1), ct = cos(theta), st = sin(theta);
+    const double cx = c[2 * k + 0], cy = c[2 * k + 1];
+    *ux = u0 + f * ((ct * cx - st * cy) + dl[2 * i + 0]);
+    *uy = u0 + f * ((st * cx + ct * cy) + dl[2 * i + 1]);
+}
+
 /* Model of epoch i on the data grid: M_i = D S_i (h + sum_k a_ki r_k) + f^2 Gamma_i. */
 static void deconv_model_epoch(int i, int N, int f, int K, int M, const double *s_i, const double *params,
                                size_t oa, size_t oc, size_t od, size_t og, double *fimg, double *conv, double *model,
-                               int translate) {
+                               int translate, const double *theta) {
     int F = f * N;
     size_t n = (size_t)F * F;
-    if (translate) /* h moved by the epoch's shift f * delta_i */
+    if (theta) /* h seen in the epoch's rotated (and, when translating, shifted) frame */
+        orc_warp(F, theta[i], translate ? f * params[od + 2 * (size_t)i] : 0.0,
+                 translate ? f * params[od + 2 * (size_t)i + 1] : 0.0, params, fimg);
+    else if (translate) /* h moved by the epoch's shift f * delta_i */
         orc_translate(F, f * params[od + 2 * (size_t)i], f * params[od + 2 * (size_t)i + 1], params, fimg);
     else
         memcpy(fimg, params, sizeof(double) * n); /* h */
     for (int k = 0; k < M; ++k) {
         double ux, uy;
-        source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
+        if (theta)
+            source_centre_rot(F, f, params + oc, params + od, k, i, theta[i], &ux, &uy);
+        else
+            source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
         orc_add_gaussian(F, params[oa + (size_t)i * M + k], ux, uy, fimg);
     }
     orc_conv_same(F, K, fimg, s_i, conv);
@@ -436,9 +519,8 @@ static void deconv_model_epoch(int i, int N, int f, int K, int M, const double *
     for (int p = 0; p < N * N; ++p) model[p] += bg;
 }
 
-static double inv_var(double sigma) { return isinf(sigma) ? 0.0 : 1.0 / (sigma * sigma); }
-
-int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const double *params, double *model_out) {
+static int deconv_model(int E, int N, int f, int K, int M, const double *s, const double *params, double *model_out,
+                        int translate, const double *theta) {
     if (E <= 0 || N <= 0 || f <= 0 || K <= 0 || M < 0) return ORC_ERR_SHAPE;
     int F = f * N;
     size_t oh, oa, oc, od, og, tot;
@@ -457,11 +539,24 @@ int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const d
 #pragma omp for schedule(static)
             for (int i = 0; i < E; ++i)
                 deconv_model_epoch(i, N, f, K, M, s + (size_t)i * K * K, params, oa, oc, od, og, fimg, conv,
-                                   model_out + (size_t)i * N * N, 0);
+                                   model_out + (size_t)i * N * N, translate, theta);
         }
         free(fimg); free(conv);
     }
     return err ? ORC_ERR_OOM : ORC_OK;
+}
+
+static double inv_var(double sigma) { return isinf(sigma) ? 0.0 : 1.0 / (sigma * sigma); }
+
+int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const double *params, double *model_out) {
+    return deconv_model(E, N, f, K, M, s, params, model_out, 0, NULL);
+}
+
+/* The model with the frame variants: translate moves h by f delta_i, theta (NULL: none) rotates
+ * epoch i's frame by theta[i] radians (warp_point). */
+int orc_deconv_model_ex(int E, int N, int f, int K, int M, const double *s, const double *params, double *model_out,
+                        int translate, const double *theta) {
+    return deconv_model(E, N, f, K, M, s, params, model_out, translate, theta);
 }
 
 /* Loss and gradient of the deconvolution problem.
@@ -471,7 +566,7 @@ int orc_deconv_model(int E, int N, int f, int K, int M, const double *s, const d
  *   chi2_epoch (nullable) receives the chi^2 of each epoch. */
 static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d,
                             const double *sigma, const double *s, const double *W, const double *params, double *parts,
-                            double *grad, double *chi2_epoch, int nthreads, int translate) {
+                            double *grad, double *chi2_epoch, int nthreads, int translate, const double *theta) {
     if (E <= 0 || N <= 0 || f <= 0 || K <= 0 || M < 0) return ORC_ERR_SHAPE;
     int F = f * N;
     if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
@@ -505,7 +600,7 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
 #pragma omp for schedule(dynamic, 1)
             for (int i = 0; i < E; ++i) {
                 const double *s_i = s + (size_t)i * K * K;
-                deconv_model_epoch(i, N, f, K, M, s_i, params, oa, oc, od, og, fimg, conv, model, translate);
+                deconv_model_epoch(i, N, f, K, M, s_i, params, oa, oc, od, og, fimg, conv, model, translate, theta);
                 double c2 = 0.0;
                 for (int p = 0; p < N * N; ++p) {
                     size_t ip = (size_t)i * N * N + p;
@@ -527,7 +622,10 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
                 /* point sources: d/da_ki and d/d(centre) through the Gaussian */
                 for (int k = 0; k < M; ++k) {
                     double ux, uy;
-                    source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
+                    if (theta)
+                        source_centre_rot(F, f, params + oc, params + od, k, i, theta[i], &ux, &uy);
+                    else
+                        source_centre(F, f, params + oc, params + od, k, i, &ux, &uy);
                     double aki = params[oa + (size_t)i * M + k];
                     double ga = 0.0, gx = 0.0, gy = 0.0;
                     for (int vy = 0; vy < F; ++vy)
@@ -546,7 +644,10 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
                 if (translate) {
                     /* the moved h: d/d delta_i = f sum_u G(u) d(T h)(u)/d s (conv and ey as scratch) */
                     const double sx = f * params[od + 2 * (size_t)i], sy = f * params[od + 2 * (size_t)i + 1];
-                    translate_dshift(F, sx, sy, params, conv, ey);
+                    if (theta)
+                        warp_dshift(F, theta[i], sx, sy, params, conv, ey);
+                    else
+                        translate_dshift(F, sx, sy, params, conv, ey);
                     double tx = 0.0, ty = 0.0;
                     for (size_t u = 0; u < n; ++u) {
                         tx += G[u] * conv[u];
@@ -561,14 +662,21 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
     }
     if (err) { free(chi); free(gfine); free(dcen); free(dshift); return ORC_ERR_OOM; }
     if (grad) {
-        /* fine centre = u0 + f (c_k + delta_i): both chain factors are f */
+        /* fine centre = u0 + f (R_i c_k + delta_i): the chain factor of delta_i is f, of c_k f R_i^T */
         for (int i = 0; i < E; ++i)
-            for (int k = 0; k < M; ++k)
-                for (int ax = 0; ax < 2; ++ax) {
-                    double v = f * dcen[((size_t)i * M + k) * 2 + ax];
-                    grad[oc + 2 * k + ax] += v;
-                    grad[od + 2 * i + ax] += v;
+            for (int k = 0; k < M; ++k) {
+                const double vx = f * dcen[((size_t)i * M + k) * 2 + 0], vy = f * dcen[((size_t)i * M + k) * 2 + 1];
+                if (theta) {
+                    const double ct = cos(theta[i]), st = sin(theta[i]);
+                    grad[oc + 2 * k + 0] += ct * vx + st * vy;
+                    grad[oc + 2 * k + 1] += -st * vx + ct * vy;
+                } else {
+                    grad[oc + 2 * k + 0] += vx;
+                    grad[oc + 2 * k + 1] += vy;
                 }
+                grad[od + 2 * i + 0] += vx;
+                grad[od + 2 * i + 1] += vy;
+            }
         if (translate)
             for (int i = 0; i < E; ++i)
                 for (int ax = 0; ax < 2; ++ax) grad[od + 2 * i + ax] += dshift[2 * i + ax];
@@ -580,14 +688,18 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
     double prior = 0.0;
     double *gprior = grad ? malloc(sizeof(double) * n) : NULL;
     int rc = orc_starlet_prior(F, J, lam, W, params + oh, &prior, gprior);
-    if (grad && rc == ORC_OK && translate) {
+    if (grad && rc == ORC_OK && (translate || theta)) {
         /* d/dh = sum_i T_i^T G_i (epochs in order), plus the prior's part */
         double *tg = malloc(sizeof(double) * n);
         if (!tg) rc = ORC_ERR_OOM;
         for (size_t u = 0; tg && u < n; ++u) grad[oh + u] = gprior[u];
         for (int i = 0; tg && i < E; ++i) {
-            orc_translate_adjoint(F, f * params[od + 2 * (size_t)i], f * params[od + 2 * (size_t)i + 1],
-                                  gfine + (size_t)i * n, tg);
+            const double sx = translate ? f * params[od + 2 * (size_t)i] : 0.0;
+            const double sy = translate ? f * params[od + 2 * (size_t)i + 1] : 0.0;
+            if (theta)
+                orc_warp_adjoint(F, theta[i], sx, sy, gfine + (size_t)i * n, tg);
+            else
+                orc_translate_adjoint(F, sx, sy, gfine + (size_t)i * n, tg);
             for (size_t u = 0; u < n; ++u) grad[oh + u] += tg[u];
         }
         free(tg);
@@ -607,7 +719,7 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
 int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d, const double *sigma,
                          const double *s, const double *W, const double *params, double *parts, double *grad,
                          double *chi2_epoch, int nthreads) {
-    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 0);
+    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 0, NULL);
 }
 
 /* The same with the extended channel moved by each epoch's shift: f_i = T_{f delta_i} h + P_i
@@ -615,7 +727,16 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
 int orc_deconv_loss_grad_shifted(int E, int N, int f, int K, int M, int J, double lam, const double *d,
                                  const double *sigma, const double *s, const double *W, const double *params,
                                  double *parts, double *grad, double *chi2_epoch, int nthreads) {
-    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 1);
+    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 1, NULL);
+}
+
+/* The same with the frame variants of orc_deconv_model_ex: translate (0 or 1) and theta (NULL or
+ * [E] rotation angles in radians, fixed inputs: no gradient). */
+int orc_deconv_loss_grad_ex(int E, int N, int f, int K, int M, int J, double lam, const double *d, const double *sigma,
+                            const double *s, const double *W, const double *params, double *parts, double *grad,
+                            double *chi2_epoch, int nthreads, int translate, const double *theta) {
+    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads,
+                            translate, theta);
 }
 
 /* Point-source prior, the third term of Eq. 11 (sec. 2.2):
