@@ -197,6 +197,21 @@ sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts);
  * returns SR_ERR_STATE until it is re-created. */
 sr_status sr_set_translate_h(sr_problem *p, int enable);
 
+/* Rotated frames (sec. 5 names rotations between frames; no equation in the paper, so this is the
+ * reading): epoch i's frame is the reference frame turned by theta[i] radians about the grid
+ * centre u0 = (F - 1)/2 and, when sr_set_translate_h is on, shifted by f * delta_i.  Fine pixel u of
+ * the epoch sees the extended channel at q = u0 + R^T (u - u0 - s), R = [[cos, -sin], [sin, cos]]
+ * on (x, y), bilinear with zero outside the grid, and point source k sits at u0 + f (R c_k +
+ * delta_i); the angles are fixed inputs (no gradient).  theta: host array of n_epochs finite
+ * doubles (copied; SR_ERR_NONFINITE otherwise), or NULL to turn the rotations off.  DECONV only
+ * (SR_ERR_STATE otherwise); SR_ERR_UNSUPPORTED with conv_mode FFT or PLAIN; under AUTO the problem
+ * is evaluated in the direct form while they are on.  New angles take effect at the next evaluation
+ * (captured optimiser steps included); turning them on or off drops the problem's plan and its
+ * optimiser state, and a batch created before that returns SR_ERR_STATE until it is re-created.
+ * The point-source prior and the App. C estimate stay in the reference frame.  Synchronises the
+ * problem's stream; allocates 2 n_epochs floats on the first call. */
+sr_status sr_set_rotations(sr_problem *p, const double *theta);
+
 /* lambda_pts from a model, by the ratio of App. C:
  *   lambda (|| W o Phi^T fbar ||_1 - || W o Phi^T h ||_1) / sum_k <a_k> || W o Phi^T r_k ||_1,
  * fbar = (1/E) sum_i (h + sum_k a_ki r_k(c_k + delta_i)) the mean of the epochs' fine images,
@@ -384,6 +399,23 @@ sr_status sr_lbfgsb(sr_problem *p, float *params_dev, const sr_lbfgsb_cfg *cfg, 
  * evaluation per line-search trial.  Arguments and errors as sr_lbfgsb, on the batch's stream. */
 sr_status sr_batch_lbfgsb(sr_batch *b, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
                           sr_lbfgsb_info *info);
+
+/* Independent L-BFGS-B runs, one per field of the batch (the algorithm and configuration of
+ * sr_lbfgsb), advanced together: every iteration builds the direction of each field still running
+ * from its own memory of pairs, then runs line-search rounds, each one batched evaluation of all
+ * fields, until every running field has its strong-Wolfe step or has used max_ls evaluations; a
+ * field stops on its own criteria (its projected gradient, its relative decrease, its iteration
+ * count) and keeps its parameters while the others go on.  A field's iterates do not depend on
+ * the other fields of the batch.  params_dev: the packed parameters of sr_batch_param_offset
+ * (device, overwritten with each field's last accepted iterate, bounded entries clipped first).
+ * f_history: NULL or a host array [fields][max_iter + 1] (each field's start and iterates, NaN
+ * after its last); info: NULL or a host array of one sr_lbfgsb_info per field; rounds: NULL or
+ * receives the number of batched evaluations after the first.  The 2m x 2m algebra and the
+ * breakpoints run on the host in FP64, fields in parallel on up to 16 host threads; every n-long
+ * operation runs on the device, per field.  Allocates and frees 2 (m + 1) + 5 vectors of the batch's
+ * parameter count; synchronises the stream.  Errors as sr_batch_lbfgsb. */
+sr_status sr_batch_lbfgsb_fields(sr_batch *b, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
+                                 sr_lbfgsb_info *info, int *rounds);
 
 /* Phase timings of one sr_noise_weights call: CUDA-event durations on its stream, summed over
  * the batches of realisations. */

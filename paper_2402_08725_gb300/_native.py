@@ -97,11 +97,14 @@ PROTOTYPES = {
     "sr_measure_fp32_peak": ([P_double], c_int),
     "sr_set_lambda_pts": ([c_void_p, c_double], c_int),
     "sr_set_translate_h": ([c_void_p, c_int], c_int),
+    "sr_set_rotations": ([c_void_p, P_double], c_int),
     "sr_psf_model": ([c_void_p, c_void_p, c_void_p], c_int),
     "sr_batch_set_data": ([c_void_p, c_void_p, c_int], c_int),
     "sr_batch_set_noise": ([c_void_p, c_void_p, c_int], c_int),
     "sr_batch_set_psfs": ([c_void_p, c_void_p, c_int], c_int),
     "sr_batch_lbfgsb": ([c_void_p, c_void_p, ctypes.POINTER(LbfgsbCfg), P_double, ctypes.POINTER(LbfgsbInfo)], c_int),
+    "sr_batch_lbfgsb_fields": ([c_void_p, c_void_p, ctypes.POINTER(LbfgsbCfg), P_double, ctypes.POINTER(LbfgsbInfo),
+                                ctypes.POINTER(c_int)], c_int),
     "sr_lbfgsb": ([c_void_p, c_void_p, ctypes.POINTER(LbfgsbCfg), P_double, ctypes.POINTER(LbfgsbInfo)], c_int),
     "sr_estimate_lambda_pts": ([c_void_p, c_void_p, P_double], c_int),
     "sr_noise_weights": ([c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int, ctypes.c_uint64, P_float,

@@ -129,6 +129,17 @@ class Problem:
         sr_set_translate_h.  Direct form only; drops the problem's plan and optimiser state."""
         nat.check(self.lib.sr_set_translate_h(self.handle, 1 if enable else 0), "sr_set_translate_h")
 
+    def set_rotations(self, theta=None):
+        """Rotate each epoch's frame by theta[i] radians about the grid centre (sec. 5), or None
+        to turn the rotations off; sr_set_rotations.  Direct form only."""
+        if theta is None:
+            nat.check(self.lib.sr_set_rotations(self.handle, None), "sr_set_rotations")
+            return
+        a = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        if a.size != self.E:
+            raise ValueError(f"expected {self.E} angles")
+        nat.check(self.lib.sr_set_rotations(self.handle, a.ctypes.data_as(nat.P_double)), "sr_set_rotations")
+
     def estimate_lambda_pts(self, params: torch.Tensor) -> float:
         """lambda_pts from the model `params` by the ratio of App. C; sr_estimate_lambda_pts."""
         out = ctypes.c_double()
@@ -328,6 +339,27 @@ class Batch:
         return {"iterations": info.iterations, "evaluations": info.evaluations,
                 "status": nat.LBFGSB_STATUS.get(info.status, str(info.status)), "f": info.f, "pg_norm": info.pg_norm,
                 "history": hist[:info.iterations + 1]}
+
+    def lbfgsb_fields(self, params: torch.Tensor, max_iter: int = 100, m: int = 10, max_ls: int = 20,
+                      pgtol: float = 1e-5, factr: float = 1e7):
+        """One L-BFGS-B run per field from `params` (overwritten); sr_batch_lbfgsb_fields.  Returns
+        (a dict per field: iterations, evaluations, status, f, pg_norm, history; the number of
+        batched evaluations after the first)."""
+        cfg = nat.LbfgsbCfg(int(m), int(max_iter), int(max_ls), float(pgtol), float(factr))
+        nf = len(self.problems)
+        infos = (nat.LbfgsbInfo * nf)()
+        hist = np.zeros((nf, int(max_iter) + 1))
+        rounds = ctypes.c_int()
+        nat.check(self.lib.sr_batch_lbfgsb_fields(self.handle, _cuda_f32(params, self.n_params, "params"),
+                                                  ctypes.byref(cfg), hist.ctypes.data_as(nat.P_double), infos,
+                                                  ctypes.byref(rounds)), "sr_batch_lbfgsb_fields")
+        out = []
+        for f in range(nf):
+            info = infos[f]
+            out.append({"iterations": info.iterations, "evaluations": info.evaluations,
+                        "status": nat.LBFGSB_STATUS.get(info.status, str(info.status)), "f": info.f,
+                        "pg_norm": info.pg_norm, "history": hist[f, :info.iterations + 1].copy()})
+        return out, rounds.value
 
     def reset_optimizer(self):
         nat.check(self.lib.sr_batch_reset_optimizer(self.handle), "sr_batch_reset_optimizer")

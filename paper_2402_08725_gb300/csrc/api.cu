@@ -234,6 +234,10 @@ struct sr_problem {
     float2 *big_zb = nullptr, *big_zt = nullptr;
     // the extended channel moved with each epoch's shift (sr_set_translate_h; direct form only)
     bool translate_h = false;
+    // rotated frames (sr_set_rotations; direct form only): per epoch (cos, sin) on the device
+    bool rot_on = false;
+    float *rot_dev = nullptr;
+    std::vector<float> rot_host;
     int fft_L = 0;
     float2 *fft_tw = nullptr, *khat = nullptr;
     int *d_flag = nullptr;
@@ -256,6 +260,7 @@ struct sr_batch {
     std::vector<sr_problem *> probs;
     std::vector<char> pts_enabled;  // each problem's point-source prior state when the plan was built
     std::vector<char> translate;    // each problem's moved-channel state when the plan was built
+    std::vector<char> rotate;       // each problem's rotated-frame state when the plan was built
     // batched input set-up (sr_batch_set_*), built at its first use
     DevArena bio_arena;
     BioEntry *bio_tab = nullptr;
@@ -377,6 +382,7 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
     fd.fft_khat = p->khat;
     fd.translate = p->translate_h ? 1 : 0;
     fd.hs_off = 0;
+    fd.rot = p->rot_on ? reinterpret_cast<const float2 *>(p->rot_dev) : nullptr;
 }
 
 // Epochs per work item of the frequency-domain form (one accumulator per item).
@@ -597,7 +603,8 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
                 for (int k = 0; k < fd.M; ++k) ps.push_back(make_int4(i, e, k, 0));
             psslot += (long long)fd.E * fd.M;
         } else if (pl->kind == SR_DECONV) {
-            if (fd.translate) return fail(SR_ERR_UNSUPPORTED, "the plain form does not move the extended channel");
+            if (fd.translate || fd.rot)
+                return fail(SR_ERR_UNSUPPORTED, "the plain form does not move or rotate the extended channel");
             // plain form: per-epoch partials of the residual kernel, one slot per 256 data px
             const int nb = (fd.N * fd.N + 255) / 256;
             fd.n_tiles = nb;
@@ -882,7 +889,7 @@ static sr_status time_form(sr_problem *p, int mode, float *ms) {
 }
 
 static bool field_uses_fft(sr_problem *p, const PlanOptions &opt) {
-    if (p->translate_h) return false;  // the moved channel is evaluated in the direct form only
+    if (p->translate_h || p->rot_on) return false;  // the frame variants are evaluated in the direct form only
     if (opt.mode_override >= 0) return opt.mode_override == 1 && p->fft_ok;
     if (!p->fft_ok) return false;
     if (p->desc.conv_mode == SR_CONV_FFT) return true;
@@ -1217,6 +1224,35 @@ sr_status sr_set_translate_h(sr_problem *p, int enable) {
     return SR_OK;
 }
 
+sr_status sr_set_rotations(sr_problem *p, const double *theta) {
+    if (!p) return fail(SR_ERR_ARG, "problem is NULL");
+    if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "rotated frames belong to deconvolution problems");
+    const bool on = theta != nullptr;
+    const int E = p->desc.n_epochs;
+    if (on) {
+        if (p->desc.conv_mode == SR_CONV_FFT || p->desc.conv_mode == SR_CONV_PLAIN)
+            return fail(SR_ERR_UNSUPPORTED, "rotated frames need conv_mode AUTO or DIRECT");
+        for (int i = 0; i < E; ++i)
+            if (!std::isfinite(theta[i])) return fail(SR_ERR_NONFINITE, "theta[%d] is not finite", i);
+        sr_status st;
+        if (!p->rot_dev && (st = p->arena.alloc(&p->rot_dev, 2 * (size_t)E)) != SR_OK) return st;
+        p->rot_host.resize(2 * (size_t)E);
+        for (int i = 0; i < E; ++i) {
+            p->rot_host[2 * (size_t)i] = (float)std::cos(theta[i]);
+            p->rot_host[2 * (size_t)i + 1] = (float)std::sin(theta[i]);
+        }
+        SR_CUDA(cudaMemcpyAsync(p->rot_dev, p->rot_host.data(), sizeof(float) * 2 * E, cudaMemcpyHostToDevice,
+                                p->stream));
+    }
+    SR_CUDA(cudaStreamSynchronize(p->stream));
+    if (on != p->rot_on) {  // the next evaluation builds a plan in the direct form (the optimiser restarts)
+        p->rot_on = on;
+        delete p->plan;
+        p->plan = nullptr;
+    }
+    return SR_OK;
+}
+
 sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts) {
     if (!p) return fail(SR_ERR_ARG, "problem is NULL");
     if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "lambda_pts belongs to deconvolution problems");
@@ -1453,6 +1489,7 @@ sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream,
     for (int i = 0; i < n; ++i) {
         b->pts_enabled.push_back(problems[i]->pts_enabled ? 1 : 0);
         b->translate.push_back(problems[i]->translate_h ? 1 : 0);
+        b->rotate.push_back(problems[i]->rot_on ? 1 : 0);
     }
     b->plan = new (std::nothrow) Plan();
     if (!b->plan) {
@@ -1617,6 +1654,9 @@ static sr_status batch_pts_check(const sr_batch *b) {
             return fail(SR_ERR_STATE, "field %zu got a non-zero lambda_pts after sr_batch_create: re-create the batch", i);
         if ((b->probs[i]->translate_h ? 1 : 0) != b->translate[i])
             return fail(SR_ERR_STATE, "field %zu changed sr_set_translate_h after sr_batch_create: re-create the batch", i);
+        if ((b->probs[i]->rot_on ? 1 : 0) != b->rotate[i])
+            return fail(SR_ERR_STATE, "field %zu turned its rotations on or off after sr_batch_create: re-create the batch",
+                        i);
     }
     return SR_OK;
 }
@@ -1844,6 +1884,32 @@ sr_status sr_batch_lbfgsb(sr_batch *b, float *params_dev, const sr_lbfgsb_cfg *c
         return sr_batch_loss_and_grad(b, x, nullptr, nullptr, f, g);
     };
     return lbfgsb_run(P, params_dev, c, f_history, info, b->stream);
+}
+
+sr_status sr_batch_lbfgsb_fields(sr_batch *b, float *params_dev, const sr_lbfgsb_cfg *cfg, double *f_history,
+                                 sr_lbfgsb_info *info, int *rounds) {
+    if (!b || !params_dev || !cfg) return fail(SR_ERR_ARG, "NULL argument");
+    sr_status st;
+    if ((st = batch_check(b)) != SR_OK) return st;
+    sr_lbfgsb_cfg c;
+    if ((st = lbfgsb_config(cfg, &c)) != SR_OK) return st;
+    LbfgsbFields P;
+    P.n = (long long)b->plan->n_params;
+    const int nf = (int)b->probs.size();
+    for (int i = 0; i < nf; ++i) {
+        const sr_problem *q = b->probs[i];
+        LbfgsbProblem one;
+        add_bounds(one, q->desc, q->F, (long long)b->plan->param_off[i]);
+        P.off.push_back((long long)b->plan->param_off[i]);
+        P.len.push_back((long long)param_count(q->desc));
+        P.ranges.push_back(one.ranges);
+        P.lo.push_back(one.lo);
+    }
+    P.eval = [b](const float *x, float *g, double *losses_dev) {
+        double total = 0.0;
+        return sr_batch_loss_and_grad(b, x, losses_dev, nullptr, &total, g);
+    };
+    return lbfgsb_fields_run(P, params_dev, c, f_history, info, rounds, b->stream);
 }
 
 sr_status sr_batch_reset_optimizer(sr_batch *b) {

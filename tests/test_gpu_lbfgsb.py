@@ -187,3 +187,90 @@ def test_lbfgsb_with_a_memory_of_one_pair():
     gpu = p.lbfgsb(P, max_iter=5, m=1, pgtol=0.0, factr=0.0)
     _compare(ref, gpu, P.cpu().numpy().astype(np.float64))
     p.close()
+
+
+def _field_starts():
+    """Three fields of different shapes (one without point sources, one whose source 1 is absent
+    from epoch 0 in noiseless data and starts negative, so its bound becomes active)."""
+    fields = [syn.small_deconv(70, E=3, N=12, f=2, K=9, M=2, J=3, lam=0.5),
+              syn.small_deconv(71, E=2, N=16, f=2, K=9, M=0, J=3, lam=0.8),
+              syn.small_deconv(72, E=3, N=12, f=2, K=9, M=2, J=3, lam=0.0)]
+    starts = []
+    for i, fd in enumerate(fields):
+        h, a, c, dl, gm = syn.unpack_deconv(fd.params.astype(np.float64), fd.E, fd.N, fd.f, fd.M)
+        if i == 2:
+            a[0, 1] = 0.0
+            truth = syn.pack_deconv(h, a, c, dl, gm).astype(np.float32).astype(np.float64)
+            fd.d = oracle.deconv_model(fd.E, fd.N, fd.f, fd.K, fd.M, fd.s, truth).astype(np.float32)
+            a0 = a.copy()
+            a0[0, 1] = -50.0
+            a0[1:] *= 1.2
+            starts.append(syn.pack_deconv(h, a0, c, dl, gm))
+        else:
+            starts.append(syn.pack_deconv(0.7 * h, 1.3 * a, c + 0.15, dl, gm))
+    return fields, [s.astype(np.float32).astype(np.float64) for s in starts]
+
+
+def _run_fields(fields, starts, mode="auto", **kw):
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    probs = [Problem.from_field(fd, conv_mode=mode) for fd in fields]
+    b = Batch(probs)
+    P = torch.from_numpy(b.pack(starts).astype(np.float32)).cuda()
+    res, rounds = b.lbfgsb_fields(P, **kw)
+    x = P.cpu().numpy().astype(np.float64)
+    xs = [x[o:o + fd.params.size] for fd, o in zip(fields, b.offsets)]
+    b.close()
+    for p in probs:
+        p.close()
+    return res, rounds, xs
+
+
+@pytest.mark.parametrize("mode", ["direct", "fft"])
+def test_batch_lbfgsb_fields_match_the_oracle_field_by_field(mode):
+    """sr_batch_lbfgsb_fields: one L-BFGS-B per field, advanced together, against the oracle
+    L-BFGS-B run on each field's own loss."""
+    fields, starts = _field_starts()
+    res, rounds, xs = _run_fields(fields, starts, mode, max_iter=6, m=5, pgtol=0.0, factr=0.0)
+    for fd, s, r, x in zip(fields, starts, res, xs):
+        lo, hi = _bounds_deconv(fd)
+        ref = olb.lbfgsb(_deconv_fun(fd), s, lo, hi, m=5, max_iter=6, pgtol=0.0, factr=0.0)
+        _compare(ref, r, x)
+        assert np.all(np.diff(r["history"]) < 0)
+    F, EM = fields[2].F, fields[2].E * fields[2].M
+    amps = xs[2][F * F:F * F + EM]
+    assert np.all(amps >= 0.0)
+    assert amps[1] <= 1e-9 * np.abs(amps).max()  # the amplitude absent from the data stays at its bound
+    assert rounds >= 6
+
+
+def test_batch_lbfgsb_fields_do_not_depend_on_their_batch_mates():
+    """Each field's run in a batch equals its run in a batch of its own, bit for bit, also when
+    the fields stop at different iterations on their own criteria."""
+    fields, starts = _field_starts()
+    kw = dict(max_iter=40, m=4, pgtol=0.0, factr=1e13)
+    res, rounds, xs = _run_fields(fields, starts, "direct", **kw)
+    iters = set()
+    for i in range(len(fields)):
+        r1, _, x1 = _run_fields([fields[i]], [starts[i]], "direct", **kw)
+        assert r1[0]["iterations"] == res[i]["iterations"]
+        assert r1[0]["status"] == res[i]["status"]
+        assert np.array_equal(r1[0]["history"], res[i]["history"])
+        assert np.array_equal(x1[0], xs[i])
+        iters.add(res[i]["iterations"])
+    assert len(iters) > 1, res  # the fields stopped at different iterations
+
+
+def test_batch_lbfgsb_fields_stopping_criteria():
+    fields, starts = _field_starts()
+    res, _, _ = _run_fields(fields, starts, max_iter=0)
+    assert all(r["iterations"] == 0 and r["status"] == "max_iter" for r in res)
+    res, _, _ = _run_fields(fields, starts, max_iter=50, pgtol=1e30)
+    assert all(r["iterations"] == 0 and r["status"] == "pgtol" for r in res)
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    p = Problem.from_field(fields[0])
+    b = Batch([p])
+    P = torch.from_numpy(b.pack([starts[0]]).astype(np.float32)).cuda()
+    with pytest.raises(RuntimeError):
+        b.lbfgsb_fields(P, m=11)
+    b.close()
+    p.close()
