@@ -67,10 +67,22 @@ struct FieldDev {
     // zero outside; direct form only) and the offset of its shift gradients (2 per epoch)
     int translate;
     long long hs_off;
+    // rotated frames: per epoch (cos theta_i, sin theta_i) of the frame's turn about the grid
+    // centre (device, owned by the problem), or NULL; direct form only
+    const float2 *rot;
 };
 
 // Whole and fractional parts of the bilinear read of a channel moved by s fine pixels: output u
 // reads u + n (weight 1 - t) and u + n + 1 (weight t), n = floor(-s), t = -s - n in [0, 1).
+// The reference-frame point seen by fine pixel (ux, uy) of a rotated frame:
+// q = u0 + R^T (u - u0 - s), R = [[c, -s], [s, c]] with (c, s) = cs; sh the frame's shift.  One
+// code path with explicit fused operations, so that every kernel takes the same cell decisions.
+__device__ __forceinline__ float2 frame_point(int F, float2 cs, float2 sh, int ux, int uy) {
+    const float u0 = 0.5f * (float)(F - 1);
+    const float dx = (float)ux - __fadd_rn(u0, sh.x), dy = (float)uy - __fadd_rn(u0, sh.y);
+    return make_float2(__fmaf_rn(cs.y, dy, __fmaf_rn(cs.x, dx, u0)), __fmaf_rn(cs.x, dy, __fmaf_rn(-cs.y, dx, u0)));
+}
+
 __device__ __forceinline__ void shift_split(float s, int *n, float *t) {
     const float fl = floorf(-s);
     *n = (int)fl;

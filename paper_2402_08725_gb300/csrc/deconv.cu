@@ -81,11 +81,39 @@ __device__ __forceinline__ int align4(int n) { return (n + 3) & ~3; }
 // ceil(a / b) for b > 0 and any sign of a
 __device__ __forceinline__ int ceil_div(int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); }
 
-// Fine-grid centre of point source k in epoch i: (F-1)/2 + f (c_k + delta_i).
-__device__ __forceinline__ float2 source_centre(const float *__restrict__ c, const float *__restrict__ dl, int k,
-                                                int F, int f) {
+// Position of point source k in epoch i's frame: R_i c_k in a rotated frame, else c_k.
+__device__ __forceinline__ float2 frame_pos(const FieldDev &fd, const float *__restrict__ c, int k, int i) {
+    const float cx = c[2 * k], cy = c[2 * k + 1];
+    if (!fd.rot) return make_float2(cx, cy);
+    const float2 r = fd.rot[i];
+    return make_float2(r.x * cx - r.y * cy, r.y * cx + r.x * cy);
+}
+
+// Fine-grid centre of a point source at frame position p in epoch i: (F-1)/2 + f (p + delta_i).
+__device__ __forceinline__ float2 source_centre(float2 p, const float *__restrict__ dl, int F, int f) {
     const float u0 = 0.5f * (float)(F - 1);
-    return make_float2(u0 + (float)f * (c[2 * k] + dl[0]), u0 + (float)f * (c[2 * k + 1] + dl[1]));
+    return make_float2(u0 + (float)f * (p.x + dl[0]), u0 + (float)f * (p.y + dl[1]));
+}
+
+// Bilinear value of h (F x F, zero outside) at the reference-frame point q, and its cell.
+__device__ __forceinline__ float bilinear_h(const float *__restrict__ h, int F, float2 q) {
+    const float fx = floorf(q.x), fy = floorf(q.y);
+    const int x0 = (int)fx, y0 = (int)fy;
+    const float tx = q.x - fx, ty = q.y - fy;
+    float v = 0.f;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int yy = y0 + b;
+        if (yy < 0 || yy >= F) continue;
+        const float wy = b ? ty : 1.f - ty;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int xx = x0 + a;
+            if (xx < 0 || xx >= F) continue;
+            v += wy * (a ? tx : 1.f - tx) * __ldg(h + (long long)yy * F + xx);
+        }
+    }
+    return v;
 }
 
 // Point sources are added while the tile is staged, each pixel summing the sources whose window
@@ -133,11 +161,15 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
             shift_split((float)f * dpar[0], &snx, &stx);
             shift_split((float)f * dpar[1], &sny, &sty);
         }
+        // a rotated frame reads h bilinearly at frame_point(u) instead
+        const float2 rcs = fd.rot ? fd.rot[t.epoch] : make_float2(1.f, 0.f);
+        const float2 rsh = fd.translate ? make_float2((float)f * dpar[0], (float)f * dpar[1]) : make_float2(0.f, 0.f);
 
         // point sources of this epoch: fine centre, amplitude and window origin (Eq. 9)
         if (tid < M) {
-            const float2 cen = source_centre(cpar, dpar, tid, F, f);
-            s_src[tid] = make_float4(cpar[2 * tid], cpar[2 * tid + 1], apar[tid], 0.f);
+            const float2 pos = frame_pos(fd, cpar, tid, t.epoch);
+            const float2 cen = source_centre(pos, dpar, F, f);
+            s_src[tid] = make_float4(pos.x, pos.y, apar[tid], 0.f);
             s_win[tid] = make_int2((int)floorf(cen.x) - kWinLo, (int)floorf(cen.y) - kWinLo);
         }
         __syncthreads();
@@ -173,7 +205,9 @@ fwd_kernel(const FieldDev *__restrict__ fields, const TileItem *__restrict__ ite
                     float v = 0.f;
                     if (mx >= 0 && mx < N) {
                         const int ux = f * mx + phx;
-                        if (fd.translate) {
+                        if (fd.rot) {
+                            v = bilinear_h(hpar, F, frame_point(F, rcs, rsh, ux, uy));
+                        } else if (fd.translate) {
                             // bilinear read at u - s, zero outside the grid
                             v = 0.f;
 #pragma unroll
@@ -349,7 +383,8 @@ __global__ void psgrad_kernel(const FieldDev *__restrict__ fields, const int4 *_
     const float *cpar = hpar + (long long)F * F + (long long)E * M;
     const float *dpar = cpar + 2 * M + 2 * i;
     const float a = hpar[(long long)F * F + (long long)i * M + k];
-    const float2 cen = source_centre(cpar, dpar, k, F, f);
+    const float2 pos = frame_pos(fd, cpar, k, i);
+    const float2 cen = source_centre(pos, dpar, F, f);
     const int uy_lo = (int)floorf(cen.y) - kWinLo, ux_lo = (int)floorf(cen.x) - kWinLo;
     const float *G = gbuf + fd.gbuf_off + (long long)i * nph * N * N;
     float sa = 0.f, sx = 0.f, sy = 0.f;
@@ -359,8 +394,8 @@ __global__ void psgrad_kernel(const FieldDev *__restrict__ fields, const int4 *_
         const int my = uy / f, mx = ux / f;
         const int ph = (uy - my * f) * f + (ux - mx * f);
         const float gv = G[((long long)ph * N + my) * N + mx];
-        const float dx = src_offset(ux, F, f, cpar[2 * k], dpar[0]);
-        const float dy = src_offset(uy, F, f, cpar[2 * k + 1], dpar[1]);
+        const float dx = src_offset(ux, F, f, pos.x, dpar[0]);
+        const float dy = src_offset(uy, F, f, pos.y, dpar[1]);
         const float gg = gv * gauss_at(dx, dy);
         sa += gg;
         sx += gg * dx;
@@ -392,6 +427,41 @@ __global__ void hgrad_kernel(const FieldDev *__restrict__ fields, const ChunkIte
     const int f = fd.f, N = fd.N, F = fd.F;
     if (q >= F * F) return;
     const long long plane = (long long)f * f * N * N;
+    if (fd.rot) {
+        // dL/dh = sum_i W_i^T G_i: pixel v gathers every u whose bilinear read (frame_point) has v
+        // in its cell; those u lie within 1.5 pixels of u0 + s + R (v - u0) on each axis
+        const int ph = q / (N * N), m = q - ph * N * N;
+        const int vy = f * (m / N) + ph / f, vx = f * (m % N) + ph % f;
+        const float *cpar = params + fd.param_off + (long long)F * F + (long long)fd.E * fd.M + 2 * fd.M;
+        const float *Gb = gbuf + fd.gbuf_off;
+        const float u0 = 0.5f * (float)(F - 1);
+        float acc = 0.f;
+        for (int i = 0; i < fd.E; ++i) {
+            const float2 cs = fd.rot[i];
+            const float2 sh = fd.translate ? make_float2((float)f * cpar[2 * i], (float)f * cpar[2 * i + 1])
+                                           : make_float2(0.f, 0.f);
+            const float ex = (float)vx - u0, ey = (float)vy - u0;
+            const float cx = u0 + sh.x + (cs.x * ex - cs.y * ey), cy = u0 + sh.y + (cs.y * ex + cs.x * ey);
+            const int ux0 = max(0, (int)ceilf(cx - 1.5f)), ux1 = min(F - 1, (int)floorf(cx + 1.5f));
+            const int uy0 = max(0, (int)ceilf(cy - 1.5f)), uy1 = min(F - 1, (int)floorf(cy + 1.5f));
+            float gi = 0.f;
+            for (int uy = uy0; uy <= uy1; ++uy)
+                for (int ux = ux0; ux <= ux1; ++ux) {
+                    const float2 qp = frame_point(F, cs, sh, ux, uy);
+                    const float fx = floorf(qp.x), fy = floorf(qp.y);
+                    const int a = vx - (int)fx, b = vy - (int)fy;
+                    if ((unsigned)a > 1u || (unsigned)b > 1u) continue;
+                    const float tx = qp.x - fx, ty = qp.y - fy;
+                    const int uph = (uy % f) * f + ux % f;
+                    gi += (b ? ty : 1.f - ty) * (a ? tx : 1.f - tx) *
+                          Gb[(long long)i * plane + (long long)uph * N * N + (uy / f) * N + ux / f];
+                }
+            acc += gi;
+        }
+        const int u = vy * F + vx;
+        grad[fd.param_off + u] = acc + fd.starlet[(long long)fd.J * F * F + u];
+        return;
+    }
     if (fd.translate) {
         // dL/dh = sum_i T_i^T G_i: pixel v gathers G_i(v - n - (0 | 1)) with the read's weights
         const int ph = q / (N * N), m = q - ph * N * N;
@@ -463,15 +533,27 @@ hshift_grad_kernel(const FieldDev *__restrict__ fields, const float *__restrict_
     shift_split((float)f * cpar[2 * i + 1], &ny, &ty);
     const float *Gi = gbuf + fd.gbuf_off + (long long)i * f * f * N * N;
     auto hv = [&](int y, int x) { return (y < 0 || y >= F || x < 0 || x >= F) ? 0.f : h[(long long)y * F + x]; };
+    const float2 cs = fd.rot ? fd.rot[i] : make_float2(1.f, 0.f);
+    const float2 sh = make_float2((float)f * cpar[2 * i], (float)f * cpar[2 * i + 1]);
     FSum sx = fsum_zero(), sy = fsum_zero();
     for (int q = threadIdx.x; q < F * F; q += blockDim.x) {
         const int ph = q / (N * N), m = q - ph * N * N;
         const int uy = f * (m / N) + ph / f, ux = f * (m % N) + ph % f;
         const float G = Gi[q];
-        const int x0 = ux + nx, y0 = uy + ny;
+        int x0 = ux + nx, y0 = uy + ny;
+        float wx = tx, wy = ty;
+        if (fd.rot) {  // the cell of frame_point(u); d out / d s = -R grad H
+            const float2 qp = frame_point(F, cs, sh, ux, uy);
+            const float fx = floorf(qp.x), fy = floorf(qp.y);
+            x0 = (int)fx;
+            y0 = (int)fy;
+            wx = qp.x - fx;
+            wy = qp.y - fy;
+        }
         const float h00 = hv(y0, x0), h01 = hv(y0, x0 + 1), h10 = hv(y0 + 1, x0), h11 = hv(y0 + 1, x0 + 1);
-        const float dx = -((1.f - ty) * (h01 - h00) + ty * (h11 - h10));
-        const float dy = -((1.f - tx) * (h10 - h00) + tx * (h11 - h01));
+        const float gx = (1.f - wy) * (h01 - h00) + wy * (h11 - h10);
+        const float gy = (1.f - wx) * (h10 - h00) + wx * (h11 - h01);
+        const float dx = -(cs.x * gx - cs.y * gy), dy = -(cs.y * gx + cs.x * gy);
         sx = fsum_add(sx, G * dx);
         sy = fsum_add(sy, G * dy);
     }
@@ -518,7 +600,15 @@ finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ 
     for (int s = threadIdx.x; s < 2 * M; s += blockDim.x) {
         const int k = s >> 1, ax = s & 1;
         double acc = 0.0;
-        for (int i = 0; i < E; ++i) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
+        if (fd.rot) {  // the centre is u0 + f (R_i c_k + delta_i): d/dc_k = f sum_i R_i^T d/d(centre)
+            for (int i = 0; i < E; ++i) {
+                const float2 r = fd.rot[i];
+                const long long b = 2 * (fd.ps_slot + (long long)i * M + k);
+                const double gx = ps_du[b], gy = ps_du[b + 1];
+                acc += ax == 0 ? (double)r.x * gx + (double)r.y * gy : -(double)r.y * gx + (double)r.x * gy;
+            }
+        } else
+            for (int i = 0; i < E; ++i) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
         gc[s] = sd ? (float)(f * acc + (double)pts_g[3 * (sd->ps_slot + k) + 1 + ax]) : (float)(f * acc);
     }
     float *gd = gc + 2 * M;

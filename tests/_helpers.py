@@ -125,11 +125,11 @@ def loss_errors(loss, L_ref, d, sigma, near_zero):
     return abs(loss - L_ref) / scale, rel_L, scale > abs(L_ref)
 
 
-def check_deconv(fd, loss, grad, params=None, report=None, lam_pts=0.0, near_zero=False, shifted=False):
+def check_deconv(fd, loss, grad, params=None, report=None, lam_pts=0.0, near_zero=False, shifted=False, theta=None):
     """lam_pts > 0 adds the point-source prior of Eq. 11 to the reference; near_zero=True for
     evaluations at a noiseless truth (see the module docstring); shifted=True takes the oracle
-    whose extended channel moves with each epoch's shift."""
-    L_ref, _, g_ref, _ = oracle_deconv(fd, params, shifted=shifted)
+    whose extended channel moves with each epoch's shift, theta the one with rotated frames."""
+    L_ref, _, g_ref, _ = oracle_deconv(fd, params, shifted=shifted, theta=theta)
     if lam_pts > 0.0:
         P = fd.params if params is None else params
         v, gp = oracle.pts_prior(fd.E, fd.N, fd.f, fd.M, fd.J, lam_pts, fd.W, P)
