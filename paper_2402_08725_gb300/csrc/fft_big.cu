@@ -283,10 +283,28 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
             float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
             const long long off = (long long)kx * L + ky;
             if (MODE == BG_MODEL) {
-                for (int ph = 0; ph < nph; ++ph) {
-                    A = cadd(A, cmul(a.khat[((long long)e0 * nph + ph) * SL + off], a.fhat[((long long)e0 * nph + ph) * SL + off]));
-                    if (has1)
-                        B = cadd(B, cmul(a.khat[((long long)e1 * nph + ph) * SL + off], a.fhat[((long long)e1 * nph + ph) * SL + off]));
+                // the loads of four phases in flight together, added in phase order
+                const float2 *__restrict__ k0 = a.khat + (long long)e0 * nph * SL + off;
+                const float2 *__restrict__ x0 = a.fhat + (long long)e0 * nph * SL + off;
+                const float2 *__restrict__ k1 = a.khat + (long long)e1 * nph * SL + off;
+                const float2 *__restrict__ x1 = a.fhat + (long long)e1 * nph * SL + off;
+                for (int p0 = 0; p0 < nph; p0 += 4) {
+                    float2 ka[4], xa[4], kb[4], xb[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const long long o = (long long)(p0 + u) * SL;
+                        const bool in = p0 + u < nph;
+                        ka[u] = in ? __ldg(k0 + o) : make_float2(0.f, 0.f);
+                        xa[u] = in ? __ldg(x0 + o) : make_float2(0.f, 0.f);
+                        kb[u] = in && has1 ? __ldg(k1 + o) : make_float2(0.f, 0.f);
+                        xb[u] = in && has1 ? __ldg(x1 + o) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (p0 + u >= nph) break;
+                        A = cadd(A, cmul(ka[u], xa[u]));
+                        if (has1) B = cadd(B, cmul(kb[u], xb[u]));
+                    }
                 }
             } else {  // HJOIN: phases 2j and 2j + 1, the frame pairs' adjoint spectra added in order
                 for (int p = 0; p < a.npairs; ++p) {
@@ -343,11 +361,26 @@ __global__ void __launch_bounds__(kBgThreads) big_cols_kernel(FieldDev fd, BgArg
         } else {  // ADJ: the pair's acc_phi = conj(Khat_{e0,phi}) ehat_e0 + conj(Khat_{e1,phi}) ehat_e1
             const int e0 = 2 * j, e1 = e0 + 1;
             const bool has1 = e1 < E;
-            float2 *ap = a.acc + (long long)j * nph * SL;
-            for (int ph = 0; ph < nph; ++ph) {
-                float2 run = cmulc(xa, a.khat[((long long)e0 * nph + ph) * SL + off]);
-                if (has1) run = cadd(run, cmulc(xb, a.khat[((long long)e1 * nph + ph) * SL + off]));
-                ap[(long long)ph * SL + off] = run;
+            float2 *__restrict__ ap = a.acc + (long long)j * nph * SL + off;
+            const float2 *__restrict__ k0 = a.khat + (long long)e0 * nph * SL + off;
+            const float2 *__restrict__ k1 = a.khat + (long long)e1 * nph * SL + off;
+            // the kernel spectra of four phases in flight together
+            for (int p0 = 0; p0 < nph; p0 += 4) {
+                float2 ka[4], kb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long o = (long long)(p0 + u) * SL;
+                    const bool in = p0 + u < nph;
+                    ka[u] = in ? __ldg(k0 + o) : make_float2(0.f, 0.f);
+                    kb[u] = in && has1 ? __ldg(k1 + o) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (p0 + u >= nph) break;
+                    float2 run = cmulc(xa, ka[u]);
+                    if (has1) run = cadd(run, cmulc(xb, kb[u]));
+                    ap[(long long)(p0 + u) * SL] = run;
+                }
             }
         }
     }

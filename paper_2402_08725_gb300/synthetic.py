@@ -227,9 +227,23 @@ def render_host(components, n_pix, scale=1.0, widen=0.0, rng=None, texture=0.0):
     return img
 
 
+def blurred_host_stack(components, N, f, fwhm_data, beta, sub=4):
+    """The host seen through each epoch's seeing, on the data grid: the Sersic components
+    integrated over each data pixel (sub x sub samples), convolved (FFT, 'same') with a unit-sum
+    Moffat of the epoch's effective width (fwhm_data data pixels, exponent beta).  [E, N, N]."""
+    from scipy.signal import fftconvolve
+    fine = render_host(components, N * sub, scale=sub / f)
+    sharp = fine.reshape(N, sub, N, sub).mean(axis=(1, 3)) * (sub * sub)
+    out = np.empty((len(fwhm_data), N, N), dtype=np.float32)
+    for i, (fw, b) in enumerate(zip(fwhm_data, beta)):
+        kern = moffat_stamp(2 * N - 1, float(fw), float(b))
+        out[i] = fftconvolve(sharp, kern, mode="same")
+    return out
+
+
 def make_deconv_field(rng, E, N, f, K, M, J, lam, *, psf_fwhm=(2.0, 3.0), psf_beta=(2.0, 4.0),
                       amp_range=(1e3, 1e4), pos_half=8.0, shift_std=0.1, host=None, sky=(5.0, 5.0),
-                      light_curve=None, positions=None, texture=0.0):
+                      light_curve=None, positions=None, texture=0.0, host_blur="mean"):
     F = f * N
     fwhm = rng.uniform(*psf_fwhm, size=E)
     beta = rng.uniform(*psf_beta, size=E)
@@ -246,14 +260,18 @@ def make_deconv_field(rng, E, N, f, K, M, J, lam, *, psf_fwhm=(2.0, 3.0), psf_be
     if host is None:
         host = [{"flux": 2e4, "n": 2.0, "re": 6.0}]
     # evaluation point: the host on the fine grid; data: the same components
-    # drawn directly on the data grid, widened by the mean seeing, plus point
+    # drawn directly on the data grid, widened by the mean seeing (host_blur="mean") or seen
+    # through each epoch's own seeing (host_blur="epoch", blurred_host_stack), plus point
     # sources drawn at data resolution with each epoch's effective width.
     h = render_host(host, F, rng=rng, texture=texture)
     fwhm_eff = np.sqrt(fwhm ** 2 + 4.0) / f
-    hd = render_host(host, N, scale=1.0 / f, widen=float(np.mean(fwhm_eff)) / 2.355)
     centre = (N - 1) / 2.0
     pos = centre + c[None, :, :] + delta[:, None, :]
-    model = _data_stamp_sources(N, E, pos, a, fwhm_eff, beta) + hd[None].astype(np.float32)
+    if host_blur == "epoch":
+        hd = blurred_host_stack(host, N, f, fwhm_eff, beta) if host else np.zeros((E, N, N), np.float32)
+    else:
+        hd = render_host(host, N, scale=1.0 / f, widen=float(np.mean(fwhm_eff)) / 2.355)[None].astype(np.float32)
+    model = _data_stamp_sources(N, E, pos, a, fwhm_eff, beta) + hd
     sky_e = rng.uniform(*sky, size=E)
     d, sigma = _noise(rng, model, sky_e)
     W = starlet_weights(J, sigma, f, E)
@@ -282,7 +300,7 @@ def _drw(rng, n, tau, sf_inf, dt):
     return m
 
 
-def config3(seed=None, E=300) -> DeconvField:
+def config3(seed=None, E=300, host_blur="mean") -> DeconvField:
     """Lensed-quasar light curves: 4 images at 1.2" (6 data px at 0.2"/px), 64x64
     stamps, f=2, 300 epochs each with a Moffat PSF (FWHM U[0.6,1.2]" = U[6,12]
     fine px, beta U[2,4]), ring Sersic arc plus lens galaxy, DRW fluxes, sky U[3,10]."""
@@ -297,7 +315,7 @@ def config3(seed=None, E=300) -> DeconvField:
     lc = 1e4 * magn[None, :] * 10 ** (-0.4 * mag)
     host = [{"flux": 2e4, "n": 1.0, "re": 1.5, "ring": 12.0}, {"flux": 3e4, "n": 3.0, "re": 8.0}]
     return make_deconv_field(rng, E=E, N=N, f=f, K=K, M=M, J=4, lam=2.0, psf_fwhm=(6.0, 12.0),
-                             host=host, sky=(3.0, 10.0), light_curve=lc, positions=pos)
+                             host=host, sky=(3.0, 10.0), light_curve=lc, positions=pos, host_blur=host_blur)
 
 
 CONFIG4_SIZES = (32, 48, 64, 96, 128)
@@ -312,7 +330,7 @@ def config4_shapes(seed=None, n_fields=256):
     return [(int(n), int(e), int(j)) for n, e, j in zip(Ns, Es, Js)]
 
 
-def config4_field(index, N, E, J, seed=None) -> DeconvField:
+def config4_field(index, N, E, J, seed=None, host_blur="mean") -> DeconvField:
     """One SN + host field of the uneven batch: Gaussian-pulse SN light curve
     (peak 1e4 at a random epoch, width 20 epochs), two-Sersic host (n=4 bulge,
     n=1 disc) with a 10% random-field texture, f=2, K=64, 1 point source."""
@@ -326,7 +344,8 @@ def config4_field(index, N, E, J, seed=None) -> DeconvField:
     host = [{"flux": 3e4, "n": 4.0, "re": 4.0 * re_scale}, {"flux": 5e4, "n": 1.0, "re": 12.0 * re_scale, "q": 0.6}]
     pos = rng.uniform(-N / 8, N / 8, size=(1, 2))
     return make_deconv_field(rng, E=E, N=N, f=f, K=K, M=M, J=J, lam=2.0, psf_fwhm=(4.0, 10.0),
-                             host=host, sky=(3.0, 10.0), light_curve=lc[:, None], positions=pos, texture=0.1)
+                             host=host, sky=(3.0, 10.0), light_curve=lc[:, None], positions=pos, texture=0.1,
+                             host_blur=host_blur)
 
 
 def point_source_field(seed, E, N, M, light_curve=None, positions=None, J=4) -> DeconvField:
