@@ -80,6 +80,9 @@ def _load():
             "orc_starlet_analysis": ([i, i, _dp, _dp], i),
             "orc_starlet_adjoint": ([i, i, _dp, _dp], i),
             "orc_starlet_prior": ([i, i, d, _dp, _dp, _dp, _dp], i),
+            "orc_starlet_prior_map": ([i, i, d, _dp, _dp, _dp, _dp], i),
+            "orc_psf_loss_grad_map": ([i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, i], i),
+            "orc_pts_prior_map": ([i, i, i, i, i, d, _dp, _dp, _dp, _dp], i),
             "orc_add_gaussian": ([i, d, d, d, _dp], i),
             "orc_deconv_param_count": ([i, i, i, i], sz),
             "orc_deconv_model": ([i, i, i, i, i, _dp, _dp, _dp], i),
@@ -89,7 +92,8 @@ def _load():
             "orc_warp": ([i, d, d, d, _dp, _dp], i),
             "orc_warp_adjoint": ([i, d, d, d, _dp, _dp], i),
             "orc_deconv_model_ex": ([i, i, i, i, i, _dp, _dp, _dp, i, _dp], i),
-            "orc_deconv_loss_grad_ex": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i, i, _dp], i),
+            "orc_deconv_loss_grad_ex": ([i, i, i, i, i, i, d, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, i, i, _dp, _dp],
+                                        i),
             "orc_translate_adjoint": ([i, d, d, _dp, _dp], i),
             "orc_moffat": ([i, d, d, _dp, _dp, _dp], i),
             "orc_psf_param_count": ([i, i, i], sz),
@@ -229,11 +233,17 @@ def starlet_adjoint(y):
 
 
 def starlet_prior(h, J: int, lam: float, W, grad: bool = True):
+    """lam sum_j W_j ||w_j||_1; W of shape (J-1,) per scale, or (J-1, F, F) per coefficient."""
     h, W = _f64(h), _f64(W)
     F = h.shape[0]
     p = np.zeros(1)
     g = np.empty((F, F)) if grad else None
-    _check(_load().orc_starlet_prior(F, J, float(lam), _ptr(W), _ptr(h), _ptr(p), _ptr(g)), "starlet_prior")
+    if W.ndim == 3:
+        if W.shape != (J - 1, F, F):
+            raise ValueError(f"weight map of shape {W.shape}, expected {(J - 1, F, F)}")
+        _check(_load().orc_starlet_prior_map(F, J, float(lam), _ptr(W), _ptr(h), _ptr(p), _ptr(g)), "starlet_prior")
+    else:
+        _check(_load().orc_starlet_prior(F, J, float(lam), _ptr(W), _ptr(h), _ptr(p), _ptr(g)), "starlet_prior")
     return (float(p[0]), g) if grad else float(p[0])
 
 
@@ -268,7 +278,8 @@ def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, n
                      theta=None):
     """Return (loss, parts[chi2, prior], grad or None, chi2 per epoch).  shifted=True moves the
     extended channel h by each epoch's shift f * delta_i (translate) before the convolution;
-    theta (E angles in radians) rotates each epoch's frame about the grid centre (warp)."""
+    theta (E angles in radians) rotates each epoch's frame about the grid centre (warp).  W of
+    shape (J-1,) weights each scale, of shape (J-1, F, F) each coefficient."""
     d, sigma, s, W, params = _f64(d), _f64(sigma), _f64(s), _f64(W), _f64(params)
     n = deconv_param_count(E, N, f, M)
     if params.size != n:
@@ -276,13 +287,17 @@ def deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, grad=True, n
     parts = np.zeros(2)
     g = np.empty(n) if grad else None
     chi = np.empty(E)
-    if theta is not None:
-        th = _f64(theta)
-        if th.size != E:
+    if theta is not None or W.ndim == 3:
+        th = None if theta is None else _f64(theta)
+        if th is not None and th.size != E:
             raise ValueError(f"theta has {th.size} values, expected {E}")
-        rc = _load().orc_deconv_loss_grad_ex(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W),
-                                             _ptr(params), _ptr(parts), _ptr(g), _ptr(chi), int(nthreads),
-                                             int(bool(shifted)), _ptr(th))
+        wmap = W if W.ndim == 3 else None
+        if wmap is not None and wmap.shape != (J - 1, f * N, f * N):
+            raise ValueError(f"weight map of shape {wmap.shape}, expected {(J - 1, f * N, f * N)}")
+        rc = _load().orc_deconv_loss_grad_ex(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s),
+                                             _ptr(W if wmap is None else np.zeros(J - 1)), _ptr(params), _ptr(parts),
+                                             _ptr(g), _ptr(chi), int(nthreads), int(bool(shifted)), _ptr(th),
+                                             _ptr(wmap))
     else:
         fn = _load().orc_deconv_loss_grad_shifted if shifted else _load().orc_deconv_loss_grad
         rc = fn(E, N, f, K, M, J, float(lam), _ptr(d), _ptr(sigma), _ptr(s), _ptr(W), _ptr(params), _ptr(parts),
@@ -300,8 +315,9 @@ def pts_prior(E, N, f, M, J, lam_pts, W, params, grad=True):
     Wv = _f64(W)
     v = ctypes.c_double()
     g = np.zeros_like(P) if grad else None
-    _check(_load().orc_pts_prior(int(E), int(N), int(f), int(M), int(J), float(lam_pts), _ptr(Wv), _ptr(P),
-                                 ctypes.byref(v), _ptr(g) if grad else None), "pts_prior")
+    fn = _load().orc_pts_prior_map if Wv.ndim == 3 else _load().orc_pts_prior
+    _check(fn(int(E), int(N), int(f), int(M), int(J), float(lam_pts), _ptr(Wv), _ptr(P),
+              ctypes.byref(v), _ptr(g) if grad else None), "pts_prior")
     return v.value, g
 
 
@@ -337,8 +353,8 @@ def psf_loss_grad(S, N, f, J, lam, t, sigma, W, params, grad=True, nthreads=0):
         raise ValueError(f"params has {params.size} values, expected {n}")
     parts = np.zeros(2)
     g = np.empty(n) if grad else None
-    rc = _load().orc_psf_loss_grad(S, N, f, J, float(lam), _ptr(t), _ptr(sigma), _ptr(W), _ptr(params),
-                                   _ptr(parts), _ptr(g), int(nthreads))
+    fn = _load().orc_psf_loss_grad_map if W.ndim == 3 else _load().orc_psf_loss_grad
+    rc = fn(S, N, f, J, float(lam), _ptr(t), _ptr(sigma), _ptr(W), _ptr(params), _ptr(parts), _ptr(g), int(nthreads))
     _check(rc, "psf_loss_grad")
     return float(parts.sum()), parts, g
 

@@ -312,6 +312,40 @@ int orc_starlet_prior(int F, int J, double lam, const double *W, const double *h
     return rc;
 }
 
+/* The prior with one weight per coefficient (sec. 2.3 and App. B propagate the noise to a map per
+ * scale; the paper then takes one value per scale, R15): lambda sum_j sum_u Wmap[j][u] |w_j(u)|
+ * over the J - 1 detail planes, Wmap [J-1][F][F]; gradient A^T (lambda Wmap o sign(A h)). */
+int orc_starlet_prior_map(int F, int J, double lam, const double *Wmap, const double *h, double *prior,
+                          double *grad) {
+    if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
+    size_t n = (size_t)F * F;
+    double *planes = malloc(sizeof(double) * n * J);
+    if (!planes) return ORC_ERR_OOM;
+    int rc = orc_starlet_analysis(F, J, h, planes);
+    if (rc) { free(planes); return rc; }
+    double p = 0.0;
+    for (int j = 0; j < J - 1; ++j)
+        for (size_t k = 0; k < n; ++k) p += lam * Wmap[(size_t)j * n + k] * fabs(planes[(size_t)j * n + k]);
+    *prior = p;
+    if (grad) {
+        for (int j = 0; j < J - 1; ++j)
+            for (size_t k = 0; k < n; ++k) {
+                double w = planes[(size_t)j * n + k];
+                planes[(size_t)j * n + k] = lam * Wmap[(size_t)j * n + k] * (w > 0 ? 1.0 : (w < 0 ? -1.0 : 0.0));
+            }
+        memset(planes + (size_t)(J - 1) * n, 0, sizeof(double) * n);
+        rc = orc_starlet_adjoint(F, J, planes, grad);
+    }
+    free(planes);
+    return rc;
+}
+
+/* The prior with per-scale weights W, or with the per-coefficient map Wmap when it is not NULL. */
+static int prior_w(int F, int J, double lam, const double *W, const double *Wmap, const double *h, double *prior,
+                   double *grad) {
+    return Wmap ? orc_starlet_prior_map(F, J, lam, Wmap, h, prior, grad) : orc_starlet_prior(F, J, lam, W, h, prior, grad);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Point-source channel (Eq. 9, sec. 2.2; r_k of Eq. 3)                       */
 /* ------------------------------------------------------------------------- */
@@ -566,7 +600,8 @@ int orc_deconv_model_ex(int E, int N, int f, int K, int M, const double *s, cons
  *   chi2_epoch (nullable) receives the chi^2 of each epoch. */
 static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d,
                             const double *sigma, const double *s, const double *W, const double *params, double *parts,
-                            double *grad, double *chi2_epoch, int nthreads, int translate, const double *theta) {
+                            double *grad, double *chi2_epoch, int nthreads, int translate, const double *theta,
+                            const double *Wmap) {
     if (E <= 0 || N <= 0 || f <= 0 || K <= 0 || M < 0) return ORC_ERR_SHAPE;
     int F = f * N;
     if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
@@ -687,7 +722,7 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
     if (chi2_epoch) memcpy(chi2_epoch, chi, sizeof(double) * E);
     double prior = 0.0;
     double *gprior = grad ? malloc(sizeof(double) * n) : NULL;
-    int rc = orc_starlet_prior(F, J, lam, W, params + oh, &prior, gprior);
+    int rc = prior_w(F, J, lam, W, Wmap, params + oh, &prior, gprior);
     if (grad && rc == ORC_OK && (translate || theta)) {
         /* d/dh = sum_i T_i^T G_i (epochs in order), plus the prior's part */
         double *tg = malloc(sizeof(double) * n);
@@ -719,7 +754,8 @@ static int deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam
 int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, const double *d, const double *sigma,
                          const double *s, const double *W, const double *params, double *parts, double *grad,
                          double *chi2_epoch, int nthreads) {
-    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 0, NULL);
+    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 0, NULL,
+                            NULL);
 }
 
 /* The same with the extended channel moved by each epoch's shift: f_i = T_{f delta_i} h + P_i
@@ -727,16 +763,18 @@ int orc_deconv_loss_grad(int E, int N, int f, int K, int M, int J, double lam, c
 int orc_deconv_loss_grad_shifted(int E, int N, int f, int K, int M, int J, double lam, const double *d,
                                  const double *sigma, const double *s, const double *W, const double *params,
                                  double *parts, double *grad, double *chi2_epoch, int nthreads) {
-    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 1, NULL);
+    return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads, 1, NULL,
+                            NULL);
 }
 
 /* The same with the frame variants of orc_deconv_model_ex: translate (0 or 1) and theta (NULL or
- * [E] rotation angles in radians, fixed inputs: no gradient). */
+ * [E] rotation angles in radians, fixed inputs: no gradient); Wmap (NULL or [J-1][F][F]) weights
+ * each starlet coefficient of the prior on its own (orc_starlet_prior_map) instead of W. */
 int orc_deconv_loss_grad_ex(int E, int N, int f, int K, int M, int J, double lam, const double *d, const double *sigma,
                             const double *s, const double *W, const double *params, double *parts, double *grad,
-                            double *chi2_epoch, int nthreads, int translate, const double *theta) {
+                            double *chi2_epoch, int nthreads, int translate, const double *theta, const double *Wmap) {
     return deconv_loss_grad(E, N, f, K, M, J, lam, d, sigma, s, W, params, parts, grad, chi2_epoch, nthreads,
-                            translate, theta);
+                            translate, theta, Wmap);
 }
 
 /* Point-source prior, the third term of Eq. 11 (sec. 2.2):
@@ -747,8 +785,8 @@ int orc_deconv_loss_grad_ex(int E, int N, int f, int K, int M, int J, double lam
  *   d/da_ki = (1/E) sum_u G[u] r_k[u],
  *   d/dc_k  = <a_k> sum_u G[u] d r_k[u] / d c_k,  d r_k / d c_k = f (u - centre_k) / s^2 r_k,
  * G = Phi (lambda_pts W o sign(Phi^T P)) the prior's gradient with respect to the image P. */
-int orc_pts_prior(int E, int N, int f, int M, int J, double lam_pts, const double *W, const double *params,
-                  double *value, double *grad) {
+static int pts_prior(int E, int N, int f, int M, int J, double lam_pts, const double *W, const double *Wmap,
+                     const double *params, double *value, double *grad) {
     if (E <= 0 || N <= 0 || f <= 0 || M < 0) return ORC_ERR_SHAPE;
     const int F = f * N;
     if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
@@ -765,7 +803,7 @@ int orc_pts_prior(int E, int N, int f, int M, int J, double lam_pts, const doubl
         source_centre(F, f, params + oc, zero, k, 0, &ux, &uy);
         orc_add_gaussian(F, abar[k], ux, uy, P);
     }
-    int rc = orc_starlet_prior(F, J, lam_pts, W, P, value, grad ? G : NULL);
+    int rc = prior_w(F, J, lam_pts, W, Wmap, P, value, grad ? G : NULL);
     if (rc == ORC_OK && grad) {
         const double s2 = gauss_sigma() * gauss_sigma();
         for (int k = 0; k < M; ++k) {
@@ -786,6 +824,17 @@ int orc_pts_prior(int E, int N, int f, int M, int J, double lam_pts, const doubl
     }
     free(P); free(G); free(abar); free(zero);
     return rc;
+}
+
+int orc_pts_prior(int E, int N, int f, int M, int J, double lam_pts, const double *W, const double *params,
+                  double *value, double *grad) {
+    return pts_prior(E, N, f, M, J, lam_pts, W, NULL, params, value, grad);
+}
+
+/* The point-source prior with the per-coefficient weights Wmap [J-1][F][F]. */
+int orc_pts_prior_map(int E, int N, int f, int M, int J, double lam_pts, const double *Wmap, const double *params,
+                      double *value, double *grad) {
+    return pts_prior(E, N, f, M, J, lam_pts, NULL, Wmap, params, value, grad);
 }
 
 /* Weighted L1 norm of the detail planes, sum_j W_j || (Phi^T x)_j ||_1. */
@@ -972,8 +1021,8 @@ int orc_psf_model(int S, int N, int f, const double *params, double *model_out) 
 }
 
 /* Loss (Eq. 7) and gradient of the PSF reconstruction. parts = {chi^2, prior on b}. */
-int orc_psf_loss_grad(int S, int N, int f, int J, double lam, const double *t, const double *sigma, const double *W,
-                      const double *params, double *parts, double *grad, int nthreads) {
+static int psf_loss_grad(int S, int N, int f, int J, double lam, const double *t, const double *sigma, const double *W,
+                         const double *Wmap, const double *params, double *parts, double *grad, int nthreads) {
     if (S <= 0 || N <= 0 || f <= 0) return ORC_ERR_SHAPE;
     int F = f * N;
     if (!orc_starlet_valid(F, J)) return ORC_ERR_SHAPE;
@@ -1043,7 +1092,7 @@ int orc_psf_loss_grad(int S, int N, int f, int J, double lam, const double *t, c
     for (int k = 0; k < S; ++k) chi2 += chi[k];
     double prior = 0.0;
     double *gprior = grad ? malloc(sizeof(double) * n) : NULL;
-    rc = orc_starlet_prior(F, J, lam, W, params, &prior, gprior);
+    rc = prior_w(F, J, lam, W, Wmap, params, &prior, gprior);
     if (grad && rc == ORC_OK) {
         double galpha = 0.0, gbeta = 0.0;
         for (size_t u = 0; u < n; ++u) {
@@ -1060,6 +1109,17 @@ int orc_psf_loss_grad(int S, int N, int f, int J, double lam, const double *t, c
     parts[1] = prior;
     free(gprior); free(s); free(dma); free(dmb); free(chi); free(gs_star);
     return rc;
+}
+
+int orc_psf_loss_grad(int S, int N, int f, int J, double lam, const double *t, const double *sigma, const double *W,
+                      const double *params, double *parts, double *grad, int nthreads) {
+    return psf_loss_grad(S, N, f, J, lam, t, sigma, W, NULL, params, parts, grad, nthreads);
+}
+
+/* The PSF loss with the per-coefficient prior weights Wmap [J-1][F][F]. */
+int orc_psf_loss_grad_map(int S, int N, int f, int J, double lam, const double *t, const double *sigma,
+                          const double *Wmap, const double *params, double *parts, double *grad, int nthreads) {
+    return psf_loss_grad(S, N, f, J, lam, t, sigma, NULL, Wmap, params, parts, grad, nthreads);
 }
 
 /* ------------------------------------------------------------------------- */
