@@ -174,6 +174,19 @@ sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device);
  * SR_ERR_NONFINITE otherwise); the array may be reused when the call returns. */
 sr_status sr_set_weights(sr_problem *p, const float *W);
 
+/* Prior weights per coefficient instead of per scale (sec. 2.3 and App. B propagate the noise to
+ * a map W_j(u) per scale; sr_noise_weights returns it): the prior becomes
+ *   lambda sum_j sum_u W_j(u) |w_j(u)|
+ * (and lambda_pts times the same map for the point-source prior).  Wmap: float32 [J-1][F][F],
+ * host (on_device = 0) or device pointer, each entry finite and >= 0 (SR_ERR_NONFINITE otherwise);
+ * copied, so the array may be reused when the call returns; NULL clears the map and the per-scale
+ * weights of sr_set_weights apply again.  Counts as setting the weights.  Later maps take effect at
+ * the next evaluation (captured optimiser steps included); setting the first map or clearing it
+ * drops the problem's plan and optimiser state, and a batch created before that returns
+ * SR_ERR_STATE until it is re-created.  sr_estimate_lambda_pts returns SR_ERR_UNSUPPORTED while a
+ * map is set.  Synchronises the problem's stream; allocates (J-1) F^2 floats on the first map. */
+sr_status sr_set_weight_map(sr_problem *p, const float *Wmap, int on_device);
+
 /* Point-source prior, the third term of Eq. 11 (sec. 2.2):
  *   lambda_pts || W o Phi^T sum_k <a_k> r_k ||_1,
  * <a_k> = (1/E) sum_i a_ki the mean amplitude of source k over the epochs, r_k the unit Gaussian

@@ -98,6 +98,7 @@ PROTOTYPES = {
     "sr_set_lambda_pts": ([c_void_p, c_double], c_int),
     "sr_set_translate_h": ([c_void_p, c_int], c_int),
     "sr_set_rotations": ([c_void_p, P_double], c_int),
+    "sr_set_weight_map": ([c_void_p, c_void_p, c_int], c_int),
     "sr_psf_model": ([c_void_p, c_void_p, c_void_p], c_int),
     "sr_batch_set_data": ([c_void_p, c_void_p, c_int], c_int),
     "sr_batch_set_noise": ([c_void_p, c_void_p, c_int], c_int),

@@ -120,6 +120,17 @@ class Problem:
             raise ValueError(f"expected {self.J - 1} weights")
         nat.check(self.lib.sr_set_weights(self.handle, ctypes.c_void_p(a.ctypes.data)), "sr_set_weights")
 
+    def set_weight_map(self, Wmap=None):
+        """Prior weights per starlet coefficient, [J-1][F][F] (numpy or a CUDA tensor), or None to
+        go back to the per-scale weights; sr_set_weight_map."""
+        if Wmap is None:
+            nat.check(self.lib.sr_set_weight_map(self.handle, None, 0), "sr_set_weight_map")
+            return
+        F = self.f * self.N
+        ptr, dev, keep = _as_input(Wmap, (self.J - 1) * F * F)
+        nat.check(self.lib.sr_set_weight_map(self.handle, ptr, dev), "sr_set_weight_map")
+        del keep
+
     def set_lambda_pts(self, lambda_pts: float):
         """Strength of the point-source prior (Eq. 11, third term); sr_set_lambda_pts."""
         nat.check(self.lib.sr_set_lambda_pts(self.handle, float(lambda_pts)), "sr_set_lambda_pts")

@@ -170,7 +170,7 @@ struct Plan {
     ChunkItem *d_chunks = nullptr;
     int Jmax = 0;
     int Fmax = 0;               // widest fine grid of the table (the starlet band grid)
-    bool any_unbanded = false;  // some field's starlet runs as passes rather than bands
+    int starlet_forms = 0;  // 1 << starlet_field_form of every field (bands, tiles, passes)
     float *ebuf = nullptr, *gbuf = nullptr, *ps_da = nullptr, *ps_du = nullptr;
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
     // frequency-domain form
@@ -187,7 +187,7 @@ struct Plan {
     int hs_Emax = 0;
     // point-source prior (Eq. 11, third term): shadow entries of the fields that have it
     int n_sh = 0, sh_Fmax = 0, sh_Jmax = 0, sh_Mmax = 0, n_sh_chunks = 0;
-    bool sh_any_unbanded = false;
+    int sh_starlet_forms = 0;
     FieldDev *d_sh = nullptr;
     ChunkItem *d_sh_chunks = nullptr;
     float *pbar = nullptr, *abar = nullptr, *pts_g = nullptr;
@@ -238,10 +238,14 @@ struct sr_problem {
     bool rot_on = false;
     float *rot_dev = nullptr;
     std::vector<float> rot_host;
+    // per-coefficient prior weights (sr_set_weight_map): [J-1][F][F] on the device
+    bool wmap_on = false;
+    float *wmap_dev = nullptr;
     int fft_L = 0;
     float2 *fft_tw = nullptr, *khat = nullptr;
     int *d_flag = nullptr;
     float W_host[kMaxScales] = {0};
+    float Wd_host[kMaxScales] = {0};  // staging of the factors upload_weights writes
     // point-source prior: lambda_pts, its weights lambda_pts W_j (device, and the host copy they
     // are sent from) and the starlet scratch of the mean point-source image; pts_enabled once a
     // non-zero lambda_pts was set (the evaluation then carries the term)
@@ -261,6 +265,7 @@ struct sr_batch {
     std::vector<char> pts_enabled;  // each problem's point-source prior state when the plan was built
     std::vector<char> translate;    // each problem's moved-channel state when the plan was built
     std::vector<char> rotate;       // each problem's rotated-frame state when the plan was built
+    std::vector<char> wmap;         // each problem's weight-map state when the plan was built
     // batched input set-up (sr_batch_set_*), built at its first use
     DevArena bio_arena;
     BioEntry *bio_tab = nullptr;
@@ -383,6 +388,7 @@ static void fill_field_common(FieldDev &fd, sr_problem *p) {
     fd.translate = p->translate_h ? 1 : 0;
     fd.hs_off = 0;
     fd.rot = p->rot_on ? reinterpret_cast<const float2 *>(p->rot_dev) : nullptr;
+    fd.Wmap = p->wmap_on ? p->wmap_dev : nullptr;
 }
 
 // Epochs per work item of the frequency-domain form (one accumulator per item).
@@ -522,7 +528,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         for (int c = 0; c < fd.n_chunks; ++c) chunks.push_back(ChunkItem{i, c * 256, c});
         Jmax = std::max(Jmax, fd.J);
         pl->Fmax = std::max(pl->Fmax, fd.F);
-        if (!starlet_field_banded(fd.F, fd.J)) pl->any_unbanded = true;
+        pl->starlet_forms |= 1 << starlet_field_form(fd.F, fd.J);
         if (pl->kind == SR_DECONV && !plain && p->fft_big && field_uses_fft(p, opt)) {
             // global-memory transforms: one chi^2 / sum e slot per data row, the window adjoint
             // images of the point sources in gbuf, and per (epoch, source) gradient slots
@@ -632,7 +638,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             pl->sh_Fmax = std::max(pl->sh_Fmax, fd.F);
             pl->sh_Jmax = std::max(pl->sh_Jmax, fd.J);
             pl->sh_Mmax = std::max(pl->sh_Mmax, fd.M);
-            if (!starlet_field_banded(fd.F, fd.J)) pl->sh_any_unbanded = true;
+            pl->sh_starlet_forms |= 1 << starlet_field_form(fd.F, fd.J);
             sh.push_back(sd);
         }
     }
@@ -827,7 +833,7 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
         launch_psgrad(pl->d_fields, pl->d_ps, pl->n_ps, params, pl->gbuf, pl->ps_da, pl->ps_du, st);
         ++n;
     }
-    n += launch_starlet(pl->d_fields, pl->n_fields, pl->Fmax, pl->any_unbanded, pl->d_chunks, pl->n_chunks, pl->Jmax,
+    n += launch_starlet(pl->d_fields, pl->n_fields, pl->Fmax, pl->starlet_forms, pl->d_chunks, pl->n_chunks, pl->Jmax,
                         params, pl->l1_part, st);
     if (pl->n_items > 0) {
         launch_hgrad(pl->d_fields, pl->d_chunks, pl->n_chunks, pl->gbuf, grad, params, st);
@@ -845,7 +851,7 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
     for (size_t b = 0; b < pl->big_fields.size(); ++b)
         n += launch_big_hgrad(pl->h_fields[pl->big_fields[b]], pl->big_buf[b], grad, st);
     if (pl->n_sh > 0)
-        n += launch_pts_prior(pl->d_sh, pl->d_fields, pl->n_sh, pl->sh_Fmax, pl->sh_Mmax, pl->sh_any_unbanded,
+        n += launch_pts_prior(pl->d_sh, pl->d_fields, pl->n_sh, pl->sh_Fmax, pl->sh_Mmax, pl->sh_starlet_forms,
                               pl->d_sh_chunks, pl->n_sh_chunks, pl->sh_Jmax, params, pl->abar, pl->pbar, pl->l1_pts,
                               pl->pts_g, st);
     launch_finalize(pl->d_fields, pl->n_fields, pl->chi_part, pl->se_part, pl->l1_part, pl->ps_da, pl->ps_du, grad,
@@ -1190,6 +1196,20 @@ sr_status sr_set_psfs(sr_problem *p, const float *s, int on_device) {
     return SR_OK;
 }
 
+// The per-scale factors the starlet kernels apply: W_j, or 1 with a per-coefficient map (which
+// then carries the weights); the point-source shadow entry's lambda_pts times the same.
+static sr_status upload_weights(sr_problem *p) {
+    float w[kMaxScales];
+    for (int j = 0; j < kMaxScales; ++j) w[j] = p->wmap_on ? 1.f : p->W_host[j];
+    memcpy(p->Wd_host, w, sizeof w);
+    SR_CUDA(cudaMemcpyAsync(p->Wd, p->Wd_host, sizeof w, cudaMemcpyHostToDevice, p->stream));
+    if (p->Wpts) {
+        for (int j = 0; j < kMaxScales; ++j) p->Wpts_host[j] = (float)(p->lam_pts * w[j]);
+        SR_CUDA(cudaMemcpyAsync(p->Wpts, p->Wpts_host, sizeof p->Wpts_host, cudaMemcpyHostToDevice, p->stream));
+    }
+    return SR_OK;
+}
+
 sr_status sr_set_weights(sr_problem *p, const float *W) {
     if (!p || !W) return fail(SR_ERR_ARG, "NULL argument");
     const int nw = p->desc.n_scales - 1;
@@ -1199,13 +1219,37 @@ sr_status sr_set_weights(sr_problem *p, const float *W) {
     memcpy(tmp, W, sizeof(float) * nw);
     // staged through the problem's host copy so the caller's array may be reused at once
     memcpy(p->W_host, tmp, sizeof tmp);
-    SR_CUDA(cudaMemcpyAsync(p->Wd, p->W_host, sizeof tmp, cudaMemcpyHostToDevice, p->stream));
     p->has_weights = true;
-    if (p->Wpts) {
-        for (int j = 0; j < kMaxScales; ++j) p->Wpts_host[j] = (float)(p->lam_pts * p->W_host[j]);
-        SR_CUDA(cudaMemcpyAsync(p->Wpts, p->Wpts_host, sizeof p->Wpts_host, cudaMemcpyHostToDevice, p->stream));
+    return upload_weights(p);
+}
+
+sr_status sr_set_weight_map(sr_problem *p, const float *Wmap, int on_device) {
+    if (!p) return fail(SR_ERR_ARG, "problem is NULL");
+    const bool on = Wmap != nullptr;
+    sr_status st;
+    if (on) {
+        const size_t n = (size_t)(p->desc.n_scales - 1) * p->F * p->F;
+        std::vector<float> h(n);
+        if (on_device) {
+            SR_CUDA(cudaMemcpyAsync(h.data(), Wmap, sizeof(float) * n, cudaMemcpyDeviceToHost, p->stream));
+            SR_CUDA(cudaStreamSynchronize(p->stream));
+        } else {
+            memcpy(h.data(), Wmap, sizeof(float) * n);
+        }
+        for (size_t i = 0; i < n; ++i)
+            if (!(h[i] >= 0.f) || !std::isfinite(h[i]))
+                return fail(SR_ERR_NONFINITE, "weight-map entry %zu is not finite and >= 0", i);
+        if (!p->wmap_dev && (st = p->arena.alloc(&p->wmap_dev, n)) != SR_OK) return st;
+        SR_CUDA(cudaMemcpyAsync(p->wmap_dev, h.data(), sizeof(float) * n, cudaMemcpyHostToDevice, p->stream));
+        p->has_weights = true;
     }
-    return SR_OK;
+    SR_CUDA(cudaStreamSynchronize(p->stream));
+    if (on != p->wmap_on) {  // the next evaluation builds a plan with (or without) the map
+        p->wmap_on = on;
+        delete p->plan;
+        p->plan = nullptr;
+    }
+    return upload_weights(p);
 }
 
 sr_status sr_set_translate_h(sr_problem *p, int enable) {
@@ -1286,11 +1330,7 @@ sr_status sr_set_lambda_pts(sr_problem *p, double lambda_pts) {
         }
     }
     p->lam_pts = lambda_pts;
-    if (p->Wpts) {
-        for (int j = 0; j < kMaxScales; ++j) p->Wpts_host[j] = (float)(lambda_pts * p->W_host[j]);
-        SR_CUDA(cudaMemcpyAsync(p->Wpts, p->Wpts_host, sizeof p->Wpts_host, cudaMemcpyHostToDevice, p->stream));
-    }
-    return SR_OK;
+    return upload_weights(p);
 }
 
 sr_status sr_psf_model(sr_problem *p, const float *params_dev, float *s_dev) {
@@ -1349,6 +1389,7 @@ sr_status sr_estimate_lambda_pts(sr_problem *p, const float *params_dev, double 
     if (!p || !params_dev || !lambda_pts) return fail(SR_ERR_ARG, "NULL argument");
     if (p->desc.kind != SR_DECONV) return fail(SR_ERR_STATE, "lambda_pts belongs to deconvolution problems");
     if (!p->has_weights) return fail(SR_ERR_STATE, "weights not set");
+    if (p->wmap_on) return fail(SR_ERR_UNSUPPORTED, "the App. C estimate takes per-scale weights (no weight map)");
     FieldDev fd;
     fill_field_common(fd, p);
     fd.param_off = 0;
@@ -1490,6 +1531,7 @@ sr_status sr_batch_create(sr_problem *const *problems, int n, void *cuda_stream,
         b->pts_enabled.push_back(problems[i]->pts_enabled ? 1 : 0);
         b->translate.push_back(problems[i]->translate_h ? 1 : 0);
         b->rotate.push_back(problems[i]->rot_on ? 1 : 0);
+        b->wmap.push_back(problems[i]->wmap_on ? 1 : 0);
     }
     b->plan = new (std::nothrow) Plan();
     if (!b->plan) {
@@ -1654,6 +1696,9 @@ static sr_status batch_pts_check(const sr_batch *b) {
             return fail(SR_ERR_STATE, "field %zu got a non-zero lambda_pts after sr_batch_create: re-create the batch", i);
         if ((b->probs[i]->translate_h ? 1 : 0) != b->translate[i])
             return fail(SR_ERR_STATE, "field %zu changed sr_set_translate_h after sr_batch_create: re-create the batch", i);
+        if ((b->probs[i]->wmap_on ? 1 : 0) != b->wmap[i])
+            return fail(SR_ERR_STATE, "field %zu set or cleared its weight map after sr_batch_create: re-create the batch",
+                        i);
         if ((b->probs[i]->rot_on ? 1 : 0) != b->rotate[i])
             return fail(SR_ERR_STATE, "field %zu turned its rotations on or off after sr_batch_create: re-create the batch",
                         i);

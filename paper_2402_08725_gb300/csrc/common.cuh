@@ -70,7 +70,16 @@ struct FieldDev {
     // rotated frames: per epoch (cos theta_i, sin theta_i) of the frame's turn about the grid
     // centre (device, owned by the problem), or NULL; direct form only
     const float2 *rot;
+    // per-coefficient prior weights [J-1][F][F] (device, owned by the problem), or NULL: the prior
+    // is then lambda Wd[j] |w_j| per scale; with a map, lambda Wd[j] Wmap[j][u] |w_j(u)| (Wd = 1,
+    // or lambda_pts for a point-source shadow entry)
+    const float *Wmap;
 };
+
+// The weight of coefficient u of detail plane j: the map's value, 1 without a map.
+__device__ __forceinline__ float wmap_at(const FieldDev &fd, int j, long long u) {
+    return fd.Wmap ? __ldg(fd.Wmap + (long long)j * fd.F * fd.F + u) : 1.f;
+}
 
 // Whole and fractional parts of the bilinear read of a channel moved by s fine pixels: output u
 // reads u + n (weight 1 - t) and u + n + 1 (weight t), n = floor(-s), t = -s - n in [0, 1).

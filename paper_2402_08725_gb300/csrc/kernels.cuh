@@ -100,11 +100,12 @@ void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long lon
 // --- starlet prior (starlet.cu) ---
 // Forward levels then adjoint levels for every field of the table (n_fields of them, grids at
 // most Fmax wide); writes the per-(level, chunk) prior partial sums and leaves T0 = dP/dh in
-// plane J of each field's starlet scratch.  Fields for which starlet_field_banded(F, J) holds
-// run as row bands; any_unbanded says whether the table has others (they run as passes over
-// the 256-pixel chunks).  Returns the number of launches issued.
-bool starlet_field_banded(int F, int J);
-int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unbanded, const ChunkItem *chunks,
+// plane J of each field's starlet scratch.  starlet_field_form(F, J) says how a field runs: 0 as
+// row bands, 1 as tiles, 2 as passes over the 256-pixel chunks; forms has bit 1 << form set for
+// every form of the table's fields beyond the bands (whose launches always run).  Returns the
+// number of launches issued.
+int starlet_field_form(int F, int J);
+int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st);
 
 // --- point-source prior and lambda_pts estimate (pts.cu) ---
@@ -112,7 +113,7 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unba
 // image at param_off in pbar, lambda 1, weights lambda_pts W_j, its own starlet scratch, l1 slots
 // in l1_pts and source slots ps_slot in abar / pts_g): value partial sums in l1_pts and per source
 // (sum G r, d/dc_x, d/dc_y) in pts_g.  Returns the number of launches.
-int launch_pts_prior(const FieldDev *sh, const FieldDev *fields, int n_sh, int Fmax, int Mmax, bool any_unbanded,
+int launch_pts_prior(const FieldDev *sh, const FieldDev *fields, int n_sh, int Fmax, int Mmax, int starlet_forms,
                      const ChunkItem *chunks, int n_chunks, int Jmax, const float *params, float *abar, float *pbar,
                      double *l1_pts, float *pts_g, cudaStream_t st);
 // The App. C ratio for one field (fd.param_off into params); synchronises st.

@@ -212,13 +212,13 @@ __global__ void est_final_kernel(FieldDev fd, const float *__restrict__ params, 
 
 }  // namespace
 
-int launch_pts_prior(const FieldDev *sh, const FieldDev *fields, int n_sh, int Fmax, int Mmax, bool any_unbanded,
+int launch_pts_prior(const FieldDev *sh, const FieldDev *fields, int n_sh, int Fmax, int Mmax, int starlet_forms,
                      const ChunkItem *chunks, int n_chunks, int Jmax, const float *params, float *abar, float *pbar,
                      double *l1_pts, float *pts_g, cudaStream_t st) {
     pts_mean_kernel<<<n_sh, 64, 0, st>>>(sh, fields, params, abar);
     const long long FF = (long long)Fmax * Fmax;
     pts_raster_kernel<<<dim3((unsigned)((FF + 255) / 256), n_sh), 256, 0, st>>>(sh, fields, params, abar, pbar);
-    int n = 2 + launch_starlet(sh, n_sh, Fmax, any_unbanded, chunks, n_chunks, Jmax, pbar, l1_pts, st);
+    int n = 2 + launch_starlet(sh, n_sh, Fmax, starlet_forms, chunks, n_chunks, Jmax, pbar, l1_pts, st);
     pts_grad_kernel<<<n_sh, 32 * std::min(std::max(Mmax, 1), 8), 0, st>>>(sh, fields, params, abar, pts_g);
     return n + 1;
 }

@@ -17,7 +17,11 @@
 //    propagates V_j = T_j - gamma_j instead of T_j (V_{J-1} = -gamma_{J-1} is formed while
 //    loading), so that its column pass reads one plane per tap; the signs are taken from the c
 //    planes once per output pixel.  Same arithmetic, in the same order, as the passes below.
-//  * passes (fields too wide for the shared-memory budget): one launch per pass and level,
+//  * tiles (fields too wide for a band of whole rows): the same as the bands on tiles of 16 rows
+//    by 128 columns, with the 2 * 2^j halo along x as well (the forward reads its row taps from
+//    the c plane directly; the adjoint stages the V rows and the column-adjoint values of the
+//    tile's columns and halo, which hold every mirror preimage its row gather reaches).
+//  * passes (fields too deep for the tiles' shared-memory budget): one launch per pass and level,
 //    every field of the table in 256-pixel chunks; the adjoint first writes V_{j+1} = T_{j+1} -
 //    gamma_{j+1} over T_{j+1} in place (pass 4), so that its column pass reads one plane per tap.
 // Fields deeper than a level skip it.
@@ -39,6 +43,22 @@ constexpr int kBandSmemBytes = 100 * 1024;     // shared memory of a band block 
 __host__ __device__ inline bool starlet_banded(int F, int J) {
     const long long s = 1LL << (J - 2);
     return (2LL * kBandRows + 4 * s) * F * (long long)sizeof(float) <= kBandSmemBytes;
+}
+
+constexpr int kTileCols = 128;                 // output columns per block in the tile kernels
+constexpr int kTileSmemBytes = 160 * 1024;     // shared memory of a tile block at its deepest level
+
+// Shared memory (floats) of the tile kernels at level j: the forward's row-filtered rows
+// (16 + 4 s rows of 128 columns), the adjoint's V rows and column-adjoint rows (16 + 4 s and 16 rows
+// of 128 + 4 s columns); s = 2^j.
+__host__ __device__ inline long long tile_fwd_floats(int j) { return (kBandRows + 4LL * (1 << j)) * kTileCols; }
+__host__ __device__ inline long long tile_adj_floats(int j) {
+    const long long s = 1LL << j;
+    return (2LL * kBandRows + 4 * s) * (kTileCols + 4 * s);
+}
+// Whether a field that does not run as bands runs as tiles: its deepest level fits the budget.
+__host__ __device__ inline bool starlet_tiled(int F, int J) {
+    return !starlet_banded(F, J) && tile_adj_floats(J - 2) * (long long)sizeof(float) <= kTileSmemBytes;
 }
 
 __device__ __forceinline__ int mirror_at(int t, int F) { return t < 0 ? -t : (t > F - 1 ? 2 * (F - 1) - t : t); }
@@ -91,7 +111,8 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
         if (c >= n_chunks) break;  // uniform over the block
         const ChunkItem ch = chunks[c];
         const FieldDev &fd = fields[ch.field];
-        if (j > fd.J - 2 || starlet_banded(fd.F, fd.J)) continue;  // no level j here, or run as bands
+        if (j > fd.J - 2 || starlet_banded(fd.F, fd.J) || starlet_tiled(fd.F, fd.J))
+            continue;  // no level j here, or run as bands or tiles
         const int F = fd.F;
         const int px = ch.start + threadIdx.x;
         const bool valid = px < F * F;
@@ -115,7 +136,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
                 cn[px] = acc;
                 const float wv = c_plane(fd, params, j)[px] - acc;
-                l1 = FSum{fabsf(wv), 0.f};
+                l1 = FSum{fabsf(wv) * wmap_at(fd, j, px), 0.f};
             }
         } else if (pass == 4) {
             if (valid) {
@@ -125,7 +146,8 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 const bool has_t = (j + 1) < (fd.J - 1);
                 float *Tn = t_plane(fd, j + 1);
                 const float wv = cj[px] - cn[px];
-                const float g = wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f);
+                const float lwu = lw * wmap_at(fd, j, px);
+                const float g = wv > 0.f ? lwu : (wv < 0.f ? -lwu : 0.f);
                 Tn[px] = (has_t ? Tn[px] : 0.f) - g;
             }
         } else if (pass == 2) {
@@ -139,7 +161,8 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 const float *tmp = pass_plane(fd) + (long long)y * F;
                 const float acc = adj_1d(tmp, x, F, step, 1);
                 const float wv = c_plane(fd, params, j)[px] - fd.starlet[(long long)j * F * F + px];
-                const float g = wv > 0.f ? lw : (wv < 0.f ? -lw : 0.f);
+                const float lwu = lw * wmap_at(fd, j, px);
+                const float g = wv > 0.f ? lwu : (wv < 0.f ? -lwu : 0.f);
                 t_plane(fd, j)[px] = g + acc;
             }
         }
@@ -156,7 +179,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
             if (c < n_chunks) {
                 const ChunkItem ch = chunks[c];
                 const FieldDev &fd = fields[ch.field];
-                if (j <= fd.J - 2 && !starlet_banded(fd.F, fd.J)) {
+                if (j <= fd.J - 2 && !starlet_banded(fd.F, fd.J) && !starlet_tiled(fd.F, fd.J)) {
                     FSum s = fsum_zero();
                     for (int i = 0; i < 8; ++i) s = fsum_add(s, FSum{s_red[threadIdx.x][i].x, s_red[threadIdx.x][i].y});
                     l1_part[fd.l1_slot + (long long)j * fd.n_chunks + ch.chunk] =
@@ -187,6 +210,7 @@ starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     for (int i = warp; i < R; i += nwarp) {
         const float *row = cj + (long long)mirror_at(r0 + i, F) * F;
         float *dst = sb + (long long)i * F;
+#pragma unroll 4
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
 #pragma unroll
@@ -201,12 +225,13 @@ starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const long long ro = (long long)(y0 + yy) * F;
         float l1_row = 0.f;
+#pragma unroll 4
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
 #pragma unroll
             for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(yy + 2 * s + m * s) * F + x];
             cn[ro + x] = acc;
-            l1_row += fabsf(cj[ro + x] - acc);
+            l1_row += fabsf(cj[ro + x] - acc) * wmap_at(fd, j, ro + x);
         }
         l1 = fsum_add(l1, l1_row);
     }
@@ -248,8 +273,10 @@ starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     const float *Vn = fd.starlet + (long long)(J + ((j + 1) & 1)) * F * F;
     for (int i = warp; i < vhi - vlo; i += nwarp) {
         const long long ro = (long long)(vlo + i) * F;
+#pragma unroll 4
         for (int x = lane; x < F; x += 32)
-            vb[(long long)i * F + x] = top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1) : Vn[ro + x];
+            vb[(long long)i * F + x] =
+                top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) : Vn[ro + x];
     }
     __syncthreads();
     for (int yy = warp; yy < Tr; yy += nwarp) {
@@ -276,24 +303,159 @@ starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const long long ro = (long long)(y0 + yy) * F;
         const float *trow = tb + (long long)yy * F;
+#pragma unroll 4
         for (int x = lane; x < F; x += 32) {
             const float acc = adj_1d(trow, x, F, s, 1);
-            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1) + acc;
-            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0) : tj;
+            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) + acc;
+            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0 * wmap_at(fd, j - 1, ro + x)) : tj;
         }
     }
 }
 
-bool starlet_field_banded(int F, int J) { return starlet_banded(F, J); }
+// Forward level j as tiles: c_{j+1} = Col_j Row_j c_j on rows [y0, y0 + 16) x columns [x0, x0 + 128)
+// and the prior partial of the tile.  Block (tile, field); the row taps are read from c_j.
+__global__ void __launch_bounds__(256)
+starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
+                        double *__restrict__ l1_part, int j) {
+    extern __shared__ float sb[];
+    __shared__ float2 s_red[8];
+    const FieldDev &fd = fields[blockIdx.y];
+    const int F = fd.F, J = fd.J;
+    if (j > J - 2 || !starlet_tiled(F, J)) return;
+    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + kBandRows - 1) / kBandRows;
+    const int t = blockIdx.x;
+    if (t >= nbx * nby) return;
+    const int by = t / nbx, bx = t - by * nbx, y0 = by * kBandRows, x0 = bx * kTileCols;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int s = 1 << j, Tr = min(kBandRows, F - y0), Tc = min(kTileCols, F - x0), r0 = y0 - 2 * s;
+    const int R = Tr + 4 * s;
+    const float *cj = c_plane(fd, params, j);
+    for (int i = warp; i < R; i += nwarp) {
+        const float *row = cj + (long long)mirror_at(r0 + i, F) * F;
+        float *dst = sb + (long long)i * kTileCols;
+#pragma unroll 4
+        for (int xx = lane; xx < Tc; xx += 32) {
+            const int x = x0 + xx;
+            float acc = 0.f;
+#pragma unroll
+            for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+            dst[xx] = acc;
+        }
+    }
+    __syncthreads();
+    float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
+    FSum l1 = fsum_zero();
+    for (int yy = warp; yy < Tr; yy += nwarp) {
+        const long long ro = (long long)(y0 + yy) * F;
+        float l1_row = 0.f;
+#pragma unroll 4
+        for (int xx = lane; xx < Tc; xx += 32) {
+            const int x = x0 + xx;
+            float acc = 0.f;
+#pragma unroll
+            for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(yy + 2 * s + m * s) * kTileCols + xx];
+            cn[ro + x] = acc;
+            l1_row += fabsf(cj[ro + x] - acc) * wmap_at(fd, j, ro + x);
+        }
+        l1 = fsum_add(l1, l1_row);
+    }
+    l1 = fsum_warp(l1);
+    if (lane == 0) s_red[warp] = make_float2(l1.hi, l1.lo);
+    __syncthreads();
+    const long long base = fd.l1_slot + (long long)j * fd.n_chunks;
+    if (threadIdx.x == 0) {
+        FSum tt = fsum_zero();
+        for (int w = 0; w < nwarp; ++w) tt = fsum_add(tt, FSum{s_red[w].x, s_red[w].y});
+        l1_part[base + t] = (double)fd.lambda * (double)fd.Wd[j] * fsum_value(tt);
+    }
+    if (t == 0)  // the level's remaining partial-sum slots stay zero
+        for (int c = nbx * nby + threadIdx.x; c < fd.n_chunks; c += blockDim.x) l1_part[base + c] = 0.0;
+}
 
-int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unbanded, const ChunkItem *chunks,
+// Adjoint level j as tiles: V_j (or T_0) on rows [y0, y0 + 16) x columns [x0, x0 + 128), as the
+// band adjoint with the column gather over the tile's columns and their 2 s halo (clipped to the
+// grid), which the row gather then reads, mirror preimages included.
+__global__ void __launch_bounds__(256)
+starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
+    extern __shared__ float sb[];
+    const FieldDev &fd = fields[blockIdx.y];
+    const int F = fd.F, J = fd.J;
+    if (j > J - 2 || !starlet_tiled(F, J)) return;
+    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + kBandRows - 1) / kBandRows;
+    const int t = blockIdx.x;
+    if (t >= nbx * nby) return;
+    const int by = t / nbx, bx = t - by * nbx, y0 = by * kBandRows, x0 = bx * kTileCols;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int s = 1 << j, Tr = min(kBandRows, F - y0), Tc = min(kTileCols, F - x0);
+    const int vlo = max(0, y0 - 2 * s), vhi = min(F, y0 + Tr + 2 * s);
+    const int xlo = max(0, x0 - 2 * s), xhi = min(F, x0 + Tc + 2 * s), W = xhi - xlo;
+    const int WP = kTileCols + 4 * s;  // row pitch of both staged arrays
+    float *vb = sb, *tb = sb + (long long)(kBandRows + 4 * s) * WP;
+    const float lw1 = fd.lambda * fd.Wd[j];
+    const float *cj = c_plane(fd, params, j), *cn = fd.starlet + (long long)j * F * F;  // c_j, c_{j+1}
+    const bool top = j + 1 == J - 1;
+    const float *Vn = fd.starlet + (long long)(J + ((j + 1) & 1)) * F * F;
+    for (int i = warp; i < vhi - vlo; i += nwarp) {
+        const long long ro = (long long)(vlo + i) * F;
+#pragma unroll 6
+        for (int xx = lane; xx < W; xx += 32) {
+            const int x = xlo + xx;
+            vb[(long long)i * WP + xx] =
+                top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) : Vn[ro + x];
+        }
+    }
+    __syncthreads();
+    for (int yy = warp; yy < Tr; yy += nwarp) {
+        const int y = y0 + yy;
+        for (int xx = lane; xx < W; xx += 32) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = -2; m <= 2; ++m) {
+                const float bm = kB3[m + 2];
+                const int k1 = y - m * s;
+                if (k1 >= 0 && k1 < F) acc += bm * vb[(long long)(k1 - vlo) * WP + xx];
+                const int k2 = -y - m * s;
+                if (y > 0 && k2 >= 0 && k2 < F) acc += bm * vb[(long long)(k2 - vlo) * WP + xx];
+                const int k3 = 2 * (F - 1) - y - m * s;
+                if (y < F - 1 && k3 >= 0 && k3 < F) acc += bm * vb[(long long)(k3 - vlo) * WP + xx];
+            }
+            tb[(long long)yy * WP + xx] = acc;
+        }
+    }
+    __syncthreads();
+    const float lw0 = j >= 1 ? fd.lambda * fd.Wd[j - 1] : 0.f;
+    const float *cjm = j >= 1 ? c_plane(fd, params, j - 1) : cj;  // c_{j-1}
+    float *out = fd.starlet + (long long)(J + (j & 1)) * F * F;
+    for (int yy = warp; yy < Tr; yy += nwarp) {
+        const long long ro = (long long)(y0 + yy) * F;
+        const float *trow = tb + (long long)yy * WP - xlo;  // indexed by the grid column
+#pragma unroll 4
+        for (int xx = lane; xx < Tc; xx += 32) {
+            const int x = x0 + xx;
+            const float acc = adj_1d(trow, x, F, s, 1);
+            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) + acc;
+            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0 * wmap_at(fd, j - 1, ro + x)) : tj;
+        }
+    }
+}
+
+int starlet_field_form(int F, int J) { return starlet_banded(F, J) ? 0 : starlet_tiled(F, J) ? 1 : 2; }
+
+int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st) {
     static bool configured = false;
-    if (!configured) {  // the band kernels take kBandSmemBytes of dynamic shared memory
+    if (!configured) {  // the band and tile kernels take their budgets of dynamic shared memory
         cudaFuncSetAttribute(starlet_band_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
         cudaFuncSetAttribute(starlet_band_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_tile_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
+        cudaFuncSetAttribute(starlet_tile_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
         configured = true;
     }
+    const bool tiles = (forms & 2) != 0, passes = (forms & 4) != 0;
+    const dim3 tgrid((unsigned)(((Fmax + kBandRows - 1) / kBandRows) * ((Fmax + kTileCols - 1) / kTileCols)), n_fields);
+    auto tile_smem = [&](long long floats) {
+        return (int)std::min<long long>(floats * (long long)sizeof(float), kTileSmemBytes);
+    };
     int n = 0;
     const int grid = (n_chunks + kStarletChunks - 1) / kStarletChunks;
     const dim3 bgrid((Fmax + kBandRows - 1) / kBandRows, n_fields);
@@ -306,7 +468,11 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unba
     for (int j = 0; j <= Jmax - 2; ++j) {
         starlet_band_fwd_kernel<<<bgrid, 256, band_smem(j), st>>>(fields, params, l1_part, j);
         ++n;
-        if (any_unbanded) {
+        if (tiles) {
+            starlet_tile_fwd_kernel<<<tgrid, 256, tile_smem(tile_fwd_floats(j)), st>>>(fields, params, l1_part, j);
+            ++n;
+        }
+        if (passes) {
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 0);
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 1);
             n += 2;
@@ -315,7 +481,11 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, bool any_unba
     for (int j = Jmax - 2; j >= 0; --j) {
         starlet_band_adj_kernel<<<bgrid, 256, band_smem(j), st>>>(fields, params, j);
         ++n;
-        if (any_unbanded) {
+        if (tiles) {
+            starlet_tile_adj_kernel<<<tgrid, 256, tile_smem(tile_adj_floats(j)), st>>>(fields, params, j);
+            ++n;
+        }
+        if (passes) {
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 4);
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
             starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 3);

@@ -95,7 +95,8 @@ def prior_kinks(h, J, lam, W, safety=16.0):
         k = int(amb.sum())
         if k:
             n += k
-            allow += 2.0 * lam * float(W[j - 1]) * _box_count(amb, 2 * (2 ** j - 1))
+            Wj = np.asarray(W, dtype=np.float64)[j - 1]
+            allow += 2.0 * lam * float(np.max(Wj)) * _box_count(amb, 2 * (2 ** j - 1))
         cabs_prev = cabs
     return n, allow
 

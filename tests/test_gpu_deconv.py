@@ -425,3 +425,14 @@ def test_schedules_forced_and_tuned_agree(tmp_path, monkeypatch):
     batch2.close()
     for pr in probs:
         pr.close()
+
+
+# Starlet forms of wide fields: F = 420 with J = 5 and J = 6 is too wide for whole-row bands and
+# runs as 16 x 128 tiles (the last tile column 36 wide); F = 300 with J = 7 is too deep for the
+# tiles' budget and runs as passes.
+@pytest.mark.parametrize("E,N,f,K,M,J", [(2, 140, 3, 15, 2, 5), (2, 140, 3, 15, 1, 6), (2, 150, 2, 9, 1, 7)])
+def test_wide_field_starlet_forms_match_oracle(E, N, f, K, M, J):
+    fd = syn.small_deconv(seed=3000 + N + J, E=E, N=N, f=f, K=K, M=M, J=J, lam=1.4, pos_half=N / 5)
+    loss, g = _run(fd, conv_mode="direct")
+    r = check_deconv(fd, loss, g)
+    print("wide starlet", N, f, J, r)
