@@ -480,9 +480,12 @@ def measure_extraction(stream, n_steps=200):
         for opt, steps in (("adabelief", n_steps), ("lbfgsb", n_steps // 2)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = extract(fd, c0, n_steps=steps, lambda_pts=0.0, stream=stream, optimizer=opt)
+            # fields with a host take the point-source prior at the App. C estimate, which keeps h
+            # from absorbing the point sources (sec. 2.2); point sources alone need none
+            lp = "app_c" if "host" in name else 0.0
+            r = extract(fd, c0, n_steps=steps, lambda_pts=lp, stream=stream, optimizer=opt)
             wall = time.perf_counter() - t0
-            row[opt] = {"steps": steps, "loss_evaluations": r["evaluations"], "wall_s": round(wall, 3),
+            row[opt] = {"steps": steps, "lambda_pts": lp, "loss_evaluations": r["evaluations"], "wall_s": round(wall, 3),
                         "device_ms": round(r["ms"], 2),
                         "chi2_over_half_npix": round(float(r["losses"][-1]) / (0.5 * fd.E * fd.N * fd.N), 4),
                         "A_photo": round(mt.a_photo(a_t, r["a"], bright), 5),
@@ -499,8 +502,10 @@ def measure_psf_fit(stream, steps=300):
     """PSF reconstruction quality (sec. 3, MAE_PSF) on config 2 (16 stars of 64 x 64, f = 2): the
     fit from b = 0, alpha x 1.3, beta = 3.5, amplitudes from the background-subtracted stamp sums
     and centres 0.1 px off, by AdaBelief (300 steps) and by L-BFGS-B (100 iterations) with the
-    workload's synthetic weights, and by AdaBelief with the weights of the noise propagation of
-    sec. 2.3 (sr_noise_weights, 1000 realisations, the 2-px Gaussian as the operator on b).  The stars
+    prior weights of the noise propagation of sec. 2.3 (sr_noise_weights, 1000 realisations, the
+    2-px Gaussian as the operator on b, the noise in units of the normalised stars), and by
+    AdaBelief with the workload's synthetic weights (in data units, not scaled to the stars' fluxes:
+    the prior then weighs about a star amplitude too little and b fits the noise).  The stars
     of config 2 are drawn on the data grid from the Moffat profile of the effective width times a
     faint copy of a random texture, not through the model, so no narrow PSF reproduces them exactly;
     the reference PSF is the Moffat that drew them, both PSFs normalised to unit sum.  Beside each
@@ -532,19 +537,22 @@ def measure_psf_fit(stream, steps=300):
         P0 = torch.from_numpy(start.astype(np.float32)).cuda()
         out["mae_psf_start"] = round(mt.mae_psf(s_ref, unit(prob.psf_model(P0))), 5)
         # prior weights by the noise propagation of sec. 2.3: for a PSF fit the pixel grid b is
-        # convolved with the 2-px-FWHM Gaussian r (Eq. 3), the stars' noise co-added
+        # convolved with the 2-px-FWHM Gaussian r (Eq. 3), the stars' noise co-added in units of
+        # the normalised stars (sigma_k / a_k, a_k from the starting amplitudes)
         from paper_2402_08725_gb300.binding import noise_weights
         K = 9
         yy, xx = np.mgrid[0:K, 0:K] - K // 2
         r = np.exp(-(xx * xx + yy * yy) * np.log(2.0))
-        W_mc, _, _ = noise_weights(N, f, K, pb.J, torch.from_numpy(pb.sigma.astype(np.float32)).cuda(),
+        sig_n = (pb.sigma / start[F * F + 2:F * F + 2 + S, None, None]).astype(np.float32)
+        W_mc, _, _ = noise_weights(N, f, K, pb.J, torch.from_numpy(sig_n).cuda(),
                                    torch.from_numpy((r / r.sum()).astype(np.float32)).cuda(), 1000, 7,
                                    want_map=False, stream=stream)
         out["noise_weights"] = [float(w) for w in W_mc]
-        for opt in ("adabelief", "lbfgsb", "adabelief_noise_weights"):
+        out["workload_weights"] = [float(w) for w in pb.W]
+        for opt in ("adabelief", "lbfgsb", "adabelief_workload_weights"):
             P = P0.clone()
-            if opt == "adabelief_noise_weights":
-                prob.set_weights(W_mc)
+            prob.reset_optimizer()
+            prob.set_weights(pb.W if opt == "adabelief_workload_weights" else W_mc)
             stream.synchronize()
             t0 = time.perf_counter()
             if opt.startswith("adabelief"):
