@@ -528,7 +528,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         for (int c = 0; c < fd.n_chunks; ++c) chunks.push_back(ChunkItem{i, c * 256, c});
         Jmax = std::max(Jmax, fd.J);
         pl->Fmax = std::max(pl->Fmax, fd.F);
-        pl->starlet_forms |= 1 << starlet_field_form(fd.F, fd.J);
+        pl->starlet_forms |= (1 << starlet_field_form(fd.F, fd.J)) | (fd.Wmap ? kStarletMapBit : 0);
         if (pl->kind == SR_DECONV && !plain && p->fft_big && field_uses_fft(p, opt)) {
             // global-memory transforms: one chi^2 / sum e slot per data row, the window adjoint
             // images of the point sources in gbuf, and per (epoch, source) gradient slots
@@ -638,7 +638,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             pl->sh_Fmax = std::max(pl->sh_Fmax, fd.F);
             pl->sh_Jmax = std::max(pl->sh_Jmax, fd.J);
             pl->sh_Mmax = std::max(pl->sh_Mmax, fd.M);
-            pl->sh_starlet_forms |= 1 << starlet_field_form(fd.F, fd.J);
+            pl->sh_starlet_forms |= (1 << starlet_field_form(fd.F, fd.J)) | (fd.Wmap ? kStarletMapBit : 0);
             sh.push_back(sd);
         }
     }

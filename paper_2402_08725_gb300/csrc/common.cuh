@@ -76,10 +76,13 @@ struct FieldDev {
     const float *Wmap;
 };
 
-// The weight of coefficient u of detail plane j: the map's value, 1 without a map.
-__device__ __forceinline__ float wmap_at(const FieldDev &fd, int j, long long u) {
-    return fd.Wmap ? __ldg(fd.Wmap + (long long)j * fd.F * fd.F + u) : 1.f;
+// Plane j of the weight map (NULL without a map), read once per kernel into a register: the
+// field table lives in global memory, where the kernels' stores could alias it.
+__device__ __forceinline__ const float *wmap_plane(const FieldDev &fd, int j) {
+    return (fd.Wmap && j >= 0) ? fd.Wmap + (long long)j * fd.F * fd.F : nullptr;
 }
+// The weight of coefficient u of that plane: the map's value, 1 without a map.
+__device__ __forceinline__ float wmap_w(const float *__restrict__ wm, long long u) { return wm ? __ldg(wm + u) : 1.f; }
 
 // Whole and fractional parts of the bilinear read of a channel moved by s fine pixels: output u
 // reads u + n (weight 1 - t) and u + n + 1 (weight t), n = floor(-s), t = -s - n in [0, 1).

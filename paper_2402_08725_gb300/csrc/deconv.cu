@@ -619,8 +619,17 @@ finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ 
         gd[s] = (float)(f * acc) + ((hs && fd.translate) ? hs[fd.hs_off + s] : 0.f);
     }
     float *gg = gd + 2 * E;
-    // dGamma_i = f^2 sum over the epoch's tiles: one warp per epoch (lanes stride the tiles, then a
-    // fixed shuffle tree), so that fields with many tiles per epoch keep their loads in flight
+    // dGamma_i = f^2 sum over the epoch's tiles: one thread per epoch for a few tiles per epoch;
+    // one warp per epoch (lanes stride the tiles, then a fixed shuffle tree) for many, so that
+    // their loads are in flight together
+    if (fd.n_tiles <= 32) {
+        for (int i = threadIdx.x; i < E; i += blockDim.x) {
+            double acc = 0.0;
+            for (int tt = 0; tt < fd.n_tiles; ++tt) acc += se_part[fd.tile_slot + (long long)i * fd.n_tiles + tt];
+            gg[i] = (float)((double)(f * f) * acc);
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     for (int i = threadIdx.x >> 5; i < E; i += nwarp) {
         double acc = 0.0;

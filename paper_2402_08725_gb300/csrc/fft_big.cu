@@ -537,11 +537,8 @@ __global__ void __launch_bounds__(kWinThreads) big_window_adj_kernel(FieldDev fd
     const int pw = nxp + Tk - 1, phh = nyp + Tk - 1;
     float *K = wsm, *X = wsm + Tk * Tk;
     const float *kap = fd.kappa + ((long long)e * nph + ph) * Tk * Tk;
-    // staging loops unrolled so that several loads per thread are in flight
-#pragma unroll 8
-    for (int t = threadIdx.x; t < Tk * Tk; t += blockDim.x) K[t] = __ldg(kap + t);
+    for (int t = threadIdx.x; t < Tk * Tk; t += blockDim.x) K[t] = kap[t];
     const float *ep = ebuf + fd.ebuf_off + (long long)e * N * N;
-#pragma unroll 8
     for (int t = threadIdx.x; t < phh * pw; t += blockDim.x) {
         const int iy = t / pw, ix = t - iy * pw;
         const int my = my0 + tlo + iy, mx = mx0 + tlo + ix;
@@ -555,17 +552,9 @@ __global__ void __launch_bounds__(kWinThreads) big_window_adj_kernel(FieldDev fd
     if (grp < groups) {
         for (int ty = grp; ty < Tk; ty += groups) {
             const float *xr = X + (py + ty) * pw + px, *kr = K + ty * Tk;
-            // four independent chains over the row's taps, added in a fixed order
-            float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
-            int tx = 0;
-            for (; tx + 4 <= Tk; tx += 4) {
-                r0 = fmaf(kr[tx], xr[tx], r0);
-                r1 = fmaf(kr[tx + 1], xr[tx + 1], r1);
-                r2 = fmaf(kr[tx + 2], xr[tx + 2], r2);
-                r3 = fmaf(kr[tx + 3], xr[tx + 3], r3);
-            }
-            for (; tx < Tk; ++tx) r0 = fmaf(kr[tx], xr[tx], r0);
-            part += (r0 + r1) + (r2 + r3);
+            float rs = 0.f;
+            for (int tx = 0; tx < Tk; ++tx) rs = fmaf(kr[tx], xr[tx], rs);
+            part += rs;
         }
     }
     s_part[threadIdx.x] = part;

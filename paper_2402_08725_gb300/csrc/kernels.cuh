@@ -101,9 +101,10 @@ void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long lon
 // Forward levels then adjoint levels for every field of the table (n_fields of them, grids at
 // most Fmax wide); writes the per-(level, chunk) prior partial sums and leaves T0 = dP/dh in
 // plane J of each field's starlet scratch.  starlet_field_form(F, J) says how a field runs: 0 as
-// row bands, 1 as tiles, 2 as passes over the 256-pixel chunks; forms has bit 1 << form set for
-// every form of the table's fields beyond the bands (whose launches always run).  Returns the
-// number of launches issued.
+// row bands, 1 as tiles, 2 as passes over the 256-pixel chunks, 3 as comb bands; forms has bit
+// 1 << form set for every form of the table's fields, and kStarletMapBit when some field has a
+// per-coefficient weight map.  Returns the number of launches issued.
+constexpr int kStarletMapBit = 16;
 int starlet_field_form(int F, int J);
 int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st);

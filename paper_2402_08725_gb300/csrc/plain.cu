@@ -230,8 +230,8 @@ int launch_plain_eval(const FieldDev *fields, const FieldDev &hf, const float *s
         if (hf.M > 0) plain_psgrad_kernel<<<1, 32 * hf.M, 0, st>>>(fields, params, i, pb.gi, ps_da, ps_du);
         n += hf.M > 0 ? 6 : 5;
     }
-    n += launch_starlet(fields, 1, hf.F, 1 << starlet_field_form(hf.F, hf.J), chunks, n_chunks, hf.J, params, l1_part,
-                        st);
+    const int forms = (1 << starlet_field_form(hf.F, hf.J)) | (hf.Wmap ? kStarletMapBit : 0);
+    n += launch_starlet(fields, 1, hf.F, forms, chunks, n_chunks, hf.J, params, l1_part, st);
     plain_hgrad_kernel<<<gF, 256, 0, st>>>(fields, pb.gsum, grad);
     ++n;
     launch_finalize(fields, 1, chi_part, se_part, l1_part, ps_da, ps_du, grad, losses, total, st);

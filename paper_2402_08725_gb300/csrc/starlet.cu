@@ -11,16 +11,21 @@
 // Scratch per field (planes of F*F floats): c_1..c_{J-1} (planes 0..J-2), a pass buffer (J-1),
 // and two T planes (J, J+1) used alternately; T_0 ends in plane J.
 //
-// Two ways to run a level, chosen per field (starlet_banded):
+// Four ways to run a level, chosen per field (starlet_form):
+//  * comb bands (most fields): the rows rho, rho + s, rho + 2 s, ... of level j (step s = 2^j)
+//    are one column tap apart, so a block taking 16 consecutive rows of one such comb stages
+//    only 20 input rows at any level; otherwise the same as the bands below, whose arithmetic
+//    and order it keeps (the column gather's mirror preimages are read from the plane).
 //  * bands: one launch per level; a block takes 16 output rows of one field, filters the rows it
 //    needs (with their 2 * 2^j-row halo) along x into shared memory, then along y.  The adjoint
 //    propagates V_j = T_j - gamma_j instead of T_j (V_{J-1} = -gamma_{J-1} is formed while
 //    loading), so that its column pass reads one plane per tap; the signs are taken from the c
 //    planes once per output pixel.  Same arithmetic, in the same order, as the passes below.
 //  * tiles (fields too wide for a band of whole rows): the same as the bands on tiles of 16 rows
-//    by 128 columns, with the 2 * 2^j halo along x as well (the forward reads its row taps from
-//    the c plane directly; the adjoint stages the V rows and the column-adjoint values of the
-//    tile's columns and halo, which hold every mirror preimage its row gather reaches).
+//    (32 from level 3 on) by 128 columns, with the 2 * 2^j halo along x as well (the forward
+//    reads its row taps from the c plane directly; the adjoint stages the V rows and the
+//    column-adjoint values of the tile's columns and halo, which hold every mirror preimage its
+//    row gather reaches).
 //  * passes (fields too deep for the tiles' shared-memory budget): one launch per pass and level,
 //    every field of the table in 256-pixel chunks; the adjoint first writes V_{j+1} = T_{j+1} -
 //    gamma_{j+1} over T_{j+1} in place (pass 4), so that its column pass reads one plane per tap.
@@ -48,17 +53,41 @@ __host__ __device__ inline bool starlet_banded(int F, int J) {
 constexpr int kTileCols = 128;                 // output columns per block in the tile kernels
 constexpr int kTileSmemBytes = 160 * 1024;     // shared memory of a tile block at its deepest level
 
+// Output rows of a tile at level j: 16, and 32 from level 3 on, where the 2 s-row halos on both
+// sides would otherwise stage several times the tile's own rows.
+__host__ __device__ inline int tile_rows(int j) { return j >= 3 ? 2 * kBandRows : kBandRows; }
 // Shared memory (floats) of the tile kernels at level j: the forward's row-filtered rows
-// (16 + 4 s rows of 128 columns), the adjoint's V rows and column-adjoint rows (16 + 4 s and 16 rows
-// of 128 + 4 s columns); s = 2^j.
-__host__ __device__ inline long long tile_fwd_floats(int j) { return (kBandRows + 4LL * (1 << j)) * kTileCols; }
+// (R + 4 s rows of 128 columns), the adjoint's V rows and column-adjoint rows (R + 4 s and R rows
+// of 128 + 4 s columns); s = 2^j, R = tile_rows(j).
+__host__ __device__ inline long long tile_fwd_floats(int j) { return (tile_rows(j) + 4LL * (1 << j)) * kTileCols; }
 __host__ __device__ inline long long tile_adj_floats(int j) {
     const long long s = 1LL << j;
-    return (2LL * kBandRows + 4 * s) * (kTileCols + 4 * s);
+    return (2LL * tile_rows(j) + 4 * s) * (kTileCols + 4 * s);
 }
 // Whether a field that does not run as bands runs as tiles: its deepest level fits the budget.
 __host__ __device__ inline bool starlet_tiled(int F, int J) {
     return !starlet_banded(F, J) && tile_adj_floats(J - 2) * (long long)sizeof(float) <= kTileSmemBytes;
+}
+
+// Comb bands: at level j (step s = 2^j) the rows congruent to rho modulo s form a comb whose rows
+// are s apart, which is exactly the spacing of the level's column taps; a block takes 16
+// consecutive rows of one comb and stages 20 (two more on each side) instead of 16 + 4 s.
+constexpr int kCombRows = 16;
+constexpr int kCombMaxF = kBandSmemBytes / ((2 * kCombRows + 4) * (int)sizeof(float));  // adjoint budget
+// Blocks of level j: s combs of ceil(ceil(F / s) / 16) chunks each.
+__host__ __device__ inline int comb_chunks(int F, int s) { return ((F + s - 1) / s + kCombRows - 1) / kCombRows; }
+// A field runs its levels as comb bands when a row of the adjoint's staging fits the budget and
+// every level's blocks fit the prior partial-sum slots of a level (one per 256 pixels).
+__host__ __device__ inline bool starlet_combed(int F, int J) {
+    if (F > kCombMaxF) return false;
+    const int slots = (F * F + 255) / 256;
+    for (int j = 0; j <= J - 2; ++j)
+        if ((1 << j) * comb_chunks(F, 1 << j) > slots) return false;
+    return true;
+}
+// 0 bands, 1 tiles, 2 passes, 3 comb bands
+__host__ __device__ inline int starlet_form(int F, int J) {
+    return starlet_combed(F, J) ? 3 : starlet_banded(F, J) ? 0 : starlet_tiled(F, J) ? 1 : 2;
 }
 
 __device__ __forceinline__ int mirror_at(int t, int F) { return t < 0 ? -t : (t > F - 1 ? 2 * (F - 1) - t : t); }
@@ -111,13 +140,13 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
         if (c >= n_chunks) break;  // uniform over the block
         const ChunkItem ch = chunks[c];
         const FieldDev &fd = fields[ch.field];
-        if (j > fd.J - 2 || starlet_banded(fd.F, fd.J) || starlet_tiled(fd.F, fd.J))
-            continue;  // no level j here, or run as bands or tiles
+        if (j > fd.J - 2 || starlet_form(fd.F, fd.J) != 2) continue;  // no level j here, or another form
         const int F = fd.F;
         const int px = ch.start + threadIdx.x;
         const bool valid = px < F * F;
         const int y = valid ? px / F : 0, x = valid ? px - y * F : 0;
         const float lw = fd.lambda * fd.Wd[j];
+        const float *wm1 = wmap_plane(fd, j);
         FSum l1 = fsum_zero();
         if (pass == 0) {
             if (valid) {
@@ -136,7 +165,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
                 cn[px] = acc;
                 const float wv = c_plane(fd, params, j)[px] - acc;
-                l1 = FSum{fabsf(wv) * wmap_at(fd, j, px), 0.f};
+                l1 = FSum{fabsf(wv) * wmap_w(wm1, px), 0.f};
             }
         } else if (pass == 4) {
             if (valid) {
@@ -146,7 +175,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 const bool has_t = (j + 1) < (fd.J - 1);
                 float *Tn = t_plane(fd, j + 1);
                 const float wv = cj[px] - cn[px];
-                const float lwu = lw * wmap_at(fd, j, px);
+                const float lwu = lw * wmap_w(wm1, px);
                 const float g = wv > 0.f ? lwu : (wv < 0.f ? -lwu : 0.f);
                 Tn[px] = (has_t ? Tn[px] : 0.f) - g;
             }
@@ -161,7 +190,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
                 const float *tmp = pass_plane(fd) + (long long)y * F;
                 const float acc = adj_1d(tmp, x, F, step, 1);
                 const float wv = c_plane(fd, params, j)[px] - fd.starlet[(long long)j * F * F + px];
-                const float lwu = lw * wmap_at(fd, j, px);
+                const float lwu = lw * wmap_w(wm1, px);
                 const float g = wv > 0.f ? lwu : (wv < 0.f ? -lwu : 0.f);
                 t_plane(fd, j)[px] = g + acc;
             }
@@ -179,7 +208,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
             if (c < n_chunks) {
                 const ChunkItem ch = chunks[c];
                 const FieldDev &fd = fields[ch.field];
-                if (j <= fd.J - 2 && !starlet_banded(fd.F, fd.J) && !starlet_tiled(fd.F, fd.J)) {
+                if (j <= fd.J - 2 && starlet_form(fd.F, fd.J) == 2) {
                     FSum s = fsum_zero();
                     for (int i = 0; i < 8; ++i) s = fsum_add(s, FSum{s_red[threadIdx.x][i].x, s_red[threadIdx.x][i].y});
                     l1_part[fd.l1_slot + (long long)j * fd.n_chunks + ch.chunk] =
@@ -192,6 +221,7 @@ starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__rest
 
 // Forward level j as bands: c_{j+1} = Col_j Row_j c_j on rows [y0, y0 + 16) and the prior
 // partial lambda W_j sum |c_j - c_{j+1}| of the band.  Block (b, field).
+template <bool MAP>
 __global__ void __launch_bounds__(256)
 starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
                         double *__restrict__ l1_part, int j) {
@@ -199,7 +229,7 @@ starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     __shared__ float2 s_red[8];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
-    if (j > J - 2 || !starlet_banded(F, J)) return;
+    if (j > J - 2 || starlet_form(F, J) != 0) return;
     const int b = blockIdx.x, y0 = b * kBandRows;
     if (y0 >= F) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -207,10 +237,10 @@ starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     // rows r0 .. y0 + Tr - 1 + 2s (mirrored: one reflection, as 2 s <= F - 1), filtered along x
     const int R = Tr + 4 * s;
     const float *cj = c_plane(fd, params, j);
+    const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr;
     for (int i = warp; i < R; i += nwarp) {
         const float *row = cj + (long long)mirror_at(r0 + i, F) * F;
         float *dst = sb + (long long)i * F;
-#pragma unroll 4
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
 #pragma unroll
@@ -225,13 +255,12 @@ starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const long long ro = (long long)(y0 + yy) * F;
         float l1_row = 0.f;
-#pragma unroll 4
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
 #pragma unroll
             for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(yy + 2 * s + m * s) * F + x];
             cn[ro + x] = acc;
-            l1_row += fabsf(cj[ro + x] - acc) * wmap_at(fd, j, ro + x);
+            l1_row += fabsf(cj[ro + x] - acc) * wmap_w(wm1, ro + x);
         }
         l1 = fsum_add(l1, l1_row);
     }
@@ -254,12 +283,13 @@ __device__ __forceinline__ float gamma_of(float wv, float lw) { return wv > 0.f 
 
 // Adjoint level j as bands: T_j = gamma_{j+1} + Row_j^T Col_j^T V_{j+1} on rows [y0, y0 + 16),
 // written as V_j = T_j - gamma_j (j >= 1) or T_0 (j = 0) into plane J + (j & 1).
+template <bool MAP>
 __global__ void __launch_bounds__(256, 4)  // at most 64 registers: four blocks per SM
 starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
     extern __shared__ float sb[];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
-    if (j > J - 2 || !starlet_banded(F, J)) return;
+    if (j > J - 2 || starlet_form(F, J) != 0) return;
     const int b = blockIdx.x, y0 = b * kBandRows;
     if (y0 >= F) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -268,15 +298,15 @@ starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     const int vlo = max(0, y0 - 2 * s), vhi = min(F, y0 + Tr + 2 * s);
     float *vb = sb, *tb = sb + (long long)(kBandRows + 4 * s) * F;
     const float lw1 = fd.lambda * fd.Wd[j];
+    const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr, *wm0 = MAP ? wmap_plane(fd, j - 1) : nullptr;
     const float *cj = c_plane(fd, params, j), *cn = fd.starlet + (long long)j * F * F;  // c_j, c_{j+1}
     const bool top = j + 1 == J - 1;
     const float *Vn = fd.starlet + (long long)(J + ((j + 1) & 1)) * F * F;
     for (int i = warp; i < vhi - vlo; i += nwarp) {
         const long long ro = (long long)(vlo + i) * F;
-#pragma unroll 4
         for (int x = lane; x < F; x += 32)
             vb[(long long)i * F + x] =
-                top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) : Vn[ro + x];
+                top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_w(wm1, ro + x)) : Vn[ro + x];
     }
     __syncthreads();
     for (int yy = warp; yy < Tr; yy += nwarp) {
@@ -303,17 +333,143 @@ starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const long long ro = (long long)(y0 + yy) * F;
         const float *trow = tb + (long long)yy * F;
-#pragma unroll 4
         for (int x = lane; x < F; x += 32) {
             const float acc = adj_1d(trow, x, F, s, 1);
-            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) + acc;
-            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0 * wmap_at(fd, j - 1, ro + x)) : tj;
+            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_w(wm1, ro + x)) + acc;
+            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0 * wmap_w(wm0, ro + x)) : tj;
+        }
+    }
+}
+
+// Forward level j as comb bands: block b takes rows y_t = rho + s (k0 + t), t < 16, of comb rho,
+// filters rows rho + s (k0 - 2 + i), i < 20 (mirrored), along x into shared memory, then along
+// y: each output row's five taps are staged rows t .. t + 4.  The same values, in the same order,
+// as the bands.  Block (b, field), b = rho * nk + k0 / 16.
+template <bool MAP>
+__global__ void __launch_bounds__(256)
+starlet_comb_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
+                        double *__restrict__ l1_part, int j) {
+    extern __shared__ float sb[];
+    __shared__ float2 s_red[8];
+    const FieldDev &fd = fields[blockIdx.y];
+    const int F = fd.F, J = fd.J;
+    if (j > J - 2 || starlet_form(F, J) != 3) return;
+    const int s = 1 << j, nk = comb_chunks(F, s), b = blockIdx.x;
+    if (b >= s * nk) return;
+    const int rho = b / nk, k0 = (b - rho * nk) * kCombRows;
+    const int Tr = max(0, min(kCombRows, (F - rho + s - 1) / s - k0));  // rows of the comb in the grid
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const float *cj = c_plane(fd, params, j);
+    const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr;
+    const int R = Tr > 0 ? Tr + 4 : 0;
+    for (int i = warp; i < R; i += nwarp) {
+        const float *row = cj + (long long)mirror_at(rho + s * (k0 - 2 + i), F) * F;
+        float *dst = sb + (long long)i * F;
+        for (int x = lane; x < F; x += 32) {
+            float acc = 0.f;
+#pragma unroll
+            for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+            dst[x] = acc;
+        }
+    }
+    __syncthreads();
+    float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
+    FSum l1 = fsum_zero();
+    for (int t = warp; t < Tr; t += nwarp) {
+        const long long ro = (long long)(rho + s * (k0 + t)) * F;
+        float l1_row = 0.f;
+        for (int x = lane; x < F; x += 32) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(t + 2 + m) * F + x];
+            cn[ro + x] = acc;
+            l1_row += fabsf(cj[ro + x] - acc) * wmap_w(wm1, ro + x);
+        }
+        l1 = fsum_add(l1, l1_row);
+    }
+    l1 = fsum_warp(l1);
+    if (lane == 0) s_red[warp] = make_float2(l1.hi, l1.lo);
+    __syncthreads();
+    const long long base = fd.l1_slot + (long long)j * fd.n_chunks;
+    if (threadIdx.x == 0) {
+        FSum tt = fsum_zero();
+        for (int w = 0; w < nwarp; ++w) tt = fsum_add(tt, FSum{s_red[w].x, s_red[w].y});
+        l1_part[base + b] = (double)fd.lambda * (double)fd.Wd[j] * fsum_value(tt);
+    }
+    if (b == 0)  // the level's remaining partial-sum slots stay zero
+        for (int c = s * nk + threadIdx.x; c < fd.n_chunks; c += blockDim.x) l1_part[base + c] = 0.0;
+}
+
+// Adjoint level j as comb bands: T_j = gamma_{j+1} + Row_j^T Col_j^T V_{j+1} on the comb rows of
+// block b, written as V_j = T_j - gamma_j (j >= 1) or T_0 (j = 0) into plane J + (j & 1).  The
+// direct taps y - m s of the column gather are the staged comb rows t - m + 2; its mirror
+// preimages (rows within 2 s of the grid's edges, in other combs) are read from the plane.  The
+// same values, in the same order, as the bands.
+template <bool MAP>
+__global__ void __launch_bounds__(256, 4)  // at most 64 registers: four blocks per SM
+starlet_comb_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
+    extern __shared__ float sb[];
+    const FieldDev &fd = fields[blockIdx.y];
+    const int F = fd.F, J = fd.J;
+    if (j > J - 2 || starlet_form(F, J) != 3) return;
+    const int s = 1 << j, nk = comb_chunks(F, s), b = blockIdx.x;
+    if (b >= s * nk) return;
+    const int rho = b / nk, k0 = (b - rho * nk) * kCombRows;
+    const int Tr = max(0, min(kCombRows, (F - rho + s - 1) / s - k0));
+    if (Tr == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    float *vb = sb, *tb = sb + (long long)(kCombRows + 4) * F;
+    const float lw1 = fd.lambda * fd.Wd[j];
+    const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr, *wm0 = MAP ? wmap_plane(fd, j - 1) : nullptr;
+    const float *cj = c_plane(fd, params, j), *cn = fd.starlet + (long long)j * F * F;  // c_j, c_{j+1}
+    const bool top = j + 1 == J - 1;
+    const float *Vn = fd.starlet + (long long)(J + ((j + 1) & 1)) * F * F;
+    // V_{j+1} (for the top level -gamma_{J-1}, formed on the fly) at row r, column x
+    auto vval = [&](int r, int x) {
+        const long long o = (long long)r * F + x;
+        return top ? 0.f - gamma_of(cj[o] - cn[o], lw1 * wmap_w(wm1, o)) : Vn[o];
+    };
+    for (int i = warp; i < Tr + 4; i += nwarp) {
+        const int r = rho + s * (k0 - 2 + i);
+        if (r < 0 || r >= F) continue;  // never read: the gather tests the same range
+        for (int x = lane; x < F; x += 32) vb[(long long)i * F + x] = vval(r, x);
+    }
+    __syncthreads();
+    for (int t = warp; t < Tr; t += nwarp) {
+        const int y = rho + s * (k0 + t);
+        for (int x = lane; x < F; x += 32) {
+            float acc = 0.f;
+#pragma unroll
+            for (int m = -2; m <= 2; ++m) {
+                const float bm = kB3[m + 2];
+                const int k1 = y - m * s;
+                if (k1 >= 0 && k1 < F) acc += bm * vb[(long long)(t - m + 2) * F + x];
+                const int k2 = -y - m * s;
+                if (y > 0 && k2 >= 0 && k2 < F) acc += bm * vval(k2, x);
+                const int k3 = 2 * (F - 1) - y - m * s;
+                if (y < F - 1 && k3 >= 0 && k3 < F) acc += bm * vval(k3, x);
+            }
+            tb[(long long)t * F + x] = acc;
+        }
+    }
+    __syncthreads();
+    const float lw0 = j >= 1 ? fd.lambda * fd.Wd[j - 1] : 0.f;
+    const float *cjm = j >= 1 ? c_plane(fd, params, j - 1) : cj;  // c_{j-1}
+    float *out = fd.starlet + (long long)(J + (j & 1)) * F * F;
+    for (int t = warp; t < Tr; t += nwarp) {
+        const long long ro = (long long)(rho + s * (k0 + t)) * F;
+        const float *trow = tb + (long long)t * F;
+        for (int x = lane; x < F; x += 32) {
+            const float acc = adj_1d(trow, x, F, s, 1);
+            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_w(wm1, ro + x)) + acc;
+            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0 * wmap_w(wm0, ro + x)) : tj;
         }
     }
 }
 
 // Forward level j as tiles: c_{j+1} = Col_j Row_j c_j on rows [y0, y0 + 16) x columns [x0, x0 + 128)
 // and the prior partial of the tile.  Block (tile, field); the row taps are read from c_j.
+template <bool MAP>
 __global__ void __launch_bounds__(256)
 starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
                         double *__restrict__ l1_part, int j) {
@@ -321,19 +477,20 @@ starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     __shared__ float2 s_red[8];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
-    if (j > J - 2 || !starlet_tiled(F, J)) return;
-    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + kBandRows - 1) / kBandRows;
+    if (j > J - 2 || starlet_form(F, J) != 1) return;
+    const int TR = tile_rows(j);
+    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + TR - 1) / TR;
     const int t = blockIdx.x;
     if (t >= nbx * nby) return;
-    const int by = t / nbx, bx = t - by * nbx, y0 = by * kBandRows, x0 = bx * kTileCols;
+    const int by = t / nbx, bx = t - by * nbx, y0 = by * TR, x0 = bx * kTileCols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int s = 1 << j, Tr = min(kBandRows, F - y0), Tc = min(kTileCols, F - x0), r0 = y0 - 2 * s;
+    const int s = 1 << j, Tr = min(TR, F - y0), Tc = min(kTileCols, F - x0), r0 = y0 - 2 * s;
     const int R = Tr + 4 * s;
     const float *cj = c_plane(fd, params, j);
+    const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr;
     for (int i = warp; i < R; i += nwarp) {
         const float *row = cj + (long long)mirror_at(r0 + i, F) * F;
         float *dst = sb + (long long)i * kTileCols;
-#pragma unroll 4
         for (int xx = lane; xx < Tc; xx += 32) {
             const int x = x0 + xx;
             float acc = 0.f;
@@ -348,14 +505,13 @@ starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const long long ro = (long long)(y0 + yy) * F;
         float l1_row = 0.f;
-#pragma unroll 4
         for (int xx = lane; xx < Tc; xx += 32) {
             const int x = x0 + xx;
             float acc = 0.f;
 #pragma unroll
             for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(yy + 2 * s + m * s) * kTileCols + xx];
             cn[ro + x] = acc;
-            l1_row += fabsf(cj[ro + x] - acc) * wmap_at(fd, j, ro + x);
+            l1_row += fabsf(cj[ro + x] - acc) * wmap_w(wm1, ro + x);
         }
         l1 = fsum_add(l1, l1_row);
     }
@@ -375,33 +531,35 @@ starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
 // Adjoint level j as tiles: V_j (or T_0) on rows [y0, y0 + 16) x columns [x0, x0 + 128), as the
 // band adjoint with the column gather over the tile's columns and their 2 s halo (clipped to the
 // grid), which the row gather then reads, mirror preimages included.
+template <bool MAP>
 __global__ void __launch_bounds__(256)
 starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
     extern __shared__ float sb[];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
-    if (j > J - 2 || !starlet_tiled(F, J)) return;
-    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + kBandRows - 1) / kBandRows;
+    if (j > J - 2 || starlet_form(F, J) != 1) return;
+    const int TR = tile_rows(j);
+    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + TR - 1) / TR;
     const int t = blockIdx.x;
     if (t >= nbx * nby) return;
-    const int by = t / nbx, bx = t - by * nbx, y0 = by * kBandRows, x0 = bx * kTileCols;
+    const int by = t / nbx, bx = t - by * nbx, y0 = by * TR, x0 = bx * kTileCols;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int s = 1 << j, Tr = min(kBandRows, F - y0), Tc = min(kTileCols, F - x0);
+    const int s = 1 << j, Tr = min(TR, F - y0), Tc = min(kTileCols, F - x0);
     const int vlo = max(0, y0 - 2 * s), vhi = min(F, y0 + Tr + 2 * s);
     const int xlo = max(0, x0 - 2 * s), xhi = min(F, x0 + Tc + 2 * s), W = xhi - xlo;
     const int WP = kTileCols + 4 * s;  // row pitch of both staged arrays
-    float *vb = sb, *tb = sb + (long long)(kBandRows + 4 * s) * WP;
+    float *vb = sb, *tb = sb + (long long)(TR + 4 * s) * WP;
     const float lw1 = fd.lambda * fd.Wd[j];
+    const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr, *wm0 = MAP ? wmap_plane(fd, j - 1) : nullptr;
     const float *cj = c_plane(fd, params, j), *cn = fd.starlet + (long long)j * F * F;  // c_j, c_{j+1}
     const bool top = j + 1 == J - 1;
     const float *Vn = fd.starlet + (long long)(J + ((j + 1) & 1)) * F * F;
     for (int i = warp; i < vhi - vlo; i += nwarp) {
         const long long ro = (long long)(vlo + i) * F;
-#pragma unroll 6
         for (int xx = lane; xx < W; xx += 32) {
             const int x = xlo + xx;
             vb[(long long)i * WP + xx] =
-                top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) : Vn[ro + x];
+                top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_w(wm1, ro + x)) : Vn[ro + x];
         }
     }
     __syncthreads();
@@ -429,30 +587,47 @@ starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const long long ro = (long long)(y0 + yy) * F;
         const float *trow = tb + (long long)yy * WP - xlo;  // indexed by the grid column
-#pragma unroll 4
         for (int xx = lane; xx < Tc; xx += 32) {
             const int x = x0 + xx;
             const float acc = adj_1d(trow, x, F, s, 1);
-            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_at(fd, j, ro + x)) + acc;
-            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0 * wmap_at(fd, j - 1, ro + x)) : tj;
+            const float tj = gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_w(wm1, ro + x)) + acc;
+            out[ro + x] = j >= 1 ? tj - gamma_of(cjm[ro + x] - cj[ro + x], lw0 * wmap_w(wm0, ro + x)) : tj;
         }
     }
 }
 
-int starlet_field_form(int F, int J) { return starlet_banded(F, J) ? 0 : starlet_tiled(F, J) ? 1 : 2; }
+int starlet_field_form(int F, int J) { return starlet_form(F, J); }
 
 int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {  // the band and tile kernels take their budgets of dynamic shared memory
-        cudaFuncSetAttribute(starlet_band_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
-        cudaFuncSetAttribute(starlet_band_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
-        cudaFuncSetAttribute(starlet_tile_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
-        cudaFuncSetAttribute(starlet_tile_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
+        cudaFuncSetAttribute(starlet_band_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_band_adj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_tile_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
+        cudaFuncSetAttribute(starlet_tile_adj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
+        cudaFuncSetAttribute(starlet_band_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_band_adj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_tile_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
+        cudaFuncSetAttribute(starlet_tile_adj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
+        cudaFuncSetAttribute(starlet_comb_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_comb_adj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_comb_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
+        cudaFuncSetAttribute(starlet_comb_adj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
         configured = true;
     }
-    const bool tiles = (forms & 2) != 0, passes = (forms & 4) != 0;
-    const dim3 tgrid((unsigned)(((Fmax + kBandRows - 1) / kBandRows) * ((Fmax + kTileCols - 1) / kTileCols)), n_fields);
+    const bool bands = (forms & 1) != 0, tiles = (forms & 2) != 0, passes = (forms & 4) != 0;
+    const bool combs = (forms & 8) != 0, map = (forms & kStarletMapBit) != 0;
+    // comb bands: s combs of comb_chunks blocks at level j; staging of 20 (forward) or 36 (adjoint)
+    // rows of the widest comb-band grid
+    const int Fc = std::min(Fmax, kCombMaxF);
+    auto cgrid = [&](int j) { return dim3((unsigned)((1 << j) * comb_chunks(Fc, 1 << j)), n_fields); };
+    const int comb_fwd_smem = (kCombRows + 4) * Fc * (int)sizeof(float);
+    const int comb_adj_smem = (2 * kCombRows + 4) * Fc * (int)sizeof(float);
+    auto tgrid = [&](int j) {
+        const int tr = tile_rows(j);
+        return dim3((unsigned)(((Fmax + tr - 1) / tr) * ((Fmax + kTileCols - 1) / kTileCols)), n_fields);
+    };
     auto tile_smem = [&](long long floats) {
         return (int)std::min<long long>(floats * (long long)sizeof(float), kTileSmemBytes);
     };
@@ -466,10 +641,26 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
         return (int)std::min<long long>(b, kBandSmemBytes);
     };
     for (int j = 0; j <= Jmax - 2; ++j) {
-        starlet_band_fwd_kernel<<<bgrid, 256, band_smem(j), st>>>(fields, params, l1_part, j);
-        ++n;
+        if (bands) {
+            if (map)
+                starlet_band_fwd_kernel<true><<<bgrid, 256, band_smem(j), st>>>(fields, params, l1_part, j);
+            else
+                starlet_band_fwd_kernel<false><<<bgrid, 256, band_smem(j), st>>>(fields, params, l1_part, j);
+            ++n;
+        }
+        if (combs) {
+            if (map)
+                starlet_comb_fwd_kernel<true><<<cgrid(j), 256, comb_fwd_smem, st>>>(fields, params, l1_part, j);
+            else
+                starlet_comb_fwd_kernel<false><<<cgrid(j), 256, comb_fwd_smem, st>>>(fields, params, l1_part, j);
+            ++n;
+        }
         if (tiles) {
-            starlet_tile_fwd_kernel<<<tgrid, 256, tile_smem(tile_fwd_floats(j)), st>>>(fields, params, l1_part, j);
+            const int sm = tile_smem(tile_fwd_floats(j));
+            if (map)
+                starlet_tile_fwd_kernel<true><<<tgrid(j), 256, sm, st>>>(fields, params, l1_part, j);
+            else
+                starlet_tile_fwd_kernel<false><<<tgrid(j), 256, sm, st>>>(fields, params, l1_part, j);
             ++n;
         }
         if (passes) {
@@ -479,10 +670,26 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
         }
     }
     for (int j = Jmax - 2; j >= 0; --j) {
-        starlet_band_adj_kernel<<<bgrid, 256, band_smem(j), st>>>(fields, params, j);
-        ++n;
+        if (bands) {
+            if (map)
+                starlet_band_adj_kernel<true><<<bgrid, 256, band_smem(j), st>>>(fields, params, j);
+            else
+                starlet_band_adj_kernel<false><<<bgrid, 256, band_smem(j), st>>>(fields, params, j);
+            ++n;
+        }
+        if (combs) {
+            if (map)
+                starlet_comb_adj_kernel<true><<<cgrid(j), 256, comb_adj_smem, st>>>(fields, params, j);
+            else
+                starlet_comb_adj_kernel<false><<<cgrid(j), 256, comb_adj_smem, st>>>(fields, params, j);
+            ++n;
+        }
         if (tiles) {
-            starlet_tile_adj_kernel<<<tgrid, 256, tile_smem(tile_adj_floats(j)), st>>>(fields, params, j);
+            const int sm = tile_smem(tile_adj_floats(j));
+            if (map)
+                starlet_tile_adj_kernel<true><<<tgrid(j), 256, sm, st>>>(fields, params, j);
+            else
+                starlet_tile_adj_kernel<false><<<tgrid(j), 256, sm, st>>>(fields, params, j);
             ++n;
         }
         if (passes) {
