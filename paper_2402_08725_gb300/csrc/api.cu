@@ -175,6 +175,7 @@ struct Plan {
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
     // frequency-domain form
     int n_fft_items = 0, n_fft_fields = 0, max_pairs = 1, smem_fft = 0, smem_fx = 0, grid_fft = 0;
+    int max_acc_points = 0;  // largest f^2 L (L/2 + 1) of the transform fields
     int chunk = kFftChunk, gp_cap = 0;  // the schedule the plan was built with (epochs per item, pair cap)
     int4 *d_fft_items = nullptr;
     int *d_fft_fields = nullptr;
@@ -564,6 +565,7 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
             hhat_len += (long long)nph * L * (H + 1);
             fft_fields.push_back(i);
             pl->max_pairs = std::max(pl->max_pairs, (nph + 1) / 2);
+            pl->max_acc_points = std::max(pl->max_acc_points, nph * fd.fft_L * (fd.fft_L / 2 + 1));
             smem_fft = std::max(smem_fft, fft_pair_field_smem(L));
             // epoch pairs side by side: the widest group the kernel is compiled for at this size
             // (more than one pair only with at most one source) if its buffers fit, else one pair
@@ -667,6 +669,19 @@ static sr_status build_plan(Plan *pl, sr_problem *const *probs, int n, bool plai
         const double cb = (double)fb.fft_L * fb.fft_L * (fb.fft_n_chunks + 1);
         return ca > cb;
     });
+    {  // shorter comb-band blocks for tables too small to fill the GPU with 16-row ones
+        std::vector<int> Fs, Js, sFs, sJs;
+        for (int i = 0; i < n; ++i) {
+            Fs.push_back(pl->h_fields[i].F);
+            Js.push_back(pl->h_fields[i].J);
+        }
+        for (const FieldDev &sd : sh) {
+            sFs.push_back(sd.F);
+            sJs.push_back(sd.J);
+        }
+        pl->starlet_forms |= starlet_comb_rows_bits(Fs.data(), Js.data(), n, g_num_sms);
+        if (!sh.empty()) pl->sh_starlet_forms |= starlet_comb_rows_bits(sFs.data(), sJs.data(), (int)sh.size(), g_num_sms);
+    }
     pl->n_fft_items = (int)fft_items.size();
     pl->n_fft_fields = (int)fft_fields.size();
     pl->n_items = (int)items.size();
@@ -844,9 +859,8 @@ static int run_eval(Plan *pl, const float *params, float *grad, cudaStream_t st,
         }
     }
     if (pl->n_fft_items > 0) {
-        launch_fft_hgrad_pair(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_pairs, pl->smem_fft,
-                              pl->fft_acc, grad, st);
-        ++n;
+        n += launch_fft_hgrad_pair(pl->d_fields, pl->d_fft_fields, pl->n_fft_fields, pl->max_pairs, pl->smem_fft,
+                                   pl->fft_acc, grad, pl->max_acc_points, g_num_sms, st);
     }
     for (size_t b = 0; b < pl->big_fields.size(); ++b)
         n += launch_big_hgrad(pl->h_fields[pl->big_fields[b]], pl->big_buf[b], grad, st);

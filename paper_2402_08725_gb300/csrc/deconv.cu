@@ -597,19 +597,28 @@ finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ 
     for (int s = threadIdx.x; s < E * M; s += blockDim.x)
         g[s] = sd ? ps_da[fd.ps_slot + s] + pts_g[3 * (sd->ps_slot + s % M)] / (float)E : ps_da[fd.ps_slot + s];
     float *gc = g + (long long)E * M;
-    for (int s = threadIdx.x; s < 2 * M; s += blockDim.x) {
-        const int k = s >> 1, ax = s & 1;
-        double acc = 0.0;
-        if (fd.rot) {  // the centre is u0 + f (R_i c_k + delta_i): d/dc_k = f sum_i R_i^T d/d(centre)
-            for (int i = 0; i < E; ++i) {
-                const float2 r = fd.rot[i];
-                const long long b = 2 * (fd.ps_slot + (long long)i * M + k);
-                const double gx = ps_du[b], gy = ps_du[b + 1];
-                acc += ax == 0 ? (double)r.x * gx + (double)r.y * gy : -(double)r.y * gx + (double)r.x * gy;
+    // d/dc_k sums over the epochs: one warp per (source, axis), lanes striding the epochs, then a
+    // fixed shuffle tree (many epochs per field keep their loads in flight together)
+    {
+        const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+        for (int s = threadIdx.x >> 5; s < 2 * M; s += nwarp) {
+            const int k = s >> 1, ax = s & 1;
+            double acc = 0.0;
+            if (fd.rot) {  // the centre is u0 + f (R_i c_k + delta_i): d/dc_k = f sum_i R_i^T d/d(centre)
+                for (int i = lane; i < E; i += 32) {
+                    const float2 r = fd.rot[i];
+                    const long long b = 2 * (fd.ps_slot + (long long)i * M + k);
+                    const double gx = ps_du[b], gy = ps_du[b + 1];
+                    acc += ax == 0 ? (double)r.x * gx + (double)r.y * gy : -(double)r.y * gx + (double)r.x * gy;
+                }
+            } else {
+                for (int i = lane; i < E; i += 32) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
             }
-        } else
-            for (int i = 0; i < E; ++i) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
-        gc[s] = sd ? (float)(f * acc + (double)pts_g[3 * (sd->ps_slot + k) + 1 + ax]) : (float)(f * acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0)
+                gc[s] = sd ? (float)(f * acc + (double)pts_g[3 * (sd->ps_slot + k) + 1 + ax]) : (float)(f * acc);
+        }
     }
     float *gd = gc + 2 * M;
     for (int s = threadIdx.x; s < 2 * E; s += blockDim.x) {

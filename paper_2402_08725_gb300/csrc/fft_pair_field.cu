@@ -138,9 +138,38 @@ __device__ __noinline__ void hhat_pair(const FieldDev &fd, const float *__restri
 // dL/dh for the transform fields: the chunk accumulators of two phases summed in a fixed order,
 // joined as Z = A_a + i A_b on the whole plane (Hermitian extension of each half spectrum),
 // transformed back, plus the prior's gradient.
+// The sum over a field's work items of their adjoint accumulators at one spectral point p (phase,
+// row ky, column kx < H), in the order of hgrad_pair's own loop (four interleaved partial sums,
+// item c into c mod 4, combined in a fixed order), written over the first item's accumulator: one
+// thread per point, so that fields with many items are summed by many blocks.
+template <int L>
+__device__ __forceinline__ void acc_reduce(const FieldDev &fd, float2 *__restrict__ acc_all, int p) {
+    using G = Pr<L>;
+    constexpr int H = G::H, HP = G::HP, LHP = L * HP;
+    const int nph = fd.f * fd.f;
+    if (p >= nph * L * H) return;
+    const int ph = p / (L * H), r = p - ph * (L * H), ky = r / H, kx = r - ky * H;
+    const int n_chunks = fd.fft_n_chunks;
+    const long long cs = (long long)nph * LHP;
+    float2 *ac = acc_all + fd.fft_acc_off + (long long)ph * LHP + ky * HP + kx;
+    float2 p4[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p4[u] = make_float2(0.f, 0.f);
+    int c = 0;
+    for (; c + 4 <= n_chunks; c += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (c + u < n_chunks) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
+    ac[0] = cadd(cadd(p4[0], p4[1]), cadd(p4[2], p4[3]));
+}
+
+// reduced: the items' accumulators were already summed into the first item's (acc_reduce)
 template <int L>
 __device__ __noinline__ void hgrad_pair(const FieldDev &fd, const float2 *__restrict__ acc_all,
-                                        float *__restrict__ grad, int q) {
+                                        float *__restrict__ grad, int q, bool reduced) {
     using G = Pr<L>;
     constexpr int P = G::P, H = G::H, HP = G::HP, LHP = L * HP;
     float2 *Z = pr_dyn, *TWL = Z + G::ZN;
@@ -148,7 +177,7 @@ __device__ __noinline__ void hgrad_pair(const FieldDev &fd, const float2 *__rest
     const int f = fd.f, N = fd.N, F = fd.F, nph = f * f;
     const int pa = 2 * q, pb = 2 * q + 1;
     const bool hasb = pb < nph;
-    const int n_chunks = fd.fft_n_chunks;
+    const int n_chunks = reduced ? 1 : fd.fft_n_chunks;
     const long long cs = (long long)nph * LHP;
     const float2 *base = acc_all + fd.fft_acc_off;
     for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) {
@@ -223,16 +252,34 @@ fft_hhat_pair_kernel(const FieldDev *__restrict__ fields, const int *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(256)
+fft_acc_reduce_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
+                      float2 *__restrict__ acc_all) {
+    const FieldDev &fd = fields[fft_fields[blockIdx.y]];
+    if (fd.fft_n_chunks <= 1) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    switch (fd.fft_L) {
+#define SR_PR_RCASE(LL)                  \
+    case LL:                             \
+        acc_reduce<LL>(fd, acc_all, p);  \
+        break;
+        SR_PR_SIZES(SR_PR_RCASE)
+#undef SR_PR_RCASE
+        default:
+            break;
+    }
+}
+
 __global__ void __launch_bounds__(kFftThreads, 1)
 fft_hgrad_pair_kernel(const FieldDev *__restrict__ fields, const int *__restrict__ fft_fields,
-                      const float2 *__restrict__ acc_all, float *__restrict__ grad) {
+                      const float2 *__restrict__ acc_all, float *__restrict__ grad, int reduced) {
     const FieldDev &fd = fields[fft_fields[blockIdx.y]];
     const int q = blockIdx.x;
     if (2 * q >= fd.f * fd.f) return;
     switch (fd.fft_L) {
-#define SR_PR_GCASE(LL)                             \
-    case LL:                                        \
-        hgrad_pair<LL>(fd, acc_all, grad, q);       \
+#define SR_PR_GCASE(LL)                                      \
+    case LL:                                                 \
+        hgrad_pair<LL>(fd, acc_all, grad, q, reduced != 0);  \
         break;
         SR_PR_SIZES(SR_PR_GCASE)
 #undef SR_PR_GCASE
@@ -286,9 +333,16 @@ void launch_fft_hhat_pair(const FieldDev *fields, const int *fft_fields, int n_f
     fft_hhat_pair_kernel<<<dim3(max_pairs, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, params, hhat);
 }
 
-void launch_fft_hgrad_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
-                           const float2 *acc, float *grad, cudaStream_t st) {
-    fft_hgrad_pair_kernel<<<dim3(max_pairs, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, acc, grad);
+int launch_fft_hgrad_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
+                          float2 *acc, float *grad, int max_points, int n_sms, cudaStream_t st) {
+    // with fewer (field, phase pair) blocks than SMs, the sums over the work items run first on
+    // one thread per spectral point; the result is the same either way (same order of the sums)
+    const bool reduce = (long long)n_fft_fields * max_pairs < n_sms;
+    if (reduce)
+        fft_acc_reduce_kernel<<<dim3((max_points + 255) / 256, n_fft_fields), 256, 0, st>>>(fields, fft_fields, acc);
+    fft_hgrad_pair_kernel<<<dim3(max_pairs, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, acc, grad,
+                                                                                     reduce ? 1 : 0);
+    return reduce ? 2 : 1;
 }
 
 }  // namespace sr

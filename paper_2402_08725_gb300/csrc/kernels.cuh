@@ -54,8 +54,12 @@ sr_status launch_fft_kappa_pair_batch(const FieldDev *fields, const int2 *items,
                                       cudaStream_t st);
 void launch_fft_hhat_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
                           const float *params, float2 *hhat, cudaStream_t st);
-void launch_fft_hgrad_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
-                           const float2 *acc, float *grad, cudaStream_t st);
+// dL/dh of the transform fields: one block per (field, pair of phases) adds the work items'
+// accumulators and transforms back; when those blocks are fewer than n_sms, the sums run first
+// on one thread per spectral point into the first item's accumulator (max_points = the largest
+// f^2 L (L/2 + 1) of the fields).  Returns the number of launches.
+int launch_fft_hgrad_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
+                          float2 *acc, float *grad, int max_points, int n_sms, cudaStream_t st);
 sr_status occupancy_fft_pair(int smem, int *blocks);
 void launch_fft_chunks_pair(const FieldDev *fields, const int4 *items, int n_items, int *counter, const float *params,
                             const float2 *hhat, float2 *acc, double *chi_part, double *se_part, float *ps_da,
@@ -105,7 +109,13 @@ void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long lon
 // 1 << form set for every form of the table's fields, and kStarletMapBit when some field has a
 // per-coefficient weight map.  Returns the number of launches issued.
 constexpr int kStarletMapBit = 16;
+// bits of forms that shorten the comb-band blocks to 4 or 8 rows (starlet_comb_rows_bits)
+constexpr int kStarletRows4 = 32, kStarletRows8 = 64;
 int starlet_field_form(int F, int J);
+int starlet_comb_rows_of(int forms);
+int starlet_comb_rows_bits(const int *F, const int *J, int n, int n_sms);
+// forms of a table holding one field (with or without a weight map)
+int starlet_forms_single(int F, int J, bool map);
 int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st);
 

@@ -223,7 +223,7 @@ extern "C" sr_status sr_loss_and_grad_noalloc(const sr_problem_desc *desc, const
     launch_fwd(d_fd, items, (int)n_items, counters, params_dev, ebuf, chi, se, grid_fwd, smem_fwd, st);
     launch_adj(d_fd, items, (int)n_items, counters + 1, ebuf, gbuf, grid_adj, smem_adj, st);
     if (E * M > 0) launch_psgrad(d_fd, ps, E * M, params_dev, gbuf, da, du, st);
-    launch_starlet(d_fd, 1, F, 1 << starlet_field_form(F, J), chunks, n_chunks, J, params_dev, l1, st);
+    launch_starlet(d_fd, 1, F, starlet_forms_single(F, J, false), chunks, n_chunks, J, params_dev, l1, st);
     launch_hgrad(d_fd, chunks, n_chunks, gbuf, grad_dev, params_dev, st);
     launch_finalize(d_fd, 1, chi, se, l1, da, du, grad_dev, loss_field, loss_dev, st);
     // a sigma that is NaN or <= 0 has no inverse variance: the loss reports it as NaN

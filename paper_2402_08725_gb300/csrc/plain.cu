@@ -230,7 +230,7 @@ int launch_plain_eval(const FieldDev *fields, const FieldDev &hf, const float *s
         if (hf.M > 0) plain_psgrad_kernel<<<1, 32 * hf.M, 0, st>>>(fields, params, i, pb.gi, ps_da, ps_du);
         n += hf.M > 0 ? 6 : 5;
     }
-    const int forms = (1 << starlet_field_form(hf.F, hf.J)) | (hf.Wmap ? kStarletMapBit : 0);
+    const int forms = starlet_forms_single(hf.F, hf.J, hf.Wmap != nullptr);
     n += launch_starlet(fields, 1, hf.F, forms, chunks, n_chunks, hf.J, params, l1_part, st);
     plain_hgrad_kernel<<<gF, 256, 0, st>>>(fields, pb.gsum, grad);
     ++n;

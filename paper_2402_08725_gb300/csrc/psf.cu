@@ -272,7 +272,7 @@ int launch_psf_eval(const FieldDev *fields, const FieldDev &hf, const ChunkItem 
                                                                  pb.n_dchunks); ++n;
     psf_adj_col_kernel<<<gS, 256, 0, st>>>(fields, params, pb.ebuf); ++n;
     psf_adj_row_kernel<<<gS, 256, 0, st>>>(fields, params); ++n;
-    const int forms = (1 << starlet_field_form(hf.F, hf.J)) | (hf.Wmap ? kStarletMapBit : 0);
+    const int forms = starlet_forms_single(hf.F, hf.J, hf.Wmap != nullptr);
     n += launch_starlet(fields, 1, hf.F, forms, chunks, n_chunks, hf.J, params, l1_part, st);
     psf_reduce_kernel<<<gF, 256, 0, st>>>(fields, params, grad, pb.ab_part); ++n;
     psf_finalize_kernel<<<1, 256, 0, st>>>(fields, params, grad, pb.star_part, pb.n_dchunks, pb.ab_part, gF,

@@ -72,17 +72,22 @@ __host__ __device__ inline bool starlet_tiled(int F, int J) {
 // Comb bands: at level j (step s = 2^j) the rows congruent to rho modulo s form a comb whose rows
 // are s apart, which is exactly the spacing of the level's column taps; a block takes 16
 // consecutive rows of one comb and stages 20 (two more on each side) instead of 16 + 4 s.
-constexpr int kCombRows = 16;
+constexpr int kCombRows = 16;  // rows of a comb per block (fewer for small tables, see comb_rows)
 constexpr int kCombMaxF = kBandSmemBytes / ((2 * kCombRows + 4) * (int)sizeof(float));  // adjoint budget
-// Blocks of level j: s combs of ceil(ceil(F / s) / 16) chunks each.
-__host__ __device__ inline int comb_chunks(int F, int s) { return ((F + s - 1) / s + kCombRows - 1) / kCombRows; }
+// Blocks of level j: s combs of ceil(ceil(F / s) / cr) chunks each.
+__host__ __device__ inline int comb_chunks(int F, int s, int cr = kCombRows) {
+    return ((F + s - 1) / s + cr - 1) / cr;
+}
+// The prior's partial sums of a comb-band level are kept per group of 4 consecutive comb rows
+// (whatever the rows per block), so that the sum does not depend on the block shape.
+constexpr int kCombGroup = 4;
 // A field runs its levels as comb bands when a row of the adjoint's staging fits the budget and
-// every level's blocks fit the prior partial-sum slots of a level (one per 256 pixels).
+// every level's row groups fit the prior partial-sum slots of a level (one per 256 pixels).
 __host__ __device__ inline bool starlet_combed(int F, int J) {
     if (F > kCombMaxF) return false;
     const int slots = (F * F + 255) / 256;
     for (int j = 0; j <= J - 2; ++j)
-        if ((1 << j) * comb_chunks(F, 1 << j) > slots) return false;
+        if ((1 << j) * comb_chunks(F, 1 << j, kCombGroup) > slots) return false;
     return true;
 }
 // 0 bands, 1 tiles, 2 passes, 3 comb bands
@@ -341,23 +346,23 @@ starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     }
 }
 
-// Forward level j as comb bands: block b takes rows y_t = rho + s (k0 + t), t < 16, of comb rho,
-// filters rows rho + s (k0 - 2 + i), i < 20 (mirrored), along x into shared memory, then along
+// Forward level j as comb bands: block b takes rows y_t = rho + s (k0 + t), t < cr, of comb rho,
+// filters rows rho + s (k0 - 2 + i), i < cr + 4 (mirrored), along x into shared memory, then along
 // y: each output row's five taps are staged rows t .. t + 4.  The same values, in the same order,
-// as the bands.  Block (b, field), b = rho * nk + k0 / 16.
+// as the bands.  Block (b, field), b = rho * nk + k0 / cr.
 template <bool MAP>
 __global__ void __launch_bounds__(256)
 starlet_comb_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
-                        double *__restrict__ l1_part, int j) {
+                        double *__restrict__ l1_part, int j, int cr) {
     extern __shared__ float sb[];
-    __shared__ float2 s_red[8];
+    __shared__ float2 s_row[kCombRows];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
     if (j > J - 2 || starlet_form(F, J) != 3) return;
-    const int s = 1 << j, nk = comb_chunks(F, s), b = blockIdx.x;
+    const int s = 1 << j, nk = comb_chunks(F, s, cr), b = blockIdx.x;
     if (b >= s * nk) return;
-    const int rho = b / nk, k0 = (b - rho * nk) * kCombRows;
-    const int Tr = max(0, min(kCombRows, (F - rho + s - 1) / s - k0));  // rows of the comb in the grid
+    const int rho = b / nk, k0 = (b - rho * nk) * cr;
+    const int Tr = max(0, min(cr, (F - rho + s - 1) / s - k0));  // rows of the comb in the grid
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const float *cj = c_plane(fd, params, j);
     const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr;
@@ -374,7 +379,6 @@ starlet_comb_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     }
     __syncthreads();
     float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
-    FSum l1 = fsum_zero();
     for (int t = warp; t < Tr; t += nwarp) {
         const long long ro = (long long)(rho + s * (k0 + t)) * F;
         float l1_row = 0.f;
@@ -385,19 +389,22 @@ starlet_comb_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
             cn[ro + x] = acc;
             l1_row += fabsf(cj[ro + x] - acc) * wmap_w(wm1, ro + x);
         }
-        l1 = fsum_add(l1, l1_row);
+        const FSum r = fsum_warp(FSum{l1_row, 0.f});  // the row's sum (lanes in a fixed tree)
+        if (lane == 0) s_row[t] = make_float2(r.hi, r.lo);
     }
-    l1 = fsum_warp(l1);
-    if (lane == 0) s_red[warp] = make_float2(l1.hi, l1.lo);
     __syncthreads();
+    // the partial of each group of 4 comb rows (its rows' sums in order) into the group's slot
+    const int nk4 = comb_chunks(F, s, kCombGroup), g0 = k0 / kCombGroup;
     const long long base = fd.l1_slot + (long long)j * fd.n_chunks;
-    if (threadIdx.x == 0) {
-        FSum tt = fsum_zero();
-        for (int w = 0; w < nwarp; ++w) tt = fsum_add(tt, FSum{s_red[w].x, s_red[w].y});
-        l1_part[base + b] = (double)fd.lambda * (double)fd.Wd[j] * fsum_value(tt);
+    for (int g = threadIdx.x; g < cr / kCombGroup; g += blockDim.x) {
+        if (g0 + g >= nk4) break;
+        FSum a = fsum_zero();
+        for (int t = kCombGroup * g; t < min(kCombGroup * (g + 1), Tr); ++t)
+            a = fsum_add(a, FSum{s_row[t].x, s_row[t].y});
+        l1_part[base + (long long)rho * nk4 + g0 + g] = (double)fd.lambda * (double)fd.Wd[j] * fsum_value(a);
     }
     if (b == 0)  // the level's remaining partial-sum slots stay zero
-        for (int c = s * nk + threadIdx.x; c < fd.n_chunks; c += blockDim.x) l1_part[base + c] = 0.0;
+        for (int c = s * nk4 + threadIdx.x; c < fd.n_chunks; c += blockDim.x) l1_part[base + c] = 0.0;
 }
 
 // Adjoint level j as comb bands: T_j = gamma_{j+1} + Row_j^T Col_j^T V_{j+1} on the comb rows of
@@ -407,18 +414,18 @@ starlet_comb_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
 // same values, in the same order, as the bands.
 template <bool MAP>
 __global__ void __launch_bounds__(256, 4)  // at most 64 registers: four blocks per SM
-starlet_comb_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
+starlet_comb_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j, int cr) {
     extern __shared__ float sb[];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
     if (j > J - 2 || starlet_form(F, J) != 3) return;
-    const int s = 1 << j, nk = comb_chunks(F, s), b = blockIdx.x;
+    const int s = 1 << j, nk = comb_chunks(F, s, cr), b = blockIdx.x;
     if (b >= s * nk) return;
-    const int rho = b / nk, k0 = (b - rho * nk) * kCombRows;
-    const int Tr = max(0, min(kCombRows, (F - rho + s - 1) / s - k0));
+    const int rho = b / nk, k0 = (b - rho * nk) * cr;
+    const int Tr = max(0, min(cr, (F - rho + s - 1) / s - k0));
     if (Tr == 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    float *vb = sb, *tb = sb + (long long)(kCombRows + 4) * F;
+    float *vb = sb, *tb = sb + (long long)(cr + 4) * F;
     const float lw1 = fd.lambda * fd.Wd[j];
     const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr, *wm0 = MAP ? wmap_plane(fd, j - 1) : nullptr;
     const float *cj = c_plane(fd, params, j), *cn = fd.starlet + (long long)j * F * F;  // c_j, c_{j+1}
@@ -598,6 +605,31 @@ starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
 
 int starlet_field_form(int F, int J) { return starlet_form(F, J); }
 
+int starlet_forms_single(int F, int J, bool map) {
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                       cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    const int forms = (1 << starlet_form(F, J)) | (map ? kStarletMapBit : 0);
+    return forms | starlet_comb_rows_bits(&F, &J, 1, sms);
+}
+
+int starlet_comb_rows_of(int forms) { return (forms & kStarletRows8) ? 8 : (forms & kStarletRows4) ? 4 : kCombRows; }
+
+// Rows per comb block for a table of comb-band fields (F, J of each): 16, or 8 or 4 when the
+// table's level-0 blocks would not fill twice the SMs.  The results do not depend on it (the
+// prior's partial sums are kept per 4-row group).  Returns the forms bit to add (0 for 16 rows).
+int starlet_comb_rows_bits(const int *F, const int *J, int n, int n_sms) {
+    long long blocks = 0;
+    for (int i = 0; i < n; ++i)
+        if (starlet_form(F[i], J[i]) == 3) blocks += comb_chunks(F[i], 1);
+    if (blocks == 0 || blocks >= 2LL * n_sms) return 0;
+    return 2 * blocks >= 2LL * n_sms ? kStarletRows8 : kStarletRows4;
+}
+
 int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st) {
     static bool configured = false;
@@ -618,12 +650,13 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
     }
     const bool bands = (forms & 1) != 0, tiles = (forms & 2) != 0, passes = (forms & 4) != 0;
     const bool combs = (forms & 8) != 0, map = (forms & kStarletMapBit) != 0;
-    // comb bands: s combs of comb_chunks blocks at level j; staging of 20 (forward) or 36 (adjoint)
-    // rows of the widest comb-band grid
+    // comb bands: s combs of comb_chunks blocks at level j; staging of cr + 4 (forward) or
+    // 2 cr + 4 (adjoint) rows of the widest comb-band grid
+    const int cr = starlet_comb_rows_of(forms);
     const int Fc = std::min(Fmax, kCombMaxF);
-    auto cgrid = [&](int j) { return dim3((unsigned)((1 << j) * comb_chunks(Fc, 1 << j)), n_fields); };
-    const int comb_fwd_smem = (kCombRows + 4) * Fc * (int)sizeof(float);
-    const int comb_adj_smem = (2 * kCombRows + 4) * Fc * (int)sizeof(float);
+    auto cgrid = [&](int j) { return dim3((unsigned)((1 << j) * comb_chunks(Fc, 1 << j, cr)), n_fields); };
+    const int comb_fwd_smem = (cr + 4) * Fc * (int)sizeof(float);
+    const int comb_adj_smem = (2 * cr + 4) * Fc * (int)sizeof(float);
     auto tgrid = [&](int j) {
         const int tr = tile_rows(j);
         return dim3((unsigned)(((Fmax + tr - 1) / tr) * ((Fmax + kTileCols - 1) / kTileCols)), n_fields);
@@ -650,9 +683,9 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
         }
         if (combs) {
             if (map)
-                starlet_comb_fwd_kernel<true><<<cgrid(j), 256, comb_fwd_smem, st>>>(fields, params, l1_part, j);
+                starlet_comb_fwd_kernel<true><<<cgrid(j), 256, comb_fwd_smem, st>>>(fields, params, l1_part, j, cr);
             else
-                starlet_comb_fwd_kernel<false><<<cgrid(j), 256, comb_fwd_smem, st>>>(fields, params, l1_part, j);
+                starlet_comb_fwd_kernel<false><<<cgrid(j), 256, comb_fwd_smem, st>>>(fields, params, l1_part, j, cr);
             ++n;
         }
         if (tiles) {
@@ -679,9 +712,9 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
         }
         if (combs) {
             if (map)
-                starlet_comb_adj_kernel<true><<<cgrid(j), 256, comb_adj_smem, st>>>(fields, params, j);
+                starlet_comb_adj_kernel<true><<<cgrid(j), 256, comb_adj_smem, st>>>(fields, params, j, cr);
             else
-                starlet_comb_adj_kernel<false><<<cgrid(j), 256, comb_adj_smem, st>>>(fields, params, j);
+                starlet_comb_adj_kernel<false><<<cgrid(j), 256, comb_adj_smem, st>>>(fields, params, j, cr);
             ++n;
         }
         if (tiles) {
