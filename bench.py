@@ -196,9 +196,10 @@ def chunk_source_hash():
 
 
 def profiled_traffic():
-    """DRAM bytes (read + write) of one full-size config-4 launch of the transform chunk kernel,
-    from the committed ncu summary, or None if that summary was taken on another version of the
-    kernel's source (its recorded hash differs)."""
+    """DRAM bytes (read + write) of one config-4 launch of the transform chunk kernel, from the
+    committed ncu summary (a 24-field capture scaled by the epoch-pixels to the full batch), or
+    None if that summary was taken on another version of the kernel's source (its recorded hash
+    differs)."""
     import re
     try:
         txt = open(CHUNK_PROFILE).read()
@@ -724,6 +725,9 @@ def run_ours(args):
                     "frac": round(ach / hbm, 4), "traffic": profiled_traffic() if full else None,
                     "kernel": "fft_hhat_pair_kernel + fft_chunk_pair_kernel",
                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+            if roof["traffic"] is not None:
+                roof["traffic_source"] = ("fft_chunk_pair_kernel DRAM bytes per launch: ncu on the first 24 fields, "
+                                          "scaled by the epoch-pixels (profiles/fft_chunk_pair_kernel_config4.md)")
         else:
             fl = fwd_flops(direct_fields)
             dom_ms, dom = (avg_f, "fwd") if avg_f >= avg_a else (avg_a, "adj")

@@ -107,9 +107,16 @@ __device__ __forceinline__ float *t_plane(const FieldDev &fd, int j) {
     return fd.starlet + (long long)(fd.J + (j & 1)) * fd.F * fd.F;
 }
 
-// (H^T y)[n] along one axis: sum over taps m and over the mirror preimages of n.
+// (H^T y)[n] along one axis: sum over taps m and over the mirror preimages of n.  Away from the
+// edges (2 step < n < F - 1 - 2 step) every tap is direct and no preimage exists: the same sum
+// without the tests.
 __device__ __forceinline__ float adj_1d(const float *__restrict__ y, int n, int F, int step, int stride) {
     float acc = 0.f;
+    if (n > 2 * step && n < F - 1 - 2 * step) {
+#pragma unroll
+        for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * y[(long long)(n - m * step) * stride];
+        return acc;
+    }
 #pragma unroll
     for (int m = -2; m <= 2; ++m) {
         const float b = kB3[m + 2];
@@ -248,8 +255,13 @@ starlet_band_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
         float *dst = sb + (long long)i * F;
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
+            if (x >= 2 * s && x <= F - 1 - 2 * s) {  // all taps inside: no mirror
 #pragma unroll
-            for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[x + n * s];
+            } else {
+#pragma unroll
+                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+            }
             dst[x] = acc;
         }
     }
@@ -316,8 +328,15 @@ starlet_band_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     __syncthreads();
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const int y = y0 + yy;
+        const bool inner = y > 2 * s && y < F - 1 - 2 * s;  // direct taps only (no mirror preimage)
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
+            if (inner) {
+#pragma unroll
+                for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * vb[(long long)(y - m * s - vlo) * F + x];
+                tb[(long long)yy * F + x] = acc;
+                continue;
+            }
 #pragma unroll
             for (int m = -2; m <= 2; ++m) {
                 const float bm = kB3[m + 2];
@@ -372,8 +391,13 @@ starlet_comb_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
         float *dst = sb + (long long)i * F;
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
+            if (x >= 2 * s && x <= F - 1 - 2 * s) {  // all taps inside: no mirror
 #pragma unroll
-            for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[x + n * s];
+            } else {
+#pragma unroll
+                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+            }
             dst[x] = acc;
         }
     }
@@ -444,8 +468,15 @@ starlet_comb_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     __syncthreads();
     for (int t = warp; t < Tr; t += nwarp) {
         const int y = rho + s * (k0 + t);
+        const bool inner = y > 2 * s && y < F - 1 - 2 * s;  // direct taps only (no mirror preimage)
         for (int x = lane; x < F; x += 32) {
             float acc = 0.f;
+            if (inner) {
+#pragma unroll
+                for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * vb[(long long)(t - m + 2) * F + x];
+                tb[(long long)t * F + x] = acc;
+                continue;
+            }
 #pragma unroll
             for (int m = -2; m <= 2; ++m) {
                 const float bm = kB3[m + 2];
@@ -501,8 +532,13 @@ starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
         for (int xx = lane; xx < Tc; xx += 32) {
             const int x = x0 + xx;
             float acc = 0.f;
+            if (x >= 2 * s && x <= F - 1 - 2 * s) {  // all taps inside: no mirror
 #pragma unroll
-            for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[x + n * s];
+            } else {
+#pragma unroll
+                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * row[mirror_at(x + n * s, F)];
+            }
             dst[xx] = acc;
         }
     }
@@ -572,8 +608,15 @@ starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     __syncthreads();
     for (int yy = warp; yy < Tr; yy += nwarp) {
         const int y = y0 + yy;
+        const bool inner = y > 2 * s && y < F - 1 - 2 * s;  // direct taps only (no mirror preimage)
         for (int xx = lane; xx < W; xx += 32) {
             float acc = 0.f;
+            if (inner) {
+#pragma unroll
+                for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * vb[(long long)(y - m * s - vlo) * WP + xx];
+                tb[(long long)yy * WP + xx] = acc;
+                continue;
+            }
 #pragma unroll
             for (int m = -2; m <= 2; ++m) {
                 const float bm = kB3[m + 2];
