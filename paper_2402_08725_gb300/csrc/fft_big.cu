@@ -509,12 +509,13 @@ __global__ void __launch_bounds__(kBgThreads) big_rows_kernel(FieldDev fd, float
 // sources whose windows overlap write the same value twice.
 // ---------------------------------------------------------------------------------------------
 constexpr int kWinThreads = 256;
+constexpr int kWinRun = 6;  // window positions per thread and pass (the whole row at f = 3)
 
 __global__ void __launch_bounds__(kWinThreads) big_window_adj_kernel(FieldDev fd, const float *__restrict__ params,
                                                                      const float *__restrict__ ebuf,
                                                                      float *__restrict__ gbuf) {
     extern __shared__ __align__(16) float wsm[];
-    __shared__ float s_part[kWinThreads];
+    __shared__ float s_part[kWinThreads * kWinRun];
     const int f = fd.f, N = fd.N, F = fd.F, M = fd.M, E = fd.E, Tk = fd.Tk, tlo = fd.tau_lo, nph = f * f;
     const int b = blockIdx.x;
     const int ph = b % nph, k = (b / nph) % M, e = b / (nph * M);
@@ -545,25 +546,44 @@ __global__ void __launch_bounds__(kWinThreads) big_window_adj_kernel(FieldDev fd
         X[t] = (my >= 0 && my < N && mx >= 0 && mx < N) ? ep[(long long)my * N + mx] : 0.f;
     }
     __syncthreads();
-    const int groups = max(1, min(kWinThreads / npos, Tk));
-    const int pos = threadIdx.x % npos, grp = threadIdx.x / npos;
-    const int py = pos / nxp, px = pos - py * nxp;
-    float part = 0.f;
-    if (grp < groups) {
-        for (int ty = grp; ty < Tk; ty += groups) {
-            const float *xr = X + (py + ty) * pw + px, *kr = K + ty * Tk;
-            float rs = 0.f;
-            for (int tx = 0; tx < Tk; ++tx) rs = fmaf(kr[tx], xr[tx], rs);
-            part += rs;
+    // thread (py, grp): row py of the positions, kernel rows ty = grp mod groups, kWinRun
+    // consecutive positions at a time (x values slide through registers: two shared loads per
+    // kWinRun multiply-adds); the groups' partials are added in order per position
+    const int groups = max(1, min(kWinThreads / nyp, Tk));
+    const int py = threadIdx.x % nyp, grp = threadIdx.x / nyp;
+    for (int px0 = 0; px0 < nxp; px0 += kWinRun) {
+        float acc[kWinRun];
+#pragma unroll
+        for (int p = 0; p < kWinRun; ++p) acc[p] = 0.f;
+        if (grp < groups) {
+            for (int ty = grp; ty < Tk; ty += groups) {
+                const float *xr = X + (py + ty) * pw + px0, *kr = K + ty * Tk;
+                // X rows are pw = nxp + Tk - 1 wide: positions beyond nxp read at most kWinRun - 1
+                // values past the row, inside the staged patch or its padding (never used)
+                float v[kWinRun];
+#pragma unroll
+                for (int p = 0; p < kWinRun - 1; ++p) v[p + 1] = xr[p];
+                for (int tx = 0; tx < Tk; ++tx) {
+#pragma unroll
+                    for (int p = 0; p < kWinRun - 1; ++p) v[p] = v[p + 1];
+                    v[kWinRun - 1] = xr[tx + kWinRun - 1];
+                    const float kv = kr[tx];
+#pragma unroll
+                    for (int p = 0; p < kWinRun; ++p) acc[p] = fmaf(kv, v[p], acc[p]);
+                }
+            }
         }
-    }
-    s_part[threadIdx.x] = part;
-    __syncthreads();
-    if (threadIdx.x < npos) {
-        float g = 0.f;
-        for (int u = 0; u < groups; ++u) g += s_part[u * npos + threadIdx.x];
-        const int my = my0 + threadIdx.x / nxp, mx = mx0 + threadIdx.x % nxp;
-        gbuf[fd.gbuf_off + ((long long)e * nph + ph) * N * N + (long long)my * N + mx] = g;
+#pragma unroll
+        for (int p = 0; p < kWinRun; ++p) s_part[threadIdx.x * kWinRun + p] = acc[p];
+        __syncthreads();
+        for (int q = threadIdx.x; q < nyp * kWinRun; q += blockDim.x) {
+            const int qy = q / kWinRun, p = q - qy * kWinRun, qx = px0 + p;
+            if (qx >= nxp) continue;
+            float g = 0.f;
+            for (int u = 0; u < groups; ++u) g += s_part[(u * nyp + qy) * kWinRun + p];
+            gbuf[fd.gbuf_off + ((long long)e * nph + ph) * N * N + (long long)(my0 + qy) * N + (mx0 + qx)] = g;
+        }
+        __syncthreads();
     }
 }
 
@@ -598,7 +618,9 @@ int fft_big_next(int need) {
 
 int fft_big_window_smem(int Tk, int f) {
     const int np = kWin / f + 1;
-    return (Tk * Tk + (np + Tk - 1) * (np + Tk - 1)) * (int)sizeof(float);
+    // the kernel and the patch, and kWinRun floats past the patch that the last row's sliding
+    // window reads for positions beyond the row (their sums are never used)
+    return (Tk * Tk + (np + Tk - 1) * (np + Tk - 1) + kWinRun) * (int)sizeof(float);
 }
 
 sr_status configure_fft_big(int optin) {
