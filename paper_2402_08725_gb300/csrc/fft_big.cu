@@ -167,36 +167,57 @@ __global__ void __launch_bounds__(kBgThreads) big_load_rows_kernel(FieldDev fd, 
         s_rowmask[r][w] = m;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < kBgRows * nx; t += blockDim.x) {
-        const int r = t / nx, x = t - r * nx;
-        const int y = y0 + r;
-        float2 v = make_float2(0.f, 0.f);
-        if (y < ny) {
-            if (mode == 1) {
+    if (mode == 1) {
+        for (int t = threadIdx.x; t < kBgRows * nx; t += blockDim.x) {
+            const int r = t / nx, x = t - r * nx;
+            const int y = y0 + r;
+            float2 v = make_float2(0.f, 0.f);
+            if (y < ny) {
                 const float *ka = fd.kappa + ((long long)e * nph + pa) * fd.Tk * fd.Tk + y * fd.Tk + x;
                 v = make_float2(ka[0], hasb ? ka[fd.Tk * fd.Tk] : 0.f);
-            } else {
-                float val[2] = {0.f, 0.f};
-#pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    const int ph = w ? pb : pa;
-                    if (w == 1 && !hasb) break;
-                    const int phy = ph / f, phx = ph - phy * f;
-                    const int uy = f * y + phy, ux = f * x + phx;
-                    float s = hpar[(long long)uy * F + ux];
-                    // the sources whose window holds the pixel, in index order
-                    for (unsigned long long m = s_rowmask[r][w]; m; m &= m - 1) {
-                        const int k = __ffsll((long long)m) - 1;
-                        if ((unsigned)(ux - s_win[k].x) < (unsigned)kWin)
-                            s += s_src[k].z * gauss2(src_offset(ux, F, f, s_src[k].x, dpar[0]),
-                                                     src_offset(uy, F, f, s_src[k].y, dpar[1]));
-                    }
-                    val[w] = s;
-                }
-                v = make_float2(val[0], val[1]);
             }
+            Z[r * G::RW + bpx<L>(x)] = v;
         }
-        Z[r * G::RW + bpx<L>(x)] = v;
+    } else {
+        // h at the two phases first (independent loads, several in flight per thread), then the
+        // point sources of the rows that have any, added in index order to the same elements by
+        // the same threads
+        const int pay = pa / f, pax = pa - pay * f, pby = pb / f, pbx = pb - pby * f;
+#pragma unroll 4
+        for (int t = threadIdx.x; t < kBgRows * nx; t += blockDim.x) {
+            const int r = t / nx, x = t - r * nx;
+            const int y = y0 + r;
+            float2 v = make_float2(0.f, 0.f);
+            if (y < ny) {
+                v.x = __ldg(hpar + (long long)(f * y + pay) * F + f * x + pax);
+                if (hasb) v.y = __ldg(hpar + (long long)(f * y + pby) * F + f * x + pbx);
+            }
+            Z[r * G::RW + bpx<L>(x)] = v;
+        }
+        for (int t = threadIdx.x; t < kBgRows * nx; t += blockDim.x) {
+            const int r = t / nx, x = t - r * nx;
+            const int y = y0 + r;
+            if (y >= ny || (s_rowmask[r][0] | s_rowmask[r][1]) == 0ull) continue;
+            float2 &z = Z[r * G::RW + bpx<L>(x)];
+            float val[2] = {z.x, z.y};
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const int ph = w ? pb : pa;
+                if (w == 1 && !hasb) break;
+                const int phy = ph / f, phx = ph - phy * f;
+                const int uy = f * y + phy, ux = f * x + phx;
+                float s = val[w];
+                // the sources whose window holds the pixel, in index order
+                for (unsigned long long m = s_rowmask[r][w]; m; m &= m - 1) {
+                    const int k = __ffsll((long long)m) - 1;
+                    if ((unsigned)(ux - s_win[k].x) < (unsigned)kWin)
+                        s += s_src[k].z * gauss2(src_offset(ux, F, f, s_src[k].x, dpar[0]),
+                                                 src_offset(uy, F, f, s_src[k].y, dpar[1]));
+                }
+                val[w] = s;
+            }
+            z = make_float2(val[0], val[1]);
+        }
     }
     __syncthreads();
     bg_fwd<L>(Z, kBgRows, nx, TWL);
@@ -533,7 +554,6 @@ __global__ void __launch_bounds__(kWinThreads) big_window_adj_kernel(FieldDev fd
     const int my1 = min((wy + kWin - 1 - phy) >= 0 ? (wy + kWin - 1 - phy) / f : -1, N - 1);
     const int nxp = mx1 - mx0 + 1, nyp = my1 - my0 + 1;
     if (nxp <= 0 || nyp <= 0) return;
-    const int npos = nxp * nyp;
     // e patch rows [my0 + tlo, my1 + tlo + Tk), cols [mx0 + tlo, mx1 + tlo + Tk)
     const int pw = nxp + Tk - 1, phh = nyp + Tk - 1;
     float *K = wsm, *X = wsm + Tk * Tk;
