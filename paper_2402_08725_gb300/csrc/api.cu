@@ -170,7 +170,7 @@ struct Plan {
     ChunkItem *d_chunks = nullptr;
     int Jmax = 0;
     int Fmax = 0;               // widest fine grid of the table (the starlet band grid)
-    int starlet_forms = 0;  // 1 << starlet_field_form of every field (bands, tiles, passes)
+    int starlet_forms = 0;  // 1 << starlet_field_form of every field (bands, tiles, comb bands)
     float *ebuf = nullptr, *gbuf = nullptr, *ps_da = nullptr, *ps_du = nullptr;
     double *chi_part = nullptr, *se_part = nullptr, *l1_part = nullptr, *losses = nullptr, *total = nullptr;
     // frequency-domain form
@@ -301,6 +301,9 @@ static sr_status validate_desc(const sr_problem_desc *d) {
     if (d->data_n < 1 || d->data_n > 4096) return fail(SR_ERR_SHAPE, "data_n %d out of range", d->data_n);
     if (d->supersampling < 1 || d->supersampling > 8) return fail(SR_ERR_SHAPE, "supersampling %d out of range", d->supersampling);
     if (d->n_scales < 2 || d->n_scales > kMaxScales) return fail(SR_ERR_SHAPE, "n_scales %d out of range", d->n_scales);
+    if (starlet_field_form(d->data_n * d->supersampling, d->n_scales) == 2)  // not reached for these bounds
+        return fail(SR_ERR_SHAPE, "no starlet form for a %d-pixel grid with %d scales", d->data_n * d->supersampling,
+                    d->n_scales);
     const int F = d->supersampling * d->data_n;
     if (2 * (1 << (d->n_scales - 2)) > F - 1)
         return fail(SR_ERR_SHAPE, "starlet with %d scales needs a grid wider than %d", d->n_scales, F);

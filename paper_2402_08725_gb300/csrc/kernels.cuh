@@ -105,9 +105,10 @@ void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long lon
 // Forward levels then adjoint levels for every field of the table (n_fields of them, grids at
 // most Fmax wide); writes the per-(level, chunk) prior partial sums and leaves T0 = dP/dh in
 // plane J of each field's starlet scratch.  starlet_field_form(F, J) says how a field runs: 0 as
-// row bands, 1 as tiles, 2 as passes over the 256-pixel chunks, 3 as comb bands; forms has bit
-// 1 << form set for every form of the table's fields, and kStarletMapBit when some field has a
-// per-coefficient weight map.  Returns the number of launches issued.
+// row bands, 1 as comb tiles, 3 as comb bands (2: no form, which no valid shape has); forms has
+// bit 1 << form set for every form of the table's fields, and kStarletMapBit when some field has
+// a per-coefficient weight map (chunks and n_chunks are not used).  Returns the number of launches
+// issued.
 constexpr int kStarletMapBit = 16;
 // bits of forms that shorten the comb-band blocks to 4 or 8 rows (starlet_comb_rows_bits)
 constexpr int kStarletRows4 = 32, kStarletRows8 = 64;

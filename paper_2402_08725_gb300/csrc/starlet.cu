@@ -8,10 +8,10 @@
 // and H_j^T = (row pass)^T (column pass)^T is evaluated in gather form: each output sums the
 // (up to three) input positions that the mirror map sends onto it.
 //
-// Scratch per field (planes of F*F floats): c_1..c_{J-1} (planes 0..J-2), a pass buffer (J-1),
+// Scratch per field (planes of F*F floats): c_1..c_{J-1} (planes 0..J-2), a spare plane (J-1),
 // and two T planes (J, J+1) used alternately; T_0 ends in plane J.
 //
-// Four ways to run a level, chosen per field (starlet_form):
+// Three ways to run a level, chosen per field (starlet_form):
 //  * comb bands (most fields): the rows rho, rho + s, rho + 2 s, ... of level j (step s = 2^j)
 //    are one column tap apart, so a block taking 16 consecutive rows of one such comb stages
 //    only 20 input rows at any level; otherwise the same as the bands below, whose arithmetic
@@ -20,15 +20,11 @@
 //    needs (with their 2 * 2^j-row halo) along x into shared memory, then along y.  The adjoint
 //    propagates V_j = T_j - gamma_j instead of T_j (V_{J-1} = -gamma_{J-1} is formed while
 //    loading), so that its column pass reads one plane per tap; the signs are taken from the c
-//    planes once per output pixel.  Same arithmetic, in the same order, as the passes below.
-//  * tiles (fields too wide for a band of whole rows): the same as the bands on tiles of 16 rows
-//    (32 from level 3 on) by 128 columns, with the 2 * 2^j halo along x as well (the forward
-//    reads its row taps from the c plane directly; the adjoint stages the V rows and the
-//    column-adjoint values of the tile's columns and halo, which hold every mirror preimage its
-//    row gather reaches).
-//  * passes (fields too deep for the tiles' shared-memory budget): one launch per pass and level,
-//    every field of the table in 256-pixel chunks; the adjoint first writes V_{j+1} = T_{j+1} -
-//    gamma_{j+1} over T_{j+1} in place (pass 4), so that its column pass reads one plane per tap.
+//    planes once per output pixel.
+//  * tiles (fields too wide for comb bands of whole rows): the comb bands on 128 columns, with
+//    the 2 * 2^j halo along x (the forward reads its row taps from the c plane directly; the
+//    adjoint stages the V rows and the column-adjoint values of the tile's columns and halo,
+//    which hold every mirror preimage its row gather reaches).
 // Fields deeper than a level skip it.
 #include <algorithm>
 
@@ -53,22 +49,6 @@ __host__ __device__ inline bool starlet_banded(int F, int J) {
 constexpr int kTileCols = 128;                 // output columns per block in the tile kernels
 constexpr int kTileSmemBytes = 160 * 1024;     // shared memory of a tile block at its deepest level
 
-// Output rows of a tile at level j: 16, and 32 from level 3 on, where the 2 s-row halos on both
-// sides would otherwise stage several times the tile's own rows.
-__host__ __device__ inline int tile_rows(int j) { return j >= 3 ? 2 * kBandRows : kBandRows; }
-// Shared memory (floats) of the tile kernels at level j: the forward's row-filtered rows
-// (R + 4 s rows of 128 columns), the adjoint's V rows and column-adjoint rows (R + 4 s and R rows
-// of 128 + 4 s columns); s = 2^j, R = tile_rows(j).
-__host__ __device__ inline long long tile_fwd_floats(int j) { return (tile_rows(j) + 4LL * (1 << j)) * kTileCols; }
-__host__ __device__ inline long long tile_adj_floats(int j) {
-    const long long s = 1LL << j;
-    return (2LL * tile_rows(j) + 4 * s) * (kTileCols + 4 * s);
-}
-// Whether a field that does not run as bands runs as tiles: its deepest level fits the budget.
-__host__ __device__ inline bool starlet_tiled(int F, int J) {
-    return !starlet_banded(F, J) && tile_adj_floats(J - 2) * (long long)sizeof(float) <= kTileSmemBytes;
-}
-
 // Comb bands: at level j (step s = 2^j) the rows congruent to rho modulo s form a comb whose rows
 // are s apart, which is exactly the spacing of the level's column taps; a block takes 16
 // consecutive rows of one comb and stages 20 (two more on each side) instead of 16 + 4 s.
@@ -90,7 +70,26 @@ __host__ __device__ inline bool starlet_combed(int F, int J) {
         if ((1 << j) * comb_chunks(F, 1 << j, kCombGroup) > slots) return false;
     return true;
 }
-// 0 bands, 1 tiles, 2 passes, 3 comb bands
+// Tiles (grids too wide for the comb bands): comb rows as above by 128 columns with the 2 s halo
+// along x.  Shared memory (floats) at level j: the forward's row-filtered rows (20 rows of 128),
+// the adjoint's V rows and column-adjoint rows (20 and 16 rows of 128 + 4 s).
+__host__ __device__ inline long long tile_fwd_floats(int) { return (long long)(kCombRows + 4) * kTileCols; }
+__host__ __device__ inline long long tile_adj_floats(int j) {
+    const long long s = 1LL << j;
+    return (2LL * kCombRows + 4) * (kTileCols + 4 * s);
+}
+// Whether a field too wide for the comb bands runs as tiles: its deepest level fits the budget
+// and every level's (4-row group, column tile) partial sums fit the slots of a level.
+__host__ __device__ inline bool starlet_tiled(int F, int J) {
+    if (starlet_banded(F, J) || tile_adj_floats(J - 2) * (long long)sizeof(float) > kTileSmemBytes) return false;
+    const int slots = (F * F + 255) / 256, nbx = (F + kTileCols - 1) / kTileCols;
+    for (int j = 0; j <= J - 2; ++j)
+        if ((long long)(1 << j) * comb_chunks(F, 1 << j, kCombGroup) * nbx > slots) return false;
+    return true;
+}
+
+// 0 bands, 1 tiles, 3 comb bands; 2: none (no shape of at most 8 scales on a grid of at most
+// 32768 pixels comes here; sr_create_problem rejects one that would)
 __host__ __device__ inline int starlet_form(int F, int J) {
     return starlet_combed(F, J) ? 3 : starlet_banded(F, J) ? 0 : starlet_tiled(F, J) ? 1 : 2;
 }
@@ -99,9 +98,6 @@ __device__ __forceinline__ int mirror_at(int t, int F) { return t < 0 ? -t : (t 
 
 __device__ __forceinline__ const float *c_plane(const FieldDev &fd, const float *params, int j) {
     return j == 0 ? params + fd.param_off : fd.starlet + (long long)(j - 1) * fd.F * fd.F;
-}
-__device__ __forceinline__ float *pass_plane(const FieldDev &fd) {
-    return fd.starlet + (long long)(fd.J - 1) * fd.F * fd.F;
 }
 __device__ __forceinline__ float *t_plane(const FieldDev &fd, int j) {
     return fd.starlet + (long long)(fd.J + (j & 1)) * fd.F * fd.F;
@@ -132,103 +128,6 @@ __device__ __forceinline__ float adj_1d(const float *__restrict__ y, int n, int 
         }
     }
     return acc;
-}
-
-// Chunk items (256 pixels each) per block: their loads are in flight together, and the block's
-// set-up (item, field) is paid once per 1024 pixels.
-constexpr int kStarletChunks = 4;
-
-// pass = 0: forward row pass; 1: forward column pass (+ detail plane, L1 partial);
-//        4: V_{j+1} = T_{j+1} - gamma_{j+1} in place; 2: adjoint column pass of V_{j+1};
-//        3: adjoint row pass (+ gamma).
-__global__ void __launch_bounds__(256)
-starlet_pass_kernel(const FieldDev *__restrict__ fields, const ChunkItem *__restrict__ chunks, int n_chunks,
-                    const float *__restrict__ params, double *__restrict__ l1_part, int j, int pass) {
-    __shared__ float2 s_red[kStarletChunks][8];
-    const int step = 1 << j;
-#pragma unroll
-    for (int q = 0; q < kStarletChunks; ++q) {
-        const int c = blockIdx.x * kStarletChunks + q;
-        if (c >= n_chunks) break;  // uniform over the block
-        const ChunkItem ch = chunks[c];
-        const FieldDev &fd = fields[ch.field];
-        if (j > fd.J - 2 || starlet_form(fd.F, fd.J) != 2) continue;  // no level j here, or another form
-        const int F = fd.F;
-        const int px = ch.start + threadIdx.x;
-        const bool valid = px < F * F;
-        const int y = valid ? px / F : 0, x = valid ? px - y * F : 0;
-        const float lw = fd.lambda * fd.Wd[j];
-        const float *wm1 = wmap_plane(fd, j);
-        FSum l1 = fsum_zero();
-        if (pass == 0) {
-            if (valid) {
-                const float *cj = c_plane(fd, params, j) + (long long)y * F;
-                float acc = 0.f;
-#pragma unroll
-                for (int n = -2; n <= 2; ++n) acc += kB3[n + 2] * cj[mirror_at(x + n * step, F)];
-                pass_plane(fd)[px] = acc;
-            }
-        } else if (pass == 1) {
-            if (valid) {
-                const float *tmp = pass_plane(fd);
-                float acc = 0.f;
-#pragma unroll
-                for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * tmp[(long long)mirror_at(y + m * step, F) * F + x];
-                float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
-                cn[px] = acc;
-                const float wv = c_plane(fd, params, j)[px] - acc;
-                l1 = FSum{fabsf(wv) * wmap_w(wm1, px), 0.f};
-            }
-        } else if (pass == 4) {
-            if (valid) {
-                // V_{j+1} = T_{j+1} - gamma_{j+1}, written over T_{j+1} (T_{J-1} = 0)
-                const float *cj = c_plane(fd, params, j);
-                const float *cn = fd.starlet + (long long)j * F * F;
-                const bool has_t = (j + 1) < (fd.J - 1);
-                float *Tn = t_plane(fd, j + 1);
-                const float wv = cj[px] - cn[px];
-                const float lwu = lw * wmap_w(wm1, px);
-                const float g = wv > 0.f ? lwu : (wv < 0.f ? -lwu : 0.f);
-                Tn[px] = (has_t ? Tn[px] : 0.f) - g;
-            }
-        } else if (pass == 2) {
-            if (valid) {
-                // tmp = Col^T V_{j+1}, gathered over the (up to three) rows k whose mirrored taps
-                // land on row y
-                pass_plane(fd)[px] = adj_1d(t_plane(fd, j + 1) + x, y, F, step, F);
-            }
-        } else {
-            if (valid) {
-                const float *tmp = pass_plane(fd) + (long long)y * F;
-                const float acc = adj_1d(tmp, x, F, step, 1);
-                const float wv = c_plane(fd, params, j)[px] - fd.starlet[(long long)j * F * F + px];
-                const float lwu = lw * wmap_w(wm1, px);
-                const float g = wv > 0.f ? lwu : (wv < 0.f ? -lwu : 0.f);
-                t_plane(fd, j)[px] = g + acc;
-            }
-        }
-        if (pass == 1) {
-            // deterministic reduction of |w| over the item's 256 pixels (compensated FP32 pairs)
-            l1 = fsum_warp(l1);
-            if ((threadIdx.x & 31) == 0) s_red[q][threadIdx.x >> 5] = make_float2(l1.hi, l1.lo);
-        }
-    }
-    if (pass == 1) {
-        __syncthreads();
-        if (threadIdx.x < kStarletChunks) {
-            const int c = blockIdx.x * kStarletChunks + threadIdx.x;
-            if (c < n_chunks) {
-                const ChunkItem ch = chunks[c];
-                const FieldDev &fd = fields[ch.field];
-                if (j <= fd.J - 2 && starlet_form(fd.F, fd.J) == 2) {
-                    FSum s = fsum_zero();
-                    for (int i = 0; i < 8; ++i) s = fsum_add(s, FSum{s_red[threadIdx.x][i].x, s_red[threadIdx.x][i].y});
-                    l1_part[fd.l1_slot + (long long)j * fd.n_chunks + ch.chunk] =
-                        (double)fd.lambda * (double)fd.Wd[j] * fsum_value(s);
-                }
-            }
-        }
-    }
 }
 
 // Forward level j as bands: c_{j+1} = Col_j Row_j c_j on rows [y0, y0 + 16) and the prior
@@ -505,29 +404,30 @@ starlet_comb_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     }
 }
 
-// Forward level j as tiles: c_{j+1} = Col_j Row_j c_j on rows [y0, y0 + 16) x columns [x0, x0 + 128)
-// and the prior partial of the tile.  Block (tile, field); the row taps are read from c_j.
+// Forward level j as tiles: the comb-band forward on the columns [x0, x0 + 128) (the row taps read
+// from c_j directly).  Block (t, field), t = (rho * nk + k0 / 16) * nbx + x0 / 128; the prior's
+// partial sums per (4-row comb group, column tile).
 template <bool MAP>
 __global__ void __launch_bounds__(256)
 starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params,
                         double *__restrict__ l1_part, int j) {
     extern __shared__ float sb[];
-    __shared__ float2 s_red[8];
+    __shared__ float2 s_row[kCombRows];
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
     if (j > J - 2 || starlet_form(F, J) != 1) return;
-    const int TR = tile_rows(j);
-    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + TR - 1) / TR;
-    const int t = blockIdx.x;
-    if (t >= nbx * nby) return;
-    const int by = t / nbx, bx = t - by * nbx, y0 = by * TR, x0 = bx * kTileCols;
+    const int s = 1 << j, nk = comb_chunks(F, s), nbx = (F + kTileCols - 1) / kTileCols;
+    const int t0 = blockIdx.x;
+    if (t0 >= s * nk * nbx) return;
+    const int cb = t0 / nbx, bx = t0 - cb * nbx, x0 = bx * kTileCols, Tc = min(kTileCols, F - x0);
+    const int rho = cb / nk, k0 = (cb - rho * nk) * kCombRows;
+    const int Tr = max(0, min(kCombRows, (F - rho + s - 1) / s - k0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int s = 1 << j, Tr = min(TR, F - y0), Tc = min(kTileCols, F - x0), r0 = y0 - 2 * s;
-    const int R = Tr + 4 * s;
     const float *cj = c_plane(fd, params, j);
     const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr;
+    const int R = Tr > 0 ? Tr + 4 : 0;
     for (int i = warp; i < R; i += nwarp) {
-        const float *row = cj + (long long)mirror_at(r0 + i, F) * F;
+        const float *row = cj + (long long)mirror_at(rho + s * (k0 - 2 + i), F) * F;
         float *dst = sb + (long long)i * kTileCols;
         for (int xx = lane; xx < Tc; xx += 32) {
             const int x = x0 + xx;
@@ -544,36 +444,40 @@ starlet_tile_fwd_kernel(const FieldDev *__restrict__ fields, const float *__rest
     }
     __syncthreads();
     float *cn = fd.starlet + (long long)j * F * F;  // c_{j+1}
-    FSum l1 = fsum_zero();
-    for (int yy = warp; yy < Tr; yy += nwarp) {
-        const long long ro = (long long)(y0 + yy) * F;
+    for (int t = warp; t < Tr; t += nwarp) {
+        const long long ro = (long long)(rho + s * (k0 + t)) * F;
         float l1_row = 0.f;
         for (int xx = lane; xx < Tc; xx += 32) {
             const int x = x0 + xx;
             float acc = 0.f;
 #pragma unroll
-            for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(yy + 2 * s + m * s) * kTileCols + xx];
+            for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * sb[(long long)(t + 2 + m) * kTileCols + xx];
             cn[ro + x] = acc;
             l1_row += fabsf(cj[ro + x] - acc) * wmap_w(wm1, ro + x);
         }
-        l1 = fsum_add(l1, l1_row);
+        const FSum r = fsum_warp(FSum{l1_row, 0.f});
+        if (lane == 0) s_row[t] = make_float2(r.hi, r.lo);
     }
-    l1 = fsum_warp(l1);
-    if (lane == 0) s_red[warp] = make_float2(l1.hi, l1.lo);
     __syncthreads();
+    const int nk4 = comb_chunks(F, s, kCombGroup), g0 = k0 / kCombGroup;
     const long long base = fd.l1_slot + (long long)j * fd.n_chunks;
-    if (threadIdx.x == 0) {
-        FSum tt = fsum_zero();
-        for (int w = 0; w < nwarp; ++w) tt = fsum_add(tt, FSum{s_red[w].x, s_red[w].y});
-        l1_part[base + t] = (double)fd.lambda * (double)fd.Wd[j] * fsum_value(tt);
+    for (int g = threadIdx.x; g < kCombRows / kCombGroup; g += blockDim.x) {
+        if (g0 + g >= nk4) break;
+        FSum a = fsum_zero();
+        for (int t = kCombGroup * g; t < min(kCombGroup * (g + 1), Tr); ++t)
+            a = fsum_add(a, FSum{s_row[t].x, s_row[t].y});
+        l1_part[base + ((long long)rho * nk4 + g0 + g) * nbx + bx] =
+            (double)fd.lambda * (double)fd.Wd[j] * fsum_value(a);
     }
-    if (t == 0)  // the level's remaining partial-sum slots stay zero
-        for (int c = nbx * nby + threadIdx.x; c < fd.n_chunks; c += blockDim.x) l1_part[base + c] = 0.0;
+    if (t0 == 0)  // the level's remaining partial-sum slots stay zero
+        for (long long c = (long long)s * nk4 * nbx + threadIdx.x; c < fd.n_chunks; c += blockDim.x)
+            l1_part[base + c] = 0.0;
 }
 
-// Adjoint level j as tiles: V_j (or T_0) on rows [y0, y0 + 16) x columns [x0, x0 + 128), as the
-// band adjoint with the column gather over the tile's columns and their 2 s halo (clipped to the
-// grid), which the row gather then reads, mirror preimages included.
+// Adjoint level j as tiles: the comb-band adjoint on the columns [x0, x0 + 128): the V rows and
+// the column-adjoint values are staged over the tile's columns and their 2 s halo (clipped to the
+// grid), which hold every mirror preimage of the row gather; the column gather's mirror
+// preimages are read from the plane.
 template <bool MAP>
 __global__ void __launch_bounds__(256)
 starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__restrict__ params, int j) {
@@ -581,62 +485,64 @@ starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
     const FieldDev &fd = fields[blockIdx.y];
     const int F = fd.F, J = fd.J;
     if (j > J - 2 || starlet_form(F, J) != 1) return;
-    const int TR = tile_rows(j);
-    const int nbx = (F + kTileCols - 1) / kTileCols, nby = (F + TR - 1) / TR;
-    const int t = blockIdx.x;
-    if (t >= nbx * nby) return;
-    const int by = t / nbx, bx = t - by * nbx, y0 = by * TR, x0 = bx * kTileCols;
+    const int s = 1 << j, nk = comb_chunks(F, s), nbx = (F + kTileCols - 1) / kTileCols;
+    const int t0 = blockIdx.x;
+    if (t0 >= s * nk * nbx) return;
+    const int cb = t0 / nbx, bx = t0 - cb * nbx, x0 = bx * kTileCols, Tc = min(kTileCols, F - x0);
+    const int rho = cb / nk, k0 = (cb - rho * nk) * kCombRows;
+    const int Tr = max(0, min(kCombRows, (F - rho + s - 1) / s - k0));
+    if (Tr == 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int s = 1 << j, Tr = min(TR, F - y0), Tc = min(kTileCols, F - x0);
-    const int vlo = max(0, y0 - 2 * s), vhi = min(F, y0 + Tr + 2 * s);
     const int xlo = max(0, x0 - 2 * s), xhi = min(F, x0 + Tc + 2 * s), W = xhi - xlo;
     const int WP = kTileCols + 4 * s;  // row pitch of both staged arrays
-    float *vb = sb, *tb = sb + (long long)(TR + 4 * s) * WP;
+    float *vb = sb, *tb = sb + (long long)(kCombRows + 4) * WP;
     const float lw1 = fd.lambda * fd.Wd[j];
     const float *wm1 = MAP ? wmap_plane(fd, j) : nullptr, *wm0 = MAP ? wmap_plane(fd, j - 1) : nullptr;
     const float *cj = c_plane(fd, params, j), *cn = fd.starlet + (long long)j * F * F;  // c_j, c_{j+1}
     const bool top = j + 1 == J - 1;
     const float *Vn = fd.starlet + (long long)(J + ((j + 1) & 1)) * F * F;
-    for (int i = warp; i < vhi - vlo; i += nwarp) {
-        const long long ro = (long long)(vlo + i) * F;
-        for (int xx = lane; xx < W; xx += 32) {
-            const int x = xlo + xx;
-            vb[(long long)i * WP + xx] =
-                top ? 0.f - gamma_of(cj[ro + x] - cn[ro + x], lw1 * wmap_w(wm1, ro + x)) : Vn[ro + x];
-        }
+    auto vval = [&](int r, int x) {
+        const long long o = (long long)r * F + x;
+        return top ? 0.f - gamma_of(cj[o] - cn[o], lw1 * wmap_w(wm1, o)) : Vn[o];
+    };
+    for (int i = warp; i < Tr + 4; i += nwarp) {
+        const int r = rho + s * (k0 - 2 + i);
+        if (r < 0 || r >= F) continue;  // never read: the gather tests the same range
+        for (int xx = lane; xx < W; xx += 32) vb[(long long)i * WP + xx] = vval(r, xlo + xx);
     }
     __syncthreads();
-    for (int yy = warp; yy < Tr; yy += nwarp) {
-        const int y = y0 + yy;
+    for (int t = warp; t < Tr; t += nwarp) {
+        const int y = rho + s * (k0 + t);
         const bool inner = y > 2 * s && y < F - 1 - 2 * s;  // direct taps only (no mirror preimage)
         for (int xx = lane; xx < W; xx += 32) {
             float acc = 0.f;
             if (inner) {
 #pragma unroll
-                for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * vb[(long long)(y - m * s - vlo) * WP + xx];
-                tb[(long long)yy * WP + xx] = acc;
+                for (int m = -2; m <= 2; ++m) acc += kB3[m + 2] * vb[(long long)(t - m + 2) * WP + xx];
+                tb[(long long)t * WP + xx] = acc;
                 continue;
             }
+            const int x = xlo + xx;
 #pragma unroll
             for (int m = -2; m <= 2; ++m) {
                 const float bm = kB3[m + 2];
                 const int k1 = y - m * s;
-                if (k1 >= 0 && k1 < F) acc += bm * vb[(long long)(k1 - vlo) * WP + xx];
+                if (k1 >= 0 && k1 < F) acc += bm * vb[(long long)(t - m + 2) * WP + xx];
                 const int k2 = -y - m * s;
-                if (y > 0 && k2 >= 0 && k2 < F) acc += bm * vb[(long long)(k2 - vlo) * WP + xx];
+                if (y > 0 && k2 >= 0 && k2 < F) acc += bm * vval(k2, x);
                 const int k3 = 2 * (F - 1) - y - m * s;
-                if (y < F - 1 && k3 >= 0 && k3 < F) acc += bm * vb[(long long)(k3 - vlo) * WP + xx];
+                if (y < F - 1 && k3 >= 0 && k3 < F) acc += bm * vval(k3, x);
             }
-            tb[(long long)yy * WP + xx] = acc;
+            tb[(long long)t * WP + xx] = acc;
         }
     }
     __syncthreads();
     const float lw0 = j >= 1 ? fd.lambda * fd.Wd[j - 1] : 0.f;
     const float *cjm = j >= 1 ? c_plane(fd, params, j - 1) : cj;  // c_{j-1}
     float *out = fd.starlet + (long long)(J + (j & 1)) * F * F;
-    for (int yy = warp; yy < Tr; yy += nwarp) {
-        const long long ro = (long long)(y0 + yy) * F;
-        const float *trow = tb + (long long)yy * WP - xlo;  // indexed by the grid column
+    for (int t = warp; t < Tr; t += nwarp) {
+        const long long ro = (long long)(rho + s * (k0 + t)) * F;
+        const float *trow = tb + (long long)t * WP - xlo;  // indexed by the grid column
         for (int xx = lane; xx < Tc; xx += 32) {
             const int x = x0 + xx;
             const float acc = adj_1d(trow, x, F, s, 1);
@@ -691,7 +597,7 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
         cudaFuncSetAttribute(starlet_comb_adj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
         configured = true;
     }
-    const bool bands = (forms & 1) != 0, tiles = (forms & 2) != 0, passes = (forms & 4) != 0;
+    const bool bands = (forms & 1) != 0, tiles = (forms & 2) != 0;
     const bool combs = (forms & 8) != 0, map = (forms & kStarletMapBit) != 0;
     // comb bands: s combs of comb_chunks blocks at level j; staging of cr + 4 (forward) or
     // 2 cr + 4 (adjoint) rows of the widest comb-band grid
@@ -701,14 +607,13 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
     const int comb_fwd_smem = (cr + 4) * Fc * (int)sizeof(float);
     const int comb_adj_smem = (2 * cr + 4) * Fc * (int)sizeof(float);
     auto tgrid = [&](int j) {
-        const int tr = tile_rows(j);
-        return dim3((unsigned)(((Fmax + tr - 1) / tr) * ((Fmax + kTileCols - 1) / kTileCols)), n_fields);
+        const int sj = 1 << j;
+        return dim3((unsigned)(sj * comb_chunks(Fmax, sj) * ((Fmax + kTileCols - 1) / kTileCols)), n_fields);
     };
     auto tile_smem = [&](long long floats) {
         return (int)std::min<long long>(floats * (long long)sizeof(float), kTileSmemBytes);
     };
     int n = 0;
-    const int grid = (n_chunks + kStarletChunks - 1) / kStarletChunks;
     const dim3 bgrid((Fmax + kBandRows - 1) / kBandRows, n_fields);
     // shared memory of level j: (2 * 16 + 4 * 2^j) rows of the widest grid, at most the budget
     // (which every banded field's deepest level fits, so its shallower levels fit too)
@@ -739,11 +644,6 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
                 starlet_tile_fwd_kernel<false><<<tgrid(j), 256, sm, st>>>(fields, params, l1_part, j);
             ++n;
         }
-        if (passes) {
-            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 0);
-            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 1);
-            n += 2;
-        }
     }
     for (int j = Jmax - 2; j >= 0; --j) {
         if (bands) {
@@ -767,12 +667,6 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
             else
                 starlet_tile_adj_kernel<false><<<tgrid(j), 256, sm, st>>>(fields, params, j);
             ++n;
-        }
-        if (passes) {
-            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 4);
-            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 2);
-            starlet_pass_kernel<<<grid, 256, 0, st>>>(fields, chunks, n_chunks, params, l1_part, j, 3);
-            n += 3;
         }
     }
     return n;

@@ -429,10 +429,9 @@ def test_schedules_forced_and_tuned_agree(tmp_path, monkeypatch):
 
 # Starlet forms of wide fields: F = 420 (J = 5, 6) and F = 300 (J = 7) run as comb bands (rows
 # rho + s k of one comb per block, the mirror preimages read from the plane); F = 720 is too wide
-# for them: with J = 5 it runs as 16 x 128 tiles (32 rows from level 3 on; the last tile column 80
-# wide), with J = 7 it is too deep for the tiles' budget and runs as passes.
+# for them and runs as comb tiles of 128 columns (the last tile column 80 wide) with J = 5, 7, 8.
 @pytest.mark.parametrize("E,N,f,K,M,J", [(2, 140, 3, 15, 2, 5), (2, 140, 3, 15, 1, 6), (2, 150, 2, 9, 1, 7),
-                                         (2, 240, 3, 9, 1, 5), (2, 240, 3, 9, 1, 7)])
+                                         (2, 240, 3, 9, 1, 5), (2, 240, 3, 9, 1, 7), (2, 240, 3, 9, 1, 8)])
 def test_wide_field_starlet_forms_match_oracle(E, N, f, K, M, J):
     fd = syn.small_deconv(seed=3000 + N + J, E=E, N=N, f=f, K=K, M=M, J=J, lam=1.4, pos_half=N / 5)
     loss, g = _run(fd, conv_mode="direct")
