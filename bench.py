@@ -218,7 +218,56 @@ def lr_groups(fd):
 
 # --- clocks --------------------------------------------------------------------------------
 
+class _NvmlClocks:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the driver): the SM clock,
+    its maximum and the active clock-event reasons of one GPU, sampled by a host thread."""
+    # nvmlClocksEventReasons bits (nvml.h)
+    BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(cuda_index).uuid)
+            for u in (uuid, "GPU-" + uuid):
+                if self.lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(self.h)) == 0:
+                    ok = True
+                    break
+        except Exception:
+            ok = False
+        if not ok:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            ids = [x for x in vis.split(",") if x.strip()]
+            idx = int(ids[cuda_index]) if ids and all(x.strip().isdigit() for x in ids) else cuda_index
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(self.h)) != 0:
+                raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        c, m, r = self.ct.c_uint(), self.ct.c_uint(), self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(c)) != 0:
+            return None
+        if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(m)) != 0:
+            return None
+        if self.reasons_fn(self.h, self.ct.byref(r)) != 0:
+            return None
+        return float(c.value), float(m.value), {n for bit, n in self.BITS.items() if r.value & bit}
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
+    """Clocks and throttle reasons during the timed region: NVML every 10 ms from a host thread
+    (the main thread waits in a stream synchronisation meanwhile), else nvidia-smi every 200 ms."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -227,8 +276,30 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.nvml = None
+        self.thread = None
+        self.samples = []
 
     def start(self):
+        try:
+            self.nvml = _NvmlClocks(self.gpu)
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            import threading
+            self.stop_ev = threading.Event()
+            first = self.nvml.sample()
+            if first is not None:
+                self.samples.append(first)
+
+            def run():
+                while not self.stop_ev.wait(0.010):
+                    v = self.nvml.sample()
+                    if v is not None:
+                        self.samples.append(v)
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -240,6 +311,21 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=5)
+            last = self.nvml.sample()
+            if last is not None:
+                self.samples.append(last)
+            self.nvml.close()
+            if not self.samples:
+                return None
+            reasons = set()
+            for _, _, r in self.samples:
+                reasons |= r
+            return {"sm_mhz": statistics.median(v[0] for v in self.samples),
+                    "sm_max_mhz": max(v[1] for v in self.samples), "reasons": sorted(reasons),
+                    "samples": len(self.samples), "source": "NVML, every 10 ms during the timed steps"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -267,7 +353,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, every 200 ms during the timed steps"}
 
 
 def load_peaks():
@@ -991,7 +1077,11 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
     the device through the C ABI, evaluates, and reads back the gradient and the loss.  The
     batch's inputs go in packed, one call per kind for all fields (sr_batch_set_psfs first, so that
     the PSFs' folding and kernel spectra run under the data and noise copies, which the library
-    issues on its copy stream), then the evaluation from host buffers."""
+    issues on its copy stream), then the evaluation from host buffers.  Two ways: pipelined (the
+    evaluation queued with sr_batch_loss_and_grad_host_async, so that the next step's input
+    copies run under this step's evaluation; one sr_batch_sync at the end, every step's gradient
+    and total read back into page-locked memory), the reported value; and synchronous
+    (sr_batch_loss_and_grad_host, which waits for each step), for comparison."""
     import torch
 
     def pinned(a):
@@ -1001,9 +1091,10 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
     scat = pinned(np.concatenate([fd.sigma.ravel() for fd in fields]))
     pcat = pinned(np.concatenate([fd.s.ravel() for fd in fields]))
     params = pinned(np.concatenate([fd.params for fd in fields])).numpy()
-    grad = torch.empty(batch.n_params, dtype=torch.float32).pin_memory().numpy()
+    grads = [torch.empty(batch.n_params, dtype=torch.float32).pin_memory().numpy() for _ in range(2)]
+    totals = [torch.empty(1, dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
     h2d = (dcat.numel() + scat.numel() + pcat.numel()) * 4 + params.nbytes
-    d2h = grad.nbytes + 8
+    d2h = grads[0].nbytes + 8
     if psf is not None:
         qd, qs = pinned(pb.t), pinned(pb.sigma)
         qp = pinned(pb.params).numpy()
@@ -1012,25 +1103,38 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
         d2h += qg.nbytes + 8
     units = units_of(fields, pb)
 
-    def one():
-        batch.set_psfs(pcat)
-        batch.set_data(dcat)
-        batch.set_noise(scat)
-        batch.loss_and_grad_host(params, grad)
+    def one(k, pipelined):
         if psf is not None:
             psf.set_data(qd)
             psf.set_noise(qs)
             psf.loss_and_grad_host(qp, qg)
+        batch.set_psfs(pcat)
+        batch.set_data(dcat)
+        batch.set_noise(scat)
+        if pipelined:
+            batch.loss_and_grad_host_async(params, grads[k & 1], totals[k & 1])
+        else:
+            totals[0][0] = batch.loss_and_grad_host(params, grads[0])[0]
 
-    one()
-    stream.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        one()
-    stream.synchronize()
-    dt = time.perf_counter() - t0
-    return {"value": units * steps / dt, "unit": "epoch-px/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": steps}
+    out = {}
+    for pipelined in (False, True):
+        one(0, pipelined)
+        batch.sync()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            one(k, pipelined)
+        batch.sync()
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        if not all(np.isfinite(t[0]) for t in totals):
+            raise RuntimeError("non-finite total in the end-to-end steps")
+        out[pipelined] = units * steps / dt
+    return {"value": out[True], "unit": "epoch-px/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "mode": "pipelined: each step's input copies run under the previous step's evaluation",
+            "synchronous": {"value": out[False], "unit": "epoch-px/s",
+                            "mode": "each step waits for its evaluation before the next step's copies"}}
 
 
 def measure_plain(fields, batched_value, stream, max_fields=6, evals=2):

@@ -308,6 +308,20 @@ sr_status sr_batch_loss_and_grad(sr_batch *b, const float *params_dev, double *l
                                  double *total_host, float *grad_dev);
 /* End-to-end variant with HOST buffers (see sr_loss_and_grad_host). */
 sr_status sr_batch_loss_and_grad_host(sr_batch *b, const float *params_host, double *total_host, float *grad_host);
+/* The same evaluation queued without waiting: the parameters' copy in, the evaluation and the
+ * copies of the gradient and the total out are ordered on the batch's stream, and the call
+ * returns once they are queued.  Successive calls with batched set-up between them pipeline:
+ * the next step's input copies (sr_batch_set_* from host memory, staged on the internal stream)
+ * run while this step computes.  With page-locked host buffers nothing blocks the host;
+ * params_host must stay unchanged and grad_host / total_host untouched until sr_batch_sync (or
+ * any synchronisation of the batch's stream) returns.  Input checks (non-finite values, sigma
+ * <= 0) are gathered over every queued step and reported by sr_batch_sync; the totals are not
+ * checked for finiteness (the caller reads them). */
+sr_status sr_batch_loss_and_grad_host_async(sr_batch *b, const float *params_host, double *total_host,
+                                            float *grad_host);
+/* Waits for everything queued on the batch's stream and reports the input checks of the batched
+ * set-up calls since the last check (SR_ERR_NONFINITE names the first field concerned). */
+sr_status sr_batch_sync(sr_batch *b);
 /* n_steps optimiser updates of all fields at once (same cfg for every field),
  * captured as one CUDA graph and replayed. */
 sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_optim_cfg *cfg,

@@ -83,6 +83,8 @@ PROTOTYPES = {
     "sr_batch_param_offset": ([c_void_p, c_int, ctypes.POINTER(c_size_t)], c_int),
     "sr_batch_loss_and_grad": ([c_void_p, c_void_p, c_void_p, c_void_p, P_double, c_void_p], c_int),
     "sr_batch_loss_and_grad_host": ([c_void_p, c_void_p, P_double, c_void_p], c_int),
+    "sr_batch_loss_and_grad_host_async": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "sr_batch_sync": ([c_void_p], c_int),
     "sr_batch_step": ([c_void_p, c_void_p, c_int, ctypes.POINTER(OptimCfg), P_double], c_int),
     "sr_batch_reset_optimizer": ([c_void_p], c_int),
     "sr_launches_per_eval": ([c_void_p], c_int),

@@ -331,6 +331,25 @@ class Batch:
                   "sr_batch_loss_and_grad_host")
         return tot.value, grad_host
 
+    def loss_and_grad_host_async(self, params_host, grad_host, total_host):
+        """Queue the host-buffer evaluation without waiting (sr_batch_loss_and_grad_host_async).
+        params_host, grad_host (n_params float32) and total_host (one float64) are host arrays,
+        page-locked for the call to return at once (numpy views of pinned torch tensors); they are
+        written or read until sync()."""
+        for a, n, dt, name in ((params_host, self.n_params, np.float32, "params_host"),
+                               (grad_host, self.n_params, np.float32, "grad_host"),
+                               (total_host, 1, np.float64, "total_host")):
+            if not isinstance(a, np.ndarray) or a.dtype != dt or a.size < n or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError(f"{name} must be a contiguous {np.dtype(dt).name} array of {n} values")
+        nat.check(self.lib.sr_batch_loss_and_grad_host_async(self.handle, ctypes.c_void_p(params_host.ctypes.data),
+                                                             ctypes.c_void_p(total_host.ctypes.data),
+                                                             ctypes.c_void_p(grad_host.ctypes.data)),
+                  "sr_batch_loss_and_grad_host_async")
+
+    def sync(self):
+        """Wait for the batch's stream and raise on the queued set-up's input checks (sr_batch_sync)."""
+        nat.check(self.lib.sr_batch_sync(self.handle), "sr_batch_sync")
+
     def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg, sync: bool = True) -> float | None:
         """n_steps optimiser updates of every field (sr_batch_step).  Returns the last total loss
         (synchronises the batch's stream), or None without reading it back when sync=False."""

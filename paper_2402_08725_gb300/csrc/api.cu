@@ -272,6 +272,7 @@ struct sr_batch {
     BioEntry *bio_tab = nullptr;
     long long *bio_off_d = nullptr, *bio_off_s = nullptr, *bio_off_k = nullptr;
     long long bio_total_d = 0, bio_total_s = 0, bio_total_k = 0;
+    bool bio_vec_d = false, bio_vec_s = false;  // every packed offset a multiple of 4 (float4 moves)
     int2 *bio_items = nullptr;
     std::vector<std::array<int, 3>> bio_ranges;  // (transform size L, first item, items) per size
     // host inputs are staged per kind (0 data, 1 noise, 2 PSFs) by copies on an internal stream:
@@ -1450,6 +1451,44 @@ sr_status sr_loss(sr_problem *p, const float *params_dev, double *loss_host) {
     return sr_loss_and_grad(p, params_dev, loss_host, nullptr, p->plan->grad_int);
 }
 
+// The device address of page-locked host memory (cudaHostAlloc'ed or registered), else null.
+static void *mapped_address(const void *host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Parameters in and results out of the host-buffer evaluations.  From and to page-locked memory
+// these are kernels reading or writing its mapped address: a copy-engine transfer queued behind
+// the evaluation would hold up, in the engine's queue, the staging copies that later set-up calls
+// issue on the internal stream (measured: no overlap of the next step's inputs with this step).
+static sr_status params_in(float *dev, const float *host, size_t n, cudaStream_t st) {
+    if (const float *m = static_cast<const float *>(mapped_address(host))) {
+        launch_host_copy(m, dev, (long long)n, nullptr, nullptr, st);
+        SR_CUDA(cudaGetLastError());
+        return SR_OK;
+    }
+    SR_CUDA(cudaMemcpyAsync(dev, host, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    return SR_OK;
+}
+
+static sr_status results_out(float *grad_host, const float *grad_dev, size_t n, double *total_host,
+                             const double *total_dev, cudaStream_t st) {
+    float *mg = static_cast<float *>(mapped_address(grad_host));
+    double *mt = static_cast<double *>(mapped_address(total_host));
+    if (mg) {
+        launch_host_copy(grad_dev, mg, (long long)n, mt ? total_dev : nullptr, mt, st);
+        SR_CUDA(cudaGetLastError());
+    } else {
+        SR_CUDA(cudaMemcpyAsync(grad_host, grad_dev, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    }
+    if (!mg || !mt) SR_CUDA(cudaMemcpyAsync(total_host, total_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return SR_OK;
+}
+
 sr_status sr_loss_and_grad_host(sr_problem *p, const float *params_host, double *loss_host, float *grad_host) {
     sr_status st = check_ready(p);
     if (st != SR_OK) return st;
@@ -1458,10 +1497,9 @@ sr_status sr_loss_and_grad_host(sr_problem *p, const float *params_host, double 
     Plan *pl = p->plan;
     if ((st = ensure_opt_buffers(pl)) != SR_OK) return st;
     if (!pl->params_int && (st = pl->arena.alloc(&pl->params_int, pl->n_params)) != SR_OK) return st;
-    SR_CUDA(cudaMemcpyAsync(pl->params_int, params_host, sizeof(float) * pl->n_params, cudaMemcpyHostToDevice, p->stream));
+    if ((st = params_in(pl->params_int, params_host, pl->n_params, p->stream)) != SR_OK) return st;
     if ((st = sr_loss_and_grad(p, pl->params_int, nullptr, nullptr, pl->grad_int)) != SR_OK) return st;
-    SR_CUDA(cudaMemcpyAsync(grad_host, pl->grad_int, sizeof(float) * pl->n_params, cudaMemcpyDeviceToHost, p->stream));
-    SR_CUDA(cudaMemcpyAsync(loss_host, pl->total, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    if ((st = results_out(grad_host, pl->grad_int, pl->n_params, loss_host, pl->total, p->stream)) != SR_OK) return st;
     SR_CUDA(cudaStreamSynchronize(p->stream));
     if (p->pending_check && (st = check_flag(p)) != SR_OK) return st;
     if (!std::isfinite(*loss_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
@@ -1775,14 +1813,34 @@ sr_status sr_batch_loss_and_grad_host(sr_batch *b, const float *params_host, dou
     sr_status st;
     if ((st = ensure_opt_buffers(pl)) != SR_OK) return st;
     if (!pl->params_int && (st = pl->arena.alloc(&pl->params_int, pl->n_params)) != SR_OK) return st;
-    SR_CUDA(cudaMemcpyAsync(pl->params_int, params_host, sizeof(float) * pl->n_params, cudaMemcpyHostToDevice, b->stream));
+    if ((st = params_in(pl->params_int, params_host, pl->n_params, b->stream)) != SR_OK) return st;
     if ((st = sr_batch_loss_and_grad(b, pl->params_int, nullptr, nullptr, nullptr, pl->grad_int)) != SR_OK) return st;
-    SR_CUDA(cudaMemcpyAsync(grad_host, pl->grad_int, sizeof(float) * pl->n_params, cudaMemcpyDeviceToHost, b->stream));
-    SR_CUDA(cudaMemcpyAsync(total_host, pl->total, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    if ((st = results_out(grad_host, pl->grad_int, pl->n_params, total_host, pl->total, b->stream)) != SR_OK) return st;
     SR_CUDA(cudaStreamSynchronize(b->stream));
     if ((st = batch_check(b)) != SR_OK) return st;
     if (!std::isfinite(*total_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
     return SR_OK;
+}
+
+// Queued form of the host-buffer evaluation: the same copies and launches on the batch's stream,
+// no synchronisation; the inputs' checks wait for sr_batch_sync.
+sr_status sr_batch_loss_and_grad_host_async(sr_batch *b, const float *params_host, double *total_host,
+                                            float *grad_host) {
+    if (!b || !params_host || !total_host || !grad_host) return fail(SR_ERR_ARG, "NULL argument");
+    Plan *pl = b->plan;
+    sr_status st;
+    if ((st = ensure_opt_buffers(pl)) != SR_OK) return st;
+    if (!pl->params_int && (st = pl->arena.alloc(&pl->params_int, pl->n_params)) != SR_OK) return st;
+    if ((st = params_in(pl->params_int, params_host, pl->n_params, b->stream)) != SR_OK) return st;
+    if ((st = sr_batch_loss_and_grad(b, pl->params_int, nullptr, nullptr, nullptr, pl->grad_int)) != SR_OK) return st;
+    if ((st = results_out(grad_host, pl->grad_int, pl->n_params, total_host, pl->total, b->stream)) != SR_OK) return st;
+    return SR_OK;
+}
+
+sr_status sr_batch_sync(sr_batch *b) {
+    if (!b) return fail(SR_ERR_ARG, "NULL argument");
+    SR_CUDA(cudaStreamSynchronize(b->stream));
+    return batch_check(b);
 }
 
 sr_status sr_batch_step(sr_batch *b, float *params_dev, int n_steps, const sr_optim_cfg *cfg, double *last_total_host) {
@@ -1862,8 +1920,15 @@ static sr_status batch_io_prepare(sr_batch *b) {
     b->bio_total_d = od[n];
     b->bio_total_s = os[n];
     b->bio_total_k = ok[n];
+    b->bio_vec_d = b->bio_vec_s = true;
+    for (int i = 0; i <= n; ++i) {
+        if (od[i] % 4) b->bio_vec_d = false;
+        if (os[i] % 4) b->bio_vec_s = false;
+    }
     return SR_OK;
 }
+
+static bool aligned16(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
 // The packed input of kind k on the device: the caller's device array, or the kind's staging
 // buffer after one copy on the internal stream (ordered as described at bio_stage).
@@ -1887,7 +1952,8 @@ sr_status sr_batch_set_data(sr_batch *b, const float *d, int on_device) {
     const float *src;
     if ((st = batch_io_prepare(b)) != SR_OK) return st;
     if ((st = batch_io_source(b, 0, d, b->bio_total_d, on_device, &src)) != SR_OK) return st;
-    launch_bio_data(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d, b->stream);
+    launch_bio_data(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d,
+                    b->bio_vec_d && aligned16(src), b->stream);
     SR_CUDA(cudaGetLastError());
     SR_CUDA(cudaEventRecord(b->bio_free[0], b->stream));
     b->bio_pending = true;
@@ -1900,7 +1966,8 @@ sr_status sr_batch_set_noise(sr_batch *b, const float *sigma, int on_device) {
     const float *src;
     if ((st = batch_io_prepare(b)) != SR_OK) return st;
     if ((st = batch_io_source(b, 1, sigma, b->bio_total_d, on_device, &src)) != SR_OK) return st;
-    launch_bio_noise(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d, b->stream);
+    launch_bio_noise(b->bio_tab, b->bio_off_d, (int)b->probs.size(), src, b->bio_total_d,
+                     b->bio_vec_d && aligned16(src), b->stream);
     SR_CUDA(cudaGetLastError());
     SR_CUDA(cudaEventRecord(b->bio_free[1], b->stream));
     b->bio_pending = true;
@@ -1914,7 +1981,7 @@ sr_status sr_batch_set_psfs(sr_batch *b, const float *s, int on_device) {
     if ((st = batch_io_prepare(b)) != SR_OK) return st;
     if ((st = batch_io_source(b, 2, s, b->bio_total_s, on_device, &src)) != SR_OK) return st;
     launch_bio_psfs(b->bio_tab, b->bio_off_s, b->bio_off_k, (int)b->probs.size(), src, b->bio_total_s,
-                    b->bio_total_k, b->stream);
+                    b->bio_total_k, b->bio_vec_s && aligned16(src), b->stream);
     SR_CUDA(cudaEventRecord(b->bio_free[2], b->stream));  // the staged PSFs are read by the copy kernel only
     for (const auto &r : b->bio_ranges)
         if ((st = launch_fft_kappa_pair_batch(b->plan->d_fields, b->bio_items + r[1], r[2], r[0], g_num_sms,

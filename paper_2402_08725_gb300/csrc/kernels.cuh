@@ -93,13 +93,17 @@ struct BioEntry {
     int *flag;
     int E, N, K, f, Tk, tau_lo;
 };
-void launch_bio_data(const BioEntry *tab, const long long *off, int n, const float *src, long long total,
+// vec: every offset and the total are multiples of 4 and src is 16-byte aligned (float4 moves)
+void launch_bio_data(const BioEntry *tab, const long long *off, int n, const float *src, long long total, bool vec,
                      cudaStream_t st);
 void launch_bio_flags(const BioEntry *tab, int n, int *out, cudaStream_t st);
-void launch_bio_noise(const BioEntry *tab, const long long *off, int n, const float *src, long long total,
+void launch_bio_noise(const BioEntry *tab, const long long *off, int n, const float *src, long long total, bool vec,
                       cudaStream_t st);
 void launch_bio_psfs(const BioEntry *tab, const long long *off_s, const long long *off_k, int n, const float *src,
-                     long long total_s, long long total_k, cudaStream_t st);
+                     long long total_s, long long total_k, bool vec, cudaStream_t st);
+// n floats src -> dst and (when tdst is not null) one double tsrc -> tdst in one kernel; either side
+// may be the mapped address of page-locked host memory
+void launch_host_copy(const float *src, float *dst, long long n, const double *tsrc, double *tdst, cudaStream_t st);
 
 // --- starlet prior (starlet.cu) ---
 // Forward levels then adjoint levels for every field of the table (n_fields of them, grids at

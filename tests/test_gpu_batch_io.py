@@ -90,3 +90,106 @@ def test_batch_set_reports_bad_inputs():
     b.close()
     for p in pr:
         p.close()
+
+
+def test_pipelined_host_steps_equal_synchronous_ones():
+    """Steps queued with sr_batch_loss_and_grad_host_async, each with its own inputs (three sets
+    of data, noise, PSFs and parameters in turn, from page-locked memory), give the synchronous
+    call's loss and gradient for those inputs bit for bit: the next step's staged copies overlap
+    this step's evaluation without overwriting what it reads."""
+    fields = _fields()
+    modes = ["fft", "direct", "fft", "auto"]
+    rng = np.random.default_rng(9)
+    cat = lambda xs: np.concatenate([x.ravel() for x in xs]).astype(np.float32)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    sets = []
+    for k in range(3):
+        d = cat([fd.d * (1.0 + 0.1 * k) + k for fd in fields])
+        s = cat([fd.sigma * rng.uniform(0.9, 1.1, fd.sigma.shape) for fd in fields])
+        p = cat([syn.moffat_stack(fd.K, rng.uniform(2, 3, fd.E), rng.uniform(2, 4, fd.E)) for fd in fields])
+        q = cat([fd.params * (1.0 + 0.05 * k) for fd in fields])
+        sets.append((pin(d), pin(s), pin(p), pin(q)))
+    pr, b = _batch(fields, modes)
+    ref = []
+    for d, s, p, q in sets:
+        b.set_psfs(p)
+        b.set_data(d)
+        b.set_noise(s)
+        tot, g = b.loss_and_grad_host(q.numpy())
+        ref.append((tot, g.copy()))
+    order = [0, 1, 2, 1, 0, 2]
+    outs = [(torch.empty(b.n_params, dtype=torch.float32).pin_memory().numpy(),
+             torch.empty(1, dtype=torch.float64).pin_memory().numpy()) for _ in order]
+    for k, (g, t) in zip(order, outs):
+        d, s, p, q = sets[k]
+        b.set_psfs(p)
+        b.set_data(d)
+        b.set_noise(s)
+        b.loss_and_grad_host_async(q.numpy(), g, t)
+    b.sync()
+    for k, (g, t) in zip(order, outs):
+        assert t[0] == ref[k][0] and np.array_equal(g, ref[k][1]), k
+    b.close()
+    for p_ in pr:
+        p_.close()
+
+
+def test_pipelined_sync_reports_bad_inputs():
+    fields = _fields()
+    pr, b = _batch(fields, ["auto"] * len(fields))
+    d = np.concatenate([fd.d.ravel() for fd in fields]).astype(np.float32)
+    d[3] = np.inf
+    q = b.pack([fd.params for fd in fields])
+    g = np.empty(b.n_params, dtype=np.float32)
+    t = np.empty(1, dtype=np.float64)
+    b.set_data(d)
+    b.loss_and_grad_host_async(q, g, t)
+    with pytest.raises(RuntimeError, match="SR_ERR_NONFINITE"):
+        b.sync()
+    b.close()
+    for p_ in pr:
+        p_.close()
+
+
+def test_batch_set_scalar_paths_and_unaligned_host_buffers():
+    """Packed offsets that are not multiples of 4 (odd stamp and PSF sizes) take the per-element
+    set-up path, and page-locked parameter / gradient buffers that start off a 16-byte boundary
+    the per-element host-copy kernel; both give the members' own set-up and the device-buffer
+    evaluation bit for bit."""
+    fields = [syn.small_deconv(80, E=3, N=15, f=2, K=13, M=1, J=3, lam=0.5),
+              syn.small_deconv(81, E=2, N=17, f=2, K=9, M=0, J=3, lam=0.5)]
+    modes = ["fft", "direct"]
+    rng = np.random.default_rng(12)
+    new_d = [(fd.d * 0.9 + 1.0).astype(np.float32) for fd in fields]
+    new_s = [(fd.sigma * rng.uniform(0.9, 1.1, fd.sigma.shape)).astype(np.float32) for fd in fields]
+    new_p = [syn.moffat_stack(fd.K, rng.uniform(2, 3, fd.E), rng.uniform(2, 4, fd.E)) for fd in fields]
+    pa, ba = _batch(fields, modes)
+    for pr, d, s, p in zip(pa, new_d, new_s, new_p):
+        pr.set_data(d)
+        pr.set_noise(s)
+        pr.set_psfs(p)
+    ta, ga = _eval(ba, fields)
+    pb, bb = _batch(fields, modes)
+    cat = lambda xs: np.concatenate([x.ravel() for x in xs]).astype(np.float32)
+    bb.set_data(cat(new_d))
+    bb.set_noise(cat(new_s))
+    bb.set_psfs(cat(new_p))
+    tb, gb = _eval(bb, fields)
+    assert ta == tb and np.array_equal(ga, gb)
+    # the same evaluation from page-locked buffers one float past a 16-byte boundary
+    n = bb.n_params
+    qbuf = torch.empty(n + 1, dtype=torch.float32).pin_memory()
+    qbuf[1:] = torch.from_numpy(bb.pack([fd.params for fd in fields]))
+    gbuf = torch.empty(n + 1, dtype=torch.float32).pin_memory()
+    tbuf = torch.empty(1, dtype=torch.float64).pin_memory()
+    q, g, t = qbuf.numpy()[1:], gbuf.numpy()[1:], tbuf.numpy()
+    assert q.ctypes.data % 16 != 0 and g.ctypes.data % 16 != 0
+    bb.loss_and_grad_host_async(q, g, t)
+    bb.sync()
+    assert t[0] == tb and np.array_equal(g, gb)
+    tc, gc = bb.loss_and_grad_host(q, g)
+    assert tc == tb and np.array_equal(gc, gb)
+    for x in (ba, bb):
+        x.close()
+    for pr in pa + pb:
+        pr.close()
