@@ -774,7 +774,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e and batch is not None:
-        e2e = measure_e2e(fields, probs, batch, psf, pb, max(2, min(args.steps, 6)), stream, side)
+        e2e = measure_e2e(fields, probs, batch, psf, pb, max(2, min(args.steps, 10)), stream, side)
 
     peaks, peak_src = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -1078,10 +1078,11 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
     batch's inputs go in packed, one call per kind for all fields (sr_batch_set_psfs first, so that
     the PSFs' folding and kernel spectra run under the data and noise copies, which the library
     issues on its copy stream), then the evaluation from host buffers.  Two ways: pipelined (the
-    evaluation queued with sr_batch_loss_and_grad_host_async, so that the next step's input
-    copies run under this step's evaluation; one sr_batch_sync at the end, every step's gradient
-    and total read back into page-locked memory), the reported value; and synchronous
-    (sr_batch_loss_and_grad_host, which waits for each step), for comparison."""
+    evaluations queued with sr_batch_loss_and_grad_host_async and, for the PSF fit,
+    sr_loss_and_grad_host_async, so that the next step's input copies run under this step's
+    evaluation; one synchronisation at the end, every step's gradient and loss read back into
+    page-locked memory), the reported value; and synchronous (each step waits for its results
+    before the next step's copies), for comparison.  The first timed step fills the pipeline."""
     import torch
 
     def pinned(a):
@@ -1099,6 +1100,7 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
         qd, qs = pinned(pb.t), pinned(pb.sigma)
         qp = pinned(pb.params).numpy()
         qg = torch.empty(psf.n_params, dtype=torch.float32).pin_memory().numpy()
+        ql = torch.empty(1, dtype=torch.float64).pin_memory().numpy()
         h2d += (qd.numel() + qs.numel()) * 4 + qp.nbytes
         d2h += qg.nbytes + 8
     units = units_of(fields, pb)
@@ -1107,7 +1109,10 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
         if psf is not None:
             psf.set_data(qd)
             psf.set_noise(qs)
-            psf.loss_and_grad_host(qp, qg)
+            if pipelined:
+                psf.loss_and_grad_host_async(qp, qg, ql)
+            else:
+                ql[0] = psf.loss_and_grad_host(qp, qg)[0]
         batch.set_psfs(pcat)
         batch.set_data(dcat)
         batch.set_noise(scat)
@@ -1118,16 +1123,19 @@ def measure_e2e(fields, probs, batch, psf, pb, steps, stream, side):
 
     out = {}
     for pipelined in (False, True):
+        def sync():
+            batch.sync()
+            if psf is not None:
+                psf.sync()
+            stream.synchronize()
         one(0, pipelined)
-        batch.sync()
-        stream.synchronize()
+        sync()
         t0 = time.perf_counter()
         for k in range(steps):
             one(k, pipelined)
-        batch.sync()
-        stream.synchronize()
+        sync()
         dt = time.perf_counter() - t0
-        if not all(np.isfinite(t[0]) for t in totals):
+        if not all(np.isfinite(t[0]) for t in totals) or (psf is not None and not np.isfinite(ql[0])):
             raise RuntimeError("non-finite total in the end-to-end steps")
         out[pipelined] = units * steps / dt
     return {"value": out[True], "unit": "epoch-px/s", "h2d_bytes_per_step": int(h2d),

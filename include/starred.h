@@ -255,8 +255,21 @@ sr_status sr_loss_and_grad(sr_problem *p, const float *params_dev, double *loss_
 /* End-to-end variant with HOST buffers: copies params_host (sr_param_count
  * floats) to the device, evaluates, and copies the gradient back to grad_host
  * and the loss to *loss_host.  Synchronises.  For best throughput the host
- * buffers should be page-locked. */
+ * buffers should be page-locked: from and to page-locked memory (as for the
+ * host arrays of sr_set_data / _noise / _psfs) the library moves the values
+ * with kernels through the memory's mapped address rather than the copy
+ * engines, so that its transfers never wait in an engine's queue ahead of
+ * other streams' copies. */
 sr_status sr_loss_and_grad_host(sr_problem *p, const float *params_host, double *loss_host, float *grad_host);
+/* The same, queued without waiting: returns once the copies and the evaluation
+ * are queued on the problem's stream.  params_host must stay unchanged and
+ * grad_host / *loss_host untouched until sr_sync (or any synchronisation of
+ * the stream) returns; the loss is not checked for finiteness (the caller
+ * reads it).  With pageable buffers the copies may block the host. */
+sr_status sr_loss_and_grad_host_async(sr_problem *p, const float *params_host, double *loss_host, float *grad_host);
+/* Waits for the problem's stream and reports the input checks of the set-up
+ * calls since the last check (SR_ERR_NONFINITE). */
+sr_status sr_sync(sr_problem *p);
 
 /* Optimiser: run n_steps of {loss_and_grad; update} on params_dev in place.
  * The moment buffers and step counter live in the problem (sr_reset_optimizer

@@ -73,6 +73,8 @@ PROTOTYPES = {
     "sr_loss": ([c_void_p, c_void_p, P_double], c_int),
     "sr_loss_and_grad": ([c_void_p, c_void_p, P_double, c_void_p, c_void_p], c_int),
     "sr_loss_and_grad_host": ([c_void_p, c_void_p, P_double, c_void_p], c_int),
+    "sr_loss_and_grad_host_async": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "sr_sync": ([c_void_p], c_int),
     "sr_step": ([c_void_p, c_void_p, c_int, ctypes.POINTER(OptimCfg), c_void_p, P_double], c_int),
     "sr_reset_optimizer": ([c_void_p], c_int),
     "sr_get_state": ([c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_int64)], c_int),

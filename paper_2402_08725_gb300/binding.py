@@ -37,6 +37,12 @@ def _as_input(x, n_expected: int):
     return ctypes.c_void_p(a.ctypes.data), 0, a
 
 
+def _check_host_arrays(specs):
+    for a, n, dt, name in specs:
+        if not isinstance(a, np.ndarray) or a.dtype != dt or a.size < n or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"{name} must be a contiguous {np.dtype(dt).name} array of {n} values")
+
+
 def _cuda_f32(t: torch.Tensor, n: int, name: str):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
         raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
@@ -193,6 +199,22 @@ class Problem:
                                                  ctypes.c_void_p(grad_host.ctypes.data)), "sr_loss_and_grad_host")
         return loss.value, grad_host
 
+    def loss_and_grad_host_async(self, params_host, grad_host, loss_host):
+        """Queue the host-buffer evaluation without waiting (sr_loss_and_grad_host_async).
+        params_host, grad_host (n_params float32) and loss_host (one float64) are host arrays,
+        page-locked for the call to return at once; they are read or written until sync()."""
+        _check_host_arrays(((params_host, self.n_params, np.float32, "params_host"),
+                            (grad_host, self.n_params, np.float32, "grad_host"),
+                            (loss_host, 1, np.float64, "loss_host")))
+        nat.check(self.lib.sr_loss_and_grad_host_async(self.handle, ctypes.c_void_p(params_host.ctypes.data),
+                                                       ctypes.c_void_p(loss_host.ctypes.data),
+                                                       ctypes.c_void_p(grad_host.ctypes.data)),
+                  "sr_loss_and_grad_host_async")
+
+    def sync(self):
+        """Wait for the problem's stream and raise on the set-up's input checks (sr_sync)."""
+        nat.check(self.lib.sr_sync(self.handle), "sr_sync")
+
     def step(self, params: torch.Tensor, n_steps: int, cfg: nat.OptimCfg, losses: torch.Tensor | None = None,
              sync: bool = True) -> float | None:
         """n_steps optimiser updates in place (sr_step).  Returns the last loss, read back with a
@@ -336,11 +358,9 @@ class Batch:
         params_host, grad_host (n_params float32) and total_host (one float64) are host arrays,
         page-locked for the call to return at once (numpy views of pinned torch tensors); they are
         written or read until sync()."""
-        for a, n, dt, name in ((params_host, self.n_params, np.float32, "params_host"),
-                               (grad_host, self.n_params, np.float32, "grad_host"),
-                               (total_host, 1, np.float64, "total_host")):
-            if not isinstance(a, np.ndarray) or a.dtype != dt or a.size < n or not a.flags["C_CONTIGUOUS"]:
-                raise TypeError(f"{name} must be a contiguous {np.dtype(dt).name} array of {n} values")
+        _check_host_arrays(((params_host, self.n_params, np.float32, "params_host"),
+                            (grad_host, self.n_params, np.float32, "grad_host"),
+                            (total_host, 1, np.float64, "total_host")))
         nat.check(self.lib.sr_batch_loss_and_grad_host_async(self.handle, ctypes.c_void_p(params_host.ctypes.data),
                                                              ctypes.c_void_p(total_host.ctypes.data),
                                                              ctypes.c_void_p(grad_host.ctypes.data)),

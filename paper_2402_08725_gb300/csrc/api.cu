@@ -1164,9 +1164,48 @@ sr_status sr_destroy(sr_problem *p) {
     return SR_OK;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc'ed or registered), else null.
+static void *mapped_address(const void *host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Inputs in and results out of host memory.  From and to page-locked memory these are kernels
+// reading or writing its mapped address: a copy-engine transfer that waits on earlier work of its
+// stream (an evaluation, or kernels held back by a persistent launch of another stream) holds up,
+// in the engine's queue, the staging copies that later set-up calls issue on the internal stream
+// (measured: no overlap of the next step's inputs with this step's evaluation).
+static sr_status params_in(float *dev, const float *host, size_t n, cudaStream_t st) {  // host -> device
+    if (const float *m = static_cast<const float *>(mapped_address(host))) {
+        launch_host_copy(m, dev, (long long)n, nullptr, nullptr, st);
+        SR_CUDA(cudaGetLastError());
+        return SR_OK;
+    }
+    SR_CUDA(cudaMemcpyAsync(dev, host, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    return SR_OK;
+}
+
+static sr_status results_out(float *grad_host, const float *grad_dev, size_t n, double *total_host,
+                             const double *total_dev, cudaStream_t st) {
+    float *mg = static_cast<float *>(mapped_address(grad_host));
+    double *mt = static_cast<double *>(mapped_address(total_host));
+    if (mg) {
+        launch_host_copy(grad_dev, mg, (long long)n, mt ? total_dev : nullptr, mt, st);
+        SR_CUDA(cudaGetLastError());
+    } else {
+        SR_CUDA(cudaMemcpyAsync(grad_host, grad_dev, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    }
+    if (!mg || !mt) SR_CUDA(cudaMemcpyAsync(total_host, total_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return SR_OK;
+}
+
 static sr_status copy_in(sr_problem *p, float *dst, const float *src, size_t n, int on_device) {
-    SR_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            p->stream));
+    if (!on_device) return params_in(dst, src, n, p->stream);
+    SR_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
     return SR_OK;
 }
 
@@ -1451,44 +1490,6 @@ sr_status sr_loss(sr_problem *p, const float *params_dev, double *loss_host) {
     return sr_loss_and_grad(p, params_dev, loss_host, nullptr, p->plan->grad_int);
 }
 
-// The device address of page-locked host memory (cudaHostAlloc'ed or registered), else null.
-static void *mapped_address(const void *host) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
-}
-
-// Parameters in and results out of the host-buffer evaluations.  From and to page-locked memory
-// these are kernels reading or writing its mapped address: a copy-engine transfer queued behind
-// the evaluation would hold up, in the engine's queue, the staging copies that later set-up calls
-// issue on the internal stream (measured: no overlap of the next step's inputs with this step).
-static sr_status params_in(float *dev, const float *host, size_t n, cudaStream_t st) {
-    if (const float *m = static_cast<const float *>(mapped_address(host))) {
-        launch_host_copy(m, dev, (long long)n, nullptr, nullptr, st);
-        SR_CUDA(cudaGetLastError());
-        return SR_OK;
-    }
-    SR_CUDA(cudaMemcpyAsync(dev, host, sizeof(float) * n, cudaMemcpyHostToDevice, st));
-    return SR_OK;
-}
-
-static sr_status results_out(float *grad_host, const float *grad_dev, size_t n, double *total_host,
-                             const double *total_dev, cudaStream_t st) {
-    float *mg = static_cast<float *>(mapped_address(grad_host));
-    double *mt = static_cast<double *>(mapped_address(total_host));
-    if (mg) {
-        launch_host_copy(grad_dev, mg, (long long)n, mt ? total_dev : nullptr, mt, st);
-        SR_CUDA(cudaGetLastError());
-    } else {
-        SR_CUDA(cudaMemcpyAsync(grad_host, grad_dev, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
-    }
-    if (!mg || !mt) SR_CUDA(cudaMemcpyAsync(total_host, total_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
-    return SR_OK;
-}
-
 sr_status sr_loss_and_grad_host(sr_problem *p, const float *params_host, double *loss_host, float *grad_host) {
     sr_status st = check_ready(p);
     if (st != SR_OK) return st;
@@ -1503,6 +1504,26 @@ sr_status sr_loss_and_grad_host(sr_problem *p, const float *params_host, double 
     SR_CUDA(cudaStreamSynchronize(p->stream));
     if (p->pending_check && (st = check_flag(p)) != SR_OK) return st;
     if (!std::isfinite(*loss_host)) return fail(SR_ERR_NONFINITE, "the loss is not finite");
+    return SR_OK;
+}
+
+sr_status sr_loss_and_grad_host_async(sr_problem *p, const float *params_host, double *loss_host, float *grad_host) {
+    sr_status st = check_ready(p);
+    if (st != SR_OK) return st;
+    if (!params_host || !loss_host || !grad_host) return fail(SR_ERR_ARG, "NULL argument");
+    if ((st = ensure_plan(p)) != SR_OK) return st;
+    Plan *pl = p->plan;
+    if ((st = ensure_opt_buffers(pl)) != SR_OK) return st;
+    if (!pl->params_int && (st = pl->arena.alloc(&pl->params_int, pl->n_params)) != SR_OK) return st;
+    if ((st = params_in(pl->params_int, params_host, pl->n_params, p->stream)) != SR_OK) return st;
+    if ((st = sr_loss_and_grad(p, pl->params_int, nullptr, nullptr, pl->grad_int)) != SR_OK) return st;
+    return results_out(grad_host, pl->grad_int, pl->n_params, loss_host, pl->total, p->stream);
+}
+
+sr_status sr_sync(sr_problem *p) {
+    if (!p) return fail(SR_ERR_ARG, "problem is NULL");
+    SR_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->pending_check) return check_flag(p);
     return SR_OK;
 }
 

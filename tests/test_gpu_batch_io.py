@@ -193,3 +193,36 @@ def test_batch_set_scalar_paths_and_unaligned_host_buffers():
         x.close()
     for pr in pa + pb:
         pr.close()
+
+
+@pytest.mark.parametrize("kind", ["deconv", "psf"])
+def test_problem_async_host_evaluation_equals_synchronous(kind):
+    """sr_loss_and_grad_host_async + sr_sync give sr_loss_and_grad_host's loss and gradient bit
+    for bit, with the inputs set from page-locked memory (copied by kernels) in between."""
+    from paper_2402_08725_gb300.binding import Problem
+    if kind == "deconv":
+        fd = syn.small_deconv(90, E=4, N=16, f=2, K=13, M=2, J=3, lam=0.5)
+        pr = Problem.from_field(fd)
+        d, s, q0 = fd.d, fd.sigma, fd.params
+    else:
+        fd = syn.small_psf(seed=91, S=3, N=16, f=2, J=3, lam=1.0)
+        pr = Problem.from_psf(fd)
+        d, s, q0 = fd.t, fd.sigma, fd.params
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+    sets = [(pin(d * (1.0 + 0.2 * k)), pin(s), pin(q0 * (1.0 + 0.01 * k)).numpy()) for k in range(3)]
+    ref = []
+    for dk, sk, qk in sets:
+        pr.set_data(dk)
+        pr.set_noise(sk)
+        loss, g = pr.loss_and_grad_host(qk)
+        ref.append((loss, g.copy()))
+    outs = [(torch.empty(pr.n_params, dtype=torch.float32).pin_memory().numpy(),
+             torch.empty(1, dtype=torch.float64).pin_memory().numpy()) for _ in sets]
+    for (dk, sk, qk), (g, l) in zip(sets, outs):
+        pr.set_data(dk)
+        pr.set_noise(sk)
+        pr.loss_and_grad_host_async(qk, g, l)
+    pr.sync()
+    for (g, l), (rl, rg) in zip(outs, ref):
+        assert l[0] == rl and np.array_equal(g, rg)
+    pr.close()
