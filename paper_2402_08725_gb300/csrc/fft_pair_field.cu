@@ -17,27 +17,104 @@ namespace {
 // --- per-PSF and per-field transforms (two phases per block) ---------------------------------
 // Half spectra of the pair in Z: X_a at out_a, X_b at out_b (if any), rows of pitch HP with the pad
 // column zero; each value times W_L^((ky + kx) sh) (sh = 0: no shift).
+// The two half spectra of a pair transform Z = X_a + i X_b, in global layout [L][HP]:
+//   X_a(k) = (Z(k) + conj Z(-k)) / 2,  X_b(k) = (Z(k) - conj Z(-k)) / (2i),
+// each times W_L^((ky + kx) sh) when sh != 0 (the shift theorem); out_b may be null.  A thread
+// keeps one column kx (its physical columns and W_L^(kx sh) index) and walks the rows; the
+// twiddle of (ky + kx) sh mod L is read from the table, its index kept by additions.
 template <int L>
 __device__ void split_store(const float2 *Z, float2 *out_a, float2 *out_b, int sh, const float2 *tw) {
     using G = Pr<L>;
     constexpr int H = G::H, HP = G::HP, P = G::P;
-    for (int idx = threadIdx.x; idx < L * HP; idx += blockDim.x) {
-        const int ky = idx / HP, kx = idx - ky * HP;
+    const int rows = blockDim.x / HP;  // rows in parallel
+    const int kx = threadIdx.x % HP, ty = threadIdx.x / HP;
+    if (ty >= rows) return;
+    const bool live = kx < H;
+    const int cx = live ? kcol<L>(kx) : 0, cxm = live ? kcol<L>(neg_mod(kx, L)) : 0;
+    const int wx = (int)(((long long)kx * sh) % L);
+    const int wstep = (int)(((long long)rows * sh) % L);
+    int wi = (int)(((long long)ty * sh) % L) + wx;
+    if (wi >= L) wi -= L;
+    for (int ky = ty; ky < L; ky += rows) {
         float2 xa = make_float2(0.f, 0.f), xb = make_float2(0.f, 0.f);
-        if (kx < H) {
-            const float2 A = Z[krow<L>(ky) * P + kcol<L>(kx)];
-            const float2 B = Z[krow<L>(neg_mod(ky, L)) * P + kcol<L>(neg_mod(kx, L))];
+        if (live) {
+            const float2 A = Z[krow<L>(ky) * P + cx];
+            const float2 B = Z[krow<L>(neg_mod(ky, L)) * P + cxm];
             xa = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
             xb = make_float2(0.5f * (A.y + B.y), 0.5f * (B.x - A.x));
             if (sh) {
-                const float2 w = tw[((ky + kx) * sh) % L];
+                const float2 w = tw[wi];
                 xa = cmul(xa, w);
                 xb = cmul(xb, w);
             }
         }
-        out_a[idx] = xa;
-        if (out_b) out_b[idx] = xb;
+        out_a[ky * HP + kx] = xa;
+        if (out_b) out_b[ky * HP + kx] = xb;
+        wi += wstep;
+        if (wi >= L) wi -= L;
     }
+}
+
+// The forward transform along y of a pair whose rows y >= ylim are zero, with ylim <= L/2
+// (NZ = 8) or <= L/4 (NZ = 4) and R1 = 16: pass A's 16-point DFTs see non-zero inputs only at
+// n1 < NZ, so their first radix-4 stage reduces to one (NZ = 4) or two (NZ = 8) terms; pass B is
+// that of cols_fwd.  Same values as cols_fwd (the dropped terms are exact zeros).
+template <int L, int NZ>
+__device__ __noinline__ void cols_fwd_lead(float2 *Z, int ylim, const float2 *TWL) {
+    using G = Pr<L>;
+    constexpr int R1 = G::R1, R2 = G::R2, P = G::P;
+    static_assert(R1 == 16 && (NZ == 4 || NZ == 8), "pruned column pass: R1 = 16, NZ = 4 or 8");
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < R2 * L; t += nt) {
+        const int p = t % L, n2 = t / L;
+        float2 *z = Z + pcol<L>(p) + n2 * P;
+        float2 v[NZ];
+#pragma unroll
+        for (int n1 = 0; n1 < NZ; ++n1) v[n1] = n2 + R2 * n1 < ylim ? z[R2 * n1 * P] : make_float2(0.f, 0.f);
+        // 16 = 4 x 4: first stage over m1 of v[4 m1 + m2] (only m1 < NZ / 4 non-zero), twiddles
+        // W_16^(m2 k1), then 4-point DFTs over m2; X[k1 + 4 k2] is output k1 + 4 k2 of the 16
+        float2 a[16];
+#pragma unroll
+        for (int m2 = 0; m2 < 4; ++m2) {
+            float2 q[4];
+            if (NZ == 4) {
+                q[0] = q[1] = q[2] = q[3] = v[m2];
+            } else {
+                const float2 t0 = v[m2], t1 = v[4 + m2];
+                const float2 t1i = make_float2(t1.y, -t1.x);  // -i t1 (forward W_4)
+                q[0] = cadd(t0, t1);
+                q[1] = cadd(t0, t1i);
+                q[2] = csub(t0, t1);
+                q[3] = csub(t0, t1i);
+            }
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) a[k1 * 4 + m2] = twiddle<16, false>(q[k1], m2 * k1);
+        }
+        float2 out[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 u[4];
+#pragma unroll
+            for (int m2 = 0; m2 < 4; ++m2) u[m2] = a[k1 * 4 + m2];
+            dft<4, false>(u);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) out[k1 + 4 * k2] = u[k2];
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) z[R2 * k1 * P] = k1 == 0 ? out[0] : cmul(out[k1], TWL[k1 * R2 + n2]);
+    }
+    __syncthreads();
+    for (int t = tid; t < R1 * L; t += nt) {
+        const int p = t % L, k1 = t / L;
+        float2 *z = Z + pcol<L>(p) + R2 * k1 * P;
+        float2 v[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = z[n2 * P];
+        dft<R2, false>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) z[k2 * P] = v[k2];
+    }
+    __syncthreads();
 }
 
 // Spectra of the folded PSF kernels (at set_psfs): item = epoch * n_pairs + pair of phases.  The
@@ -64,7 +141,13 @@ __device__ __noinline__ void kappa_item_pair(const FieldDev &fd, const float *__
     }
     __syncthreads();
     rows_fwd<L>(Z, 1, Tk, Tk, TWL);
-    cols_fwd<L>(Z, 1, Tk, TWL);
+    if constexpr (Pr<L>::R1 == 16) {
+        if (4 * Tk <= L) cols_fwd_lead<L, 4>(Z, Tk, TWL);
+        else if (2 * Tk <= L) cols_fwd_lead<L, 8>(Z, Tk, TWL);
+        else cols_fwd<L>(Z, 1, Tk, TWL);
+    } else {
+        cols_fwd<L>(Z, 1, Tk, TWL);
+    }
     const int sh = ((fd.tau_lo % L) + L) % L;  // tau_lo mod L
     float2 *out = khat + ((long long)i * nph + pa) * L * HP;
     split_store<L>(Z, out, kb ? out + L * HP : nullptr, sh, fd.fft_tw);
