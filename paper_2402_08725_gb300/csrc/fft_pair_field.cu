@@ -395,20 +395,46 @@ sr_status configure_fft_pair_field(int optin, int *field_limit) {
     return SR_OK;
 }
 
+// Block size of the kernel-spectra launches: of 512, 256 and 128 threads, the one with the most
+// threads resident per SM at this shared-memory size, ties to the smaller block (independent blocks
+// cover each other's barriers between the passes).  Every output of an item is computed the same
+// way whatever the block size, so the spectra do not depend on it.
+template <typename K>
+static void kappa_block(K kernel, int smem, int *threads, int *occ) {
+    *threads = kFftThreads;
+    *occ = 1;
+    int best = 0;
+    for (int t : {kFftThreads, kFftThreads / 2, kFftThreads / 4}) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, t, smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (o >= 1 && o * t >= best) {
+            best = o * t;
+            *threads = t;
+            *occ = o;
+        }
+    }
+}
+
 sr_status launch_fft_kappa_pair_batch(const FieldDev *fields, const int2 *items, int n_items, int L, int n_sms,
                                       cudaStream_t st) {
     if (n_items <= 0) return SR_OK;
     const int smem = fft_pair_field_smem(L);
-    int occ = 0;
-    SR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fft_kappa_pair_batch_kernel, kFftThreads, smem));
-    const int grid = std::min(n_items, std::max(occ, 1) * n_sms);
-    fft_kappa_pair_batch_kernel<<<grid, kFftThreads, smem, st>>>(fields, items, n_items);
+    int threads = 0, occ = 0;
+    kappa_block(fft_kappa_pair_batch_kernel, smem, &threads, &occ);
+    const int grid = std::min(n_items, occ * n_sms);
+    fft_kappa_pair_batch_kernel<<<grid, threads, smem, st>>>(fields, items, n_items);
     return SR_OK;
 }
 
 void launch_fft_kappa_pair(const FieldDev &fd, const float *kappa, float2 *khat, cudaStream_t st) {
     const int n_items = fd.E * ((fd.f * fd.f + 1) / 2);
-    fft_kappa_pair_kernel<<<n_items, kFftThreads, fft_pair_field_smem(fd.fft_L), st>>>(fd, kappa, khat);
+    const int smem = fft_pair_field_smem(fd.fft_L);
+    int threads = 0, occ = 0;
+    kappa_block(fft_kappa_pair_kernel, smem, &threads, &occ);
+    fft_kappa_pair_kernel<<<n_items, threads, smem, st>>>(fd, kappa, khat);
 }
 
 void launch_fft_hhat_pair(const FieldDev *fields, const int *fft_fields, int n_fft_fields, int max_pairs, int smem,
