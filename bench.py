@@ -63,6 +63,9 @@ def parse():
                     help="convolution form of every field (auto: timed per shape on first use)")
     ap.add_argument("--fields", type=int, default=0,
                     help="config4 only: evaluate the first FIELDS fields (a smaller case for profiling)")
+    ap.add_argument("--schedule", default="",
+                    help="EPOCHS,PAIRS: the transform form's schedule instead of tuning it (profiling runs, "
+                         "whose timings under a profiler would mislead the tuner)")
     return ap.parse_args()
 
 
@@ -692,7 +695,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         batch = Batch(probs, stream=stream) if probs else None
         # the transform form's schedule (epochs per work item, pair cap), timed on the batch
-        schedule = batch.tune_schedule() if batch is not None else None
+        schedule = None
+        if batch is not None and args.schedule:
+            ce, cg = (int(x) for x in args.schedule.split(","))
+            batch.set_schedule(ce, cg)
+            schedule = {"epochs_per_item": ce, "pairs_per_group": cg, "ms_per_eval": None, "fixed": True}
+        elif batch is not None:
+            schedule = batch.tune_schedule()
         # the PSF fit is independent of the batch: it runs on its own stream, forked from and
         # joined to `stream` in every step, so that its small launches overlap the batch's
         psf_stream = torch.cuda.Stream()
