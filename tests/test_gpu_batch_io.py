@@ -226,3 +226,24 @@ def test_problem_async_host_evaluation_equals_synchronous(kind):
     for (g, l), (rl, rg) in zip(outs, ref):
         assert l[0] == rl and np.array_equal(g, rg)
     pr.close()
+
+
+def test_queued_evaluation_from_pageable_buffers():
+    """sr_batch_loss_and_grad_host_async with ordinary (pageable) numpy buffers takes the copy
+    path instead of the mapped-memory kernels and still gives the synchronous result bit for bit;
+    sr_batch_sync with nothing queued returns at once."""
+    fields = _fields()
+    pr, b = _batch(fields, ["fft", "direct", "fft", "auto"])
+    b.sync()
+    q = b.pack([fd.params for fd in fields])
+    tot, gref = b.loss_and_grad_host(q)
+    g = np.empty(b.n_params, dtype=np.float32)
+    t = np.empty(1, dtype=np.float64)
+    b.loss_and_grad_host_async(q, g, t)
+    b.sync()
+    assert t[0] == tot and np.array_equal(g, gref)
+    with pytest.raises(TypeError):
+        b.loss_and_grad_host_async(q.astype(np.float64), g, t)
+    b.close()
+    for p_ in pr:
+        p_.close()
