@@ -221,32 +221,69 @@ __device__ __noinline__ void hhat_pair(const FieldDev &fd, const float *__restri
 // dL/dh for the transform fields: the chunk accumulators of two phases summed in a fixed order,
 // joined as Z = A_a + i A_b on the whole plane (Hermitian extension of each half spectrum),
 // transformed back, plus the prior's gradient.
-// The sum over a field's work items of their adjoint accumulators at one spectral point p (phase,
-// row ky, column kx < H), in the order of hgrad_pair's own loop (four interleaved partial sums,
-// item c into c mod 4, combined in a fixed order), written over the first item's accumulator: one
-// thread per point, so that fields with many items are summed by many blocks.
+// The sum over a field's work items of their adjoint accumulators at one spectral point, in a
+// fixed order shared by acc_reduce and hgrad_pair: 16 interleaved partial sums (item c into
+// c mod 16, each in increasing c), combined as a fixed binary tree.
+constexpr int kAccParts = 16;
+
+__device__ __forceinline__ float2 acc_tree(const float2 *q) {  // q[0..3] of one group of four parts
+    return cadd(cadd(q[0], q[1]), cadd(q[2], q[3]));
+}
+
+// Parts 4t .. 4t+3 of the sum at one point (t = 0..3), over items c = u, u + 16, ...
+__device__ __forceinline__ float2 acc_group(const float2 *__restrict__ ac, long long cs, int n_chunks, int t) {
+    float2 q[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[v] = make_float2(0.f, 0.f);
+    for (int c = 4 * t; c < n_chunks; c += kAccParts) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (c + v < n_chunks) q[v] = cadd(q[v], __ldg(&ac[(c + v) * cs]));
+    }
+    return acc_tree(q);
+}
+
+// The whole sum at one point by one thread: the 16 parts advanced together (16 loads in flight),
+// each in increasing c as in acc_group, then the same trees.
+__device__ __forceinline__ float2 acc_sum(const float2 *__restrict__ ac, long long cs, int n_chunks) {
+    float2 q[kAccParts];
+#pragma unroll
+    for (int u = 0; u < kAccParts; ++u) q[u] = make_float2(0.f, 0.f);
+    for (int c = 0; c < n_chunks; c += kAccParts) {
+#pragma unroll
+        for (int u = 0; u < kAccParts; ++u)
+            if (c + u < n_chunks) q[u] = cadd(q[u], __ldg(&ac[(c + u) * cs]));
+    }
+    float2 g[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) g[t] = acc_tree(q + 4 * t);
+    return acc_tree(g);
+}
+
+// Four threads per spectral point p (phase, row ky, column kx < H), lanes 4i .. 4i+3 of a warp:
+// thread t sums parts 4t .. 4t+3, the tree over the four groups is taken by shuffles, and the
+// point's sum is written over the first item's accumulator.  Many short chains instead of one
+// thread walking every item, so that fields with many items are summed by many blocks.
 template <int L>
-__device__ __forceinline__ void acc_reduce(const FieldDev &fd, float2 *__restrict__ acc_all, int p) {
+__device__ __forceinline__ void acc_reduce(const FieldDev &fd, float2 *__restrict__ acc_all, int p, int t) {
     using G = Pr<L>;
     constexpr int H = G::H, HP = G::HP, LHP = L * HP;
     const int nph = fd.f * fd.f;
-    if (p >= nph * L * H) return;
-    const int ph = p / (L * H), r = p - ph * (L * H), ky = r / H, kx = r - ky * H;
-    const int n_chunks = fd.fft_n_chunks;
+    const bool live = p < nph * L * H;
+    const int pp = live ? p : 0;
+    const int ph = pp / (L * H), r = pp - ph * (L * H), ky = r / H, kx = r - ky * H;
     const long long cs = (long long)nph * LHP;
     float2 *ac = acc_all + fd.fft_acc_off + (long long)ph * LHP + ky * HP + kx;
-    float2 p4[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) p4[u] = make_float2(0.f, 0.f);
-    int c = 0;
-    for (; c + 4 <= n_chunks; c += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-        if (c + u < n_chunks) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
-    ac[0] = cadd(cadd(p4[0], p4[1]), cadd(p4[2], p4[3]));
+    float2 g = live ? acc_group(ac, cs, fd.fft_n_chunks, t) : make_float2(0.f, 0.f);
+    // (g0 + g1) + (g2 + g3) across the four lanes of the point
+    float2 o;
+    o.x = __shfl_down_sync(0xffffffffu, g.x, 1, 4);
+    o.y = __shfl_down_sync(0xffffffffu, g.y, 1, 4);
+    g = cadd(g, o);
+    o.x = __shfl_down_sync(0xffffffffu, g.x, 2, 4);
+    o.y = __shfl_down_sync(0xffffffffu, g.y, 2, 4);
+    g = cadd(g, o);
+    if (live && t == 0) ac[0] = g;
 }
 
 // reduced: the items' accumulators were already summed into the first item's (acc_reduce)
@@ -272,20 +309,9 @@ __device__ __noinline__ void hgrad_pair(const FieldDev &fd, const float2 *__rest
         for (int w = 0; w < 2; ++w) {
             s[w] = make_float2(0.f, 0.f);
             if (w == 1 && !hasb) continue;
-            // four interleaved partial sums (chunk c into c mod 4) combined in a fixed order
+            // the items' sum in acc_reduce's order (a single item: its accumulator as it is)
             const float2 *ac = base + (long long)(w ? pb : pa) * LHP + ky * HP + kx;
-            float2 p4[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) p4[u] = make_float2(0.f, 0.f);
-            int c = 0;
-            for (; c + 4 <= n_chunks; c += 4) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (c + u < n_chunks) p4[u] = cadd(p4[u], __ldg(&ac[(c + u) * cs]));
-            s[w] = cadd(cadd(p4[0], p4[1]), cadd(p4[2], p4[3]));
+            s[w] = n_chunks == 1 ? __ldg(ac) : acc_sum(ac, cs, n_chunks);
         }
         const float2 A = s[0], B = s[1];
         const int r = krow<L>(ky), cx = kcol<L>(kx);
@@ -340,11 +366,12 @@ fft_acc_reduce_kernel(const FieldDev *__restrict__ fields, const int *__restrict
                       float2 *__restrict__ acc_all) {
     const FieldDev &fd = fields[fft_fields[blockIdx.y]];
     if (fd.fft_n_chunks <= 1) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = g >> 2, t = g & 3;  // four lanes per point
     switch (fd.fft_L) {
-#define SR_PR_RCASE(LL)                  \
-    case LL:                             \
-        acc_reduce<LL>(fd, acc_all, p);  \
+#define SR_PR_RCASE(LL)                     \
+    case LL:                                \
+        acc_reduce<LL>(fd, acc_all, p, t);  \
         break;
         SR_PR_SIZES(SR_PR_RCASE)
 #undef SR_PR_RCASE
@@ -448,7 +475,7 @@ int launch_fft_hgrad_pair(const FieldDev *fields, const int *fft_fields, int n_f
     // one thread per spectral point; the result is the same either way (same order of the sums)
     const bool reduce = (long long)n_fft_fields * max_pairs < n_sms;
     if (reduce)
-        fft_acc_reduce_kernel<<<dim3((max_points + 255) / 256, n_fft_fields), 256, 0, st>>>(fields, fft_fields, acc);
+        fft_acc_reduce_kernel<<<dim3((4 * max_points + 255) / 256, n_fft_fields), 256, 0, st>>>(fields, fft_fields, acc);
     fft_hgrad_pair_kernel<<<dim3(max_pairs, n_fft_fields), kFftThreads, smem, st>>>(fields, fft_fields, acc, grad,
                                                                                      reduce ? 1 : 0);
     return reduce ? 2 : 1;

@@ -437,3 +437,28 @@ def test_wide_field_starlet_forms_match_oracle(E, N, f, K, M, J):
     loss, g = _run(fd, conv_mode="direct")
     r = check_deconv(fd, loss, g)
     print("wide starlet", N, f, J, r)
+
+
+def test_item_sums_alone_and_in_a_large_batch_bitwise():
+    """A transform-form field of many work items (300 epochs: 19 items of 16) evaluated alone
+    (few blocks: its items' accumulators are pre-summed, four lanes per spectral point) and inside
+    a batch with enough transform fields to skip the pre-sum (each block sums its points itself)
+    gives the same loss and gradient bit for bit: both take the items in the same 16-part order."""
+    from paper_2402_08725_gb300.binding import Batch, Problem
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    big = syn.small_deconv(seed=611, E=300, N=16, f=2, K=9, M=1, J=3, lam=1.0)
+    small = [syn.small_deconv(seed=620 + i, E=2, N=12, f=2, K=7, M=1, J=3, lam=1.0) for i in range(n_sms // 2 + 2)]
+    single = Problem.from_field(big, conv_mode="fft")
+    l1, g1 = single.loss_and_grad(torch.from_numpy(big.params).cuda())
+    g1 = g1.clone()
+    check_deconv(big, l1, g1.cpu().numpy())
+    probs = [Problem.from_field(fd, conv_mode="fft") for fd in [big] + small]
+    batch = Batch(probs)
+    P = torch.from_numpy(batch.pack([fd.params for fd in [big] + small])).cuda()
+    losses = torch.empty(len(probs), dtype=torch.float64, device="cuda")
+    _, grad = batch.loss_and_grad(P, losses=losses)
+    assert losses[0].item() == l1
+    assert torch.equal(grad[:big.n_params], g1)
+    batch.close()
+    for q in probs + [single]:
+        q.close()
