@@ -584,13 +584,14 @@ finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ 
     const int E = fd.E, M = fd.M, F = fd.F, f = fd.f;
     // point-source prior of the field (Eq. 11, third term), if it has one
     const FieldDev *sd = (pts_fields && fd.pts > 0) ? &pts_fields[fd.pts - 1] : nullptr;
-    double chi = 0.0, l1 = 0.0;
+    // four interleaved partial sums per thread (slot s into (s / blockDim) mod 4), combined in a
+    // fixed order: wide grids have tens of thousands of prior partials per field, whose loads a
+    // single dependent chain per thread would serialise
     const long long nt = (long long)E * fd.n_tiles;
-    for (long long s = threadIdx.x; s < nt; s += blockDim.x) chi += chi_part[fd.tile_slot + s];
     const long long nl = (long long)(fd.J - 1) * fd.n_chunks;
-    for (long long s = threadIdx.x; s < nl; s += blockDim.x) l1 += l1_part[fd.l1_slot + s];
-    if (sd)
-        for (long long s = threadIdx.x; s < nl; s += blockDim.x) l1 += l1_pts[sd->l1_slot + s];
+    double chi = strided_sum4(chi_part + fd.tile_slot, nt);
+    double l1 = strided_sum4(l1_part + fd.l1_slot, nl);
+    if (sd) l1 += strided_sum4(l1_pts + sd->l1_slot, nl);
     block_sum2(chi, l1, s_red);
     if (threadIdx.x == 0) losses[blockIdx.x] = chi + l1;
     float *g = grad + fd.param_off + (long long)F * F;  // a block
@@ -621,10 +622,21 @@ finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ 
         }
     }
     float *gd = gc + 2 * M;
+    // d/ddelta_i: the epoch's sources in four interleaved partial sums (k mod 4, each in increasing
+    // k), combined in a fixed order, so that a thread's loads are in flight together
     for (int s = threadIdx.x; s < 2 * E; s += blockDim.x) {
         const int i = s >> 1, ax = s & 1;
-        double acc = 0.0;
-        for (int k = 0; k < M; ++k) acc += (double)ps_du[2 * (fd.ps_slot + (long long)i * M + k) + ax];
+        const float *pu = ps_du + 2 * (fd.ps_slot + (long long)i * M) + ax;
+        double p[4] = {0.0, 0.0, 0.0, 0.0};
+        int k = 0;
+        for (; k + 4 <= M; k += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] += (double)pu[2 * (k + u)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k + u < M) p[u] += (double)pu[2 * (k + u)];
+        const double acc = (p[0] + p[1]) + (p[2] + p[3]);
         gd[s] = (float)(f * acc) + ((hs && fd.translate) ? hs[fd.hs_off + s] : 0.f);
     }
     float *gg = gd + 2 * E;
@@ -633,9 +645,17 @@ finalize_kernel(const FieldDev *__restrict__ fields, const double *__restrict__ 
     // their loads are in flight together
     if (fd.n_tiles <= 32) {
         for (int i = threadIdx.x; i < E; i += blockDim.x) {
-            double acc = 0.0;
-            for (int tt = 0; tt < fd.n_tiles; ++tt) acc += se_part[fd.tile_slot + (long long)i * fd.n_tiles + tt];
-            gg[i] = (float)((double)(f * f) * acc);
+            const double *sp = se_part + fd.tile_slot + (long long)i * fd.n_tiles;
+            double p[4] = {0.0, 0.0, 0.0, 0.0};
+            int tt = 0;
+            for (; tt + 4 <= fd.n_tiles; tt += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) p[u] += sp[tt + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (tt + u < fd.n_tiles) p[u] += sp[tt + u];
+            gg[i] = (float)((double)(f * f) * ((p[0] + p[1]) + (p[2] + p[3])));
         }
         return;
     }

@@ -12,6 +12,23 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// This thread's share of sum_{s < n} v[s] over the block (slots s = tid + k blockDim): four
+// interleaved partial sums (k mod 4), each in increasing s, combined as (p0 + p1) + (p2 + p3), so
+// that four loads per thread are in flight; the same result for the same block size.
+__device__ __forceinline__ double strided_sum4(const double *__restrict__ v, long long n) {
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long b = blockDim.x;
+    long long s = threadIdx.x;
+    for (; s + 3 * b < n; s += 4 * b) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] += v[s + u * b];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (s + u * b < n) p[u] += v[s + u * b];
+    return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
 // Deterministic block sum of two doubles (fixed shuffle tree, warps summed in order).
 __device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[kThreads / 32]) {
     a = warp_sum(a);
