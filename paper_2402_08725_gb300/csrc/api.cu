@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -104,20 +105,33 @@ static int g_num_sms = 0;
 static int g_fft_smem_limit = 0;  // dynamic shared memory the transform kernels can take
 static int g_fx_smem_limit = 0;   // ... and the per-epoch chunk kernel
 
+// The limits are published (g_dev_ready, set last) only once every kernel is configured; host
+// threads making their first calls together configure once, under the lock.
+static std::mutex g_dev_mutex;
+static std::atomic<bool> g_dev_ready{false};
+
 static sr_status device_limits() {
-    if (g_smem_optin >= 0) return SR_OK;
-    int dev = 0;
+    if (g_dev_ready.load(std::memory_order_acquire)) return SR_OK;
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if (g_dev_ready.load(std::memory_order_relaxed)) return SR_OK;
+    int dev = 0, optin = 0, sms = 0;
     SR_CUDA(cudaGetDevice(&dev));
-    SR_CUDA(cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    SR_CUDA(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    SR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    SR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     // reserve the static shared memory of the tile kernels
-    const int dyn = g_smem_optin - kTileStaticReserve;
+    const int dyn = optin - kTileStaticReserve;
     sr_status s = configure_tile_kernels(dyn, dyn);
     if (s != SR_OK) return s;
-    s = configure_fft_pair(g_smem_optin, &g_fx_smem_limit, &g_fft_smem_limit);
+    int fx = 0, fft = 0;
+    s = configure_fft_pair(optin, &fx, &fft);
     if (s != SR_OK) return s;
-    s = configure_fft_big(g_smem_optin);
+    s = configure_fft_big(optin);
     if (s != SR_OK) return s;
+    g_smem_optin = optin;
+    g_num_sms = sms;
+    g_fx_smem_limit = fx;
+    g_fft_smem_limit = fft;
+    g_dev_ready.store(true, std::memory_order_release);
     return SR_OK;
 }
 

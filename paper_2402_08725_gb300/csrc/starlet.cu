@@ -27,6 +27,7 @@
 //    which hold every mirror preimage its row gather reaches).
 // Fields deeper than a level skip it.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "ffsum.cuh"
@@ -581,8 +582,8 @@ int starlet_comb_rows_bits(const int *F, const int *J, int n, int n_sms) {
 
 int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, const ChunkItem *chunks,
                    int n_chunks, int Jmax, const float *params, double *l1_part, cudaStream_t st) {
-    static bool configured = false;
-    if (!configured) {  // the band and tile kernels take their budgets of dynamic shared memory
+    static std::once_flag configured;  // host threads evaluating at once configure the kernels once
+    std::call_once(configured, [] {  // the band and tile kernels take their budgets of dynamic shared memory
         cudaFuncSetAttribute(starlet_band_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
         cudaFuncSetAttribute(starlet_band_adj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
         cudaFuncSetAttribute(starlet_tile_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmemBytes);
@@ -595,8 +596,7 @@ int launch_starlet(const FieldDev *fields, int n_fields, int Fmax, int forms, co
         cudaFuncSetAttribute(starlet_comb_adj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
         cudaFuncSetAttribute(starlet_comb_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
         cudaFuncSetAttribute(starlet_comb_adj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBandSmemBytes);
-        configured = true;
-    }
+    });
     const bool bands = (forms & 1) != 0, tiles = (forms & 2) != 0;
     const bool combs = (forms & 8) != 0, map = (forms & kStarletMapBit) != 0;
     // comb bands: s combs of comb_chunks blocks at level j; staging of cr + 4 (forward) or
