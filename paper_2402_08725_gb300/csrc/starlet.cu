@@ -27,6 +27,7 @@
 //    which hold every mirror preimage its row gather reaches).
 // Fields deeper than a level skip it.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -556,12 +557,14 @@ starlet_tile_adj_kernel(const FieldDev *__restrict__ fields, const float *__rest
 int starlet_field_form(int F, int J) { return starlet_form(F, J); }
 
 int starlet_forms_single(int F, int J, bool map) {
-    static int sms = 0;
+    static std::atomic<int> sms_cached{0};  // the SM count, looked up once (any thread may store it)
+    int sms = sms_cached.load(std::memory_order_relaxed);
     if (sms <= 0) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                        cudaSuccess || sms <= 0)
             sms = 1;
+        sms_cached.store(sms, std::memory_order_relaxed);
     }
     const int forms = (1 << starlet_form(F, J)) | (map ? kStarletMapBit : 0);
     return forms | starlet_comb_rows_bits(&F, &J, 1, sms);
