@@ -68,3 +68,30 @@ def test_no_nvml_no_smi_gives_none(monkeypatch):
     cs = bench.ClockSampler(0)
     cs.start()
     assert cs.stop() is None
+
+
+def test_clock_summary_from_fake_nvidia_smi(monkeypatch, tmp_path):
+    """Without NVML the sampler reads nvidia-smi's CSV (a fake on PATH here): median and maximum
+    SM clock, and every throttle reason reported Active."""
+    bench = _bench()
+
+    def boom(idx):
+        raise OSError("no NVML")
+    monkeypatch.setattr(bench, "_NvmlClocks", boom)
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 1950, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ.get('PATH', '')}")
+    cs = bench.ClockSampler(0)
+    cs.start()
+    time.sleep(0.5)
+    out = cs.stop()
+    assert out is not None
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert "nvidia-smi" in out["source"]
